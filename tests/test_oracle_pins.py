@@ -1,0 +1,336 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (CPU only).
+
+Each test ties an oracle function to something other than itself: values the paper
+prints (tests/golden), closed forms, an independent numerical integration, invariants,
+brute force on tiny inputs, and exactness of the eleven-grid bookkeeping on shapes
+that 3-point interpolation reproduces exactly. The last block plants plausible
+mistakes in the oracle and checks that a pin fails.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate, special
+
+from oracle import marfa_oracle as O
+from workloads import LINE_DTYPE, config0_tiny, tiny_workload
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "grid_and_tables.txt")
+
+
+def golden():
+    d = {}
+    for line in open(GOLDEN):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            k, v = line.split()
+            d[k] = v
+    return d
+
+
+# ------------------------------------------------------------ paper-printed constants
+def test_grid_constants_from_paper():
+    g = golden()
+    # Sec. 2.4 / App. A: 20481 finest nodes per 10 cm^-1 (both ends included)
+    assert O.num_points(4000.0, 4010.0) == int(g["fine_nodes_per_10cm"])
+    assert O.num_points(10.0, 20.0) == int(g["fine_nodes_per_10cm"])
+    # N_i = 10 * 2^(i-1) + 1 nodes of grid i in a 10 cm^-1 interval
+    for i, key in ((1, "grid_nodes_1"), (2, "grid_nodes_2"), (10, "grid_nodes_10")):
+        nodes = (10 * 2 ** O.FIX_BITS) // O.step_fx(i) + 1
+        assert nodes == int(g[key])
+    # the finest step is 10 / (N - 1)
+    assert 2.0 ** -O.FINE_BITS == 10.0 / (int(g["fine_nodes_per_10cm"]) - 1)
+    # App. B record length
+    assert LINE_DTYPE.itemsize == int(g["line_record_bytes"])
+
+
+def test_pt_table_layout_from_paper():
+    g = golden()
+    assert O.pt_record_number(7564.0) == int(g["record_of_7564"])
+    assert O.pt_table_name(1) == g["name_of_level_1"]
+    assert O.pt_table_name(65) == g["name_of_level_65"]
+    k = np.arange(2 * (O.PT_NT - 1) + 1, dtype=np.float32)
+    img = np.frombuffer(O.pt_table_bytes(20.0, 40.0, k), dtype="<f4")
+    # records 2 and 3 (1-based) cover [20, 30] and [30, 40]; record 1 is zero-filled
+    assert len(img) == 3 * O.PT_NT
+    assert np.all(img[:O.PT_NT] == 0)
+    assert img[O.PT_NT] == 0.0 and img[2 * O.PT_NT - 1] == 20480.0
+    assert img[2 * O.PT_NT] == 20480.0  # shared boundary node repeated
+    assert img[-1] == 40960.0
+
+
+# ------------------------------------------------------------ Voigt closed forms and integral
+def test_voigt_doppler_limit():
+    x = np.linspace(-6, 6, 97)
+    assert np.allclose(O.voigt_K(x, 0.0), np.exp(-x * x), rtol=1e-13, atol=0)
+
+
+def test_voigt_at_centre_is_erfcx():
+    y = np.geomspace(1e-4, 1e3, 60)
+    assert np.allclose(O.voigt_K(0.0, y), special.erfcx(y), rtol=1e-13)
+
+
+@pytest.mark.parametrize("x,y", [(0.3, 0.01), (2.5, 0.2), (4.0, 1e-3), (7.0, 0.5), (1.0, 3.0),
+                                 (30.0, 2.0), (0.0, 0.05)])
+def test_voigt_matches_direct_integration_of_eq8(x, y):
+    # Eq. (8) with t = x + y tan(theta): K = (1/pi) int exp(-(x + y tan th)^2) dth
+    f = lambda th: math.exp(-(x + y * math.tan(th)) ** 2)
+    th0 = -math.atan(x / y)
+    val = (integrate.quad(f, -math.pi / 2, th0, epsabs=0, epsrel=1e-13, limit=400)[0]
+           + integrate.quad(f, th0, math.pi / 2, epsabs=0, epsrel=1e-13, limit=400)[0]) / math.pi
+    assert O.voigt_K(x, y) == pytest.approx(val, rel=1e-10)
+
+
+def test_voigt_large_y_is_lorentz():
+    x = np.linspace(-50, 50, 41)
+    y = 1e4
+    assert np.allclose(O.voigt_K(x, y), y / (math.sqrt(math.pi) * (x * x + y * y)), rtol=1e-7)
+
+
+def test_shapes_peak_values_and_unit_integral():
+    gL, aD = 0.07, 0.004
+    zero = np.zeros(1, dtype=np.int64)
+    fL = O.profile("lorentz", zero, 1.0, gL, aD, False)[0]
+    fG = O.profile("doppler", zero, 1.0, gL, aD, False)[0]
+    fV = O.profile("voigt", zero, 1.0, gL, aD, False)[0]
+    assert fL == pytest.approx(1.0 / (math.pi * gL), rel=1e-14)          # Eq. (4) at centre
+    assert fG == pytest.approx(math.sqrt(math.log(2) / math.pi) / aD, rel=1e-14)  # Eq. (5)
+    y = math.sqrt(math.log(2)) * gL / aD
+    assert fV == pytest.approx(math.sqrt(math.log(2) / math.pi) / aD * special.erfcx(y), rel=1e-12)
+    # unit integrals on a fine grid: Lorentz with cut-off c integrates to (2/pi) atan(c / g)
+    h = 2.0 ** -14
+    d = np.arange(-30 * 2 ** 14, 30 * 2 ** 14 + 1, dtype=np.int64) * (2 ** O.FIX_BITS // 2 ** 14)
+    for shape, expect in (("lorentz", 2 / math.pi * math.atan(30 / gL)), ("doppler", 1.0)):
+        v = O.profile(shape, d, 1.0, gL, aD, False)
+        assert integrate.trapezoid(v, dx=h) == pytest.approx(expect, rel=2e-7)
+    v = O.profile("voigt", d, 1.0, gL, aD, False)
+    # Voigt tails beyond 30 cm^-1 behave as the Lorentz tails
+    assert integrate.trapezoid(v, dx=h) == pytest.approx(2 / math.pi * math.atan(30 / gL), rel=1e-5)
+
+
+def test_appendix_c_asymptote():
+    g = golden()
+    x = float(g["voigt_lorentz_x"])
+    for y in (1e-3, 1e-2, 0.1):
+        K = O.voigt_K(x, y)
+        lor = y / (math.sqrt(math.pi) * (x * x + y * y))
+        assert abs(K / (lor * (1 + 1.5 / x ** 2)) - 1) < float(g["voigt_asymptote_tolerance"])
+        assert abs(K / lor - 1) < float(g["voigt_asymptote_tolerance"])
+
+
+# ------------------------------------------------------------ spectroscopy
+def _one_line(nu0=2349.0, S=1e-20, ga=0.07, gs=0.09, E=500.0, n=0.7, d=-0.003):
+    ln = np.zeros(1, dtype=LINE_DTYPE)
+    ln[0] = (nu0, S, ga, gs, E, n, 21, d)
+    return ln
+
+
+def _wl_one(T, p, vmr=1.0, units="sigma", **kw):
+    wl = tiny_workload(0, 5, 2300.0, 2400.0, 25.0, T=(T,), p=(p,), units=units)
+    wl = wl.with_(lines=_one_line(**kw), vmr=np.full((1, 1), vmr))
+    return wl
+
+
+def test_spectroscopy_reference_identities():
+    ln = _one_line()
+    wl = _wl_one(296.0, 0.7, vmr=0.3)
+    P = O.level_params(wl, 0)
+    assert P["S_T"][0] == pytest.approx(float(ln["S296"][0]), rel=1e-14)
+    assert P["gamma_L"][0] == pytest.approx(float(ln["gamma_air"][0]) * 0.7 * 0.7
+                                            + float(ln["gamma_self"][0]) * 0.7 * 0.3, rel=1e-14)
+    assert P["nu_shift"][0] == pytest.approx(2349.0 + float(ln["delta_air"][0]) * 0.7, rel=1e-15)
+    # Doppler HWHM from SI constants with the atomic mass unit (independent route)
+    amu = 1.66053906660e-27
+    aD = 2349.0 * math.sqrt(2 * math.log(2) * 1.380649e-23 * 296.0 / (44 * amu)) / 2.99792458e8
+    assert P["alpha_D"][0] == pytest.approx(aD, rel=1e-9)
+    assert 2.17e-3 < aD < 2.19e-3  # the textbook ~0.0022 cm^-1 of CO2 near 2349 cm^-1
+
+
+def test_number_density_loschmidt():
+    # ideal gas at 296 K and 1 atm: 2.4794e19 molecules/cm^3
+    assert O.number_density(1.0, 296.0, 1.0) == pytest.approx(2.4794e19, rel=1e-4)
+    wl = _wl_one(296.0, 1.0, units="k_cm1")
+    P = O.level_params(wl, 0)
+    assert P["amp"][0] == pytest.approx(P["S_T"][0] * 2.4794e19, rel=1e-4)
+    wl = _wl_one(296.0, 1.0, units="k_km1")
+    assert O.level_params(wl, 0)["amp"][0] == pytest.approx(P["S_T"][0] * 2.4794e24, rel=1e-4)
+
+
+def test_intensity_temperature_dependence():
+    # two lines differing only in E'': ratio follows the Boltzmann factor
+    T = 700.0
+    wa = _wl_one(T, 1.0, E=0.0)
+    wb = _wl_one(T, 1.0, E=1000.0)
+    Sa = O.level_params(wa, 0)["S_T"][0]
+    Sb = O.level_params(wb, 0)["S_T"][0]
+    assert Sb / Sa == pytest.approx(math.exp(-1.4387769 * 1000.0 * (1 / T - 1 / 296.0)), rel=1e-6)
+    # E'' = 0 and a high wavenumber: only the partition sum, Q ~ T^1.25
+    wc = _wl_one(T, 1.0, E=0.0, nu0=9000.0)
+    assert O.level_params(wc, 0)["S_T"][0] == pytest.approx(1e-20 * (296.0 / T) ** 1.25, rel=1e-6)
+    # low wavenumber: stimulated emission matters and lowers S at high T
+    wd = _wl_one(T, 1.0, E=0.0, nu0=50.0)
+    assert O.level_params(wd, 0)["S_T"][0] < 0.9 * 1e-20 * (296.0 / T) ** 1.25
+    # width scales with (296/T)^n_air
+    g1 = O.level_params(_wl_one(296.0, 1.0), 0)["gamma_L"][0]
+    g2 = O.level_params(_wl_one(592.0, 1.0), 0)["gamma_L"][0]
+    assert g2 / g1 == pytest.approx(0.5 ** float(np.float32(0.7)), rel=1e-12)
+
+
+# ------------------------------------------------------------ chi
+def test_tonkov_chi_pieces_and_near_continuity():
+    F = 2 ** O.FIX_BITS
+    d = lambda v: np.array([int(round(v * F))], dtype=np.int64)
+    assert O.chi_tonkov(d(0.0))[0] == 1.0
+    assert O.chi_tonkov(d(2.999))[0] == 1.0
+    # branch 1 includes 3: jump of 1 - 1.084 exp(-0.081) = 3.4e-4 only
+    assert abs(O.chi_tonkov(d(3.0))[0] - 1.0) < 4e-4
+    assert O.chi_tonkov(d(3.0))[0] < 1.0
+    # the three branches nearly join at 150 and 300 cm^-1 (within 2 % of each other)
+    for b in (150.0, 300.0):
+        lo = O.chi_tonkov(d(b))[0]
+        hi = O.chi_tonkov(d(b) + 1)[0]
+        assert lo != hi and abs(lo / hi - 1) < 0.02
+    # decreasing beyond 3, symmetric in the sign of the offset
+    v = O.chi_tonkov(np.arange(3, 600, 7, dtype=np.int64) * F)
+    assert np.all(np.diff(v) < 0)
+    assert O.chi_tonkov(-d(42.0))[0] == O.chi_tonkov(d(42.0))[0]
+    assert 0.33 < O.chi_tonkov(d(42.0))[0] < 0.36
+
+
+def test_gstar_thresholds():
+    for R_c in (4, 8, 16):
+        for g in range(1, 11):
+            assert O.gstar(np.array([R_c * 2.0 ** (1 - g)]), R_c)[0] == g
+            assert O.gstar(np.array([np.nextafter(R_c * 2.0 ** (1 - g), 0)]), R_c)[0] == g + 1
+    assert O.gstar(np.array([1e-9]), 8)[0] == 11
+    assert O.gstar(np.array([1e3]), 8)[0] == 1
+
+
+# ------------------------------------------------------------ eleven-grid bookkeeping
+CASES = [
+    # T, p, chi, cut-off, R_w, R_c, window
+    ((296.0,), (1.0,), "none", 25.0, 8, 8, (1000.0, 1003.3)),
+    ((200.0,), (1e-4,), "tonkov", 25.0, 8, 8, (1000.0, 1002.71)),
+    ((735.0,), (92.0,), "tonkov", 125.0, 8, 8, (1000.0, 1003.0)),
+    ((500.0,), (3.0,), "tonkov", 160.0, 4, 16, (999.13, 1001.0)),
+    ((250.0,), (0.05,), "none", 7.3, 16, 4, (1000.0, 1001.5)),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_constant_shape_counts_lines_within_cutoff(case):
+    T, p, chi, cut, Rw, Rc, (lo, hi) = case
+    wl = tiny_workload(11, 250, lo, hi, cut, T=T, p=p, shape="const", chi=chi, chi_species=1,
+                       R_w=Rw, R_c=Rc)
+    k = O.eleven_grid(wl, 0)
+    P = O.level_params(wl, 0)
+    c = O.centre_fixed(P["nu_shift"])
+    k_lo, k_hi = O.window_nodes(lo, hi)
+    X = np.arange(k_lo, k_hi + 1, dtype=np.int64) << O.fine_shift()
+    cut_fx = int(round(cut * O.FIX))
+    count = (np.abs(X[:, None] - c[None, :]) <= cut_fx).sum(axis=1)
+    assert np.abs(k - count).max() < 1e-9 * max(1, count.max())
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_quadratic_shape_eleven_grid_equals_brute_force(case):
+    T, p, chi, cut, Rw, Rc, (lo, hi) = case
+    wl = tiny_workload(12, 250, lo, hi, cut, T=T, p=p, shape="quad", chi=chi, chi_species=1,
+                       R_w=Rw, R_c=Rc)
+    k = O.eleven_grid(wl, 0)
+    kb = O.brute_force(wl, 0)
+    assert np.abs(k - kb).max() <= 1e-12 * np.abs(kb).max()
+
+
+def test_pointwise_form_agrees_with_grid_form(c0):
+    k = O.eleven_grid(c0, 0)
+    k_lo, _ = O.window_nodes(c0.nu_lo, c0.nu_hi)
+    idx = np.array([0, 1, 7, 8, 1023, 4096, 10000, 20479, 20480])
+    kp = O.eleven_grid_at(c0, 0, k_lo + idx)
+    assert np.allclose(kp, k[idx], rtol=1e-12, atol=0)
+
+
+def test_voigt_eleven_grid_within_interpolation_error(c0):
+    k = O.eleven_grid(c0, 0)
+    k_lo, _ = O.window_nodes(c0.nu_lo, c0.nu_hi)
+    idx = np.arange(0, 20481, 37)
+    kb = O.brute_force(c0, 0, k_lo + idx)
+    rel = np.abs(k[idx] / kb - 1)
+    # paper (Sec. 2.4): < 1 % at centres, up to ~5 % between lines for its constants;
+    # with R_w = R_c = 8 the 3-point scheme stays well inside that
+    assert rel.max() < 1e-2
+    # tighter constants shrink the interpolation error
+    c16 = c0.with_(R_w=16, R_c=16)
+    k16 = O.eleven_grid(c16, 0)
+    assert np.abs(k16[idx] / kb - 1).max() < rel.max() / 3
+
+
+def test_tiny_brute_force_single_line_lorentz():
+    wl = _wl_one(296.0, 1.0, units="sigma").with_(shape="lorentz", nu_lo=2348.5, nu_hi=2349.5,
+                                                 cutoff=0.3)
+    kb = O.brute_force(wl, 0)
+    P = O.level_params(wl, 0)
+    k_lo, k_hi = O.window_nodes(2348.5, 2349.5)
+    nu = np.arange(k_lo, k_hi + 1) / 2048.0
+    d = nu - P["nu_shift"][0]
+    g = P["gamma_L"][0]
+    expect = np.where(np.abs(d) <= 0.3, P["S_T"][0] * g / (math.pi * (g * g + d * d)), 0.0)
+    assert np.allclose(kb, expect, rtol=1e-12, atol=0)
+
+
+def test_eval_count_scale(c0):
+    st = {}
+    O.eleven_grid(c0, 0, stats=st)
+    total = sum(st.values())
+    # far fewer evaluations than the direct sum over the window (paper: ~100x faster)
+    lines_in_reach = 2000
+    assert total < lines_in_reach * O.num_points(c0.nu_lo, c0.nu_hi) / 200
+
+
+# ------------------------------------------------------------ planted mistakes must be caught
+def _quad_case():
+    T, p, chi, cut, Rw, Rc, (lo, hi) = CASES[1]
+    return tiny_workload(12, 120, lo, hi, cut, T=T, p=p, shape="quad", chi=chi, chi_species=1,
+                         R_w=Rw, R_c=Rc)
+
+
+def _quad_pin_holds(wl):
+    k = O.eleven_grid(wl, 0)
+    kb = O.brute_force(wl, 0)
+    return np.abs(k - kb).max() <= 1e-12 * np.abs(kb).max()
+
+
+def test_planted_mistakes_fail_a_pin(monkeypatch):
+    wl = _quad_case()
+    assert _quad_pin_holds(wl)
+    # 1. transposed interpolation weights
+    with monkeypatch.context() as m:
+        orig = O.lagrange3
+        m.setattr(O, "lagrange3", lambda t: tuple(reversed(orig(t))))
+        assert not _quad_pin_holds(wl)
+    # 2. ownership that forgets the parent test (double counting)
+    with monkeypatch.context() as m:
+        m.setattr(O, "owned", lambda g, mm, c, gs, ch, cut, Rw: O.accept(g, mm, c, gs, ch, cut, Rw))
+        assert not _quad_pin_holds(wl)
+    # 3. a wrong sign in the pressure shift breaks the Lorentz single-line pin
+    with monkeypatch.context() as m:
+        orig_lp = O.level_params
+
+        def bad(wl_, lev):
+            P = orig_lp(wl_, lev)
+            P["nu_shift"] = 2 * wl_.lines["nu0"] - P["nu_shift"]
+            return P
+        m.setattr(O, "level_params", bad)
+        with pytest.raises(AssertionError):
+            test_spectroscopy_reference_identities()
+    # 4. support tested on the near edge of a panel instead of the far edge lets
+    #    panels straddling the cut-off through: the count pin catches it
+    with monkeypatch.context() as m:
+        orig_acc = O.accept
+
+        def acc(g, mm, c, gs, ch, cut, Rw):
+            return orig_acc(g, mm, c, gs, ch, cut + (1 << O.panel_shift(g)), Rw)
+        m.setattr(O, "accept", acc)
+        with pytest.raises(AssertionError):
+            test_constant_shape_counts_lines_within_cutoff(CASES[3])
