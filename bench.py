@@ -1,0 +1,266 @@
+"""Throughput of the eleven-grid line-by-line path on the Venus workload.
+
+Workload: 200,000 band-structured CO2-like lines over 1875-3125 cm^-1, 60 Venus
+levels (735 -> 170 K, 92 -> 1e-5 atm), Voigt x Tonkov chi-factor, 125 cm^-1 cut-off,
+k(nu) on 2000-3000 cm^-1 at 2^-11 cm^-1 (2,048,001 points per level). One step =
+one marfa_absorption call over all 60 levels (level preparation, coarse grids,
+finest grid with the interpolation cascade) with the line list resident on the GPU.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line. ``value`` is fine-grid points x levels per second over all
+ranks; ``line_evals_per_s`` counts the (line, node) profile evaluations the scheme
+defines. ``e2e`` is the same metric through the public call with host buffers
+(line records and levels from pinned host memory in, k(nu) back to pinned host
+memory, every step). ``--impl reference`` times the FP64 CPU oracle on a bounded
+sample of the same workload (there is no other implementation of this path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "spectral pts x levels/s and line-evals/s, MLP-Voigt vs plain at <=1e-3 rel err"
+UNIT = "pts*levels/s"
+FLOPS_PER_EVAL = 20.0  # algorithmic FP32 flops of one far-wing profile evaluation
+N_SM = 152
+FP32_LANES = 128
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("sm_max_mhz", 2070.0), "measured"
+    return 2070.0, "fallback"
+
+
+def start_clock_sampler(path):
+    try:
+        f = open(path, "w")
+        return subprocess.Popen(
+            ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+             "--format=csv,noheader,nounits", "-lms", "200"], stdout=f, stderr=subprocess.DEVNULL), f
+    except (OSError, FileNotFoundError):
+        return None, None
+
+
+def read_clocks(path, dev_index):
+    rows = []
+    try:
+        for line in open(path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9 and parts[0] == str(dev_index):
+                rows.append(parts)
+    except OSError:
+        return None
+    if not rows:
+        return None
+    sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+    mx = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower().startswith("active")})
+    return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": reasons,
+            "samples": len(rows)}
+
+
+def cpu_baseline_sample(wl, seconds_hint=15.0):
+    """Time the FP64 oracle (as it stands) on a bounded sample of the workload: the
+    eleven-grid result of one mid-profile level on a window of 0.25 cm^-1, with the
+    line list cut to the lines that can reach it (others contribute nothing)."""
+    from oracle import marfa_oracle as O
+    lev = 30
+    lo, hi = 2500.0, 2500.25
+    keep = np.abs(wl.lines["nu0"] - 0.5 * (lo + hi)) <= wl.cutoff + 2.0
+    sub = wl.with_(lines=wl.lines[keep], nu_lo=lo, nu_hi=hi).level_subset([lev])
+    t = time.perf_counter()
+    O.eleven_grid(sub, 0)
+    dt = time.perf_counter() - t
+    pts = O.num_points(lo, hi)
+    return {"value": pts / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"level {lev}, {lo}-{hi} cm^-1 ({pts} points), {int(keep.sum())} lines in reach, "
+                      f"{dt:.1f} s single-threaded numpy/scipy FP64"}
+
+
+def run_reference(args, wl, rank, world):
+    if rank != 0:
+        return
+    from oracle import marfa_oracle as O
+    times = []
+    lev = 30
+    lo, hi = 2500.0, 2500.125
+    keep = np.abs(wl.lines["nu0"] - 0.5 * (lo + hi)) <= wl.cutoff + 2.0
+    sub = wl.with_(lines=wl.lines[keep], nu_lo=lo, nu_hi=hi).level_subset([lev])
+    pts = O.num_points(lo, hi)
+    for i in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        O.eleven_grid(sub, 0)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t)
+    dt = float(np.mean(times))
+    v = pts / dt
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "sample": f"level {lev}, {lo}-{hi} cm^-1 per step"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"level {lev}, {lo}-{hi} cm^-1 ({pts} points), {int(keep.sum())} lines"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    from workloads import config1_venus
+    wl = config1_venus()
+
+    if args.impl == "reference":
+        run_reference(args, wl, rank, world)
+        return
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2411_03418_gb300 import marfa as M
+
+    stream = torch.cuda.current_stream()
+    lines = M.marfa_prepare_lines(wl.lines, wl.species)
+    levels = M.levels_of(wl)
+    rq = M.request_of(wl)
+    npts = M.marfa_num_points(wl.nu_lo, wl.nu_hi)
+    out = torch.empty((wl.n_levels, npts), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
+
+    # evaluation count of one step (exact, from the counting variant of the kernels)
+    _, counts = M.marfa_diag_absorption_counted(lines, levels, wl.vmr, rq)
+    evals_per_step = int(counts.sum())
+
+    def step():
+        M.marfa_absorption(lines, levels, wl.vmr, rq, out, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+
+    clk_path = os.path.join(tempfile.gettempdir(), f"marfa_clocks_{os.getpid()}.csv")
+    sampler, fh = start_clock_sampler(clk_path)
+    M.marfa_diag_kernel_timing(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(float(i))  # L2 flush between steps, outside the timed events
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    kms, klaunch = M.marfa_diag_kernel_timing(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    if sampler:
+        sampler.terminate()
+        sampler.wait()
+        fh.close()
+    clocks = read_clocks(clk_path, torch.cuda.current_device()) if sampler else None
+    t_total = float(sum(step_ms)) / 1e3
+    if dist:
+        tt = torch.tensor([t_total], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+    ms_per_step = t_total / args.steps * 1e3
+    units = wl.n_levels * npts * world
+    value = units * args.steps / t_total
+    evals_s = evals_per_step * world * args.steps / t_total
+
+    # end to end through the public call with host buffers (pinned)
+    rec_h = torch.from_numpy(wl.lines.view(np.uint8)).pin_memory().numpy().view(wl.lines.dtype)
+    out_h = torch.empty((wl.n_levels, npts), dtype=torch.float32).pin_memory().numpy()
+    for _ in range(1):
+        l2 = M.marfa_prepare_lines(rec_h, wl.species)
+        M.marfa_absorption(l2, levels, wl.vmr, rq, out_h, stream)
+        M.marfa_free_lines(l2)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        l2 = M.marfa_prepare_lines(rec_h, wl.species)
+        M.marfa_absorption(l2, levels, wl.vmr, rq, out_h, stream)
+        M.marfa_free_lines(l2)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    if dist:
+        tt = torch.tensor([t_e2e], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+    e2e_value = units * args.steps / t_e2e
+
+    # roofline of the dominant kernel (FP32 pipe, algorithmic flops per evaluation)
+    names = ["level_prep", "coarse", "fine"]
+    dom = int(np.argmax(kms))
+    dom_ms = kms[dom] / max(1, klaunch[dom])
+    frac_evals = counts[:, :10].sum() / max(1, counts.sum()) if dom == 1 else counts[:, 10].sum() / max(1, counts.sum())
+    dom_evals = evals_per_step * frac_evals
+    achieved = dom_evals * FLOPS_PER_EVAL / (dom_ms * 1e-3) / 1e12
+    mhz, src = peaks()
+    peak = N_SM * FP32_LANES * 2 * mhz * 1e6 / 1e12
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl.name, "lines": int(len(wl.lines)), "levels": wl.n_levels,
+                       "npts_per_level": npts, "l2": "flushed between steps (256 MB write)"},
+            "line_evals_per_s": evals_s, "line_evals_per_step": evals_per_step,
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": int(wl.lines.nbytes + levels.nbytes + wl.vmr.nbytes),
+                    "d2h_bytes_per_step": int(out_h.nbytes)},
+            "gpu_launches": int(klaunch.sum()),
+            "kernel_ms_per_step": {n: float(kms[i] / args.steps) for i, n in enumerate(names)},
+            "roofline": {"bound": "alu", "kernel": names[dom], "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz ({src} max clock)"},
+            "clocks": clocks,
+        }
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline_sample(wl)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

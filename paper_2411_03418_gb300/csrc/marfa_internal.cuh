@@ -1,0 +1,123 @@
+// Internal layouts shared by the host runtime (marfa_api.cu) and the kernels
+// (marfa_kernels.cu) of libmarfa. Not part of the C-ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace marfa {
+
+// Positions are int64 fixed point in units of 2^-43 cm^-1, so line centres, grid
+// nodes, panel ends, cut-offs and chi-factor breakpoints compare exactly.
+constexpr int kFixBits = 43;
+constexpr double kFix = 8796093022208.0;  // 2^43
+constexpr int kFineBits = 11;             // finest step 2^-11 = 10/20480 cm^-1 (Sec. 2.4)
+constexpr int kFineShift = kFixBits - kFineBits;  // 32
+constexpr int kNGrid = 10;                // coarse grids G1..G10, h_g = 2^(1-g) cm^-1
+
+// A panel of grid g spans two steps, 2 h_g = 2^(2-g) cm^-1 = 2^(45-g) units.
+__host__ __device__ constexpr int panel_shift(int g) { return kFixBits + 2 - g; }
+__host__ __device__ constexpr int64_t step_fx(int g) { return int64_t(1) << (kFixBits + 1 - g); }
+
+__host__ __device__ __forceinline__ int64_t fl_sh(int64_t a, int s) { return a >> s; }
+__host__ __device__ __forceinline__ int64_t cl_sh(int64_t a, int s) { return -((-a) >> s); }
+
+constexpr int kShapeLorentz = 0, kShapeVoigt = 1, kShapeDoppler = 2, kShapeConst = 100,
+              kShapeQuad = 101;
+
+// Per level (host-computed in double precision).
+struct LevelDev {
+  double T, p;
+  double ratio;        // 296 / T, for the FP64 width (fallback of the g* decision)
+  int64_t smin, smax;  // bounds of c - key over all lines, fixed point (conservative)
+  float pf;            // p as float
+  float log2_ratio;    // log2(296 / T)
+  float kb_hi, kb_lo;  // -c2 (1/T - 1/296) as a float pair (Boltzmann factor exponent)
+  float c2_T, c2_Tref; // c2 / T, c2 / 296
+};
+
+// Per (level, species).
+struct LevelSpeciesDev {
+  double ps_d;    // vmr p (partial pressure, atm)
+  double sqrtv;   // sqrt(2 N_A k_B T ln2 / (M 1e-3)) (m/s), alpha_D = nu0/c * sqrtv
+  float ps;       // vmr p
+  float F;        // [n_s] Q(296)/Q(T) * internal scale: multiplies S296
+  float ad;       // alpha_D / nu0
+  int32_t chi;    // chi-factor applies (request chi on, species flag, physical shape)
+};
+
+// One request as the kernels see it.
+struct ReqDev {
+  // prepared lines (sorted by nu0)
+  int64_t n_lines;
+  const int64_t* key;       // rint(nu0 2^43)
+  int64_t key_base;         // bucket index over the keys
+  int32_t bshift;
+  int32_t nbuck;
+  const int32_t* bfirst;    // [nbuck + 1] first line with key >= key_base + b 2^bshift
+  // per-level line data [n_levels][n_lines]
+  const int64_t* c;         // shifted centre, fixed point
+  const float* amp;         // amplitude (shape normalisation, S(T), [n], internal scale)
+  const float* sx;          // x per cm^-1
+  const float* yv;          // Voigt y
+  const int8_t* gstar;      // coarsest grid resolving the core (11 = finest)
+  const uint8_t* flags;     // bit 0: chi-factor on
+  int32_t n_levels;
+  const LevelDev* lev;      // [n_levels]
+  // window and grids
+  int64_t k_lo, k_hi;       // finest node indices of the window
+  int64_t m_first[kNGrid + 1];  // per grid 1..10: first panel of the window
+  int64_t npan[kNGrid + 1];     // per grid: panels of the window
+  int64_t slot_off[kNGrid + 1]; // per grid: offset of its L|M|R arrays in a level's slots
+  int64_t slots_per_level;
+  float* slots;             // [n_levels][slots_per_level]
+  int64_t cut_fx;           // cut-off, fixed point
+  int32_t R_w;
+  int32_t shape;
+  int32_t chi_req;          // request asks for the chi-factor
+  float out_scale;          // inverse internal scale
+  float* out;               // [n_levels][npts]
+  int64_t npts;
+};
+
+// One CTA of the coarse kernel: 8 warps, each a block of kPairs consecutive node pairs.
+struct CoarseItem {
+  int32_t req, level, grid, block0;
+};
+// One CTA of the finest-grid kernel: 1024 finest nodes of one level.
+struct FineItem {
+  int32_t req, level;
+  int64_t k0;  // first node of the tile (multiple of 4)
+};
+
+constexpr int kPairs = 8;            // node pairs per warp block in the coarse kernel
+constexpr int kCoarseWarps = 8;
+constexpr int kFineThreads = 256;
+constexpr int kFinePerThread = 4;
+constexpr int kFineTile = kFineThreads * kFinePerThread;
+
+struct PrepArgs {
+  int64_t n;
+  const double* nu0;
+  const float *S296, *ga, *gs, *E, *na, *da;
+  const int16_t* species;
+  int32_t n_species;
+  const LevelDev* lev;
+  const LevelSpeciesDev* ls;   // [n_levels][n_species]
+  int32_t shape, R_c;
+  int64_t* c;
+  float *amp, *sx, *yv;
+  int8_t* gstar;
+  uint8_t* flags;
+};
+
+// kernels (marfa_kernels.cu)
+void launch_level_prep(const PrepArgs& a, int n_levels, cudaStream_t st);
+void launch_coarse(const ReqDev* reqs, const CoarseItem* items, int n_items, int64_t* counts,
+                   cudaStream_t st);
+void launch_fine(const ReqDev* reqs, const FineItem* items, int n_items, int64_t* counts,
+                 cudaStream_t st);
+void launch_diag_voigt(const float* x, const float* y, float* out, int64_t n, cudaStream_t st);
+void launch_diag_owned(const ReqDev* req, int64_t n_lines, int level, int grid, int64_t first,
+                       int count, uint8_t* out, cudaStream_t st);
+
+}  // namespace marfa

@@ -1,0 +1,109 @@
+// FP32 Voigt function K(x, y) = Re w(x + iy) (Eq. (8) of arXiv 2411.03418) for the
+// profile kernels, with a relative error of about 1e-6 over the whole (x, y >= 0)
+// plane. The paper's own Humlicek/Kuntz variant (Appendix C) is accurate to 1 % only;
+// this one is built from:
+//   |z| >= 4.5   asymptotic series of w (Abramowitz & Stegun 7.1.23),
+//                w ~ i/(sqrt(pi) z) sum_n (2n-1)!!/(2 z^2)^n, truncated by |z|
+//                (1, 5 or 14 terms), plus the Gaussian term exp(y^2-x^2) cos(2xy)
+//                for y < 1, which is the Doppler core the series cannot see;
+//   |z| < 4.5, y < 1   exact split w = exp(-z^2) + (2i/sqrt(pi)) F(z), F the complex
+//                Dawson function, K = exp(y^2-x^2) cos(2xy) - (2/sqrt(pi)) y Psi,
+//                Psi(x, y^2) = Im F / y from a table of bivariate polynomials;
+//   |z| < 4.5, y >= 1  K from a table of bivariate polynomials.
+// The tables come from gen_voigt_tables.py (mpmath, 30 digits).
+#pragma once
+#include <cuda_runtime.h>
+
+#define MARFA_VOIGT_QUAL static __device__ const
+#include "voigt_tables.inc"
+#undef MARFA_VOIGT_QUAL
+
+namespace marfa {
+
+constexpr float kInvSqrtPi = 0.56418958354775628f;  // 1/sqrt(pi)
+constexpr float kTwoOverSqrtPi = 1.1283791670955126f;
+
+// exp(y^2 - x^2) cos(2xy), with the exponent carried to about one extra word so
+// that the Gaussian core keeps its relative accuracy out to |x| ~ 4.5.
+__device__ __forceinline__ float gauss_term(float x, float y) {
+  float xx = x * x;
+  float xl = fmaf(x, x, -xx);
+  float yy = y * y;
+  float yl = fmaf(y, y, -yy);
+  float a = yy - xx;
+  float bb = a - yy;                      // TwoSum(yy, -xx)
+  float e = (yy - (a - bb)) + (-xx - bb);
+  float d = e + yl - xl;
+  return expf(a) * (1.0f + d) * cosf(2.0f * x * y);
+}
+
+// Re of the asymptotic series with N+1 terms, in real arithmetic on u = 1/z, v = u^2.
+template <int N>
+__device__ __forceinline__ float voigt_asym(float x, float y) {
+  float r2 = fmaf(x, x, y * y);
+  float inv = 1.0f / r2;
+  float ur = x * inv, ui = -y * inv;
+  float vr = ur * ur - ui * ui, vi = 2.0f * ur * ui;
+  // c_n = (2n-1)!!/2^n
+  float c[N + 1];
+  c[0] = 1.0f;
+#pragma unroll
+  for (int n = 1; n <= N; ++n) c[n] = c[n - 1] * (0.5f * (2 * n - 1));
+  float sr = c[N], si = 0.0f;
+#pragma unroll
+  for (int n = N - 1; n >= 0; --n) {
+    float tr = fmaf(sr, vr, -si * vi) + c[n];
+    float ti = fmaf(sr, vi, si * vr);
+    sr = tr;
+    si = ti;
+  }
+  // w ~ (i/sqrt(pi)) u S  ->  Re w = -Im(u S)/sqrt(pi)
+  return -(ui * sr + ur * si) * kInvSqrtPi;
+}
+
+__device__ __forceinline__ float voigt_cell(int cell, float u, float v) {
+  const float* c = kVoigtCells + cell * (VOIGT_DEG + 1) * (VOIGT_DEG + 1);
+  float acc = 0.0f;
+#pragma unroll
+  for (int p = VOIGT_DEG; p >= 0; --p) {
+    float r = 0.0f;
+#pragma unroll
+    for (int q = VOIGT_DEG; q >= 0; --q) r = fmaf(r, v, __ldg(c + p * (VOIGT_DEG + 1) + q));
+    acc = fmaf(acc, u, r);
+  }
+  return acc;
+}
+
+// Far-wing form (|z| >= 100): two terms of the series, K = y/(sqrt(pi) r^2) (1 + (3x^2 - y^2)/(2 r^4)).
+__device__ __forceinline__ float voigt_far(float x, float y) {
+  float x2 = x * x, y2 = y * y;
+  float inv = 1.0f / (x2 + y2);
+  float t = (3.0f * x2 - y2) * inv * inv * 0.5f;
+  return y * kInvSqrtPi * inv * (1.0f + t);
+}
+
+__device__ __forceinline__ float voigt_K(float x, float y) {
+  float ax = fabsf(x);
+  float r2 = fmaf(ax, ax, y * y);
+  if (r2 >= 1.0e4f) return voigt_far(ax, y);
+  if (r2 >= 64.0f) return voigt_asym<5>(ax, y);
+  if (r2 >= 20.25f) {
+    float a = voigt_asym<14>(ax, y);
+    if (y < 1.0f) a += gauss_term(ax, y);
+    return a;
+  }
+  if (y < 1.0f) {
+    int ci = min((int)(ax * 2.0f), 8);
+    float u = (ax - (0.5f * ci + 0.25f)) * 4.0f;
+    float v = 2.0f * y * y - 1.0f;
+    float ps = voigt_cell(ci, u, v);
+    return gauss_term(ax, y) - kTwoOverSqrtPi * y * ps;
+  }
+  int ix = min((int)(ax * (1.0f / 0.9f)), 4);
+  int iy = min((int)((y - 1.0f) * (1.0f / 1.75f)), 1);
+  float u = (ax - (0.9f * ix + 0.45f)) * (1.0f / 0.45f);
+  float v = (y - (1.0f + 1.75f * iy + 0.875f)) * (1.0f / 0.875f);
+  return voigt_cell(9 + ix * 2 + iy, u, v);
+}
+
+}  // namespace marfa

@@ -1,0 +1,240 @@
+"""ctypes binding of libmarfa (include/marfa.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and converts numpy
+arrays, torch tensors and CUDA streams into plain pointers and sizes. All the
+computation happens in the library's CUDA kernels; there is no fallback, and a
+missing or unloadable library raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LINE_DTYPE = np.dtype([("nu0", "<f8"), ("S296", "<f4"), ("gamma_air", "<f4"), ("gamma_self", "<f4"),
+                       ("E_lower", "<f4"), ("n_air", "<f4"), ("mol_iso", "<i4"), ("delta_air", "<f4")])
+SPECIES_DTYPE = np.dtype([("mol_iso", "<i4"), ("chi_enabled", "<i4"), ("mass_amu", "<f8"), ("q_exp", "<f8")])
+LEVEL_DTYPE = np.dtype([("T_K", "<f8"), ("p_atm", "<f8")])
+
+SHAPES = {"lorentz": 0, "voigt": 1, "doppler": 2, "const": 100, "quad": 101}
+CHI = {"none": 0, "tonkov": 1}
+UNITS = {"sigma": 0, "k_cm1": 1, "k_km1": 2}
+ERRORS = {-1: "MARFA_E_INVAL", -2: "MARFA_E_NOMEM", -3: "MARFA_E_CUDA", -4: "MARFA_E_IO",
+          -5: "MARFA_E_INTERNAL"}
+
+
+class MarfaError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class marfa_request_t(C.Structure):
+    _fields_ = [("nu_lo", C.c_double), ("nu_hi", C.c_double), ("cutoff", C.c_double),
+                ("shape", C.c_int32), ("chi", C.c_int32), ("units", C.c_int32),
+                ("surrogate", C.c_int32), ("R_w", C.c_int32), ("R_c", C.c_int32)]
+
+
+_LIB = None
+EXPORTS = ["marfa_prepare_lines", "marfa_free_lines", "marfa_num_points", "marfa_absorption",
+           "marfa_absorption_batch", "marfa_write_pt_table", "marfa_last_error", "marfa_diag_voigt",
+           "marfa_diag_level_lines", "marfa_diag_owned", "marfa_diag_absorption_counted",
+           "marfa_diag_kernel_timing"]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libmarfa (built in-tree by paper_2411_03418_gb300.build). Raises if absent."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    p = path or _build.LIB
+    if not os.path.exists(p):
+        raise RuntimeError(f"libmarfa is not built ({p} missing): call paper_2411_03418_gb300.build.build()")
+    lib = C.CDLL(p)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    sig = {
+        "marfa_prepare_lines": (C.c_int, [vp, i64, vp, i32, C.POINTER(vp)]),
+        "marfa_free_lines": (None, [vp]),
+        "marfa_num_points": (i64, [dbl, dbl]),
+        "marfa_absorption": (C.c_int, [vp, vp, vp, i32, vp, vp, vp]),
+        "marfa_absorption_batch": (C.c_int, [i32, vp, vp, vp, vp, vp, vp, vp]),
+        "marfa_write_pt_table": (C.c_int, [C.c_char_p, i32, dbl, dbl, vp, i64]),
+        "marfa_last_error": (C.c_char_p, []),
+        "marfa_diag_voigt": (C.c_int, [vp, vp, vp, i64]),
+        "marfa_diag_level_lines": (C.c_int, [vp, vp, vp, i32, vp, vp, vp, vp]),
+        "marfa_diag_owned": (C.c_int, [vp, vp, vp, i32, vp, i32, i32, i64, i32, vp]),
+        "marfa_diag_absorption_counted": (C.c_int, [vp, vp, vp, i32, vp, vp, vp]),
+        "marfa_diag_kernel_timing": (C.c_int, [i32, vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise MarfaError(rc, load().marfa_last_error().decode())
+
+
+def _ptr(a):
+    """Pointer of a numpy array or a torch tensor (host or device)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if hasattr(s, "cuda_stream"):
+        return C.c_void_p(s.cuda_stream)
+    return C.c_void_p(int(s))
+
+
+class Lines:
+    """A prepared line list (owns the library handle)."""
+
+    def __init__(self, handle, n, n_species):
+        self.handle = handle
+        self.n = n
+        self.n_species = n_species
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.marfa_free_lines(self.handle)
+            self.handle = None
+
+
+def marfa_prepare_lines(lines: np.ndarray, species: np.ndarray) -> Lines:
+    lines = np.ascontiguousarray(lines, dtype=LINE_DTYPE)
+    species = np.ascontiguousarray(species, dtype=SPECIES_DTYPE)
+    h = C.c_void_p()
+    _check(load().marfa_prepare_lines(_ptr(lines), len(lines), _ptr(species), len(species), C.byref(h)))
+    return Lines(h, len(lines), len(species))
+
+
+def marfa_free_lines(lines: Lines) -> None:
+    if lines.handle:
+        load().marfa_free_lines(lines.handle)
+        lines.handle = None
+
+
+def marfa_num_points(nu_lo: float, nu_hi: float) -> int:
+    return int(load().marfa_num_points(float(nu_lo), float(nu_hi)))
+
+
+def make_request(nu_lo, nu_hi, cutoff, shape="voigt", chi="none", units="k_cm1", surrogate=0,
+                 R_w=8, R_c=8) -> marfa_request_t:
+    return marfa_request_t(float(nu_lo), float(nu_hi), float(cutoff), SHAPES[shape], CHI[chi],
+                           UNITS[units], int(surrogate), int(R_w), int(R_c))
+
+
+def make_levels(T, p) -> np.ndarray:
+    lv = np.zeros(len(T), dtype=LEVEL_DTYPE)
+    lv["T_K"] = T
+    lv["p_atm"] = p
+    return lv
+
+
+def marfa_absorption(lines: Lines, levels: np.ndarray, vmr: np.ndarray, rq: marfa_request_t,
+                     k_out, stream=None) -> None:
+    """k_out: float32 [n_levels, npts], a numpy array (host) or a CUDA torch tensor."""
+    levels = np.ascontiguousarray(levels, dtype=LEVEL_DTYPE)
+    vmr = np.ascontiguousarray(vmr, dtype=np.float64)
+    _check(load().marfa_absorption(lines.handle, _ptr(levels), _ptr(vmr), len(levels), C.byref(rq),
+                                   _ptr(k_out), _stream(stream)))
+
+
+def marfa_absorption_batch(lines, levels, vmrs, rqs, k_outs, stream=None) -> None:
+    n = len(lines)
+    levels = [np.ascontiguousarray(x, dtype=LEVEL_DTYPE) for x in levels]
+    vmrs = [np.ascontiguousarray(v, dtype=np.float64) for v in vmrs]
+    VP = C.c_void_p * n
+    lh = VP(*[l.handle.value for l in lines])
+    lp = VP(*[x.ctypes.data for x in levels])
+    vp = VP(*[v.ctypes.data for v in vmrs])
+    nl = (C.c_int32 * n)(*[len(x) for x in levels])
+    rq = (marfa_request_t * n)(*rqs)
+    outs = VP(*[_ptr(o).value for o in k_outs])
+    _check(load().marfa_absorption_batch(n, lh, lp, vp, nl, rq, outs, _stream(stream)))
+
+
+def marfa_write_pt_table(directory: str, level_number: int, nu_lo: float, nu_hi: float, k: np.ndarray) -> None:
+    k = np.ascontiguousarray(k, dtype=np.float32)
+    _check(load().marfa_write_pt_table(directory.encode(), int(level_number), float(nu_lo), float(nu_hi),
+                                       _ptr(k), len(k)))
+
+
+def marfa_last_error() -> str:
+    return load().marfa_last_error().decode()
+
+
+def marfa_diag_voigt(x: np.ndarray, y: np.ndarray) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    out = np.empty_like(x)
+    _check(load().marfa_diag_voigt(_ptr(x), _ptr(y), _ptr(out), len(x)))
+    return out
+
+
+def marfa_diag_level_lines(lines: Lines, levels, vmr, rq):
+    levels = np.ascontiguousarray(levels, dtype=LEVEL_DTYPE)
+    vmr = np.ascontiguousarray(vmr, dtype=np.float64)
+    nl = len(levels)
+    c = np.empty((nl, lines.n), dtype=np.int64)
+    g = np.empty((nl, lines.n), dtype=np.int8)
+    perm = np.empty(lines.n, dtype=np.int64)
+    _check(load().marfa_diag_level_lines(lines.handle, _ptr(levels), _ptr(vmr), nl, C.byref(rq),
+                                         _ptr(c), _ptr(g), _ptr(perm)))
+    return c, g, perm
+
+
+def marfa_diag_owned(lines: Lines, levels, vmr, rq, level: int, grid: int, first: int, count: int):
+    levels = np.ascontiguousarray(levels, dtype=LEVEL_DTYPE)
+    vmr = np.ascontiguousarray(vmr, dtype=np.float64)
+    out = np.empty((lines.n, count), dtype=np.uint8)
+    _check(load().marfa_diag_owned(lines.handle, _ptr(levels), _ptr(vmr), len(levels), C.byref(rq),
+                                   int(level), int(grid), int(first), int(count), _ptr(out)))
+    return out
+
+
+def marfa_diag_absorption_counted(lines: Lines, levels, vmr, rq):
+    levels = np.ascontiguousarray(levels, dtype=LEVEL_DTYPE)
+    vmr = np.ascontiguousarray(vmr, dtype=np.float64)
+    n = marfa_num_points(rq.nu_lo, rq.nu_hi)
+    k = np.empty((len(levels), n), dtype=np.float32)
+    counts = np.empty((len(levels), 11), dtype=np.int64)
+    _check(load().marfa_diag_absorption_counted(lines.handle, _ptr(levels), _ptr(vmr), len(levels),
+                                                C.byref(rq), _ptr(k), _ptr(counts)))
+    return k, counts
+
+
+def marfa_diag_kernel_timing(enable: bool):
+    """Start (True) or stop (False) per-kernel event timing; stopping returns
+    (ms[3], launches[3]) for level preparation, coarse grids, finest grid."""
+    ms = np.zeros(3, dtype=np.float64)
+    n = np.zeros(3, dtype=np.int64)
+    _check(load().marfa_diag_kernel_timing(1 if enable else 0, _ptr(ms), _ptr(n)))
+    return ms, n
+
+
+# ------------------------------------------------------------------ workload marshalling
+def request_of(wl) -> marfa_request_t:
+    return make_request(wl.nu_lo, wl.nu_hi, wl.cutoff, wl.shape, wl.chi, wl.units, wl.surrogate,
+                        wl.R_w, wl.R_c)
+
+
+def levels_of(wl) -> np.ndarray:
+    return make_levels(wl.T, wl.p)

@@ -1,0 +1,95 @@
+"""The C-ABI library builds, loads without a GPU and exports what include/marfa.h
+declares; host-only entry points (PT-table writer, argument validation) checked on CPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import marfa_oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def M():
+    from paper_2411_03418_gb300 import build, marfa
+    build.build()
+    marfa.load()
+    return marfa
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "marfa.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(marfa_[a-z_]+)\s*\(", txt)))
+
+
+def test_header_and_library_exports_agree(M):
+    syms = declared_symbols()
+    assert len(syms) >= 11
+    lib = ctypes.CDLL(M.lib_path())
+    for s in syms:
+        assert hasattr(lib, s), f"{s} declared in include/marfa.h but not exported"
+    assert sorted(M.EXPORTS) == syms
+
+
+def test_struct_layouts(M):
+    assert M.LINE_DTYPE.itemsize == 36
+    assert M.SPECIES_DTYPE.itemsize == 24
+    assert ctypes.sizeof(M.marfa_request_t) == 48
+
+
+def test_num_points_matches_oracle(M):
+    for lo, hi in [(4000, 4010), (2000, 3000), (999.13, 1001.0), (0.0, 0.0001), (5.0, 4.0),
+                   (123.456, 123.457)]:
+        assert M.marfa_num_points(lo, hi) == O.num_points(lo, hi)
+    assert M.marfa_num_points(-1.0, 2.0) < 0
+    assert M.marfa_num_points(float("nan"), 2.0) < 0
+
+
+def test_pt_table_bytes_match_appendix_a_layout(M, tmp_path):
+    rng = np.random.default_rng(0)
+    n = O.num_points(20.0, 50.0)
+    k = rng.random(n).astype(np.float32)
+    M.marfa_write_pt_table(str(tmp_path), 7, 20.0, 50.0, k)
+    data = (tmp_path / "7__.ptbin").read_bytes()
+    assert data == O.pt_table_bytes(20.0, 50.0, k)
+    M.marfa_write_pt_table(str(tmp_path), 123, 20.0, 50.0, k)
+    assert (tmp_path / "123.ptbin").exists()
+
+
+@pytest.mark.parametrize("args", [(19.0, 50.0), (20.0, 20.0), (25.0, 50.0)])
+def test_pt_table_rejects_bad_windows(M, tmp_path, args):
+    k = np.zeros(10, dtype=np.float32)
+    with pytest.raises(M.MarfaError) as e:
+        M.marfa_write_pt_table(str(tmp_path), 1, args[0], args[1], k)
+    assert e.value.code == -1
+
+
+def test_pt_table_io_error(M):
+    n = O.num_points(20.0, 30.0)
+    with pytest.raises(M.MarfaError) as e:
+        M.marfa_write_pt_table("/nonexistent/dir/for/ptbin", 1, 20.0, 30.0, np.zeros(n, np.float32))
+    assert e.value.code == -4
+
+
+def test_prepare_lines_validation_before_any_device_call(M):
+    from workloads import config0_tiny
+    wl = config0_tiny()
+    bad = wl.lines.copy()
+    bad["nu0"][3] = np.nan
+    with pytest.raises(M.MarfaError) as e:
+        M.marfa_prepare_lines(bad, wl.species)
+    assert e.value.code == -1 and "nu0" in str(e.value)
+    bad = wl.lines.copy()
+    bad["mol_iso"][5] = 99
+    with pytest.raises(M.MarfaError):
+        M.marfa_prepare_lines(bad, wl.species)
+    sp2 = np.concatenate([wl.species, wl.species])
+    with pytest.raises(M.MarfaError) as e:
+        M.marfa_prepare_lines(wl.lines, sp2)
+    assert "duplicate" in str(e.value)
+    with pytest.raises(M.MarfaError):
+        M.marfa_prepare_lines(wl.lines[:0], wl.species)
