@@ -539,6 +539,8 @@ static int run_plans(std::vector<Plan>& plans, cudaStream_t st, std::vector<int6
       (e = cudaMemcpyAsync(dci, ci.data(), sizeof(CoarseItem) * ci.size(), cudaMemcpyHostToDevice, st)) ||
       (e = cudaMemcpyAsync(dfi, fi.data(), sizeof(FineItem) * fi.size(), cudaMemcpyHostToDevice, st)))
     return done(fail(MARFA_E_CUDA, "upload of work lists failed: %s", cudaGetErrorString(e)));
+  if (count && ((e = cudaMemsetAsync(dcc, 0, sz_cc, st)) || (e = cudaMemsetAsync(dfc, 0, sz_fc, st))))
+    return done(fail(MARFA_E_CUDA, "count buffers: %s", cudaGetErrorString(e)));
   cudaEvent_t ev = timing_begin(st);
   launch_coarse(drd, dci, (int)ci.size(), dcc, st);
   timing_end(ev, 1, st);
