@@ -227,11 +227,11 @@ def main():
     e2e_value = units * args.steps / t_e2e
 
     # roofline of the dominant kernel (FP32 pipe, algorithmic flops per evaluation)
-    names = ["level_prep", "coarse", "fine"]
+    names = ["level_prep", "grid1", "grids2_10", "finest"]
     dom = int(np.argmax(kms))
     dom_ms = kms[dom] / max(1, klaunch[dom])
-    frac_evals = counts[:, :10].sum() / max(1, counts.sum()) if dom == 1 else counts[:, 10].sum() / max(1, counts.sum())
-    dom_evals = evals_per_step * frac_evals
+    grid_evals = {0: 0, 1: counts[:, 0].sum(), 2: counts[:, 1:10].sum(), 3: counts[:, 10].sum()}
+    dom_evals = float(grid_evals[dom])
     achieved = dom_evals * FLOPS_PER_EVAL / (dom_ms * 1e-3) / 1e12
     mhz, src = peaks()
     peak = N_SM * FP32_LANES * 2 * mhz * 1e6 / 1e12
@@ -244,6 +244,7 @@ def main():
             "config": {"workload": wl.name, "lines": int(len(wl.lines)), "levels": wl.n_levels,
                        "npts_per_level": npts, "l2": "flushed between steps (256 MB write)"},
             "line_evals_per_s": evals_s, "line_evals_per_step": evals_per_step,
+            "line_evals_per_grid": [int(v) for v in counts.sum(axis=0)],
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(wl.lines.nbytes + levels.nbytes + wl.vmr.nbytes),
                     "d2h_bytes_per_step": int(out_h.nbytes)},

@@ -193,9 +193,9 @@ int marfa_diag_absorption_counted(const marfa_lines_t* lines, const marfa_level_
 
 /* Per-kernel device time: enable = 1 clears the totals and starts recording CUDA events
  * around every kernel launch of this library (on the launch stream); enable = 0 stops,
- * waits for the recorded events and writes, for the three kernels (0 level preparation,
- * 1 coarse grids, 2 finest grid + cascade), the summed milliseconds to ms[3] and the
- * launch counts to launches[3] (host arrays, may be NULL). */
+ * waits for the recorded events and writes, for the four kernels (0 level preparation,
+ * 1 grid 1, 2 grids 2..10, 3 finest grid + cascade), the summed milliseconds to ms[4]
+ * and the launch counts to launches[4] (host arrays, may be NULL). */
 int marfa_diag_kernel_timing(int32_t enable, double* ms, int64_t* launches);
 
 #ifdef __cplusplus

@@ -113,8 +113,8 @@ static void timing_end(cudaEvent_t a, int kind, cudaStream_t st) {
 
 extern "C" int marfa_diag_kernel_timing(int32_t enable, double* ms, int64_t* launches) {
   std::lock_guard<std::mutex> lk(g_tmu);
-  double t[3] = {0, 0, 0};
-  int64_t c[3] = {0, 0, 0};
+  double t[4] = {0, 0, 0, 0};
+  int64_t c[4] = {0, 0, 0, 0};
   for (auto& x : g_tl) {
     float f = 0;
     if (cudaEventSynchronize(x.b) == cudaSuccess && cudaEventElapsedTime(&f, x.a, x.b) == cudaSuccess) {
@@ -126,8 +126,8 @@ extern "C" int marfa_diag_kernel_timing(int32_t enable, double* ms, int64_t* lau
   }
   g_tl.clear();
   g_timing = enable != 0;
-  if (ms) std::copy(t, t + 3, ms);
-  if (launches) std::copy(c, c + 3, launches);
+  if (ms) std::copy(t, t + 4, ms);
+  if (launches) std::copy(c, c + 4, launches);
   return MARFA_OK;
 }
 
@@ -296,6 +296,7 @@ struct Plan {
   std::vector<LevelSpeciesDev> ls;
   ReqDev rd{};
   int64_t npts = 0;
+  std::vector<G1Item> g1;
   std::vector<CoarseItem> coarse;
   std::vector<FineItem> fine;
   // device buffers
@@ -417,15 +418,14 @@ static int build_plan(Plan& P, const marfa_lines_t* L, const marfa_level_t* leve
   R.out_scale = (float)(1.0 / scale);
   R.npts = P.npts;
   (void)physical;
-  // work lists: grids from coarse to fine (heaviest CTAs first)
-  for (int g = 1; g <= kNGrid; ++g) {
-    const int64_t pairs = R.npan[g] + 1;
-    const int64_t blocks = (pairs + kPairs - 1) / kPairs;
-    const int64_t ctas = (blocks + kCoarseWarps - 1) / kCoarseWarps;
+  // work lists: grid 1 in tiles of kG1Pairs pairs; grids 2..10 from coarse to fine
+  for (int l = 0; l < n_levels; ++l)
+    for (int64_t m0 = R.m_first[1]; m0 <= R.m_first[1] + R.npan[1]; m0 += kG1Pairs)
+      P.g1.push_back(G1Item{req_idx, l, m0});
+  for (int g = 2; g <= kNGrid; ++g)
     for (int l = 0; l < n_levels; ++l)
-      for (int64_t c = 0; c < ctas; ++c)
-        P.coarse.push_back(CoarseItem{req_idx, l, g, (int32_t)(c * kCoarseWarps)});
-  }
+      for (int64_t m0 = R.m_first[g]; m0 <= R.m_first[g] + R.npan[g]; m0 += kCPairs)
+        P.coarse.push_back(CoarseItem{req_idx, l, g, 0, m0});
   const int64_t kb0 = R.k_lo & ~(int64_t)3;
   for (int l = 0; l < n_levels; ++l)
     for (int64_t k0 = kb0; k0 <= R.k_hi; k0 += kFineTile) P.fine.push_back(FineItem{req_idx, l, k0});
@@ -506,28 +506,34 @@ static void release(Plan& P, cudaStream_t st) {
 static int run_plans(std::vector<Plan>& plans, cudaStream_t st, std::vector<int64_t>* coarse_counts,
                      std::vector<int64_t>* fine_counts) {
   std::vector<ReqDev> rds;
+  std::vector<G1Item> gi;
   std::vector<CoarseItem> ci;
   std::vector<FineItem> fi;
   for (auto& P : plans) rds.push_back(P.rd);
+  for (auto& P : plans) gi.insert(gi.end(), P.g1.begin(), P.g1.end());
   // interleave the coarse lists grid by grid so that the heaviest CTAs start first
   for (int g = 1; g <= kNGrid; ++g)
     for (auto& P : plans)
       for (auto& it : P.coarse)
         if (it.grid == g) ci.push_back(it);
   for (auto& P : plans) fi.insert(fi.end(), P.fine.begin(), P.fine.end());
-  if (ci.size() > 0x7fffffffu || fi.size() > 0x7fffffffu) return fail(MARFA_E_INVAL, "too much work in one call");
+  if (gi.size() > 0x7fffffffu || ci.size() > 0x7fffffffu || fi.size() > 0x7fffffffu)
+    return fail(MARFA_E_INVAL, "too much work in one call");
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-  const size_t sz_r = al(sizeof(ReqDev) * rds.size()), sz_ci = al(sizeof(CoarseItem) * ci.size()),
-               sz_fi = al(sizeof(FineItem) * fi.size());
+  const size_t sz_r = al(sizeof(ReqDev) * rds.size()), sz_gi = al(sizeof(G1Item) * gi.size()),
+               sz_ci = al(sizeof(CoarseItem) * ci.size()), sz_fi = al(sizeof(FineItem) * fi.size());
   const bool count = coarse_counts != nullptr;
-  const size_t sz_cc = count ? al(8 * ci.size() * kCoarseWarps) : 0, sz_fc = count ? al(8 * fi.size()) : 0;
+  const size_t sz_gc = count ? al(8 * gi.size()) : 0;
+  const size_t sz_cc = count ? al(8 * ci.size()) : 0, sz_fc = count ? al(8 * fi.size()) : 0;
   void* buf = nullptr;
-  int r = dev_alloc(&buf, sz_r + sz_ci + sz_fi + sz_cc + sz_fc, st);
+  int r = dev_alloc(&buf, sz_r + sz_gi + sz_ci + sz_fi + sz_gc + sz_cc + sz_fc, st);
   if (r) return r;
   char* p = (char*)buf;
   ReqDev* drd = (ReqDev*)p; p += sz_r;
+  G1Item* dgi = (G1Item*)p; p += sz_gi;
   CoarseItem* dci = (CoarseItem*)p; p += sz_ci;
   FineItem* dfi = (FineItem*)p; p += sz_fi;
+  int64_t* dgc = count ? (int64_t*)p : nullptr; p += sz_gc;
   int64_t* dcc = count ? (int64_t*)p : nullptr; p += sz_cc;
   int64_t* dfc = count ? (int64_t*)p : nullptr;
   auto done = [&](int code) {
@@ -536,22 +542,29 @@ static int run_plans(std::vector<Plan>& plans, cudaStream_t st, std::vector<int6
   };
   cudaError_t e;
   if ((e = cudaMemcpyAsync(drd, rds.data(), sizeof(ReqDev) * rds.size(), cudaMemcpyHostToDevice, st)) ||
+      (e = cudaMemcpyAsync(dgi, gi.data(), sizeof(G1Item) * gi.size(), cudaMemcpyHostToDevice, st)) ||
       (e = cudaMemcpyAsync(dci, ci.data(), sizeof(CoarseItem) * ci.size(), cudaMemcpyHostToDevice, st)) ||
       (e = cudaMemcpyAsync(dfi, fi.data(), sizeof(FineItem) * fi.size(), cudaMemcpyHostToDevice, st)))
     return done(fail(MARFA_E_CUDA, "upload of work lists failed: %s", cudaGetErrorString(e)));
-  if (count && ((e = cudaMemsetAsync(dcc, 0, sz_cc, st)) || (e = cudaMemsetAsync(dfc, 0, sz_fc, st))))
+  if (count && ((e = cudaMemsetAsync(dgc, 0, sz_gc, st)) || (e = cudaMemsetAsync(dcc, 0, sz_cc, st)) ||
+                (e = cudaMemsetAsync(dfc, 0, sz_fc, st))))
     return done(fail(MARFA_E_CUDA, "count buffers: %s", cudaGetErrorString(e)));
   cudaEvent_t ev = timing_begin(st);
-  launch_coarse(drd, dci, (int)ci.size(), dcc, st);
+  launch_g1(drd, dgi, (int)gi.size(), dgc, st);
   timing_end(ev, 1, st);
+  if ((e = cudaGetLastError())) return done(fail(MARFA_E_CUDA, "grid-1 kernel: %s", cudaGetErrorString(e)));
+  ev = timing_begin(st);
+  launch_coarse(drd, dci, (int)ci.size(), dcc, st);
+  timing_end(ev, 2, st);
   if ((e = cudaGetLastError())) return done(fail(MARFA_E_CUDA, "coarse kernel: %s", cudaGetErrorString(e)));
   ev = timing_begin(st);
   launch_fine(drd, dfi, (int)fi.size(), dfc, st);
-  timing_end(ev, 2, st);
+  timing_end(ev, 3, st);
   if ((e = cudaGetLastError())) return done(fail(MARFA_E_CUDA, "fine kernel: %s", cudaGetErrorString(e)));
   if (count) {
-    std::vector<int64_t> hc(ci.size() * kCoarseWarps), hf(fi.size());
-    if ((e = cudaMemcpyAsync(hc.data(), dcc, 8 * hc.size(), cudaMemcpyDeviceToHost, st)) ||
+    std::vector<int64_t> hg(gi.size()), hc(ci.size()), hf(fi.size());
+    if ((e = cudaMemcpyAsync(hg.data(), dgc, 8 * hg.size(), cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaMemcpyAsync(hc.data(), dcc, 8 * hc.size(), cudaMemcpyDeviceToHost, st)) ||
         (e = cudaMemcpyAsync(hf.data(), dfc, 8 * hf.size(), cudaMemcpyDeviceToHost, st)) ||
         (e = cudaStreamSynchronize(st)))
       return done(fail(MARFA_E_CUDA, "count read-back failed: %s", cudaGetErrorString(e)));
@@ -559,11 +572,9 @@ static int run_plans(std::vector<Plan>& plans, cudaStream_t st, std::vector<int6
     for (size_t q = 0; q < plans.size(); ++q) {
       coarse_counts[q].assign((size_t)plans[q].n_levels * 11, 0);
     }
-    for (size_t k = 0; k < ci.size(); ++k) {
-      int64_t t = 0;
-      for (int w = 0; w < kCoarseWarps; ++w) t += hc[k * kCoarseWarps + w];
-      coarse_counts[ci[k].req][(size_t)ci[k].level * 11 + ci[k].grid - 1] += t;
-    }
+    for (size_t k = 0; k < gi.size(); ++k) coarse_counts[gi[k].req][(size_t)gi[k].level * 11] += hg[k];
+    for (size_t k = 0; k < ci.size(); ++k)
+      coarse_counts[ci[k].req][(size_t)ci[k].level * 11 + ci[k].grid - 1] += hc[k];
     for (size_t k = 0; k < fi.size(); ++k)
       coarse_counts[fi[k].req][(size_t)fi[k].level * 11 + 10] += hf[k];
     (void)fine_counts;

@@ -79,9 +79,10 @@ struct ReqDev {
   int64_t npts;
 };
 
-// One CTA of the coarse kernel: 8 warps, each a block of kPairs consecutive node pairs.
+// One CTA of the kernel of grids 2..10: kCPairs consecutive node pairs of one grid.
 struct CoarseItem {
-  int32_t req, level, grid, block0;
+  int32_t req, level, grid, pad;
+  int64_t m0;  // first pair
 };
 // One CTA of the finest-grid kernel: 1024 finest nodes of one level.
 struct FineItem {
@@ -89,8 +90,17 @@ struct FineItem {
   int64_t k0;  // first node of the tile (multiple of 4)
 };
 
-constexpr int kPairs = 8;            // node pairs per warp block in the coarse kernel
-constexpr int kCoarseWarps = 8;
+// One CTA of the G1 kernel: kG1Pairs consecutive node pairs of grid 1 of one level.
+struct G1Item {
+  int32_t req, level;
+  int64_t m0;  // first pair
+};
+
+constexpr int kG1Pairs = 32;         // node pairs per G1 tile (one per lane)
+constexpr int kG1Warps = 8;          // warps of a G1 CTA, each takes every 8th staged line
+constexpr int kG1Batch = 512;        // lines staged in shared memory at a time
+constexpr int kCPairs = 32;          // node pairs per tile of grids 2..10
+constexpr int kCWarps = 4;           // warps of a grids-2..10 CTA
 constexpr int kFineThreads = 256;
 constexpr int kFinePerThread = 4;
 constexpr int kFineTile = kFineThreads * kFinePerThread;
@@ -112,6 +122,8 @@ struct PrepArgs {
 
 // kernels (marfa_kernels.cu)
 void launch_level_prep(const PrepArgs& a, int n_levels, cudaStream_t st);
+void launch_g1(const ReqDev* reqs, const G1Item* items, int n_items, int64_t* counts,
+               cudaStream_t st);
 void launch_coarse(const ReqDev* reqs, const CoarseItem* items, int n_items, int64_t* counts,
                    cudaStream_t st);
 void launch_fine(const ReqDev* reqs, const FineItem* items, int n_items, int64_t* counts,

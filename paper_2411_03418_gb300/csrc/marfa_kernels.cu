@@ -106,38 +106,39 @@ __device__ __constant__ int64_t kChiBreakFx[3] = {3LL << kFixBits, 150LL << kFix
                                                   300LL << kFixBits};
 
 // Bits i = 0..nb-1 stand for panels base + i; set those in the closed interval [a, b].
-__device__ __forceinline__ uint32_t rmask(int64_t a, int64_t b, int64_t base, int nb) {
+template <typename MT>
+__device__ __forceinline__ MT rmask(int64_t a, int64_t b, int64_t base, int nb) {
   int64_t lo = a - base;
   int64_t hi = b - base;
   if (lo < 0) lo = 0;
   if (hi > nb - 1) hi = nb - 1;
-  if (lo > hi) return 0u;
-  return ((2u << (int)hi) - 1u) & (0xffffffffu << (int)lo);
+  if (lo > hi) return MT(0);
+  return ((MT(2) << (int)hi) - MT(1)) & (~MT(0) << (int)lo);
 }
 
 // Panels of grid g accepted for a line, over panels [base, base + nb). With child set,
 // the accepted panels of grid g are mapped to their two children on grid g + 1 and
 // base/nb refer to grid g + 1.
-__device__ __forceinline__ uint32_t accept_mask(int g, int64_t c, int gst, bool chi,
-                                                int64_t cut, int R_w, int64_t base, int nb,
-                                                bool child) {
+template <typename MT>
+__device__ __forceinline__ MT accept_mask(int g, int64_t c, int gst, bool chi, int64_t cut,
+                                          int R_w, int64_t base, int nb, bool child) {
   const int s = panel_shift(g);
   const int64_t k = child ? 1 : 0, f = child ? 2 : 1;  // panel a of grid g -> children [2a, 2a+1]
   int64_t s_lo = cl_sh(c - cut, s), s_hi = fl_sh(c + cut, s) - 1;
-  uint32_t m = rmask(s_lo * f, s_hi * f + k, base, nb);
-  if (!m) return 0u;
+  MT m = rmask<MT>(s_lo * f, s_hi * f + k, base, nb);
+  if (!m) return MT(0);
   if (gst > g) {
     int64_t R = (int64_t)R_w * step_fx(g);
     int64_t gl = fl_sh(c - R, s), gh = cl_sh(c + R, s) - 1;
-    m &= ~rmask(gl * f, gh * f + k, base, nb);
+    m &= ~rmask<MT>(gl * f, gh * f + k, base, nb);
   }
   if (chi) {
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
       int64_t B = kChiBreakFx[b];
       int64_t s1 = c - B, s2 = c + B;
-      m &= ~rmask((cl_sh(s1, s) - 1) * f, fl_sh(s1, s) * f + k, base, nb);
-      m &= ~rmask((cl_sh(s2, s) - 1) * f, fl_sh(s2, s) * f + k, base, nb);
+      m &= ~rmask<MT>((cl_sh(s1, s) - 1) * f, fl_sh(s1, s) * f + k, base, nb);
+      m &= ~rmask<MT>((cl_sh(s2, s) - 1) * f, fl_sh(s2, s) * f + k, base, nb);
     }
   }
   return m;
@@ -146,8 +147,8 @@ __device__ __forceinline__ uint32_t accept_mask(int g, int64_t c, int gst, bool 
 // Panels of grid g (1..10) owned by a line over [base, base + nb).
 __device__ __forceinline__ uint32_t owned_mask(int g, int64_t c, int gst, bool chi, int64_t cut,
                                                int R_w, int64_t base, int nb) {
-  uint32_t m = accept_mask(g, c, gst, chi, cut, R_w, base, nb, false);
-  if (g > 1 && m) m &= ~accept_mask(g - 1, c, gst, chi, cut, R_w, base, nb, true);
+  uint32_t m = accept_mask<uint32_t>(g, c, gst, chi, cut, R_w, base, nb, false);
+  if (g > 1 && m) m &= ~accept_mask<uint32_t>(g - 1, c, gst, chi, cut, R_w, base, nb, true);
   return m;
 }
 
@@ -174,6 +175,26 @@ struct ChiThr {
     const float C = b == 1 ? 1.084f : (b == 2 ? 0.208f : 0.025f);
     const float r = b == 1 ? 0.027f : (b == 2 ? 0.016f : 0.009f);
     return C * expf(-r * absd);
+  }
+};
+
+// Position of the nodes of a line relative to its centre: with rel = X0 - c (fixed
+// point) and node spacing 2^sh units, node j sits at (j + q + phi) steps, q integer,
+// phi in [0, 1). Then x_j = ((j + q) + phi) * hs with hs = sx * step is formed as
+// fma(j + q, hs, phi * hs): j + q is exact in FP32 and only one rounding remains.
+struct NodeX {
+  float qf, hs, phs, phi;
+  __device__ __forceinline__ void init(int64_t rel, int sh, float sx) {
+    const int64_t q = fl_sh(rel, sh);
+    phi = __ll2float_rn(rel - (q << sh)) * ldexpf(1.0f, -sh);
+    qf = (float)q;
+    hs = sx * ldexpf(1.0f, sh - kFixBits);
+    phs = phi * hs;
+  }
+  __device__ __forceinline__ float x(float jf) const { return fmaf(jf + qf, hs, phs); }
+  // |nu - nu~0| in cm^-1 at node j
+  __device__ __forceinline__ float absd(float jf, int sh) const {
+    return fabsf((jf + qf) + phi) * ldexpf(1.0f, sh - kFixBits);
   }
 };
 
@@ -276,39 +297,235 @@ void launch_level_prep(const PrepArgs& a, int n_levels, cudaStream_t st) {
   k_level_prep<<<grid, 256, 0, st>>>(a);
 }
 
-// ------------------------------------------------------------------ coarse grids
-// One warp = a block of kPairs node pairs (even node 2m and odd node 2m+1 for
-// m = mb .. mb+kPairs-1) of grid g. Even node 2m carries slot L of panel m and slot R
-// of panel m-1, odd node 2m+1 slot M of panel m. The lanes stride over the lines whose
-// centres can own a panel of the block; each lane evaluates its line at the block's
-// nodes it owns; the lane sums are combined across the warp at the end.
+// ------------------------------------------------------------------ grid 1
+// Grid 1 (1 cm^-1 step) carries the long cut-off tails of every line and most of the
+// profile evaluations. A CTA owns kG1Pairs consecutive node pairs of one level: lane p
+// of every warp holds pair p (even node 2m, odd node 2m+1), and the 8 warps split the
+// candidate lines, which are staged in shared memory and read by broadcast. For a line
+// whose tile nodes are all in the far Voigt wing (|z| >= 100) the profile is the two-term
+// series y/(sqrt(pi) r^2)(1 + (3x^2 - y^2)/(2 r^4)), and the chi-factor of branch 1 is a
+// per-line factor times a per-node constant exp(-0.027 |j|); other lines take the exact path.
+__device__ __noinline__ float2 g1_exact_pair(const ReqDev& R, int64_t o, int64_t X0, int j0,
+                                            bool need0, bool need1) {
+  const int sh = panel_shift(1) - 1;
+  const int64_t c = __ldg(R.c + o);
+  const float amp = __ldg(R.amp + o), sx = __ldg(R.sx + o), y = __ldg(R.yv + o);
+  const bool use_chi = (__ldg(R.flags + o) & 1) && R.shape < kShapeConst;
+  NodeX nx;
+  nx.init(X0 - c, sh, sx);
+  ChiThr ct;
+  if (use_chi) ct.init(c, X0, sh);
+  float v[2] = {0.0f, 0.0f};
+  for (int q = 0; q < 2; ++q) {
+    if (!(q ? need1 : need0)) continue;
+    const int j = j0 + q;
+    const float jf = (float)j, xv = nx.x(jf);
+    float f = amp * (R.shape == kShapeVoigt ? voigt_K(xv, y) : shape_f(R.shape, xv, y));
+    if (use_chi) f *= ct.value(j, nx.absd(jf, sh));
+    v[q] = f;
+  }
+  return make_float2(v[0], v[1]);
+}
+
+__device__ __forceinline__ void comp_merge(float& s, float& c, float s2, float c2) {
+  const float t = s + s2;
+  const float bp = t - s;
+  const float e = (s - (t - bp)) + (s2 - bp);
+  s = t;
+  c = (c + c2) + e;
+}
+
 template <bool COUNT>
-__global__ void __launch_bounds__(kCoarseWarps * 32)
+__global__ void __launch_bounds__(kG1Warps * 32)
+    k_g1(const ReqDev* __restrict__ reqs, const G1Item* __restrict__ items,
+         int64_t* __restrict__ counts) {
+  __shared__ float4 sA[kG1Batch];               // q, sx, phi*sx, y^2
+  __shared__ float4 sB[kG1Batch];               // a_centre, a_left, a_right, -y^2/2
+  __shared__ unsigned long long sM[kG1Batch];   // owned panels m0-1 .. m0+31
+  __shared__ int4 sC[kG1Batch];                 // j_left3, j_right3, exact-path flag, -
+  __shared__ float sRed[kG1Warps][8][32];
+  __shared__ int64_t sCnt[kG1Warps];
+  const G1Item it = items[blockIdx.x];
+  const ReqDev& R = reqs[it.req];
+  const int lev = it.level;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int s = panel_shift(1);  // panel 2 cm^-1 = 2^44 units; nodes every 2^43
+  const int64_t m_first = R.m_first[1], m_last = m_first + R.npan[1] - 1;
+  const int64_t m0 = it.m0, base = m0 - 1;
+  const int nb = kG1Pairs + 1;
+  const uint64_t win = rmask<uint64_t>(m_first, m_last, base, nb);
+  const int64_t X0 = m0 << s;  // node 2 m0
+  const int64_t cut = R.cut_fx;
+  const LevelDev L = R.lev[lev];
+  const int64_t i_lo = lower_idx(R, (base << s) - cut - L.smax);
+  const int64_t i_hi = upper_idx(R, ((m0 + kG1Pairs) << s) + cut - L.smin);
+  const int64_t off = (int64_t)lev * R.n_lines;
+  const bool voigt = R.shape == kShapeVoigt;
+  const bool physical = R.shape < kShapeConst;
+
+  const int p = lane, j0 = 2 * p;
+  const float f0 = (float)j0, f1 = (float)(j0 + 1);
+  const float rR0 = expf(-0.027f * f0), rR1 = expf(-0.027f * f1);
+  const float rL0 = expf(0.027f * f0), rL1 = expf(0.027f * f1);
+  float eS = 0.f, eC = 0.f, lS = 0.f, lC = 0.f, rS = 0.f, rC = 0.f, mS = 0.f, mC = 0.f;
+  int64_t nev = 0;
+
+  for (int64_t b0 = i_lo; b0 < i_hi; b0 += kG1Batch) {
+    const int nbat = (int)min((int64_t)kG1Batch, i_hi - b0);
+    __syncthreads();
+    for (int k = tid; k < nbat; k += kG1Warps * 32) {
+      const int64_t o = off + b0 + k;
+      const int64_t c = __ldg(R.c + o);
+      const int gst = __ldg(R.gstar + o);
+      const bool chi = __ldg(R.flags + o) & 1;
+      const uint64_t msk = accept_mask<uint64_t>(1, c, gst, chi, cut, R.R_w, base, nb, false) & win;
+      const float amp = __ldg(R.amp + o), sx = __ldg(R.sx + o), y = __ldg(R.yv + o);
+      NodeX nx;
+      nx.init(X0 - c, s - 1, sx);
+      // nearest evaluated node (j = 0 .. 2 kG1Pairs - 1) to the centre
+      const int64_t Xh = X0 + ((int64_t)(2 * kG1Pairs - 1) << (s - 1));
+      const int64_t dn = c < X0 ? X0 - c : (c > Xh ? c - Xh : 0);
+      const bool far = voigt && (__ll2float_rn(dn) * ldexpf(1.0f, -kFixBits) * sx >= 100.0f || y >= 100.0f);
+      int jL = -(1 << 30), jR = 1 << 30;
+      bool exact = !far;
+      const float aC = amp * y * kInvSqrtPi;
+      float aL = aC, aR = aC;
+      if (chi && physical) {
+        jR = clamp32(cl_sh(c + kChiBreakFx[0] - X0, s - 1));
+        jL = clamp32(fl_sh(c - kChiBreakFx[0] - X0, s - 1));
+        if (cut > kChiBreakFx[1]) {  // owned nodes may lie beyond 150 cm^-1 (branches 2, 3)
+          const int jR150 = clamp32(fl_sh(c + kChiBreakFx[1] - X0, s - 1));
+          const int jL150 = clamp32(cl_sh(c - kChiBreakFx[1] - X0, s - 1));
+          if (jR150 < 2 * kG1Pairs - 1 || jL150 > 0) exact = true;
+        }
+        const float d0 = (nx.qf + nx.phi);  // offset of node 0 from the centre, cm^-1
+        aR = aC * 1.084f * expf(-0.027f * d0);
+        aL = aC * 1.084f * expf(0.027f * d0);
+      }
+      sA[k] = make_float4(nx.qf, nx.hs, nx.phs, y * y);
+      sB[k] = make_float4(aC, aL, aR, -0.5f * y * y);
+      sM[k] = msk;
+      sC[k] = make_int4(jL, jR, exact ? 1 : 0, 0);
+    }
+    __syncthreads();
+    float pe = 0.f, pl = 0.f, pr = 0.f, pm = 0.f;
+    for (int k = warp; k < nbat; k += kG1Warps) {
+      const uint64_t msk = sM[k];
+      const bool bL = (msk >> (p + 1)) & 1ull;  // panel m0+p: L of node 2m, M of node 2m+1
+      const bool bR = (msk >> p) & 1ull;        // panel m0+p-1: R of node 2m
+      if (!(bL || bR)) continue;
+      const int4 C = sC[k];
+      float v0, v1;
+      if (!C.z) {
+        const float4 a = sA[k], b = sB[k];
+        const float x0 = fmaf(f0 + a.x, a.y, a.z), x02 = x0 * x0;
+        const float i0 = __fdividef(1.0f, x02 + a.w);
+        const float s0 = fmaf(fmaf(1.5f, x02, b.w), i0 * i0, 1.0f);
+        const float am0 = j0 >= C.y ? b.z * rR0 : (j0 <= C.x ? b.y * rL0 : b.x);
+        v0 = am0 * i0 * s0;
+        const float x1 = fmaf(f1 + a.x, a.y, a.z), x12 = x1 * x1;
+        const float i1 = __fdividef(1.0f, x12 + a.w);
+        const float s1 = fmaf(fmaf(1.5f, x12, b.w), i1 * i1, 1.0f);
+        const float am1 = j0 + 1 >= C.y ? b.z * rR1 : (j0 + 1 <= C.x ? b.y * rL1 : b.x);
+        v1 = bL ? am1 * i1 * s1 : 0.0f;
+      } else {
+        const float2 v = g1_exact_pair(R, off + b0 + k, X0, j0, true, bL);
+        v0 = v.x;
+        v1 = v.y;
+      }
+      if (bL && bR) pe += v0; else if (bL) pl += v0; else pr += v0;
+      pm += v1;
+      if (COUNT) nev += 1 + (bL ? 1 : 0);
+    }
+    kahan_add(eS, eC, pe);
+    kahan_add(lS, lC, pl);
+    kahan_add(rS, rC, pr);
+    kahan_add(mS, mC, pm);
+  }
+  sRed[warp][0][lane] = eS; sRed[warp][1][lane] = eC;
+  sRed[warp][2][lane] = lS; sRed[warp][3][lane] = lC;
+  sRed[warp][4][lane] = rS; sRed[warp][5][lane] = rC;
+  sRed[warp][6][lane] = mS; sRed[warp][7][lane] = mC;
+  if (COUNT) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) nev += __shfl_xor_sync(0xffffffffu, nev, o);
+    if (lane == 0) sCnt[warp] = nev;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    float a[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) a[q] = sRed[0][q][lane];
+    for (int w = 1; w < kG1Warps; ++w) {
+      comp_merge(a[0], a[1], sRed[w][0][lane], sRed[w][1][lane]);
+      comp_merge(a[2], a[3], sRed[w][2][lane], sRed[w][3][lane]);
+      comp_merge(a[4], a[5], sRed[w][4][lane], sRed[w][5][lane]);
+      comp_merge(a[6], a[7], sRed[w][6][lane], sRed[w][7][lane]);
+    }
+    float ls = a[0], lc = a[1], rs = a[0], rc = a[1];
+    comp_merge(ls, lc, a[2], a[3]);
+    comp_merge(rs, rc, a[4], a[5]);
+    float* gp = R.slots + (int64_t)lev * R.slots_per_level + R.slot_off[1];
+    const int64_t np = R.npan[1];
+    const int64_t m = m0 + p;
+    if (m <= m_last) {
+      gp[m - m_first] = ls + lc;
+      gp[np + (m - m_first)] = a[6] + a[7];
+    }
+    if (m - 1 >= m_first && m - 1 <= m_last) gp[2 * np + (m - 1 - m_first)] = rs + rc;
+    if (COUNT && lane == 0) {
+      int64_t t = 0;
+      for (int w = 0; w < kG1Warps; ++w) t += sCnt[w];
+      counts[blockIdx.x] = t;
+    }
+  }
+}
+
+void launch_g1(const ReqDev* reqs, const G1Item* items, int n_items, int64_t* counts,
+               cudaStream_t st) {
+  if (n_items <= 0) return;
+  if (counts)
+    k_g1<true><<<n_items, kG1Warps * 32, 0, st>>>(reqs, items, counts);
+  else
+    k_g1<false><<<n_items, kG1Warps * 32, 0, st>>>(reqs, items, counts);
+}
+
+// ------------------------------------------------------------------ grids 2..10
+// A CTA owns kCPairs consecutive node pairs of grid g of one level. Each thread takes
+// one candidate line at a time, forms the exact mask of the panels the line owns in
+// the tile, evaluates the profile at the nodes of those panels only, and adds the
+// values into lane-private shared-memory slots (acc[pair][lane]); the slots are summed
+// over lanes and warps in a fixed order at the end.
+template <bool COUNT>
+__global__ void __launch_bounds__(kCWarps * 32)
     k_coarse(const ReqDev* __restrict__ reqs, const CoarseItem* __restrict__ items,
              int64_t* __restrict__ counts) {
+  __shared__ float accL[kCWarps][kCPairs][32];
+  __shared__ float accM[kCWarps][kCPairs][32];
+  __shared__ float accR[kCWarps][kCPairs][32];
+  __shared__ int64_t sCnt[kCWarps];
   const CoarseItem it = items[blockIdx.x];
   const ReqDev& R = reqs[it.req];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = it.grid;
   const int lev = it.level;
   const int64_t m_first = R.m_first[g];
   const int64_t m_last = m_first + R.npan[g] - 1;
-  const int64_t mb = m_first + ((int64_t)it.block0 + warp) * kPairs;
-  if (mb > m_last + 1) return;  // whole warp leaves together
-
-  const LevelDev L = R.lev[lev];
+  const int64_t m0 = it.m0;
   const int s = panel_shift(g);
   const int64_t cut = R.cut_fx;
-  const int64_t base = mb - 1;  // mask bit i <-> panel mb - 1 + i
-  const int nb = kPairs + 1;
-  uint32_t win = rmask(m_first, m_last, base, nb);
-
-  // candidate bands for the centres
+  const int64_t base = m0 - 1;  // mask bit b <-> panel m0 - 1 + b
+  const int nb = kCPairs + 1;
+  const uint64_t win = rmask<uint64_t>(m_first, m_last, base, nb);
+  for (int p = 0; p < kCPairs; ++p) {
+    accL[warp][p][lane] = 0.0f;
+    accM[warp][p][lane] = 0.0f;
+    accR[warp][p][lane] = 0.0f;
+  }
+  const LevelDev L = R.lev[lev];
   Bands bd;
   bd.n = 0;
-  if (g == 1) {
-    bd.add(R, L, (base << s) - cut, ((base + nb) << s) + cut);
-  } else {
+  {
     const int64_t P = int64_t(1) << s;
     const int64_t A = (base >> 1) << (s + 1);
     const int64_t B = (((base + nb - 1) >> 1) + 1) << (s + 1);
@@ -326,72 +543,77 @@ __global__ void __launch_bounds__(kCoarseWarps * 32)
     }
     bd.merge();
   }
-
-  float sL[kPairs], cL[kPairs], sR[kPairs], cR[kPairs], sM[kPairs], cM[kPairs];
-#pragma unroll
-  for (int j = 0; j < kPairs; ++j) sL[j] = cL[j] = sR[j] = cR[j] = sM[j] = cM[j] = 0.0f;
-  int64_t nev = 0;
-
   const int64_t lo_off = (int64_t)lev * R.n_lines;
-  const int64_t X0 = mb << s;            // position of node 2 mb
-  const float to_h = ldexpf(1.0f, 1 - s);  // fixed units -> units of h_g
-  const float hg = ldexpf(1.0f, 1 - g);
+  const int64_t X0 = m0 << s;  // position of node 2 m0 (j = 0)
   const bool physical = R.shape < kShapeConst;
-
+  const bool voigt = R.shape == kShapeVoigt;
+  int64_t nev = 0;
+  __syncwarp();
   for (int r = 0; r < bd.n; ++r) {
-    for (int64_t i = bd.lo[r] + lane; i < bd.hi[r]; i += 32) {
+    for (int64_t i0 = bd.lo[r]; i0 < bd.hi[r]; i0 += kCWarps * 32) {
+      const int64_t i = i0 + tid;
+      if (i >= bd.hi[r]) continue;
       const int64_t c = __ldg(R.c + lo_off + i);
       const int gst = __ldg(R.gstar + lo_off + i);
       const bool chi = __ldg(R.flags + lo_off + i) & 1;
-      uint32_t own = owned_mask(g, c, gst, chi, cut, R.R_w, base, nb) & win;
+      uint64_t own = accept_mask<uint64_t>(g, c, gst, chi, cut, R.R_w, base, nb, false) & win;
+      if (own) own &= ~accept_mask<uint64_t>(g - 1, c, gst, chi, cut, R.R_w, base, nb, true);
       if (!own) continue;
       const float amp = __ldg(R.amp + lo_off + i);
-      const float hs = __ldg(R.sx + lo_off + i) * hg;
+      const float sx = __ldg(R.sx + lo_off + i);
       const float y = __ldg(R.yv + lo_off + i);
-      const float t0 = __ll2float_rn(X0 - c) * to_h;
+      NodeX nx;
+      nx.init(X0 - c, s - 1, sx);
       ChiThr ct;
       const bool use_chi = chi && physical;
       if (use_chi) ct.init(c, X0, s - 1);
-#pragma unroll
-      for (int j = 0; j < 2 * kPairs; ++j) {
-        const int p = j >> 1;
-        const bool oA = (own >> (p + 1)) & 1u;         // L (even) or M (odd) of panel mb+p
-        const bool oR = !(j & 1) && ((own >> p) & 1u);  // R of panel mb+p-1 (even only)
-        if (!(oA || oR)) continue;
-        const float t = t0 + (float)j;
-        float v = amp * shape_f(R.shape, t * hs, y);
-        if (use_chi) v *= ct.value(j, fabsf(t) * hg);
-        if (j & 1) {
-          kahan_add(sM[p], cM[p], v);
-        } else {
-          if (oA) kahan_add(sL[p], cL[p], v);
-          if (oR) kahan_add(sR[p], cR[p], v);
+      // pair p uses bits p (R slot of node 2p) and p + 1 (L of node 2p, M of node 2p+1)
+      const int pa = max(__ffsll((long long)own) - 2, 0);
+      const int pb = min(63 - __clzll((long long)own), kCPairs - 1);
+      for (int p = pa; p <= pb; ++p) {
+        const bool bR = (own >> p) & 1ull, bL = (own >> (p + 1)) & 1ull;
+        if (!(bR || bL)) continue;
+        const float jf = (float)(2 * p);
+        const float xv = nx.x(jf);
+        float v = amp * (voigt ? voigt_K(xv, y) : shape_f(R.shape, xv, y));
+        if (use_chi) v *= ct.value(2 * p, nx.absd(jf, s - 1));
+        if (bL) accL[warp][p][lane] += v;
+        if (bR) accR[warp][p][lane] += v;
+        if (bL) {
+          const float xw = nx.x(jf + 1.0f);
+          float w = amp * (voigt ? voigt_K(xw, y) : shape_f(R.shape, xw, y));
+          if (use_chi) w *= ct.value(2 * p + 1, nx.absd(jf + 1.0f, s - 1));
+          accM[warp][p][lane] += w;
         }
-        if (COUNT) ++nev;
+        if (COUNT) nev += 1 + (bL ? 1 : 0);
       }
-    }
-  }
-
-  float* base_ptr = R.slots + (int64_t)lev * R.slots_per_level + R.slot_off[g];
-  const int64_t np = R.npan[g];
-#pragma unroll
-  for (int j = 0; j < kPairs; ++j) {
-    const float vL = warp_sum_comp(sL[j], cL[j]);
-    const float vM = warp_sum_comp(sM[j], cM[j]);
-    const float vR = warp_sum_comp(sR[j], cR[j]);
-    if (lane == j) {
-      const int64_t m = mb + j;
-      if (m <= m_last) {
-        base_ptr[m - m_first] = vL;
-        base_ptr[np + (m - m_first)] = vM;
-      }
-      if (m - 1 >= m_first && m - 1 <= m_last) base_ptr[2 * np + (m - 1 - m_first)] = vR;
     }
   }
   if (COUNT) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) nev += __shfl_xor_sync(0xffffffffu, nev, o);
-    if (lane == 0) counts[(int64_t)blockIdx.x * kCoarseWarps + warp] = nev;
+    if (lane == 0) sCnt[warp] = nev;
+  }
+  __syncthreads();
+  // thread t < 3 kCPairs sums slot (t / kCPairs, pair t % kCPairs) over warps and lanes
+  if (tid < 3 * kCPairs) {
+    const int kind = tid / kCPairs, p = tid % kCPairs;
+    float (*acc)[kCPairs][32] = kind == 0 ? accL : (kind == 1 ? accM : accR);
+    float sum = 0.0f, cmp = 0.0f;
+    for (int w = 0; w < kCWarps; ++w)
+      for (int l = 0; l < 32; ++l) kahan_add(sum, cmp, acc[w][p][(l + p) & 31]);
+    const float v = sum + cmp;
+    float* gp = R.slots + (int64_t)lev * R.slots_per_level + R.slot_off[g];
+    const int64_t np = R.npan[g];
+    const int64_t m = m0 + p;
+    if (kind == 0 && m <= m_last) gp[m - m_first] = v;
+    if (kind == 1 && m <= m_last) gp[np + (m - m_first)] = v;
+    if (kind == 2 && m - 1 >= m_first && m - 1 <= m_last) gp[2 * np + (m - 1 - m_first)] = v;
+  }
+  if (COUNT && tid == 0) {
+    int64_t t = 0;
+    for (int w = 0; w < kCWarps; ++w) t += sCnt[w];
+    counts[blockIdx.x] = t;
   }
 }
 
@@ -399,9 +621,9 @@ void launch_coarse(const ReqDev* reqs, const CoarseItem* items, int n_items, int
                    cudaStream_t st) {
   if (n_items <= 0) return;
   if (counts)
-    k_coarse<true><<<n_items, kCoarseWarps * 32, 0, st>>>(reqs, items, counts);
+    k_coarse<true><<<n_items, kCWarps * 32, 0, st>>>(reqs, items, counts);
   else
-    k_coarse<false><<<n_items, kCoarseWarps * 32, 0, st>>>(reqs, items, counts);
+    k_coarse<false><<<n_items, kCWarps * 32, 0, st>>>(reqs, items, counts);
 }
 
 // ------------------------------------------------------------------ finest grid + cascade
@@ -452,15 +674,14 @@ __global__ void __launch_bounds__(kFineThreads)
     bd.merge();
     const int64_t p10 = k0 >> 3;  // the G10 panel of the four nodes
     const int64_t lo_off = (int64_t)lev * R.n_lines;
-    const float to_h = ldexpf(1.0f, -kFineShift);
-    const float h11 = ldexpf(1.0f, -kFineBits);
     const bool physical = R.shape < kShapeConst;
+    const bool voigt = R.shape == kShapeVoigt;
     for (int r = 0; r < bd.n; ++r) {
       for (int64_t i = bd.lo[r]; i < bd.hi[r]; ++i) {
         const int64_t c = __ldg(R.c + lo_off + i);
         const int gst = __ldg(R.gstar + lo_off + i);
         const bool chi = __ldg(R.flags + lo_off + i) & 1;
-        if (accept_mask(kNGrid, c, gst, chi, cut, R.R_w, p10, 1, false)) continue;
+        if (accept_mask<uint32_t>(kNGrid, c, gst, chi, cut, R.R_w, p10, 1, false)) continue;
         uint32_t own = 0;
 #pragma unroll
         for (int q = 0; q < kFinePerThread; ++q) {
@@ -470,18 +691,20 @@ __global__ void __launch_bounds__(kFineThreads)
         own &= valid;
         if (!own) continue;
         const float amp = __ldg(R.amp + lo_off + i);
-        const float hs = __ldg(R.sx + lo_off + i) * h11;
+        const float sx = __ldg(R.sx + lo_off + i);
         const float y = __ldg(R.yv + lo_off + i);
-        const float t0 = __ll2float_rn(X0 - c) * to_h;
+        NodeX nx;
+        nx.init(X0 - c, kFineShift, sx);
         ChiThr ct;
         const bool use_chi = chi && physical;
         if (use_chi) ct.init(c, X0, kFineShift);
 #pragma unroll
         for (int q = 0; q < kFinePerThread; ++q) {
           if (!((own >> q) & 1u)) continue;
-          const float t = t0 + (float)q;
-          float v = amp * shape_f(R.shape, t * hs, y);
-          if (use_chi) v *= ct.value(q, fabsf(t) * h11);
+          const float jf = (float)q;
+          const float xv = nx.x(jf);
+          float v = amp * (voigt ? voigt_K(xv, y) : shape_f(R.shape, xv, y));
+          if (use_chi) v *= ct.value(q, nx.absd(jf, kFineShift));
           kahan_add(acc[q], cmp[q], v);
           if (COUNT) ++nev;
         }
@@ -586,7 +809,7 @@ __global__ void k_diag_owned(const ReqDev* __restrict__ req, int lev, int grid, 
     const int64_t k = first + i;
     const int64_t d = (k << kFineShift) - c;
     const bool within = (d < 0 ? -d : d) <= R.cut_fx;
-    v = within && !accept_mask(kNGrid, c, gst, chi, R.cut_fx, R.R_w, k >> 3, 1, false);
+    v = within && !accept_mask<uint32_t>(kNGrid, c, gst, chi, R.cut_fx, R.R_w, k >> 3, 1, false);
   }
   out[line * (int64_t)count + i] = v;
 }

@@ -82,10 +82,9 @@ __device__ __forceinline__ float voigt_far(float x, float y) {
   return y * kInvSqrtPi * inv * (1.0f + t);
 }
 
-__device__ __forceinline__ float voigt_K(float x, float y) {
-  float ax = fabsf(x);
+// Everything but the far wing, kept out of line so that unrolled callers stay small.
+__device__ __noinline__ float voigt_K_near(float ax, float y) {
   float r2 = fmaf(ax, ax, y * y);
-  if (r2 >= 1.0e4f) return voigt_far(ax, y);
   if (r2 >= 64.0f) return voigt_asym<5>(ax, y);
   if (r2 >= 20.25f) {
     float a = voigt_asym<14>(ax, y);
@@ -104,6 +103,13 @@ __device__ __forceinline__ float voigt_K(float x, float y) {
   float u = (ax - (0.9f * ix + 0.45f)) * (1.0f / 0.45f);
   float v = (y - (1.0f + 1.75f * iy + 0.875f)) * (1.0f / 0.875f);
   return voigt_cell(9 + ix * 2 + iy, u, v);
+}
+
+__device__ __forceinline__ float voigt_K(float x, float y) {
+  float ax = fabsf(x);
+  float r2 = fmaf(ax, ax, y * y);
+  if (r2 >= 1.0e4f) return voigt_far(ax, y);
+  return voigt_K_near(ax, y);
 }
 
 }  // namespace marfa
