@@ -227,11 +227,10 @@ def main():
     e2e_value = units * args.steps / t_e2e
 
     # roofline of the dominant kernel (FP32 pipe, algorithmic flops per evaluation)
-    names = ["level_prep", "grid1", "grids2_10", "finest"]
+    names = ["level_prep"] + [f"grid{g}" for g in range(1, 11)] + ["finest"]
     dom = int(np.argmax(kms))
     dom_ms = kms[dom] / max(1, klaunch[dom])
-    grid_evals = {0: 0, 1: counts[:, 0].sum(), 2: counts[:, 1:10].sum(), 3: counts[:, 10].sum()}
-    dom_evals = float(grid_evals[dom])
+    dom_evals = float(counts[:, dom - 1].sum()) if dom > 0 else 0.0
     achieved = dom_evals * FLOPS_PER_EVAL / (dom_ms * 1e-3) / 1e12
     mhz, src = peaks()
     peak = N_SM * FP32_LANES * 2 * mhz * 1e6 / 1e12

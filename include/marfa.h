@@ -193,9 +193,10 @@ int marfa_diag_absorption_counted(const marfa_lines_t* lines, const marfa_level_
 
 /* Per-kernel device time: enable = 1 clears the totals and starts recording CUDA events
  * around every kernel launch of this library (on the launch stream); enable = 0 stops,
- * waits for the recorded events and writes, for the four kernels (0 level preparation,
- * 1 grid 1, 2 grids 2..10, 3 finest grid + cascade), the summed milliseconds to ms[4]
- * and the launch counts to launches[4] (host arrays, may be NULL). */
+ * waits for the recorded events and writes, for the twelve kernel launches of a call
+ * (0 level preparation, g = 1..10 the sums on grid g, 11 finest grid + cascade), the
+ * summed milliseconds to ms[12] and the launch counts to launches[12] (host arrays,
+ * may be NULL). */
 int marfa_diag_kernel_timing(int32_t enable, double* ms, int64_t* launches);
 
 #ifdef __cplusplus

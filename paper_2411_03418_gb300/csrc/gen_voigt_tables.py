@@ -9,13 +9,14 @@ The FP32 Voigt K(x, y) = Re w(x + iy) (Eq. (8)) is split by region:
       w(z) ~ i / (sqrt(pi) z) sum_n (2n-1)!! / (2 z^2)^n,
   with the exponentially small Gaussian term exp(y^2 - x^2) cos(2xy) added back
   near the real axis (y < 1), where it is the Doppler core of the line;
-* |z| < 4.5, y < 1: the exact split w(z) = exp(-z^2) + (2i/sqrt(pi)) F(z), F the
+* |x| < 12, y < 1: the exact split w(z) = exp(-z^2) + (2i/sqrt(pi)) F(z), F the
   Dawson function of complex argument (A&S 7.1.3 / 7.1.17), so that
       K = exp(y^2 - x^2) cos(2xy) - (2/sqrt(pi)) y Psi(x, y^2),
       Psi(x, y^2) = Im F(x + iy) / y,
   and Psi, an entire function of (x, y^2), is tabulated as a bivariate polynomial
   on cells of x-width 0.5 (this keeps the relative accuracy of K where the Gaussian
-  core and the Lorentz wing meet);
+  core and the Lorentz wing meet, and gives the whole near wing one code path); the
+  Gaussian term is dropped beyond |x| = 6.5, where it is below 4e-19;
 * |z| < 4.5, y >= 1: K itself is smooth and bounded away from zero there and is
   tabulated as a bivariate polynomial on 0.9 x 1.75 cells.
 
@@ -29,8 +30,8 @@ import numpy as np
 
 mp.mp.dps = 30
 DEG = 8
-CORE_W = 0.5          # x-width of a core cell; cells cover x in [0, 4.5]
-CORE_NX = 9
+CORE_W = 0.5          # x-width of a core cell; cells cover x in [0, 12]
+CORE_NX = 24
 G_WX, G_WY = 0.9, 1.75
 G_NX, G_NY = 5, 2     # x in [0, 4.5], y in [1, 4.5]
 
@@ -77,7 +78,7 @@ def main():
         f.write(f"// {CORE_NX} core cells (Psi = Im F(x+iy)/y over x-width {CORE_W}, y^2 in [0,1]),\n")
         f.write(f"// then {G_NX}x{G_NY} cells of K for y >= 1 ({G_WX} x {G_WY}), row-major [ix][iy].\n")
         f.write(f"// The includer defines MARFA_VOIGT_QUAL (storage qualifiers of the table).\n")
-        f.write(f"#define VOIGT_DEG {DEG}\n#define VOIGT_NCELL {len(cells)}\n")
+        f.write(f"#define VOIGT_DEG {DEG}\n#define VOIGT_NCELL {len(cells)}\n#define VOIGT_NPSI {CORE_NX}\n")
         f.write("MARFA_VOIGT_QUAL float kVoigtCells[VOIGT_NCELL * (VOIGT_DEG + 1) * (VOIGT_DEG + 1)] = {\n")
         for c in cells:
             f.write("  " + ", ".join(f"{float(np.float32(v))!r}f" for v in c.ravel()) + ",\n")

@@ -113,8 +113,8 @@ static void timing_end(cudaEvent_t a, int kind, cudaStream_t st) {
 
 extern "C" int marfa_diag_kernel_timing(int32_t enable, double* ms, int64_t* launches) {
   std::lock_guard<std::mutex> lk(g_tmu);
-  double t[4] = {0, 0, 0, 0};
-  int64_t c[4] = {0, 0, 0, 0};
+  double t[kNGrid + 2] = {0};
+  int64_t c[kNGrid + 2] = {0};
   for (auto& x : g_tl) {
     float f = 0;
     if (cudaEventSynchronize(x.b) == cudaSuccess && cudaEventElapsedTime(&f, x.a, x.b) == cudaSuccess) {
@@ -126,8 +126,8 @@ extern "C" int marfa_diag_kernel_timing(int32_t enable, double* ms, int64_t* lau
   }
   g_tl.clear();
   g_timing = enable != 0;
-  if (ms) std::copy(t, t + 4, ms);
-  if (launches) std::copy(c, c + 4, launches);
+  if (ms) std::copy(t, t + kNGrid + 2, ms);
+  if (launches) std::copy(c, c + kNGrid + 2, launches);
   return MARFA_OK;
 }
 
@@ -219,10 +219,10 @@ extern "C" int marfa_prepare_lines(const marfa_line_t* lines, int64_t n, const m
   }
   L->delta_min = dmin;
   L->delta_max = dmax;
-  // bucket index: about four lines per bucket on average
+  // bucket index: about one line per two buckets on average, at most 2^26 buckets
   const int64_t span = std::max<int64_t>(key[n - 1] - key[0], 1);
   int bs = 20;
-  while (bs < 50 && ((int64_t)1 << (bs + 1)) * n <= 4 * span) ++bs;
+  while (bs < 50 && (((int64_t)1 << (bs + 1)) * 2 * n <= span || (span >> bs) > ((int64_t)1 << 26))) ++bs;
   L->bshift = bs;
   L->key_base = (key[0] >> bs) << bs;
   const int64_t nb64 = ((key[n - 1] - L->key_base) >> bs) + 1;
@@ -424,9 +424,9 @@ static int build_plan(Plan& P, const marfa_lines_t* L, const marfa_level_t* leve
       P.g1.push_back(G1Item{req_idx, l, m0});
   for (int g = 2; g <= kNGrid; ++g)
     for (int l = 0; l < n_levels; ++l)
-      for (int64_t m0 = R.m_first[g]; m0 <= R.m_first[g] + R.npan[g]; m0 += kCPairs)
+      for (int64_t m0 = R.m_first[g]; m0 <= R.m_first[g] + R.npan[g]; m0 += (int64_t)kCPairs * kCWarps)
         P.coarse.push_back(CoarseItem{req_idx, l, g, 0, m0});
-  const int64_t kb0 = R.k_lo & ~(int64_t)3;
+  const int64_t kb0 = R.k_lo & ~(int64_t)7;  // tiles start on a G10 panel
   for (int l = 0; l < n_levels; ++l)
     for (int64_t k0 = kb0; k0 <= R.k_hi; k0 += kFineTile) P.fine.push_back(FineItem{req_idx, l, k0});
   return MARFA_OK;
@@ -553,13 +553,20 @@ static int run_plans(std::vector<Plan>& plans, cudaStream_t st, std::vector<int6
   launch_g1(drd, dgi, (int)gi.size(), dgc, st);
   timing_end(ev, 1, st);
   if ((e = cudaGetLastError())) return done(fail(MARFA_E_CUDA, "grid-1 kernel: %s", cudaGetErrorString(e)));
-  ev = timing_begin(st);
-  launch_coarse(drd, dci, (int)ci.size(), dcc, st);
-  timing_end(ev, 2, st);
-  if ((e = cudaGetLastError())) return done(fail(MARFA_E_CUDA, "coarse kernel: %s", cudaGetErrorString(e)));
+  {
+    size_t k = 0;
+    for (int g = 2; g <= kNGrid; ++g) {  // ci is ordered by grid
+      size_t k1 = k;
+      while (k1 < ci.size() && ci[k1].grid == g) ++k1;
+      ev = timing_begin(st);
+      launch_coarse(drd, dci + k, (int)(k1 - k), dcc ? dcc + k : nullptr, st);
+      timing_end(ev, g, st);
+      k = k1;
+    }
+  }
   ev = timing_begin(st);
   launch_fine(drd, dfi, (int)fi.size(), dfc, st);
-  timing_end(ev, 3, st);
+  timing_end(ev, kNGrid + 1, st);
   if ((e = cudaGetLastError())) return done(fail(MARFA_E_CUDA, "fine kernel: %s", cudaGetErrorString(e)));
   if (count) {
     std::vector<int64_t> hg(gi.size()), hc(ci.size()), hf(fi.size());

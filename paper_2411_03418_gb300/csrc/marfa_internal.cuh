@@ -79,7 +79,8 @@ struct ReqDev {
   int64_t npts;
 };
 
-// One CTA of the kernel of grids 2..10: kCPairs consecutive node pairs of one grid.
+// One CTA of the kernel of grids 2..10: kCWarps tiles of kCPairs consecutive node pairs
+// of one grid.
 struct CoarseItem {
   int32_t req, level, grid, pad;
   int64_t m0;  // first pair
@@ -100,7 +101,7 @@ constexpr int kG1Pairs = 32;         // node pairs per G1 tile (one per lane)
 constexpr int kG1Warps = 8;          // warps of a G1 CTA, each takes every 8th staged line
 constexpr int kG1Batch = 512;        // lines staged in shared memory at a time
 constexpr int kCPairs = 32;          // node pairs per tile of grids 2..10
-constexpr int kCWarps = 4;           // warps of a grids-2..10 CTA
+constexpr int kCWarps = 4;           // warps (tiles) of a grids-2..10 CTA
 constexpr int kFineThreads = 256;
 constexpr int kFinePerThread = 4;
 constexpr int kFineTile = kFineThreads * kFinePerThread;

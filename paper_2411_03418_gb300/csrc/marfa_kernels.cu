@@ -20,6 +20,9 @@
 namespace marfa {
 
 // ------------------------------------------------------------------ helpers
+__device__ __constant__ int64_t kChiBreakFx[3] = {3LL << kFixBits, 150LL << kFixBits,
+                                                  300LL << kFixBits};
+
 __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
   float y = v - c;
   float t = s + y;
@@ -63,18 +66,32 @@ __device__ __forceinline__ int64_t upper_idx(const ReqDev& R, int64_t K) {
 }
 
 // Index ranges of the lines whose centre c may lie in one of up to 9 position bands,
-// merged into disjoint ranges so that every line is visited once.
+// merged into disjoint ranges so that every line is visited once. The 2 n boundary
+// lookups run in parallel, one per lane of a converged warp.
 struct Bands {
   int64_t lo[9], hi[9];
   int n;
-  __device__ __forceinline__ void add(const ReqDev& R, const LevelDev& L, int64_t clo, int64_t chi) {
-    int64_t a = lower_idx(R, clo - L.smax);
-    int64_t b = upper_idx(R, chi - L.smin);
-    if (a < b) {
-      lo[n] = a;
-      hi[n] = b;
-      ++n;
+  // zone z: lines with c in [zlo[z], zhi[z]] (fixed point); the shift bounds of the
+  // level turn the centre range into a conservative key range.
+  __device__ __forceinline__ void lookup(const ReqDev& R, const LevelDev& L, const int64_t* zlo,
+                                         const int64_t* zhi, int nz) {
+    const int lane = threadIdx.x & 31;
+    int64_t v = 0;
+    if (lane < 2 * nz) {
+      const int z = lane >> 1;
+      v = (lane & 1) ? upper_idx(R, zhi[z] - L.smin) : lower_idx(R, zlo[z] - L.smax);
     }
+    n = 0;
+    for (int z = 0; z < nz; ++z) {
+      const int64_t a = __shfl_sync(0xffffffffu, v, 2 * z);
+      const int64_t b = __shfl_sync(0xffffffffu, v, 2 * z + 1);
+      if (a < b) {
+        lo[n] = a;
+        hi[n] = b;
+        ++n;
+      }
+    }
+    merge();
   }
   __device__ __forceinline__ void merge() {
     for (int i = 1; i < n; ++i) {  // insertion sort by lo
@@ -102,8 +119,26 @@ struct Bands {
   }
 };
 
-__device__ __constant__ int64_t kChiBreakFx[3] = {3LL << kFixBits, 150LL << kFixBits,
-                                                  300LL << kFixBits};
+
+// Position zones where a line centre must lie for the line to own something in the
+// span [A, B]: within Rc of it (centre), at the cut-off distance (edges) or at a chi
+// breakpoint distance (kinks), each widened by the margin P.
+__device__ __forceinline__ int make_zones(int64_t A, int64_t B, int64_t Rc, int64_t cut, int64_t P,
+                                          bool chi, int64_t* zlo, int64_t* zhi) {
+  int nz = 0;
+  zlo[nz] = A - Rc - P; zhi[nz] = B + Rc + P; ++nz;
+  zlo[nz] = A - cut - P; zhi[nz] = B - cut + P; ++nz;
+  zlo[nz] = A + cut - P; zhi[nz] = B + cut + P; ++nz;
+  if (chi) {
+    for (int b = 0; b < 3; ++b) {
+      const int64_t Bk = kChiBreakFx[b];
+      if (Bk > cut + (B - A) + P) break;
+      zlo[nz] = A - Bk - P; zhi[nz] = B - Bk + P; ++nz;
+      zlo[nz] = A + Bk - P; zhi[nz] = B + Bk + P; ++nz;
+    }
+  }
+  return nz;
+}
 
 // Bits i = 0..nb-1 stand for panels base + i; set those in the closed interval [a, b].
 template <typename MT>
@@ -357,8 +392,12 @@ __global__ void __launch_bounds__(kG1Warps * 32)
   const int64_t X0 = m0 << s;  // node 2 m0
   const int64_t cut = R.cut_fx;
   const LevelDev L = R.lev[lev];
-  const int64_t i_lo = lower_idx(R, (base << s) - cut - L.smax);
-  const int64_t i_hi = upper_idx(R, ((m0 + kG1Pairs) << s) + cut - L.smin);
+  Bands bd;
+  {
+    const int64_t zlo = (base << s) - cut, zhi = ((m0 + kG1Pairs) << s) + cut;
+    bd.lookup(R, L, &zlo, &zhi, 1);
+  }
+  const int64_t i_lo = bd.n ? bd.lo[0] : 0, i_hi = bd.n ? bd.hi[0] : 0;
   const int64_t off = (int64_t)lev * R.n_lines;
   const bool voigt = R.shape == kShapeVoigt;
   const bool physical = R.shape < kShapeConst;
@@ -491,18 +530,19 @@ void launch_g1(const ReqDev* reqs, const G1Item* items, int n_items, int64_t* co
 }
 
 // ------------------------------------------------------------------ grids 2..10
-// A CTA owns kCPairs consecutive node pairs of grid g of one level. Each thread takes
-// one candidate line at a time, forms the exact mask of the panels the line owns in
-// the tile, evaluates the profile at the nodes of those panels only, and adds the
-// values into lane-private shared-memory slots (acc[pair][lane]); the slots are summed
-// over lanes and warps in a fixed order at the end.
+// Warp w of a CTA owns kCPairs consecutive node pairs of grid g of one level (lane p
+// holds pair p: even node 2m, odd node 2m+1). The warp takes 32 candidate lines at a
+// time, one per lane. Phase 1: each lane forms the exact mask of the panels its line
+// owns in the tile and evaluates the profile at the nodes of those panels, into a
+// per-warp shared buffer (row = line). Phase 2: each lane adds, for its own pair, the
+// buffered values of the lines owning its panels into compensated register sums.
 template <bool COUNT>
 __global__ void __launch_bounds__(kCWarps * 32)
     k_coarse(const ReqDev* __restrict__ reqs, const CoarseItem* __restrict__ items,
              int64_t* __restrict__ counts) {
-  __shared__ float accL[kCWarps][kCPairs][32];
-  __shared__ float accM[kCWarps][kCPairs][32];
-  __shared__ float accR[kCWarps][kCPairs][32];
+  __shared__ float bufE[kCWarps][32][kCPairs + 1];  // value at node 2p of staged line t
+  __shared__ float bufO[kCWarps][32][kCPairs + 1];  // value at node 2p + 1
+  __shared__ unsigned long long smsk[kCWarps][32];
   __shared__ int64_t sCnt[kCWarps];
   const CoarseItem it = items[blockIdx.x];
   const ReqDev& R = reqs[it.req];
@@ -511,109 +551,118 @@ __global__ void __launch_bounds__(kCWarps * 32)
   const int lev = it.level;
   const int64_t m_first = R.m_first[g];
   const int64_t m_last = m_first + R.npan[g] - 1;
-  const int64_t m0 = it.m0;
-  const int s = panel_shift(g);
-  const int64_t cut = R.cut_fx;
-  const int64_t base = m0 - 1;  // mask bit b <-> panel m0 - 1 + b
-  const int nb = kCPairs + 1;
-  const uint64_t win = rmask<uint64_t>(m_first, m_last, base, nb);
-  for (int p = 0; p < kCPairs; ++p) {
-    accL[warp][p][lane] = 0.0f;
-    accM[warp][p][lane] = 0.0f;
-    accR[warp][p][lane] = 0.0f;
-  }
-  const LevelDev L = R.lev[lev];
-  Bands bd;
-  bd.n = 0;
-  {
-    const int64_t P = int64_t(1) << s;
-    const int64_t A = (base >> 1) << (s + 1);
-    const int64_t B = (((base + nb - 1) >> 1) + 1) << (s + 1);
-    const int64_t Rg1 = (int64_t)R.R_w * step_fx(g - 1);
-    bd.add(R, L, A - Rg1 - P, B + Rg1 + P);
-    bd.add(R, L, A - cut - P, B - cut + P);
-    bd.add(R, L, A + cut - P, B + cut + P);
-    if (R.chi_req) {
-      for (int b = 0; b < 3; ++b) {
-        const int64_t Bk = kChiBreakFx[b];
-        if (Bk > cut + (B - A) + P) break;
-        bd.add(R, L, A - Bk - P, B - Bk + P);
-        bd.add(R, L, A + Bk - P, B + Bk + P);
-      }
-    }
-    bd.merge();
-  }
-  const int64_t lo_off = (int64_t)lev * R.n_lines;
-  const int64_t X0 = m0 << s;  // position of node 2 m0 (j = 0)
-  const bool physical = R.shape < kShapeConst;
-  const bool voigt = R.shape == kShapeVoigt;
+  const int64_t m0 = it.m0 + (int64_t)kCPairs * warp;  // this warp's first pair
   int64_t nev = 0;
-  __syncwarp();
-  for (int r = 0; r < bd.n; ++r) {
-    for (int64_t i0 = bd.lo[r]; i0 < bd.hi[r]; i0 += kCWarps * 32) {
-      const int64_t i = i0 + tid;
-      if (i >= bd.hi[r]) continue;
-      const int64_t c = __ldg(R.c + lo_off + i);
-      const int gst = __ldg(R.gstar + lo_off + i);
-      const bool chi = __ldg(R.flags + lo_off + i) & 1;
-      uint64_t own = accept_mask<uint64_t>(g, c, gst, chi, cut, R.R_w, base, nb, false) & win;
-      if (own) own &= ~accept_mask<uint64_t>(g - 1, c, gst, chi, cut, R.R_w, base, nb, true);
-      if (!own) continue;
-      const float amp = __ldg(R.amp + lo_off + i);
-      const float sx = __ldg(R.sx + lo_off + i);
-      const float y = __ldg(R.yv + lo_off + i);
-      NodeX nx;
-      nx.init(X0 - c, s - 1, sx);
-      ChiThr ct;
-      const bool use_chi = chi && physical;
-      if (use_chi) ct.init(c, X0, s - 1);
-      // pair p uses bits p (R slot of node 2p) and p + 1 (L of node 2p, M of node 2p+1)
-      const int pa = max(__ffsll((long long)own) - 2, 0);
-      const int pb = min(63 - __clzll((long long)own), kCPairs - 1);
-      for (int p = pa; p <= pb; ++p) {
-        const bool bR = (own >> p) & 1ull, bL = (own >> (p + 1)) & 1ull;
-        if (!(bR || bL)) continue;
-        const float jf = (float)(2 * p);
-        const float xv = nx.x(jf);
-        float v = amp * (voigt ? voigt_K(xv, y) : shape_f(R.shape, xv, y));
-        if (use_chi) v *= ct.value(2 * p, nx.absd(jf, s - 1));
-        if (bL) accL[warp][p][lane] += v;
-        if (bR) accR[warp][p][lane] += v;
-        if (bL) {
-          const float xw = nx.x(jf + 1.0f);
-          float w = amp * (voigt ? voigt_K(xw, y) : shape_f(R.shape, xw, y));
-          if (use_chi) w *= ct.value(2 * p + 1, nx.absd(jf + 1.0f, s - 1));
-          accM[warp][p][lane] += w;
+  if (m0 <= m_last + 1) {  // warp-uniform
+    const int s = panel_shift(g);
+    const int64_t cut = R.cut_fx;
+    const int64_t base = m0 - 1;  // mask bit b <-> panel m0 - 1 + b
+    const int nb = kCPairs + 1;
+    const uint64_t win = rmask<uint64_t>(m_first, m_last, base, nb);
+    const LevelDev L = R.lev[lev];
+    Bands bd;
+    {
+      const int64_t P = int64_t(1) << s;
+      const int64_t A = (base >> 1) << (s + 1);
+      const int64_t B = (((base + nb - 1) >> 1) + 1) << (s + 1);
+      int64_t zlo[9], zhi[9];
+      const int nz = make_zones(A, B, (int64_t)R.R_w * step_fx(g - 1), cut, P, R.chi_req, zlo, zhi);
+      bd.lookup(R, L, zlo, zhi, nz);
+    }
+    const int64_t lo_off = (int64_t)lev * R.n_lines;
+    const int64_t X0 = m0 << s;  // position of node 2 m0 (j = 0)
+    const bool physical = R.shape < kShapeConst;
+    const bool voigt = R.shape == kShapeVoigt;
+    const int p = lane;
+    float sL = 0.f, cL = 0.f, sR = 0.f, cR = 0.f, sM = 0.f, cM = 0.f;
+    float (*bE)[kCPairs + 1] = bufE[warp];
+    float (*bO)[kCPairs + 1] = bufO[warp];
+    unsigned long long* mk = smsk[warp];
+    for (int r = 0; r < bd.n; ++r) {
+      for (int64_t i0 = bd.lo[r]; i0 < bd.hi[r]; i0 += 32) {
+        const int64_t i = i0 + lane;
+        uint64_t own = 0;
+        int64_t c = 0;
+        bool chi = false;
+        if (i < bd.hi[r]) {
+          c = __ldg(R.c + lo_off + i);
+          const int gst = __ldg(R.gstar + lo_off + i);
+          chi = __ldg(R.flags + lo_off + i) & 1;
+          own = accept_mask<uint64_t>(g, c, gst, chi, cut, R.R_w, base, nb, false) & win;
+          if (own) own &= ~accept_mask<uint64_t>(g - 1, c, gst, chi, cut, R.R_w, base, nb, true);
         }
-        if (COUNT) nev += 1 + (bL ? 1 : 0);
+        const uint32_t any = __ballot_sync(0xffffffffu, own != 0);
+        if (!any) continue;
+        // phase 1: this lane's line at the nodes of its owned panels
+        if (own) {
+          const float amp = __ldg(R.amp + lo_off + i);
+          const float sx = __ldg(R.sx + lo_off + i);
+          const float y = __ldg(R.yv + lo_off + i);
+          NodeX nx;
+          nx.init(X0 - c, s - 1, sx);
+          ChiThr ct;
+          const bool use_chi = chi && physical;
+          if (use_chi) ct.init(c, X0, s - 1);
+          const int pa = max(__ffsll((long long)own) - 2, 0);
+          const int pb = min(63 - __clzll((long long)own), kCPairs - 1);
+          for (int q = pa; q <= pb; ++q) {
+            const bool bR = (own >> q) & 1ull, bL = (own >> (q + 1)) & 1ull;
+            if (!(bR || bL)) continue;
+            const float jf = (float)(2 * q);
+            const float xv = nx.x(jf);
+            float v = amp * (voigt ? voigt_K(xv, y) : shape_f(R.shape, xv, y));
+            if (use_chi) v *= ct.value(2 * q, nx.absd(jf, s - 1));
+            bE[lane][q] = v;
+            if (bL) {
+              const float xw = nx.x(jf + 1.0f);
+              float w = amp * (voigt ? voigt_K(xw, y) : shape_f(R.shape, xw, y));
+              if (use_chi) w *= ct.value(2 * q + 1, nx.absd(jf + 1.0f, s - 1));
+              bO[lane][q] = w;
+            }
+            if (COUNT) nev += 1 + (bL ? 1 : 0);
+          }
+        }
+        mk[lane] = own;
+        __syncwarp();
+        // phase 2: the staged lines owning panel m0+p-1 (bit p) or m0+p (bit p+1)
+        uint32_t mine = 0;
+        for (uint32_t rem = any; rem; rem &= rem - 1) {
+          const int t = __ffs(rem) - 1;
+          mine |= (((mk[t] >> p) & 3ull) ? 1u : 0u) << t;
+        }
+        while (mine) {
+          const int t = __ffs(mine) - 1;
+          mine &= mine - 1;
+          const uint64_t m2 = mk[t];
+          const float v0 = bE[t][p];
+          if ((m2 >> (p + 1)) & 1ull) {
+            kahan_add(sL, cL, v0);
+            kahan_add(sM, cM, bO[t][p]);
+          }
+          if ((m2 >> p) & 1ull) kahan_add(sR, cR, v0);
+        }
+        __syncwarp();
       }
     }
+    float* gp = R.slots + (int64_t)lev * R.slots_per_level + R.slot_off[g];
+    const int64_t np = R.npan[g];
+    const int64_t m = m0 + p;
+    if (m <= m_last) {
+      gp[m - m_first] = sL + cL;
+      gp[np + (m - m_first)] = sM + cM;
+    }
+    if (m - 1 >= m_first && m - 1 <= m_last) gp[2 * np + (m - 1 - m_first)] = sR + cR;
   }
   if (COUNT) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) nev += __shfl_xor_sync(0xffffffffu, nev, o);
     if (lane == 0) sCnt[warp] = nev;
-  }
-  __syncthreads();
-  // thread t < 3 kCPairs sums slot (t / kCPairs, pair t % kCPairs) over warps and lanes
-  if (tid < 3 * kCPairs) {
-    const int kind = tid / kCPairs, p = tid % kCPairs;
-    float (*acc)[kCPairs][32] = kind == 0 ? accL : (kind == 1 ? accM : accR);
-    float sum = 0.0f, cmp = 0.0f;
-    for (int w = 0; w < kCWarps; ++w)
-      for (int l = 0; l < 32; ++l) kahan_add(sum, cmp, acc[w][p][(l + p) & 31]);
-    const float v = sum + cmp;
-    float* gp = R.slots + (int64_t)lev * R.slots_per_level + R.slot_off[g];
-    const int64_t np = R.npan[g];
-    const int64_t m = m0 + p;
-    if (kind == 0 && m <= m_last) gp[m - m_first] = v;
-    if (kind == 1 && m <= m_last) gp[np + (m - m_first)] = v;
-    if (kind == 2 && m - 1 >= m_first && m - 1 <= m_last) gp[2 * np + (m - 1 - m_first)] = v;
-  }
-  if (COUNT && tid == 0) {
-    int64_t t = 0;
-    for (int w = 0; w < kCWarps; ++w) t += sCnt[w];
-    counts[blockIdx.x] = t;
+    __syncthreads();
+    if (tid == 0) {
+      int64_t t = 0;
+      for (int w = 0; w < kCWarps; ++w) t += sCnt[w];
+      counts[blockIdx.x] = t;
+    }
   }
 }
 
@@ -627,89 +676,138 @@ void launch_coarse(const ReqDev* reqs, const CoarseItem* items, int n_items, int
 }
 
 // ------------------------------------------------------------------ finest grid + cascade
-// Each thread owns 4 consecutive finest nodes (one G10 panel), sums the lines that the
-// finest grid owns there, adds the quadratic interpolants of the ten coarse grids and
-// the CTA writes its 1024 outputs with aligned vector stores.
+// A CTA owns 1024 consecutive finest nodes of one level; warp w owns 128 of them
+// (16 G10 panels) and lane l four consecutive nodes (one half panel). Each warp loads
+// 32 candidate lines at a time; the loading lane works out which of the warp's G10
+// panels the line leaves to the finest grid (not accepted on G10) and the node range
+// within the cut-off, and stages them in shared memory; every lane then sums the
+// staged lines that own its nodes. Finally each node adds the quadratic interpolants
+// of the ten coarse grids, and the CTA writes its outputs with aligned vector stores.
+struct FineStage {
+  float qf, hs, phs, phi;   // node positions relative to the warp's first node
+  float amp, y;
+  uint32_t pm;              // G10 panels of the warp the line leaves to the finest grid
+  int klo, khi;             // warp-relative node range within the cut-off and the window
+  int chi;                  // chi-factor applies
+  int r3, r150, r300, l3, l150, l300;
+};
+
 template <bool COUNT>
 __global__ void __launch_bounds__(kFineThreads)
     k_fine(const ReqDev* __restrict__ reqs, const FineItem* __restrict__ items,
            int64_t* __restrict__ counts) {
   __shared__ float tile[kFineTile];
+  __shared__ FineStage stg[kFineThreads / 32][32];
   __shared__ int64_t red[kFineThreads / 32];
   const FineItem it = items[blockIdx.x];
   const ReqDev& R = reqs[it.req];
   const int lev = it.level;
-  const int tid = threadIdx.x;
-  const int64_t k0 = it.k0 + (int64_t)kFinePerThread * tid;
-  uint32_t valid = 0;
-#pragma unroll
-  for (int q = 0; q < kFinePerThread; ++q)
-    if (k0 + q >= R.k_lo && k0 + q <= R.k_hi) valid |= 1u << q;
-
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t kw = it.k0 + (int64_t)kFinePerThread * 32 * warp;  // first node of the warp
+  const int64_t k0 = kw + kFinePerThread * lane;                    // first node of the lane
+  const int64_t cut = R.cut_fx;
+  const LevelDev L = R.lev[lev];
   float acc[kFinePerThread], cmp[kFinePerThread];
 #pragma unroll
   for (int q = 0; q < kFinePerThread; ++q) acc[q] = cmp[q] = 0.0f;
   int64_t nev = 0;
-
-  if (valid) {
-    const LevelDev L = R.lev[lev];
-    const int64_t cut = R.cut_fx;
-    const int64_t X0 = k0 << kFineShift;
-    const int64_t X3 = (k0 + kFinePerThread - 1) << kFineShift;
+  const int nw = kFinePerThread * 32;  // nodes of the warp
+  const int wlo = (int)max(R.k_lo - kw, (int64_t)0);
+  const int whi = (int)min(R.k_hi - kw, (int64_t)(nw - 1));
+  if (wlo <= whi) {  // warp-uniform
+    const int64_t Xa = kw << kFineShift, Xb = (kw + nw - 1) << kFineShift;
     const int64_t P10 = int64_t(1) << panel_shift(kNGrid);
-    const int64_t R10 = (int64_t)R.R_w * step_fx(kNGrid);
     Bands bd;
-    bd.n = 0;
-    bd.add(R, L, X0 - R10 - P10, X3 + R10 + P10);
-    bd.add(R, L, X0 - cut - P10, X3 - cut + P10);
-    bd.add(R, L, X0 + cut - P10, X3 + cut + P10);
-    if (R.chi_req) {
-      for (int b = 0; b < 3; ++b) {
-        const int64_t Bk = kChiBreakFx[b];
-        if (Bk > cut + 2 * P10) break;
-        bd.add(R, L, X0 - Bk - P10, X3 - Bk + P10);
-        bd.add(R, L, X0 + Bk - P10, X3 + Bk + P10);
-      }
+    {
+      int64_t zlo[9], zhi[9];
+      const int nz = make_zones(Xa, Xb, (int64_t)R.R_w * step_fx(kNGrid), cut, P10, R.chi_req, zlo, zhi);
+      bd.lookup(R, L, zlo, zhi, nz);
     }
-    bd.merge();
-    const int64_t p10 = k0 >> 3;  // the G10 panel of the four nodes
+    const int64_t pbase = kw >> 3;  // first G10 panel of the warp
     const int64_t lo_off = (int64_t)lev * R.n_lines;
     const bool physical = R.shape < kShapeConst;
     const bool voigt = R.shape == kShapeVoigt;
+    const int mypanel = lane >> 1;
+    FineStage* st = stg[warp];
     for (int r = 0; r < bd.n; ++r) {
-      for (int64_t i = bd.lo[r]; i < bd.hi[r]; ++i) {
-        const int64_t c = __ldg(R.c + lo_off + i);
-        const int gst = __ldg(R.gstar + lo_off + i);
-        const bool chi = __ldg(R.flags + lo_off + i) & 1;
-        if (accept_mask<uint32_t>(kNGrid, c, gst, chi, cut, R.R_w, p10, 1, false)) continue;
-        uint32_t own = 0;
-#pragma unroll
-        for (int q = 0; q < kFinePerThread; ++q) {
-          const int64_t d = X0 + ((int64_t)q << kFineShift) - c;
-          if ((d < 0 ? -d : d) <= cut) own |= 1u << q;
+      for (int64_t i0 = bd.lo[r]; i0 < bd.hi[r]; i0 += 32) {
+        const int64_t i = i0 + lane;
+        uint32_t pm = 0;
+        int klo = 0, khi = -1;
+        int64_t c = 0;
+        int gst = 0;
+        bool chi = false;
+        if (i < bd.hi[r]) {
+          c = __ldg(R.c + lo_off + i);
+          gst = __ldg(R.gstar + lo_off + i);
+          chi = __ldg(R.flags + lo_off + i) & 1;
+          klo = (int)max(cl_sh(c - cut, kFineShift) - kw, (int64_t)wlo);
+          khi = (int)min(fl_sh(c + cut, kFineShift) - kw, (int64_t)whi);
+          if (klo <= khi) {
+            pm = ~accept_mask<uint32_t>(kNGrid, c, gst, chi, cut, R.R_w, pbase, 16, false) &
+                 rmask<uint32_t>(klo >> 3, khi >> 3, 0, 16);
+          }
         }
-        own &= valid;
-        if (!own) continue;
-        const float amp = __ldg(R.amp + lo_off + i);
-        const float sx = __ldg(R.sx + lo_off + i);
-        const float y = __ldg(R.yv + lo_off + i);
-        NodeX nx;
-        nx.init(X0 - c, kFineShift, sx);
-        ChiThr ct;
-        const bool use_chi = chi && physical;
-        if (use_chi) ct.init(c, X0, kFineShift);
-#pragma unroll
-        for (int q = 0; q < kFinePerThread; ++q) {
-          if (!((own >> q) & 1u)) continue;
-          const float jf = (float)q;
-          const float xv = nx.x(jf);
-          float v = amp * (voigt ? voigt_K(xv, y) : shape_f(R.shape, xv, y));
-          if (use_chi) v *= ct.value(q, nx.absd(jf, kFineShift));
-          kahan_add(acc[q], cmp[q], v);
-          if (COUNT) ++nev;
+        const uint32_t any = __ballot_sync(0xffffffffu, pm != 0);
+        if (!any) continue;
+        __syncwarp();
+        if (pm) {
+          FineStage e;
+          NodeX nx;
+          const float sx = __ldg(R.sx + lo_off + i);
+          nx.init(Xa - c, kFineShift, sx);
+          e.qf = nx.qf; e.hs = nx.hs; e.phs = nx.phs; e.phi = nx.phi;
+          e.amp = __ldg(R.amp + lo_off + i);
+          e.y = __ldg(R.yv + lo_off + i);
+          e.pm = pm; e.klo = klo; e.khi = khi;
+          e.chi = chi && physical;
+          if (e.chi) {
+            ChiThr ct;
+            ct.init(c, Xa, kFineShift);
+            e.r3 = ct.r3; e.r150 = ct.r150; e.r300 = ct.r300;
+            e.l3 = ct.l3; e.l150 = ct.l150; e.l300 = ct.l300;
+          }
+          st[lane] = e;
+        } else {
+          st[lane].pm = 0;
         }
+        __syncwarp();
+        // this lane's staged lines (those that leave its G10 panel to the finest grid)
+        uint32_t mine = 0;
+        for (uint32_t rem = any; rem; rem &= rem - 1) {
+          const int e_i = __ffs(rem) - 1;
+          mine |= ((st[e_i].pm >> mypanel) & 1u) << e_i;
+        }
+        while (mine) {
+          const int e_i = __ffs(mine) - 1;
+          mine &= mine - 1;
+          const FineStage& e = st[e_i];
+          ChiThr ct;
+          if (e.chi) {
+            ct.r3 = e.r3; ct.r150 = e.r150; ct.r300 = e.r300;
+            ct.l3 = e.l3; ct.l150 = e.l150; ct.l300 = e.l300;
+          }
+#pragma unroll
+          for (int q = 0; q < kFinePerThread; ++q) {
+            const int j = kFinePerThread * lane + q;
+            if (j < e.klo || j > e.khi) continue;
+            const float jf = (float)j;
+            const float xv = fmaf(jf + e.qf, e.hs, e.phs);
+            float v = e.amp * (voigt ? voigt_K(xv, e.y) : shape_f(R.shape, xv, e.y));
+            if (e.chi) v *= ct.value(j, fabsf((jf + e.qf) + e.phi) * ldexpf(1.0f, -kFineBits));
+            kahan_add(acc[q], cmp[q], v);
+            if (COUNT) ++nev;
+          }
+        }
+        __syncwarp();
       }
     }
+  }
+  uint32_t valid = 0;
+#pragma unroll
+  for (int q = 0; q < kFinePerThread; ++q)
+    if (k0 + q >= R.k_lo && k0 + q <= R.k_hi) valid |= 1u << q;
+  if (valid) {
     // cascade: quadratic through the panel-local L, M, R of every coarse grid
     const float* sl = R.slots + (int64_t)lev * R.slots_per_level;
     float out[kFinePerThread];
@@ -746,7 +844,6 @@ __global__ void __launch_bounds__(kFineThreads)
     const int n = (int)(b - a + 1);
     const int t0 = (int)(a - it.k0);         // its position in the tile
     float* dst = row + i0;
-    // elements before the first 16-byte boundary
     int head = (int)((16 - ((uintptr_t)dst & 15)) & 15) / 4;
     if (head > n) head = n;
     if (tid < head) dst[tid] = tile[t0 + tid];
@@ -762,7 +859,7 @@ __global__ void __launch_bounds__(kFineThreads)
   if (COUNT) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) nev += __shfl_xor_sync(0xffffffffu, nev, o);
-    if ((tid & 31) == 0) red[tid >> 5] = nev;
+    if (lane == 0) red[warp] = nev;
     __syncthreads();
     if (tid == 0) {
       int64_t t = 0;

@@ -2,14 +2,14 @@
 // profile kernels, with a relative error of about 1e-6 over the whole (x, y >= 0)
 // plane. The paper's own Humlicek/Kuntz variant (Appendix C) is accurate to 1 % only;
 // this one is built from:
-//   |z| >= 4.5   asymptotic series of w (Abramowitz & Stegun 7.1.23),
-//                w ~ i/(sqrt(pi) z) sum_n (2n-1)!!/(2 z^2)^n, truncated by |z|
-//                (1, 5 or 14 terms), plus the Gaussian term exp(y^2-x^2) cos(2xy)
-//                for y < 1, which is the Doppler core the series cannot see;
-//   |z| < 4.5, y < 1   exact split w = exp(-z^2) + (2i/sqrt(pi)) F(z), F the complex
+//   y < 1, |x| < 12    exact split w = exp(-z^2) + (2i/sqrt(pi)) F(z), F the complex
 //                Dawson function, K = exp(y^2-x^2) cos(2xy) - (2/sqrt(pi)) y Psi,
-//                Psi(x, y^2) = Im F / y from a table of bivariate polynomials;
-//   |z| < 4.5, y >= 1  K from a table of bivariate polynomials.
+//                Psi(x, y^2) = Im F / y from a table of bivariate polynomials (the
+//                Gaussian term is below 4e-19 and dropped for |x| >= 6.5);
+//   |z| < 4.5, y >= 1  K from a table of bivariate polynomials;
+//   elsewhere   asymptotic series of w (Abramowitz & Stegun 7.1.23),
+//                w ~ i/(sqrt(pi) z) sum_n (2n-1)!!/(2 z^2)^n, truncated by |z|
+//                (2 terms for |z| >= 100, 6 for |z| >= 8, 15 for |z| >= 4.5).
 // The tables come from gen_voigt_tables.py (mpmath, 30 digits).
 #pragma once
 #include <cuda_runtime.h>
@@ -83,26 +83,25 @@ __device__ __forceinline__ float voigt_far(float x, float y) {
 }
 
 // Everything but the far wing, kept out of line so that unrolled callers stay small.
+// The Dawson-table branch covers the whole near wing of narrow lines (y < 1, |x| < 12)
+// so that one line's nodes on the fine grids take a single code path.
 __device__ __noinline__ float voigt_K_near(float ax, float y) {
-  float r2 = fmaf(ax, ax, y * y);
-  if (r2 >= 64.0f) return voigt_asym<5>(ax, y);
-  if (r2 >= 20.25f) {
-    float a = voigt_asym<14>(ax, y);
-    if (y < 1.0f) a += gauss_term(ax, y);
-    return a;
-  }
-  if (y < 1.0f) {
-    int ci = min((int)(ax * 2.0f), 8);
+  if (y < 1.0f && ax < 12.0f) {
+    int ci = min((int)(ax * 2.0f), VOIGT_NPSI - 1);
     float u = (ax - (0.5f * ci + 0.25f)) * 4.0f;
     float v = 2.0f * y * y - 1.0f;
     float ps = voigt_cell(ci, u, v);
-    return gauss_term(ax, y) - kTwoOverSqrtPi * y * ps;
+    float gt = ax < 6.5f ? gauss_term(ax, y) : 0.0f;
+    return gt - kTwoOverSqrtPi * y * ps;
   }
+  float r2 = fmaf(ax, ax, y * y);
+  if (r2 >= 64.0f) return voigt_asym<5>(ax, y);
+  if (r2 >= 20.25f) return voigt_asym<14>(ax, y);  // here y >= 1
   int ix = min((int)(ax * (1.0f / 0.9f)), 4);
   int iy = min((int)((y - 1.0f) * (1.0f / 1.75f)), 1);
   float u = (ax - (0.9f * ix + 0.45f)) * (1.0f / 0.45f);
   float v = (y - (1.0f + 1.75f * iy + 0.875f)) * (1.0f / 0.875f);
-  return voigt_cell(9 + ix * 2 + iy, u, v);
+  return voigt_cell(VOIGT_NPSI + ix * 2 + iy, u, v);
 }
 
 __device__ __forceinline__ float voigt_K(float x, float y) {

@@ -223,9 +223,9 @@ def marfa_diag_absorption_counted(lines: Lines, levels, vmr, rq):
 
 def marfa_diag_kernel_timing(enable: bool):
     """Start (True) or stop (False) per-kernel event timing; stopping returns
-    (ms[4], launches[4]) for level preparation, grid 1, grids 2..10, finest grid."""
-    ms = np.zeros(4, dtype=np.float64)
-    n = np.zeros(4, dtype=np.int64)
+    (ms[12], launches[12]): level preparation, grids 1..10, finest grid."""
+    ms = np.zeros(12, dtype=np.float64)
+    n = np.zeros(12, dtype=np.int64)
     _check(load().marfa_diag_kernel_timing(1 if enable else 0, _ptr(ms), _ptr(n)))
     return ms, n
 
