@@ -157,6 +157,34 @@ int marfa_absorption_batch(int32_t n_req, const marfa_lines_t* const* lines,
 int marfa_write_pt_table(const char* dir, int32_t level_number, double nu_lo,
                          double nu_hi, const float* k, int64_t npts);
 
+/*
+ * marfa_absorption without any device allocation, for callers that cannot allocate
+ * device memory: a host model that has given all free device memory to its own pool
+ * (so cudaMalloc would fail or fragment it), or a pipeline that must not let an
+ * allocation or a free synchronise the device while its other streams run. The paper
+ * has no counterpart of this call; it computes the same k(nu) as marfa_absorption.
+ *   - Scratch: a file-scope __device__ array of 32 MiB (MARFA_NOALLOC_SCRATCH_BYTES)
+ *     that every GPU loading the library holds until the process exits. A request
+ *     whose per-level line data, grid slots and work lists exceed it is rejected with
+ *     MARFA_E_INVAL (for example: one level of 200,000 lines on a 1000 cm^-1 window
+ *     fits; sixty such levels do not).
+ *   - k_out must be device memory ([n_levels][npts] float32); host outputs are
+ *     rejected with MARFA_E_INVAL. lines comes from marfa_prepare_lines.
+ *   - The first call on a device looks up the scratch's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call before
+ *     any stream capture.
+ *   - Every call reuses the same scratch and leaves its contents there; the kernels
+ *     write every value they read, so nothing needs clearing between calls. Calls
+ *     whose work overlaps on the GPU (other streams, other host threads) race on the
+ *     scratch: serialise them.
+ *   - Asynchronous on stream (NULL = legacy default stream); the copies of the level
+ *     tables and work lists come from pageable host memory into the scratch.
+ */
+#define MARFA_NOALLOC_SCRATCH_BYTES (32u << 20)
+int marfa_absorption_noalloc(const marfa_lines_t* lines, const marfa_level_t* levels,
+                             const double* vmr, int32_t n_levels, const marfa_request_t* rq,
+                             float* k_out, void* stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* marfa_last_error(void);
 

@@ -684,6 +684,109 @@ extern "C" int marfa_write_pt_table(const char* dir, int32_t level_number, doubl
   return MARFA_OK;
 }
 
+// ------------------------------------------------------------------ absorption without allocation
+// Callers that cannot allocate device memory (a host model that has handed all free
+// device memory to its own pool, so that cudaMalloc fails or fragments it, or a
+// pipeline that must not let an allocation or a free synchronise the device while
+// other streams run) use marfa_absorption_noalloc. Its scratch is this file-scope
+// array: every GPU that loads the library holds it until the process exits.
+static constexpr size_t kNoAllocBytes = (size_t)32 << 20;  // 32 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Device address of g_noalloc_scratch, looked up once per device with that device
+// current (in host code the symbol is only a host-side stand-in).
+static int noalloc_scratch(char** out) {
+  static std::mutex mu;
+  static void* addr[64] = {nullptr};
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(MARFA_E_INVAL, "device %d out of range", dev);
+  std::lock_guard<std::mutex> lk(mu);
+  if (!addr[dev]) {
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr)
+      return fail(MARFA_E_CUDA, "cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
+    addr[dev] = ptr;
+  }
+  *out = (char*)addr[dev];
+  return MARFA_OK;
+}
+
+extern "C" int marfa_absorption_noalloc(const marfa_lines_t* lines, const marfa_level_t* levels,
+                                        const double* vmr, int32_t n_levels,
+                                        const marfa_request_t* rq, float* k_out, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  Plan P;
+  int r = build_plan(P, lines, levels, vmr, n_levels, rq, 0);
+  if (r) return r;
+  if (!k_out || !is_device_ptr(k_out))
+    return fail(MARFA_E_INVAL, "k_out must be device memory for marfa_absorption_noalloc");
+  const marfa_lines_t* L = P.lines;
+  const int64_t n = L->n, nl = P.n_levels;
+  const int ns = (int)L->species.size();
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t pairs = (size_t)(n * nl);
+  const size_t sz_c = al(8 * pairs), sz_f = al(4 * pairs), sz_b = al(pairs);
+  const size_t sz_slots = al(4 * (size_t)P.rd.slots_per_level * nl);
+  const size_t sz_lev = al(sizeof(LevelDev) * nl), sz_ls = al(sizeof(LevelSpeciesDev) * nl * ns);
+  const size_t sz_r = al(sizeof(ReqDev)), sz_gi = al(sizeof(G1Item) * P.g1.size()),
+               sz_ci = al(sizeof(CoarseItem) * P.coarse.size()), sz_fi = al(sizeof(FineItem) * P.fine.size());
+  const size_t total = sz_c + 3 * sz_f + 2 * sz_b + sz_slots + sz_lev + sz_ls + sz_r + sz_gi + sz_ci + sz_fi;
+  if (total > kNoAllocBytes)
+    return fail(MARFA_E_INVAL, "request needs %zu bytes of scratch; marfa_absorption_noalloc holds %zu",
+                total, kNoAllocBytes);
+  char* p = nullptr;
+  r = noalloc_scratch(&p);
+  if (r) return r;
+  ReqDev& R = P.rd;
+  int64_t* c = (int64_t*)p; p += sz_c;
+  float* amp = (float*)p; p += sz_f;
+  float* sx = (float*)p; p += sz_f;
+  float* yv = (float*)p; p += sz_f;
+  int8_t* gst = (int8_t*)p; p += sz_b;
+  uint8_t* fl = (uint8_t*)p; p += sz_b;
+  R.slots = (float*)p; p += sz_slots;
+  LevelDev* dlev = (LevelDev*)p; p += sz_lev;
+  LevelSpeciesDev* dls = (LevelSpeciesDev*)p; p += sz_ls;
+  ReqDev* drd = (ReqDev*)p; p += sz_r;
+  G1Item* dgi = (G1Item*)p; p += sz_gi;
+  CoarseItem* dci = (CoarseItem*)p; p += sz_ci;
+  FineItem* dfi = (FineItem*)p;
+  R.c = c; R.amp = amp; R.sx = sx; R.yv = yv; R.gstar = gst; R.flags = fl; R.lev = dlev;
+  R.out = k_out;
+  CK(cudaMemcpyAsync(dlev, P.lev.data(), sizeof(LevelDev) * nl, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dls, P.ls.data(), sizeof(LevelSpeciesDev) * nl * ns, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(drd, &R, sizeof(ReqDev), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dgi, P.g1.data(), sizeof(G1Item) * P.g1.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dci, P.coarse.data(), sizeof(CoarseItem) * P.coarse.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dfi, P.fine.data(), sizeof(FineItem) * P.fine.size(), cudaMemcpyHostToDevice, st));
+  PrepArgs a;
+  a.n = n;
+  a.nu0 = L->nu0; a.S296 = L->S296; a.ga = L->ga; a.gs = L->gs; a.E = L->E; a.na = L->na; a.da = L->da;
+  a.species = L->sp;
+  a.n_species = ns;
+  a.lev = dlev;
+  a.ls = dls;
+  a.shape = P.rq.shape;
+  a.R_c = P.rq.R_c;
+  a.c = c; a.amp = amp; a.sx = sx; a.yv = yv; a.gstar = gst; a.flags = fl;
+  // Every slot and per-level value is written by these kernels before it is read, so
+  // nothing left in the scratch by an earlier call needs clearing.
+  launch_level_prep(a, (int)nl, st);
+  launch_g1(drd, dgi, (int)P.g1.size(), nullptr, st);
+  size_t k = 0;
+  for (int g = 2; g <= kNGrid; ++g) {  // P.coarse is ordered by grid
+    size_t k1 = k;
+    while (k1 < P.coarse.size() && P.coarse[k1].grid == g) ++k1;
+    launch_coarse(drd, dci + k, (int)(k1 - k), nullptr, st);
+    k = k1;
+  }
+  launch_fine(drd, dfi, (int)P.fine.size(), nullptr, st);
+  CK(cudaGetLastError());
+  return MARFA_OK;
+}
+
 // ------------------------------------------------------------------ diagnostics
 extern "C" int marfa_diag_voigt(const float* x, const float* y, float* out, int64_t n) {
   if (n < 0 || (n > 0 && (!x || !y || !out))) return fail(MARFA_E_INVAL, "bad arguments");

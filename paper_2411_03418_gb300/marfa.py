@@ -42,7 +42,7 @@ _LIB = None
 EXPORTS = ["marfa_prepare_lines", "marfa_free_lines", "marfa_num_points", "marfa_absorption",
            "marfa_absorption_batch", "marfa_write_pt_table", "marfa_last_error", "marfa_diag_voigt",
            "marfa_diag_level_lines", "marfa_diag_owned", "marfa_diag_absorption_counted",
-           "marfa_diag_kernel_timing"]
+           "marfa_diag_kernel_timing", "marfa_absorption_noalloc"]
 
 
 def lib_path() -> str:
@@ -72,6 +72,7 @@ def load(path: str | None = None):
         "marfa_diag_owned": (C.c_int, [vp, vp, vp, i32, vp, i32, i32, i64, i32, vp]),
         "marfa_diag_absorption_counted": (C.c_int, [vp, vp, vp, i32, vp, vp, vp]),
         "marfa_diag_kernel_timing": (C.c_int, [i32, vp, vp]),
+        "marfa_absorption_noalloc": (C.c_int, [vp, vp, vp, i32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -155,6 +156,16 @@ def marfa_absorption(lines: Lines, levels: np.ndarray, vmr: np.ndarray, rq: marf
     vmr = np.ascontiguousarray(vmr, dtype=np.float64)
     _check(load().marfa_absorption(lines.handle, _ptr(levels), _ptr(vmr), len(levels), C.byref(rq),
                                    _ptr(k_out), _stream(stream)))
+
+
+def marfa_absorption_noalloc(lines: Lines, levels: np.ndarray, vmr: np.ndarray, rq: marfa_request_t,
+                             k_out, stream=None) -> None:
+    """marfa_absorption without device allocation (scratch in the library's own
+    32 MiB device array); k_out must be a CUDA tensor [n_levels, npts] float32."""
+    levels = np.ascontiguousarray(levels, dtype=LEVEL_DTYPE)
+    vmr = np.ascontiguousarray(vmr, dtype=np.float64)
+    _check(load().marfa_absorption_noalloc(lines.handle, _ptr(levels), _ptr(vmr), len(levels), C.byref(rq),
+                                           _ptr(k_out), _stream(stream)))
 
 
 def marfa_absorption_batch(lines, levels, vmrs, rqs, k_outs, stream=None) -> None:
