@@ -424,7 +424,8 @@ static int build_plan(Plan& P, const marfa_lines_t* L, const marfa_level_t* leve
       P.g1.push_back(G1Item{req_idx, l, m0});
   for (int g = 2; g <= kNGrid; ++g)
     for (int l = 0; l < n_levels; ++l)
-      for (int64_t m0 = R.m_first[g]; m0 <= R.m_first[g] + R.npan[g]; m0 += (int64_t)kCPairs * kCWarps)
+      for (int64_t m0 = R.m_first[g]; m0 <= R.m_first[g] + R.npan[g];
+           m0 += g <= kLastLM ? (int64_t)kLPairs : (int64_t)kCPairs * kCWarps)
         P.coarse.push_back(CoarseItem{req_idx, l, g, 0, m0});
   const int64_t kb0 = R.k_lo & ~(int64_t)7;  // tiles start on a G10 panel
   for (int l = 0; l < n_levels; ++l)
@@ -559,7 +560,10 @@ static int run_plans(std::vector<Plan>& plans, cudaStream_t st, std::vector<int6
       size_t k1 = k;
       while (k1 < ci.size() && ci[k1].grid == g) ++k1;
       ev = timing_begin(st);
-      launch_coarse(drd, dci + k, (int)(k1 - k), dcc ? dcc + k : nullptr, st);
+      if (g <= kLastLM)
+        launch_coarse_lm(drd, dci + k, (int)(k1 - k), dcc ? dcc + k : nullptr, st);
+      else
+        launch_coarse(drd, dci + k, (int)(k1 - k), dcc ? dcc + k : nullptr, st);
       timing_end(ev, g, st);
       k = k1;
     }
@@ -779,7 +783,10 @@ extern "C" int marfa_absorption_noalloc(const marfa_lines_t* lines, const marfa_
   for (int g = 2; g <= kNGrid; ++g) {  // P.coarse is ordered by grid
     size_t k1 = k;
     while (k1 < P.coarse.size() && P.coarse[k1].grid == g) ++k1;
-    launch_coarse(drd, dci + k, (int)(k1 - k), nullptr, st);
+    if (g <= kLastLM)
+      launch_coarse_lm(drd, dci + k, (int)(k1 - k), nullptr, st);
+    else
+      launch_coarse(drd, dci + k, (int)(k1 - k), nullptr, st);
     k = k1;
   }
   launch_fine(drd, dfi, (int)P.fine.size(), nullptr, st);

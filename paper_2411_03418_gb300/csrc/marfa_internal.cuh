@@ -100,7 +100,10 @@ struct G1Item {
 constexpr int kG1Pairs = 32;         // node pairs per G1 tile (one per lane)
 constexpr int kG1Warps = 8;          // warps of a G1 CTA, each takes every 8th staged line
 constexpr int kG1Batch = 512;        // lines staged in shared memory at a time
-constexpr int kCPairs = 32;          // node pairs per tile of grids 2..10
+constexpr int kLPairs = 32;          // node pairs per CTA of the line-major kernel (grids 2..kLastLM)
+constexpr int kLWarps = 4;
+constexpr int kLastLM = 7;           // grids 2..7 line-major, 8..10 two-phase
+constexpr int kCPairs = 32;          // node pairs per warp tile of the two-phase kernel
 constexpr int kCWarps = 4;           // warps (tiles) of a grids-2..10 CTA
 constexpr int kFineThreads = 256;
 constexpr int kFinePerThread = 4;
@@ -127,6 +130,8 @@ void launch_g1(const ReqDev* reqs, const G1Item* items, int n_items, int64_t* co
                cudaStream_t st);
 void launch_coarse(const ReqDev* reqs, const CoarseItem* items, int n_items, int64_t* counts,
                    cudaStream_t st);
+void launch_coarse_lm(const ReqDev* reqs, const CoarseItem* items, int n_items, int64_t* counts,
+                      cudaStream_t st);
 void launch_fine(const ReqDev* reqs, const FineItem* items, int n_items, int64_t* counts,
                  cudaStream_t st);
 void launch_diag_voigt(const float* x, const float* y, float* out, int64_t n, cudaStream_t st);

@@ -162,18 +162,29 @@ __device__ __forceinline__ MT accept_mask(int g, int64_t c, int gst, bool chi, i
   int64_t s_lo = cl_sh(c - cut, s), s_hi = fl_sh(c + cut, s) - 1;
   MT m = rmask<MT>(s_lo * f, s_hi * f + k, base, nb);
   if (!m) return MT(0);
+  // the span covered by the mask bits, in fixed point
+  const int sb = child ? s - 1 : s;
+  const int64_t xa = base << sb, xb = (base + nb) << sb;
+  const int64_t P = int64_t(1) << s;  // panel width of grid g: a gap or kink panel lies
+                                      // within one panel width of c +- R or c +- B
   if (gst > g) {
-    int64_t R = (int64_t)R_w * step_fx(g);
-    int64_t gl = fl_sh(c - R, s), gh = cl_sh(c + R, s) - 1;
-    m &= ~rmask<MT>(gl * f, gh * f + k, base, nb);
+    const int64_t R = (int64_t)R_w * step_fx(g);
+    if (c + R + P >= xa && c - R - P <= xb) {
+      int64_t gl = fl_sh(c - R, s), gh = cl_sh(c + R, s) - 1;
+      m &= ~rmask<MT>(gl * f, gh * f + k, base, nb);
+    }
   }
   if (chi) {
+    // a panel holding a breakpoint beyond the cut-off already fails the support test
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      int64_t B = kChiBreakFx[b];
-      int64_t s1 = c - B, s2 = c + B;
-      m &= ~rmask<MT>((cl_sh(s1, s) - 1) * f, fl_sh(s1, s) * f + k, base, nb);
-      m &= ~rmask<MT>((cl_sh(s2, s) - 1) * f, fl_sh(s2, s) * f + k, base, nb);
+      const int64_t B = kChiBreakFx[b];
+      if (B > cut) break;
+      const int64_t s1 = c - B, s2 = c + B;
+      if (s1 >= xa - P && s1 <= xb + P)
+        m &= ~rmask<MT>((cl_sh(s1, s) - 1) * f, fl_sh(s1, s) * f + k, base, nb);
+      if (s2 >= xa - P && s2 <= xb + P)
+        m &= ~rmask<MT>((cl_sh(s2, s) - 1) * f, fl_sh(s2, s) * f + k, base, nb);
     }
   }
   return m;
@@ -389,6 +400,7 @@ __global__ void __launch_bounds__(kG1Warps * 32)
   const int64_t m0 = it.m0, base = m0 - 1;
   const int nb = kG1Pairs + 1;
   const uint64_t win = rmask<uint64_t>(m_first, m_last, base, nb);
+  const uint64_t full_tile = (2ull << (nb - 1)) - 1ull;  // all nb panels (tile inside the window)
   const int64_t X0 = m0 << s;  // node 2 m0
   const int64_t cut = R.cut_fx;
   const LevelDev L = R.lev[lev];
@@ -441,21 +453,43 @@ __global__ void __launch_bounds__(kG1Warps * 32)
         aR = aC * 1.084f * expf(-0.027f * d0);
         aL = aC * 1.084f * expf(0.027f * d0);
       }
+      // fast-path flags: bit 0 exact path; bit 1 the line owns every panel of the tile;
+      // bits 2-3 the chi side of all evaluated nodes (1 left, 2 right, 0 centre/mixed)
+      int fl = exact ? 1 : 0;
+      if (jL >= 2 * kG1Pairs - 1) fl |= 4;        // every node at d <= -3
+      else if (jR <= 0) fl |= 8;                  // every node at d >= 3
+      const bool one_side = !(chi && physical) || (fl & 12);
+      if (msk == full_tile && one_side) fl |= 2;
       sA[k] = make_float4(nx.qf, nx.hs, nx.phs, y * y);
       sB[k] = make_float4(aC, aL, aR, -0.5f * y * y);
       sM[k] = msk;
-      sC[k] = make_int4(jL, jR, exact ? 1 : 0, 0);
+      sC[k] = make_int4(jL, jR, fl, 0);
     }
     __syncthreads();
     float pe = 0.f, pl = 0.f, pr = 0.f, pm = 0.f;
     for (int k = warp; k < nbat; k += kG1Warps) {
+      const int4 C = sC[k];
+      if ((C.z & 3) == 2) {
+        // the line owns the whole tile through the far wing, on one chi side or with no chi
+        const float4 a = sA[k], b = sB[k];
+        const bool right = C.z & 8, left = C.z & 4;
+        const float a0 = right ? b.z * rR0 : (left ? b.y * rL0 : b.x);
+        const float a1 = right ? b.z * rR1 : (left ? b.y * rL1 : b.x);
+        const float x0 = fmaf(f0 + a.x, a.y, a.z), x02 = x0 * x0;
+        const float i0 = __fdividef(1.0f, x02 + a.w);
+        const float x1 = fmaf(f1 + a.x, a.y, a.z), x12 = x1 * x1;
+        const float i1 = __fdividef(1.0f, x12 + a.w);
+        pe += a0 * i0 * fmaf(fmaf(1.5f, x02, b.w), i0 * i0, 1.0f);
+        pm += a1 * i1 * fmaf(fmaf(1.5f, x12, b.w), i1 * i1, 1.0f);
+        if (COUNT) nev += 2;
+        continue;
+      }
       const uint64_t msk = sM[k];
       const bool bL = (msk >> (p + 1)) & 1ull;  // panel m0+p: L of node 2m, M of node 2m+1
       const bool bR = (msk >> p) & 1ull;        // panel m0+p-1: R of node 2m
       if (!(bL || bR)) continue;
-      const int4 C = sC[k];
       float v0, v1;
-      if (!C.z) {
+      if (!(C.z & 1)) {
         const float4 a = sA[k], b = sB[k];
         const float x0 = fmaf(f0 + a.x, a.y, a.z), x02 = x0 * x0;
         const float i0 = __fdividef(1.0f, x02 + a.w);
@@ -529,6 +563,131 @@ void launch_g1(const ReqDev* reqs, const G1Item* items, int n_items, int64_t* co
     k_g1<false><<<n_items, kG1Warps * 32, 0, st>>>(reqs, items, counts);
 }
 
+// ------------------------------------------------------------------ grids 2..10, line-major
+// A CTA owns kLPairs consecutive node pairs of grid g of one level. Each thread takes
+// one candidate line at a time, forms the exact mask of the panels the line owns in
+// the tile, evaluates the profile at the nodes of those panels only, and adds the
+// values into lane-private shared-memory slots (acc[pair][lane]); the slots are summed
+// over lanes and warps in a fixed order at the end.
+template <bool COUNT>
+__global__ void __launch_bounds__(kLWarps * 32)
+    k_coarse_lm(const ReqDev* __restrict__ reqs, const CoarseItem* __restrict__ items,
+             int64_t* __restrict__ counts) {
+  __shared__ float accL[kLWarps][kLPairs][32];
+  __shared__ float accM[kLWarps][kLPairs][32];
+  __shared__ float accR[kLWarps][kLPairs][32];
+  __shared__ int64_t sCnt[kLWarps];
+  const CoarseItem it = items[blockIdx.x];
+  const ReqDev& R = reqs[it.req];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = it.grid;
+  const int lev = it.level;
+  const int64_t m_first = R.m_first[g];
+  const int64_t m_last = m_first + R.npan[g] - 1;
+  const int64_t m0 = it.m0;
+  const int s = panel_shift(g);
+  const int64_t cut = R.cut_fx;
+  const int64_t base = m0 - 1;  // mask bit b <-> panel m0 - 1 + b
+  const int nb = kLPairs + 1;
+  const uint64_t win = rmask<uint64_t>(m_first, m_last, base, nb);
+  for (int p = 0; p < kLPairs; ++p) {
+    accL[warp][p][lane] = 0.0f;
+    accM[warp][p][lane] = 0.0f;
+    accR[warp][p][lane] = 0.0f;
+  }
+  const LevelDev L = R.lev[lev];
+  Bands bd;
+  {
+    const int64_t P = int64_t(1) << s;
+    const int64_t A = (base >> 1) << (s + 1);
+    const int64_t B = (((base + nb - 1) >> 1) + 1) << (s + 1);
+    int64_t zlo[9], zhi[9];
+    const int nz = make_zones(A, B, (int64_t)R.R_w * step_fx(g - 1), cut, P, R.chi_req, zlo, zhi);
+    bd.lookup(R, L, zlo, zhi, nz);
+  }
+  const int64_t lo_off = (int64_t)lev * R.n_lines;
+  const int64_t X0 = m0 << s;  // position of node 2 m0 (j = 0)
+  const bool physical = R.shape < kShapeConst;
+  const bool voigt = R.shape == kShapeVoigt;
+  int64_t nev = 0;
+  __syncwarp();
+  for (int r = 0; r < bd.n; ++r) {
+    for (int64_t i0 = bd.lo[r]; i0 < bd.hi[r]; i0 += kLWarps * 32) {
+      const int64_t i = i0 + tid;
+      if (i >= bd.hi[r]) continue;
+      const int64_t c = __ldg(R.c + lo_off + i);
+      const int gst = __ldg(R.gstar + lo_off + i);
+      const bool chi = __ldg(R.flags + lo_off + i) & 1;
+      uint64_t own = accept_mask<uint64_t>(g, c, gst, chi, cut, R.R_w, base, nb, false) & win;
+      if (own) own &= ~accept_mask<uint64_t>(g - 1, c, gst, chi, cut, R.R_w, base, nb, true);
+      if (!own) continue;
+      const float amp = __ldg(R.amp + lo_off + i);
+      const float sx = __ldg(R.sx + lo_off + i);
+      const float y = __ldg(R.yv + lo_off + i);
+      NodeX nx;
+      nx.init(X0 - c, s - 1, sx);
+      ChiThr ct;
+      const bool use_chi = chi && physical;
+      if (use_chi) ct.init(c, X0, s - 1);
+      // pair p uses bits p (R slot of node 2p) and p + 1 (L of node 2p, M of node 2p+1)
+      const int pa = max(__ffsll((long long)own) - 2, 0);
+      const int pb = min(63 - __clzll((long long)own), kLPairs - 1);
+      for (int p = pa; p <= pb; ++p) {
+        const bool bR = (own >> p) & 1ull, bL = (own >> (p + 1)) & 1ull;
+        if (!(bR || bL)) continue;
+        const float jf = (float)(2 * p);
+        const float xv = nx.x(jf);
+        float v = amp * (voigt ? voigt_K(xv, y) : shape_f(R.shape, xv, y));
+        if (use_chi) v *= ct.value(2 * p, nx.absd(jf, s - 1));
+        if (bL) accL[warp][p][lane] += v;
+        if (bR) accR[warp][p][lane] += v;
+        if (bL) {
+          const float xw = nx.x(jf + 1.0f);
+          float w = amp * (voigt ? voigt_K(xw, y) : shape_f(R.shape, xw, y));
+          if (use_chi) w *= ct.value(2 * p + 1, nx.absd(jf + 1.0f, s - 1));
+          accM[warp][p][lane] += w;
+        }
+        if (COUNT) nev += 1 + (bL ? 1 : 0);
+      }
+    }
+  }
+  if (COUNT) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) nev += __shfl_xor_sync(0xffffffffu, nev, o);
+    if (lane == 0) sCnt[warp] = nev;
+  }
+  __syncthreads();
+  // thread t < 3 kLPairs sums slot (t / kLPairs, pair t % kLPairs) over warps and lanes
+  if (tid < 3 * kLPairs) {
+    const int kind = tid / kLPairs, p = tid % kLPairs;
+    float (*acc)[kLPairs][32] = kind == 0 ? accL : (kind == 1 ? accM : accR);
+    float sum = 0.0f, cmp = 0.0f;
+    for (int w = 0; w < kLWarps; ++w)
+      for (int l = 0; l < 32; ++l) kahan_add(sum, cmp, acc[w][p][(l + p) & 31]);
+    const float v = sum + cmp;
+    float* gp = R.slots + (int64_t)lev * R.slots_per_level + R.slot_off[g];
+    const int64_t np = R.npan[g];
+    const int64_t m = m0 + p;
+    if (kind == 0 && m <= m_last) gp[m - m_first] = v;
+    if (kind == 1 && m <= m_last) gp[np + (m - m_first)] = v;
+    if (kind == 2 && m - 1 >= m_first && m - 1 <= m_last) gp[2 * np + (m - 1 - m_first)] = v;
+  }
+  if (COUNT && tid == 0) {
+    int64_t t = 0;
+    for (int w = 0; w < kLWarps; ++w) t += sCnt[w];
+    counts[blockIdx.x] = t;
+  }
+}
+
+void launch_coarse_lm(const ReqDev* reqs, const CoarseItem* items, int n_items, int64_t* counts,
+                      cudaStream_t st) {
+  if (n_items <= 0) return;
+  if (counts)
+    k_coarse_lm<true><<<n_items, kLWarps * 32, 0, st>>>(reqs, items, counts);
+  else
+    k_coarse_lm<false><<<n_items, kLWarps * 32, 0, st>>>(reqs, items, counts);
+}
+
 // ------------------------------------------------------------------ grids 2..10
 // Warp w of a CTA owns kCPairs consecutive node pairs of grid g of one level (lane p
 // holds pair p: even node 2m, odd node 2m+1). The warp takes 32 candidate lines at a
@@ -540,6 +699,7 @@ template <bool COUNT>
 __global__ void __launch_bounds__(kCWarps * 32)
     k_coarse(const ReqDev* __restrict__ reqs, const CoarseItem* __restrict__ items,
              int64_t* __restrict__ counts) {
+  __shared__ float stab[kVoigtTableFloats];
   __shared__ float bufE[kCWarps][32][kCPairs + 1];  // value at node 2p of staged line t
   __shared__ float bufO[kCWarps][32][kCPairs + 1];  // value at node 2p + 1
   __shared__ unsigned long long smsk[kCWarps][32];
@@ -553,6 +713,8 @@ __global__ void __launch_bounds__(kCWarps * 32)
   const int64_t m_last = m_first + R.npan[g] - 1;
   const int64_t m0 = it.m0 + (int64_t)kCPairs * warp;  // this warp's first pair
   int64_t nev = 0;
+  voigt_table_to_smem(stab);
+  __syncthreads();
   if (m0 <= m_last + 1) {  // warp-uniform
     const int s = panel_shift(g);
     const int64_t cut = R.cut_fx;
@@ -610,12 +772,12 @@ __global__ void __launch_bounds__(kCWarps * 32)
             if (!(bR || bL)) continue;
             const float jf = (float)(2 * q);
             const float xv = nx.x(jf);
-            float v = amp * (voigt ? voigt_K(xv, y) : shape_f(R.shape, xv, y));
+            float v = amp * (voigt ? voigt_K<true>(xv, y, stab) : shape_f(R.shape, xv, y));
             if (use_chi) v *= ct.value(2 * q, nx.absd(jf, s - 1));
             bE[lane][q] = v;
             if (bL) {
               const float xw = nx.x(jf + 1.0f);
-              float w = amp * (voigt ? voigt_K(xw, y) : shape_f(R.shape, xw, y));
+              float w = amp * (voigt ? voigt_K<true>(xw, y, stab) : shape_f(R.shape, xw, y));
               if (use_chi) w *= ct.value(2 * q + 1, nx.absd(jf + 1.0f, s - 1));
               bO[lane][q] = w;
             }
@@ -683,26 +845,25 @@ void launch_coarse(const ReqDev* reqs, const CoarseItem* items, int n_items, int
 // within the cut-off, and stages them in shared memory; every lane then sums the
 // staged lines that own its nodes. Finally each node adds the quadratic interpolants
 // of the ten coarse grids, and the CTA writes its outputs with aligned vector stores.
-struct FineStage {
-  float qf, hs, phs, phi;   // node positions relative to the warp's first node
-  float amp, y;
-  uint32_t pm;              // G10 panels of the warp the line leaves to the finest grid
-  int klo, khi;             // warp-relative node range within the cut-off and the window
-  int chi;                  // chi-factor applies
-  int r3, r150, r300, l3, l150, l300;
-};
-
 template <bool COUNT>
 __global__ void __launch_bounds__(kFineThreads)
     k_fine(const ReqDev* __restrict__ reqs, const FineItem* __restrict__ items,
            int64_t* __restrict__ counts) {
+  constexpr int NW = kFineThreads / 32;
   __shared__ float tile[kFineTile];
-  __shared__ FineStage stg[kFineThreads / 32][32];
-  __shared__ int64_t red[kFineThreads / 32];
+  __shared__ float stab[kVoigtTableFloats];
+  // staged lines, one slot per lane of each warp (struct of arrays: no bank conflicts)
+  __shared__ float sQ[NW][32], sHs[NW][32], sPhs[NW][32], sPhi[NW][32], sAmp[NW][32], sY[NW][32];
+  __shared__ uint32_t sPm[NW][32];
+  __shared__ int sKlo[NW][32], sKhi[NW][32], sChi[NW][32];
+  __shared__ int sT[6][NW][32];  // chi thresholds r3, r150, r300, l3, l150, l300
+  __shared__ int64_t red[NW];
   const FineItem it = items[blockIdx.x];
   const ReqDev& R = reqs[it.req];
   const int lev = it.level;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  voigt_table_to_smem(stab);
+  __syncthreads();
   const int64_t kw = it.k0 + (int64_t)kFinePerThread * 32 * warp;  // first node of the warp
   const int64_t k0 = kw + kFinePerThread * lane;                    // first node of the lane
   const int64_t cut = R.cut_fx;
@@ -728,18 +889,16 @@ __global__ void __launch_bounds__(kFineThreads)
     const bool physical = R.shape < kShapeConst;
     const bool voigt = R.shape == kShapeVoigt;
     const int mypanel = lane >> 1;
-    FineStage* st = stg[warp];
     for (int r = 0; r < bd.n; ++r) {
       for (int64_t i0 = bd.lo[r]; i0 < bd.hi[r]; i0 += 32) {
         const int64_t i = i0 + lane;
         uint32_t pm = 0;
         int klo = 0, khi = -1;
         int64_t c = 0;
-        int gst = 0;
         bool chi = false;
         if (i < bd.hi[r]) {
           c = __ldg(R.c + lo_off + i);
-          gst = __ldg(R.gstar + lo_off + i);
+          const int gst = __ldg(R.gstar + lo_off + i);
           chi = __ldg(R.flags + lo_off + i) & 1;
           klo = (int)max(cl_sh(c - cut, kFineShift) - kw, (int64_t)wlo);
           khi = (int)min(fl_sh(c + cut, kFineShift) - kw, (int64_t)whi);
@@ -751,50 +910,54 @@ __global__ void __launch_bounds__(kFineThreads)
         const uint32_t any = __ballot_sync(0xffffffffu, pm != 0);
         if (!any) continue;
         __syncwarp();
+        sPm[warp][lane] = pm;
         if (pm) {
-          FineStage e;
           NodeX nx;
-          const float sx = __ldg(R.sx + lo_off + i);
-          nx.init(Xa - c, kFineShift, sx);
-          e.qf = nx.qf; e.hs = nx.hs; e.phs = nx.phs; e.phi = nx.phi;
-          e.amp = __ldg(R.amp + lo_off + i);
-          e.y = __ldg(R.yv + lo_off + i);
-          e.pm = pm; e.klo = klo; e.khi = khi;
-          e.chi = chi && physical;
-          if (e.chi) {
+          nx.init(Xa - c, kFineShift, __ldg(R.sx + lo_off + i));
+          sQ[warp][lane] = nx.qf;
+          sHs[warp][lane] = nx.hs;
+          sPhs[warp][lane] = nx.phs;
+          sPhi[warp][lane] = nx.phi;
+          sAmp[warp][lane] = __ldg(R.amp + lo_off + i);
+          sY[warp][lane] = __ldg(R.yv + lo_off + i);
+          sKlo[warp][lane] = klo;
+          sKhi[warp][lane] = khi;
+          const bool uc = chi && physical;
+          sChi[warp][lane] = uc;
+          if (uc) {
             ChiThr ct;
             ct.init(c, Xa, kFineShift);
-            e.r3 = ct.r3; e.r150 = ct.r150; e.r300 = ct.r300;
-            e.l3 = ct.l3; e.l150 = ct.l150; e.l300 = ct.l300;
+            sT[0][warp][lane] = ct.r3; sT[1][warp][lane] = ct.r150; sT[2][warp][lane] = ct.r300;
+            sT[3][warp][lane] = ct.l3; sT[4][warp][lane] = ct.l150; sT[5][warp][lane] = ct.l300;
           }
-          st[lane] = e;
-        } else {
-          st[lane].pm = 0;
         }
         __syncwarp();
         // this lane's staged lines (those that leave its G10 panel to the finest grid)
         uint32_t mine = 0;
         for (uint32_t rem = any; rem; rem &= rem - 1) {
-          const int e_i = __ffs(rem) - 1;
-          mine |= ((st[e_i].pm >> mypanel) & 1u) << e_i;
+          const int e = __ffs(rem) - 1;
+          mine |= ((sPm[warp][e] >> mypanel) & 1u) << e;
         }
         while (mine) {
-          const int e_i = __ffs(mine) - 1;
+          const int e = __ffs(mine) - 1;
           mine &= mine - 1;
-          const FineStage& e = st[e_i];
+          const float qf = sQ[warp][e], hs = sHs[warp][e], phs = sPhs[warp][e], phi = sPhi[warp][e];
+          const float amp = sAmp[warp][e], y = sY[warp][e];
+          const int klo_e = sKlo[warp][e], khi_e = sKhi[warp][e];
+          const bool uc = sChi[warp][e];
           ChiThr ct;
-          if (e.chi) {
-            ct.r3 = e.r3; ct.r150 = e.r150; ct.r300 = e.r300;
-            ct.l3 = e.l3; ct.l150 = e.l150; ct.l300 = e.l300;
+          if (uc) {
+            ct.r3 = sT[0][warp][e]; ct.r150 = sT[1][warp][e]; ct.r300 = sT[2][warp][e];
+            ct.l3 = sT[3][warp][e]; ct.l150 = sT[4][warp][e]; ct.l300 = sT[5][warp][e];
           }
 #pragma unroll
           for (int q = 0; q < kFinePerThread; ++q) {
             const int j = kFinePerThread * lane + q;
-            if (j < e.klo || j > e.khi) continue;
+            if (j < klo_e || j > khi_e) continue;
             const float jf = (float)j;
-            const float xv = fmaf(jf + e.qf, e.hs, e.phs);
-            float v = e.amp * (voigt ? voigt_K(xv, e.y) : shape_f(R.shape, xv, e.y));
-            if (e.chi) v *= ct.value(j, fabsf((jf + e.qf) + e.phi) * ldexpf(1.0f, -kFineBits));
+            const float xv = fmaf(jf + qf, hs, phs);
+            float v = amp * (voigt ? voigt_K<true>(xv, y, stab) : shape_f(R.shape, xv, y));
+            if (uc) v *= ct.value(j, fabsf((jf + qf) + phi) * ldexpf(1.0f, -kFineBits));
             kahan_add(acc[q], cmp[q], v);
             if (COUNT) ++nev;
           }

@@ -61,14 +61,20 @@ __device__ __forceinline__ float voigt_asym(float x, float y) {
   return -(ui * sr + ur * si) * kInvSqrtPi;
 }
 
-__device__ __forceinline__ float voigt_cell(int cell, float u, float v) {
-  const float* c = kVoigtCells + cell * (VOIGT_DEG + 1) * (VOIGT_DEG + 1);
+// One bivariate cell; tab is the coefficient table, either the global copy (read
+// through the read-only cache) or a copy a kernel placed in shared memory (SMEM).
+template <bool SMEM>
+__device__ __forceinline__ float voigt_cell(const float* tab, int cell, float u, float v) {
+  const float* c = tab + cell * (VOIGT_DEG + 1) * (VOIGT_DEG + 1);
   float acc = 0.0f;
 #pragma unroll
   for (int p = VOIGT_DEG; p >= 0; --p) {
     float r = 0.0f;
 #pragma unroll
-    for (int q = VOIGT_DEG; q >= 0; --q) r = fmaf(r, v, __ldg(c + p * (VOIGT_DEG + 1) + q));
+    for (int q = VOIGT_DEG; q >= 0; --q) {
+      const int k = p * (VOIGT_DEG + 1) + q;
+      r = fmaf(r, v, SMEM ? c[k] : __ldg(c + k));
+    }
     acc = fmaf(acc, u, r);
   }
   return acc;
@@ -85,12 +91,13 @@ __device__ __forceinline__ float voigt_far(float x, float y) {
 // Everything but the far wing, kept out of line so that unrolled callers stay small.
 // The Dawson-table branch covers the whole near wing of narrow lines (y < 1, |x| < 12)
 // so that one line's nodes on the fine grids take a single code path.
-__device__ __noinline__ float voigt_K_near(float ax, float y) {
+template <bool SMEM>
+__device__ __noinline__ float voigt_K_near(float ax, float y, const float* tab) {
   if (y < 1.0f && ax < 12.0f) {
     int ci = min((int)(ax * 2.0f), VOIGT_NPSI - 1);
     float u = (ax - (0.5f * ci + 0.25f)) * 4.0f;
     float v = 2.0f * y * y - 1.0f;
-    float ps = voigt_cell(ci, u, v);
+    float ps = voigt_cell<SMEM>(tab, ci, u, v);
     float gt = ax < 6.5f ? gauss_term(ax, y) : 0.0f;
     return gt - kTwoOverSqrtPi * y * ps;
   }
@@ -101,14 +108,25 @@ __device__ __noinline__ float voigt_K_near(float ax, float y) {
   int iy = min((int)((y - 1.0f) * (1.0f / 1.75f)), 1);
   float u = (ax - (0.9f * ix + 0.45f)) * (1.0f / 0.45f);
   float v = (y - (1.0f + 1.75f * iy + 0.875f)) * (1.0f / 0.875f);
-  return voigt_cell(VOIGT_NPSI + ix * 2 + iy, u, v);
+  return voigt_cell<SMEM>(tab, VOIGT_NPSI + ix * 2 + iy, u, v);
 }
 
-__device__ __forceinline__ float voigt_K(float x, float y) {
+template <bool SMEM>
+__device__ __forceinline__ float voigt_K(float x, float y, const float* tab) {
   float ax = fabsf(x);
   float r2 = fmaf(ax, ax, y * y);
   if (r2 >= 1.0e4f) return voigt_far(ax, y);
-  return voigt_K_near(ax, y);
+  return voigt_K_near<SMEM>(ax, y, tab);
 }
+
+__device__ __forceinline__ float voigt_K(float x, float y) { return voigt_K<false>(x, y, kVoigtCells); }
+
+// Copy the coefficient table into shared memory (all threads of the block take part).
+__device__ __forceinline__ void voigt_table_to_smem(float* dst) {
+  for (int i = threadIdx.x; i < VOIGT_NCELL * (VOIGT_DEG + 1) * (VOIGT_DEG + 1); i += blockDim.x)
+    dst[i] = kVoigtCells[i];
+}
+
+constexpr int kVoigtTableFloats = VOIGT_NCELL * (VOIGT_DEG + 1) * (VOIGT_DEG + 1);
 
 }  // namespace marfa

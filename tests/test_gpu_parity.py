@@ -283,3 +283,13 @@ def test_config1_venus_full_size_sampled(M):
         big = np.abs(ref) > FLOOR * rowmax
         assert np.all(np.abs(got[big] / ref[big] - 1) < RTOL), f"level {lev}"
         assert np.all(np.abs(got[~big] - ref[~big]) <= RTOL * FLOOR * rowmax)
+
+
+def test_wide_window_full_tiles_parity(M):
+    # a window spanning several 64 cm^-1 grid-1 tiles, so that interior tiles (where a
+    # line can own every panel) are compared at every output node
+    wl = tiny_workload(95, 260, 1000.0, 1140.0, 25.0, T=(735.0, 200.0), p=(3.0, 1e-4),
+                       chi="tonkov", chi_species=1)
+    got = run_gpu(M, wl)
+    for lev in range(wl.n_levels):
+        assert_parity(got[lev], O.eleven_grid(wl, lev), what=f"wide window level {lev}")
