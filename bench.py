@@ -128,6 +128,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nu-lo", type=float, default=None, help="narrow the window (profiling runs)")
+    ap.add_argument("--nu-hi", type=float, default=None)
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer steps")
+    ap.add_argument("--no-count", action="store_true", help="skip the evaluation-counting call")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -136,6 +140,9 @@ def main():
 
     from workloads import config1_venus
     wl = config1_venus()
+    if args.nu_lo is not None or args.nu_hi is not None:
+        wl = wl.with_(nu_lo=args.nu_lo if args.nu_lo is not None else wl.nu_lo,
+                      nu_hi=args.nu_hi if args.nu_hi is not None else wl.nu_hi)
 
     if args.impl == "reference":
         run_reference(args, wl, rank, world)
@@ -163,7 +170,10 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
 
     # evaluation count of one step (exact, from the counting variant of the kernels)
-    _, counts = M.marfa_diag_absorption_counted(lines, levels, wl.vmr, rq)
+    if args.no_count:
+        counts = np.zeros((wl.n_levels, 11), dtype=np.int64)
+    else:
+        _, counts = M.marfa_diag_absorption_counted(lines, levels, wl.vmr, rq)
     evals_per_step = int(counts.sum())
 
     def step():
@@ -206,24 +216,26 @@ def main():
     # end to end through the public call with host buffers (pinned)
     rec_h = torch.from_numpy(wl.lines.view(np.uint8)).pin_memory().numpy().view(wl.lines.dtype)
     out_h = torch.empty((wl.n_levels, npts), dtype=torch.float32).pin_memory().numpy()
-    for _ in range(1):
-        l2 = M.marfa_prepare_lines(rec_h, wl.species)
-        M.marfa_absorption(l2, levels, wl.vmr, rq, out_h, stream)
-        M.marfa_free_lines(l2)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        l2 = M.marfa_prepare_lines(rec_h, wl.species)
-        M.marfa_absorption(l2, levels, wl.vmr, rq, out_h, stream)
-        M.marfa_free_lines(l2)
-    torch.cuda.synchronize()
-    t_e2e = time.perf_counter() - t0
-    if dist:
-        tt = torch.tensor([t_e2e], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
+    t_e2e = float("nan")
+    if not args.no_e2e:
+        for _ in range(1):
+            l2 = M.marfa_prepare_lines(rec_h, wl.species)
+            M.marfa_absorption(l2, levels, wl.vmr, rq, out_h, stream)
+            M.marfa_free_lines(l2)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            l2 = M.marfa_prepare_lines(rec_h, wl.species)
+            M.marfa_absorption(l2, levels, wl.vmr, rq, out_h, stream)
+            M.marfa_free_lines(l2)
+        torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        if dist:
+            tt = torch.tensor([t_e2e], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t_e2e = float(tt.item())
     e2e_value = units * args.steps / t_e2e
 
     # roofline of the dominant kernel (FP32 pipe, algorithmic flops per evaluation)
