@@ -3,8 +3,9 @@
 Workload: 200,000 band-structured CO2-like lines over 1875-3125 cm^-1, 60 Venus
 levels (735 -> 170 K, 92 -> 1e-5 atm), Voigt x Tonkov chi-factor, 125 cm^-1 cut-off,
 k(nu) on 2000-3000 cm^-1 at 2^-11 cm^-1 (2,048,001 points per level). One step =
-one marfa_absorption call over all 60 levels (level preparation, coarse grids,
-finest grid with the interpolation cascade) with the line list resident on the GPU.
+one replay of the request's captured plan (marfa_plan_execute: level preparation,
+grid 1, grids 2..10 with their autotuned kernels, finest grid with the interpolation
+cascade, over all 60 levels) with the line list resident on the GPU.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -121,6 +122,57 @@ def run_reference(args, wl, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def surrogate_leg(args, M, wl, lines, levels, out, flush, stream, wpath, evals_plain, ms_plain, npts, dist,
+                  dev):
+    """The same workload with the learned Voigt under its guard: throughput, the share
+    of evaluations the surrogate took, and its largest relative deviation from the
+    plain FP32 path (both outputs on the device, compared where k > 1e-8 of the level's
+    maximum)."""
+    import torch
+    budget, lattice = 6e-4, 32
+    on, _ = M.marfa_surrogate_load(np.load(wpath).astype(np.float32), budget, lattice)
+    try:
+        plain = out.clone()
+        rq_s = M.request_of(wl.with_(surrogate=1))
+        if args.no_count:
+            counts = sc = np.zeros((wl.n_levels, 11), dtype=np.int64)
+        else:
+            _, counts, sc = M.marfa_diag_absorption_counted_surrogate(lines, levels, wl.vmr, rq_s)
+        plan = M.marfa_plan_create([lines], [levels], [wl.vmr], [rq_s], [out], autotune=True, stream=stream)
+        for _ in range(args.warmup):
+            M.marfa_plan_execute(plan, stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            M.marfa_plan_execute(plan, stream)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        M.marfa_plan_destroy(plan)
+        t_total = float(sum(a.elapsed_time(b) for a, b in ev)) / 1e3
+        if dist:
+            tt = torch.tensor([t_total], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t_total = float(tt.item())
+        world = dist.get_world_size() if dist else 1
+        mx = plain.abs().amax(dim=1, keepdim=True)
+        big = plain.abs() > 1e-8 * mx
+        rel = ((out - plain).abs() / plain.abs().clamp_min(1e-38))[big]
+        ms = t_total / args.steps * 1e3
+        return {"value": wl.n_levels * npts * world * args.steps / t_total, "unit": UNIT, "ms_per_step": ms,
+                "line_evals_per_s": int(counts.sum()) * world * args.steps / t_total,
+                "surrogate_evals_share": float(sc.sum() / max(1, counts.sum())),
+                "max_rel_vs_plain": float(rel.max().item()), "guard_budget": budget, "guard_lattice": lattice, "guard_cells_on": int(on),
+                "speedup_vs_plain": ms_plain / ms,
+                "note": "plain path within 1e-4 of the FP64 oracle; surrogate path within 1e-3 (tests)"}
+    finally:
+        M.marfa_surrogate_unload()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -132,6 +184,7 @@ def main():
     ap.add_argument("--nu-hi", type=float, default=None)
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer steps")
     ap.add_argument("--no-count", action="store_true", help="skip the evaluation-counting call")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-Voigt leg")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -176,8 +229,13 @@ def main():
         _, counts = M.marfa_diag_absorption_counted(lines, levels, wl.vmr, rq)
     evals_per_step = int(counts.sum())
 
+    t0 = time.perf_counter()
+    plan = M.marfa_plan_create([lines], [levels], [wl.vmr], [rq], [out], autotune=True, stream=stream)
+    plan_s = time.perf_counter() - t0
+    variant, tune_ms, _ = M.marfa_plan_info(plan)
+
     def step():
-        M.marfa_absorption(lines, levels, wl.vmr, rq, out, stream)
+        M.marfa_plan_execute(plan, stream)
 
     for _ in range(args.warmup):
         step()
@@ -187,16 +245,17 @@ def main():
 
     clk_path = os.path.join(tempfile.gettempdir(), f"marfa_clocks_{os.getpid()}.csv")
     sampler, fh = start_clock_sampler(clk_path)
-    M.marfa_diag_kernel_timing(True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kms = np.zeros(12)
     torch.cuda.synchronize()
     for i in range(args.steps):
         flush.fill_(float(i))  # L2 flush between steps, outside the timed events
         ev[i][0].record(stream)
         step()
         ev[i][1].record(stream)
+        kms += M.marfa_plan_info(plan, kernel_ms=True)[2]  # waits for this step's kernels
     torch.cuda.synchronize()
-    kms, klaunch = M.marfa_diag_kernel_timing(False)
+    klaunch = np.full(12, args.steps, dtype=np.int64)  # one launch of each kind per step
     step_ms = [a.elapsed_time(b) for a, b in ev]
     if sampler:
         sampler.terminate()
@@ -247,6 +306,13 @@ def main():
     mhz, src = peaks()
     peak = N_SM * FP32_LANES * 2 * mhz * 1e6 / 1e12
 
+    surr = None
+    wpath = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2411_03418_gb300",
+                         "surrogate_weights.npy")
+    if not args.no_surrogate and os.path.exists(wpath):
+        surr = surrogate_leg(args, M, wl, lines, levels, out, flush, stream, wpath, evals_per_step,
+                             ms_per_step, npts, dist, dev)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -260,12 +326,17 @@ def main():
                     "h2d_bytes_per_step": int(wl.lines.nbytes + levels.nbytes + wl.vmr.nbytes),
                     "d2h_bytes_per_step": int(out_h.nbytes)},
             "gpu_launches": int(klaunch.sum()),
+            "plan": {"graph": "one CUDA graph per step (12 kernel launches)", "create_s": plan_s,
+                     "variant_grids_1_10": [int(v) for v in variant],
+                     "autotune_ms_per_launch": [[round(float(a), 3), round(float(b), 3)] for a, b in tune_ms]},
             "kernel_ms_per_step": {n: float(kms[i] / args.steps) for i, n in enumerate(names)},
             "roofline": {"bound": "alu", "kernel": names[dom], "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                          "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz ({src} max clock)"},
             "clocks": clocks,
         }
+        if surr is not None:
+            line["surrogate"] = surr
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline_sample(wl)
         print(json.dumps(line), flush=True)

@@ -86,7 +86,9 @@ typedef struct {
   int32_t shape;       /* MARFA_SHAPE_*                                              */
   int32_t chi;         /* MARFA_CHI_*                                                */
   int32_t units;       /* MARFA_UNITS_*                                              */
-  int32_t surrogate;   /* must be 0: the learned Voigt is not part of this library   */
+  int32_t surrogate;   /* 0: plain FP32 Voigt; 1: the learned surrogate (loaded with
+                          marfa_surrogate_load on the current device) under its guard;
+                          Voigt shape only. Not part of the paper.                    */
   int32_t R_w;         /* wing distance, in steps of a grid, below which that grid
                           refines (1..64; 8 is the default preset)                    */
   int32_t R_c;         /* a grid resolves a core when its step <= W / R_c (1..64)      */
@@ -127,8 +129,9 @@ int64_t marfa_num_points(double nu_lo, double nu_hi);
  * The line list must cover [nu_lo - cutoff, nu_hi + cutoff] for the sum to be complete;
  * lines outside cannot contribute. The value at a given nu does not depend on the
  * window or on other requests. Errors: MARFA_E_INVAL (window, cut-off, R_w/R_c, enum
- * values, T/p/vmr not finite and positive/non-negative, surrogate != 0, more than
- * 2^31 points), MARFA_E_NOMEM, MARFA_E_CUDA.
+ * values, T/p/vmr not finite and positive/non-negative, surrogate not 0/1, surrogate
+ * with a shape other than Voigt or with no surrogate loaded on the current device, more
+ * than 2^31 points), MARFA_E_NOMEM, MARFA_E_CUDA.
  */
 int marfa_absorption(const marfa_lines_t* lines, const marfa_level_t* levels,
                      const double* vmr, int32_t n_levels, const marfa_request_t* rq,
@@ -144,6 +147,46 @@ int marfa_absorption_batch(int32_t n_req, const marfa_lines_t* const* lines,
                            const marfa_level_t* const* levels, const double* const* vmr,
                            const int32_t* n_levels, const marfa_request_t* rq,
                            float* const* k_out, void* stream);
+
+/*
+ * A batch of requests captured once as a CUDA graph and replayed on demand. Creation
+ * does everything marfa_absorption_batch does before its first kernel (validation,
+ * per-level tables, work lists, device buffers), runs the batch once (so k_out holds the
+ * result on return) and captures one graph: level preparation of every request, grid 1,
+ * grids 2..10 and the finest grid with the cascade, over all requests together.
+ *   k_out    : device, [n_req] pointers to [n_levels[r]][npts_r] float32, owned by the
+ *              caller and kept by the plan: every execution rewrites them;
+ *   lines    : must stay alive until marfa_plan_destroy; levels, vmr and rq are copied,
+ *              and so is the loaded surrogate for requests with surrogate = 1;
+ *   autotune : 1 = for each of grids 2..10, time the two summation kernels (line-major:
+ *              a thread per candidate line over 32 node pairs; two-phase: warps of 32
+ *              node pairs that stage 32 lines at a time) on this batch's own work and keep
+ *              the faster; 0 = grids 2..7 line-major, 8..10 two-phase;
+ *   stream   : used for creation (synchronised before return).
+ * Results equal marfa_absorption_batch's bit for bit when the kernel choice is the
+ * default; the other variant sums in another order (same tolerance to the oracle).
+ * Errors: those of marfa_absorption_batch, host k_out (MARFA_E_INVAL), capture errors
+ * (MARFA_E_CUDA). The paper has no counterpart (it runs one level at a time on CPUs).
+ */
+typedef struct marfa_plan marfa_plan_t;
+int marfa_plan_create(int32_t n_req, const marfa_lines_t* const* lines,
+                      const marfa_level_t* const* levels, const double* const* vmr,
+                      const int32_t* n_levels, const marfa_request_t* rq, float* const* k_out,
+                      int32_t autotune, void* stream, marfa_plan_t** out);
+
+/* Replay the plan's graph on stream (asynchronous; NULL = legacy default stream). The
+ * current device must be the plan's. */
+int marfa_plan_execute(marfa_plan_t* plan, void* stream);
+
+/* Kernel choice and timings (host arrays, each may be NULL): variant[10] for grids
+ * 1..10 (-1 grid 1, 0 line-major, 1 two-phase); tune_ms[10][2] the autotuner's time
+ * per launch of each variant (-1 when not tuned); kernel_ms[12] device time of the last
+ * execution per kernel kind (0 level preparation, 1..10 grids, 11 finest grid; waits for
+ * that execution; MARFA_E_CUDA before the first execution). */
+int marfa_plan_info(const marfa_plan_t* plan, int32_t* variant, float* tune_ms, double* kernel_ms);
+
+/* Free the plan's graph and device buffers (waits for the device). */
+void marfa_plan_destroy(marfa_plan_t* plan);
 
 /*
  * Appendix A PT-table: write k (host, npts float32 values at k 2^-11 over
@@ -185,6 +228,66 @@ int marfa_absorption_noalloc(const marfa_lines_t* lines, const marfa_level_t* le
                              const double* vmr, int32_t n_levels, const marfa_request_t* rq,
                              float* k_out, void* stream);
 
+/* ---------------------------------------------------------------- learned Voigt surrogate
+ * Not part of the paper. A 2-64-64-64-1 SiLU network predicts t = ln(K / K0) from
+ * u1 = ln y and u2 = ln(1 + |x| / (1 + y)), where
+ *   K0(x, y) = exp(-x^2) / (1 + 2y/sqrt(pi)) + y / (sqrt(pi) (x^2 + y^2 + 1)),
+ * so that K = K0 exp(t). Parameters: MARFA_MLP_PARAMS float32 packed as W1[64][2], b1[64],
+ * W2[64][64], b2[64], W3[64][64], b3[64], W4[64], b4[1] (W row-major [out][in]).
+ * Training runs on the current device in FP32 (mean squared error of t, Adam); inference
+ * runs on the tensor cores with BF16 W2, W3 and activations and FP32 accumulation.
+ */
+#define MARFA_MLP_PARAMS 8577
+#define MARFA_MLP_MAX_BATCH 65536
+/* Guard cells: |x| in [0, 12) in steps of 1/8 (index ix); y by binary exponent
+ * e in [-14, 3] and the two leading mantissa bits k, y in [2^e (1 + k/4), 2^e (1 + (k+1)/4))
+ * (index iy = 4 (e + 14) + k); cell = iy * MARFA_GUARD_NX + ix. */
+#define MARFA_GUARD_NX 96
+#define MARFA_GUARD_NY 72
+
+typedef struct {
+  int32_t steps;       /* optimiser steps (>= 1)                                     */
+  int32_t batch;       /* samples per step (1..MARFA_MLP_MAX_BATCH); step k takes the
+                          next batch of consecutive samples, wrapping at the end      */
+  int32_t qat;         /* 1: forward pass rounds W2, W3 and the hidden activations of
+                          layers 1-2 to BF16 as inference does (straight-through)     */
+  int32_t reserved;
+  float lr0, lr1;      /* Adam step size, cosine schedule from lr0 (step 0) to lr1    */
+} marfa_mlp_train_t;
+
+/* Mean squared error of the network's t over n samples and its gradient (host arrays:
+ * params [MARFA_MLP_PARAMS], x, y, t [n] with y > 0, grad [MARFA_MLP_PARAMS] out,
+ * loss out; n <= MARFA_MLP_MAX_BATCH). Runs the training kernels once (FP32; qat as
+ * in marfa_mlp_train_t). Errors: MARFA_E_INVAL, MARFA_E_NOMEM, MARFA_E_CUDA. */
+int marfa_mlp_loss_grad(const float* params, const float* x, const float* y, const float* t,
+                        int64_t n, int32_t qat, double* loss, float* grad);
+
+/* Train params (host, in/out) on the n samples (host x, y, t) with Adam; the
+ * mean-squared-error of each step goes to loss_curve[steps] (host, may be NULL).
+ * Synchronous. Errors: MARFA_E_INVAL, MARFA_E_NOMEM, MARFA_E_CUDA. */
+int marfa_mlp_train(float* params, const float* x, const float* y, const float* t, int64_t n,
+                    const marfa_mlp_train_t* cfg, float* loss_curve);
+
+/* Make params (host) the surrogate of the current device: convert them to the
+ * inference layout and build the guard. A guard cell is switched on when it lies in
+ * 1e-4 <= y <= 10, in the region where the plain FP32 Voigt takes its costly branches
+ * (y < 1, or x^2 + y^2 < 64), and the surrogate agrees with the plain FP32 Voigt within
+ * the relative budget at all samples x samples lattice points spanning the cell
+ * (2 <= samples <= 64). cells_on (may be NULL) receives the number of cells switched on
+ * and cell_err (host [MARFA_GUARD_NY * MARFA_GUARD_NX], may be NULL) the largest
+ * relative difference per cell (-1 outside the eligible region). Replaces a surrogate
+ * loaded before; not to be called while absorption calls run. Synchronous. */
+int marfa_surrogate_load(const float* params, float budget, int32_t samples, int32_t* cells_on,
+                         float* cell_err);
+
+/* Release the loaded surrogate (no-op if none). */
+int marfa_surrogate_unload(void);
+
+/* K(x, y) of the loaded surrogate at n points (host arrays; y > 0): guarded = 0 the
+ * network alone, guarded = 1 the evaluation the profile kernels use (the network where
+ * the guard holds, the plain FP32 Voigt elsewhere). */
+int marfa_surrogate_eval(const float* x, const float* y, float* out, int64_t n, int32_t guarded);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* marfa_last_error(void);
 
@@ -218,6 +321,23 @@ int marfa_diag_owned(const marfa_lines_t* lines, const marfa_level_t* levels,
 int marfa_diag_absorption_counted(const marfa_lines_t* lines, const marfa_level_t* levels,
                                   const double* vmr, int32_t n_levels,
                                   const marfa_request_t* rq, float* k_out, int64_t* counts);
+
+/* marfa_absorption with every evaluation counted: counts host array [n_levels][11][4]
+ * (grids 1..10, then the finest), per grid: all (line, node) profile evaluations, those
+ * the surrogate took, and the plain Voigt evaluations in the polynomial cells (y < 1 and
+ * |x| < 12, or |z| < 4.5) and in the 6- or 15-term asymptotic series (|z| < 100); the
+ * rest are far-wing two-term evaluations (or other shapes). */
+int marfa_diag_absorption_counts(const marfa_lines_t* lines, const marfa_level_t* levels,
+                                 const double* vmr, int32_t n_levels, const marfa_request_t* rq,
+                                 float* k_out, int64_t* counts);
+
+/* marfa_diag_absorption_counted that also returns, in surrogate_counts (host
+ * [n_levels][11]), how many of those evaluations the surrogate took. */
+int marfa_diag_absorption_counted_surrogate(const marfa_lines_t* lines,
+                                            const marfa_level_t* levels, const double* vmr,
+                                            int32_t n_levels, const marfa_request_t* rq,
+                                            float* k_out, int64_t* counts,
+                                            int64_t* surrogate_counts);
 
 /* Per-kernel device time: enable = 1 clears the totals and starts recording CUDA events
  * around every kernel launch of this library (on the launch stream); enable = 0 stops,

@@ -1,6 +1,6 @@
 """In-tree build of libmarfa (CUDA, sm_103a) with nvcc; no cmake, no setuptools.
 
-The two translation units are compiled in parallel and linked into
+The translation units are compiled in parallel and linked into
 ``paper_2411_03418_gb300/_build/libmarfa.so``. Host code is compiled with
 ``-ffp-contract=off`` so that the FP64 centre and width arithmetic rounds the same
 way on x86-64 and aarch64 hosts.
@@ -19,8 +19,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmarfa.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["marfa_api.cu", "marfa_kernels.cu"]
-DEPS = SOURCES + ["marfa_internal.cuh", "voigt.cuh", "voigt_tables.inc"]
+SOURCES = ["marfa_api.cu", "marfa_kernels.cu", "marfa_mlp.cu"]
+DEPS = SOURCES + ["marfa_internal.cuh", "mlp.cuh", "voigt.cuh", "voigt_tables.inc"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off", "-I", INCLUDE]
 

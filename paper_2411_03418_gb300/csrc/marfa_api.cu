@@ -11,6 +11,7 @@
 #include <cerrno>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -296,15 +297,34 @@ struct Plan {
   std::vector<LevelSpeciesDev> ls;
   ReqDev rd{};
   int64_t npts = 0;
+  int req_idx = 0;
   std::vector<G1Item> g1;
-  std::vector<CoarseItem> coarse;
   std::vector<FineItem> fine;
+  PrepArgs prep{};            // level-preparation launch, filled by upload()
   // device buffers
   void* dbuf = nullptr;       // per-level line data + slots + tables
   float* dout = nullptr;      // output (own buffer when the caller's is on the host)
   bool own_out = false;
   float* user_out = nullptr;
 };
+
+// ------------------------------------------------------------------ surrogate state
+// The loaded surrogate: inference weights and guard on one device.
+static std::mutex g_surr_mu;
+static int g_surr_dev = -1;
+static MlpWeights* g_surr_w = nullptr;
+
+static int surrogate_for_current_device(const MlpWeights** out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_surr_mu);
+  if (!g_surr_w) return fail(MARFA_E_INVAL, "surrogate requested but none is loaded (marfa_surrogate_load)");
+  if (g_surr_dev != dev)
+    return fail(MARFA_E_INVAL, "the surrogate is loaded on device %d, not on the current device %d",
+                g_surr_dev, dev);
+  *out = g_surr_w;
+  return MARFA_OK;
+}
 
 static int validate_request(const marfa_request_t* rq, int64_t* npts) {
   if (!rq) return fail(MARFA_E_INVAL, "request is NULL");
@@ -323,7 +343,9 @@ static int validate_request(const marfa_request_t* rq, int64_t* npts) {
     return fail(MARFA_E_INVAL, "unknown chi %d", rq->chi);
   if (rq->units < MARFA_UNITS_SIGMA || rq->units > MARFA_UNITS_K_KM1)
     return fail(MARFA_E_INVAL, "unknown units %d", rq->units);
-  if (rq->surrogate != 0) return fail(MARFA_E_INVAL, "surrogate must be 0");
+  if (rq->surrogate != 0 && rq->surrogate != 1) return fail(MARFA_E_INVAL, "surrogate must be 0 or 1");
+  if (rq->surrogate && rq->shape != MARFA_SHAPE_VOIGT)
+    return fail(MARFA_E_INVAL, "the surrogate stands in for the Voigt profile only");
   if (rq->R_w < 1 || rq->R_w > 64 || rq->R_c < 1 || rq->R_c > 64)
     return fail(MARFA_E_INVAL, "R_w and R_c must be in 1..64");
   *npts = np;
@@ -415,18 +437,20 @@ static int build_plan(Plan& P, const marfa_lines_t* L, const marfa_level_t* leve
   R.R_w = rq->R_w;
   R.shape = rq->shape;
   R.chi_req = rq->chi == MARFA_CHI_TONKOV ? 1 : 0;
+  R.mlp = nullptr;
+  if (rq->surrogate) {
+    r = surrogate_for_current_device(&R.mlp);
+    if (r) return r;
+  }
   R.out_scale = (float)(1.0 / scale);
   R.npts = P.npts;
   (void)physical;
-  // work lists: grid 1 in tiles of kG1Pairs pairs; grids 2..10 from coarse to fine
+  // work lists: grid 1 in tiles of kG1Pairs pairs and the finest grid in tiles of
+  // kFineTile nodes; grids 2..10 follow the kernel variant chosen per grid (coarse_items)
+  P.req_idx = req_idx;
   for (int l = 0; l < n_levels; ++l)
     for (int64_t m0 = R.m_first[1]; m0 <= R.m_first[1] + R.npan[1]; m0 += kG1Pairs)
       P.g1.push_back(G1Item{req_idx, l, m0});
-  for (int g = 2; g <= kNGrid; ++g)
-    for (int l = 0; l < n_levels; ++l)
-      for (int64_t m0 = R.m_first[g]; m0 <= R.m_first[g] + R.npan[g];
-           m0 += g <= kLastLM ? (int64_t)kLPairs : (int64_t)kCPairs * kCWarps)
-        P.coarse.push_back(CoarseItem{req_idx, l, g, 0, m0});
   const int64_t kb0 = R.k_lo & ~(int64_t)7;  // tiles start on a G10 panel
   for (int l = 0; l < n_levels; ++l)
     for (int64_t k0 = kb0; k0 <= R.k_hi; k0 += kFineTile) P.fine.push_back(FineItem{req_idx, l, k0});
@@ -442,8 +466,39 @@ static bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Kernel variants of grids 2..10: 0 = line-major (k_coarse_lm, kLPairs node pairs per
+// CTA), 1 = two-phase (k_coarse, kCWarps x kCPairs node pairs per CTA). Without tuning,
+// grids 2..kLastLM take the line-major kernel (few lines own a panel there, so a thread
+// per line wastes little) and the finer grids the two-phase one.
+static int default_variant(int g) { return g <= kLastLM ? 0 : 1; }
+static int64_t variant_pairs(int v) { return v == 0 ? (int64_t)kLPairs : (int64_t)kCPairs * kCWarps; }
+
+static void coarse_items(const Plan& P, int g, int v, std::vector<CoarseItem>& out) {
+  const ReqDev& R = P.rd;
+  for (int l = 0; l < P.n_levels; ++l)
+    for (int64_t m0 = R.m_first[g]; m0 <= R.m_first[g] + R.npan[g]; m0 += variant_pairs(v))
+      out.push_back(CoarseItem{P.req_idx, l, g, 0, m0});
+}
+
+static void launch_prep(const Plan& P, cudaStream_t st, bool timed) {
+  cudaEvent_t ev = timed ? timing_begin(st) : nullptr;
+  launch_level_prep(P.prep, (int)P.n_levels, st);
+  timing_end(ev, 0, st);
+}
+
+static int upload(Plan& P, float* k_out, cudaStream_t st);
+
 // Allocate the per-request device buffers of a plan and run the level preparation.
 static int upload_and_prep(Plan& P, float* k_out, cudaStream_t st) {
+  int r = upload(P, k_out, st);
+  if (r) return r;
+  launch_prep(P, st, true);
+  CK(cudaGetLastError());
+  return MARFA_OK;
+}
+
+// Allocate the per-request device buffers of a plan and copy its level tables.
+static int upload(Plan& P, float* k_out, cudaStream_t st) {
   const marfa_lines_t* L = P.lines;
   const int64_t n = L->n, nl = P.n_levels;
   const int ns = (int)L->species.size();
@@ -479,7 +534,7 @@ static int upload_and_prep(Plan& P, float* k_out, cudaStream_t st) {
     P.own_out = true;
   }
   R.out = P.dout;
-  PrepArgs a;
+  PrepArgs& a = P.prep;
   a.n = n;
   a.nu0 = L->nu0; a.S296 = L->S296; a.ga = L->ga; a.gs = L->gs; a.E = L->E; a.na = L->na; a.da = L->da;
   a.species = L->sp;
@@ -489,10 +544,6 @@ static int upload_and_prep(Plan& P, float* k_out, cudaStream_t st) {
   a.shape = P.rq.shape;
   a.R_c = P.rq.R_c;
   a.c = c; a.amp = amp; a.sx = sx; a.yv = yv; a.gstar = gst; a.flags = fl;
-  cudaEvent_t ev = timing_begin(st);
-  launch_level_prep(a, (int)nl, st);
-  timing_end(ev, 0, st);
-  CK(cudaGetLastError());
   return MARFA_OK;
 }
 
@@ -504,93 +555,162 @@ static void release(Plan& P, cudaStream_t st) {
 }
 
 // Run the coarse and finest-grid kernels for a set of prepared plans.
-static int run_plans(std::vector<Plan>& plans, cudaStream_t st, std::vector<int64_t>* coarse_counts,
-                     std::vector<int64_t>* fine_counts) {
+// ------------------------------------------------------------------ work sets
+// All launches of a set of prepared requests: the work lists of every kernel (grid 1,
+// grids 2..10 with their kernel variants, finest grid) and their device copies.
+struct WorkSet {
   std::vector<ReqDev> rds;
   std::vector<G1Item> gi;
-  std::vector<CoarseItem> ci;
+  std::vector<CoarseItem> ci[kNGrid + 1];  // grids 2..10
   std::vector<FineItem> fi;
-  for (auto& P : plans) rds.push_back(P.rd);
-  for (auto& P : plans) gi.insert(gi.end(), P.g1.begin(), P.g1.end());
-  // interleave the coarse lists grid by grid so that the heaviest CTAs start first
-  for (int g = 1; g <= kNGrid; ++g)
-    for (auto& P : plans)
-      for (auto& it : P.coarse)
-        if (it.grid == g) ci.push_back(it);
-  for (auto& P : plans) fi.insert(fi.end(), P.fine.begin(), P.fine.end());
-  if (gi.size() > 0x7fffffffu || ci.size() > 0x7fffffffu || fi.size() > 0x7fffffffu)
-    return fail(MARFA_E_INVAL, "too much work in one call");
-  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-  const size_t sz_r = al(sizeof(ReqDev) * rds.size()), sz_gi = al(sizeof(G1Item) * gi.size()),
-               sz_ci = al(sizeof(CoarseItem) * ci.size()), sz_fi = al(sizeof(FineItem) * fi.size());
-  const bool count = coarse_counts != nullptr;
-  const size_t sz_gc = count ? al(8 * gi.size()) : 0;
-  const size_t sz_cc = count ? al(8 * ci.size()) : 0, sz_fc = count ? al(8 * fi.size()) : 0;
+  int variant[kNGrid + 1] = {0};
+  bool surr = false;
+  size_t cw = 32;                          // count bytes per item (four int64)
   void* buf = nullptr;
-  int r = dev_alloc(&buf, sz_r + sz_gi + sz_ci + sz_fi + sz_gc + sz_cc + sz_fc, st);
+  ReqDev* drd = nullptr;
+  G1Item* dgi = nullptr;
+  CoarseItem* dci[kNGrid + 1] = {nullptr};
+  FineItem* dfi = nullptr;
+  int64_t* dgc = nullptr;
+  int64_t* dcc[kNGrid + 1] = {nullptr};
+  int64_t* dfc = nullptr;
+};
+
+static void free_work(WorkSet& W, cudaStream_t st) {
+  if (W.buf) cudaFreeAsync(W.buf, st);
+  W.buf = nullptr;
+}
+
+// Build the work lists of plans with kernel variant variant[g] for grid g (NULL: the
+// defaults), allocate their device copies (plus count buffers when count) and upload.
+static int build_work(std::vector<Plan>& plans, const int* variant, bool count, WorkSet& W,
+                      cudaStream_t st) {
+  for (auto& P : plans) W.rds.push_back(P.rd);
+  for (auto& R : W.rds) W.surr = W.surr || R.mlp != nullptr;
+  for (auto& P : plans) W.gi.insert(W.gi.end(), P.g1.begin(), P.g1.end());
+  for (int g = 2; g <= kNGrid; ++g) {
+    W.variant[g] = variant ? variant[g] : default_variant(g);
+    for (auto& P : plans) coarse_items(P, g, W.variant[g], W.ci[g]);
+  }
+  for (auto& P : plans) W.fi.insert(W.fi.end(), P.fine.begin(), P.fine.end());
+  size_t total_items = W.gi.size() + W.fi.size();
+  for (int g = 2; g <= kNGrid; ++g) total_items += W.ci[g].size();
+  if (W.gi.size() > 0x7fffffffu || W.fi.size() > 0x7fffffffu || total_items > ((size_t)1 << 34))
+    return fail(MARFA_E_INVAL, "too much work in one call");
+  for (int g = 2; g <= kNGrid; ++g)
+    if (W.ci[g].size() > 0x7fffffffu) return fail(MARFA_E_INVAL, "too much work in one call");
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t cw = count ? W.cw : 0;
+  size_t sz = al(sizeof(ReqDev) * W.rds.size()) + al(sizeof(G1Item) * W.gi.size()) +
+              al(sizeof(FineItem) * W.fi.size()) + al(cw * W.gi.size()) + al(cw * W.fi.size());
+  for (int g = 2; g <= kNGrid; ++g) sz += al(sizeof(CoarseItem) * W.ci[g].size()) + al(cw * W.ci[g].size());
+  int r = dev_alloc(&W.buf, sz, st);
   if (r) return r;
-  char* p = (char*)buf;
-  ReqDev* drd = (ReqDev*)p; p += sz_r;
-  G1Item* dgi = (G1Item*)p; p += sz_gi;
-  CoarseItem* dci = (CoarseItem*)p; p += sz_ci;
-  FineItem* dfi = (FineItem*)p; p += sz_fi;
-  int64_t* dgc = count ? (int64_t*)p : nullptr; p += sz_gc;
-  int64_t* dcc = count ? (int64_t*)p : nullptr; p += sz_cc;
-  int64_t* dfc = count ? (int64_t*)p : nullptr;
-  auto done = [&](int code) {
-    cudaFreeAsync(buf, st);
-    return code;
+  char* p = (char*)W.buf;
+  auto take = [&](size_t b) {
+    char* q = p;
+    p += al(b);
+    return q;
   };
-  cudaError_t e;
-  if ((e = cudaMemcpyAsync(drd, rds.data(), sizeof(ReqDev) * rds.size(), cudaMemcpyHostToDevice, st)) ||
-      (e = cudaMemcpyAsync(dgi, gi.data(), sizeof(G1Item) * gi.size(), cudaMemcpyHostToDevice, st)) ||
-      (e = cudaMemcpyAsync(dci, ci.data(), sizeof(CoarseItem) * ci.size(), cudaMemcpyHostToDevice, st)) ||
-      (e = cudaMemcpyAsync(dfi, fi.data(), sizeof(FineItem) * fi.size(), cudaMemcpyHostToDevice, st)))
-    return done(fail(MARFA_E_CUDA, "upload of work lists failed: %s", cudaGetErrorString(e)));
-  if (count && ((e = cudaMemsetAsync(dgc, 0, sz_gc, st)) || (e = cudaMemsetAsync(dcc, 0, sz_cc, st)) ||
-                (e = cudaMemsetAsync(dfc, 0, sz_fc, st))))
-    return done(fail(MARFA_E_CUDA, "count buffers: %s", cudaGetErrorString(e)));
-  cudaEvent_t ev = timing_begin(st);
-  launch_g1(drd, dgi, (int)gi.size(), dgc, st);
-  timing_end(ev, 1, st);
-  if ((e = cudaGetLastError())) return done(fail(MARFA_E_CUDA, "grid-1 kernel: %s", cudaGetErrorString(e)));
-  {
-    size_t k = 0;
-    for (int g = 2; g <= kNGrid; ++g) {  // ci is ordered by grid
-      size_t k1 = k;
-      while (k1 < ci.size() && ci[k1].grid == g) ++k1;
-      ev = timing_begin(st);
-      if (g <= kLastLM)
-        launch_coarse_lm(drd, dci + k, (int)(k1 - k), dcc ? dcc + k : nullptr, st);
-      else
-        launch_coarse(drd, dci + k, (int)(k1 - k), dcc ? dcc + k : nullptr, st);
-      timing_end(ev, g, st);
-      k = k1;
-    }
-  }
-  ev = timing_begin(st);
-  launch_fine(drd, dfi, (int)fi.size(), dfc, st);
-  timing_end(ev, kNGrid + 1, st);
-  if ((e = cudaGetLastError())) return done(fail(MARFA_E_CUDA, "fine kernel: %s", cudaGetErrorString(e)));
+  W.drd = (ReqDev*)take(sizeof(ReqDev) * W.rds.size());
+  W.dgi = (G1Item*)take(sizeof(G1Item) * W.gi.size());
+  W.dfi = (FineItem*)take(sizeof(FineItem) * W.fi.size());
+  for (int g = 2; g <= kNGrid; ++g) W.dci[g] = (CoarseItem*)take(sizeof(CoarseItem) * W.ci[g].size());
   if (count) {
-    std::vector<int64_t> hg(gi.size()), hc(ci.size()), hf(fi.size());
-    if ((e = cudaMemcpyAsync(hg.data(), dgc, 8 * hg.size(), cudaMemcpyDeviceToHost, st)) ||
-        (e = cudaMemcpyAsync(hc.data(), dcc, 8 * hc.size(), cudaMemcpyDeviceToHost, st)) ||
-        (e = cudaMemcpyAsync(hf.data(), dfc, 8 * hf.size(), cudaMemcpyDeviceToHost, st)) ||
-        (e = cudaStreamSynchronize(st)))
-      return done(fail(MARFA_E_CUDA, "count read-back failed: %s", cudaGetErrorString(e)));
-    // per (plan, level, grid)
-    for (size_t q = 0; q < plans.size(); ++q) {
-      coarse_counts[q].assign((size_t)plans[q].n_levels * 11, 0);
-    }
-    for (size_t k = 0; k < gi.size(); ++k) coarse_counts[gi[k].req][(size_t)gi[k].level * 11] += hg[k];
-    for (size_t k = 0; k < ci.size(); ++k)
-      coarse_counts[ci[k].req][(size_t)ci[k].level * 11 + ci[k].grid - 1] += hc[k];
-    for (size_t k = 0; k < fi.size(); ++k)
-      coarse_counts[fi[k].req][(size_t)fi[k].level * 11 + 10] += hf[k];
-    (void)fine_counts;
+    W.dgc = (int64_t*)take(cw * W.gi.size());
+    W.dfc = (int64_t*)take(cw * W.fi.size());
+    for (int g = 2; g <= kNGrid; ++g) W.dcc[g] = (int64_t*)take(cw * W.ci[g].size());
   }
-  return done(MARFA_OK);
+  cudaError_t e = cudaSuccess;
+  auto up = [&](void* d, const void* h, size_t b) {
+    if (!e && b) e = cudaMemcpyAsync(d, h, b, cudaMemcpyHostToDevice, st);
+  };
+  up(W.drd, W.rds.data(), sizeof(ReqDev) * W.rds.size());
+  up(W.dgi, W.gi.data(), sizeof(G1Item) * W.gi.size());
+  up(W.dfi, W.fi.data(), sizeof(FineItem) * W.fi.size());
+  for (int g = 2; g <= kNGrid; ++g) up(W.dci[g], W.ci[g].data(), sizeof(CoarseItem) * W.ci[g].size());
+  if (!e && count) {
+    e = cudaMemsetAsync(W.dgc, 0, cw * W.gi.size(), st);
+    if (!e) e = cudaMemsetAsync(W.dfc, 0, cw * W.fi.size(), st);
+    for (int g = 2; g <= kNGrid && !e; ++g) e = cudaMemsetAsync(W.dcc[g], 0, cw * W.ci[g].size(), st);
+  }
+  if (e) {
+    free_work(W, st);
+    return fail(MARFA_E_CUDA, "upload of work lists failed: %s", cudaGetErrorString(e));
+  }
+  return MARFA_OK;
+}
+
+// Grid g of a work set with kernel variant v.
+static void launch_grid(const WorkSet& W, int g, cudaStream_t st) {
+  const int n = (int)W.ci[g].size();
+  if (W.variant[g] == 0)
+    launch_coarse_lm(W.drd, W.dci[g], n, W.dcc[g], W.surr, st);
+  else
+    launch_coarse(W.drd, W.dci[g], n, W.dcc[g], W.surr, st);
+}
+
+// Every summation launch of a work set: grid 1, grids 2..10, finest grid + cascade.
+static int launch_work(const WorkSet& W, cudaStream_t st, bool timed) {
+  cudaEvent_t ev = timed ? timing_begin(st) : nullptr;
+  launch_g1(W.drd, W.dgi, (int)W.gi.size(), W.dgc, W.surr, st);
+  timing_end(ev, 1, st);
+  cudaError_t e;
+  if ((e = cudaGetLastError())) return fail(MARFA_E_CUDA, "grid-1 kernel: %s", cudaGetErrorString(e));
+  for (int g = 2; g <= kNGrid; ++g) {
+    ev = timed ? timing_begin(st) : nullptr;
+    launch_grid(W, g, st);
+    timing_end(ev, g, st);
+  }
+  if ((e = cudaGetLastError())) return fail(MARFA_E_CUDA, "coarse-grid kernel: %s", cudaGetErrorString(e));
+  ev = timed ? timing_begin(st) : nullptr;
+  launch_fine(W.drd, W.dfi, (int)W.fi.size(), W.dfc, W.surr, st);
+  timing_end(ev, kNGrid + 1, st);
+  if ((e = cudaGetLastError())) return fail(MARFA_E_CUDA, "fine kernel: %s", cudaGetErrorString(e));
+  return MARFA_OK;
+}
+
+// Read the count buffers of a work set (synchronises st): counts[q] receives, per level
+// of plan q and per grid (1..10, then the finest), four numbers: all profile evaluations,
+// those the surrogate took, plain Voigt evaluations in polynomial cells, and in the
+// asymptotic series ([n_levels][11][4]).
+static int read_counts(const WorkSet& W, std::vector<Plan>& plans, cudaStream_t st,
+                       std::vector<int64_t>* counts) {
+  std::vector<int64_t> hg(W.gi.size() * 4), hf(W.fi.size() * 4), hc[kNGrid + 1];
+  cudaError_t e = cudaSuccess;
+  auto down = [&](void* h, const void* d, size_t b) {
+    if (!e && b) e = cudaMemcpyAsync(h, d, b, cudaMemcpyDeviceToHost, st);
+  };
+  down(hg.data(), W.dgc, 8 * hg.size());
+  down(hf.data(), W.dfc, 8 * hf.size());
+  for (int g = 2; g <= kNGrid; ++g) {
+    hc[g].resize(W.ci[g].size() * 4);
+    down(hc[g].data(), W.dcc[g], 8 * hc[g].size());
+  }
+  if (!e) e = cudaStreamSynchronize(st);
+  if (e) return fail(MARFA_E_CUDA, "count read-back failed: %s", cudaGetErrorString(e));
+  for (size_t q = 0; q < plans.size(); ++q) counts[q].assign((size_t)plans[q].n_levels * 44, 0);
+  auto add = [&](int req, int level, int slot, const int64_t* v) {
+    int64_t* d = &counts[req][((size_t)level * 11 + slot) * 4];
+    for (int i = 0; i < 4; ++i) d[i] += v[i];
+  };
+  for (size_t k = 0; k < W.gi.size(); ++k) add(W.gi[k].req, W.gi[k].level, 0, &hg[k * 4]);
+  for (int g = 2; g <= kNGrid; ++g)
+    for (size_t k = 0; k < W.ci[g].size(); ++k) add(W.ci[g][k].req, W.ci[g][k].level, g - 1, &hc[g][k * 4]);
+  for (size_t k = 0; k < W.fi.size(); ++k) add(W.fi[k].req, W.fi[k].level, 10, &hf[k * 4]);
+  return MARFA_OK;
+}
+
+// Run the summation kernels for a set of prepared plans (default kernel variants);
+// counts (optional) as in read_counts.
+static int run_plans(std::vector<Plan>& plans, cudaStream_t st, std::vector<int64_t>* counts) {
+  WorkSet W;
+  int r = build_work(plans, nullptr, counts != nullptr, W, st);
+  if (r) return r;
+  r = launch_work(W, st, true);
+  if (!r && counts) r = read_counts(W, plans, st, counts);
+  free_work(W, st);
+  return r;
 }
 
 static int finish_outputs(std::vector<Plan>& plans, cudaStream_t st) {
@@ -625,7 +745,7 @@ static int absorption_impl(int32_t n_req, const marfa_lines_t* const* lines,
       return r;
     }
   }
-  int r = run_plans(plans, st, counts, nullptr);
+  int r = run_plans(plans, st, counts);
   if (r) {
     for (auto& P : plans) release(P, st);
     return r;
@@ -645,6 +765,197 @@ extern "C" int marfa_absorption_batch(int32_t n_req, const marfa_lines_t* const*
                                       const int32_t* n_levels, const marfa_request_t* rq,
                                       float* const* k_out, void* stream) {
   return absorption_impl(n_req, lines, levels, vmr, n_levels, rq, k_out, (cudaStream_t)stream, nullptr);
+}
+
+// ------------------------------------------------------------------ captured plans
+// A batch of requests prepared once and captured as one CUDA graph: level preparation
+// of every request, then grid 1, grids 2..10 and the finest grid over all requests.
+// Event-record nodes around each kernel kind give per-kernel times of the last replay.
+constexpr int kKinds = kNGrid + 2;
+
+struct marfa_plan {
+  int device = 0;
+  std::vector<Plan> plans;
+  WorkSet W;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t ev[2 * kKinds] = {nullptr};
+  float tune_ms[kNGrid + 1][2] = {};
+  bool tuned = false;
+  MlpWeights* mlp = nullptr;  // the plan's own copy of the surrogate (if any request uses it)
+};
+
+extern "C" void marfa_plan_destroy(marfa_plan_t* X) {
+  if (!X) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(X->device);
+  cudaDeviceSynchronize();
+  if (X->exec) cudaGraphExecDestroy(X->exec);
+  if (X->graph) cudaGraphDestroy(X->graph);
+  for (auto& e : X->ev)
+    if (e) cudaEventDestroy(e);
+  free_work(X->W, 0);
+  for (auto& P : X->plans) release(P, 0);
+  if (X->mlp) cudaFreeAsync(X->mlp, 0);
+  cudaDeviceSynchronize();
+  cudaSetDevice(cur);
+  delete X;
+}
+
+// Time grid g's launch with either kernel variant on the plan's own work (two timed
+// launches after one warm-up each) and keep the faster variant.
+static int plan_autotune(marfa_plan_t* X, cudaStream_t st, int* chosen) {
+  WorkSet A[2];
+  int all[2][kNGrid + 1];
+  for (int g = 0; g <= kNGrid; ++g) {
+    all[0][g] = 0;
+    all[1][g] = 1;
+  }
+  int r = build_work(X->plans, all[0], false, A[0], st);
+  if (!r) r = build_work(X->plans, all[1], false, A[1], st);
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (!r && ((e = cudaEventCreate(&a)) || (e = cudaEventCreate(&b))))
+    r = fail(MARFA_E_CUDA, "autotune events: %s", cudaGetErrorString(e));
+  for (int g = 2; g <= kNGrid && !r; ++g) {
+    for (int v = 0; v < 2 && !r; ++v) {
+      launch_grid(A[v], g, st);
+      cudaEventRecord(a, st);
+      launch_grid(A[v], g, st);
+      launch_grid(A[v], g, st);
+      cudaEventRecord(b, st);
+      float ms = 0;
+      if ((e = cudaEventSynchronize(b)) || (e = cudaEventElapsedTime(&ms, a, b)))
+        r = fail(MARFA_E_CUDA, "autotune of grid %d: %s", g, cudaGetErrorString(e));
+      X->tune_ms[g][v] = 0.5f * ms;
+    }
+    chosen[g] = X->tune_ms[g][0] <= X->tune_ms[g][1] ? 0 : 1;
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  free_work(A[0], st);
+  free_work(A[1], st);
+  X->tuned = !r;
+  return r;
+}
+
+static int plan_launch_all(marfa_plan_t* X, cudaStream_t st, bool events) {
+  if (events) cudaEventRecord(X->ev[0], st);
+  for (auto& P : X->plans) launch_prep(P, st, false);
+  if (events) cudaEventRecord(X->ev[1], st);
+  const WorkSet& W = X->W;
+  if (events) cudaEventRecord(X->ev[2], st);
+  launch_g1(W.drd, W.dgi, (int)W.gi.size(), nullptr, W.surr, st);
+  if (events) cudaEventRecord(X->ev[3], st);
+  for (int g = 2; g <= kNGrid; ++g) {
+    if (events) cudaEventRecord(X->ev[2 * g], st);
+    launch_grid(W, g, st);
+    if (events) cudaEventRecord(X->ev[2 * g + 1], st);
+  }
+  if (events) cudaEventRecord(X->ev[2 * (kNGrid + 1)], st);
+  launch_fine(W.drd, W.dfi, (int)W.fi.size(), nullptr, W.surr, st);
+  if (events) cudaEventRecord(X->ev[2 * (kNGrid + 1) + 1], st);
+  cudaError_t e = cudaGetLastError();
+  if (e) return fail(MARFA_E_CUDA, "plan launches: %s", cudaGetErrorString(e));
+  return MARFA_OK;
+}
+
+extern "C" int marfa_plan_create(int32_t n_req, const marfa_lines_t* const* lines,
+                                 const marfa_level_t* const* levels, const double* const* vmr,
+                                 const int32_t* n_levels, const marfa_request_t* rq, float* const* k_out,
+                                 int32_t autotune, void* stream, marfa_plan_t** out) {
+  if (!out) return fail(MARFA_E_INVAL, "out is NULL");
+  *out = nullptr;
+  if (n_req < 1 || !lines || !levels || !vmr || !n_levels || !rq || !k_out)
+    return fail(MARFA_E_INVAL, "bad batch arguments");
+  for (int q = 0; q < n_req; ++q)
+    if (!k_out[q] || !is_device_ptr(k_out[q]))
+      return fail(MARFA_E_INVAL, "k_out[%d] must be device memory for a captured plan", q);
+  cudaStream_t st = (cudaStream_t)stream;
+  marfa_plan_t* X = new (std::nothrow) marfa_plan_t();
+  if (!X) return fail(MARFA_E_NOMEM, "host allocation failed");
+  cudaGetDevice(&X->device);
+  X->plans.resize(n_req);
+  int r = MARFA_OK;
+  for (int q = 0; q < n_req && !r; ++q) r = build_plan(X->plans[q], lines[q], levels[q], vmr[q], n_levels[q], &rq[q], q);
+  for (int q = 0; q < n_req && !r; ++q) r = upload(X->plans[q], k_out[q], st);
+  // requests with the surrogate use the plan's own copy of its weights and guard, so that
+  // the plan does not depend on what is loaded later
+  const MlpWeights* src = nullptr;
+  for (auto& P : X->plans)
+    if (P.rd.mlp) src = P.rd.mlp;
+  if (!r && src) {
+    r = dev_alloc((void**)&X->mlp, sizeof(MlpWeights), st);
+    cudaError_t e2;
+    if (!r && (e2 = cudaMemcpyAsync(X->mlp, src, sizeof(MlpWeights), cudaMemcpyDeviceToDevice, st)))
+      r = fail(MARFA_E_CUDA, "surrogate copy: %s", cudaGetErrorString(e2));
+    for (auto& P : X->plans)
+      if (P.rd.mlp) P.rd.mlp = X->mlp;
+  }
+  int chosen[kNGrid + 1];
+  for (int g = 0; g <= kNGrid; ++g) chosen[g] = default_variant(g);
+  if (!r && autotune) {
+    for (auto& P : X->plans) launch_prep(P, st, false);
+    r = plan_autotune(X, st, chosen);
+  }
+  if (!r) r = build_work(X->plans, chosen, false, X->W, st);
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 2 * kKinds && !r; ++k)
+    if ((e = cudaEventCreate(&X->ev[k]))) r = fail(MARFA_E_CUDA, "plan events: %s", cudaGetErrorString(e));
+  // one ordinary run first: checks every launch outside capture and leaves the output valid
+  if (!r) r = plan_launch_all(X, st, false);
+  if (!r && (e = cudaStreamSynchronize(st))) r = fail(MARFA_E_CUDA, "plan run: %s", cudaGetErrorString(e));
+  cudaStream_t cs = nullptr;
+  if (!r && (e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)))
+    r = fail(MARFA_E_CUDA, "capture stream: %s", cudaGetErrorString(e));
+  if (!r) {
+    if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal))) {
+      r = fail(MARFA_E_CUDA, "begin capture: %s", cudaGetErrorString(e));
+    } else {
+      const int r2 = plan_launch_all(X, cs, true);
+      e = cudaStreamEndCapture(cs, &X->graph);
+      if (r2) r = r2;
+      else if (e) r = fail(MARFA_E_CUDA, "end capture: %s", cudaGetErrorString(e));
+      else if ((e = cudaGraphInstantiate(&X->exec, X->graph, 0)))
+        r = fail(MARFA_E_CUDA, "graph instantiation: %s", cudaGetErrorString(e));
+    }
+  }
+  if (cs) cudaStreamDestroy(cs);
+  if (r) {
+    marfa_plan_destroy(X);
+    return r;
+  }
+  *out = X;
+  return MARFA_OK;
+}
+
+extern "C" int marfa_plan_execute(marfa_plan_t* X, void* stream) {
+  if (!X || !X->exec) return fail(MARFA_E_INVAL, "plan is NULL");
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev != X->device) return fail(MARFA_E_INVAL, "plan belongs to device %d, current is %d", X->device, dev);
+  CK(cudaGraphLaunch(X->exec, (cudaStream_t)stream));
+  return MARFA_OK;
+}
+
+extern "C" int marfa_plan_info(const marfa_plan_t* X, int32_t* variant, float* tune_ms, double* kernel_ms) {
+  if (!X) return fail(MARFA_E_INVAL, "plan is NULL");
+  if (variant)
+    for (int g = 1; g <= kNGrid; ++g) variant[g - 1] = g == 1 ? -1 : X->W.variant[g];
+  if (tune_ms)
+    for (int g = 1; g <= kNGrid; ++g)
+      for (int v = 0; v < 2; ++v) tune_ms[2 * (g - 1) + v] = (X->tuned && g > 1) ? X->tune_ms[g][v] : -1.0f;
+  if (kernel_ms) {
+    for (int k = 0; k < kKinds; ++k) {
+      float ms = 0;
+      cudaError_t e;
+      if ((e = cudaEventSynchronize(X->ev[2 * k + 1])) || (e = cudaEventElapsedTime(&ms, X->ev[2 * k], X->ev[2 * k + 1])))
+        return fail(MARFA_E_CUDA, "plan kernel times: %s", cudaGetErrorString(e));
+      kernel_ms[k] = ms;
+    }
+  }
+  return MARFA_OK;
 }
 
 // ------------------------------------------------------------------ PT-table (Appendix A)
@@ -734,8 +1045,10 @@ extern "C" int marfa_absorption_noalloc(const marfa_lines_t* lines, const marfa_
   const size_t sz_c = al(8 * pairs), sz_f = al(4 * pairs), sz_b = al(pairs);
   const size_t sz_slots = al(4 * (size_t)P.rd.slots_per_level * nl);
   const size_t sz_lev = al(sizeof(LevelDev) * nl), sz_ls = al(sizeof(LevelSpeciesDev) * nl * ns);
+  std::vector<CoarseItem> coarse;  // grids 2..10 in order, default kernel variants
+  for (int g = 2; g <= kNGrid; ++g) coarse_items(P, g, default_variant(g), coarse);
   const size_t sz_r = al(sizeof(ReqDev)), sz_gi = al(sizeof(G1Item) * P.g1.size()),
-               sz_ci = al(sizeof(CoarseItem) * P.coarse.size()), sz_fi = al(sizeof(FineItem) * P.fine.size());
+               sz_ci = al(sizeof(CoarseItem) * coarse.size()), sz_fi = al(sizeof(FineItem) * P.fine.size());
   const size_t total = sz_c + 3 * sz_f + 2 * sz_b + sz_slots + sz_lev + sz_ls + sz_r + sz_gi + sz_ci + sz_fi;
   if (total > kNoAllocBytes)
     return fail(MARFA_E_INVAL, "request needs %zu bytes of scratch; marfa_absorption_noalloc holds %zu",
@@ -763,7 +1076,7 @@ extern "C" int marfa_absorption_noalloc(const marfa_lines_t* lines, const marfa_
   CK(cudaMemcpyAsync(dls, P.ls.data(), sizeof(LevelSpeciesDev) * nl * ns, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(drd, &R, sizeof(ReqDev), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(dgi, P.g1.data(), sizeof(G1Item) * P.g1.size(), cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(dci, P.coarse.data(), sizeof(CoarseItem) * P.coarse.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dci, coarse.data(), sizeof(CoarseItem) * coarse.size(), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(dfi, P.fine.data(), sizeof(FineItem) * P.fine.size(), cudaMemcpyHostToDevice, st));
   PrepArgs a;
   a.n = n;
@@ -778,18 +1091,19 @@ extern "C" int marfa_absorption_noalloc(const marfa_lines_t* lines, const marfa_
   // Every slot and per-level value is written by these kernels before it is read, so
   // nothing left in the scratch by an earlier call needs clearing.
   launch_level_prep(a, (int)nl, st);
-  launch_g1(drd, dgi, (int)P.g1.size(), nullptr, st);
+  const bool surr = R.mlp != nullptr;
+  launch_g1(drd, dgi, (int)P.g1.size(), nullptr, surr, st);
   size_t k = 0;
-  for (int g = 2; g <= kNGrid; ++g) {  // P.coarse is ordered by grid
+  for (int g = 2; g <= kNGrid; ++g) {  // coarse is ordered by grid
     size_t k1 = k;
-    while (k1 < P.coarse.size() && P.coarse[k1].grid == g) ++k1;
-    if (g <= kLastLM)
-      launch_coarse_lm(drd, dci + k, (int)(k1 - k), nullptr, st);
+    while (k1 < coarse.size() && coarse[k1].grid == g) ++k1;
+    if (default_variant(g) == 0)
+      launch_coarse_lm(drd, dci + k, (int)(k1 - k), nullptr, surr, st);
     else
-      launch_coarse(drd, dci + k, (int)(k1 - k), nullptr, st);
+      launch_coarse(drd, dci + k, (int)(k1 - k), nullptr, surr, st);
     k = k1;
   }
-  launch_fine(drd, dfi, (int)P.fine.size(), nullptr, st);
+  launch_fine(drd, dfi, (int)P.fine.size(), nullptr, surr, st);
   CK(cudaGetLastError());
   return MARFA_OK;
 }
@@ -874,9 +1188,9 @@ extern "C" int marfa_diag_owned(const marfa_lines_t* lines, const marfa_level_t*
   return MARFA_OK;
 }
 
-extern "C" int marfa_diag_absorption_counted(const marfa_lines_t* lines, const marfa_level_t* levels,
-                                             const double* vmr, int32_t n_levels,
-                                             const marfa_request_t* rq, float* k_out, int64_t* counts) {
+extern "C" int marfa_diag_absorption_counts(const marfa_lines_t* lines, const marfa_level_t* levels,
+                                            const double* vmr, int32_t n_levels, const marfa_request_t* rq,
+                                            float* k_out, int64_t* counts) {
   if (!counts) return fail(MARFA_E_INVAL, "counts is NULL");
   std::vector<int64_t> cc[1];
   float* outs[1] = {k_out};
@@ -884,5 +1198,235 @@ extern "C" int marfa_diag_absorption_counted(const marfa_lines_t* lines, const m
   if (r) return r;
   std::copy(cc[0].begin(), cc[0].end(), counts);
   CK(cudaDeviceSynchronize());
+  return MARFA_OK;
+}
+
+extern "C" int marfa_diag_absorption_counted(const marfa_lines_t* lines, const marfa_level_t* levels,
+                                             const double* vmr, int32_t n_levels,
+                                             const marfa_request_t* rq, float* k_out, int64_t* counts) {
+  if (!counts) return fail(MARFA_E_INVAL, "counts is NULL");
+  if (n_levels < 1 || n_levels > 65535) return fail(MARFA_E_INVAL, "need 1..65535 levels");
+  std::vector<int64_t> c4((size_t)n_levels * 44);
+  int r = marfa_diag_absorption_counts(lines, levels, vmr, n_levels, rq, k_out, c4.data());
+  if (r) return r;
+  for (size_t i = 0; i < (size_t)n_levels * 11; ++i) counts[i] = c4[4 * i];
+  return MARFA_OK;
+}
+
+extern "C" int marfa_diag_absorption_counted_surrogate(const marfa_lines_t* lines,
+                                                       const marfa_level_t* levels, const double* vmr,
+                                                       int32_t n_levels, const marfa_request_t* rq,
+                                                       float* k_out, int64_t* counts,
+                                                       int64_t* surrogate_counts) {
+  if (!counts || !surrogate_counts) return fail(MARFA_E_INVAL, "counts is NULL");
+  if (n_levels < 1 || n_levels > 65535) return fail(MARFA_E_INVAL, "need 1..65535 levels");
+  std::vector<int64_t> c4((size_t)n_levels * 44);
+  int r = marfa_diag_absorption_counts(lines, levels, vmr, n_levels, rq, k_out, c4.data());
+  if (r) return r;
+  for (size_t i = 0; i < (size_t)n_levels * 11; ++i) {
+    counts[i] = c4[4 * i];
+    surrogate_counts[i] = c4[4 * i + 1];
+  }
+  return MARFA_OK;
+}
+
+// ------------------------------------------------------------------ surrogate: training
+namespace {
+// Device buffers of one training or gradient call, freed on every exit path.
+struct MlpBufs {
+  float *p = nullptr, *m = nullptr, *v = nullptr, *g = nullptr, *part = nullptr, *lp = nullptr;
+  float *x = nullptr, *y = nullptr, *t = nullptr, *loss = nullptr;
+  ~MlpBufs() {
+    for (float* q : {p, m, v, g, part, lp, x, y, t, loss})
+      if (q) cudaFree(q);
+  }
+};
+}  // namespace
+
+static int mlp_check_samples(const float* x, const float* y, const float* t, int64_t n) {
+  if (!x || !y || !t || n < 1) return fail(MARFA_E_INVAL, "need n >= 1 samples (x, y, t)");
+  for (int64_t i = 0; i < n; ++i)
+    if (!std::isfinite(x[i]) || !(y[i] > 0) || !std::isfinite(y[i]) || !std::isfinite(t[i]))
+      return fail(MARFA_E_INVAL, "sample %lld: x, t must be finite and y finite and > 0", (long long)i);
+  return MARFA_OK;
+}
+
+static int mlp_upload(MlpBufs& B, const float* params, const float* x, const float* y, const float* t,
+                      int64_t n, int max_batch) {
+  const int tile = mlp_train_tile();
+  const int nblk = (max_batch + tile - 1) / tile;
+  cudaError_t e;
+  if ((e = cudaMalloc(&B.p, 4 * kMlpParams)) || (e = cudaMalloc(&B.m, 4 * kMlpParams)) ||
+      (e = cudaMalloc(&B.v, 4 * kMlpParams)) || (e = cudaMalloc(&B.g, 4 * kMlpParams)) ||
+      (e = cudaMalloc(&B.part, 4 * (size_t)nblk * kMlpParams)) ||
+      (e = cudaMalloc(&B.lp, 4 * (size_t)nblk * tile)) || (e = cudaMalloc(&B.x, 4 * (size_t)n)) ||
+      (e = cudaMalloc(&B.y, 4 * (size_t)n)) || (e = cudaMalloc(&B.t, 4 * (size_t)n)))
+    return fail(MARFA_E_NOMEM, "surrogate training buffers: %s", cudaGetErrorString(e));
+  if ((e = cudaMemcpy(B.p, params, 4 * kMlpParams, cudaMemcpyHostToDevice)) ||
+      (e = cudaMemset(B.m, 0, 4 * kMlpParams)) || (e = cudaMemset(B.v, 0, 4 * kMlpParams)) ||
+      (e = cudaMemcpy(B.x, x, 4 * (size_t)n, cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(B.y, y, 4 * (size_t)n, cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(B.t, t, 4 * (size_t)n, cudaMemcpyHostToDevice)))
+    return fail(MARFA_E_CUDA, "surrogate upload: %s", cudaGetErrorString(e));
+  return MARFA_OK;
+}
+
+extern "C" int marfa_mlp_loss_grad(const float* params, const float* x, const float* y, const float* t,
+                                   int64_t n, int32_t qat, double* loss, float* grad) {
+  if (!params || !loss || !grad) return fail(MARFA_E_INVAL, "params, loss and grad must not be NULL");
+  if (n > MARFA_MLP_MAX_BATCH) return fail(MARFA_E_INVAL, "at most %d samples", MARFA_MLP_MAX_BATCH);
+  int r = mlp_check_samples(x, y, t, n);
+  if (r) return r;
+  MlpBufs B;
+  r = mlp_upload(B, params, x, y, t, n, (int)n);
+  if (r) return r;
+  const int tile = mlp_train_tile();
+  const int nblk = (int)((n + tile - 1) / tile);
+  launch_mlp_fwd_bwd(B.p, B.x, B.y, B.t, n, 0, nblk, (float)(1.0 / (double)n), qat != 0, B.part, B.lp, 0);
+  launch_mlp_reduce(B.part, nblk, B.g, 0);
+  CK(cudaGetLastError());
+  std::vector<float> lp((size_t)nblk * tile);
+  cudaError_t e;
+  if ((e = cudaMemcpy(grad, B.g, 4 * kMlpParams, cudaMemcpyDeviceToHost)) ||
+      (e = cudaMemcpy(lp.data(), B.lp, 4 * lp.size(), cudaMemcpyDeviceToHost)))
+    return fail(MARFA_E_CUDA, "surrogate gradient: %s", cudaGetErrorString(e));
+  double sum = 0.0;
+  for (int64_t i = 0; i < n; ++i) sum += lp[(size_t)i];
+  *loss = sum / (double)n;
+  return MARFA_OK;
+}
+
+extern "C" int marfa_mlp_train(float* params, const float* x, const float* y, const float* t, int64_t n,
+                               const marfa_mlp_train_t* cfg, float* loss_curve) {
+  if (!params || !cfg) return fail(MARFA_E_INVAL, "params and cfg must not be NULL");
+  if (cfg->steps < 1 || cfg->batch < 1 || cfg->batch > MARFA_MLP_MAX_BATCH)
+    return fail(MARFA_E_INVAL, "need steps >= 1 and 1 <= batch <= %d", MARFA_MLP_MAX_BATCH);
+  if (!(cfg->lr0 > 0) || !(cfg->lr1 > 0) || !std::isfinite(cfg->lr0) || !std::isfinite(cfg->lr1))
+    return fail(MARFA_E_INVAL, "learning rates must be finite and > 0");
+  for (int i = 0; i < kMlpParams; ++i)
+    if (!std::isfinite(params[i])) return fail(MARFA_E_INVAL, "parameter %d is not finite", i);
+  int r = mlp_check_samples(x, y, t, n);
+  if (r) return r;
+  MlpBufs B;
+  r = mlp_upload(B, params, x, y, t, n, cfg->batch);
+  if (r) return r;
+  cudaError_t e;
+  if ((e = cudaMalloc(&B.loss, 4 * (size_t)cfg->steps)))
+    return fail(MARFA_E_NOMEM, "loss curve: %s", cudaGetErrorString(e));
+  const int tile = mlp_train_tile();
+  const double kPi = 3.14159265358979323846;
+  double b1t = 1.0, b2t = 1.0;
+  int64_t first = 0;
+  for (int k = 0; k < cfg->steps; ++k) {
+    const int64_t nb = std::min<int64_t>(cfg->batch, n - first);
+    const int nblk = (int)((nb + tile - 1) / tile);
+    const double lr = cfg->lr1 + 0.5 * (cfg->lr0 - cfg->lr1) * (1.0 + std::cos(kPi * k / cfg->steps));
+    b1t *= 0.9;
+    b2t *= 0.999;
+    launch_mlp_fwd_bwd(B.p, B.x, B.y, B.t, first + nb, first, nblk, (float)(1.0 / (double)nb), cfg->qat != 0,
+                       B.part, B.lp, 0);
+    launch_mlp_reduce(B.part, nblk, B.g, 0);
+    launch_mlp_adam(B.p, B.g, B.m, B.v, (float)lr, (float)b1t, (float)b2t, 0);
+    launch_mlp_loss_sum(B.lp, nblk * tile, (float)(1.0 / (double)nb), B.loss + k, 0);
+    first += nb;
+    if (first >= n) first = 0;
+  }
+  CK(cudaGetLastError());
+  if ((e = cudaMemcpy(params, B.p, 4 * kMlpParams, cudaMemcpyDeviceToHost)) ||
+      (loss_curve && (e = cudaMemcpy(loss_curve, B.loss, 4 * (size_t)cfg->steps, cudaMemcpyDeviceToHost))))
+    return fail(MARFA_E_CUDA, "surrogate training: %s", cudaGetErrorString(e));
+  return MARFA_OK;
+}
+
+// ------------------------------------------------------------------ surrogate: inference
+extern "C" int marfa_surrogate_load(const float* params, float budget, int32_t samples,
+                                    int32_t* cells_on, float* cell_err) {
+  if (!params) return fail(MARFA_E_INVAL, "params must not be NULL");
+  if (!(budget > 0) || !(budget < 1)) return fail(MARFA_E_INVAL, "budget must be in (0, 1)");
+  if (samples < 2 || samples > 64) return fail(MARFA_E_INVAL, "samples must be in 2..64");
+  for (int i = 0; i < kMlpParams; ++i)
+    if (!std::isfinite(params[i])) return fail(MARFA_E_INVAL, "parameter %d is not finite", i);
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_surr_mu);
+  if (g_surr_w) {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(g_surr_dev);
+    cudaFree(g_surr_w);
+    cudaSetDevice(cur);
+    g_surr_w = nullptr;
+    g_surr_dev = -1;
+  }
+  MlpWeights* w = nullptr;
+  float *dp = nullptr, *derr = nullptr;
+  const int cells = kGuardNx * kGuardNy;
+  cudaError_t e;
+  if ((e = cudaMalloc(&w, sizeof(MlpWeights))) || (e = cudaMalloc(&dp, 4 * kMlpParams)) ||
+      (e = cudaMalloc(&derr, 4 * cells))) {
+    cudaFree(w);
+    cudaFree(dp);
+    cudaFree(derr);
+    return fail(MARFA_E_NOMEM, "surrogate weights: %s", cudaGetErrorString(e));
+  }
+  std::vector<uint32_t> bits(kGuardWords);
+  std::vector<float> err(cells);
+  if (!(e = cudaMemcpy(dp, params, 4 * kMlpParams, cudaMemcpyHostToDevice))) {
+    launch_mlp_pack(dp, w, 0);
+    launch_mlp_guard(w, budget, samples, derr, 0);
+    if (!(e = cudaGetLastError()) &&
+        !(e = cudaMemcpy(bits.data(), (const char*)w + offsetof(MlpWeights, guard), 4 * kGuardWords,
+                         cudaMemcpyDeviceToHost)))
+      e = cudaMemcpy(err.data(), derr, 4 * cells, cudaMemcpyDeviceToHost);
+  }
+  cudaFree(dp);
+  cudaFree(derr);
+  if (e) {
+    cudaFree(w);
+    return fail(MARFA_E_CUDA, "surrogate load: %s", cudaGetErrorString(e));
+  }
+  int on = 0;
+  for (uint32_t b : bits) on += __builtin_popcount(b);
+  if (cells_on) *cells_on = on;
+  if (cell_err) std::copy(err.begin(), err.end(), cell_err);
+  g_surr_w = w;
+  g_surr_dev = dev;
+  return MARFA_OK;
+}
+
+extern "C" int marfa_surrogate_unload(void) {
+  std::lock_guard<std::mutex> lk(g_surr_mu);
+  if (g_surr_w) {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(g_surr_dev);
+    cudaError_t e = cudaFree(g_surr_w);
+    cudaSetDevice(cur);
+    g_surr_w = nullptr;
+    g_surr_dev = -1;
+    if (e) return fail(MARFA_E_CUDA, "surrogate unload: %s", cudaGetErrorString(e));
+  }
+  return MARFA_OK;
+}
+
+extern "C" int marfa_surrogate_eval(const float* x, const float* y, float* out, int64_t n, int32_t guarded) {
+  if (n < 0 || (n > 0 && (!x || !y || !out))) return fail(MARFA_E_INVAL, "bad arguments");
+  for (int64_t i = 0; i < n; ++i)
+    if (!std::isfinite(x[i]) || !(y[i] > 0) || !std::isfinite(y[i]))
+      return fail(MARFA_E_INVAL, "point %lld: x must be finite and y finite and > 0", (long long)i);
+  const MlpWeights* w = nullptr;
+  int r = surrogate_for_current_device(&w);
+  if (r) return r;
+  if (n == 0) return MARFA_OK;
+  float* d = nullptr;
+  CK(cudaMalloc(&d, 12 * (size_t)n));
+  cudaError_t e;
+  if (!(e = cudaMemcpy(d, x, 4 * (size_t)n, cudaMemcpyHostToDevice)) &&
+      !(e = cudaMemcpy(d + n, y, 4 * (size_t)n, cudaMemcpyHostToDevice))) {
+    launch_mlp_eval(w, d, d + n, d + 2 * n, n, guarded != 0, 0);
+    if (!(e = cudaGetLastError())) e = cudaMemcpy(out, d + 2 * n, 4 * (size_t)n, cudaMemcpyDeviceToHost);
+  }
+  cudaFree(d);
+  if (e) return fail(MARFA_E_CUDA, "surrogate eval: %s", cudaGetErrorString(e));
   return MARFA_OK;
 }

@@ -1,5 +1,6 @@
-// Internal layouts shared by the host runtime (marfa_api.cu) and the kernels
-// (marfa_kernels.cu) of libmarfa. Not part of the C-ABI.
+// Internal layouts shared by the host runtime (marfa_api.cu), the profile kernels
+// (marfa_kernels.cu) and the surrogate kernels (marfa_mlp.cu) of libmarfa. Not part of
+// the C-ABI.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -45,6 +46,30 @@ struct LevelSpeciesDev {
   int32_t chi;    // chi-factor applies (request chi on, species flag, physical shape)
 };
 
+// ------------------------------------------------------------------ Voigt surrogate
+// The 2-64-64-64-1 SiLU network (not part of the paper). Training parameters are FP32,
+// packed W1[64][2], b1, W2[64][64], b2, W3[64][64], b3, W4[64], b4 (W row-major
+// [out][in]); inference weights keep W2 and W3 in BF16 with rows padded to kWStride.
+constexpr int kMlpH = 64;
+constexpr int kMlpParams = 8577;
+constexpr int kMlpOffW1 = 0, kMlpOffB1 = 128, kMlpOffW2 = 192, kMlpOffB2 = 4288,
+              kMlpOffW3 = 4352, kMlpOffB3 = 8448, kMlpOffW4 = 8512, kMlpOffB4 = 8576;
+constexpr int kWStride = 72;  // BF16 row stride: conflict-free B-fragment loads
+// Guard cells: |x| in [0, 12) by 1/8; y by binary exponent e in [-14, 3] and the two
+// leading mantissa bits.
+constexpr int kGuardNx = 96, kGuardNy = 72;
+constexpr int kGuardWords = kGuardNx * kGuardNy / 32;
+
+struct __align__(16) MlpWeights {
+  float w1[2 * kMlpH];
+  float b1[kMlpH], b2[kMlpH], b3[kMlpH], w4[kMlpH];
+  float b4, pad[3];
+  uint16_t w2[kMlpH * kWStride];  // BF16 bits
+  uint16_t w3[kMlpH * kWStride];
+  uint32_t guard[kGuardWords];    // bit c: surrogate allowed in guard cell c
+};
+static_assert(sizeof(MlpWeights) % 16 == 0, "MlpWeights is copied in 16-byte words");
+
 // One request as the kernels see it.
 struct ReqDev {
   // prepared lines (sorted by nu0)
@@ -74,6 +99,7 @@ struct ReqDev {
   int32_t R_w;
   int32_t shape;
   int32_t chi_req;          // request asks for the chi-factor
+  const MlpWeights* mlp;    // surrogate weights and guard, null for the plain path
   float out_scale;          // inverse internal scale
   float* out;               // [n_levels][npts]
   int64_t npts;
@@ -124,18 +150,37 @@ struct PrepArgs {
   uint8_t* flags;
 };
 
-// kernels (marfa_kernels.cu)
+// kernels (marfa_kernels.cu). With surr set, the surrogate-capable variants run (requests
+// with mlp != null use the surrogate under its guard). counts, when given, selects the
+// counting variants and receives four entries per item: all profile evaluations, those
+// the surrogate took, and the plain Voigt evaluations in polynomial cells and in the
+// asymptotic series (voigt_class 2 and 1).
 void launch_level_prep(const PrepArgs& a, int n_levels, cudaStream_t st);
-void launch_g1(const ReqDev* reqs, const G1Item* items, int n_items, int64_t* counts,
+void launch_g1(const ReqDev* reqs, const G1Item* items, int n_items, int64_t* counts, bool surr,
                cudaStream_t st);
 void launch_coarse(const ReqDev* reqs, const CoarseItem* items, int n_items, int64_t* counts,
-                   cudaStream_t st);
+                   bool surr, cudaStream_t st);
 void launch_coarse_lm(const ReqDev* reqs, const CoarseItem* items, int n_items, int64_t* counts,
-                      cudaStream_t st);
-void launch_fine(const ReqDev* reqs, const FineItem* items, int n_items, int64_t* counts,
+                      bool surr, cudaStream_t st);
+void launch_fine(const ReqDev* reqs, const FineItem* items, int n_items, int64_t* counts, bool surr,
                  cudaStream_t st);
 void launch_diag_voigt(const float* x, const float* y, float* out, int64_t n, cudaStream_t st);
 void launch_diag_owned(const ReqDev* req, int64_t n_lines, int level, int grid, int64_t first,
                        int count, uint8_t* out, cudaStream_t st);
+
+
+// surrogate kernels (marfa_mlp.cu)
+void launch_mlp_fwd_bwd(const float* params, const float* x, const float* y, const float* t,
+                        int64_t n, int64_t first, int nblk, float inv_batch, bool qat, float* part,
+                        float* loss_part, cudaStream_t st);
+int mlp_train_tile();
+void launch_mlp_reduce(const float* part, int nblk, float* grad, cudaStream_t st);
+void launch_mlp_loss_sum(const float* lp, int n, float inv, float* out, cudaStream_t st);
+void launch_mlp_adam(float* p, const float* g, float* m, float* v, float lr, float b1t, float b2t,
+                     cudaStream_t st);
+void launch_mlp_pack(const float* p, MlpWeights* out, cudaStream_t st);
+void launch_mlp_guard(MlpWeights* w, float budget, int samples, float* cell_err, cudaStream_t st);
+void launch_mlp_eval(const MlpWeights* w, const float* x, const float* y, float* out, int64_t n,
+                     bool guarded, cudaStream_t st);
 
 }  // namespace marfa

@@ -15,6 +15,7 @@
 #include <cstdio>
 
 #include "marfa_internal.cuh"
+#include "mlp.cuh"
 #include "voigt.cuh"
 
 namespace marfa {
@@ -254,6 +255,48 @@ __device__ __forceinline__ float shape_f(int shape, float x, float y) {
   }
 }
 
+// Per-CTA evaluation counts, four per block: counts[4b] all profile evaluations,
+// counts[4b + 1] those the surrogate took, counts[4b + 2] and [4b + 3] the plain Voigt
+// evaluations of cost class 2 (polynomial cells) and 1 (asymptotic series).
+template <int NW>
+__device__ __forceinline__ void block_counts(int64_t nev, int64_t nmlp, int64_t nnear, int64_t nmid,
+                                             int64_t (*red)[NW], int64_t* counts) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t v[4] = {nev, nmlp, nnear, nmid};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    if (lane == 0) red[i][warp] = v[i];
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    int64_t t = 0;
+    for (int w = 0; w < NW; ++w) t += red[threadIdx.x][w];
+    counts[4 * (int64_t)blockIdx.x + threadIdx.x] = t;
+  }
+}
+
+// One counted evaluation at (x, y) (COUNT variants only).
+template <bool COUNT>
+__device__ __forceinline__ void count_eval(bool voigt, float x, float y, int64_t& nev, int64_t& nnear,
+                                           int64_t& nmid) {
+  if (!COUNT) return;
+  ++nev;
+  if (voigt) {
+    const int c = voigt_class(x, y);
+    nnear += c == 2 ? 1 : 0;
+    nmid += c == 1 ? 1 : 0;
+  }
+}
+
+// Launch a surrogate-capable kernel with the network weights in dynamic shared memory.
+template <class... KA, class... A>
+static void launch_surr(void (*k)(KA...), int n_items, int threads, cudaStream_t st, A... args) {
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MlpWeights));
+  k<<<n_items, threads, sizeof(MlpWeights), st>>>(args...);
+}
+
 // ------------------------------------------------------------------ K1: level prep
 __global__ void __launch_bounds__(256) k_level_prep(PrepArgs a) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -352,7 +395,7 @@ void launch_level_prep(const PrepArgs& a, int n_levels, cudaStream_t st) {
 // series y/(sqrt(pi) r^2)(1 + (3x^2 - y^2)/(2 r^4)), and the chi-factor of branch 1 is a
 // per-line factor times a per-node constant exp(-0.027 |j|); other lines take the exact path.
 __device__ __noinline__ float2 g1_exact_pair(const ReqDev& R, int64_t o, int64_t X0, int j0,
-                                            bool need0, bool need1) {
+                                            bool need0, bool need1, int& n_near, int& n_mid) {
   const int sh = panel_shift(1) - 1;
   const int64_t c = __ldg(R.c + o);
   const float amp = __ldg(R.amp + o), sx = __ldg(R.sx + o), y = __ldg(R.yv + o);
@@ -366,9 +409,42 @@ __device__ __noinline__ float2 g1_exact_pair(const ReqDev& R, int64_t o, int64_t
     if (!(q ? need1 : need0)) continue;
     const int j = j0 + q;
     const float jf = (float)j, xv = nx.x(jf);
-    float f = amp * (R.shape == kShapeVoigt ? voigt_K(xv, y) : shape_f(R.shape, xv, y));
+    const bool voigt = R.shape == kShapeVoigt;
+    float f = amp * (voigt ? voigt_K(xv, y) : shape_f(R.shape, xv, y));
     if (use_chi) f *= ct.value(j, nx.absd(jf, sh));
     v[q] = f;
+    const int cl = voigt ? voigt_class(xv, y) : 0;
+    n_near += cl == 2 ? 1 : 0;
+    n_mid += cl == 1 ? 1 : 0;
+  }
+  return make_float2(v[0], v[1]);
+}
+
+// g1_exact_pair for a converged warp with the surrogate under its guard.
+__device__ __noinline__ float2 g1_exact_pair_coll(const ReqDev& R, int64_t o, int64_t X0, int j0,
+                                                 bool need0, bool need1, const MlpWeights& S,
+                                                 int64_t& n_mlp, int& n_near, int& n_mid) {
+  const int sh = panel_shift(1) - 1;
+  const int64_t c = __ldg(R.c + o);
+  const float amp = __ldg(R.amp + o), sx = __ldg(R.sx + o), y = __ldg(R.yv + o);
+  const bool use_chi = (__ldg(R.flags + o) & 1) && R.shape < kShapeConst;
+  NodeX nx;
+  nx.init(X0 - c, sh, sx);
+  ChiThr ct;
+  if (use_chi) ct.init(c, X0, sh);
+  float v[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int j = j0 + q;
+    const float jf = (float)j;
+    const bool need = q ? need1 : need0;
+    const float xv = nx.x(jf);
+    float f = amp * voigt_K_coll<false>(xv, y, need, kVoigtCells, S, n_mlp);
+    if (use_chi && need) f *= ct.value(j, nx.absd(jf, sh));
+    v[q] = need ? f : 0.0f;
+    const int cl = need ? voigt_class(xv, y) : 0;
+    n_near += cl == 2 ? 1 : 0;
+    n_mid += cl == 1 ? 1 : 0;
   }
   return make_float2(v[0], v[1]);
 }
@@ -381,18 +457,22 @@ __device__ __forceinline__ void comp_merge(float& s, float& c, float s2, float c
   c = (c + c2) + e;
 }
 
-template <bool COUNT>
+template <bool COUNT, bool SURR>
 __global__ void __launch_bounds__(kG1Warps * 32)
     k_g1(const ReqDev* __restrict__ reqs, const G1Item* __restrict__ items,
          int64_t* __restrict__ counts) {
+  extern __shared__ __align__(16) unsigned char dsm[];  // surrogate weights (SURR only)
+  MlpWeights& S = *reinterpret_cast<MlpWeights*>(dsm);
   __shared__ float4 sA[kG1Batch];               // q, sx, phi*sx, y^2
   __shared__ float4 sB[kG1Batch];               // a_centre, a_left, a_right, -y^2/2
   __shared__ unsigned long long sM[kG1Batch];   // owned panels m0-1 .. m0+31
   __shared__ int4 sC[kG1Batch];                 // j_left3, j_right3, exact-path flag, -
   __shared__ float sRed[kG1Warps][8][32];
-  __shared__ int64_t sCnt[kG1Warps];
+  __shared__ int64_t sCnt[4][kG1Warps];
   const G1Item it = items[blockIdx.x];
   const ReqDev& R = reqs[it.req];
+  const bool use_mlp = SURR && R.mlp != nullptr;  // block-uniform
+  if (use_mlp) mlp_load_smem(S, R.mlp);  // made visible by the first barrier below
   const int lev = it.level;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int s = panel_shift(1);  // panel 2 cm^-1 = 2^44 units; nodes every 2^43
@@ -419,7 +499,8 @@ __global__ void __launch_bounds__(kG1Warps * 32)
   const float rR0 = expf(-0.027f * f0), rR1 = expf(-0.027f * f1);
   const float rL0 = expf(0.027f * f0), rL1 = expf(0.027f * f1);
   float eS = 0.f, eC = 0.f, lS = 0.f, lC = 0.f, rS = 0.f, rC = 0.f, mS = 0.f, mC = 0.f;
-  int64_t nev = 0;
+  int64_t nev = 0, nmlp = 0, nnear = 0, nmid = 0;
+  if (use_mlp) __syncthreads();
 
   for (int64_t b0 = i_lo; b0 < i_hi; b0 += kG1Batch) {
     const int nbat = (int)min((int64_t)kG1Batch, i_hi - b0);
@@ -487,6 +568,20 @@ __global__ void __launch_bounds__(kG1Warps * 32)
       const uint64_t msk = sM[k];
       const bool bL = (msk >> (p + 1)) & 1ull;  // panel m0+p: L of node 2m, M of node 2m+1
       const bool bR = (msk >> p) & 1ull;        // panel m0+p-1: R of node 2m
+      if (use_mlp && (C.z & 1)) {  // exact path, warp-uniform: every lane takes part
+        int nn = 0, nm = 0;
+        const float2 v = g1_exact_pair_coll(R, off + b0 + k, X0, j0, bL || bR, bL, S, nmlp, nn, nm);
+        if (bL || bR) {
+          if (bL && bR) pe += v.x; else if (bL) pl += v.x; else pr += v.x;
+          pm += v.y;
+          if (COUNT) {
+            nev += 1 + (bL ? 1 : 0);
+            nnear += nn;
+            nmid += nm;
+          }
+        }
+        continue;
+      }
       if (!(bL || bR)) continue;
       float v0, v1;
       if (!(C.z & 1)) {
@@ -502,9 +597,14 @@ __global__ void __launch_bounds__(kG1Warps * 32)
         const float am1 = j0 + 1 >= C.y ? b.z * rR1 : (j0 + 1 <= C.x ? b.y * rL1 : b.x);
         v1 = bL ? am1 * i1 * s1 : 0.0f;
       } else {
-        const float2 v = g1_exact_pair(R, off + b0 + k, X0, j0, true, bL);
+        int nn = 0, nm = 0;
+        const float2 v = g1_exact_pair(R, off + b0 + k, X0, j0, true, bL, nn, nm);
         v0 = v.x;
         v1 = v.y;
+        if (COUNT) {
+          nnear += nn;
+          nmid += nm;
+        }
       }
       if (bL && bR) pe += v0; else if (bL) pl += v0; else pr += v0;
       pm += v1;
@@ -519,11 +619,6 @@ __global__ void __launch_bounds__(kG1Warps * 32)
   sRed[warp][2][lane] = lS; sRed[warp][3][lane] = lC;
   sRed[warp][4][lane] = rS; sRed[warp][5][lane] = rC;
   sRed[warp][6][lane] = mS; sRed[warp][7][lane] = mC;
-  if (COUNT) {
-#pragma unroll
-    for (int o = 16; o; o >>= 1) nev += __shfl_xor_sync(0xffffffffu, nev, o);
-    if (lane == 0) sCnt[warp] = nev;
-  }
   __syncthreads();
   if (warp == 0) {
     float a[8];
@@ -546,21 +641,23 @@ __global__ void __launch_bounds__(kG1Warps * 32)
       gp[np + (m - m_first)] = a[6] + a[7];
     }
     if (m - 1 >= m_first && m - 1 <= m_last) gp[2 * np + (m - 1 - m_first)] = rs + rc;
-    if (COUNT && lane == 0) {
-      int64_t t = 0;
-      for (int w = 0; w < kG1Warps; ++w) t += sCnt[w];
-      counts[blockIdx.x] = t;
-    }
   }
+  if (COUNT) block_counts<kG1Warps>(nev, nmlp, nnear, nmid, sCnt, counts);
 }
 
-void launch_g1(const ReqDev* reqs, const G1Item* items, int n_items, int64_t* counts,
+void launch_g1(const ReqDev* reqs, const G1Item* items, int n_items, int64_t* counts, bool surr,
                cudaStream_t st) {
   if (n_items <= 0) return;
-  if (counts)
-    k_g1<true><<<n_items, kG1Warps * 32, 0, st>>>(reqs, items, counts);
-  else
-    k_g1<false><<<n_items, kG1Warps * 32, 0, st>>>(reqs, items, counts);
+  if (surr) {
+    if (counts)
+      launch_surr(k_g1<true, true>, n_items, kG1Warps * 32, st, reqs, items, counts);
+    else
+      launch_surr(k_g1<false, true>, n_items, kG1Warps * 32, st, reqs, items, counts);
+  } else if (counts) {
+    k_g1<true, false><<<n_items, kG1Warps * 32, 0, st>>>(reqs, items, counts);
+  } else {
+    k_g1<false, false><<<n_items, kG1Warps * 32, 0, st>>>(reqs, items, counts);
+  }
 }
 
 // ------------------------------------------------------------------ grids 2..10, line-major
@@ -569,14 +666,16 @@ void launch_g1(const ReqDev* reqs, const G1Item* items, int n_items, int64_t* co
 // the tile, evaluates the profile at the nodes of those panels only, and adds the
 // values into lane-private shared-memory slots (acc[pair][lane]); the slots are summed
 // over lanes and warps in a fixed order at the end.
-template <bool COUNT>
+template <bool COUNT, bool SURR>
 __global__ void __launch_bounds__(kLWarps * 32)
     k_coarse_lm(const ReqDev* __restrict__ reqs, const CoarseItem* __restrict__ items,
              int64_t* __restrict__ counts) {
+  extern __shared__ __align__(16) unsigned char dsm[];  // surrogate weights (SURR only)
+  MlpWeights& S = *reinterpret_cast<MlpWeights*>(dsm);
   __shared__ float accL[kLWarps][kLPairs][32];
   __shared__ float accM[kLWarps][kLPairs][32];
   __shared__ float accR[kLWarps][kLPairs][32];
-  __shared__ int64_t sCnt[kLWarps];
+  __shared__ int64_t sCnt[4][kLWarps];
   const CoarseItem it = items[blockIdx.x];
   const ReqDev& R = reqs[it.req];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -609,11 +708,63 @@ __global__ void __launch_bounds__(kLWarps * 32)
   const int64_t X0 = m0 << s;  // position of node 2 m0 (j = 0)
   const bool physical = R.shape < kShapeConst;
   const bool voigt = R.shape == kShapeVoigt;
-  int64_t nev = 0;
+  int64_t nev = 0, nmlp = 0, nnear = 0, nmid = 0;
+  const bool use_mlp = SURR && R.mlp != nullptr;  // block-uniform
+  if (use_mlp) {
+    mlp_load_smem(S, R.mlp);
+    __syncthreads();
+  }
   __syncwarp();
   for (int r = 0; r < bd.n; ++r) {
     for (int64_t i0 = bd.lo[r]; i0 < bd.hi[r]; i0 += kLWarps * 32) {
       const int64_t i = i0 + tid;
+      if (use_mlp) {
+        // all lanes step through the union of their pair ranges together
+        uint64_t own = 0;
+        int64_t c = 0;
+        bool chi = false;
+        if (i < bd.hi[r]) {
+          c = __ldg(R.c + lo_off + i);
+          const int gst = __ldg(R.gstar + lo_off + i);
+          chi = __ldg(R.flags + lo_off + i) & 1;
+          own = accept_mask<uint64_t>(g, c, gst, chi, cut, R.R_w, base, nb, false) & win;
+          if (own) own &= ~accept_mask<uint64_t>(g - 1, c, gst, chi, cut, R.R_w, base, nb, true);
+        }
+        float amp = 0.0f, y = 1.0f;
+        NodeX nx;
+        nx.qf = nx.hs = nx.phs = nx.phi = 0.0f;
+        ChiThr ct;
+        const bool use_chi = own && chi && physical;
+        int pa = 1 << 20, pb = -1;
+        if (own) {
+          amp = __ldg(R.amp + lo_off + i);
+          y = __ldg(R.yv + lo_off + i);
+          nx.init(X0 - c, s - 1, __ldg(R.sx + lo_off + i));
+          if (use_chi) ct.init(c, X0, s - 1);
+          pa = max(__ffsll((long long)own) - 2, 0);
+          pb = min(63 - __clzll((long long)own), kLPairs - 1);
+        }
+        const int qa = __reduce_min_sync(0xffffffffu, pa), qb = __reduce_max_sync(0xffffffffu, pb);
+        for (int p = qa; p <= qb; ++p) {
+          const bool bR = (own >> p) & 1ull, bL = (own >> (p + 1)) & 1ull;
+          const float jf = (float)(2 * p);
+          const float xe = nx.x(jf), xo = nx.x(jf + 1.0f);
+          const float ke = voigt_K_coll<false>(xe, y, bR || bL, kVoigtCells, S, nmlp);
+          const float ko = voigt_K_coll<false>(xo, y, bL, kVoigtCells, S, nmlp);
+          if (bR || bL) count_eval<COUNT>(true, xe, y, nev, nnear, nmid);
+          if (bL) count_eval<COUNT>(true, xo, y, nev, nnear, nmid);
+          float v = amp * ke;
+          if (use_chi && (bR || bL)) v *= ct.value(2 * p, nx.absd(jf, s - 1));
+          if (bL) accL[warp][p][lane] += v;
+          if (bR) accR[warp][p][lane] += v;
+          if (bL) {
+            float w = amp * ko;
+            if (use_chi) w *= ct.value(2 * p + 1, nx.absd(jf + 1.0f, s - 1));
+            accM[warp][p][lane] += w;
+          }
+        }
+        continue;
+      }
       if (i >= bd.hi[r]) continue;
       const int64_t c = __ldg(R.c + lo_off + i);
       const int gst = __ldg(R.gstar + lo_off + i);
@@ -641,20 +792,16 @@ __global__ void __launch_bounds__(kLWarps * 32)
         if (use_chi) v *= ct.value(2 * p, nx.absd(jf, s - 1));
         if (bL) accL[warp][p][lane] += v;
         if (bR) accR[warp][p][lane] += v;
+        count_eval<COUNT>(voigt, xv, y, nev, nnear, nmid);
         if (bL) {
           const float xw = nx.x(jf + 1.0f);
           float w = amp * (voigt ? voigt_K(xw, y) : shape_f(R.shape, xw, y));
           if (use_chi) w *= ct.value(2 * p + 1, nx.absd(jf + 1.0f, s - 1));
           accM[warp][p][lane] += w;
+          count_eval<COUNT>(voigt, xw, y, nev, nnear, nmid);
         }
-        if (COUNT) nev += 1 + (bL ? 1 : 0);
       }
     }
-  }
-  if (COUNT) {
-#pragma unroll
-    for (int o = 16; o; o >>= 1) nev += __shfl_xor_sync(0xffffffffu, nev, o);
-    if (lane == 0) sCnt[warp] = nev;
   }
   __syncthreads();
   // thread t < 3 kLPairs sums slot (t / kLPairs, pair t % kLPairs) over warps and lanes
@@ -672,20 +819,22 @@ __global__ void __launch_bounds__(kLWarps * 32)
     if (kind == 1 && m <= m_last) gp[np + (m - m_first)] = v;
     if (kind == 2 && m - 1 >= m_first && m - 1 <= m_last) gp[2 * np + (m - 1 - m_first)] = v;
   }
-  if (COUNT && tid == 0) {
-    int64_t t = 0;
-    for (int w = 0; w < kLWarps; ++w) t += sCnt[w];
-    counts[blockIdx.x] = t;
-  }
+  if (COUNT) block_counts<kLWarps>(nev, nmlp, nnear, nmid, sCnt, counts);
 }
 
 void launch_coarse_lm(const ReqDev* reqs, const CoarseItem* items, int n_items, int64_t* counts,
-                      cudaStream_t st) {
+                      bool surr, cudaStream_t st) {
   if (n_items <= 0) return;
-  if (counts)
-    k_coarse_lm<true><<<n_items, kLWarps * 32, 0, st>>>(reqs, items, counts);
-  else
-    k_coarse_lm<false><<<n_items, kLWarps * 32, 0, st>>>(reqs, items, counts);
+  if (surr) {
+    if (counts)
+      launch_surr(k_coarse_lm<true, true>, n_items, kLWarps * 32, st, reqs, items, counts);
+    else
+      launch_surr(k_coarse_lm<false, true>, n_items, kLWarps * 32, st, reqs, items, counts);
+  } else if (counts) {
+    k_coarse_lm<true, false><<<n_items, kLWarps * 32, 0, st>>>(reqs, items, counts);
+  } else {
+    k_coarse_lm<false, false><<<n_items, kLWarps * 32, 0, st>>>(reqs, items, counts);
+  }
 }
 
 // ------------------------------------------------------------------ grids 2..10
@@ -695,15 +844,17 @@ void launch_coarse_lm(const ReqDev* reqs, const CoarseItem* items, int n_items, 
 // owns in the tile and evaluates the profile at the nodes of those panels, into a
 // per-warp shared buffer (row = line). Phase 2: each lane adds, for its own pair, the
 // buffered values of the lines owning its panels into compensated register sums.
-template <bool COUNT>
+template <bool COUNT, bool SURR>
 __global__ void __launch_bounds__(kCWarps * 32)
     k_coarse(const ReqDev* __restrict__ reqs, const CoarseItem* __restrict__ items,
              int64_t* __restrict__ counts) {
+  extern __shared__ __align__(16) unsigned char dsm[];  // surrogate weights (SURR only)
+  MlpWeights& S = *reinterpret_cast<MlpWeights*>(dsm);
   __shared__ float stab[kVoigtTableFloats];
   __shared__ float bufE[kCWarps][32][kCPairs + 1];  // value at node 2p of staged line t
   __shared__ float bufO[kCWarps][32][kCPairs + 1];  // value at node 2p + 1
   __shared__ unsigned long long smsk[kCWarps][32];
-  __shared__ int64_t sCnt[kCWarps];
+  __shared__ int64_t sCnt[4][kCWarps];
   const CoarseItem it = items[blockIdx.x];
   const ReqDev& R = reqs[it.req];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -712,8 +863,10 @@ __global__ void __launch_bounds__(kCWarps * 32)
   const int64_t m_first = R.m_first[g];
   const int64_t m_last = m_first + R.npan[g] - 1;
   const int64_t m0 = it.m0 + (int64_t)kCPairs * warp;  // this warp's first pair
-  int64_t nev = 0;
+  int64_t nev = 0, nmlp = 0, nnear = 0, nmid = 0;
+  const bool use_mlp = SURR && R.mlp != nullptr;  // block-uniform
   voigt_table_to_smem(stab);
+  if (use_mlp) mlp_load_smem(S, R.mlp);
   __syncthreads();
   if (m0 <= m_last + 1) {  // warp-uniform
     const int s = panel_shift(g);
@@ -756,7 +909,43 @@ __global__ void __launch_bounds__(kCWarps * 32)
         const uint32_t any = __ballot_sync(0xffffffffu, own != 0);
         if (!any) continue;
         // phase 1: this lane's line at the nodes of its owned panels
-        if (own) {
+        if (use_mlp) {
+          // all lanes step through the union of their pair ranges together
+          float amp = 0.0f, y = 1.0f;
+          NodeX nx;
+          nx.qf = nx.hs = nx.phs = nx.phi = 0.0f;
+          ChiThr ct;
+          const bool use_chi = own && chi && physical;
+          int pa = 1 << 20, pb = -1;
+          if (own) {
+            amp = __ldg(R.amp + lo_off + i);
+            y = __ldg(R.yv + lo_off + i);
+            nx.init(X0 - c, s - 1, __ldg(R.sx + lo_off + i));
+            if (use_chi) ct.init(c, X0, s - 1);
+            pa = max(__ffsll((long long)own) - 2, 0);
+            pb = min(63 - __clzll((long long)own), kCPairs - 1);
+          }
+          const int qa = __reduce_min_sync(0xffffffffu, pa), qb = __reduce_max_sync(0xffffffffu, pb);
+          for (int q = qa; q <= qb; ++q) {
+            const bool bR = (own >> q) & 1ull, bL = (own >> (q + 1)) & 1ull;
+            const float jf = (float)(2 * q);
+            const float xv = nx.x(jf), xw = nx.x(jf + 1.0f);
+            const float ke = voigt_K_coll<true>(xv, y, bR || bL, stab, S, nmlp);
+            const float ko = voigt_K_coll<true>(xw, y, bL, stab, S, nmlp);
+            if (bR || bL) {
+              float v = amp * ke;
+              if (use_chi) v *= ct.value(2 * q, nx.absd(jf, s - 1));
+              bE[lane][q] = v;
+              count_eval<COUNT>(true, xv, y, nev, nnear, nmid);
+            }
+            if (bL) {
+              float w = amp * ko;
+              if (use_chi) w *= ct.value(2 * q + 1, nx.absd(jf + 1.0f, s - 1));
+              bO[lane][q] = w;
+              count_eval<COUNT>(true, xw, y, nev, nnear, nmid);
+            }
+          }
+        } else if (own) {
           const float amp = __ldg(R.amp + lo_off + i);
           const float sx = __ldg(R.sx + lo_off + i);
           const float y = __ldg(R.yv + lo_off + i);
@@ -775,13 +964,14 @@ __global__ void __launch_bounds__(kCWarps * 32)
             float v = amp * (voigt ? voigt_K<true>(xv, y, stab) : shape_f(R.shape, xv, y));
             if (use_chi) v *= ct.value(2 * q, nx.absd(jf, s - 1));
             bE[lane][q] = v;
+            count_eval<COUNT>(voigt, xv, y, nev, nnear, nmid);
             if (bL) {
               const float xw = nx.x(jf + 1.0f);
               float w = amp * (voigt ? voigt_K<true>(xw, y, stab) : shape_f(R.shape, xw, y));
               if (use_chi) w *= ct.value(2 * q + 1, nx.absd(jf + 1.0f, s - 1));
               bO[lane][q] = w;
+              count_eval<COUNT>(voigt, xw, y, nev, nnear, nmid);
             }
-            if (COUNT) nev += 1 + (bL ? 1 : 0);
           }
         }
         mk[lane] = own;
@@ -815,26 +1005,22 @@ __global__ void __launch_bounds__(kCWarps * 32)
     }
     if (m - 1 >= m_first && m - 1 <= m_last) gp[2 * np + (m - 1 - m_first)] = sR + cR;
   }
-  if (COUNT) {
-#pragma unroll
-    for (int o = 16; o; o >>= 1) nev += __shfl_xor_sync(0xffffffffu, nev, o);
-    if (lane == 0) sCnt[warp] = nev;
-    __syncthreads();
-    if (tid == 0) {
-      int64_t t = 0;
-      for (int w = 0; w < kCWarps; ++w) t += sCnt[w];
-      counts[blockIdx.x] = t;
-    }
-  }
+  if (COUNT) block_counts<kCWarps>(nev, nmlp, nnear, nmid, sCnt, counts);
 }
 
 void launch_coarse(const ReqDev* reqs, const CoarseItem* items, int n_items, int64_t* counts,
-                   cudaStream_t st) {
+                   bool surr, cudaStream_t st) {
   if (n_items <= 0) return;
-  if (counts)
-    k_coarse<true><<<n_items, kCWarps * 32, 0, st>>>(reqs, items, counts);
-  else
-    k_coarse<false><<<n_items, kCWarps * 32, 0, st>>>(reqs, items, counts);
+  if (surr) {
+    if (counts)
+      launch_surr(k_coarse<true, true>, n_items, kCWarps * 32, st, reqs, items, counts);
+    else
+      launch_surr(k_coarse<false, true>, n_items, kCWarps * 32, st, reqs, items, counts);
+  } else if (counts) {
+    k_coarse<true, false><<<n_items, kCWarps * 32, 0, st>>>(reqs, items, counts);
+  } else {
+    k_coarse<false, false><<<n_items, kCWarps * 32, 0, st>>>(reqs, items, counts);
+  }
 }
 
 // ------------------------------------------------------------------ finest grid + cascade
@@ -845,11 +1031,13 @@ void launch_coarse(const ReqDev* reqs, const CoarseItem* items, int n_items, int
 // within the cut-off, and stages them in shared memory; every lane then sums the
 // staged lines that own its nodes. Finally each node adds the quadratic interpolants
 // of the ten coarse grids, and the CTA writes its outputs with aligned vector stores.
-template <bool COUNT>
+template <bool COUNT, bool SURR>
 __global__ void __launch_bounds__(kFineThreads)
     k_fine(const ReqDev* __restrict__ reqs, const FineItem* __restrict__ items,
            int64_t* __restrict__ counts) {
   constexpr int NW = kFineThreads / 32;
+  extern __shared__ __align__(16) unsigned char dsm[];  // surrogate weights (SURR only)
+  MlpWeights& S = *reinterpret_cast<MlpWeights*>(dsm);
   __shared__ float tile[kFineTile];
   __shared__ float stab[kVoigtTableFloats];
   // staged lines, one slot per lane of each warp (struct of arrays: no bank conflicts)
@@ -857,12 +1045,14 @@ __global__ void __launch_bounds__(kFineThreads)
   __shared__ uint32_t sPm[NW][32];
   __shared__ int sKlo[NW][32], sKhi[NW][32], sChi[NW][32];
   __shared__ int sT[6][NW][32];  // chi thresholds r3, r150, r300, l3, l150, l300
-  __shared__ int64_t red[NW];
+  __shared__ int64_t red[4][NW];
   const FineItem it = items[blockIdx.x];
   const ReqDev& R = reqs[it.req];
   const int lev = it.level;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool use_mlp = SURR && R.mlp != nullptr;  // block-uniform
   voigt_table_to_smem(stab);
+  if (use_mlp) mlp_load_smem(S, R.mlp);
   __syncthreads();
   const int64_t kw = it.k0 + (int64_t)kFinePerThread * 32 * warp;  // first node of the warp
   const int64_t k0 = kw + kFinePerThread * lane;                    // first node of the lane
@@ -871,7 +1061,7 @@ __global__ void __launch_bounds__(kFineThreads)
   float acc[kFinePerThread], cmp[kFinePerThread];
 #pragma unroll
   for (int q = 0; q < kFinePerThread; ++q) acc[q] = cmp[q] = 0.0f;
-  int64_t nev = 0;
+  int64_t nev = 0, nmlp = 0, nnear = 0, nmid = 0;
   const int nw = kFinePerThread * 32;  // nodes of the warp
   const int wlo = (int)max(R.k_lo - kw, (int64_t)0);
   const int whi = (int)min(R.k_hi - kw, (int64_t)(nw - 1));
@@ -938,7 +1128,41 @@ __global__ void __launch_bounds__(kFineThreads)
           const int e = __ffs(rem) - 1;
           mine |= ((sPm[warp][e] >> mypanel) & 1u) << e;
         }
-        while (mine) {
+        if (use_mlp) {
+          // the warp steps through the lanes' lists together, one staged line per lane
+          // and round, so that the surrogate can evaluate 32 inputs at once
+          while (__any_sync(0xffffffffu, mine != 0)) {
+            int e = -1;
+            if (mine) {
+              e = __ffs(mine) - 1;
+              mine &= mine - 1;
+            }
+            const int es = e < 0 ? 0 : e;
+            const float qf = sQ[warp][es], hs = sHs[warp][es], phs = sPhs[warp][es], phi = sPhi[warp][es];
+            const float amp = sAmp[warp][es], y = e < 0 ? 1.0f : sY[warp][es];
+            const int klo_e = e < 0 ? 1 : sKlo[warp][es], khi_e = e < 0 ? 0 : sKhi[warp][es];
+            const bool uc = e >= 0 && sChi[warp][es];
+            ChiThr ct;
+            if (uc) {
+              ct.r3 = sT[0][warp][es]; ct.r150 = sT[1][warp][es]; ct.r300 = sT[2][warp][es];
+              ct.l3 = sT[3][warp][es]; ct.l150 = sT[4][warp][es]; ct.l300 = sT[5][warp][es];
+            }
+#pragma unroll
+            for (int q = 0; q < kFinePerThread; ++q) {
+              const int j = kFinePerThread * lane + q;
+              const bool act = j >= klo_e && j <= khi_e;
+              const float jf = (float)j;
+              const float xv = fmaf(jf + qf, hs, phs);
+              float v = amp * voigt_K_coll<true>(xv, y, act, stab, S, nmlp);
+              if (act) {
+                if (uc) v *= ct.value(j, fabsf((jf + qf) + phi) * ldexpf(1.0f, -kFineBits));
+                kahan_add(acc[q], cmp[q], v);
+                count_eval<COUNT>(true, xv, y, nev, nnear, nmid);
+              }
+            }
+          }
+        }
+        while (!use_mlp && mine) {
           const int e = __ffs(mine) - 1;
           mine &= mine - 1;
           const float qf = sQ[warp][e], hs = sHs[warp][e], phs = sPhs[warp][e], phi = sPhi[warp][e];
@@ -959,7 +1183,7 @@ __global__ void __launch_bounds__(kFineThreads)
             float v = amp * (voigt ? voigt_K<true>(xv, y, stab) : shape_f(R.shape, xv, y));
             if (uc) v *= ct.value(j, fabsf((jf + qf) + phi) * ldexpf(1.0f, -kFineBits));
             kahan_add(acc[q], cmp[q], v);
-            if (COUNT) ++nev;
+            count_eval<COUNT>(voigt, xv, y, nev, nnear, nmid);
           }
         }
         __syncwarp();
@@ -1019,26 +1243,22 @@ __global__ void __launch_bounds__(kFineThreads)
     const int done = head + 4 * nv;
     if (tid < n - done) dst[done + tid] = tile[t0 + done + tid];
   }
-  if (COUNT) {
-#pragma unroll
-    for (int o = 16; o; o >>= 1) nev += __shfl_xor_sync(0xffffffffu, nev, o);
-    if (lane == 0) red[warp] = nev;
-    __syncthreads();
-    if (tid == 0) {
-      int64_t t = 0;
-      for (int w = 0; w < kFineThreads / 32; ++w) t += red[w];
-      counts[blockIdx.x] = t;
-    }
-  }
+  if (COUNT) block_counts<NW>(nev, nmlp, nnear, nmid, red, counts);
 }
 
-void launch_fine(const ReqDev* reqs, const FineItem* items, int n_items, int64_t* counts,
+void launch_fine(const ReqDev* reqs, const FineItem* items, int n_items, int64_t* counts, bool surr,
                  cudaStream_t st) {
   if (n_items <= 0) return;
-  if (counts)
-    k_fine<true><<<n_items, kFineThreads, 0, st>>>(reqs, items, counts);
-  else
-    k_fine<false><<<n_items, kFineThreads, 0, st>>>(reqs, items, counts);
+  if (surr) {
+    if (counts)
+      launch_surr(k_fine<true, true>, n_items, kFineThreads, st, reqs, items, counts);
+    else
+      launch_surr(k_fine<false, true>, n_items, kFineThreads, st, reqs, items, counts);
+  } else if (counts) {
+    k_fine<true, false><<<n_items, kFineThreads, 0, st>>>(reqs, items, counts);
+  } else {
+    k_fine<false, false><<<n_items, kFineThreads, 0, st>>>(reqs, items, counts);
+  }
 }
 
 // ------------------------------------------------------------------ diagnostics

@@ -121,6 +121,16 @@ __device__ __forceinline__ float voigt_K(float x, float y, const float* tab) {
 
 __device__ __forceinline__ float voigt_K(float x, float y) { return voigt_K<false>(x, y, kVoigtCells); }
 
+// Cost class of one voigt_K evaluation, for operation counts: 0 the far-wing two-term
+// series, 1 the 6- or 15-term asymptotic series, 2 a polynomial cell (Dawson or K table).
+__device__ __forceinline__ int voigt_class(float x, float y) {
+  const float ax = fabsf(x);
+  const float r2 = fmaf(ax, ax, y * y);
+  if (r2 >= 1.0e4f) return 0;
+  if (y < 1.0f && ax < 12.0f) return 2;
+  return r2 >= 20.25f ? 1 : 2;
+}
+
 // Copy the coefficient table into shared memory (all threads of the block take part).
 __device__ __forceinline__ void voigt_table_to_smem(float* dst) {
   for (int i = threadIdx.x; i < VOIGT_NCELL * (VOIGT_DEG + 1) * (VOIGT_DEG + 1); i += blockDim.x)

@@ -42,7 +42,19 @@ _LIB = None
 EXPORTS = ["marfa_prepare_lines", "marfa_free_lines", "marfa_num_points", "marfa_absorption",
            "marfa_absorption_batch", "marfa_write_pt_table", "marfa_last_error", "marfa_diag_voigt",
            "marfa_diag_level_lines", "marfa_diag_owned", "marfa_diag_absorption_counted",
-           "marfa_diag_kernel_timing", "marfa_absorption_noalloc"]
+           "marfa_diag_kernel_timing", "marfa_absorption_noalloc", "marfa_mlp_loss_grad",
+           "marfa_mlp_train", "marfa_surrogate_load", "marfa_surrogate_unload", "marfa_surrogate_eval",
+           "marfa_diag_absorption_counted_surrogate", "marfa_plan_create", "marfa_plan_execute",
+           "marfa_plan_info", "marfa_plan_destroy", "marfa_diag_absorption_counts"]
+
+MLP_PARAMS = 8577
+MLP_MAX_BATCH = 65536
+GUARD_NX, GUARD_NY = 96, 72
+
+
+class marfa_mlp_train_t(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("batch", C.c_int32), ("qat", C.c_int32), ("reserved", C.c_int32),
+                ("lr0", C.c_float), ("lr1", C.c_float)]
 
 
 def lib_path() -> str:
@@ -73,6 +85,17 @@ def load(path: str | None = None):
         "marfa_diag_absorption_counted": (C.c_int, [vp, vp, vp, i32, vp, vp, vp]),
         "marfa_diag_kernel_timing": (C.c_int, [i32, vp, vp]),
         "marfa_absorption_noalloc": (C.c_int, [vp, vp, vp, i32, vp, vp, vp]),
+        "marfa_mlp_loss_grad": (C.c_int, [vp, vp, vp, vp, i64, i32, vp, vp]),
+        "marfa_mlp_train": (C.c_int, [vp, vp, vp, vp, i64, vp, vp]),
+        "marfa_surrogate_load": (C.c_int, [vp, C.c_float, i32, vp, vp]),
+        "marfa_surrogate_unload": (C.c_int, []),
+        "marfa_surrogate_eval": (C.c_int, [vp, vp, vp, i64, i32]),
+        "marfa_diag_absorption_counted_surrogate": (C.c_int, [vp, vp, vp, i32, vp, vp, vp, vp]),
+        "marfa_plan_create": (C.c_int, [i32, vp, vp, vp, vp, vp, vp, i32, vp, C.POINTER(vp)]),
+        "marfa_plan_execute": (C.c_int, [vp, vp]),
+        "marfa_plan_info": (C.c_int, [vp, vp, vp, vp]),
+        "marfa_plan_destroy": (None, [vp]),
+        "marfa_diag_absorption_counts": (C.c_int, [vp, vp, vp, i32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -182,6 +205,55 @@ def marfa_absorption_batch(lines, levels, vmrs, rqs, k_outs, stream=None) -> Non
     _check(load().marfa_absorption_batch(n, lh, lp, vp, nl, rq, outs, _stream(stream)))
 
 
+class Plan:
+    """A captured batch (marfa_plan_create); keeps its line lists and outputs alive."""
+
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self._keep = keep
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.marfa_plan_destroy(self.handle)
+            self.handle = None
+
+
+def marfa_plan_create(lines, levels, vmrs, rqs, k_outs, autotune: bool = False, stream=None) -> Plan:
+    """k_outs: CUDA tensors [n_levels, npts] float32, rewritten by every execution."""
+    n = len(lines)
+    levels = [np.ascontiguousarray(x, dtype=LEVEL_DTYPE) for x in levels]
+    vmrs = [np.ascontiguousarray(v, dtype=np.float64) for v in vmrs]
+    VP = C.c_void_p * n
+    lh = VP(*[l.handle.value for l in lines])
+    lp = VP(*[x.ctypes.data for x in levels])
+    vp = VP(*[v.ctypes.data for v in vmrs])
+    nl = (C.c_int32 * n)(*[len(x) for x in levels])
+    rq = (marfa_request_t * n)(*rqs)
+    outs = VP(*[_ptr(o).value for o in k_outs])
+    h = C.c_void_p()
+    _check(load().marfa_plan_create(n, lh, lp, vp, nl, rq, outs, int(autotune), _stream(stream), C.byref(h)))
+    return Plan(h, (list(lines), list(k_outs)))
+
+
+def marfa_plan_execute(plan: Plan, stream=None) -> None:
+    _check(load().marfa_plan_execute(plan.handle, _stream(stream)))
+
+
+def marfa_plan_info(plan: Plan, kernel_ms: bool = False):
+    """(variant[10], tune_ms[10, 2], kernel_ms[12] or None)."""
+    v = np.empty(10, dtype=np.int32)
+    t = np.empty((10, 2), dtype=np.float32)
+    k = np.empty(12, dtype=np.float64) if kernel_ms else None
+    _check(load().marfa_plan_info(plan.handle, _ptr(v), _ptr(t), _ptr(k)))
+    return v, t, k
+
+
+def marfa_plan_destroy(plan: Plan) -> None:
+    if plan.handle:
+        load().marfa_plan_destroy(plan.handle)
+        plan.handle = None
+
+
 def marfa_write_pt_table(directory: str, level_number: int, nu_lo: float, nu_hi: float, k: np.ndarray) -> None:
     k = np.ascontiguousarray(k, dtype=np.float32)
     _check(load().marfa_write_pt_table(directory.encode(), int(level_number), float(nu_lo), float(nu_hi),
@@ -230,6 +302,81 @@ def marfa_diag_absorption_counted(lines: Lines, levels, vmr, rq):
     _check(load().marfa_diag_absorption_counted(lines.handle, _ptr(levels), _ptr(vmr), len(levels),
                                                 C.byref(rq), _ptr(k), _ptr(counts)))
     return k, counts
+
+
+def marfa_diag_absorption_counts(lines: Lines, levels, vmr, rq):
+    """(k, counts[n_levels, 11, 4]): all, surrogate, polynomial-cell and asymptotic
+    evaluations per level and grid."""
+    levels = np.ascontiguousarray(levels, dtype=LEVEL_DTYPE)
+    vmr = np.ascontiguousarray(vmr, dtype=np.float64)
+    n = marfa_num_points(rq.nu_lo, rq.nu_hi)
+    k = np.empty((len(levels), n), dtype=np.float32)
+    counts = np.empty((len(levels), 11, 4), dtype=np.int64)
+    _check(load().marfa_diag_absorption_counts(lines.handle, _ptr(levels), _ptr(vmr), len(levels),
+                                               C.byref(rq), _ptr(k), _ptr(counts)))
+    return k, counts
+
+
+def marfa_diag_absorption_counted_surrogate(lines: Lines, levels, vmr, rq):
+    """(k, counts, surrogate_counts), counts [n_levels, 11] per grid."""
+    levels = np.ascontiguousarray(levels, dtype=LEVEL_DTYPE)
+    vmr = np.ascontiguousarray(vmr, dtype=np.float64)
+    n = marfa_num_points(rq.nu_lo, rq.nu_hi)
+    k = np.empty((len(levels), n), dtype=np.float32)
+    counts = np.empty((len(levels), 11), dtype=np.int64)
+    sc = np.empty((len(levels), 11), dtype=np.int64)
+    _check(load().marfa_diag_absorption_counted_surrogate(lines.handle, _ptr(levels), _ptr(vmr), len(levels),
+                                                          C.byref(rq), _ptr(k), _ptr(counts), _ptr(sc)))
+    return k, counts, sc
+
+
+# ------------------------------------------------------------------ learned Voigt surrogate
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def marfa_mlp_loss_grad(params, x, y, t, qat: bool = False):
+    """(loss, grad[MLP_PARAMS]) of the mean squared error of t over the samples."""
+    params, x, y, t = _f32(params), _f32(x), _f32(y), _f32(t)
+    assert params.shape == (MLP_PARAMS,)
+    grad = np.empty(MLP_PARAMS, dtype=np.float32)
+    loss = C.c_double()
+    _check(load().marfa_mlp_loss_grad(_ptr(params), _ptr(x), _ptr(y), _ptr(t), len(x), int(qat),
+                                      C.byref(loss), _ptr(grad)))
+    return loss.value, grad
+
+
+def marfa_mlp_train(params, x, y, t, steps: int, batch: int, lr0: float, lr1: float, qat: bool = True):
+    """Train a copy of params; returns (params, loss_curve[steps])."""
+    p = _f32(params).copy()
+    assert p.shape == (MLP_PARAMS,)
+    x, y, t = _f32(x), _f32(y), _f32(t)
+    cfg = marfa_mlp_train_t(int(steps), int(batch), int(qat), 0, float(lr0), float(lr1))
+    curve = np.empty(int(steps), dtype=np.float32)
+    _check(load().marfa_mlp_train(_ptr(p), _ptr(x), _ptr(y), _ptr(t), len(x), C.byref(cfg), _ptr(curve)))
+    return p, curve
+
+
+def marfa_surrogate_load(params, budget: float = 8e-4, samples: int = 16):
+    """Load params as the surrogate of the current device; returns (cells_on,
+    cell_err[GUARD_NY, GUARD_NX])."""
+    params = _f32(params)
+    assert params.shape == (MLP_PARAMS,)
+    on = C.c_int32()
+    err = np.empty((GUARD_NY, GUARD_NX), dtype=np.float32)
+    _check(load().marfa_surrogate_load(_ptr(params), float(budget), int(samples), C.byref(on), _ptr(err)))
+    return on.value, err
+
+
+def marfa_surrogate_unload() -> None:
+    _check(load().marfa_surrogate_unload())
+
+
+def marfa_surrogate_eval(x, y, guarded: bool = False) -> np.ndarray:
+    x, y = _f32(x), _f32(y)
+    out = np.empty_like(x)
+    _check(load().marfa_surrogate_eval(_ptr(x), _ptr(y), _ptr(out), len(x), int(guarded)))
+    return out
 
 
 def marfa_diag_kernel_timing(enable: bool):
