@@ -8,6 +8,11 @@ grid 1, grids 2..10 with their autotuned kernels, finest grid with the interpola
 cascade, over all 60 levels) with the line list resident on the GPU.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload venus|batch|earth|tiny]
+
+The default (and headline) workload is the Venus one; --workload times the other
+configurations the same way (batch: 256 uneven requests in one plan; earth: 1.2M lines
+x 50 levels; tiny: 2,000 lines x 1 level).
 
 Prints one JSON line. ``value`` is fine-grid points x levels per second over all
 ranks; ``line_evals_per_s`` counts the (line, node) profile evaluations the scheme
@@ -33,7 +38,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "spectral pts x levels/s and line-evals/s, MLP-Voigt vs plain at <=1e-3 rel err"
 UNIT = "pts*levels/s"
-FLOPS_PER_EVAL = 20.0  # algorithmic FP32 flops of one far-wing profile evaluation
+# FP32 flops of one profile evaluation by Voigt cost class, counted from the formulas
+# (x, the profile, amplitude, chi-factor and the compensated add): far-wing two-term
+# series, 6/15-term asymptotic series (the 6-term count is used for both), polynomial
+# cell (9 x 9 bivariate Horner plus the Gaussian term).
+FLOPS_FAR, FLOPS_MID, FLOPS_NEAR = 20.0, 70.0, 200.0
 N_SM = 152
 FP32_LANES = 128
 
@@ -135,9 +144,10 @@ def surrogate_leg(args, M, wl, lines, levels, out, flush, stream, wpath, evals_p
         plain = out.clone()
         rq_s = M.request_of(wl.with_(surrogate=1))
         if args.no_count:
-            counts = sc = np.zeros((wl.n_levels, 11), dtype=np.int64)
+            c4 = np.zeros((wl.n_levels, 11, 4), dtype=np.int64)
         else:
-            _, counts, sc = M.marfa_diag_absorption_counted_surrogate(lines, levels, wl.vmr, rq_s)
+            _, c4 = M.marfa_diag_absorption_counts(lines, levels, wl.vmr, rq_s)
+        counts, sc = c4[:, :, 0], c4[:, :, 1]
         plan = M.marfa_plan_create([lines], [levels], [wl.vmr], [rq_s], [out], autotune=True, stream=stream)
         for _ in range(args.warmup):
             M.marfa_plan_execute(plan, stream)
@@ -152,6 +162,7 @@ def surrogate_leg(args, M, wl, lines, levels, out, flush, stream, wpath, evals_p
             M.marfa_plan_execute(plan, stream)
             ev[i][1].record(stream)
         torch.cuda.synchronize()
+        kms_s = M.marfa_plan_info(plan, kernel_ms=True)[2]
         M.marfa_plan_destroy(plan)
         t_total = float(sum(a.elapsed_time(b) for a, b in ev)) / 1e3
         if dist:
@@ -166,11 +177,25 @@ def surrogate_leg(args, M, wl, lines, levels, out, flush, stream, wpath, evals_p
         return {"value": wl.n_levels * npts * world * args.steps / t_total, "unit": UNIT, "ms_per_step": ms,
                 "line_evals_per_s": int(counts.sum()) * world * args.steps / t_total,
                 "surrogate_evals_share": float(sc.sum() / max(1, counts.sum())),
+                "surrogate_evals_per_grid": [int(v) for v in sc.sum(axis=0)],
+                "kernel_ms_last_step": [round(float(v), 3) for v in kms_s],
                 "max_rel_vs_plain": float(rel.max().item()), "guard_budget": budget, "guard_lattice": lattice, "guard_cells_on": int(on),
                 "speedup_vs_plain": ms_plain / ms,
                 "note": "plain path within 1e-4 of the FP64 oracle; surrogate path within 1e-3 (tests)"}
     finally:
         M.marfa_surrogate_unload()
+
+
+def load_workloads(name):
+    from workloads import config0_tiny, config1_venus, config2_batch, config3_earth
+    if name == "venus":
+        return [config1_venus()], "venus"
+    if name == "batch":
+        return config2_batch(), "batch: 256 uneven requests (1-50 cm-1 windows in 500-5000, 1k-50k lines, " \
+                                "1-100 Venus levels, cut-off 25/125)"
+    if name == "earth":
+        return [config3_earth()], None
+    return [config0_tiny()], None
 
 
 def main():
@@ -179,6 +204,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["venus", "batch", "earth", "tiny"], default="venus",
+                    help="venus (default, the headline), or a parity configuration timed the same way")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nu-lo", type=float, default=None, help="narrow the window (profiling runs)")
     ap.add_argument("--nu-hi", type=float, default=None)
@@ -191,11 +218,14 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
-    from workloads import config1_venus
-    wl = config1_venus()
+    wls, wname = load_workloads(args.workload)
     if args.nu_lo is not None or args.nu_hi is not None:
-        wl = wl.with_(nu_lo=args.nu_lo if args.nu_lo is not None else wl.nu_lo,
-                      nu_hi=args.nu_hi if args.nu_hi is not None else wl.nu_hi)
+        wls = [w.with_(nu_lo=args.nu_lo if args.nu_lo is not None else w.nu_lo,
+                       nu_hi=args.nu_hi if args.nu_hi is not None else w.nu_hi) for w in wls]
+    wl = wls[0]
+    wname = wname or wl.name
+    if wname == "venus":
+        wname = wl.name
 
     if args.impl == "reference":
         run_reference(args, wl, rank, world)
@@ -215,22 +245,27 @@ def main():
     from paper_2411_03418_gb300 import marfa as M
 
     stream = torch.cuda.current_stream()
-    lines = M.marfa_prepare_lines(wl.lines, wl.species)
-    levels = M.levels_of(wl)
-    rq = M.request_of(wl)
-    npts = M.marfa_num_points(wl.nu_lo, wl.nu_hi)
-    out = torch.empty((wl.n_levels, npts), dtype=torch.float32, device=dev)
+    lines = [M.marfa_prepare_lines(w.lines, w.species) for w in wls]
+    levels = [M.levels_of(w) for w in wls]
+    rqs = [M.request_of(w) for w in wls]
+    npts = [M.marfa_num_points(w.nu_lo, w.nu_hi) for w in wls]
+    outs = [torch.empty((w.n_levels, n), dtype=torch.float32, device=dev) for w, n in zip(wls, npts)]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
 
-    # evaluation count of one step (exact, from the counting variant of the kernels)
-    if args.no_count:
-        counts = np.zeros((wl.n_levels, 11), dtype=np.int64)
-    else:
-        _, counts = M.marfa_diag_absorption_counted(lines, levels, wl.vmr, rq)
-    evals_per_step = int(counts.sum())
+    # evaluation counts of one step (exact, from the counting variant of the kernels)
+    c4 = np.zeros((11, 4), dtype=np.int64)
+    if not args.no_count:
+        for q, w in enumerate(wls):
+            c4 += M.marfa_diag_absorption_counts(lines[q], levels[q], w.vmr, rqs[q])[1].sum(axis=0)
+    counts_grid = c4[:, 0]
+    evals_per_step = int(counts_grid.sum())
+    # algorithmic flops per grid: far-wing, asymptotic-series and polynomial-cell evaluations
+    n_near, n_mid = c4[:, 2], c4[:, 3]
+    n_far = counts_grid - n_near - n_mid
+    flops_grid = FLOPS_FAR * n_far + FLOPS_MID * n_mid + FLOPS_NEAR * n_near
 
     t0 = time.perf_counter()
-    plan = M.marfa_plan_create([lines], [levels], [wl.vmr], [rq], [out], autotune=True, stream=stream)
+    plan = M.marfa_plan_create(lines, levels, [w.vmr for w in wls], rqs, outs, autotune=True, stream=stream)
     plan_s = time.perf_counter() - t0
     variant, tune_ms, _ = M.marfa_plan_info(plan)
 
@@ -268,27 +303,33 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_total = float(tt.item())
     ms_per_step = t_total / args.steps * 1e3
-    units = wl.n_levels * npts * world
+    units = sum(w.n_levels * n for w, n in zip(wls, npts)) * world
     value = units * args.steps / t_total
     evals_s = evals_per_step * world * args.steps / t_total
 
-    # end to end through the public call with host buffers (pinned)
-    rec_h = torch.from_numpy(wl.lines.view(np.uint8)).pin_memory().numpy().view(wl.lines.dtype)
-    out_h = torch.empty((wl.n_levels, npts), dtype=torch.float32).pin_memory().numpy()
+    # end to end through the public call with host buffers (pinned): line records in,
+    # prepare, absorption (batch call for several requests), k(nu) back, every step
+    rec_h = [torch.from_numpy(w.lines.view(np.uint8)).pin_memory().numpy().view(w.lines.dtype) for w in wls]
+    out_h = [torch.empty((w.n_levels, n), dtype=torch.float32).pin_memory().numpy() for w, n in zip(wls, npts)]
+
+    def e2e_step():
+        l2 = [M.marfa_prepare_lines(r, w.species) for r, w in zip(rec_h, wls)]
+        if len(wls) == 1:
+            M.marfa_absorption(l2[0], levels[0], wls[0].vmr, rqs[0], out_h[0], stream)
+        else:
+            M.marfa_absorption_batch(l2, levels, [w.vmr for w in wls], rqs, out_h, stream)
+        for x in l2:
+            M.marfa_free_lines(x)
+
     t_e2e = float("nan")
     if not args.no_e2e:
-        for _ in range(1):
-            l2 = M.marfa_prepare_lines(rec_h, wl.species)
-            M.marfa_absorption(l2, levels, wl.vmr, rq, out_h, stream)
-            M.marfa_free_lines(l2)
+        e2e_step()
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            l2 = M.marfa_prepare_lines(rec_h, wl.species)
-            M.marfa_absorption(l2, levels, wl.vmr, rq, out_h, stream)
-            M.marfa_free_lines(l2)
+            e2e_step()
         torch.cuda.synchronize()
         t_e2e = time.perf_counter() - t0
         if dist:
@@ -301,30 +342,39 @@ def main():
     names = ["level_prep"] + [f"grid{g}" for g in range(1, 11)] + ["finest"]
     dom = int(np.argmax(kms))
     dom_ms = kms[dom] / max(1, klaunch[dom])
-    dom_evals = float(counts[:, dom - 1].sum()) if dom > 0 else 0.0
-    achieved = dom_evals * FLOPS_PER_EVAL / (dom_ms * 1e-3) / 1e12
+    dom_flops = float(flops_grid[dom - 1]) if dom > 0 else 0.0
+    achieved = dom_flops / (dom_ms * 1e-3) / 1e12
     mhz, src = peaks()
     peak = N_SM * FP32_LANES * 2 * mhz * 1e6 / 1e12
 
     surr = None
     wpath = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2411_03418_gb300",
                          "surrogate_weights.npy")
-    if not args.no_surrogate and os.path.exists(wpath):
-        surr = surrogate_leg(args, M, wl, lines, levels, out, flush, stream, wpath, evals_per_step,
-                             ms_per_step, npts, dist, dev)
+    if args.workload == "venus" and not args.no_surrogate and os.path.exists(wpath):
+        surr = surrogate_leg(args, M, wl, lines[0], levels[0], outs[0], flush, stream, wpath, evals_per_step,
+                             ms_per_step, npts[0], dist, dev)
 
     if rank == 0:
+        cfg = {"workload": wname, "requests": len(wls), "lines": int(sum(len(w.lines) for w in wls)),
+               "levels": int(sum(w.n_levels for w in wls)), "points_x_levels_per_step": int(units // world),
+               "l2": "flushed between steps (256 MB write)"}
+        if len(wls) == 1:
+            cfg["npts_per_level"] = npts[0]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": wl.name, "lines": int(len(wl.lines)), "levels": wl.n_levels,
-                       "npts_per_level": npts, "l2": "flushed between steps (256 MB write)"},
+            "config": cfg,
             "line_evals_per_s": evals_s, "line_evals_per_step": evals_per_step,
-            "line_evals_per_grid": [int(v) for v in counts.sum(axis=0)],
+            "line_evals_per_grid": [int(v) for v in counts_grid],
+            "line_evals_class_per_grid": {"poly_cell": [int(v) for v in n_near],
+                                          "asymptotic": [int(v) for v in n_mid]},
+            "fp32_tflops_per_kernel": {n: (float(flops_grid[i - 1]) / (kms[i] / args.steps * 1e-3) / 1e12
+                                           if i > 0 and kms[i] > 0 else None) for i, n in enumerate(names)},
             "e2e": {"value": e2e_value, "unit": UNIT,
-                    "h2d_bytes_per_step": int(wl.lines.nbytes + levels.nbytes + wl.vmr.nbytes),
-                    "d2h_bytes_per_step": int(out_h.nbytes)},
+                    "h2d_bytes_per_step": int(sum(w.lines.nbytes + lv.nbytes + w.vmr.nbytes
+                                                  for w, lv in zip(wls, levels))),
+                    "d2h_bytes_per_step": int(sum(o.nbytes for o in out_h))},
             "gpu_launches": int(klaunch.sum()),
             "plan": {"graph": "one CUDA graph per step (12 kernel launches)", "create_s": plan_s,
                      "variant_grids_1_10": [int(v) for v in variant],
@@ -332,12 +382,13 @@ def main():
             "kernel_ms_per_step": {n: float(kms[i] / args.steps) for i, n in enumerate(names)},
             "roofline": {"bound": "alu", "kernel": names[dom], "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "flops_per_eval": {"far": FLOPS_FAR, "asymptotic": FLOPS_MID, "poly_cell": FLOPS_NEAR},
                          "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz ({src} max clock)"},
             "clocks": clocks,
         }
         if surr is not None:
             line["surrogate"] = surr
-        if not args.no_cpu_baseline and world == 1:
+        if not args.no_cpu_baseline and world == 1 and args.workload == "venus":
             line["cpu_baseline"] = cpu_baseline_sample(wl)
         print(json.dumps(line), flush=True)
     if dist:

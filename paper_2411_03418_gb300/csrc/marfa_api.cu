@@ -840,22 +840,28 @@ static int plan_autotune(marfa_plan_t* X, cudaStream_t st, int* chosen) {
   return r;
 }
 
+// All launches of a plan; with events (inside stream capture) event-record nodes
+// bracket each kernel kind (cudaEventRecordExternal makes them graph nodes that a replay
+// records, rather than capture-internal dependencies).
 static int plan_launch_all(marfa_plan_t* X, cudaStream_t st, bool events) {
-  if (events) cudaEventRecord(X->ev[0], st);
+  auto rec = [&](int k) {
+    if (events) cudaEventRecordWithFlags(X->ev[k], st, cudaEventRecordExternal);
+  };
+  rec(0);
   for (auto& P : X->plans) launch_prep(P, st, false);
-  if (events) cudaEventRecord(X->ev[1], st);
+  rec(1);
   const WorkSet& W = X->W;
-  if (events) cudaEventRecord(X->ev[2], st);
+  rec(2);
   launch_g1(W.drd, W.dgi, (int)W.gi.size(), nullptr, W.surr, st);
-  if (events) cudaEventRecord(X->ev[3], st);
+  rec(3);
   for (int g = 2; g <= kNGrid; ++g) {
-    if (events) cudaEventRecord(X->ev[2 * g], st);
+    rec(2 * g);
     launch_grid(W, g, st);
-    if (events) cudaEventRecord(X->ev[2 * g + 1], st);
+    rec(2 * g + 1);
   }
-  if (events) cudaEventRecord(X->ev[2 * (kNGrid + 1)], st);
+  rec(2 * (kNGrid + 1));
   launch_fine(W.drd, W.dfi, (int)W.fi.size(), nullptr, W.surr, st);
-  if (events) cudaEventRecord(X->ev[2 * (kNGrid + 1) + 1], st);
+  rec(2 * (kNGrid + 1) + 1);
   cudaError_t e = cudaGetLastError();
   if (e) return fail(MARFA_E_CUDA, "plan launches: %s", cudaGetErrorString(e));
   return MARFA_OK;
@@ -950,8 +956,11 @@ extern "C" int marfa_plan_info(const marfa_plan_t* X, int32_t* variant, float* t
     for (int k = 0; k < kKinds; ++k) {
       float ms = 0;
       cudaError_t e;
-      if ((e = cudaEventSynchronize(X->ev[2 * k + 1])) || (e = cudaEventElapsedTime(&ms, X->ev[2 * k], X->ev[2 * k + 1])))
+      if ((e = cudaEventSynchronize(X->ev[2 * k + 1])) ||
+          (e = cudaEventElapsedTime(&ms, X->ev[2 * k], X->ev[2 * k + 1]))) {
+        cudaGetLastError();  // not a sticky error: clear it for later calls
         return fail(MARFA_E_CUDA, "plan kernel times: %s", cudaGetErrorString(e));
+      }
       kernel_ms[k] = ms;
     }
   }

@@ -290,11 +290,13 @@ __device__ __forceinline__ void count_eval(bool voigt, float x, float y, int64_t
   }
 }
 
-// Launch a surrogate-capable kernel with the network weights in dynamic shared memory.
+// Launch a surrogate-capable kernel with the network weights and one queue per warp in
+// dynamic shared memory.
 template <class... KA, class... A>
 static void launch_surr(void (*k)(KA...), int n_items, int threads, cudaStream_t st, A... args) {
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MlpWeights));
-  k<<<n_items, threads, sizeof(MlpWeights), st>>>(args...);
+  const size_t bytes = sizeof(MlpWeights) + (size_t)(threads / 32) * sizeof(SurrQueue);
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  k<<<n_items, threads, bytes, st>>>(args...);
 }
 
 // ------------------------------------------------------------------ K1: level prep
@@ -420,33 +422,30 @@ __device__ __noinline__ float2 g1_exact_pair(const ReqDev& R, int64_t o, int64_t
   return make_float2(v[0], v[1]);
 }
 
-// g1_exact_pair for a converged warp with the surrogate under its guard.
-__device__ __noinline__ float2 g1_exact_pair_coll(const ReqDev& R, int64_t o, int64_t X0, int j0,
-                                                 bool need0, bool need1, const MlpWeights& S,
-                                                 int64_t& n_mlp, int& n_near, int& n_mid) {
+// The exact-path nodes j0, j0 + 1 of a grid-1 line for the surrogate variant: x at both
+// nodes, y, and the weights amp * chi.
+struct G1Nodes {
+  float x0, x1, y, w0, w1;
+};
+__device__ __noinline__ G1Nodes g1_exact_nodes(const ReqDev& R, int64_t o, int64_t X0, int j0) {
   const int sh = panel_shift(1) - 1;
   const int64_t c = __ldg(R.c + o);
-  const float amp = __ldg(R.amp + o), sx = __ldg(R.sx + o), y = __ldg(R.yv + o);
+  const float amp = __ldg(R.amp + o), sx = __ldg(R.sx + o);
   const bool use_chi = (__ldg(R.flags + o) & 1) && R.shape < kShapeConst;
   NodeX nx;
   nx.init(X0 - c, sh, sx);
-  ChiThr ct;
-  if (use_chi) ct.init(c, X0, sh);
-  float v[2];
-#pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    const int j = j0 + q;
-    const float jf = (float)j;
-    const bool need = q ? need1 : need0;
-    const float xv = nx.x(jf);
-    float f = amp * voigt_K_coll<false>(xv, y, need, kVoigtCells, S, n_mlp);
-    if (use_chi && need) f *= ct.value(j, nx.absd(jf, sh));
-    v[q] = need ? f : 0.0f;
-    const int cl = need ? voigt_class(xv, y) : 0;
-    n_near += cl == 2 ? 1 : 0;
-    n_mid += cl == 1 ? 1 : 0;
+  G1Nodes r;
+  r.y = __ldg(R.yv + o);
+  r.x0 = nx.x((float)j0);
+  r.x1 = nx.x((float)(j0 + 1));
+  r.w0 = r.w1 = amp;
+  if (use_chi) {
+    ChiThr ct;
+    ct.init(c, X0, sh);
+    r.w0 = amp * ct.value(j0, nx.absd((float)j0, sh));
+    r.w1 = amp * ct.value(j0 + 1, nx.absd((float)(j0 + 1), sh));
   }
-  return make_float2(v[0], v[1]);
+  return r;
 }
 
 __device__ __forceinline__ void comp_merge(float& s, float& c, float s2, float c2) {
@@ -461,7 +460,7 @@ template <bool COUNT, bool SURR>
 __global__ void __launch_bounds__(kG1Warps * 32)
     k_g1(const ReqDev* __restrict__ reqs, const G1Item* __restrict__ items,
          int64_t* __restrict__ counts) {
-  extern __shared__ __align__(16) unsigned char dsm[];  // surrogate weights (SURR only)
+  extern __shared__ __align__(16) unsigned char dsm[];  // surrogate weights and queues (SURR only)
   MlpWeights& S = *reinterpret_cast<MlpWeights*>(dsm);
   __shared__ float4 sA[kG1Batch];               // q, sx, phi*sx, y^2
   __shared__ float4 sB[kG1Batch];               // a_centre, a_left, a_right, -y^2/2
@@ -501,6 +500,7 @@ __global__ void __launch_bounds__(kG1Warps * 32)
   float eS = 0.f, eC = 0.f, lS = 0.f, lC = 0.f, rS = 0.f, rC = 0.f, mS = 0.f, mC = 0.f;
   int64_t nev = 0, nmlp = 0, nnear = 0, nmid = 0;
   if (use_mlp) __syncthreads();
+  int qn = 0;  // entries in this warp's surrogate queue (warp-uniform)
 
   for (int64_t b0 = i_lo; b0 < i_hi; b0 += kG1Batch) {
     const int nbat = (int)min((int64_t)kG1Batch, i_hi - b0);
@@ -548,6 +548,13 @@ __global__ void __launch_bounds__(kG1Warps * 32)
     }
     __syncthreads();
     float pe = 0.f, pl = 0.f, pr = 0.f, pm = 0.f;
+    // surrogate results: tag bit 0 odd node; bits 1, 2 the even node's L and R slots
+    auto g1_apply = [&](int tag, float v) {
+      if (tag & 1) pm += v;
+      else if ((tag & 6) == 6) pe += v;
+      else if (tag & 2) pl += v;
+      else pr += v;
+    };
     for (int k = warp; k < nbat; k += kG1Warps) {
       const int4 C = sC[k];
       if ((C.z & 3) == 2) {
@@ -568,18 +575,18 @@ __global__ void __launch_bounds__(kG1Warps * 32)
       const uint64_t msk = sM[k];
       const bool bL = (msk >> (p + 1)) & 1ull;  // panel m0+p: L of node 2m, M of node 2m+1
       const bool bR = (msk >> p) & 1ull;        // panel m0+p-1: R of node 2m
-      if (use_mlp && (C.z & 1)) {  // exact path, warp-uniform: every lane takes part
-        int nn = 0, nm = 0;
-        const float2 v = g1_exact_pair_coll(R, off + b0 + k, X0, j0, bL || bR, bL, S, nmlp, nn, nm);
-        if (bL || bR) {
-          if (bL && bR) pe += v.x; else if (bL) pl += v.x; else pr += v.x;
-          pm += v.y;
-          if (COUNT) {
-            nev += 1 + (bL ? 1 : 0);
-            nnear += nn;
-            nmid += nm;
-          }
-        }
+      if (SURR && use_mlp && (C.z & 1)) {  // exact path, warp-uniform: every lane takes part
+        if (qn > kQCap - 64) q_flush(warp_queue(dsm), qn, S, g1_apply);
+        const G1Nodes nd = g1_exact_nodes(R, off + b0 + k, X0, j0);
+        const bool a0 = bL || bR, a1 = bL;
+        const bool u0 = a0 && mlp_guard(S, nd.x0, nd.y), u1 = a1 && mlp_guard(S, nd.x1, nd.y);
+        q_push(warp_queue(dsm), qn, u0, nd.x0, nd.y, nd.w0, (bL ? 2 : 0) | (bR ? 4 : 0));
+        q_push(warp_queue(dsm), qn, u1, nd.x1, nd.y, nd.w1, 1);
+        if (a0 && !u0) g1_apply((bL ? 2 : 0) | (bR ? 4 : 0), nd.w0 * voigt_K(nd.x0, nd.y));
+        if (a1 && !u1) g1_apply(1, nd.w1 * voigt_K(nd.x1, nd.y));
+        if (a0) count_eval<COUNT>(true, nd.x0, nd.y, nev, nnear, nmid);
+        if (a1) count_eval<COUNT>(true, nd.x1, nd.y, nev, nnear, nmid);
+        if (COUNT) nmlp += (u0 ? 1 : 0) + (u1 ? 1 : 0);
         continue;
       }
       if (!(bL || bR)) continue;
@@ -610,6 +617,7 @@ __global__ void __launch_bounds__(kG1Warps * 32)
       pm += v1;
       if (COUNT) nev += 1 + (bL ? 1 : 0);
     }
+    if (SURR && use_mlp) q_flush(warp_queue(dsm), qn, S, g1_apply);
     kahan_add(eS, eC, pe);
     kahan_add(lS, lC, pl);
     kahan_add(rS, rC, pr);
@@ -714,12 +722,24 @@ __global__ void __launch_bounds__(kLWarps * 32)
     mlp_load_smem(S, R.mlp);
     __syncthreads();
   }
+  int qn = 0;  // entries in this warp's surrogate queue (warp-uniform)
+  // surrogate results: tag bits 0-4 pair, 5 L slot, 6 R slot, 7 odd node (M slot)
+  auto lm_apply = [&](int tag, float v) {
+    const int p = tag & 31;
+    if (tag & 128) {
+      accM[warp][p][lane] += v;
+    } else {
+      if (tag & 32) accL[warp][p][lane] += v;
+      if (tag & 64) accR[warp][p][lane] += v;
+    }
+  };
   __syncwarp();
   for (int r = 0; r < bd.n; ++r) {
     for (int64_t i0 = bd.lo[r]; i0 < bd.hi[r]; i0 += kLWarps * 32) {
       const int64_t i = i0 + tid;
-      if (use_mlp) {
-        // all lanes step through the union of their pair ranges together
+      if (SURR && use_mlp) {
+        // all lanes step through the union of their pair ranges together; evaluations
+        // that pass the guard go to the warp's queue
         uint64_t own = 0;
         int64_t c = 0;
         bool chi = false;
@@ -746,22 +766,30 @@ __global__ void __launch_bounds__(kLWarps * 32)
         }
         const int qa = __reduce_min_sync(0xffffffffu, pa), qb = __reduce_max_sync(0xffffffffu, pb);
         for (int p = qa; p <= qb; ++p) {
+          if (qn > kQCap - 64) q_flush(warp_queue(dsm), qn, S, lm_apply);
           const bool bR = (own >> p) & 1ull, bL = (own >> (p + 1)) & 1ull;
+          const bool ae = bR || bL, ao = bL;
           const float jf = (float)(2 * p);
           const float xe = nx.x(jf), xo = nx.x(jf + 1.0f);
-          const float ke = voigt_K_coll<false>(xe, y, bR || bL, kVoigtCells, S, nmlp);
-          const float ko = voigt_K_coll<false>(xo, y, bL, kVoigtCells, S, nmlp);
-          if (bR || bL) count_eval<COUNT>(true, xe, y, nev, nnear, nmid);
-          if (bL) count_eval<COUNT>(true, xo, y, nev, nnear, nmid);
-          float v = amp * ke;
-          if (use_chi && (bR || bL)) v *= ct.value(2 * p, nx.absd(jf, s - 1));
-          if (bL) accL[warp][p][lane] += v;
-          if (bR) accR[warp][p][lane] += v;
-          if (bL) {
-            float w = amp * ko;
-            if (use_chi) w *= ct.value(2 * p + 1, nx.absd(jf + 1.0f, s - 1));
-            accM[warp][p][lane] += w;
+          const bool ue = ae && mlp_guard(S, xe, y), uo = ao && mlp_guard(S, xo, y);
+          const float ce = (use_chi && ae) ? ct.value(2 * p, nx.absd(jf, s - 1)) : 1.0f;
+          const float co = (use_chi && ao) ? ct.value(2 * p + 1, nx.absd(jf + 1.0f, s - 1)) : 1.0f;
+          const int te = p | (bL ? 32 : 0) | (bR ? 64 : 0), to = p | 128;
+          q_push(warp_queue(dsm), qn, ue, xe, y, amp * ce, te);
+          q_push(warp_queue(dsm), qn, uo, xo, y, amp * co, to);
+          if (ae && !ue) {
+            float v = amp * voigt_K(xe, y);
+            if (use_chi) v *= ce;
+            lm_apply(te, v);
           }
+          if (ao && !uo) {
+            float w = amp * voigt_K(xo, y);
+            if (use_chi) w *= co;
+            lm_apply(to, w);
+          }
+          if (ae) count_eval<COUNT>(true, xe, y, nev, nnear, nmid);
+          if (ao) count_eval<COUNT>(true, xo, y, nev, nnear, nmid);
+          if (COUNT) nmlp += (ue ? 1 : 0) + (uo ? 1 : 0);
         }
         continue;
       }
@@ -803,6 +831,7 @@ __global__ void __launch_bounds__(kLWarps * 32)
       }
     }
   }
+  if (SURR && use_mlp) q_flush(warp_queue(dsm), qn, S, lm_apply);
   __syncthreads();
   // thread t < 3 kLPairs sums slot (t / kLPairs, pair t % kLPairs) over warps and lanes
   if (tid < 3 * kLPairs) {
@@ -893,6 +922,12 @@ __global__ void __launch_bounds__(kCWarps * 32)
     float (*bE)[kCPairs + 1] = bufE[warp];
     float (*bO)[kCPairs + 1] = bufO[warp];
     unsigned long long* mk = smsk[warp];
+    int qn = 0;  // entries in this warp's surrogate queue (warp-uniform)
+    // surrogate results: tag bits 0-4 pair, bit 5 odd node
+    auto tp_apply = [&](int tag, float v) {
+      if (tag & 32) bO[lane][tag & 31] = v;
+      else bE[lane][tag & 31] = v;
+    };
     for (int r = 0; r < bd.n; ++r) {
       for (int64_t i0 = bd.lo[r]; i0 < bd.hi[r]; i0 += 32) {
         const int64_t i = i0 + lane;
@@ -909,8 +944,9 @@ __global__ void __launch_bounds__(kCWarps * 32)
         const uint32_t any = __ballot_sync(0xffffffffu, own != 0);
         if (!any) continue;
         // phase 1: this lane's line at the nodes of its owned panels
-        if (use_mlp) {
-          // all lanes step through the union of their pair ranges together
+        if (SURR && use_mlp) {
+          // all lanes step through the union of their pair ranges together; evaluations
+          // that pass the guard go to the warp's queue, flushed before phase 2
           float amp = 0.0f, y = 1.0f;
           NodeX nx;
           nx.qf = nx.hs = nx.phs = nx.phi = 0.0f;
@@ -927,24 +963,31 @@ __global__ void __launch_bounds__(kCWarps * 32)
           }
           const int qa = __reduce_min_sync(0xffffffffu, pa), qb = __reduce_max_sync(0xffffffffu, pb);
           for (int q = qa; q <= qb; ++q) {
+            if (qn > kQCap - 64) q_flush(warp_queue(dsm), qn, S, tp_apply);
             const bool bR = (own >> q) & 1ull, bL = (own >> (q + 1)) & 1ull;
+            const bool ae = bR || bL, ao = bL;
             const float jf = (float)(2 * q);
             const float xv = nx.x(jf), xw = nx.x(jf + 1.0f);
-            const float ke = voigt_K_coll<true>(xv, y, bR || bL, stab, S, nmlp);
-            const float ko = voigt_K_coll<true>(xw, y, bL, stab, S, nmlp);
-            if (bR || bL) {
-              float v = amp * ke;
-              if (use_chi) v *= ct.value(2 * q, nx.absd(jf, s - 1));
+            const bool ue = ae && mlp_guard(S, xv, y), uo = ao && mlp_guard(S, xw, y);
+            const float ce = (use_chi && ae) ? ct.value(2 * q, nx.absd(jf, s - 1)) : 1.0f;
+            const float co = (use_chi && ao) ? ct.value(2 * q + 1, nx.absd(jf + 1.0f, s - 1)) : 1.0f;
+            q_push(warp_queue(dsm), qn, ue, xv, y, amp * ce, q);
+            q_push(warp_queue(dsm), qn, uo, xw, y, amp * co, q | 32);
+            if (ae && !ue) {
+              float v = amp * voigt_K<true>(xv, y, stab);
+              if (use_chi) v *= ce;
               bE[lane][q] = v;
-              count_eval<COUNT>(true, xv, y, nev, nnear, nmid);
             }
-            if (bL) {
-              float w = amp * ko;
-              if (use_chi) w *= ct.value(2 * q + 1, nx.absd(jf + 1.0f, s - 1));
+            if (ao && !uo) {
+              float w = amp * voigt_K<true>(xw, y, stab);
+              if (use_chi) w *= co;
               bO[lane][q] = w;
-              count_eval<COUNT>(true, xw, y, nev, nnear, nmid);
             }
+            if (ae) count_eval<COUNT>(true, xv, y, nev, nnear, nmid);
+            if (ao) count_eval<COUNT>(true, xw, y, nev, nnear, nmid);
+            if (COUNT) nmlp += (ue ? 1 : 0) + (uo ? 1 : 0);
           }
+          q_flush(warp_queue(dsm), qn, S, tp_apply);
         } else if (own) {
           const float amp = __ldg(R.amp + lo_off + i);
           const float sx = __ldg(R.sx + lo_off + i);
@@ -1063,6 +1106,13 @@ __global__ void __launch_bounds__(kFineThreads)
   for (int q = 0; q < kFinePerThread; ++q) acc[q] = cmp[q] = 0.0f;
   int64_t nev = 0, nmlp = 0, nnear = 0, nmid = 0;
   const int nw = kFinePerThread * 32;  // nodes of the warp
+  int qn = 0;  // entries in this warp's surrogate queue (warp-uniform)
+  // surrogate results: the tag is the node q of the owning lane
+  auto fine_apply = [&](int tag, float v) {
+#pragma unroll
+    for (int q = 0; q < kFinePerThread; ++q)
+      if (tag == q) kahan_add(acc[q], cmp[q], v);
+  };
   const int wlo = (int)max(R.k_lo - kw, (int64_t)0);
   const int whi = (int)min(R.k_hi - kw, (int64_t)(nw - 1));
   if (wlo <= whi) {  // warp-uniform
@@ -1128,10 +1178,11 @@ __global__ void __launch_bounds__(kFineThreads)
           const int e = __ffs(rem) - 1;
           mine |= ((sPm[warp][e] >> mypanel) & 1u) << e;
         }
-        if (use_mlp) {
-          // the warp steps through the lanes' lists together, one staged line per lane
-          // and round, so that the surrogate can evaluate 32 inputs at once
+        if (SURR && use_mlp) {
+          // the warp steps through the lanes' lists together, one staged line per lane and
+          // round; evaluations that pass the guard go to the warp's queue
           while (__any_sync(0xffffffffu, mine != 0)) {
+            if (qn > kQCap - 32 * kFinePerThread) q_flush(warp_queue(dsm), qn, S, fine_apply);
             int e = -1;
             if (mine) {
               e = __ffs(mine) - 1;
@@ -1153,12 +1204,16 @@ __global__ void __launch_bounds__(kFineThreads)
               const bool act = j >= klo_e && j <= khi_e;
               const float jf = (float)j;
               const float xv = fmaf(jf + qf, hs, phs);
-              float v = amp * voigt_K_coll<true>(xv, y, act, stab, S, nmlp);
-              if (act) {
-                if (uc) v *= ct.value(j, fabsf((jf + qf) + phi) * ldexpf(1.0f, -kFineBits));
+              const bool use = act && mlp_guard(S, xv, y);
+              const float cv = (act && uc) ? ct.value(j, fabsf((jf + qf) + phi) * ldexpf(1.0f, -kFineBits)) : 1.0f;
+              q_push(warp_queue(dsm), qn, use, xv, y, amp * cv, q);
+              if (act && !use) {
+                float v = amp * voigt_K<true>(xv, y, stab);
+                if (uc) v *= cv;
                 kahan_add(acc[q], cmp[q], v);
-                count_eval<COUNT>(true, xv, y, nev, nnear, nmid);
               }
+              if (act) count_eval<COUNT>(true, xv, y, nev, nnear, nmid);
+              if (COUNT && use) ++nmlp;
             }
           }
         }
@@ -1190,6 +1245,7 @@ __global__ void __launch_bounds__(kFineThreads)
       }
     }
   }
+  if (SURR && use_mlp) q_flush(warp_queue(dsm), qn, S, fine_apply);  // warp-uniform
   uint32_t valid = 0;
 #pragma unroll
   for (int q = 0; q < kFinePerThread; ++q)

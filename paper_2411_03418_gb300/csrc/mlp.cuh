@@ -55,104 +55,80 @@ __device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// One 64 -> 64 layer for 32 samples: in = A fragments [2 m-tiles][4 k-tiles][4 regs],
+// One 64 -> 64 layer for one m-tile of 16 samples: in = A fragments [4 k-tiles][4 regs],
 // W rows [out][kWStride] in BF16, bias FP32. Accumulators start at the bias; the
-// callback f(nt, d) consumes n-tile nt (columns 8nt + 2t, +1; rows g, g + 8).
+// callback f(nt, d) consumes n-tile nt (columns 8nt + 2t, +1 of rows g, g + 8).
 template <class F>
-__device__ __forceinline__ void mlp_layer(const uint32_t (&in)[2][4][4], const uint16_t* W,
-                                          const float* b, int lane, F&& f) {
+__device__ __forceinline__ void mlp_layer(const uint32_t (&in)[4][4], const uint16_t* W, const float* b,
+                                          int lane, F&& f) {
   const int g = lane >> 2, t = lane & 3;
 #pragma unroll
   for (int nt = 0; nt < 8; ++nt) {
-    float d[2][4];
     const float bl = b[8 * nt + 2 * t], bh = b[8 * nt + 2 * t + 1];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-      d[mt][0] = bl; d[mt][1] = bh; d[mt][2] = bl; d[mt][3] = bh;
-    }
+    float d[4] = {bl, bh, bl, bh};
     const uint16_t* wr = W + (8 * nt + g) * kWStride + 2 * t;
 #pragma unroll
     for (int kt = 0; kt < 4; ++kt) {
       const uint32_t b0 = *reinterpret_cast<const uint32_t*>(wr + 16 * kt);
       const uint32_t b1 = *reinterpret_cast<const uint32_t*>(wr + 16 * kt + 8);
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt) mma16816(d[mt], in[mt][kt], b0, b1);
+      mma16816(d, in[kt], b0, b1);
     }
     f(nt, d);
   }
 }
 
-// Surrogate K(x, y) for the 32 lanes of a converged warp, one input per lane.
+// Surrogate K(x, y) for the 32 lanes of a converged warp, one input per lane. The two
+// m-tiles (samples 0-15 and 16-31) go through the network one after the other, which
+// keeps a tile's activations (16 + 16 registers) the only large live state.
 static __device__ __noinline__ float mlp_warp_K(const MlpWeights& S, float x, float y) {
   const int lane = threadIdx.x & 31;
   const int g = lane >> 2, t = lane & 3;
   const float ax = fabsf(x);
   const float u1 = __logf(y);
   const float u2 = __logf(1.0f + __fdividef(ax, 1.0f + y));
-  // the inputs of A-fragment rows g and g + 8 of m-tile mt: samples 16 mt + g (+ 8)
-  float su1[2][2], su2[2][2];
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      su1[mt][r] = __shfl_sync(0xffffffffu, u1, 16 * mt + g + 8 * r);
-      su2[mt][r] = __shfl_sync(0xffffffffu, u2, 16 * mt + g + 8 * r);
-    }
-  // layer 1 into A fragments: k-tile kt holds hidden units 16kt + 2t + {0, 1} (regs 0, 1)
-  // and 16kt + 8 + 2t + {0, 1} (regs 2, 3); reg parity picks row g or g + 8.
-  uint32_t a1[2][4][4];
-#pragma unroll
-  for (int kt = 0; kt < 4; ++kt)
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const int c0 = 16 * kt + 8 * half + 2 * t;
-      const float w00 = S.w1[2 * c0], w01 = S.w1[2 * c0 + 1], bb0 = S.b1[c0];
-      const float w10 = S.w1[2 * c0 + 2], w11 = S.w1[2 * c0 + 3], bb1 = S.b1[c0 + 1];
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-          const float z0 = fmaf(w00, su1[mt][r], fmaf(w01, su2[mt][r], bb0));
-          const float z1 = fmaf(w10, su1[mt][r], fmaf(w11, su2[mt][r], bb1));
-          a1[mt][kt][2 * half + r] = pack_bf16(mlp_silu_bf(z0), mlp_silu_bf(z1));
-        }
-    }
-  // layer 2: the outputs of n-tile nt are k-tile nt / 2, half nt % 2 of layer 3's input
-  uint32_t a2[2][4][4];
-  mlp_layer(a1, S.w2, S.b2, lane, [&](int nt, float (&d)[2][4]) {
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-      a2[mt][nt >> 1][(nt & 1) ? 2 : 0] = pack_bf16(mlp_silu_bf(d[mt][0]), mlp_silu_bf(d[mt][1]));
-      a2[mt][nt >> 1][(nt & 1) ? 3 : 1] = pack_bf16(mlp_silu_bf(d[mt][2]), mlp_silu_bf(d[mt][3]));
-    }
-  });
-  // layer 3 and the output layer: per-lane partial dot products with W4 in FP32
-  float part[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
-  mlp_layer(a2, S.w3, S.b3, lane, [&](int nt, float (&d)[2][4]) {
-    const float wl = S.w4[8 * nt + 2 * t], wh = S.w4[8 * nt + 2 * t + 1];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-      part[mt][0] = fmaf(wl, mlp_silu_acc(d[mt][0]), fmaf(wh, mlp_silu_acc(d[mt][1]), part[mt][0]));
-      part[mt][1] = fmaf(wl, mlp_silu_acc(d[mt][2]), fmaf(wh, mlp_silu_acc(d[mt][3]), part[mt][1]));
-    }
-  });
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      part[mt][r] += __shfl_xor_sync(0xffffffffu, part[mt][r], 1);
-      part[mt][r] += __shfl_xor_sync(0xffffffffu, part[mt][r], 2);
-    }
-  // sample s = 16 mt + 8 r + gg sits in part[mt][r] of lanes 4gg .. 4gg + 3
-  const int smt = lane >> 4, sr = (lane >> 3) & 1, sg = lane & 7;
   float tv = 0.0f;
+#pragma unroll 1
+  for (int mt = 0; mt < 2; ++mt) {
+    // inputs of A-fragment rows g and g + 8: samples 16 mt + g (+ 8)
+    const float p0 = __shfl_sync(0xffffffffu, u1, 16 * mt + g), q0 = __shfl_sync(0xffffffffu, u2, 16 * mt + g);
+    const float p1 = __shfl_sync(0xffffffffu, u1, 16 * mt + g + 8), q1 = __shfl_sync(0xffffffffu, u2, 16 * mt + g + 8);
+    // layer 1 into A fragments: k-tile kt holds hidden units 16kt + 2t + {0, 1} (regs 0, 1)
+    // and 16kt + 8 + 2t + {0, 1} (regs 2, 3); reg parity picks row g or g + 8
+    uint32_t a1[4][4];
 #pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
+    for (int kt = 0; kt < 4; ++kt)
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const float v = __shfl_sync(0xffffffffu, part[mt][r], 4 * sg);
-      if (mt == smt && r == sr) tv = v;
-    }
+      for (int half = 0; half < 2; ++half) {
+        const int c0 = 16 * kt + 8 * half + 2 * t;
+        const float w00 = S.w1[2 * c0], w01 = S.w1[2 * c0 + 1], bb0 = S.b1[c0];
+        const float w10 = S.w1[2 * c0 + 2], w11 = S.w1[2 * c0 + 3], bb1 = S.b1[c0 + 1];
+        a1[kt][2 * half] = pack_bf16(mlp_silu_bf(fmaf(w00, p0, fmaf(w01, q0, bb0))),
+                                     mlp_silu_bf(fmaf(w10, p0, fmaf(w11, q0, bb1))));
+        a1[kt][2 * half + 1] = pack_bf16(mlp_silu_bf(fmaf(w00, p1, fmaf(w01, q1, bb0))),
+                                         mlp_silu_bf(fmaf(w10, p1, fmaf(w11, q1, bb1))));
+      }
+    // layer 2: the outputs of n-tile nt are k-tile nt / 2, half nt % 2 of layer 3's input
+    uint32_t a2[4][4];
+    mlp_layer(a1, S.w2, S.b2, lane, [&](int nt, float (&d)[4]) {
+      a2[nt >> 1][(nt & 1) ? 2 : 0] = pack_bf16(mlp_silu_bf(d[0]), mlp_silu_bf(d[1]));
+      a2[nt >> 1][(nt & 1) ? 3 : 1] = pack_bf16(mlp_silu_bf(d[2]), mlp_silu_bf(d[3]));
+    });
+    // layer 3 and the output layer: per-lane partial dot products with W4 in FP32
+    float part0 = 0.0f, part1 = 0.0f;
+    mlp_layer(a2, S.w3, S.b3, lane, [&](int nt, float (&d)[4]) {
+      const float wl = S.w4[8 * nt + 2 * t], wh = S.w4[8 * nt + 2 * t + 1];
+      part0 = fmaf(wl, mlp_silu_acc(d[0]), fmaf(wh, mlp_silu_acc(d[1]), part0));
+      part1 = fmaf(wl, mlp_silu_acc(d[2]), fmaf(wh, mlp_silu_acc(d[3]), part1));
+    });
+    part0 += __shfl_xor_sync(0xffffffffu, part0, 1);
+    part0 += __shfl_xor_sync(0xffffffffu, part0, 2);
+    part1 += __shfl_xor_sync(0xffffffffu, part1, 1);
+    part1 += __shfl_xor_sync(0xffffffffu, part1, 2);
+    // sample 16 mt + 8 r + gg sits in part_r of lanes 4gg .. 4gg + 3
+    const float v0 = __shfl_sync(0xffffffffu, part0, 4 * (lane & 7));
+    const float v1 = __shfl_sync(0xffffffffu, part1, 4 * (lane & 7));
+    if ((lane >> 4) == mt) tv = ((lane >> 3) & 1) ? v1 : v0;
+  }
   tv += S.b4;
   return mlp_baseline_fast(x, y) * __expf(tv);
 }
@@ -185,6 +161,63 @@ __host__ __device__ __forceinline__ int mlp_guard_cell(float x, float y) {
 __device__ __forceinline__ bool mlp_guard(const MlpWeights& S, float x, float y) {
   const int c = mlp_guard_cell(x, y);
   return c >= 0 && ((S.guard[c >> 5] >> (c & 31)) & 1u);
+}
+
+// ------------------------------------------------------------------ per-warp queue
+// The profile kernels do not call the network where an evaluation passes the guard:
+// they push (x, y, weight, tag) into their warp's queue in shared memory and go on with
+// the plain evaluations. When the queue is nearly full, and wherever the kernel needs
+// the results, the warp flushes it: the network runs on full batches of 32 entries, and
+// each lane then applies the results of its own entries, in queue order, through the
+// kernel's callback (weight x K, tag says where it goes). All calls are warp-collective.
+constexpr int kQCap = 256;
+struct SurrQueue {
+  float x[kQCap], y[kQCap], w[kQCap], r[kQCap];
+  uint16_t tag[kQCap];
+  uint8_t owner[kQCap];
+};
+
+__device__ __forceinline__ void q_push(SurrQueue& Q, int& n, bool want, float x, float y, float w,
+                                       int tag) {
+  const int lane = threadIdx.x & 31;
+  const unsigned b = __ballot_sync(0xffffffffu, want);
+  if (want) {
+    const int pos = n + __popc(b & ((1u << lane) - 1u));
+    Q.x[pos] = x;
+    Q.y[pos] = y;
+    Q.w[pos] = w;
+    Q.tag[pos] = (uint16_t)tag;
+    Q.owner[pos] = (uint8_t)lane;
+  }
+  n += __popc(b);
+}
+
+template <class Apply>
+__device__ __forceinline__ void q_flush(SurrQueue& Q, int& n, const MlpWeights& S, Apply&& apply) {
+  if (n == 0) return;  // n is warp-uniform
+  const int lane = threadIdx.x & 31;
+  __syncwarp();
+  for (int b = 0; b < n; b += 32) {
+    const int i = b + lane;
+    const bool act = i < n;
+    const float k = mlp_warp_K(S, act ? Q.x[i] : 0.0f, act ? Q.y[i] : 1.0f);
+    if (act) Q.r[i] = k * Q.w[i];
+  }
+  __syncwarp();
+  for (int i = 0; i < n; ++i)
+    if (Q.owner[i] == lane) apply((int)Q.tag[i], Q.r[i]);
+  __syncwarp();
+  n = 0;
+}
+
+// Dynamic shared memory of a surrogate-capable kernel with NW warps: the weights, then
+// one queue per warp.
+template <int NW>
+constexpr size_t surr_smem_bytes() {
+  return sizeof(MlpWeights) + (size_t)NW * sizeof(SurrQueue);
+}
+__device__ __forceinline__ SurrQueue& warp_queue(unsigned char* dsm) {
+  return reinterpret_cast<SurrQueue*>(dsm + sizeof(MlpWeights))[threadIdx.x >> 5];
 }
 
 // The Voigt K for a converged warp: the surrogate for the lanes whose (x, y) passes the
