@@ -40,9 +40,9 @@ METRIC = "spectral pts x levels/s and line-evals/s, MLP-Voigt vs plain at <=1e-3
 UNIT = "pts*levels/s"
 # FP32 flops of one profile evaluation by Voigt cost class, counted from the formulas
 # (x, the profile, amplitude, chi-factor and the compensated add): far-wing two-term
-# series, 6/15-term asymptotic series (the 6-term count is used for both), polynomial
-# cell (9 x 9 bivariate Horner plus the Gaussian term).
-FLOPS_FAR, FLOPS_MID, FLOPS_NEAR = 20.0, 70.0, 200.0
+# series, 6/15-term asymptotic series (the 6-term count is used for both), 9 x 9
+# polynomial cell plus the Gaussian term, small-y cell (6 x 4 terms) plus the Gaussian term.
+FLOPS_FAR, FLOPS_MID, FLOPS_NEAR, FLOPS_SMALL = 20.0, 70.0, 200.0, 90.0
 N_SM = 152
 FP32_LANES = 128
 
@@ -144,10 +144,10 @@ def surrogate_leg(args, M, wl, lines, levels, out, flush, stream, wpath, evals_p
         plain = out.clone()
         rq_s = M.request_of(wl.with_(surrogate=1))
         if args.no_count:
-            c4 = np.zeros((wl.n_levels, 11, 4), dtype=np.int64)
+            c5 = np.zeros((wl.n_levels, 11, 5), dtype=np.int64)
         else:
-            _, c4 = M.marfa_diag_absorption_counts(lines, levels, wl.vmr, rq_s)
-        counts, sc = c4[:, :, 0], c4[:, :, 1]
+            _, c5 = M.marfa_diag_absorption_counts(lines, levels, wl.vmr, rq_s)
+        counts, sc = c5[:, :, 0], c5[:, :, 1]
         plan = M.marfa_plan_create([lines], [levels], [wl.vmr], [rq_s], [out], autotune=True, stream=stream)
         for _ in range(args.warmup):
             M.marfa_plan_execute(plan, stream)
@@ -253,20 +253,20 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
 
     # evaluation counts of one step (exact, from the counting variant of the kernels)
-    c4 = np.zeros((11, 4), dtype=np.int64)
+    c5 = np.zeros((11, 5), dtype=np.int64)
     if not args.no_count:
         for q, w in enumerate(wls):
-            c4 += M.marfa_diag_absorption_counts(lines[q], levels[q], w.vmr, rqs[q])[1].sum(axis=0)
-    counts_grid = c4[:, 0]
+            c5 += M.marfa_diag_absorption_counts(lines[q], levels[q], w.vmr, rqs[q])[1].sum(axis=0)
+    counts_grid = c5[:, 0]
     evals_per_step = int(counts_grid.sum())
-    # algorithmic flops per grid: far-wing, asymptotic-series and polynomial-cell evaluations
-    n_near, n_mid = c4[:, 2], c4[:, 3]
-    n_far = counts_grid - n_near - n_mid
-    flops_grid = FLOPS_FAR * n_far + FLOPS_MID * n_mid + FLOPS_NEAR * n_near
+    # algorithmic flops per grid by Voigt cost class
+    n_near, n_mid, n_small = c5[:, 2], c5[:, 3], c5[:, 4]
+    n_far = counts_grid - n_near - n_mid - n_small
+    flops_grid = FLOPS_FAR * n_far + FLOPS_MID * n_mid + FLOPS_NEAR * n_near + FLOPS_SMALL * n_small
 
     t0 = time.perf_counter()
     plan = M.marfa_plan_create(lines, levels, [w.vmr for w in wls], rqs, outs, autotune=True, stream=stream)
-    plan_s = time.perf_counter() - t0
+    plan_s_create = time.perf_counter() - t0
     variant, tune_ms, _ = M.marfa_plan_info(plan)
 
     def step():
@@ -281,14 +281,12 @@ def main():
     clk_path = os.path.join(tempfile.gettempdir(), f"marfa_clocks_{os.getpid()}.csv")
     sampler, fh = start_clock_sampler(clk_path)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    kms = np.zeros(12)
     torch.cuda.synchronize()
     for i in range(args.steps):
         flush.fill_(float(i))  # L2 flush between steps, outside the timed events
         ev[i][0].record(stream)
         step()
         ev[i][1].record(stream)
-        kms += M.marfa_plan_info(plan, kernel_ms=True)[2]  # waits for this step's kernels
     torch.cuda.synchronize()
     klaunch = np.full(12, args.steps, dtype=np.int64)  # one launch of each kind per step
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -303,6 +301,23 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_total = float(tt.item())
     ms_per_step = t_total / args.steps * 1e3
+    M.marfa_plan_destroy(plan)
+    # per-kernel times for the roofline: the same work as a serial plan (the kernels one
+    # after the other, so that no launch shares the GPU with another), same L2 flushes
+    plan_s = M.marfa_plan_create(lines, levels, [w.vmr for w in wls], rqs, outs, autotune=True, serial=True,
+                                 stream=stream)
+    M.marfa_plan_execute(plan_s, stream)
+    kms = np.zeros(12)
+    ev_s = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev_s[i][0].record(stream)
+        M.marfa_plan_execute(plan_s, stream)
+        ev_s[i][1].record(stream)
+        kms += M.marfa_plan_info(plan_s, kernel_ms=True)[2]
+    torch.cuda.synchronize()
+    serial_ms = float(sum(a.elapsed_time(b) for a, b in ev_s)) / args.steps
+    M.marfa_plan_destroy(plan_s)
     units = sum(w.n_levels * n for w, n in zip(wls, npts)) * world
     value = units * args.steps / t_total
     evals_s = evals_per_step * world * args.steps / t_total
@@ -368,7 +383,9 @@ def main():
             "line_evals_per_s": evals_s, "line_evals_per_step": evals_per_step,
             "line_evals_per_grid": [int(v) for v in counts_grid],
             "line_evals_class_per_grid": {"poly_cell": [int(v) for v in n_near],
-                                          "asymptotic": [int(v) for v in n_mid]},
+                                          "asymptotic": [int(v) for v in n_mid],
+                                          "small_y_cell": [int(v) for v in n_small]},
+            "step_fp32_tflops": float(flops_grid.sum()) * world * args.steps / t_total / 1e12,
             "fp32_tflops_per_kernel": {n: (float(flops_grid[i - 1]) / (kms[i] / args.steps * 1e-3) / 1e12
                                            if i > 0 and kms[i] > 0 else None) for i, n in enumerate(names)},
             "e2e": {"value": e2e_value, "unit": UNIT,
@@ -376,13 +393,15 @@ def main():
                                                   for w, lv in zip(wls, levels))),
                     "d2h_bytes_per_step": int(sum(o.nbytes for o in out_h))},
             "gpu_launches": int(klaunch.sum()),
-            "plan": {"graph": "one CUDA graph per step (12 kernel launches)", "create_s": plan_s,
+            "plan": {"graph": "one CUDA graph per step (12 kernel launches; grids 1-10 as parallel branches)",
+                     "create_s": plan_s_create, "serial_ms_per_step": serial_ms,
                      "variant_grids_1_10": [int(v) for v in variant],
                      "autotune_ms_per_launch": [[round(float(a), 3), round(float(b), 3)] for a, b in tune_ms]},
-            "kernel_ms_per_step": {n: float(kms[i] / args.steps) for i, n in enumerate(names)},
+            "kernel_ms_per_step_serial": {n: float(kms[i] / args.steps) for i, n in enumerate(names)},
             "roofline": {"bound": "alu", "kernel": names[dom], "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                         "flops_per_eval": {"far": FLOPS_FAR, "asymptotic": FLOPS_MID, "poly_cell": FLOPS_NEAR},
+                         "flops_per_eval": {"far": FLOPS_FAR, "asymptotic": FLOPS_MID, "poly_cell": FLOPS_NEAR,
+                                            "small_y_cell": FLOPS_SMALL},
                          "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz ({src} max clock)"},
             "clocks": clocks,
         }

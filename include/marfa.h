@@ -158,10 +158,13 @@ int marfa_absorption_batch(int32_t n_req, const marfa_lines_t* const* lines,
  *              caller and kept by the plan: every execution rewrites them;
  *   lines    : must stay alive until marfa_plan_destroy; levels, vmr and rq are copied,
  *              and so is the loaded surrogate for requests with surrogate = 1;
- *   autotune : 1 = for each of grids 2..10, time the two summation kernels (line-major:
- *              a thread per candidate line over 32 node pairs; two-phase: warps of 32
- *              node pairs that stage 32 lines at a time) on this batch's own work and keep
- *              the faster; 0 = grids 2..7 line-major, 8..10 two-phase;
+ *   flags    : MARFA_PLAN_AUTOTUNE: for each of grids 2..10, time the two summation
+ *              kernels (line-major: a thread per candidate line over 32 node pairs;
+ *              two-phase: warps of 32 node pairs that stage 32 lines at a time) on this
+ *              batch's own work and keep the faster (otherwise grids 2..7 line-major,
+ *              8..10 two-phase); MARFA_PLAN_SERIAL: capture grids 1..10 one after the
+ *              other (otherwise they are parallel branches of the graph, which the GPU
+ *              runs concurrently, and per-kernel times overlap);
  *   stream   : used for creation (synchronised before return).
  * Results equal marfa_absorption_batch's bit for bit when the kernel choice is the
  * default; the other variant sums in another order (same tolerance to the oracle).
@@ -169,10 +172,12 @@ int marfa_absorption_batch(int32_t n_req, const marfa_lines_t* const* lines,
  * (MARFA_E_CUDA). The paper has no counterpart (it runs one level at a time on CPUs).
  */
 typedef struct marfa_plan marfa_plan_t;
+#define MARFA_PLAN_AUTOTUNE 1
+#define MARFA_PLAN_SERIAL 2
 int marfa_plan_create(int32_t n_req, const marfa_lines_t* const* lines,
                       const marfa_level_t* const* levels, const double* const* vmr,
                       const int32_t* n_levels, const marfa_request_t* rq, float* const* k_out,
-                      int32_t autotune, void* stream, marfa_plan_t** out);
+                      int32_t flags, void* stream, marfa_plan_t** out);
 
 /* Replay the plan's graph on stream (asynchronous; NULL = legacy default stream). The
  * current device must be the plan's. */
@@ -322,11 +327,12 @@ int marfa_diag_absorption_counted(const marfa_lines_t* lines, const marfa_level_
                                   const double* vmr, int32_t n_levels,
                                   const marfa_request_t* rq, float* k_out, int64_t* counts);
 
-/* marfa_absorption with every evaluation counted: counts host array [n_levels][11][4]
+/* marfa_absorption with every evaluation counted: counts host array [n_levels][11][5]
  * (grids 1..10, then the finest), per grid: all (line, node) profile evaluations, those
- * the surrogate took, and the plain Voigt evaluations in the polynomial cells (y < 1 and
- * |x| < 12, or |z| < 4.5) and in the 6- or 15-term asymptotic series (|z| < 100); the
- * rest are far-wing two-term evaluations (or other shapes). */
+ * the surrogate took, and the plain Voigt evaluations in the 9 x 9 polynomial cells
+ * (1/4 <= y < 1 and |x| < 12, or |z| < 4.5 with y >= 1), in the 6- or 15-term
+ * asymptotic series (|z| < 100) and in the small-y cells (y < 1/4, |x| < 12); the rest
+ * are far-wing two-term evaluations (or other shapes). */
 int marfa_diag_absorption_counts(const marfa_lines_t* lines, const marfa_level_t* levels,
                                  const double* vmr, int32_t n_levels, const marfa_request_t* rq,
                                  float* k_out, int64_t* counts);

@@ -22,6 +22,10 @@ The FP32 Voigt K(x, y) = Re w(x + iy) (Eq. (8)) is split by region:
 
 Each cell stores (DEG+1)^2 coefficients c[p][q] of u^p v^q with u, v the cell-local
 coordinates in [-1, 1], fitted by least squares on an oversampled Chebyshev grid.
+
+For y < 1/4 (y^2 < 1/16) a second table covers the same Psi with far fewer terms:
+cells of x-width 0.25, degree SMALL_DX in u and SMALL_DV in v = 32 y^2 - 1 (Psi is
+entire in y^2 and y^2 is small there); relative error of K about 4e-8 against mpmath.
 """
 import os
 
@@ -34,6 +38,9 @@ CORE_W = 0.5          # x-width of a core cell; cells cover x in [0, 12]
 CORE_NX = 24
 G_WX, G_WY = 0.9, 1.75
 G_NX, G_NY = 5, 2     # x in [0, 4.5], y in [1, 4.5]
+SMALL_W, SMALL_NX = 0.25, 48   # small-y cells cover x in [0, 12]
+SMALL_DX, SMALL_DV = 5, 3
+SMALL_ETA = 1.0 / 16.0         # y^2 range of the small-y table
 
 
 def psi(x, eta):
@@ -52,15 +59,17 @@ def voigt(x, y):
     return (mp.exp(-z * z) * mp.erfc(-1j * z)).real
 
 
-def fit(fun, x0, x1, y0, y1, deg=DEG, ov=2):
-    n = ov * (deg + 1)
-    u = np.cos(np.pi * (np.arange(n) + 0.5) / n)
-    X = (x0 + x1) / 2 + (x1 - x0) / 2 * u
-    Y = (y0 + y1) / 2 + (y1 - y0) / 2 * u
-    A = np.array([[u[i] ** p * u[j] ** q for p in range(deg + 1) for q in range(deg + 1)]
-                  for i in range(n) for j in range(n)])
-    b = np.array([float(fun(X[i], Y[j])) for i in range(n) for j in range(n)])
-    return np.linalg.lstsq(A, b, rcond=None)[0].reshape(deg + 1, deg + 1)
+def fit(fun, x0, x1, y0, y1, deg=DEG, ov=2, deg_v=None):
+    dv = deg if deg_v is None else deg_v
+    nx, ny = ov * (deg + 1), ov * (dv + 1)
+    ux = np.cos(np.pi * (np.arange(nx) + 0.5) / nx)
+    uy = np.cos(np.pi * (np.arange(ny) + 0.5) / ny)
+    X = (x0 + x1) / 2 + (x1 - x0) / 2 * ux
+    Y = (y0 + y1) / 2 + (y1 - y0) / 2 * uy
+    A = np.array([[ux[i] ** p * uy[j] ** q for p in range(deg + 1) for q in range(dv + 1)]
+                  for i in range(nx) for j in range(ny)])
+    b = np.array([float(fun(X[i], Y[j])) for i in range(nx) for j in range(ny)])
+    return np.linalg.lstsq(A, b, rcond=None)[0].reshape(deg + 1, dv + 1)
 
 
 def main():
@@ -72,6 +81,10 @@ def main():
         for j in range(G_NY):
             x0, y0 = i * G_WX, 1.0 + j * G_WY
             cells.append(fit(voigt, x0, x0 + G_WX, y0, y0 + G_WY))
+    small = []
+    for i in range(SMALL_NX):
+        x0 = i * SMALL_W
+        small.append(fit(psi, x0, x0 + SMALL_W, 0.0, SMALL_ETA, deg=SMALL_DX, deg_v=SMALL_DV))
     out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "voigt_tables.inc")
     with open(out, "w") as f:
         f.write("// Generated by gen_voigt_tables.py: bivariate polynomial cells of the FP32 Voigt.\n")
@@ -81,6 +94,14 @@ def main():
         f.write(f"#define VOIGT_DEG {DEG}\n#define VOIGT_NCELL {len(cells)}\n#define VOIGT_NPSI {CORE_NX}\n")
         f.write("MARFA_VOIGT_QUAL float kVoigtCells[VOIGT_NCELL * (VOIGT_DEG + 1) * (VOIGT_DEG + 1)] = {\n")
         for c in cells:
+            f.write("  " + ", ".join(f"{float(np.float32(v))!r}f" for v in c.ravel()) + ",\n")
+        f.write("};\n")
+        f.write(f"// {SMALL_NX} small-y cells (Psi over x-width {SMALL_W}, y^2 in [0, {SMALL_ETA}]),\n")
+        f.write(f"// degree {SMALL_DX} in u and {SMALL_DV} in v = 2 y^2 / {SMALL_ETA} - 1, c[p][q] row-major.\n")
+        f.write(f"#define VOIGT_SMALL_NX {SMALL_NX}\n#define VOIGT_SMALL_DX {SMALL_DX}\n"
+                f"#define VOIGT_SMALL_DV {SMALL_DV}\n")
+        f.write("MARFA_VOIGT_QUAL float kVoigtSmall[VOIGT_SMALL_NX * (VOIGT_SMALL_DX + 1) * (VOIGT_SMALL_DV + 1)] = {\n")
+        for c in small:
             f.write("  " + ", ".join(f"{float(np.float32(v))!r}f" for v in c.ravel()) + ",\n")
         f.write("};\n")
     print("wrote", out)

@@ -430,7 +430,7 @@ static int build_plan(Plan& P, const marfa_lines_t* L, const marfa_level_t* leve
     R.m_first[g] = X_lo >> s;
     R.npan[g] = (X_hi >> s) - R.m_first[g] + 1;
     R.slot_off[g] = off;
-    off += 3 * R.npan[g];
+    off += 3 * R.npan[g] * (g == 1 ? kG1Split : 1);
   }
   R.slots_per_level = off;
   R.cut_fx = (int64_t)std::nearbyint(rq->cutoff * kFix);
@@ -450,7 +450,7 @@ static int build_plan(Plan& P, const marfa_lines_t* L, const marfa_level_t* leve
   P.req_idx = req_idx;
   for (int l = 0; l < n_levels; ++l)
     for (int64_t m0 = R.m_first[1]; m0 <= R.m_first[1] + R.npan[1]; m0 += kG1Pairs)
-      P.g1.push_back(G1Item{req_idx, l, m0});
+      for (int part = 0; part < kG1Split; ++part) P.g1.push_back(G1Item{req_idx, l, m0, part, 0});
   const int64_t kb0 = R.k_lo & ~(int64_t)7;  // tiles start on a G10 panel
   for (int l = 0; l < n_levels; ++l)
     for (int64_t k0 = kb0; k0 <= R.k_hi; k0 += kFineTile) P.fine.push_back(FineItem{req_idx, l, k0});
@@ -565,7 +565,7 @@ struct WorkSet {
   std::vector<FineItem> fi;
   int variant[kNGrid + 1] = {0};
   bool surr = false;
-  size_t cw = 32;                          // count bytes per item (four int64)
+  size_t cw = 8 * kCountFields;            // count bytes per item
   void* buf = nullptr;
   ReqDev* drd = nullptr;
   G1Item* dgi = nullptr;
@@ -671,12 +671,13 @@ static int launch_work(const WorkSet& W, cudaStream_t st, bool timed) {
 }
 
 // Read the count buffers of a work set (synchronises st): counts[q] receives, per level
-// of plan q and per grid (1..10, then the finest), four numbers: all profile evaluations,
-// those the surrogate took, plain Voigt evaluations in polynomial cells, and in the
-// asymptotic series ([n_levels][11][4]).
+// of plan q and per grid (1..10, then the finest), kCountFields numbers: all profile
+// evaluations, those the surrogate took, plain Voigt evaluations in 9 x 9 polynomial
+// cells, in the asymptotic series and in small-y cells ([n_levels][11][kCountFields]).
 static int read_counts(const WorkSet& W, std::vector<Plan>& plans, cudaStream_t st,
                        std::vector<int64_t>* counts) {
-  std::vector<int64_t> hg(W.gi.size() * 4), hf(W.fi.size() * 4), hc[kNGrid + 1];
+  constexpr int F = kCountFields;
+  std::vector<int64_t> hg(W.gi.size() * F), hf(W.fi.size() * F), hc[kNGrid + 1];
   cudaError_t e = cudaSuccess;
   auto down = [&](void* h, const void* d, size_t b) {
     if (!e && b) e = cudaMemcpyAsync(h, d, b, cudaMemcpyDeviceToHost, st);
@@ -684,20 +685,20 @@ static int read_counts(const WorkSet& W, std::vector<Plan>& plans, cudaStream_t 
   down(hg.data(), W.dgc, 8 * hg.size());
   down(hf.data(), W.dfc, 8 * hf.size());
   for (int g = 2; g <= kNGrid; ++g) {
-    hc[g].resize(W.ci[g].size() * 4);
+    hc[g].resize(W.ci[g].size() * F);
     down(hc[g].data(), W.dcc[g], 8 * hc[g].size());
   }
   if (!e) e = cudaStreamSynchronize(st);
   if (e) return fail(MARFA_E_CUDA, "count read-back failed: %s", cudaGetErrorString(e));
-  for (size_t q = 0; q < plans.size(); ++q) counts[q].assign((size_t)plans[q].n_levels * 44, 0);
+  for (size_t q = 0; q < plans.size(); ++q) counts[q].assign((size_t)plans[q].n_levels * 11 * F, 0);
   auto add = [&](int req, int level, int slot, const int64_t* v) {
-    int64_t* d = &counts[req][((size_t)level * 11 + slot) * 4];
-    for (int i = 0; i < 4; ++i) d[i] += v[i];
+    int64_t* d = &counts[req][((size_t)level * 11 + slot) * F];
+    for (int i = 0; i < F; ++i) d[i] += v[i];
   };
-  for (size_t k = 0; k < W.gi.size(); ++k) add(W.gi[k].req, W.gi[k].level, 0, &hg[k * 4]);
+  for (size_t k = 0; k < W.gi.size(); ++k) add(W.gi[k].req, W.gi[k].level, 0, &hg[k * F]);
   for (int g = 2; g <= kNGrid; ++g)
-    for (size_t k = 0; k < W.ci[g].size(); ++k) add(W.ci[g][k].req, W.ci[g][k].level, g - 1, &hc[g][k * 4]);
-  for (size_t k = 0; k < W.fi.size(); ++k) add(W.fi[k].req, W.fi[k].level, 10, &hf[k * 4]);
+    for (size_t k = 0; k < W.ci[g].size(); ++k) add(W.ci[g][k].req, W.ci[g][k].level, g - 1, &hc[g][k * F]);
+  for (size_t k = 0; k < W.fi.size(); ++k) add(W.fi[k].req, W.fi[k].level, 10, &hf[k * F]);
   return MARFA_OK;
 }
 
@@ -772,6 +773,7 @@ extern "C" int marfa_absorption_batch(int32_t n_req, const marfa_lines_t* const*
 // of every request, then grid 1, grids 2..10 and the finest grid over all requests.
 // Event-record nodes around each kernel kind give per-kernel times of the last replay.
 constexpr int kKinds = kNGrid + 2;
+constexpr int kSide = 4;  // capture streams of the parallel coarse-grid branches
 
 struct marfa_plan {
   int device = 0;
@@ -783,6 +785,9 @@ struct marfa_plan {
   float tune_ms[kNGrid + 1][2] = {};
   bool tuned = false;
   MlpWeights* mlp = nullptr;  // the plan's own copy of the surrogate (if any request uses it)
+  bool serial = false;        // capture the coarse grids one after the other
+  cudaStream_t side[kSide] = {nullptr};
+  cudaEvent_t fork = nullptr, join[kSide] = {nullptr};
 };
 
 extern "C" void marfa_plan_destroy(marfa_plan_t* X) {
@@ -795,6 +800,11 @@ extern "C" void marfa_plan_destroy(marfa_plan_t* X) {
   if (X->graph) cudaGraphDestroy(X->graph);
   for (auto& e : X->ev)
     if (e) cudaEventDestroy(e);
+  for (auto& e : X->join)
+    if (e) cudaEventDestroy(e);
+  if (X->fork) cudaEventDestroy(X->fork);
+  for (auto& s : X->side)
+    if (s) cudaStreamDestroy(s);
   free_work(X->W, 0);
   for (auto& P : X->plans) release(P, 0);
   if (X->mlp) cudaFreeAsync(X->mlp, 0);
@@ -840,28 +850,43 @@ static int plan_autotune(marfa_plan_t* X, cudaStream_t st, int* chosen) {
   return r;
 }
 
-// All launches of a plan; with events (inside stream capture) event-record nodes
-// bracket each kernel kind (cudaEventRecordExternal makes them graph nodes that a replay
-// records, rather than capture-internal dependencies).
-static int plan_launch_all(marfa_plan_t* X, cudaStream_t st, bool events) {
-  auto rec = [&](int k) {
-    if (events) cudaEventRecordWithFlags(X->ev[k], st, cudaEventRecordExternal);
+// All launches of a plan. With side streams (inside stream capture) the ten coarse-grid
+// launches fork from the level preparation into parallel graph branches, which the GPU
+// runs concurrently (each writes only its own grid's slots), and join before the finest
+// grid; event-record nodes bracket each kernel kind (cudaEventRecordExternal makes them
+// graph nodes that a replay records, rather than capture-internal dependencies).
+static int plan_launch_all(marfa_plan_t* X, cudaStream_t st, bool capture) {
+  auto rec = [&](int k, cudaStream_t s) {
+    if (capture) cudaEventRecordWithFlags(X->ev[k], s, cudaEventRecordExternal);
   };
-  rec(0);
+  const bool branches = capture && !X->serial;
+  rec(0, st);
   for (auto& P : X->plans) launch_prep(P, st, false);
-  rec(1);
+  rec(1, st);
   const WorkSet& W = X->W;
-  rec(2);
-  launch_g1(W.drd, W.dgi, (int)W.gi.size(), nullptr, W.surr, st);
-  rec(3);
-  for (int g = 2; g <= kNGrid; ++g) {
-    rec(2 * g);
-    launch_grid(W, g, st);
-    rec(2 * g + 1);
+  // grid g runs on branch stream br[g] (capture) or on st
+  cudaStream_t br[kNGrid + 1];
+  for (int g = 1; g <= kNGrid; ++g) br[g] = branches ? X->side[(g == 1 ? 0 : 1 + (kNGrid - g)) % kSide] : st;
+  if (branches) {
+    cudaEventRecord(X->fork, st);
+    for (int i = 0; i < kSide; ++i) cudaStreamWaitEvent(X->side[i], X->fork, 0);
   }
-  rec(2 * (kNGrid + 1));
+  rec(2, br[1]);
+  launch_g1(W.drd, W.dgi, (int)W.gi.size(), nullptr, W.surr, br[1]);
+  rec(3, br[1]);
+  for (int g = kNGrid; g >= 2; --g) {  // the finer grids carry more work: start them first
+    rec(2 * g, br[g]);
+    launch_grid(W, g, br[g]);
+    rec(2 * g + 1, br[g]);
+  }
+  if (branches)
+    for (int i = 0; i < kSide; ++i) {
+      cudaEventRecord(X->join[i], X->side[i]);
+      cudaStreamWaitEvent(st, X->join[i], 0);
+    }
+  rec(2 * (kNGrid + 1), st);
   launch_fine(W.drd, W.dfi, (int)W.fi.size(), nullptr, W.surr, st);
-  rec(2 * (kNGrid + 1) + 1);
+  rec(2 * (kNGrid + 1) + 1, st);
   cudaError_t e = cudaGetLastError();
   if (e) return fail(MARFA_E_CUDA, "plan launches: %s", cudaGetErrorString(e));
   return MARFA_OK;
@@ -870,9 +895,11 @@ static int plan_launch_all(marfa_plan_t* X, cudaStream_t st, bool events) {
 extern "C" int marfa_plan_create(int32_t n_req, const marfa_lines_t* const* lines,
                                  const marfa_level_t* const* levels, const double* const* vmr,
                                  const int32_t* n_levels, const marfa_request_t* rq, float* const* k_out,
-                                 int32_t autotune, void* stream, marfa_plan_t** out) {
+                                 int32_t flags, void* stream, marfa_plan_t** out) {
+  const bool autotune = flags & MARFA_PLAN_AUTOTUNE;
   if (!out) return fail(MARFA_E_INVAL, "out is NULL");
   *out = nullptr;
+  if (flags & ~(MARFA_PLAN_AUTOTUNE | MARFA_PLAN_SERIAL)) return fail(MARFA_E_INVAL, "unknown plan flags");
   if (n_req < 1 || !lines || !levels || !vmr || !n_levels || !rq || !k_out)
     return fail(MARFA_E_INVAL, "bad batch arguments");
   for (int q = 0; q < n_req; ++q)
@@ -882,6 +909,7 @@ extern "C" int marfa_plan_create(int32_t n_req, const marfa_lines_t* const* line
   marfa_plan_t* X = new (std::nothrow) marfa_plan_t();
   if (!X) return fail(MARFA_E_NOMEM, "host allocation failed");
   cudaGetDevice(&X->device);
+  X->serial = flags & MARFA_PLAN_SERIAL;
   X->plans.resize(n_req);
   int r = MARFA_OK;
   for (int q = 0; q < n_req && !r; ++q) r = build_plan(X->plans[q], lines[q], levels[q], vmr[q], n_levels[q], &rq[q], q);
@@ -909,6 +937,12 @@ extern "C" int marfa_plan_create(int32_t n_req, const marfa_lines_t* const* line
   cudaError_t e = cudaSuccess;
   for (int k = 0; k < 2 * kKinds && !r; ++k)
     if ((e = cudaEventCreate(&X->ev[k]))) r = fail(MARFA_E_CUDA, "plan events: %s", cudaGetErrorString(e));
+  if (!r && (e = cudaEventCreateWithFlags(&X->fork, cudaEventDisableTiming)))
+    r = fail(MARFA_E_CUDA, "plan events: %s", cudaGetErrorString(e));
+  for (int i = 0; i < kSide && !r; ++i)
+    if ((e = cudaEventCreateWithFlags(&X->join[i], cudaEventDisableTiming)) ||
+        (e = cudaStreamCreateWithFlags(&X->side[i], cudaStreamNonBlocking)))
+      r = fail(MARFA_E_CUDA, "plan streams: %s", cudaGetErrorString(e));
   // one ordinary run first: checks every launch outside capture and leaves the output valid
   if (!r) r = plan_launch_all(X, st, false);
   if (!r && (e = cudaStreamSynchronize(st))) r = fail(MARFA_E_CUDA, "plan run: %s", cudaGetErrorString(e));
@@ -1215,10 +1249,10 @@ extern "C" int marfa_diag_absorption_counted(const marfa_lines_t* lines, const m
                                              const marfa_request_t* rq, float* k_out, int64_t* counts) {
   if (!counts) return fail(MARFA_E_INVAL, "counts is NULL");
   if (n_levels < 1 || n_levels > 65535) return fail(MARFA_E_INVAL, "need 1..65535 levels");
-  std::vector<int64_t> c4((size_t)n_levels * 44);
-  int r = marfa_diag_absorption_counts(lines, levels, vmr, n_levels, rq, k_out, c4.data());
+  std::vector<int64_t> c5((size_t)n_levels * 11 * kCountFields);
+  int r = marfa_diag_absorption_counts(lines, levels, vmr, n_levels, rq, k_out, c5.data());
   if (r) return r;
-  for (size_t i = 0; i < (size_t)n_levels * 11; ++i) counts[i] = c4[4 * i];
+  for (size_t i = 0; i < (size_t)n_levels * 11; ++i) counts[i] = c5[kCountFields * i];
   return MARFA_OK;
 }
 
@@ -1229,12 +1263,12 @@ extern "C" int marfa_diag_absorption_counted_surrogate(const marfa_lines_t* line
                                                        int64_t* surrogate_counts) {
   if (!counts || !surrogate_counts) return fail(MARFA_E_INVAL, "counts is NULL");
   if (n_levels < 1 || n_levels > 65535) return fail(MARFA_E_INVAL, "need 1..65535 levels");
-  std::vector<int64_t> c4((size_t)n_levels * 44);
-  int r = marfa_diag_absorption_counts(lines, levels, vmr, n_levels, rq, k_out, c4.data());
+  std::vector<int64_t> c5((size_t)n_levels * 11 * kCountFields);
+  int r = marfa_diag_absorption_counts(lines, levels, vmr, n_levels, rq, k_out, c5.data());
   if (r) return r;
   for (size_t i = 0; i < (size_t)n_levels * 11; ++i) {
-    counts[i] = c4[4 * i];
-    surrogate_counts[i] = c4[4 * i + 1];
+    counts[i] = c5[kCountFields * i];
+    surrogate_counts[i] = c5[kCountFields * i + 1];
   }
   return MARFA_OK;
 }

@@ -93,6 +93,7 @@ struct ReqDev {
   int64_t m_first[kNGrid + 1];  // per grid 1..10: first panel of the window
   int64_t npan[kNGrid + 1];     // per grid: panels of the window
   int64_t slot_off[kNGrid + 1]; // per grid: offset of its L|M|R arrays in a level's slots
+                                // (grid 1: kG1Split copies, [part][L|M|R][npan])
   int64_t slots_per_level;
   float* slots;             // [n_levels][slots_per_level]
   int64_t cut_fx;           // cut-off, fixed point
@@ -117,13 +118,17 @@ struct FineItem {
   int64_t k0;  // first node of the tile (multiple of 4)
 };
 
-// One CTA of the G1 kernel: kG1Pairs consecutive node pairs of grid 1 of one level.
+// One CTA of the G1 kernel: kG1Pairs consecutive node pairs of grid 1 of one level, and
+// part `part` of kG1Split equal shares of the tile's candidate lines.
 struct G1Item {
   int32_t req, level;
   int64_t m0;  // first pair
+  int32_t part, pad;
 };
 
 constexpr int kG1Pairs = 32;         // node pairs per G1 tile (one per lane)
+constexpr int kG1Split = 4;          // CTAs sharing one G1 tile's candidate lines; each
+                                     // writes its own copy of the tile's slots
 constexpr int kG1Warps = 8;          // warps of a G1 CTA, each takes every 8th staged line
 constexpr int kG1Batch = 512;        // lines staged in shared memory at a time
 constexpr int kLPairs = 32;          // node pairs per CTA of the line-major kernel (grids 2..kLastLM)
@@ -152,9 +157,10 @@ struct PrepArgs {
 
 // kernels (marfa_kernels.cu). With surr set, the surrogate-capable variants run (requests
 // with mlp != null use the surrogate under its guard). counts, when given, selects the
-// counting variants and receives four entries per item: all profile evaluations, those
-// the surrogate took, and the plain Voigt evaluations in polynomial cells and in the
-// asymptotic series (voigt_class 2 and 1).
+// counting variants and receives kCountFields entries per item: all profile evaluations,
+// those the surrogate took, and the plain Voigt evaluations in 9 x 9 polynomial cells,
+// in the asymptotic series and in small-y cells (voigt_class 2, 1 and 3).
+constexpr int kCountFields = 5;
 void launch_level_prep(const PrepArgs& a, int n_levels, cudaStream_t st);
 void launch_g1(const ReqDev* reqs, const G1Item* items, int n_items, int64_t* counts, bool surr,
                cudaStream_t st);

@@ -13,6 +13,9 @@
 // the finest-grid pass adds, at every node, its own sum and the quadratic through
 // the L, M, R of the panel containing the node on each coarse grid.
 #include <cstdio>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "marfa_internal.cuh"
 #include "mlp.cuh"
@@ -255,48 +258,76 @@ __device__ __forceinline__ float shape_f(int shape, float x, float y) {
   }
 }
 
-// Per-CTA evaluation counts, four per block: counts[4b] all profile evaluations,
-// counts[4b + 1] those the surrogate took, counts[4b + 2] and [4b + 3] the plain Voigt
-// evaluations of cost class 2 (polynomial cells) and 1 (asymptotic series).
+// Per-CTA evaluation counts, kCountFields per block: all profile evaluations, those the
+// surrogate took, and the plain Voigt evaluations in 9 x 9 polynomial cells (cost class
+// 2), in the asymptotic series (class 1) and in small-y cells (class 3).
 template <int NW>
 __device__ __forceinline__ void block_counts(int64_t nev, int64_t nmlp, int64_t nnear, int64_t nmid,
-                                             int64_t (*red)[NW], int64_t* counts) {
+                                             int64_t nsmall, int64_t (*red)[NW], int64_t* counts) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int64_t v[4] = {nev, nmlp, nnear, nmid};
+  int64_t v[kCountFields] = {nev, nmlp, nnear, nmid, nsmall};
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < kCountFields; ++i) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
     if (lane == 0) red[i][warp] = v[i];
   }
   __syncthreads();
-  if (threadIdx.x < 4) {
+  if (threadIdx.x < kCountFields) {
     int64_t t = 0;
     for (int w = 0; w < NW; ++w) t += red[threadIdx.x][w];
-    counts[4 * (int64_t)blockIdx.x + threadIdx.x] = t;
+    counts[kCountFields * (int64_t)blockIdx.x + threadIdx.x] = t;
   }
 }
 
 // One counted evaluation at (x, y) (COUNT variants only).
 template <bool COUNT>
 __device__ __forceinline__ void count_eval(bool voigt, float x, float y, int64_t& nev, int64_t& nnear,
-                                           int64_t& nmid) {
+                                           int64_t& nmid, int64_t& nsmall) {
   if (!COUNT) return;
   ++nev;
   if (voigt) {
     const int c = voigt_class(x, y);
     nnear += c == 2 ? 1 : 0;
     nmid += c == 1 ? 1 : 0;
+    nsmall += c == 3 ? 1 : 0;
   }
+}
+
+// Raise a kernel's dynamic shared-memory limit to `bytes` once per kernel, device and size.
+static void dyn_smem_optin(const void* k, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::tuple<const void*, int, size_t>, bool> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  auto key = std::make_tuple(k, dev, bytes);
+  if (done.count(key)) return;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  done[key] = true;
+}
+
+// Launch with `bytes` of dynamic shared memory.
+template <class... KA, class... A>
+static void launch_dyn(void (*k)(KA...), int n_items, int threads, size_t bytes, cudaStream_t st,
+                       A... args) {
+  dyn_smem_optin(reinterpret_cast<const void*>(k), bytes);
+  k<<<n_items, threads, bytes, st>>>(args...);
+}
+
+// Shared-memory copy of the Voigt tables at the start of a kernel's dynamic shared memory.
+constexpr size_t kStabBytes = ((size_t)kVoigtTableFloats * 4 + 15) & ~(size_t)15;
+
+// Dynamic shared memory of the surrogate part: the network weights and one queue per warp.
+constexpr size_t surr_bytes(int threads) {
+  return sizeof(MlpWeights) + (size_t)(threads / 32) * sizeof(SurrQueue);
 }
 
 // Launch a surrogate-capable kernel with the network weights and one queue per warp in
 // dynamic shared memory.
 template <class... KA, class... A>
 static void launch_surr(void (*k)(KA...), int n_items, int threads, cudaStream_t st, A... args) {
-  const size_t bytes = sizeof(MlpWeights) + (size_t)(threads / 32) * sizeof(SurrQueue);
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  k<<<n_items, threads, bytes, st>>>(args...);
+  launch_dyn(k, n_items, threads, surr_bytes(threads), st, args...);
 }
 
 // ------------------------------------------------------------------ K1: level prep
@@ -397,7 +428,8 @@ void launch_level_prep(const PrepArgs& a, int n_levels, cudaStream_t st) {
 // series y/(sqrt(pi) r^2)(1 + (3x^2 - y^2)/(2 r^4)), and the chi-factor of branch 1 is a
 // per-line factor times a per-node constant exp(-0.027 |j|); other lines take the exact path.
 __device__ __noinline__ float2 g1_exact_pair(const ReqDev& R, int64_t o, int64_t X0, int j0,
-                                            bool need0, bool need1, int& n_near, int& n_mid) {
+                                            bool need0, bool need1, int& n_near, int& n_mid,
+                                            int& n_small) {
   const int sh = panel_shift(1) - 1;
   const int64_t c = __ldg(R.c + o);
   const float amp = __ldg(R.amp + o), sx = __ldg(R.sx + o), y = __ldg(R.yv + o);
@@ -418,6 +450,7 @@ __device__ __noinline__ float2 g1_exact_pair(const ReqDev& R, int64_t o, int64_t
     const int cl = voigt ? voigt_class(xv, y) : 0;
     n_near += cl == 2 ? 1 : 0;
     n_mid += cl == 1 ? 1 : 0;
+    n_small += cl == 3 ? 1 : 0;
   }
   return make_float2(v[0], v[1]);
 }
@@ -467,7 +500,7 @@ __global__ void __launch_bounds__(kG1Warps * 32)
   __shared__ unsigned long long sM[kG1Batch];   // owned panels m0-1 .. m0+31
   __shared__ int4 sC[kG1Batch];                 // j_left3, j_right3, exact-path flag, -
   __shared__ float sRed[kG1Warps][8][32];
-  __shared__ int64_t sCnt[4][kG1Warps];
+  __shared__ int64_t sCnt[kCountFields][kG1Warps];
   const G1Item it = items[blockIdx.x];
   const ReqDev& R = reqs[it.req];
   const bool use_mlp = SURR && R.mlp != nullptr;  // block-uniform
@@ -488,7 +521,9 @@ __global__ void __launch_bounds__(kG1Warps * 32)
     const int64_t zlo = (base << s) - cut, zhi = ((m0 + kG1Pairs) << s) + cut;
     bd.lookup(R, L, &zlo, &zhi, 1);
   }
-  const int64_t i_lo = bd.n ? bd.lo[0] : 0, i_hi = bd.n ? bd.hi[0] : 0;
+  // this CTA's share of the candidate lines
+  const int64_t c_lo = bd.n ? bd.lo[0] : 0, c_n = bd.n ? bd.hi[0] - c_lo : 0;
+  const int64_t i_lo = c_lo + c_n * it.part / kG1Split, i_hi = c_lo + c_n * (it.part + 1) / kG1Split;
   const int64_t off = (int64_t)lev * R.n_lines;
   const bool voigt = R.shape == kShapeVoigt;
   const bool physical = R.shape < kShapeConst;
@@ -498,7 +533,7 @@ __global__ void __launch_bounds__(kG1Warps * 32)
   const float rR0 = expf(-0.027f * f0), rR1 = expf(-0.027f * f1);
   const float rL0 = expf(0.027f * f0), rL1 = expf(0.027f * f1);
   float eS = 0.f, eC = 0.f, lS = 0.f, lC = 0.f, rS = 0.f, rC = 0.f, mS = 0.f, mC = 0.f;
-  int64_t nev = 0, nmlp = 0, nnear = 0, nmid = 0;
+  int64_t nev = 0, nmlp = 0, nnear = 0, nmid = 0, nsmall = 0;
   if (use_mlp) __syncthreads();
   int qn = 0;  // entries in this warp's surrogate queue (warp-uniform)
 
@@ -514,9 +549,20 @@ __global__ void __launch_bounds__(kG1Warps * 32)
       const float amp = __ldg(R.amp + o), sx = __ldg(R.sx + o), y = __ldg(R.yv + o);
       NodeX nx;
       nx.init(X0 - c, s - 1, sx);
-      // nearest evaluated node (j = 0 .. 2 kG1Pairs - 1) to the centre
-      const int64_t Xh = X0 + ((int64_t)(2 * kG1Pairs - 1) << (s - 1));
-      const int64_t dn = c < X0 ? X0 - c : (c > Xh ? c - Xh : 0);
+      // distance from the centre to the nearest node of the owned panels (bit b <-> panel
+      // base + b, nodes 2(base + b) .. 2(base + b) + 2): the owned panels nearest to c
+      // below and above it bound it from below
+      int64_t dn = 0;
+      if (msk) {
+        const int64_t pc = fl_sh(c, s) - base;  // panel holding c, relative to base
+        const uint64_t below = pc <= 0 ? 0ull : (pc >= nb ? msk : msk & ((1ull << pc) - 1ull));
+        const uint64_t above = pc < 0 ? msk : (pc >= nb - 1 ? 0ull : msk & ~((2ull << pc) - 1ull));
+        const bool inside = pc >= 0 && pc < nb && ((msk >> pc) & 1ull);
+        int64_t d1 = INT64_MAX, d2 = INT64_MAX;
+        if (below) d1 = c - ((base + (63 - __clzll((long long)below)) + 1) << s);  // end of that panel
+        if (above) d2 = ((base + (__ffsll((long long)above) - 1)) << s) - c;       // start of that panel
+        dn = inside ? 0 : min(d1, d2);
+      }
       const bool far = voigt && (__ll2float_rn(dn) * ldexpf(1.0f, -kFixBits) * sx >= 100.0f || y >= 100.0f);
       int jL = -(1 << 30), jR = 1 << 30;
       bool exact = !far;
@@ -584,8 +630,8 @@ __global__ void __launch_bounds__(kG1Warps * 32)
         q_push(warp_queue(dsm), qn, u1, nd.x1, nd.y, nd.w1, 1);
         if (a0 && !u0) g1_apply((bL ? 2 : 0) | (bR ? 4 : 0), nd.w0 * voigt_K(nd.x0, nd.y));
         if (a1 && !u1) g1_apply(1, nd.w1 * voigt_K(nd.x1, nd.y));
-        if (a0) count_eval<COUNT>(true, nd.x0, nd.y, nev, nnear, nmid);
-        if (a1) count_eval<COUNT>(true, nd.x1, nd.y, nev, nnear, nmid);
+        if (a0) count_eval<COUNT>(true, nd.x0, nd.y, nev, nnear, nmid, nsmall);
+        if (a1) count_eval<COUNT>(true, nd.x1, nd.y, nev, nnear, nmid, nsmall);
         if (COUNT) nmlp += (u0 ? 1 : 0) + (u1 ? 1 : 0);
         continue;
       }
@@ -604,13 +650,14 @@ __global__ void __launch_bounds__(kG1Warps * 32)
         const float am1 = j0 + 1 >= C.y ? b.z * rR1 : (j0 + 1 <= C.x ? b.y * rL1 : b.x);
         v1 = bL ? am1 * i1 * s1 : 0.0f;
       } else {
-        int nn = 0, nm = 0;
-        const float2 v = g1_exact_pair(R, off + b0 + k, X0, j0, true, bL, nn, nm);
+        int nn = 0, nm = 0, ns = 0;
+        const float2 v = g1_exact_pair(R, off + b0 + k, X0, j0, true, bL, nn, nm, ns);
         v0 = v.x;
         v1 = v.y;
         if (COUNT) {
           nnear += nn;
           nmid += nm;
+          nsmall += ns;
         }
       }
       if (bL && bR) pe += v0; else if (bL) pl += v0; else pr += v0;
@@ -641,8 +688,8 @@ __global__ void __launch_bounds__(kG1Warps * 32)
     float ls = a[0], lc = a[1], rs = a[0], rc = a[1];
     comp_merge(ls, lc, a[2], a[3]);
     comp_merge(rs, rc, a[4], a[5]);
-    float* gp = R.slots + (int64_t)lev * R.slots_per_level + R.slot_off[1];
     const int64_t np = R.npan[1];
+    float* gp = R.slots + (int64_t)lev * R.slots_per_level + R.slot_off[1] + 3 * np * it.part;
     const int64_t m = m0 + p;
     if (m <= m_last) {
       gp[m - m_first] = ls + lc;
@@ -650,7 +697,7 @@ __global__ void __launch_bounds__(kG1Warps * 32)
     }
     if (m - 1 >= m_first && m - 1 <= m_last) gp[2 * np + (m - 1 - m_first)] = rs + rc;
   }
-  if (COUNT) block_counts<kG1Warps>(nev, nmlp, nnear, nmid, sCnt, counts);
+  if (COUNT) block_counts<kG1Warps>(nev, nmlp, nnear, nmid, nsmall, sCnt, counts);
 }
 
 void launch_g1(const ReqDev* reqs, const G1Item* items, int n_items, int64_t* counts, bool surr,
@@ -683,7 +730,7 @@ __global__ void __launch_bounds__(kLWarps * 32)
   __shared__ float accL[kLWarps][kLPairs][32];
   __shared__ float accM[kLWarps][kLPairs][32];
   __shared__ float accR[kLWarps][kLPairs][32];
-  __shared__ int64_t sCnt[4][kLWarps];
+  __shared__ int64_t sCnt[kCountFields][kLWarps];
   const CoarseItem it = items[blockIdx.x];
   const ReqDev& R = reqs[it.req];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -716,7 +763,7 @@ __global__ void __launch_bounds__(kLWarps * 32)
   const int64_t X0 = m0 << s;  // position of node 2 m0 (j = 0)
   const bool physical = R.shape < kShapeConst;
   const bool voigt = R.shape == kShapeVoigt;
-  int64_t nev = 0, nmlp = 0, nnear = 0, nmid = 0;
+  int64_t nev = 0, nmlp = 0, nnear = 0, nmid = 0, nsmall = 0;
   const bool use_mlp = SURR && R.mlp != nullptr;  // block-uniform
   if (use_mlp) {
     mlp_load_smem(S, R.mlp);
@@ -787,8 +834,8 @@ __global__ void __launch_bounds__(kLWarps * 32)
             if (use_chi) w *= co;
             lm_apply(to, w);
           }
-          if (ae) count_eval<COUNT>(true, xe, y, nev, nnear, nmid);
-          if (ao) count_eval<COUNT>(true, xo, y, nev, nnear, nmid);
+          if (ae) count_eval<COUNT>(true, xe, y, nev, nnear, nmid, nsmall);
+          if (ao) count_eval<COUNT>(true, xo, y, nev, nnear, nmid, nsmall);
           if (COUNT) nmlp += (ue ? 1 : 0) + (uo ? 1 : 0);
         }
         continue;
@@ -820,13 +867,13 @@ __global__ void __launch_bounds__(kLWarps * 32)
         if (use_chi) v *= ct.value(2 * p, nx.absd(jf, s - 1));
         if (bL) accL[warp][p][lane] += v;
         if (bR) accR[warp][p][lane] += v;
-        count_eval<COUNT>(voigt, xv, y, nev, nnear, nmid);
+        count_eval<COUNT>(voigt, xv, y, nev, nnear, nmid, nsmall);
         if (bL) {
           const float xw = nx.x(jf + 1.0f);
           float w = amp * (voigt ? voigt_K(xw, y) : shape_f(R.shape, xw, y));
           if (use_chi) w *= ct.value(2 * p + 1, nx.absd(jf + 1.0f, s - 1));
           accM[warp][p][lane] += w;
-          count_eval<COUNT>(voigt, xw, y, nev, nnear, nmid);
+          count_eval<COUNT>(voigt, xw, y, nev, nnear, nmid, nsmall);
         }
       }
     }
@@ -848,7 +895,7 @@ __global__ void __launch_bounds__(kLWarps * 32)
     if (kind == 1 && m <= m_last) gp[np + (m - m_first)] = v;
     if (kind == 2 && m - 1 >= m_first && m - 1 <= m_last) gp[2 * np + (m - 1 - m_first)] = v;
   }
-  if (COUNT) block_counts<kLWarps>(nev, nmlp, nnear, nmid, sCnt, counts);
+  if (COUNT) block_counts<kLWarps>(nev, nmlp, nnear, nmid, nsmall, sCnt, counts);
 }
 
 void launch_coarse_lm(const ReqDev* reqs, const CoarseItem* items, int n_items, int64_t* counts,
@@ -877,13 +924,15 @@ template <bool COUNT, bool SURR>
 __global__ void __launch_bounds__(kCWarps * 32)
     k_coarse(const ReqDev* __restrict__ reqs, const CoarseItem* __restrict__ items,
              int64_t* __restrict__ counts) {
-  extern __shared__ __align__(16) unsigned char dsm[];  // surrogate weights (SURR only)
+  // dynamic shared memory: the Voigt tables, then (SURR) the surrogate weights and queues
+  extern __shared__ __align__(16) unsigned char dsm0[];
+  float* stab = reinterpret_cast<float*>(dsm0);
+  unsigned char* dsm = dsm0 + kStabBytes;
   MlpWeights& S = *reinterpret_cast<MlpWeights*>(dsm);
-  __shared__ float stab[kVoigtTableFloats];
   __shared__ float bufE[kCWarps][32][kCPairs + 1];  // value at node 2p of staged line t
   __shared__ float bufO[kCWarps][32][kCPairs + 1];  // value at node 2p + 1
   __shared__ unsigned long long smsk[kCWarps][32];
-  __shared__ int64_t sCnt[4][kCWarps];
+  __shared__ int64_t sCnt[kCountFields][kCWarps];
   const CoarseItem it = items[blockIdx.x];
   const ReqDev& R = reqs[it.req];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -892,7 +941,7 @@ __global__ void __launch_bounds__(kCWarps * 32)
   const int64_t m_first = R.m_first[g];
   const int64_t m_last = m_first + R.npan[g] - 1;
   const int64_t m0 = it.m0 + (int64_t)kCPairs * warp;  // this warp's first pair
-  int64_t nev = 0, nmlp = 0, nnear = 0, nmid = 0;
+  int64_t nev = 0, nmlp = 0, nnear = 0, nmid = 0, nsmall = 0;
   const bool use_mlp = SURR && R.mlp != nullptr;  // block-uniform
   voigt_table_to_smem(stab);
   if (use_mlp) mlp_load_smem(S, R.mlp);
@@ -983,8 +1032,8 @@ __global__ void __launch_bounds__(kCWarps * 32)
               if (use_chi) w *= co;
               bO[lane][q] = w;
             }
-            if (ae) count_eval<COUNT>(true, xv, y, nev, nnear, nmid);
-            if (ao) count_eval<COUNT>(true, xw, y, nev, nnear, nmid);
+            if (ae) count_eval<COUNT>(true, xv, y, nev, nnear, nmid, nsmall);
+            if (ao) count_eval<COUNT>(true, xw, y, nev, nnear, nmid, nsmall);
             if (COUNT) nmlp += (ue ? 1 : 0) + (uo ? 1 : 0);
           }
           q_flush(warp_queue(dsm), qn, S, tp_apply);
@@ -1007,13 +1056,13 @@ __global__ void __launch_bounds__(kCWarps * 32)
             float v = amp * (voigt ? voigt_K<true>(xv, y, stab) : shape_f(R.shape, xv, y));
             if (use_chi) v *= ct.value(2 * q, nx.absd(jf, s - 1));
             bE[lane][q] = v;
-            count_eval<COUNT>(voigt, xv, y, nev, nnear, nmid);
+            count_eval<COUNT>(voigt, xv, y, nev, nnear, nmid, nsmall);
             if (bL) {
               const float xw = nx.x(jf + 1.0f);
               float w = amp * (voigt ? voigt_K<true>(xw, y, stab) : shape_f(R.shape, xw, y));
               if (use_chi) w *= ct.value(2 * q + 1, nx.absd(jf + 1.0f, s - 1));
               bO[lane][q] = w;
-              count_eval<COUNT>(voigt, xw, y, nev, nnear, nmid);
+              count_eval<COUNT>(voigt, xw, y, nev, nnear, nmid, nsmall);
             }
           }
         }
@@ -1048,21 +1097,22 @@ __global__ void __launch_bounds__(kCWarps * 32)
     }
     if (m - 1 >= m_first && m - 1 <= m_last) gp[2 * np + (m - 1 - m_first)] = sR + cR;
   }
-  if (COUNT) block_counts<kCWarps>(nev, nmlp, nnear, nmid, sCnt, counts);
+  if (COUNT) block_counts<kCWarps>(nev, nmlp, nnear, nmid, nsmall, sCnt, counts);
 }
 
 void launch_coarse(const ReqDev* reqs, const CoarseItem* items, int n_items, int64_t* counts,
                    bool surr, cudaStream_t st) {
   if (n_items <= 0) return;
+  const int T = kCWarps * 32;
   if (surr) {
     if (counts)
-      launch_surr(k_coarse<true, true>, n_items, kCWarps * 32, st, reqs, items, counts);
+      launch_dyn(k_coarse<true, true>, n_items, T, kStabBytes + surr_bytes(T), st, reqs, items, counts);
     else
-      launch_surr(k_coarse<false, true>, n_items, kCWarps * 32, st, reqs, items, counts);
+      launch_dyn(k_coarse<false, true>, n_items, T, kStabBytes + surr_bytes(T), st, reqs, items, counts);
   } else if (counts) {
-    k_coarse<true, false><<<n_items, kCWarps * 32, 0, st>>>(reqs, items, counts);
+    launch_dyn(k_coarse<true, false>, n_items, T, kStabBytes, st, reqs, items, counts);
   } else {
-    k_coarse<false, false><<<n_items, kCWarps * 32, 0, st>>>(reqs, items, counts);
+    launch_dyn(k_coarse<false, false>, n_items, T, kStabBytes, st, reqs, items, counts);
   }
 }
 
@@ -1088,7 +1138,7 @@ __global__ void __launch_bounds__(kFineThreads)
   __shared__ uint32_t sPm[NW][32];
   __shared__ int sKlo[NW][32], sKhi[NW][32], sChi[NW][32];
   __shared__ int sT[6][NW][32];  // chi thresholds r3, r150, r300, l3, l150, l300
-  __shared__ int64_t red[4][NW];
+  __shared__ int64_t red[kCountFields][NW];
   const FineItem it = items[blockIdx.x];
   const ReqDev& R = reqs[it.req];
   const int lev = it.level;
@@ -1104,7 +1154,7 @@ __global__ void __launch_bounds__(kFineThreads)
   float acc[kFinePerThread], cmp[kFinePerThread];
 #pragma unroll
   for (int q = 0; q < kFinePerThread; ++q) acc[q] = cmp[q] = 0.0f;
-  int64_t nev = 0, nmlp = 0, nnear = 0, nmid = 0;
+  int64_t nev = 0, nmlp = 0, nnear = 0, nmid = 0, nsmall = 0;
   const int nw = kFinePerThread * 32;  // nodes of the warp
   int qn = 0;  // entries in this warp's surrogate queue (warp-uniform)
   // surrogate results: the tag is the node q of the owning lane
@@ -1212,7 +1262,7 @@ __global__ void __launch_bounds__(kFineThreads)
                 if (uc) v *= cv;
                 kahan_add(acc[q], cmp[q], v);
               }
-              if (act) count_eval<COUNT>(true, xv, y, nev, nnear, nmid);
+              if (act) count_eval<COUNT>(true, xv, y, nev, nnear, nmid, nsmall);
               if (COUNT && use) ++nmlp;
             }
           }
@@ -1238,7 +1288,7 @@ __global__ void __launch_bounds__(kFineThreads)
             float v = amp * (voigt ? voigt_K<true>(xv, y, stab) : shape_f(R.shape, xv, y));
             if (uc) v *= ct.value(j, fabsf((jf + qf) + phi) * ldexpf(1.0f, -kFineBits));
             kahan_add(acc[q], cmp[q], v);
-            count_eval<COUNT>(voigt, xv, y, nev, nnear, nmid);
+            count_eval<COUNT>(voigt, xv, y, nev, nnear, nmid, nsmall);
           }
         }
         __syncwarp();
@@ -1263,7 +1313,16 @@ __global__ void __launch_bounds__(kFineThreads)
       const int64_t idx = m - R.m_first[g];
       const int64_t np = R.npan[g];
       const float* gp = sl + R.slot_off[g];
-      const float vL = __ldg(gp + idx), vM = __ldg(gp + np + idx), vR = __ldg(gp + 2 * np + idx);
+      float vL = __ldg(gp + idx), vM = __ldg(gp + np + idx), vR = __ldg(gp + 2 * np + idx);
+      if (g == 1) {  // the kG1Split partial copies of grid 1, summed in part order
+#pragma unroll
+        for (int part = 1; part < kG1Split; ++part) {
+          const float* gq = gp + 3 * np * part;
+          vL += __ldg(gq + idx);
+          vM += __ldg(gq + np + idx);
+          vR += __ldg(gq + 2 * np + idx);
+        }
+      }
       const int off0 = (int)(k0 - (m << sh));
       const float inv_h = ldexpf(1.0f, 1 - sh);
 #pragma unroll
@@ -1299,7 +1358,7 @@ __global__ void __launch_bounds__(kFineThreads)
     const int done = head + 4 * nv;
     if (tid < n - done) dst[done + tid] = tile[t0 + done + tid];
   }
-  if (COUNT) block_counts<NW>(nev, nmlp, nnear, nmid, red, counts);
+  if (COUNT) block_counts<NW>(nev, nmlp, nnear, nmid, nsmall, red, counts);
 }
 
 void launch_fine(const ReqDev* reqs, const FineItem* items, int n_items, int64_t* counts, bool surr,

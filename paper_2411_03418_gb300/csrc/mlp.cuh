@@ -210,12 +210,8 @@ __device__ __forceinline__ void q_flush(SurrQueue& Q, int& n, const MlpWeights& 
   n = 0;
 }
 
-// Dynamic shared memory of a surrogate-capable kernel with NW warps: the weights, then
-// one queue per warp.
-template <int NW>
-constexpr size_t surr_smem_bytes() {
-  return sizeof(MlpWeights) + (size_t)NW * sizeof(SurrQueue);
-}
+// The queue of the calling warp, in a surrogate block of shared memory laid out as the
+// weights followed by one queue per warp.
 __device__ __forceinline__ SurrQueue& warp_queue(unsigned char* dsm) {
   return reinterpret_cast<SurrQueue*>(dsm + sizeof(MlpWeights))[threadIdx.x >> 5];
 }

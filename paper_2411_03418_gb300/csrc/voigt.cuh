@@ -5,7 +5,9 @@
 //   y < 1, |x| < 12    exact split w = exp(-z^2) + (2i/sqrt(pi)) F(z), F the complex
 //                Dawson function, K = exp(y^2-x^2) cos(2xy) - (2/sqrt(pi)) y Psi,
 //                Psi(x, y^2) = Im F / y from a table of bivariate polynomials (the
-//                Gaussian term is below 4e-19 and dropped for |x| >= 6.5);
+//                Gaussian term is below 4e-19 and dropped for |x| >= 6.5); below
+//                y = 1/4 a second table of low degree in y^2 (6 x 4 terms per cell
+//                instead of 9 x 9) serves the narrow lines;
 //   |z| < 4.5, y >= 1  K from a table of bivariate polynomials;
 //   elsewhere   asymptotic series of w (Abramowitz & Stegun 7.1.23),
 //                w ~ i/(sqrt(pi) z) sum_n (2n-1)!!/(2 z^2)^n, truncated by |z|
@@ -80,6 +82,25 @@ __device__ __forceinline__ float voigt_cell(const float* tab, int cell, float u,
   return acc;
 }
 
+// One small-y cell (degree VOIGT_SMALL_DX in u, VOIGT_SMALL_DV in v).
+template <bool SMEM>
+__device__ __forceinline__ float voigt_cell_small(const float* tab, int cell, float u, float v) {
+  constexpr int NQ = VOIGT_SMALL_DV + 1;
+  const float* c = tab + cell * (VOIGT_SMALL_DX + 1) * NQ;
+  float acc = 0.0f;
+#pragma unroll
+  for (int p = VOIGT_SMALL_DX; p >= 0; --p) {
+    float r = 0.0f;
+#pragma unroll
+    for (int q = VOIGT_SMALL_DV; q >= 0; --q) r = fmaf(r, v, SMEM ? c[p * NQ + q] : __ldg(c + p * NQ + q));
+    acc = fmaf(acc, u, r);
+  }
+  return acc;
+}
+
+// Floats of the large table; the small-y table follows it in a kernel's shared copy.
+constexpr int kVoigtBigFloats = VOIGT_NCELL * (VOIGT_DEG + 1) * (VOIGT_DEG + 1);
+
 // Far-wing form (|z| >= 100): two terms of the series, K = y/(sqrt(pi) r^2) (1 + (3x^2 - y^2)/(2 r^4)).
 __device__ __forceinline__ float voigt_far(float x, float y) {
   float x2 = x * x, y2 = y * y;
@@ -93,6 +114,14 @@ __device__ __forceinline__ float voigt_far(float x, float y) {
 // so that one line's nodes on the fine grids take a single code path.
 template <bool SMEM>
 __device__ __noinline__ float voigt_K_near(float ax, float y, const float* tab) {
+  if (y < 0.25f && ax < 12.0f) {
+    const int ci = min((int)(ax * 4.0f), VOIGT_SMALL_NX - 1);
+    const float u = (ax - (0.25f * ci + 0.125f)) * 8.0f;
+    const float v = fmaf(32.0f * y, y, -1.0f);
+    const float ps = voigt_cell_small<SMEM>(SMEM ? tab + kVoigtBigFloats : kVoigtSmall, ci, u, v);
+    const float gt = ax < 6.5f ? gauss_term(ax, y) : 0.0f;
+    return gt - kTwoOverSqrtPi * y * ps;
+  }
   if (y < 1.0f && ax < 12.0f) {
     int ci = min((int)(ax * 2.0f), VOIGT_NPSI - 1);
     float u = (ax - (0.5f * ci + 0.25f)) * 4.0f;
@@ -122,21 +151,24 @@ __device__ __forceinline__ float voigt_K(float x, float y, const float* tab) {
 __device__ __forceinline__ float voigt_K(float x, float y) { return voigt_K<false>(x, y, kVoigtCells); }
 
 // Cost class of one voigt_K evaluation, for operation counts: 0 the far-wing two-term
-// series, 1 the 6- or 15-term asymptotic series, 2 a polynomial cell (Dawson or K table).
+// series, 1 the 6- or 15-term asymptotic series, 2 a 9 x 9 polynomial cell (Dawson or K
+// table), 3 a small-y cell.
 __device__ __forceinline__ int voigt_class(float x, float y) {
   const float ax = fabsf(x);
   const float r2 = fmaf(ax, ax, y * y);
   if (r2 >= 1.0e4f) return 0;
+  if (y < 0.25f && ax < 12.0f) return 3;
   if (y < 1.0f && ax < 12.0f) return 2;
   return r2 >= 20.25f ? 1 : 2;
 }
 
-// Copy the coefficient table into shared memory (all threads of the block take part).
-__device__ __forceinline__ void voigt_table_to_smem(float* dst) {
-  for (int i = threadIdx.x; i < VOIGT_NCELL * (VOIGT_DEG + 1) * (VOIGT_DEG + 1); i += blockDim.x)
-    dst[i] = kVoigtCells[i];
-}
+constexpr int kVoigtSmallFloats = VOIGT_SMALL_NX * (VOIGT_SMALL_DX + 1) * (VOIGT_SMALL_DV + 1);
+constexpr int kVoigtTableFloats = kVoigtBigFloats + kVoigtSmallFloats;
 
-constexpr int kVoigtTableFloats = VOIGT_NCELL * (VOIGT_DEG + 1) * (VOIGT_DEG + 1);
+// Copy both coefficient tables into shared memory (all threads of the block take part).
+__device__ __forceinline__ void voigt_table_to_smem(float* dst) {
+  for (int i = threadIdx.x; i < kVoigtTableFloats; i += blockDim.x)
+    dst[i] = i < kVoigtBigFloats ? kVoigtCells[i] : kVoigtSmall[i - kVoigtBigFloats];
+}
 
 }  // namespace marfa

@@ -218,7 +218,11 @@ class Plan:
             self.handle = None
 
 
-def marfa_plan_create(lines, levels, vmrs, rqs, k_outs, autotune: bool = False, stream=None) -> Plan:
+PLAN_AUTOTUNE, PLAN_SERIAL = 1, 2
+
+
+def marfa_plan_create(lines, levels, vmrs, rqs, k_outs, autotune: bool = False, serial: bool = False,
+                      stream=None) -> Plan:
     """k_outs: CUDA tensors [n_levels, npts] float32, rewritten by every execution."""
     n = len(lines)
     levels = [np.ascontiguousarray(x, dtype=LEVEL_DTYPE) for x in levels]
@@ -231,7 +235,8 @@ def marfa_plan_create(lines, levels, vmrs, rqs, k_outs, autotune: bool = False, 
     rq = (marfa_request_t * n)(*rqs)
     outs = VP(*[_ptr(o).value for o in k_outs])
     h = C.c_void_p()
-    _check(load().marfa_plan_create(n, lh, lp, vp, nl, rq, outs, int(autotune), _stream(stream), C.byref(h)))
+    flags = (PLAN_AUTOTUNE if autotune else 0) | (PLAN_SERIAL if serial else 0)
+    _check(load().marfa_plan_create(n, lh, lp, vp, nl, rq, outs, flags, _stream(stream), C.byref(h)))
     return Plan(h, (list(lines), list(k_outs)))
 
 
@@ -305,13 +310,13 @@ def marfa_diag_absorption_counted(lines: Lines, levels, vmr, rq):
 
 
 def marfa_diag_absorption_counts(lines: Lines, levels, vmr, rq):
-    """(k, counts[n_levels, 11, 4]): all, surrogate, polynomial-cell and asymptotic
-    evaluations per level and grid."""
+    """(k, counts[n_levels, 11, 5]): all, surrogate, 9x9 polynomial-cell, asymptotic and
+    small-y-cell evaluations per level and grid."""
     levels = np.ascontiguousarray(levels, dtype=LEVEL_DTYPE)
     vmr = np.ascontiguousarray(vmr, dtype=np.float64)
     n = marfa_num_points(rq.nu_lo, rq.nu_hi)
     k = np.empty((len(levels), n), dtype=np.float32)
-    counts = np.empty((len(levels), 11, 4), dtype=np.int64)
+    counts = np.empty((len(levels), 11, 5), dtype=np.int64)
     _check(load().marfa_diag_absorption_counts(lines.handle, _ptr(levels), _ptr(vmr), len(levels),
                                                C.byref(rq), _ptr(k), _ptr(counts)))
     return k, counts

@@ -69,9 +69,27 @@ def test_voigt_fp32_error_map(M):
     rel = np.abs(got / ref - 1)
     assert rel.max() < 5e-6, f"max rel err {rel.max():.3e} at x={x[np.argmax(rel)]}, y={y[np.argmax(rel)]}"
     # region boundaries and the pure-Lorentz far wing
-    for xb, yb in [(4.5, 1e-3), (4.4999, 0.5), (0.0, 1.0), (8.0, 1e-4), (99.9, 0.1), (0.0, 4.5)]:
+    for xb, yb in [(4.5, 1e-3), (4.4999, 0.5), (0.0, 1.0), (8.0, 1e-4), (99.9, 0.1), (0.0, 4.5),
+                   (3.0, 0.2499), (3.0, 0.25), (11.99, 0.1), (0.0, 1e-5), (6.4999, 0.2), (0.25, 0.0)]:
         g = M.marfa_diag_voigt(np.array([xb], np.float32), np.array([yb], np.float32))[0]
         assert abs(g / O.voigt_K(np.float32(xb), np.float32(yb)) - 1) < 5e-6
+
+
+def test_evaluation_cost_classes(M):
+    """Per-grid counts by Voigt cost class: they stay within the plain evaluations, both
+    table kinds occur (y ~ 0.06 and y ~ 0.6 here), and they vanish for a non-Voigt shape."""
+    wl = tiny_workload(61, 250, 2100.0, 2102.0, 25.0, T=(296.0, 200.0), p=(0.002, 0.02))
+    lines = M.marfa_prepare_lines(wl.lines, wl.species)
+    _, c5 = M.marfa_diag_absorption_counts(lines, M.levels_of(wl), wl.vmr, M.request_of(wl))
+    assert c5.shape == (2, 11, 5)
+    assert np.all(c5[:, :, 1] == 0)
+    assert np.all(c5[:, :, 2] + c5[:, :, 3] + c5[:, :, 4] <= c5[:, :, 0])
+    assert c5[0, :, 4].sum() > 0 and c5[1, :, 2].sum() > 0  # small-y at 0.002 atm, 9x9 cells at 0.02 atm
+    _, tot = M.marfa_diag_absorption_counted(lines, M.levels_of(wl), wl.vmr, M.request_of(wl))
+    assert np.array_equal(tot, c5[:, :, 0])
+    wl2 = wl.with_(shape="lorentz")
+    _, c5l = M.marfa_diag_absorption_counts(lines, M.levels_of(wl2), wl2.vmr, M.request_of(wl2))
+    assert np.all(c5l[:, :, 2:] == 0) and c5l[:, :, 0].sum() > 0
 
 
 # ------------------------------------------------------------ integer work, bit-exact
