@@ -224,7 +224,7 @@ struct ChiThr {
     if (b == 0) return 1.0f;
     const float C = b == 1 ? 1.084f : (b == 2 ? 0.208f : 0.025f);
     const float r = b == 1 ? 0.027f : (b == 2 ? 0.016f : 0.009f);
-    return C * expf(-r * absd);
+    return C * __expf(-r * absd);
   }
 };
 
@@ -863,14 +863,14 @@ __global__ void __launch_bounds__(kLWarps * 32)
         if (!(bR || bL)) continue;
         const float jf = (float)(2 * p);
         const float xv = nx.x(jf);
-        float v = amp * (voigt ? voigt_K(xv, y) : shape_f(R.shape, xv, y));
+        float v = amp * (voigt ? voigt_K<false, true>(xv, y, kVoigtCells) : shape_f(R.shape, xv, y));
         if (use_chi) v *= ct.value(2 * p, nx.absd(jf, s - 1));
         if (bL) accL[warp][p][lane] += v;
         if (bR) accR[warp][p][lane] += v;
         count_eval<COUNT>(voigt, xv, y, nev, nnear, nmid, nsmall);
         if (bL) {
           const float xw = nx.x(jf + 1.0f);
-          float w = amp * (voigt ? voigt_K(xw, y) : shape_f(R.shape, xw, y));
+          float w = amp * (voigt ? voigt_K<false, true>(xw, y, kVoigtCells) : shape_f(R.shape, xw, y));
           if (use_chi) w *= ct.value(2 * p + 1, nx.absd(jf + 1.0f, s - 1));
           accM[warp][p][lane] += w;
           count_eval<COUNT>(voigt, xw, y, nev, nnear, nmid, nsmall);

@@ -11,7 +11,8 @@
 //   |z| < 4.5, y >= 1  K from a table of bivariate polynomials;
 //   elsewhere   asymptotic series of w (Abramowitz & Stegun 7.1.23),
 //                w ~ i/(sqrt(pi) z) sum_n (2n-1)!!/(2 z^2)^n, truncated by |z|
-//                (2 terms for |z| >= 100, 6 for |z| >= 8, 15 for |z| >= 4.5).
+//                (2 terms for |z| >= 100, 6 for |z| >= 8 (or 3 for |z| >= 22.5 where
+//                the caller asks for it), 15 for |z| >= 4.5).
 // The tables come from gen_voigt_tables.py (mpmath, 30 digits).
 #pragma once
 #include <cuda_runtime.h>
@@ -140,11 +141,16 @@ __device__ __noinline__ float voigt_K_near(float ax, float y, const float* tab) 
   return voigt_cell<SMEM>(tab, VOIGT_NPSI + ix * 2 + iy, u, v);
 }
 
-template <bool SMEM>
+// MID3: evaluate 22.5 <= |z| < 100 inline with three terms of the series (the first
+// omitted term is below 7 (15/8) / |z|^6 < 1e-7 relative, also for Re w near the real
+// axis) instead of the six terms of voigt_K_near; it pays where most evaluations lie in
+// the mid wing (grids 2..8) and costs registers and branches elsewhere.
+template <bool SMEM, bool MID3 = false>
 __device__ __forceinline__ float voigt_K(float x, float y, const float* tab) {
   float ax = fabsf(x);
   float r2 = fmaf(ax, ax, y * y);
   if (r2 >= 1.0e4f) return voigt_far(ax, y);
+  if (MID3 && r2 >= 506.25f) return voigt_asym<2>(ax, y);
   return voigt_K_near<SMEM>(ax, y, tab);
 }
 
