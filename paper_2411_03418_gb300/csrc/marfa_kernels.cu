@@ -194,6 +194,26 @@ __device__ __forceinline__ MT accept_mask(int g, int64_t c, int gst, bool chi, i
   return m;
 }
 
+// Quick rejection for grids 2..10: with its core on a coarser grid (gst < g) a line
+// owns panels of grid g only where the parent panel holds its cut-off edge or a chi
+// breakpoint, i.e. within one panel width P of the child; if no edge or breakpoint lies
+// within P of the span [xa, xb] of the tile's panels, the line owns nothing there.
+__device__ __forceinline__ bool owns_nothing(int g, int64_t c, int gst, bool chi, int64_t cut,
+                                             int64_t xa, int64_t xb, int64_t P) {
+  if (gst >= g) return false;
+  const int64_t lo = xa - P, hi = xb + P;
+  if ((c - cut >= lo && c - cut <= hi) || (c + cut >= lo && c + cut <= hi)) return false;
+  if (chi) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const int64_t B = kChiBreakFx[b];
+      if (B > cut) break;
+      if ((c - B >= lo && c - B <= hi) || (c + B >= lo && c + B <= hi)) return false;
+    }
+  }
+  return true;
+}
+
 // Panels of grid g (1..10) owned by a line over [base, base + nb).
 __device__ __forceinline__ uint32_t owned_mask(int g, int64_t c, int gst, bool chi, int64_t cut,
                                                int R_w, int64_t base, int nb) {
@@ -217,14 +237,44 @@ struct ChiThr {
     l150 = clamp32(cl_sh(c - kChiBreakFx[1] - X0, sh));
     l300 = clamp32(cl_sh(c - kChiBreakFx[2] - X0, sh));
   }
+  __device__ __forceinline__ int branch(int j) const {
+    return (j >= r3) + (j > r150) + (j > r300) + (j <= l3) + (j < l150) + (j < l300);
+  }
+  // The branch is the same at every node of [ja, jb] (it changes only at j = r3,
+  // r150 + 1, r300 + 1, l3 + 1, l150, l300).
+  __device__ __forceinline__ bool uniform(int ja, int jb) const {
+    auto in = [&](int t) { return t > ja && t <= jb; };
+    return !(in(r3) || in(r150 + 1) || in(r300 + 1) || in(l3 + 1) || in(l150) || in(l300));
+  }
   // Eq. (10): 1 below 3 cm^-1; 1.084 e^{-0.027|d|} on [3, 150]; 0.208 e^{-0.016|d|} on
   // (150, 300]; 0.025 e^{-0.009|d|} above 300. Branch chosen on the exact node index.
   __device__ __forceinline__ float value(int j, float absd) const {
-    int b = (j >= r3) + (j > r150) + (j > r300) + (j <= l3) + (j < l150) + (j < l300);
+    int b = branch(j);
     if (b == 0) return 1.0f;
     const float C = b == 1 ? 1.084f : (b == 2 ? 0.208f : 0.025f);
     const float r = b == 1 ? 0.027f : (b == 2 ? 0.016f : 0.009f);
     return C * __expf(-r * absd);
+  }
+};
+
+// chi-factor along the nodes ja, ja + 1, ... of one line when its branch is the same at
+// all of them (ChiThr::uniform): chi(ja) once, then a constant ratio per node step
+// (e^{-r h} on the side right of the centre, e^{+r h} on the left), so each node costs
+// one multiplication; at most 64 steps, about 4e-6 relative drift.
+struct ChiRun {
+  float v = 1.0f, ratio = 1.0f;  // chi at the current node, ratio per node step
+  __device__ __forceinline__ void init(const ChiThr& ct, int ja, float absd_a, int sh) {
+    const int b = ct.branch(ja);
+    if (b == 0) {
+      v = 1.0f;
+      ratio = 1.0f;
+      return;
+    }
+    const float C = b == 1 ? 1.084f : (b == 2 ? 0.208f : 0.025f);
+    const float r = b == 1 ? 0.027f : (b == 2 ? 0.016f : 0.009f);
+    v = C * __expf(-r * absd_a);
+    const float h = ldexpf(1.0f, sh - kFixBits);  // node step, cm^-1
+    ratio = __expf((ja >= ct.r3 ? -r : r) * h);
   }
 };
 
@@ -761,6 +811,7 @@ __global__ void __launch_bounds__(kLWarps * 32)
   }
   const int64_t lo_off = (int64_t)lev * R.n_lines;
   const int64_t X0 = m0 << s;  // position of node 2 m0 (j = 0)
+  const int64_t xa_t = base << s, xb_t = (base + nb) << s, P_t = int64_t(1) << s;  // span of the mask's panels
   const bool physical = R.shape < kShapeConst;
   const bool voigt = R.shape == kShapeVoigt;
   int64_t nev = 0, nmlp = 0, nnear = 0, nmid = 0, nsmall = 0;
@@ -844,6 +895,7 @@ __global__ void __launch_bounds__(kLWarps * 32)
       const int64_t c = __ldg(R.c + lo_off + i);
       const int gst = __ldg(R.gstar + lo_off + i);
       const bool chi = __ldg(R.flags + lo_off + i) & 1;
+      if (owns_nothing(g, c, gst, chi, cut, xa_t, xb_t, P_t)) continue;
       uint64_t own = accept_mask<uint64_t>(g, c, gst, chi, cut, R.R_w, base, nb, false) & win;
       if (own) own &= ~accept_mask<uint64_t>(g - 1, c, gst, chi, cut, R.R_w, base, nb, true);
       if (!own) continue;
@@ -858,20 +910,25 @@ __global__ void __launch_bounds__(kLWarps * 32)
       // pair p uses bits p (R slot of node 2p) and p + 1 (L of node 2p, M of node 2p+1)
       const int pa = max(__ffsll((long long)own) - 2, 0);
       const int pb = min(63 - __clzll((long long)own), kLPairs - 1);
-      for (int p = pa; p <= pb; ++p) {
+      // a chi branch common to all nodes 2pa .. 2pb + 1: one exponential per line
+      const bool run = use_chi && ct.uniform(2 * pa, 2 * pb + 1);
+      ChiRun cr;
+      if (run) cr.init(ct, 2 * pa, nx.absd((float)(2 * pa), s - 1), s - 1);
+      const float r2 = run ? cr.ratio * cr.ratio : 1.0f;
+      for (int p = pa; p <= pb; ++p, cr.v *= r2) {
         const bool bR = (own >> p) & 1ull, bL = (own >> (p + 1)) & 1ull;
         if (!(bR || bL)) continue;
         const float jf = (float)(2 * p);
         const float xv = nx.x(jf);
         float v = amp * (voigt ? voigt_K<false, true>(xv, y, kVoigtCells) : shape_f(R.shape, xv, y));
-        if (use_chi) v *= ct.value(2 * p, nx.absd(jf, s - 1));
+        if (use_chi) v *= run ? cr.v : ct.value(2 * p, nx.absd(jf, s - 1));
         if (bL) accL[warp][p][lane] += v;
         if (bR) accR[warp][p][lane] += v;
         count_eval<COUNT>(voigt, xv, y, nev, nnear, nmid, nsmall);
         if (bL) {
           const float xw = nx.x(jf + 1.0f);
           float w = amp * (voigt ? voigt_K<false, true>(xw, y, kVoigtCells) : shape_f(R.shape, xw, y));
-          if (use_chi) w *= ct.value(2 * p + 1, nx.absd(jf + 1.0f, s - 1));
+          if (use_chi) w *= run ? cr.v * cr.ratio : ct.value(2 * p + 1, nx.absd(jf + 1.0f, s - 1));
           accM[warp][p][lane] += w;
           count_eval<COUNT>(voigt, xw, y, nev, nnear, nmid, nsmall);
         }
@@ -964,6 +1021,7 @@ __global__ void __launch_bounds__(kCWarps * 32)
     }
     const int64_t lo_off = (int64_t)lev * R.n_lines;
     const int64_t X0 = m0 << s;  // position of node 2 m0 (j = 0)
+    const int64_t xa_t = base << s, xb_t = (base + nb) << s, P_t = int64_t(1) << s;  // span of the mask's panels
     const bool physical = R.shape < kShapeConst;
     const bool voigt = R.shape == kShapeVoigt;
     const int p = lane;
@@ -987,8 +1045,10 @@ __global__ void __launch_bounds__(kCWarps * 32)
           c = __ldg(R.c + lo_off + i);
           const int gst = __ldg(R.gstar + lo_off + i);
           chi = __ldg(R.flags + lo_off + i) & 1;
-          own = accept_mask<uint64_t>(g, c, gst, chi, cut, R.R_w, base, nb, false) & win;
-          if (own) own &= ~accept_mask<uint64_t>(g - 1, c, gst, chi, cut, R.R_w, base, nb, true);
+          if (!owns_nothing(g, c, gst, chi, cut, xa_t, xb_t, P_t)) {
+            own = accept_mask<uint64_t>(g, c, gst, chi, cut, R.R_w, base, nb, false) & win;
+            if (own) own &= ~accept_mask<uint64_t>(g - 1, c, gst, chi, cut, R.R_w, base, nb, true);
+          }
         }
         const uint32_t any = __ballot_sync(0xffffffffu, own != 0);
         if (!any) continue;
@@ -1048,19 +1108,24 @@ __global__ void __launch_bounds__(kCWarps * 32)
           if (use_chi) ct.init(c, X0, s - 1);
           const int pa = max(__ffsll((long long)own) - 2, 0);
           const int pb = min(63 - __clzll((long long)own), kCPairs - 1);
-          for (int q = pa; q <= pb; ++q) {
+          // a chi branch common to all nodes 2pa .. 2pb + 1: one exponential per line
+          const bool run = use_chi && ct.uniform(2 * pa, 2 * pb + 1);
+          ChiRun cr;
+          if (run) cr.init(ct, 2 * pa, nx.absd((float)(2 * pa), s - 1), s - 1);
+          const float r2 = run ? cr.ratio * cr.ratio : 1.0f;
+          for (int q = pa; q <= pb; ++q, cr.v *= r2) {
             const bool bR = (own >> q) & 1ull, bL = (own >> (q + 1)) & 1ull;
             if (!(bR || bL)) continue;
             const float jf = (float)(2 * q);
             const float xv = nx.x(jf);
             float v = amp * (voigt ? voigt_K<true>(xv, y, stab) : shape_f(R.shape, xv, y));
-            if (use_chi) v *= ct.value(2 * q, nx.absd(jf, s - 1));
+            if (use_chi) v *= run ? cr.v : ct.value(2 * q, nx.absd(jf, s - 1));
             bE[lane][q] = v;
             count_eval<COUNT>(voigt, xv, y, nev, nnear, nmid, nsmall);
             if (bL) {
               const float xw = nx.x(jf + 1.0f);
               float w = amp * (voigt ? voigt_K<true>(xw, y, stab) : shape_f(R.shape, xw, y));
-              if (use_chi) w *= ct.value(2 * q + 1, nx.absd(jf + 1.0f, s - 1));
+              if (use_chi) w *= run ? cr.v * cr.ratio : ct.value(2 * q + 1, nx.absd(jf + 1.0f, s - 1));
               bO[lane][q] = w;
               count_eval<COUNT>(voigt, xw, y, nev, nnear, nmid, nsmall);
             }
