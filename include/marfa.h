@@ -158,16 +158,19 @@ int marfa_absorption_batch(int32_t n_req, const marfa_lines_t* const* lines,
  *              caller and kept by the plan: every execution rewrites them;
  *   lines    : must stay alive until marfa_plan_destroy; levels, vmr and rq are copied,
  *              and so is the loaded surrogate for requests with surrogate = 1;
- *   flags    : MARFA_PLAN_AUTOTUNE: for each of grids 2..10, time the two summation
- *              kernels (line-major: a thread per candidate line over 32 node pairs;
- *              two-phase: warps of 32 node pairs that stage 32 lines at a time) on this
- *              batch's own work and keep the faster (otherwise grids 2..7 line-major,
- *              8..10 two-phase); MARFA_PLAN_SERIAL: capture grids 1..10 one after the
+ *   flags    : MARFA_PLAN_AUTOTUNE: for each of grids 2..10, time the three summation
+ *              kernels (line-major: a thread per candidate line over 32 or over 16 node
+ *              pairs; two-phase: warps of 32 node pairs that stage 32 lines at a time)
+ *              on this batch's own work and keep the fastest (otherwise grids 2..7
+ *              line-major over 32 pairs, 8..10 two-phase); MARFA_PLAN_SERIAL: capture
+ *              grids 1..10 one after the
  *              other (otherwise they are parallel branches of the graph, which the GPU
  *              runs concurrently, and per-kernel times overlap);
  *   stream   : used for creation (synchronised before return).
  * Results equal marfa_absorption_batch's bit for bit when the kernel choice is the
- * default; the other variant sums in another order (same tolerance to the oracle).
+ * default; the other variants sum in another order (same tolerance to the oracle). With
+ * surrogate requests, creation also makes one counted run and gives the grids where the
+ * surrogate's guard never holds for this batch the plain kernels (same results).
  * Errors: those of marfa_absorption_batch, host k_out (MARFA_E_INVAL), capture errors
  * (MARFA_E_CUDA). The paper has no counterpart (it runs one level at a time on CPUs).
  */
@@ -184,8 +187,9 @@ int marfa_plan_create(int32_t n_req, const marfa_lines_t* const* lines,
 int marfa_plan_execute(marfa_plan_t* plan, void* stream);
 
 /* Kernel choice and timings (host arrays, each may be NULL): variant[10] for grids
- * 1..10 (-1 grid 1, 0 line-major, 1 two-phase); tune_ms[10][2] the autotuner's time
- * per launch of each variant (-1 when not tuned); kernel_ms[12] device time of the last
+ * 1..10 (-1 grid 1, 0 line-major over 32 pairs, 1 two-phase, 2 line-major over 16
+ * pairs); tune_ms[10][3] the autotuner's time per launch of each variant (-1 when not
+ * tuned); kernel_ms[12] device time of the last
  * execution per kernel kind (0 level preparation, 1..10 grids, 11 finest grid; waits for
  * that execution; MARFA_E_CUDA before the first execution). */
 int marfa_plan_info(const marfa_plan_t* plan, int32_t* variant, float* tune_ms, double* kernel_ms);

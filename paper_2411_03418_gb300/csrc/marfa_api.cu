@@ -467,11 +467,15 @@ static bool is_device_ptr(const void* p) {
 }
 
 // Kernel variants of grids 2..10: 0 = line-major (k_coarse_lm, kLPairs node pairs per
-// CTA), 1 = two-phase (k_coarse, kCWarps x kCPairs node pairs per CTA). Without tuning,
+// CTA), 1 = two-phase (k_coarse, kCWarps x kCPairs node pairs per CTA), 2 = line-major
+// with 16 node pairs per CTA (half the shared memory, narrower tiles). Without tuning,
 // grids 2..kLastLM take the line-major kernel (few lines own a panel there, so a thread
 // per line wastes little) and the finer grids the two-phase one.
+constexpr int kNVariants = 3;
 static int default_variant(int g) { return g <= kLastLM ? 0 : 1; }
-static int64_t variant_pairs(int v) { return v == 0 ? (int64_t)kLPairs : (int64_t)kCPairs * kCWarps; }
+static int64_t variant_pairs(int v) {
+  return v == 0 ? (int64_t)kLPairs : (v == 1 ? (int64_t)kCPairs * kCWarps : (int64_t)16);
+}
 
 static void coarse_items(const Plan& P, int g, int v, std::vector<CoarseItem>& out) {
   const ReqDev& R = P.rd;
@@ -564,7 +568,8 @@ struct WorkSet {
   std::vector<CoarseItem> ci[kNGrid + 1];  // grids 2..10
   std::vector<FineItem> fi;
   int variant[kNGrid + 1] = {0};
-  bool surr = false;
+  bool surr = false;                       // some request uses the surrogate
+  bool surr_grid[kNGrid + 2] = {false};    // surrogate-capable kernels for grid 1..10, 11 finest
   size_t cw = 8 * kCountFields;            // count bytes per item
   void* buf = nullptr;
   ReqDev* drd = nullptr;
@@ -587,6 +592,7 @@ static int build_work(std::vector<Plan>& plans, const int* variant, bool count, 
                       cudaStream_t st) {
   for (auto& P : plans) W.rds.push_back(P.rd);
   for (auto& R : W.rds) W.surr = W.surr || R.mlp != nullptr;
+  for (int g = 1; g <= kNGrid + 1; ++g) W.surr_grid[g] = W.surr;
   for (auto& P : plans) W.gi.insert(W.gi.end(), P.g1.begin(), P.g1.end());
   for (int g = 2; g <= kNGrid; ++g) {
     W.variant[g] = variant ? variant[g] : default_variant(g);
@@ -644,16 +650,16 @@ static int build_work(std::vector<Plan>& plans, const int* variant, bool count, 
 // Grid g of a work set with kernel variant v.
 static void launch_grid(const WorkSet& W, int g, cudaStream_t st) {
   const int n = (int)W.ci[g].size();
-  if (W.variant[g] == 0)
-    launch_coarse_lm(W.drd, W.dci[g], n, W.dcc[g], W.surr, st);
+  if (W.variant[g] == 1)
+    launch_coarse(W.drd, W.dci[g], n, W.dcc[g], W.surr_grid[g], st);
   else
-    launch_coarse(W.drd, W.dci[g], n, W.dcc[g], W.surr, st);
+    launch_coarse_lm(W.drd, W.dci[g], n, W.dcc[g], W.surr_grid[g], W.variant[g] == 2 ? 16 : kLPairs, st);
 }
 
 // Every summation launch of a work set: grid 1, grids 2..10, finest grid + cascade.
 static int launch_work(const WorkSet& W, cudaStream_t st, bool timed) {
   cudaEvent_t ev = timed ? timing_begin(st) : nullptr;
-  launch_g1(W.drd, W.dgi, (int)W.gi.size(), W.dgc, W.surr, st);
+  launch_g1(W.drd, W.dgi, (int)W.gi.size(), W.dgc, W.surr_grid[1], st);
   timing_end(ev, 1, st);
   cudaError_t e;
   if ((e = cudaGetLastError())) return fail(MARFA_E_CUDA, "grid-1 kernel: %s", cudaGetErrorString(e));
@@ -664,7 +670,7 @@ static int launch_work(const WorkSet& W, cudaStream_t st, bool timed) {
   }
   if ((e = cudaGetLastError())) return fail(MARFA_E_CUDA, "coarse-grid kernel: %s", cudaGetErrorString(e));
   ev = timed ? timing_begin(st) : nullptr;
-  launch_fine(W.drd, W.dfi, (int)W.fi.size(), W.dfc, W.surr, st);
+  launch_fine(W.drd, W.dfi, (int)W.fi.size(), W.dfc, W.surr_grid[kNGrid + 1], st);
   timing_end(ev, kNGrid + 1, st);
   if ((e = cudaGetLastError())) return fail(MARFA_E_CUDA, "fine kernel: %s", cudaGetErrorString(e));
   return MARFA_OK;
@@ -782,7 +788,7 @@ struct marfa_plan {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t ev[2 * kKinds] = {nullptr};
-  float tune_ms[kNGrid + 1][2] = {};
+  float tune_ms[kNGrid + 1][kNVariants] = {};
   bool tuned = false;
   MlpWeights* mlp = nullptr;  // the plan's own copy of the surrogate (if any request uses it)
   bool serial = false;        // capture the coarse grids one after the other
@@ -813,23 +819,21 @@ extern "C" void marfa_plan_destroy(marfa_plan_t* X) {
   delete X;
 }
 
-// Time grid g's launch with either kernel variant on the plan's own work (two timed
-// launches after one warm-up each) and keep the faster variant.
+// Time grid g's launch with each kernel variant on the plan's own work (two timed
+// launches after one warm-up each) and keep the fastest.
 static int plan_autotune(marfa_plan_t* X, cudaStream_t st, int* chosen) {
-  WorkSet A[2];
-  int all[2][kNGrid + 1];
-  for (int g = 0; g <= kNGrid; ++g) {
-    all[0][g] = 0;
-    all[1][g] = 1;
-  }
-  int r = build_work(X->plans, all[0], false, A[0], st);
-  if (!r) r = build_work(X->plans, all[1], false, A[1], st);
+  WorkSet A[kNVariants];
+  int all[kNVariants][kNGrid + 1];
+  for (int v = 0; v < kNVariants; ++v)
+    for (int g = 0; g <= kNGrid; ++g) all[v][g] = v;
+  int r = MARFA_OK;
+  for (int v = 0; v < kNVariants && !r; ++v) r = build_work(X->plans, all[v], false, A[v], st);
   cudaEvent_t a = nullptr, b = nullptr;
   cudaError_t e = cudaSuccess;
   if (!r && ((e = cudaEventCreate(&a)) || (e = cudaEventCreate(&b))))
     r = fail(MARFA_E_CUDA, "autotune events: %s", cudaGetErrorString(e));
   for (int g = 2; g <= kNGrid && !r; ++g) {
-    for (int v = 0; v < 2 && !r; ++v) {
+    for (int v = 0; v < kNVariants && !r; ++v) {
       launch_grid(A[v], g, st);
       cudaEventRecord(a, st);
       launch_grid(A[v], g, st);
@@ -840,21 +844,18 @@ static int plan_autotune(marfa_plan_t* X, cudaStream_t st, int* chosen) {
         r = fail(MARFA_E_CUDA, "autotune of grid %d: %s", g, cudaGetErrorString(e));
       X->tune_ms[g][v] = 0.5f * ms;
     }
-    chosen[g] = X->tune_ms[g][0] <= X->tune_ms[g][1] ? 0 : 1;
+    int best = 0;
+    for (int v = 1; v < kNVariants; ++v)
+      if (X->tune_ms[g][v] < X->tune_ms[g][best]) best = v;
+    chosen[g] = best;
   }
   if (a) cudaEventDestroy(a);
   if (b) cudaEventDestroy(b);
-  free_work(A[0], st);
-  free_work(A[1], st);
+  for (int v = 0; v < kNVariants; ++v) free_work(A[v], st);
   X->tuned = !r;
   return r;
 }
 
-// All launches of a plan. With side streams (inside stream capture) the ten coarse-grid
-// launches fork from the level preparation into parallel graph branches, which the GPU
-// runs concurrently (each writes only its own grid's slots), and join before the finest
-// grid; event-record nodes bracket each kernel kind (cudaEventRecordExternal makes them
-// graph nodes that a replay records, rather than capture-internal dependencies).
 static int plan_launch_all(marfa_plan_t* X, cudaStream_t st, bool capture) {
   auto rec = [&](int k, cudaStream_t s) {
     if (capture) cudaEventRecordWithFlags(X->ev[k], s, cudaEventRecordExternal);
@@ -872,7 +873,7 @@ static int plan_launch_all(marfa_plan_t* X, cudaStream_t st, bool capture) {
     for (int i = 0; i < kSide; ++i) cudaStreamWaitEvent(X->side[i], X->fork, 0);
   }
   rec(2, br[1]);
-  launch_g1(W.drd, W.dgi, (int)W.gi.size(), nullptr, W.surr, br[1]);
+  launch_g1(W.drd, W.dgi, (int)W.gi.size(), nullptr, W.surr_grid[1], br[1]);
   rec(3, br[1]);
   for (int g = kNGrid; g >= 2; --g) {  // the finer grids carry more work: start them first
     rec(2 * g, br[g]);
@@ -885,7 +886,7 @@ static int plan_launch_all(marfa_plan_t* X, cudaStream_t st, bool capture) {
       cudaStreamWaitEvent(st, X->join[i], 0);
     }
   rec(2 * (kNGrid + 1), st);
-  launch_fine(W.drd, W.dfi, (int)W.fi.size(), nullptr, W.surr, st);
+  launch_fine(W.drd, W.dfi, (int)W.fi.size(), nullptr, W.surr_grid[kNGrid + 1], st);
   rec(2 * (kNGrid + 1) + 1, st);
   cudaError_t e = cudaGetLastError();
   if (e) return fail(MARFA_E_CUDA, "plan launches: %s", cudaGetErrorString(e));
@@ -934,6 +935,26 @@ extern "C" int marfa_plan_create(int32_t n_req, const marfa_lines_t* const* line
     r = plan_autotune(X, st, chosen);
   }
   if (!r) r = build_work(X->plans, chosen, false, X->W, st);
+  // with the surrogate: one counted run; grids where its guard never holds for this batch
+  // take the plain kernels (same results, without the network's registers and shared
+  // memory)
+  if (!r && X->W.surr) {
+    WorkSet C;
+    r = build_work(X->plans, chosen, true, C, st);
+    if (!r) {
+      for (auto& P : X->plans) launch_prep(P, st, false);
+      r = launch_work(C, st, false);
+    }
+    std::vector<std::vector<int64_t>> cnt(X->plans.size());
+    if (!r) r = read_counts(C, X->plans, st, cnt.data());
+    if (!r) {
+      int64_t per_grid[kNGrid + 2] = {0};
+      for (auto& v : cnt)
+        for (size_t i = 0; i < v.size() / kCountFields; ++i) per_grid[1 + i % 11] += v[kCountFields * i + 1];
+      for (int g = 1; g <= kNGrid + 1; ++g) X->W.surr_grid[g] = per_grid[g] > 0;
+    }
+    free_work(C, st);
+  }
   cudaError_t e = cudaSuccess;
   for (int k = 0; k < 2 * kKinds && !r; ++k)
     if ((e = cudaEventCreate(&X->ev[k]))) r = fail(MARFA_E_CUDA, "plan events: %s", cudaGetErrorString(e));
@@ -985,7 +1006,8 @@ extern "C" int marfa_plan_info(const marfa_plan_t* X, int32_t* variant, float* t
     for (int g = 1; g <= kNGrid; ++g) variant[g - 1] = g == 1 ? -1 : X->W.variant[g];
   if (tune_ms)
     for (int g = 1; g <= kNGrid; ++g)
-      for (int v = 0; v < 2; ++v) tune_ms[2 * (g - 1) + v] = (X->tuned && g > 1) ? X->tune_ms[g][v] : -1.0f;
+      for (int v = 0; v < kNVariants; ++v)
+        tune_ms[kNVariants * (g - 1) + v] = (X->tuned && g > 1) ? X->tune_ms[g][v] : -1.0f;
   if (kernel_ms) {
     for (int k = 0; k < kKinds; ++k) {
       float ms = 0;
@@ -1141,7 +1163,7 @@ extern "C" int marfa_absorption_noalloc(const marfa_lines_t* lines, const marfa_
     size_t k1 = k;
     while (k1 < coarse.size() && coarse[k1].grid == g) ++k1;
     if (default_variant(g) == 0)
-      launch_coarse_lm(drd, dci + k, (int)(k1 - k), nullptr, surr, st);
+      launch_coarse_lm(drd, dci + k, (int)(k1 - k), nullptr, surr, kLPairs, st);
     else
       launch_coarse(drd, dci + k, (int)(k1 - k), nullptr, surr, st);
     k = k1;

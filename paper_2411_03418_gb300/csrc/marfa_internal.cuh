@@ -131,7 +131,7 @@ constexpr int kG1Split = 4;          // CTAs sharing one G1 tile's candidate lin
                                      // writes its own copy of the tile's slots
 constexpr int kG1Warps = 8;          // warps of a G1 CTA, each takes every 8th staged line
 constexpr int kG1Batch = 512;        // lines staged in shared memory at a time
-constexpr int kLPairs = 32;          // node pairs per CTA of the line-major kernel (grids 2..kLastLM)
+constexpr int kLPairs = 32;          // node pairs per CTA of the line-major kernel (or 16)
 constexpr int kLWarps = 4;
 constexpr int kLastLM = 7;           // grids 2..7 line-major, 8..10 two-phase
 constexpr int kCPairs = 32;          // node pairs per warp tile of the two-phase kernel
@@ -167,7 +167,7 @@ void launch_g1(const ReqDev* reqs, const G1Item* items, int n_items, int64_t* co
 void launch_coarse(const ReqDev* reqs, const CoarseItem* items, int n_items, int64_t* counts,
                    bool surr, cudaStream_t st);
 void launch_coarse_lm(const ReqDev* reqs, const CoarseItem* items, int n_items, int64_t* counts,
-                      bool surr, cudaStream_t st);
+                      bool surr, int pairs, cudaStream_t st);
 void launch_fine(const ReqDev* reqs, const FineItem* items, int n_items, int64_t* counts, bool surr,
                  cudaStream_t st);
 void launch_diag_voigt(const float* x, const float* y, float* out, int64_t n, cudaStream_t st);

@@ -766,20 +766,20 @@ void launch_g1(const ReqDev* reqs, const G1Item* items, int n_items, int64_t* co
 }
 
 // ------------------------------------------------------------------ grids 2..10, line-major
-// A CTA owns kLPairs consecutive node pairs of grid g of one level. Each thread takes
+// A CTA owns PAIRS (16 or 32) consecutive node pairs of grid g of one level. Each thread takes
 // one candidate line at a time, forms the exact mask of the panels the line owns in
 // the tile, evaluates the profile at the nodes of those panels only, and adds the
 // values into lane-private shared-memory slots (acc[pair][lane]); the slots are summed
 // over lanes and warps in a fixed order at the end.
-template <bool COUNT, bool SURR>
+template <bool COUNT, bool SURR, int PAIRS>
 __global__ void __launch_bounds__(kLWarps * 32)
     k_coarse_lm(const ReqDev* __restrict__ reqs, const CoarseItem* __restrict__ items,
              int64_t* __restrict__ counts) {
   extern __shared__ __align__(16) unsigned char dsm[];  // surrogate weights (SURR only)
   MlpWeights& S = *reinterpret_cast<MlpWeights*>(dsm);
-  __shared__ float accL[kLWarps][kLPairs][32];
-  __shared__ float accM[kLWarps][kLPairs][32];
-  __shared__ float accR[kLWarps][kLPairs][32];
+  __shared__ float accL[kLWarps][PAIRS][32];
+  __shared__ float accM[kLWarps][PAIRS][32];
+  __shared__ float accR[kLWarps][PAIRS][32];
   __shared__ int64_t sCnt[kCountFields][kLWarps];
   const CoarseItem it = items[blockIdx.x];
   const ReqDev& R = reqs[it.req];
@@ -792,9 +792,9 @@ __global__ void __launch_bounds__(kLWarps * 32)
   const int s = panel_shift(g);
   const int64_t cut = R.cut_fx;
   const int64_t base = m0 - 1;  // mask bit b <-> panel m0 - 1 + b
-  const int nb = kLPairs + 1;
+  const int nb = PAIRS + 1;
   const uint64_t win = rmask<uint64_t>(m_first, m_last, base, nb);
-  for (int p = 0; p < kLPairs; ++p) {
+  for (int p = 0; p < PAIRS; ++p) {
     accL[warp][p][lane] = 0.0f;
     accM[warp][p][lane] = 0.0f;
     accR[warp][p][lane] = 0.0f;
@@ -860,7 +860,7 @@ __global__ void __launch_bounds__(kLWarps * 32)
           nx.init(X0 - c, s - 1, __ldg(R.sx + lo_off + i));
           if (use_chi) ct.init(c, X0, s - 1);
           pa = max(__ffsll((long long)own) - 2, 0);
-          pb = min(63 - __clzll((long long)own), kLPairs - 1);
+          pb = min(63 - __clzll((long long)own), PAIRS - 1);
         }
         const int qa = __reduce_min_sync(0xffffffffu, pa), qb = __reduce_max_sync(0xffffffffu, pb);
         for (int p = qa; p <= qb; ++p) {
@@ -909,7 +909,7 @@ __global__ void __launch_bounds__(kLWarps * 32)
       if (use_chi) ct.init(c, X0, s - 1);
       // pair p uses bits p (R slot of node 2p) and p + 1 (L of node 2p, M of node 2p+1)
       const int pa = max(__ffsll((long long)own) - 2, 0);
-      const int pb = min(63 - __clzll((long long)own), kLPairs - 1);
+      const int pb = min(63 - __clzll((long long)own), PAIRS - 1);
       // a chi branch common to all nodes 2pa .. 2pb + 1: one exponential per line
       const bool run = use_chi && ct.uniform(2 * pa, 2 * pb + 1);
       ChiRun cr;
@@ -937,10 +937,10 @@ __global__ void __launch_bounds__(kLWarps * 32)
   }
   if (SURR && use_mlp) q_flush(warp_queue(dsm), qn, S, lm_apply);
   __syncthreads();
-  // thread t < 3 kLPairs sums slot (t / kLPairs, pair t % kLPairs) over warps and lanes
-  if (tid < 3 * kLPairs) {
-    const int kind = tid / kLPairs, p = tid % kLPairs;
-    float (*acc)[kLPairs][32] = kind == 0 ? accL : (kind == 1 ? accM : accR);
+  // thread t < 3 PAIRS sums slot (t / PAIRS, pair t % PAIRS) over warps and lanes
+  if (tid < 3 * PAIRS) {
+    const int kind = tid / PAIRS, p = tid % PAIRS;
+    float (*acc)[PAIRS][32] = kind == 0 ? accL : (kind == 1 ? accM : accR);
     float sum = 0.0f, cmp = 0.0f;
     for (int w = 0; w < kLWarps; ++w)
       for (int l = 0; l < 32; ++l) kahan_add(sum, cmp, acc[w][p][(l + p) & 31]);
@@ -956,17 +956,31 @@ __global__ void __launch_bounds__(kLWarps * 32)
 }
 
 void launch_coarse_lm(const ReqDev* reqs, const CoarseItem* items, int n_items, int64_t* counts,
-                      bool surr, cudaStream_t st) {
+                      bool surr, int pairs, cudaStream_t st) {
   if (n_items <= 0) return;
+  const int T = kLWarps * 32;
+  if (pairs == 16) {
+    if (surr) {
+      if (counts)
+        launch_surr(k_coarse_lm<true, true, 16>, n_items, T, st, reqs, items, counts);
+      else
+        launch_surr(k_coarse_lm<false, true, 16>, n_items, T, st, reqs, items, counts);
+    } else if (counts) {
+      k_coarse_lm<true, false, 16><<<n_items, T, 0, st>>>(reqs, items, counts);
+    } else {
+      k_coarse_lm<false, false, 16><<<n_items, T, 0, st>>>(reqs, items, counts);
+    }
+    return;
+  }
   if (surr) {
     if (counts)
-      launch_surr(k_coarse_lm<true, true>, n_items, kLWarps * 32, st, reqs, items, counts);
+      launch_surr(k_coarse_lm<true, true, 32>, n_items, T, st, reqs, items, counts);
     else
-      launch_surr(k_coarse_lm<false, true>, n_items, kLWarps * 32, st, reqs, items, counts);
+      launch_surr(k_coarse_lm<false, true, 32>, n_items, T, st, reqs, items, counts);
   } else if (counts) {
-    k_coarse_lm<true, false><<<n_items, kLWarps * 32, 0, st>>>(reqs, items, counts);
+    k_coarse_lm<true, false, 32><<<n_items, T, 0, st>>>(reqs, items, counts);
   } else {
-    k_coarse_lm<false, false><<<n_items, kLWarps * 32, 0, st>>>(reqs, items, counts);
+    k_coarse_lm<false, false, 32><<<n_items, T, 0, st>>>(reqs, items, counts);
   }
 }
 
@@ -1025,15 +1039,20 @@ __global__ void __launch_bounds__(kCWarps * 32)
     const bool physical = R.shape < kShapeConst;
     const bool voigt = R.shape == kShapeVoigt;
     const int p = lane;
-    float sL = 0.f, cL = 0.f, sR = 0.f, cR = 0.f, sM = 0.f, cM = 0.f;
     float (*bE)[kCPairs + 1] = bufE[warp];
     float (*bO)[kCPairs + 1] = bufO[warp];
     unsigned long long* mk = smsk[warp];
     int qn = 0;  // entries in this warp's surrogate queue (warp-uniform)
-    // surrogate results: tag bits 0-4 pair, bit 5 odd node
+    float sL = 0.f, cL = 0.f, sR = 0.f, cR = 0.f, sM = 0.f, cM = 0.f;
+    // surrogate results, applied by the lane of the pair they belong to (the queue owner):
+    // tag bits 0-4 pair, 5 L slot, 6 R slot (even node), 7 M slot (odd node)
     auto tp_apply = [&](int tag, float v) {
-      if (tag & 32) bO[lane][tag & 31] = v;
-      else bE[lane][tag & 31] = v;
+      if (tag & 128) {
+        kahan_add(sM, cM, v);
+      } else {
+        if (tag & 32) kahan_add(sL, cL, v);
+        if (tag & 64) kahan_add(sR, cR, v);
+      }
     };
     for (int r = 0; r < bd.n; ++r) {
       for (int64_t i0 = bd.lo[r]; i0 < bd.hi[r]; i0 += 32) {
@@ -1080,23 +1099,29 @@ __global__ void __launch_bounds__(kCWarps * 32)
             const bool ue = ae && mlp_guard(S, xv, y), uo = ao && mlp_guard(S, xw, y);
             const float ce = (use_chi && ae) ? ct.value(2 * q, nx.absd(jf, s - 1)) : 1.0f;
             const float co = (use_chi && ao) ? ct.value(2 * q + 1, nx.absd(jf + 1.0f, s - 1)) : 1.0f;
-            q_push(warp_queue(dsm), qn, ue, xv, y, amp * ce, q);
-            q_push(warp_queue(dsm), qn, uo, xw, y, amp * co, q | 32);
-            if (ae && !ue) {
-              float v = amp * voigt_K<true>(xv, y, stab);
-              if (use_chi) v *= ce;
+            // deferred values go straight to the pair's lane; the buffer gets 0 there
+            q_push(warp_queue(dsm), qn, ue, xv, y, amp * ce, q | (bL ? 32 : 0) | (bR ? 64 : 0), q);
+            q_push(warp_queue(dsm), qn, uo, xw, y, amp * co, q | 128, q);
+            if (ae) {
+              float v = 0.0f;
+              if (!ue) {
+                v = amp * voigt_K<true>(xv, y, stab);
+                if (use_chi) v *= ce;
+              }
               bE[lane][q] = v;
             }
-            if (ao && !uo) {
-              float w = amp * voigt_K<true>(xw, y, stab);
-              if (use_chi) w *= co;
+            if (ao) {
+              float w = 0.0f;
+              if (!uo) {
+                w = amp * voigt_K<true>(xw, y, stab);
+                if (use_chi) w *= co;
+              }
               bO[lane][q] = w;
             }
             if (ae) count_eval<COUNT>(true, xv, y, nev, nnear, nmid, nsmall);
             if (ao) count_eval<COUNT>(true, xw, y, nev, nnear, nmid, nsmall);
             if (COUNT) nmlp += (ue ? 1 : 0) + (uo ? 1 : 0);
           }
-          q_flush(warp_queue(dsm), qn, S, tp_apply);
         } else if (own) {
           const float amp = __ldg(R.amp + lo_off + i);
           const float sx = __ldg(R.sx + lo_off + i);
@@ -1153,6 +1178,7 @@ __global__ void __launch_bounds__(kCWarps * 32)
         __syncwarp();
       }
     }
+    if (SURR && use_mlp) q_flush(warp_queue(dsm), qn, S, tp_apply);  // warp-uniform
     float* gp = R.slots + (int64_t)lev * R.slots_per_level + R.slot_off[g];
     const int64_t np = R.npan[g];
     const int64_t m = m0 + p;

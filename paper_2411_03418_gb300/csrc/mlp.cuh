@@ -177,8 +177,9 @@ struct SurrQueue {
   uint8_t owner[kQCap];
 };
 
+// owner: the lane that applies the result (default: the pushing lane).
 __device__ __forceinline__ void q_push(SurrQueue& Q, int& n, bool want, float x, float y, float w,
-                                       int tag) {
+                                       int tag, int owner = -1) {
   const int lane = threadIdx.x & 31;
   const unsigned b = __ballot_sync(0xffffffffu, want);
   if (want) {
@@ -187,7 +188,7 @@ __device__ __forceinline__ void q_push(SurrQueue& Q, int& n, bool want, float x,
     Q.y[pos] = y;
     Q.w[pos] = w;
     Q.tag[pos] = (uint16_t)tag;
-    Q.owner[pos] = (uint8_t)lane;
+    Q.owner[pos] = (uint8_t)(owner < 0 ? lane : owner);
   }
   n += __popc(b);
 }

@@ -245,9 +245,9 @@ def marfa_plan_execute(plan: Plan, stream=None) -> None:
 
 
 def marfa_plan_info(plan: Plan, kernel_ms: bool = False):
-    """(variant[10], tune_ms[10, 2], kernel_ms[12] or None)."""
+    """(variant[10], tune_ms[10, 3], kernel_ms[12] or None)."""
     v = np.empty(10, dtype=np.int32)
-    t = np.empty((10, 2), dtype=np.float32)
+    t = np.empty((10, 3), dtype=np.float32)
     k = np.empty(12, dtype=np.float64) if kernel_ms else None
     _check(load().marfa_plan_info(plan.handle, _ptr(v), _ptr(t), _ptr(k)))
     return v, t, k

@@ -84,10 +84,10 @@ def test_autotuned_plan_parity(M):
     M.marfa_plan_execute(plan)
     torch.cuda.synchronize()
     v, t, _ = M.marfa_plan_info(plan)
-    assert set(v[1:].tolist()) <= {0, 1}
+    assert set(v[1:].tolist()) <= {0, 1, 2}
     assert np.all(t[1:] > 0)
-    for g in range(1, 10):  # the chosen variant is the faster one
-        assert t[g, v[g]] <= t[g, 1 - v[g]]
+    for g in range(1, 10):  # the chosen variant is the fastest one
+        assert t[g, v[g]] <= t[g].min()
     for q, w in enumerate(SMALL):
         got = outs[q].cpu().numpy()
         for lev in range(w.n_levels):

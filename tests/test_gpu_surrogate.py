@@ -215,6 +215,25 @@ def test_surrogate_batch_matches_single(M, loaded):
     assert np.array_equal(oa, ka) and np.array_equal(ob, kb)
 
 
+def test_surrogate_plan_matches_call(M, loaded):
+    """A captured plan of a surrogate request (grids whose guard never fires for the batch
+    switched to the plain kernels) against the direct call and the oracle."""
+    import torch
+    wl = SURR_CASES[0].with_(surrogate=1)
+    direct = _run(M, wl)
+    lines = M.marfa_prepare_lines(wl.lines, wl.species)
+    out = torch.empty(direct.shape, dtype=torch.float32, device="cuda")
+    plan = M.marfa_plan_create([lines], [M.levels_of(wl)], [wl.vmr], [M.request_of(wl)], [out])
+    out.fill_(float("nan"))
+    M.marfa_plan_execute(plan)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    for lev in range(wl.n_levels):
+        _assert_close(got[lev], direct[lev], 1e-5, f"plan vs call level {lev}")
+        _assert_close(got[lev], O.eleven_grid(wl, lev), SURR_RTOL, f"plan vs oracle level {lev}")
+    M.marfa_plan_destroy(plan)
+
+
 def test_surrogate_request_validation(M, weights):
     wl = SURR_CASES[1].with_(surrogate=1)
     M.marfa_surrogate_unload()
