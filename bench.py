@@ -164,18 +164,15 @@ def surrogate_leg(args, M, wl, lines, levels, out, flush, stream, wpath, evals_p
         torch.cuda.synchronize()
         kms_s = M.marfa_plan_info(plan, kernel_ms=True)[2]
         M.marfa_plan_destroy(plan)
-        t_total = float(sum(a.elapsed_time(b) for a, b in ev)) / 1e3
-        if dist:
-            tt = torch.tensor([t_total], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t_total = float(tt.item())
+        t_total = max_over_ranks(float(sum(a.elapsed_time(b) for a, b in ev)) / 1e3, dist, dev)
         world = dist.get_world_size() if dist else 1
         mx = plain.abs().amax(dim=1, keepdim=True)
         big = plain.abs() > 1e-8 * mx
         rel = ((out - plain).abs() / plain.abs().clamp_min(1e-38))[big]
         ms = t_total / args.steps * 1e3
-        return {"value": wl.n_levels * npts * world * args.steps / t_total, "unit": UNIT, "ms_per_step": ms,
-                "line_evals_per_s": int(counts.sum()) * world * args.steps / t_total,
+        return {"value": job_throughput(wl.n_levels * npts, world, args.steps, t_total), "unit": UNIT,
+                "ms_per_step": ms,
+                "line_evals_per_s": job_throughput(int(counts.sum()), world, args.steps, t_total),
                 "surrogate_evals_share": float(sc.sum() / max(1, counts.sum())),
                 "surrogate_evals_per_grid": [int(v) for v in sc.sum(axis=0)],
                 "kernel_ms_last_step": [round(float(v), 3) for v in kms_s],
@@ -184,6 +181,23 @@ def surrogate_leg(args, M, wl, lines, levels, out, flush, stream, wpath, evals_p
                 "note": "plain path within 1e-4 of the FP64 oracle; surrogate path within 1e-3 (tests)"}
     finally:
         M.marfa_surrogate_unload()
+
+
+def max_over_ranks(t, dist, dev):
+    """The largest of the ranks' values of t (a float), or t itself on one rank."""
+    if not dist:
+        return float(t)
+    import torch
+    tt = torch.tensor([float(t)], dtype=torch.float64, device=dev)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_throughput(units_per_rank, world, steps, t_max):
+    """Whole-job rate: every rank processes the same workload (weak scaling, one
+    replica per GPU), so the job's units per second are world x units x steps over the
+    slowest rank's time."""
+    return units_per_rank * world * steps / t_max
 
 
 def load_workloads(name):
@@ -241,7 +255,11 @@ def main():
     torch.cuda.set_device(dev)
 
     import __graft_entry__
-    __graft_entry__.build()
+    if rank == 0 or not dist:
+        __graft_entry__.build()  # one rank compiles (if needed); the others wait
+    if dist:
+        dist.barrier()
+        __graft_entry__.build()  # finds the library up to date
     from paper_2411_03418_gb300 import marfa as M
 
     stream = torch.cuda.current_stream()
@@ -295,11 +313,7 @@ def main():
         sampler.wait()
         fh.close()
     clocks = read_clocks(clk_path, torch.cuda.current_device()) if sampler else None
-    t_total = float(sum(step_ms)) / 1e3
-    if dist:
-        tt = torch.tensor([t_total], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total = float(tt.item())
+    t_total = max_over_ranks(float(sum(step_ms)) / 1e3, dist, dev)
     ms_per_step = t_total / args.steps * 1e3
     M.marfa_plan_destroy(plan)
     # per-kernel times for the roofline: the same work as a serial plan (the kernels one
@@ -318,9 +332,10 @@ def main():
     torch.cuda.synchronize()
     serial_ms = float(sum(a.elapsed_time(b) for a, b in ev_s)) / args.steps
     M.marfa_plan_destroy(plan_s)
-    units = sum(w.n_levels * n for w, n in zip(wls, npts)) * world
-    value = units * args.steps / t_total
-    evals_s = evals_per_step * world * args.steps / t_total
+    units_rank = sum(w.n_levels * n for w, n in zip(wls, npts))
+    units = units_rank * world
+    value = job_throughput(units_rank, world, args.steps, t_total)
+    evals_s = job_throughput(evals_per_step, world, args.steps, t_total)
 
     # end to end through the public call with host buffers (pinned): line records in,
     # prepare, absorption (batch call for several requests), k(nu) back, every step
@@ -346,12 +361,8 @@ def main():
         for _ in range(args.steps):
             e2e_step()
         torch.cuda.synchronize()
-        t_e2e = time.perf_counter() - t0
-        if dist:
-            tt = torch.tensor([t_e2e], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t_e2e = float(tt.item())
-    e2e_value = units * args.steps / t_e2e
+        t_e2e = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    e2e_value = job_throughput(units_rank, world, args.steps, t_e2e)
 
     # roofline of the dominant kernel (FP32 pipe, algorithmic flops per evaluation)
     names = ["level_prep"] + [f"grid{g}" for g in range(1, 11)] + ["finest"]

@@ -1,0 +1,50 @@
+"""The multi-rank logic of bench.py on CPU: two gloo ranks (127.0.0.1), each with its own
+time; the job's time is the slowest rank's and its throughput counts every rank's
+replica of the workload (weak scaling, no data-path collective)."""
+import os
+import socket
+
+import pytest
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    t = 1.0 + rank  # rank 1 is slower
+    tmax = bench.max_over_ranks(t, dist, "cpu")
+    v = bench.job_throughput(1000, world, 4, tmax)
+    dist.barrier()
+    dist.destroy_process_group()
+    q.put((rank, tmax, v))
+
+
+def test_two_gloo_ranks_max_time_and_weak_scaling():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    res = sorted(q.get(timeout=10) for _ in range(2))
+    for rank, tmax, v in res:
+        assert tmax == 2.0                    # the slowest rank's time on both ranks
+        assert v == pytest.approx(1000 * 2 * 4 / 2.0)  # both replicas' units over that time
+
+
+def test_single_rank_is_identity():
+    import bench
+    assert bench.max_over_ranks(3.5, None, "cpu") == 3.5
+    assert bench.job_throughput(10, 1, 2, 4.0) == 5.0
