@@ -97,6 +97,13 @@ struct Bands {
     }
     merge();
   }
+  // All candidates of the bands as one sequence 0 .. total-1, so that a loop over them
+  // by a block or a warp leaves idle lanes only in its last round.
+  __device__ __forceinline__ int64_t total() const {
+    int64_t t = 0;
+    for (int r = 0; r < n; ++r) t += hi[r] - lo[r];
+    return t;
+  }
   __device__ __forceinline__ void merge() {
     for (int i = 1; i < n; ++i) {  // insertion sort by lo
       int64_t a = lo[i], b = hi[i];
@@ -123,6 +130,20 @@ struct Bands {
   }
 };
 
+
+// Maps increasing positions t of the flattened candidate sequence of a Bands to line
+// indices (each thread walks forward through the bands).
+struct BandCursor {
+  int r = 0;
+  int64_t start = 0;  // position of band r's first line in the sequence
+  __device__ __forceinline__ int64_t line(const Bands& bd, int64_t t) {
+    while (t - start >= bd.hi[r] - bd.lo[r]) {
+      start += bd.hi[r] - bd.lo[r];
+      ++r;
+    }
+    return bd.lo[r] + (t - start);
+  }
+};
 
 // Position zones where a line centre must lie for the line to own something in the
 // span [A, B]: within Rc of it (centre), at the cut-off distance (edges) or at a chi
@@ -832,16 +853,19 @@ __global__ void __launch_bounds__(kLWarps * 32)
     }
   };
   __syncwarp();
-  for (int r = 0; r < bd.n; ++r) {
-    for (int64_t i0 = bd.lo[r]; i0 < bd.hi[r]; i0 += kLWarps * 32) {
-      const int64_t i = i0 + tid;
+  const int64_t n_cand = bd.total();
+  BandCursor cur;
+  {
+    for (int64_t t0 = 0; t0 < n_cand; t0 += kLWarps * 32) {  // block-uniform
+      const bool valid = t0 + tid < n_cand;
+      const int64_t i = valid ? cur.line(bd, t0 + tid) : 0;
       if (SURR && use_mlp) {
         // all lanes step through the union of their pair ranges together; evaluations
         // that pass the guard go to the warp's queue
         uint64_t own = 0;
         int64_t c = 0;
         bool chi = false;
-        if (i < bd.hi[r]) {
+        if (valid) {
           c = __ldg(R.c + lo_off + i);
           const int gst = __ldg(R.gstar + lo_off + i);
           chi = __ldg(R.flags + lo_off + i) & 1;
@@ -891,7 +915,7 @@ __global__ void __launch_bounds__(kLWarps * 32)
         }
         continue;
       }
-      if (i >= bd.hi[r]) continue;
+      if (!valid) continue;
       const int64_t c = __ldg(R.c + lo_off + i);
       const int gst = __ldg(R.gstar + lo_off + i);
       const bool chi = __ldg(R.flags + lo_off + i) & 1;
@@ -1054,13 +1078,16 @@ __global__ void __launch_bounds__(kCWarps * 32)
         if (tag & 64) kahan_add(sR, cR, v);
       }
     };
-    for (int r = 0; r < bd.n; ++r) {
-      for (int64_t i0 = bd.lo[r]; i0 < bd.hi[r]; i0 += 32) {
-        const int64_t i = i0 + lane;
+    const int64_t n_cand = bd.total();
+    BandCursor cur;
+    {
+      for (int64_t t0 = 0; t0 < n_cand; t0 += 32) {  // warp-uniform
+        const bool valid = t0 + lane < n_cand;
+        const int64_t i = valid ? cur.line(bd, t0 + lane) : 0;
         uint64_t own = 0;
         int64_t c = 0;
         bool chi = false;
-        if (i < bd.hi[r]) {
+        if (valid) {
           c = __ldg(R.c + lo_off + i);
           const int gst = __ldg(R.gstar + lo_off + i);
           chi = __ldg(R.flags + lo_off + i) & 1;
@@ -1270,14 +1297,17 @@ __global__ void __launch_bounds__(kFineThreads)
     const bool physical = R.shape < kShapeConst;
     const bool voigt = R.shape == kShapeVoigt;
     const int mypanel = lane >> 1;
-    for (int r = 0; r < bd.n; ++r) {
-      for (int64_t i0 = bd.lo[r]; i0 < bd.hi[r]; i0 += 32) {
-        const int64_t i = i0 + lane;
+    const int64_t n_cand = bd.total();
+    BandCursor cur;
+    {
+      for (int64_t t0 = 0; t0 < n_cand; t0 += 32) {  // warp-uniform
+        const bool valid = t0 + lane < n_cand;
+        const int64_t i = valid ? cur.line(bd, t0 + lane) : 0;
         uint32_t pm = 0;
         int klo = 0, khi = -1;
         int64_t c = 0;
         bool chi = false;
-        if (i < bd.hi[r]) {
+        if (valid) {
           c = __ldg(R.c + lo_off + i);
           const int gst = __ldg(R.gstar + lo_off + i);
           chi = __ldg(R.flags + lo_off + i) & 1;
