@@ -965,9 +965,17 @@ __global__ void __launch_bounds__(kLWarps * 32)
   if (tid < 3 * PAIRS) {
     const int kind = tid / PAIRS, p = tid % PAIRS;
     float (*acc)[PAIRS][32] = kind == 0 ? accL : (kind == 1 ? accM : accR);
-    float sum = 0.0f, cmp = 0.0f;
-    for (int w = 0; w < kLWarps; ++w)
-      for (int l = 0; l < 32; ++l) kahan_add(sum, cmp, acc[w][p][(l + p) & 31]);
+    // one compensated sum per warp's lanes, interleaved (independent chains), then the
+    // warps' sums merged in warp order
+    float sw[kLWarps], cw[kLWarps];
+#pragma unroll
+    for (int w = 0; w < kLWarps; ++w) sw[w] = cw[w] = 0.0f;
+    for (int l = 0; l < 32; ++l)
+#pragma unroll
+      for (int w = 0; w < kLWarps; ++w) kahan_add(sw[w], cw[w], acc[w][p][(l + p) & 31]);
+    float sum = sw[0], cmp = cw[0];
+#pragma unroll
+    for (int w = 1; w < kLWarps; ++w) comp_merge(sum, cmp, sw[w], cw[w]);
     const float v = sum + cmp;
     float* gp = R.slots + (int64_t)lev * R.slots_per_level + R.slot_off[g];
     const int64_t np = R.npan[g];
