@@ -1244,26 +1244,39 @@ void launch_coarse(const ReqDev* reqs, const CoarseItem* items, int n_items, int
 
 // ------------------------------------------------------------------ finest grid + cascade
 // A CTA owns 1024 consecutive finest nodes of one level; warp w owns 128 of them
-// (16 G10 panels) and lane l four consecutive nodes (one half panel). Each warp loads
-// 32 candidate lines at a time; the loading lane works out which of the warp's G10
-// panels the line leaves to the finest grid (not accepted on G10) and the node range
-// within the cut-off, and stages them in shared memory; every lane then sums the
-// staged lines that own its nodes. Finally each node adds the quadratic interpolants
-// of the ten coarse grids, and the CTA writes its outputs with aligned vector stores.
+// (16 G10 panels of 8 nodes). Each warp loads 32 candidate lines at a time; the loading
+// lane works out which of the warp's G10 panels the line leaves to the finest grid (not
+// accepted on G10) and the node range within the cut-off, and stages them in shared
+// memory. The warp then sums the staged lines over its nodes in four passes: in pass s
+// the lane group gi = lane / 8 takes panel 4 s + gi and lane node 32 s + lane, and each
+// group steps through the staged lines owning its panel in line order, so the eight
+// lanes of a group evaluate one line at eight neighbouring nodes (one code path of the
+// profile per group). Per-node compensated sums live in shared memory. Finally each node
+// adds the quadratic interpolants of the ten coarse grids, and the CTA writes its
+// outputs with aligned vector stores.
+struct __align__(16) FineLine {
+  int klo, khi;        // nodes of the warp in the cut-off
+  float amp, y;
+  float qf, hs, phs, phi;  // NodeX of the line relative to the warp's first node
+};
+struct __align__(16) FineChi {
+  int r3, r150, r300, l3, l150, l300;  // ChiThr relative to the warp's first node
+  int on, pad;                          // chi-factor applies
+};
+
 template <bool COUNT, bool SURR>
 __global__ void __launch_bounds__(kFineThreads)
     k_fine(const ReqDev* __restrict__ reqs, const FineItem* __restrict__ items,
            int64_t* __restrict__ counts) {
   constexpr int NW = kFineThreads / 32;
+  constexpr int kWarpNodes = kFinePerThread * 32;  // nodes of a warp
   extern __shared__ __align__(16) unsigned char dsm[];  // surrogate weights (SURR only)
   MlpWeights& S = *reinterpret_cast<MlpWeights*>(dsm);
   __shared__ float tile[kFineTile];
   __shared__ float stab[kVoigtTableFloats];
-  // staged lines, one slot per lane of each warp (struct of arrays: no bank conflicts)
-  __shared__ float sQ[NW][32], sHs[NW][32], sPhs[NW][32], sPhi[NW][32], sAmp[NW][32], sY[NW][32];
-  __shared__ uint32_t sPm[NW][32];
-  __shared__ int sKlo[NW][32], sKhi[NW][32], sChi[NW][32];
-  __shared__ int sT[6][NW][32];  // chi thresholds r3, r150, r300, l3, l150, l300
+  __shared__ FineLine sL[NW][32];  // staged lines, one per lane of each warp
+  __shared__ FineChi sC[NW][32];
+  __shared__ __align__(16) float sAcc[NW][kWarpNodes], sCmp[NW][kWarpNodes];
   __shared__ int64_t red[kCountFields][NW];
   const FineItem it = items[blockIdx.x];
   const ReqDev& R = reqs[it.req];
@@ -1272,27 +1285,21 @@ __global__ void __launch_bounds__(kFineThreads)
   const bool use_mlp = SURR && R.mlp != nullptr;  // block-uniform
   voigt_table_to_smem(stab);
   if (use_mlp) mlp_load_smem(S, R.mlp);
+#pragma unroll
+  for (int q = 0; q < kFinePerThread; ++q) sAcc[warp][32 * q + lane] = sCmp[warp][32 * q + lane] = 0.0f;
   __syncthreads();
-  const int64_t kw = it.k0 + (int64_t)kFinePerThread * 32 * warp;  // first node of the warp
-  const int64_t k0 = kw + kFinePerThread * lane;                    // first node of the lane
+  const int64_t kw = it.k0 + (int64_t)kWarpNodes * warp;  // first node of the warp
+  const int64_t k0 = kw + kFinePerThread * lane;           // first node of the lane's output
   const int64_t cut = R.cut_fx;
   const LevelDev L = R.lev[lev];
-  float acc[kFinePerThread], cmp[kFinePerThread];
-#pragma unroll
-  for (int q = 0; q < kFinePerThread; ++q) acc[q] = cmp[q] = 0.0f;
   int64_t nev = 0, nmlp = 0, nnear = 0, nmid = 0, nsmall = 0;
-  const int nw = kFinePerThread * 32;  // nodes of the warp
   int qn = 0;  // entries in this warp's surrogate queue (warp-uniform)
-  // surrogate results: the tag is the node q of the owning lane
-  auto fine_apply = [&](int tag, float v) {
-#pragma unroll
-    for (int q = 0; q < kFinePerThread; ++q)
-      if (tag == q) kahan_add(acc[q], cmp[q], v);
-  };
+  // surrogate results: the tag is the warp node
+  auto fine_apply = [&](int tag, float v) { kahan_add(sAcc[warp][tag], sCmp[warp][tag], v); };
   const int wlo = (int)max(R.k_lo - kw, (int64_t)0);
-  const int whi = (int)min(R.k_hi - kw, (int64_t)(nw - 1));
+  const int whi = (int)min(R.k_hi - kw, (int64_t)(kWarpNodes - 1));
   if (wlo <= whi) {  // warp-uniform
-    const int64_t Xa = kw << kFineShift, Xb = (kw + nw - 1) << kFineShift;
+    const int64_t Xa = kw << kFineShift, Xb = (kw + kWarpNodes - 1) << kFineShift;
     const int64_t P10 = int64_t(1) << panel_shift(kNGrid);
     Bands bd;
     {
@@ -1304,127 +1311,120 @@ __global__ void __launch_bounds__(kFineThreads)
     const int64_t lo_off = (int64_t)lev * R.n_lines;
     const bool physical = R.shape < kShapeConst;
     const bool voigt = R.shape == kShapeVoigt;
-    const int mypanel = lane >> 1;
+    const int gi = lane >> 3;  // lane group
     const int64_t n_cand = bd.total();
     BandCursor cur;
-    {
-      for (int64_t t0 = 0; t0 < n_cand; t0 += 32) {  // warp-uniform
-        const bool valid = t0 + lane < n_cand;
-        const int64_t i = valid ? cur.line(bd, t0 + lane) : 0;
-        uint32_t pm = 0;
-        int klo = 0, khi = -1;
-        int64_t c = 0;
-        bool chi = false;
-        if (valid) {
-          c = __ldg(R.c + lo_off + i);
-          const int gst = __ldg(R.gstar + lo_off + i);
-          chi = __ldg(R.flags + lo_off + i) & 1;
-          klo = (int)max(cl_sh(c - cut, kFineShift) - kw, (int64_t)wlo);
-          khi = (int)min(fl_sh(c + cut, kFineShift) - kw, (int64_t)whi);
-          if (klo <= khi) {
-            pm = ~accept_mask<uint32_t>(kNGrid, c, gst, chi, cut, R.R_w, pbase, 16, false) &
-                 rmask<uint32_t>(klo >> 3, khi >> 3, 0, 16);
-          }
+    for (int64_t t0 = 0; t0 < n_cand; t0 += 32) {  // warp-uniform
+      const bool valid = t0 + lane < n_cand;
+      const int64_t i = valid ? cur.line(bd, t0 + lane) : 0;
+      uint32_t pm = 0;
+      int klo = 0, khi = -1;
+      int64_t c = 0;
+      bool chi = false;
+      if (valid) {
+        c = __ldg(R.c + lo_off + i);
+        const int gst = __ldg(R.gstar + lo_off + i);
+        chi = __ldg(R.flags + lo_off + i) & 1;
+        klo = (int)max(cl_sh(c - cut, kFineShift) - kw, (int64_t)wlo);
+        khi = (int)min(fl_sh(c + cut, kFineShift) - kw, (int64_t)whi);
+        if (klo <= khi) {
+          pm = ~accept_mask<uint32_t>(kNGrid, c, gst, chi, cut, R.R_w, pbase, 16, false) &
+               rmask<uint32_t>(klo >> 3, khi >> 3, 0, 16);
         }
-        const uint32_t any = __ballot_sync(0xffffffffu, pm != 0);
-        if (!any) continue;
-        __syncwarp();
-        sPm[warp][lane] = pm;
-        if (pm) {
-          NodeX nx;
-          nx.init(Xa - c, kFineShift, __ldg(R.sx + lo_off + i));
-          sQ[warp][lane] = nx.qf;
-          sHs[warp][lane] = nx.hs;
-          sPhs[warp][lane] = nx.phs;
-          sPhi[warp][lane] = nx.phi;
-          sAmp[warp][lane] = __ldg(R.amp + lo_off + i);
-          sY[warp][lane] = __ldg(R.yv + lo_off + i);
-          sKlo[warp][lane] = klo;
-          sKhi[warp][lane] = khi;
-          const bool uc = chi && physical;
-          sChi[warp][lane] = uc;
-          if (uc) {
-            ChiThr ct;
-            ct.init(c, Xa, kFineShift);
-            sT[0][warp][lane] = ct.r3; sT[1][warp][lane] = ct.r150; sT[2][warp][lane] = ct.r300;
-            sT[3][warp][lane] = ct.l3; sT[4][warp][lane] = ct.l150; sT[5][warp][lane] = ct.l300;
-          }
+      }
+      if (!__ballot_sync(0xffffffffu, pm != 0)) continue;
+      __syncwarp();
+      if (pm) {
+        NodeX nx;
+        nx.init(Xa - c, kFineShift, __ldg(R.sx + lo_off + i));
+        FineLine fl;
+        fl.klo = klo;
+        fl.khi = khi;
+        fl.amp = __ldg(R.amp + lo_off + i);
+        fl.y = __ldg(R.yv + lo_off + i);
+        fl.qf = nx.qf;
+        fl.hs = nx.hs;
+        fl.phs = nx.phs;
+        fl.phi = nx.phi;
+        sL[warp][lane] = fl;
+        FineChi fc;
+        fc.on = chi && physical;
+        if (fc.on) {
+          ChiThr ct;
+          ct.init(c, Xa, kFineShift);
+          fc.r3 = ct.r3; fc.r150 = ct.r150; fc.r300 = ct.r300;
+          fc.l3 = ct.l3; fc.l150 = ct.l150; fc.l300 = ct.l300;
         }
-        __syncwarp();
-        // this lane's staged lines (those that leave its G10 panel to the finest grid)
+        sC[warp][lane] = fc;
+      }
+      __syncwarp();
+#pragma unroll 1
+      for (int s = 0; s < kFinePerThread; ++s) {
+        // the staged lines owning this group's panel 4 s + gi
         uint32_t mine = 0;
-        for (uint32_t rem = any; rem; rem &= rem - 1) {
-          const int e = __ffs(rem) - 1;
-          mine |= ((sPm[warp][e] >> mypanel) & 1u) << e;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const uint32_t b = __ballot_sync(0xffffffffu, (pm >> (4 * s + k)) & 1u);
+          if (k == gi) mine = b;
         }
+        if (!__any_sync(0xffffffffu, mine != 0)) continue;
+        const int j = 32 * s + lane;
+        const float jf = (float)j;
         if (SURR && use_mlp) {
-          // the warp steps through the lanes' lists together, one staged line per lane and
-          // round; evaluations that pass the guard go to the warp's queue
+          // groups step together; evaluations that pass the guard go to the warp's queue
           while (__any_sync(0xffffffffu, mine != 0)) {
-            if (qn > kQCap - 32 * kFinePerThread) q_flush(warp_queue(dsm), qn, S, fine_apply);
+            if (qn > kQCap - 32) q_flush(warp_queue(dsm), qn, S, fine_apply);
             int e = -1;
             if (mine) {
               e = __ffs(mine) - 1;
               mine &= mine - 1;
             }
-            const int es = e < 0 ? 0 : e;
-            const float qf = sQ[warp][es], hs = sHs[warp][es], phs = sPhs[warp][es], phi = sPhi[warp][es];
-            const float amp = sAmp[warp][es], y = e < 0 ? 1.0f : sY[warp][es];
-            const int klo_e = e < 0 ? 1 : sKlo[warp][es], khi_e = e < 0 ? 0 : sKhi[warp][es];
-            const bool uc = e >= 0 && sChi[warp][es];
-            ChiThr ct;
-            if (uc) {
-              ct.r3 = sT[0][warp][es]; ct.r150 = sT[1][warp][es]; ct.r300 = sT[2][warp][es];
-              ct.l3 = sT[3][warp][es]; ct.l150 = sT[4][warp][es]; ct.l300 = sT[5][warp][es];
+            const FineLine fl = sL[warp][e < 0 ? 0 : e];
+            const bool act = e >= 0 && j >= fl.klo && j <= fl.khi;
+            const float y = act ? fl.y : 1.0f;
+            const float xv = fmaf(jf + fl.qf, fl.hs, fl.phs);
+            const bool use = act && mlp_guard(S, xv, y);
+            float cv = 1.0f;
+            if (act && sC[warp][e].on) {
+              const FineChi fc = sC[warp][e];
+              const ChiThr ct{fc.r3, fc.r150, fc.r300, fc.l3, fc.l150, fc.l300};
+              cv = ct.value(j, fabsf((jf + fl.qf) + fl.phi) * ldexpf(1.0f, -kFineBits));
             }
-#pragma unroll
-            for (int q = 0; q < kFinePerThread; ++q) {
-              const int j = kFinePerThread * lane + q;
-              const bool act = j >= klo_e && j <= khi_e;
-              const float jf = (float)j;
-              const float xv = fmaf(jf + qf, hs, phs);
-              const bool use = act && mlp_guard(S, xv, y);
-              const float cv = (act && uc) ? ct.value(j, fabsf((jf + qf) + phi) * ldexpf(1.0f, -kFineBits)) : 1.0f;
-              q_push(warp_queue(dsm), qn, use, xv, y, amp * cv, q);
-              if (act && !use) {
-                float v = amp * voigt_K<true>(xv, y, stab);
-                if (uc) v *= cv;
-                kahan_add(acc[q], cmp[q], v);
-              }
-              if (act) count_eval<COUNT>(true, xv, y, nev, nnear, nmid, nsmall);
-              if (COUNT && use) ++nmlp;
+            q_push(warp_queue(dsm), qn, use, xv, y, fl.amp * cv, j);
+            if (act && !use) {
+              float v = fl.amp * voigt_K<true>(xv, y, stab);
+              v *= cv;
+              kahan_add(sAcc[warp][j], sCmp[warp][j], v);
             }
+            if (act) count_eval<COUNT>(true, xv, y, nev, nnear, nmid, nsmall);
+            if (COUNT && use) ++nmlp;
           }
+        } else {
+          float a = sAcc[warp][j], cp = sCmp[warp][j];
+          while (mine) {  // uniform within a group
+            const int e = __ffs(mine) - 1;
+            mine &= mine - 1;
+            const FineLine fl = sL[warp][e];
+            if (j < fl.klo || j > fl.khi) continue;
+            const float xv = fmaf(jf + fl.qf, fl.hs, fl.phs);
+            float v = fl.amp * (voigt ? voigt_K<true>(xv, fl.y, stab) : shape_f(R.shape, xv, fl.y));
+            const FineChi fc = sC[warp][e];
+            if (fc.on) {
+              const ChiThr ct{fc.r3, fc.r150, fc.r300, fc.l3, fc.l150, fc.l300};
+              v *= ct.value(j, fabsf((jf + fl.qf) + fl.phi) * ldexpf(1.0f, -kFineBits));
+            }
+            kahan_add(a, cp, v);
+            count_eval<COUNT>(voigt, xv, fl.y, nev, nnear, nmid, nsmall);
+          }
+          sAcc[warp][j] = a;
+          sCmp[warp][j] = cp;
         }
-        while (!use_mlp && mine) {
-          const int e = __ffs(mine) - 1;
-          mine &= mine - 1;
-          const float qf = sQ[warp][e], hs = sHs[warp][e], phs = sPhs[warp][e], phi = sPhi[warp][e];
-          const float amp = sAmp[warp][e], y = sY[warp][e];
-          const int klo_e = sKlo[warp][e], khi_e = sKhi[warp][e];
-          const bool uc = sChi[warp][e];
-          ChiThr ct;
-          if (uc) {
-            ct.r3 = sT[0][warp][e]; ct.r150 = sT[1][warp][e]; ct.r300 = sT[2][warp][e];
-            ct.l3 = sT[3][warp][e]; ct.l150 = sT[4][warp][e]; ct.l300 = sT[5][warp][e];
-          }
-#pragma unroll
-          for (int q = 0; q < kFinePerThread; ++q) {
-            const int j = kFinePerThread * lane + q;
-            if (j < klo_e || j > khi_e) continue;
-            const float jf = (float)j;
-            const float xv = fmaf(jf + qf, hs, phs);
-            float v = amp * (voigt ? voigt_K<true>(xv, y, stab) : shape_f(R.shape, xv, y));
-            if (uc) v *= ct.value(j, fabsf((jf + qf) + phi) * ldexpf(1.0f, -kFineBits));
-            kahan_add(acc[q], cmp[q], v);
-            count_eval<COUNT>(voigt, xv, y, nev, nnear, nmid, nsmall);
-          }
-        }
-        __syncwarp();
       }
+      __syncwarp();
     }
   }
   if (SURR && use_mlp) q_flush(warp_queue(dsm), qn, S, fine_apply);  // warp-uniform
+  __syncwarp();
   uint32_t valid = 0;
 #pragma unroll
   for (int q = 0; q < kFinePerThread; ++q)
@@ -1434,7 +1434,8 @@ __global__ void __launch_bounds__(kFineThreads)
     const float* sl = R.slots + (int64_t)lev * R.slots_per_level;
     float out[kFinePerThread];
 #pragma unroll
-    for (int q = 0; q < kFinePerThread; ++q) out[q] = acc[q] + cmp[q];
+    for (int q = 0; q < kFinePerThread; ++q)
+      out[q] = sAcc[warp][kFinePerThread * lane + q] + sCmp[warp][kFinePerThread * lane + q];
 #pragma unroll
     for (int g = 1; g <= kNGrid; ++g) {
       const int sh = 13 - g;  // finest nodes per panel of grid g: 2^(13-g)
