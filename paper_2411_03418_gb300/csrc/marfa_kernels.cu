@@ -386,9 +386,6 @@ static void launch_dyn(void (*k)(KA...), int n_items, int threads, size_t bytes,
   k<<<n_items, threads, bytes, st>>>(args...);
 }
 
-// Shared-memory copy of the Voigt tables at the start of a kernel's dynamic shared memory.
-constexpr size_t kStabBytes = ((size_t)kVoigtTableFloats * 4 + 15) & ~(size_t)15;
-
 // Dynamic shared memory of the surrogate part: the network weights and one queue per warp.
 constexpr size_t surr_bytes(int threads) {
   return sizeof(MlpWeights) + (size_t)(threads / 32) * sizeof(SurrQueue);
@@ -1023,14 +1020,13 @@ void launch_coarse_lm(const ReqDev* reqs, const CoarseItem* items, int n_items, 
 // owns in the tile and evaluates the profile at the nodes of those panels, into a
 // per-warp shared buffer (row = line). Phase 2: each lane adds, for its own pair, the
 // buffered values of the lines owning its panels into compensated register sums.
+// At most 80 registers a thread in the plain variants (168 with the surrogate): with the
+// Voigt tables read through the read-only cache (no shared copy), six CTAs fit on an SM.
 template <bool COUNT, bool SURR>
-__global__ void __launch_bounds__(kCWarps * 32)
+__global__ void __launch_bounds__(kCWarps * 32, SURR ? 3 : 6)
     k_coarse(const ReqDev* __restrict__ reqs, const CoarseItem* __restrict__ items,
              int64_t* __restrict__ counts) {
-  // dynamic shared memory: the Voigt tables, then (SURR) the surrogate weights and queues
-  extern __shared__ __align__(16) unsigned char dsm0[];
-  float* stab = reinterpret_cast<float*>(dsm0);
-  unsigned char* dsm = dsm0 + kStabBytes;
+  extern __shared__ __align__(16) unsigned char dsm[];  // surrogate weights and queues (SURR only)
   MlpWeights& S = *reinterpret_cast<MlpWeights*>(dsm);
   __shared__ float bufE[kCWarps][32][kCPairs + 1];  // value at node 2p of staged line t
   __shared__ float bufO[kCWarps][32][kCPairs + 1];  // value at node 2p + 1
@@ -1046,7 +1042,6 @@ __global__ void __launch_bounds__(kCWarps * 32)
   const int64_t m0 = it.m0 + (int64_t)kCPairs * warp;  // this warp's first pair
   int64_t nev = 0, nmlp = 0, nnear = 0, nmid = 0, nsmall = 0;
   const bool use_mlp = SURR && R.mlp != nullptr;  // block-uniform
-  voigt_table_to_smem(stab);
   if (use_mlp) mlp_load_smem(S, R.mlp);
   __syncthreads();
   if (m0 <= m_last + 1) {  // warp-uniform
@@ -1140,7 +1135,7 @@ __global__ void __launch_bounds__(kCWarps * 32)
             if (ae) {
               float v = 0.0f;
               if (!ue) {
-                v = amp * voigt_K<true>(xv, y, stab);
+                v = amp * voigt_K(xv, y);
                 if (use_chi) v *= ce;
               }
               bE[lane][q] = v;
@@ -1148,7 +1143,7 @@ __global__ void __launch_bounds__(kCWarps * 32)
             if (ao) {
               float w = 0.0f;
               if (!uo) {
-                w = amp * voigt_K<true>(xw, y, stab);
+                w = amp * voigt_K(xw, y);
                 if (use_chi) w *= co;
               }
               bO[lane][q] = w;
@@ -1178,13 +1173,13 @@ __global__ void __launch_bounds__(kCWarps * 32)
             if (!(bR || bL)) continue;
             const float jf = (float)(2 * q);
             const float xv = nx.x(jf);
-            float v = amp * (voigt ? voigt_K<true>(xv, y, stab) : shape_f(R.shape, xv, y));
+            float v = amp * (voigt ? voigt_K(xv, y) : shape_f(R.shape, xv, y));
             if (use_chi) v *= run ? cr.v : ct.value(2 * q, nx.absd(jf, s - 1));
             bE[lane][q] = v;
             count_eval<COUNT>(voigt, xv, y, nev, nnear, nmid, nsmall);
             if (bL) {
               const float xw = nx.x(jf + 1.0f);
-              float w = amp * (voigt ? voigt_K<true>(xw, y, stab) : shape_f(R.shape, xw, y));
+              float w = amp * (voigt ? voigt_K(xw, y) : shape_f(R.shape, xw, y));
               if (use_chi) w *= run ? cr.v * cr.ratio : ct.value(2 * q + 1, nx.absd(jf + 1.0f, s - 1));
               bO[lane][q] = w;
               count_eval<COUNT>(voigt, xw, y, nev, nnear, nmid, nsmall);
@@ -1232,13 +1227,13 @@ void launch_coarse(const ReqDev* reqs, const CoarseItem* items, int n_items, int
   const int T = kCWarps * 32;
   if (surr) {
     if (counts)
-      launch_dyn(k_coarse<true, true>, n_items, T, kStabBytes + surr_bytes(T), st, reqs, items, counts);
+      launch_surr(k_coarse<true, true>, n_items, T, st, reqs, items, counts);
     else
-      launch_dyn(k_coarse<false, true>, n_items, T, kStabBytes + surr_bytes(T), st, reqs, items, counts);
+      launch_surr(k_coarse<false, true>, n_items, T, st, reqs, items, counts);
   } else if (counts) {
-    launch_dyn(k_coarse<true, false>, n_items, T, kStabBytes, st, reqs, items, counts);
+    k_coarse<true, false><<<n_items, T, 0, st>>>(reqs, items, counts);
   } else {
-    launch_dyn(k_coarse<false, false>, n_items, T, kStabBytes, st, reqs, items, counts);
+    k_coarse<false, false><<<n_items, T, 0, st>>>(reqs, items, counts);
   }
 }
 
