@@ -16,6 +16,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 
 #include "marfa_internal.cuh"
 #include "mlp.cuh"
@@ -164,6 +165,12 @@ __device__ __forceinline__ int make_zones(int64_t A, int64_t B, int64_t Rc, int6
   }
   return nz;
 }
+
+// Lowest and highest set bit of a non-zero panel mask.
+__device__ __forceinline__ int mask_lowest(uint32_t m) { return __ffs((int)m) - 1; }
+__device__ __forceinline__ int mask_lowest(uint64_t m) { return __ffsll((long long)m) - 1; }
+__device__ __forceinline__ int mask_highest(uint32_t m) { return 31 - __clz((int)m); }
+__device__ __forceinline__ int mask_highest(uint64_t m) { return 63 - __clzll((long long)m); }
 
 // Bits i = 0..nb-1 stand for panels base + i; set those in the closed interval [a, b].
 template <typename MT>
@@ -811,7 +818,9 @@ __global__ void __launch_bounds__(kLWarps * 32)
   const int64_t cut = R.cut_fx;
   const int64_t base = m0 - 1;  // mask bit b <-> panel m0 - 1 + b
   const int nb = PAIRS + 1;
-  const uint64_t win = rmask<uint64_t>(m_first, m_last, base, nb);
+  // panel masks of PAIRS + 1 bits: 32-bit words for 16 pairs
+  using MT = typename std::conditional<(PAIRS < 32), uint32_t, uint64_t>::type;
+  const MT win = rmask<MT>(m_first, m_last, base, nb);
   for (int p = 0; p < PAIRS; ++p) {
     accL[warp][p][lane] = 0.0f;
     accM[warp][p][lane] = 0.0f;
@@ -859,15 +868,15 @@ __global__ void __launch_bounds__(kLWarps * 32)
       if (SURR && use_mlp) {
         // all lanes step through the union of their pair ranges together; evaluations
         // that pass the guard go to the warp's queue
-        uint64_t own = 0;
+        MT own = 0;
         int64_t c = 0;
         bool chi = false;
         if (valid) {
           c = __ldg(R.c + lo_off + i);
           const int gst = __ldg(R.gstar + lo_off + i);
           chi = __ldg(R.flags + lo_off + i) & 1;
-          own = accept_mask<uint64_t>(g, c, gst, chi, cut, R.R_w, base, nb, false) & win;
-          if (own) own &= ~accept_mask<uint64_t>(g - 1, c, gst, chi, cut, R.R_w, base, nb, true);
+          own = accept_mask<MT>(g, c, gst, chi, cut, R.R_w, base, nb, false) & win;
+          if (own) own &= ~accept_mask<MT>(g - 1, c, gst, chi, cut, R.R_w, base, nb, true);
         }
         float amp = 0.0f, y = 1.0f;
         NodeX nx;
@@ -880,13 +889,13 @@ __global__ void __launch_bounds__(kLWarps * 32)
           y = __ldg(R.yv + lo_off + i);
           nx.init(X0 - c, s - 1, __ldg(R.sx + lo_off + i));
           if (use_chi) ct.init(c, X0, s - 1);
-          pa = max(__ffsll((long long)own) - 2, 0);
-          pb = min(63 - __clzll((long long)own), PAIRS - 1);
+          pa = max(mask_lowest(own) - 1, 0);
+          pb = min(mask_highest(own), PAIRS - 1);
         }
         const int qa = __reduce_min_sync(0xffffffffu, pa), qb = __reduce_max_sync(0xffffffffu, pb);
         for (int p = qa; p <= qb; ++p) {
           if (qn > kQCap - 64) q_flush(warp_queue(dsm), qn, S, lm_apply);
-          const bool bR = (own >> p) & 1ull, bL = (own >> (p + 1)) & 1ull;
+          const bool bR = (own >> p) & MT(1), bL = (own >> (p + 1)) & MT(1);
           const bool ae = bR || bL, ao = bL;
           const float jf = (float)(2 * p);
           const float xe = nx.x(jf), xo = nx.x(jf + 1.0f);
@@ -917,8 +926,8 @@ __global__ void __launch_bounds__(kLWarps * 32)
       const int gst = __ldg(R.gstar + lo_off + i);
       const bool chi = __ldg(R.flags + lo_off + i) & 1;
       if (owns_nothing(g, c, gst, chi, cut, xa_t, xb_t, P_t)) continue;
-      uint64_t own = accept_mask<uint64_t>(g, c, gst, chi, cut, R.R_w, base, nb, false) & win;
-      if (own) own &= ~accept_mask<uint64_t>(g - 1, c, gst, chi, cut, R.R_w, base, nb, true);
+      MT own = accept_mask<MT>(g, c, gst, chi, cut, R.R_w, base, nb, false) & win;
+      if (own) own &= ~accept_mask<MT>(g - 1, c, gst, chi, cut, R.R_w, base, nb, true);
       if (!own) continue;
       const float amp = __ldg(R.amp + lo_off + i);
       const float sx = __ldg(R.sx + lo_off + i);
@@ -929,15 +938,15 @@ __global__ void __launch_bounds__(kLWarps * 32)
       const bool use_chi = chi && physical;
       if (use_chi) ct.init(c, X0, s - 1);
       // pair p uses bits p (R slot of node 2p) and p + 1 (L of node 2p, M of node 2p+1)
-      const int pa = max(__ffsll((long long)own) - 2, 0);
-      const int pb = min(63 - __clzll((long long)own), PAIRS - 1);
+      const int pa = max(mask_lowest(own) - 1, 0);
+      const int pb = min(mask_highest(own), PAIRS - 1);
       // a chi branch common to all nodes 2pa .. 2pb + 1: one exponential per line
       const bool run = use_chi && ct.uniform(2 * pa, 2 * pb + 1);
       ChiRun cr;
       if (run) cr.init(ct, 2 * pa, nx.absd((float)(2 * pa), s - 1), s - 1);
       const float r2 = run ? cr.ratio * cr.ratio : 1.0f;
       for (int p = pa; p <= pb; ++p, cr.v *= r2) {
-        const bool bR = (own >> p) & 1ull, bL = (own >> (p + 1)) & 1ull;
+        const bool bR = (own >> p) & MT(1), bL = (own >> (p + 1)) & MT(1);
         if (!(bR || bL)) continue;
         const float jf = (float)(2 * p);
         const float xv = nx.x(jf);
