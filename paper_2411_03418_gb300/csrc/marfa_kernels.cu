@@ -1182,13 +1182,13 @@ __global__ void __launch_bounds__(kCWarps * 32, SURR ? 3 : 6)
             if (!(bR || bL)) continue;
             const float jf = (float)(2 * q);
             const float xv = nx.x(jf);
-            float v = amp * (voigt ? voigt_K(xv, y) : shape_f(R.shape, xv, y));
+            float v = amp * (voigt ? voigt_K<false, false, true>(xv, y, kVoigtCells) : shape_f(R.shape, xv, y));
             if (use_chi) v *= run ? cr.v : ct.value(2 * q, nx.absd(jf, s - 1));
             bE[lane][q] = v;
             count_eval<COUNT>(voigt, xv, y, nev, nnear, nmid, nsmall);
             if (bL) {
               const float xw = nx.x(jf + 1.0f);
-              float w = amp * (voigt ? voigt_K(xw, y) : shape_f(R.shape, xw, y));
+              float w = amp * (voigt ? voigt_K<false, false, true>(xw, y, kVoigtCells) : shape_f(R.shape, xw, y));
               if (use_chi) w *= run ? cr.v * cr.ratio : ct.value(2 * q + 1, nx.absd(jf + 1.0f, s - 1));
               bO[lane][q] = w;
               count_eval<COUNT>(voigt, xw, y, nev, nnear, nmid, nsmall);
@@ -1411,7 +1411,7 @@ __global__ void __launch_bounds__(kFineThreads)
             const FineLine fl = sL[warp][e];
             if (j < fl.klo || j > fl.khi) continue;
             const float xv = fmaf(jf + fl.qf, fl.hs, fl.phs);
-            float v = fl.amp * (voigt ? voigt_K<true>(xv, fl.y, stab) : shape_f(R.shape, xv, fl.y));
+            float v = fl.amp * (voigt ? voigt_K<true, false, true>(xv, fl.y, stab) : shape_f(R.shape, xv, fl.y));
             const FineChi fc = sC[warp][e];
             if (fc.on) {
               const ChiThr ct{fc.r3, fc.r150, fc.r300, fc.l3, fc.l150, fc.l300};

@@ -113,11 +113,11 @@ __device__ __forceinline__ float voigt_far(float x, float y) {
   return y * kInvSqrtPi * inv * (1.0f + t);
 }
 
-// Everything but the far wing, kept out of line so that unrolled callers stay small.
-// The Dawson-table branch covers the whole near wing of narrow lines (y < 1, |x| < 12)
-// so that one line's nodes on the fine grids take a single code path.
+// Everything but the far wing. The Dawson-table branch covers the whole near wing of
+// narrow lines (y < 1, |x| < 12) so that one line's nodes on the fine grids take a
+// single code path.
 template <bool SMEM>
-__device__ __noinline__ float voigt_K_near(float ax, float y, const float* tab) {
+__device__ __forceinline__ float voigt_near_body(float ax, float y, const float* tab) {
   if (y < 0.25f && ax < 12.0f) {
     const int ci = min((int)(ax * 4.0f), VOIGT_SMALL_NX - 1);
     const float u = (ax - (0.25f * ci + 0.125f)) * 8.0f;
@@ -144,17 +144,24 @@ __device__ __noinline__ float voigt_K_near(float ax, float y, const float* tab) 
   return voigt_cell<SMEM>(tab, VOIGT_NPSI + ix * 2 + iy, u, v);
 }
 
+// The same out of line, so that callers with several evaluation sites stay small.
+template <bool SMEM>
+__device__ __noinline__ float voigt_K_near(float ax, float y, const float* tab) {
+  return voigt_near_body<SMEM>(ax, y, tab);
+}
+
 // MID3: evaluate 22.5 <= |z| < 100 inline with three terms of the series (the first
 // omitted term is below 7 (15/8) / |z|^6 < 1e-7 relative, also for Re w near the real
 // axis) instead of the six terms of voigt_K_near; it pays where most evaluations lie in
-// the mid wing (grids 2..8) and costs registers and branches elsewhere.
-template <bool SMEM, bool MID3 = false>
+// the mid wing (grids 2..8) and costs registers and branches elsewhere. INL: the near
+// wing inline (one evaluation site in the caller's loop) instead of a call.
+template <bool SMEM, bool MID3 = false, bool INL = false>
 __device__ __forceinline__ float voigt_K(float x, float y, const float* tab) {
   float ax = fabsf(x);
   float r2 = fmaf(ax, ax, y * y);
   if (r2 >= 1.0e4f) return voigt_far(ax, y);
   if (MID3 && r2 >= 506.25f) return voigt_asym<2>(ax, y);
-  return voigt_K_near<SMEM>(ax, y, tab);
+  return INL ? voigt_near_body<SMEM>(ax, y, tab) : voigt_K_near<SMEM>(ax, y, tab);
 }
 
 __device__ __forceinline__ float voigt_K(float x, float y) { return voigt_K<false>(x, y, kVoigtCells); }
