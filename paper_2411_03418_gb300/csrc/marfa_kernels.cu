@@ -1358,6 +1358,8 @@ __global__ void __launch_bounds__(kFineThreads)
           ct.init(c, Xa, kFineShift);
           fc.r3 = ct.r3; fc.r150 = ct.r150; fc.r300 = ct.r300;
           fc.l3 = ct.l3; fc.l150 = ct.l150; fc.l300 = ct.l300;
+          // within 3 cm^-1 of the centre at all its nodes of the warp: chi = 1 exactly
+          if (ct.uniform(klo, khi) && ct.branch(klo) == 0) fc.on = 0;
         }
         sC[warp][lane] = fc;
       }
@@ -1412,8 +1414,8 @@ __global__ void __launch_bounds__(kFineThreads)
             if (j < fl.klo || j > fl.khi) continue;
             const float xv = fmaf(jf + fl.qf, fl.hs, fl.phs);
             float v = fl.amp * (voigt ? voigt_K<true, false, true>(xv, fl.y, stab) : shape_f(R.shape, xv, fl.y));
-            const FineChi fc = sC[warp][e];
-            if (fc.on) {
+            if (sC[warp][e].on) {
+              const FineChi fc = sC[warp][e];
               const ChiThr ct{fc.r3, fc.r150, fc.r300, fc.l3, fc.l150, fc.l300};
               v *= ct.value(j, fabsf((jf + fl.qf) + fl.phi) * ldexpf(1.0f, -kFineBits));
             }
