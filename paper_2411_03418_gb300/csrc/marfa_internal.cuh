@@ -127,7 +127,7 @@ struct G1Item {
 };
 
 constexpr int kG1Pairs = 32;         // node pairs per G1 tile (one per lane)
-constexpr int kG1Split = 4;          // CTAs sharing one G1 tile's candidate lines; each
+constexpr int kG1Split = 6;          // CTAs sharing one G1 tile's candidate lines; each
                                      // writes its own copy of the tile's slots
 constexpr int kG1Warps = 8;          // warps of a G1 CTA, each takes every 8th staged line
 constexpr int kG1Batch = 512;        // lines staged in shared memory at a time

@@ -286,24 +286,29 @@ struct ChiThr {
 };
 
 // chi-factor along the nodes ja, ja + 1, ... of one line when its branch is the same at
-// all of them (ChiThr::uniform): chi(ja) once, then a constant ratio per node step
-// (e^{-r h} on the side right of the centre, e^{+r h} on the left), so each node costs
-// one multiplication; at most 64 steps, about 4e-6 relative drift.
+// all of them (ChiThr::uniform): chi(ja) once, and a constant ratio per node step
+// (e^{-r h} on the side right of the centre, e^{+r h} on the left), so that node ja + k
+// costs one exp2 (at(k)); lr = log2 of the ratio, 0 where chi = 1.
 struct ChiRun {
-  float v = 1.0f, ratio = 1.0f;  // chi at the current node, ratio per node step
+  float v = 1.0f, ratio = 1.0f, lr = 0.0f;  // chi at node ja, ratio per node step
   __device__ __forceinline__ void init(const ChiThr& ct, int ja, float absd_a, int sh) {
     const int b = ct.branch(ja);
     if (b == 0) {
       v = 1.0f;
       ratio = 1.0f;
+      lr = 0.0f;
       return;
     }
     const float C = b == 1 ? 1.084f : (b == 2 ? 0.208f : 0.025f);
     const float r = b == 1 ? 0.027f : (b == 2 ? 0.016f : 0.009f);
     v = C * __expf(-r * absd_a);
     const float h = ldexpf(1.0f, sh - kFixBits);  // node step, cm^-1
-    ratio = __expf((ja >= ct.r3 ? -r : r) * h);
+    const float rh = (ja >= ct.r3 ? -r : r) * h;
+    ratio = __expf(rh);
+    lr = rh * 1.4426950408889634f;
   }
+  // chi at node ja + k
+  __device__ __forceinline__ float at(int k) const { return lr != 0.0f ? v * exp2f(lr * (float)k) : v; }
 };
 
 // Position of the nodes of a line relative to its centre: with rel = X0 - c (fixed
@@ -944,21 +949,23 @@ __global__ void __launch_bounds__(kLWarps * 32)
       const bool run = use_chi && ct.uniform(2 * pa, 2 * pb + 1);
       ChiRun cr;
       if (run) cr.init(ct, 2 * pa, nx.absd((float)(2 * pa), s - 1), s - 1);
-      const float r2 = run ? cr.ratio * cr.ratio : 1.0f;
-      for (int p = pa; p <= pb; ++p, cr.v *= r2) {
+      // the touched pairs only (not the gap inside a line's ring)
+      const uint32_t touched = (uint32_t)(own | (own >> 1)) & (PAIRS == 32 ? 0xffffffffu : 0xffffu);
+      for (uint32_t tm = touched; tm; tm &= tm - 1) {
+        const int p = __ffs((int)tm) - 1;
         const bool bR = (own >> p) & MT(1), bL = (own >> (p + 1)) & MT(1);
-        if (!(bR || bL)) continue;
+        const float cv = run ? cr.at(2 * (p - pa)) : 1.0f;
         const float jf = (float)(2 * p);
         const float xv = nx.x(jf);
         float v = amp * (voigt ? voigt_K<false, true>(xv, y, kVoigtCells) : shape_f(R.shape, xv, y));
-        if (use_chi) v *= run ? cr.v : ct.value(2 * p, nx.absd(jf, s - 1));
+        if (use_chi) v *= run ? cv : ct.value(2 * p, nx.absd(jf, s - 1));
         if (bL) accL[warp][p][lane] += v;
         if (bR) accR[warp][p][lane] += v;
         count_eval<COUNT>(voigt, xv, y, nev, nnear, nmid, nsmall);
         if (bL) {
           const float xw = nx.x(jf + 1.0f);
           float w = amp * (voigt ? voigt_K<false, true>(xw, y, kVoigtCells) : shape_f(R.shape, xw, y));
-          if (use_chi) w *= run ? cr.v * cr.ratio : ct.value(2 * p + 1, nx.absd(jf + 1.0f, s - 1));
+          if (use_chi) w *= run ? cv * cr.ratio : ct.value(2 * p + 1, nx.absd(jf + 1.0f, s - 1));
           accM[warp][p][lane] += w;
           count_eval<COUNT>(voigt, xw, y, nev, nnear, nmid, nsmall);
         }
@@ -1176,20 +1183,21 @@ __global__ void __launch_bounds__(kCWarps * 32, SURR ? 3 : 6)
           const bool run = use_chi && ct.uniform(2 * pa, 2 * pb + 1);
           ChiRun cr;
           if (run) cr.init(ct, 2 * pa, nx.absd((float)(2 * pa), s - 1), s - 1);
-          const float r2 = run ? cr.ratio * cr.ratio : 1.0f;
-          for (int q = pa; q <= pb; ++q, cr.v *= r2) {
-            const bool bR = (own >> q) & 1ull, bL = (own >> (q + 1)) & 1ull;
-            if (!(bR || bL)) continue;
+          // the touched pairs only (not the gap inside a line's ring)
+          for (uint32_t tm = (uint32_t)(own | (own >> 1)); tm; tm &= tm - 1) {
+            const int q = __ffs((int)tm) - 1;
+            const bool bL = (own >> (q + 1)) & 1ull;
+            const float cv = run ? cr.at(2 * (q - pa)) : 1.0f;
             const float jf = (float)(2 * q);
             const float xv = nx.x(jf);
             float v = amp * (voigt ? voigt_K<false, false, true>(xv, y, kVoigtCells) : shape_f(R.shape, xv, y));
-            if (use_chi) v *= run ? cr.v : ct.value(2 * q, nx.absd(jf, s - 1));
+            if (use_chi) v *= run ? cv : ct.value(2 * q, nx.absd(jf, s - 1));
             bE[lane][q] = v;
             count_eval<COUNT>(voigt, xv, y, nev, nnear, nmid, nsmall);
             if (bL) {
               const float xw = nx.x(jf + 1.0f);
               float w = amp * (voigt ? voigt_K<false, false, true>(xw, y, kVoigtCells) : shape_f(R.shape, xw, y));
-              if (use_chi) w *= run ? cr.v * cr.ratio : ct.value(2 * q + 1, nx.absd(jf + 1.0f, s - 1));
+              if (use_chi) w *= run ? cv * cr.ratio : ct.value(2 * q + 1, nx.absd(jf + 1.0f, s - 1));
               bO[lane][q] = w;
               count_eval<COUNT>(voigt, xw, y, nev, nnear, nmid, nsmall);
             }
