@@ -949,25 +949,47 @@ __global__ void __launch_bounds__(kLWarps * 32)
       const bool run = use_chi && ct.uniform(2 * pa, 2 * pb + 1);
       ChiRun cr;
       if (run) cr.init(ct, 2 * pa, nx.absd((float)(2 * pa), s - 1), s - 1);
-      // the touched pairs only (not the gap inside a line's ring)
-      const uint32_t touched = (uint32_t)(own | (own >> 1)) & (PAIRS == 32 ? 0xffffffffu : 0xffffu);
-      for (uint32_t tm = touched; tm; tm &= tm - 1) {
-        const int p = __ffs((int)tm) - 1;
-        const bool bR = (own >> p) & MT(1), bL = (own >> (p + 1)) & MT(1);
-        const float cv = run ? cr.at(2 * (p - pa)) : 1.0f;
-        const float jf = (float)(2 * p);
-        const float xv = nx.x(jf);
-        float v = amp * (voigt ? voigt_K<false, true>(xv, y, kVoigtCells) : shape_f(R.shape, xv, y));
-        if (use_chi) v *= run ? cv : ct.value(2 * p, nx.absd(jf, s - 1));
-        if (bL) accL[warp][p][lane] += v;
-        if (bR) accR[warp][p][lane] += v;
-        count_eval<COUNT>(voigt, xv, y, nev, nnear, nmid, nsmall);
-        if (bL) {
-          const float xw = nx.x(jf + 1.0f);
-          float w = amp * (voigt ? voigt_K<false, true>(xw, y, kVoigtCells) : shape_f(R.shape, xw, y));
-          if (use_chi) w *= run ? cv * cr.ratio : ct.value(2 * p + 1, nx.absd(jf + 1.0f, s - 1));
-          accM[warp][p][lane] += w;
-          count_eval<COUNT>(voigt, xw, y, nev, nnear, nmid, nsmall);
+      if (PAIRS == 16) {
+        // 16 pairs: every pair of pa..pb, chi by a running product (cheaper than exp2 here)
+        const float r2 = run ? cr.ratio * cr.ratio : 1.0f;
+        for (int p = pa; p <= pb; ++p, cr.v *= r2) {
+          const bool bR = (own >> p) & MT(1), bL = (own >> (p + 1)) & MT(1);
+          if (!(bR || bL)) continue;
+          const float jf = (float)(2 * p);
+          const float xv = nx.x(jf);
+          float v = amp * (voigt ? voigt_K<false, true>(xv, y, kVoigtCells) : shape_f(R.shape, xv, y));
+          if (use_chi) v *= run ? cr.v : ct.value(2 * p, nx.absd(jf, s - 1));
+          if (bL) accL[warp][p][lane] += v;
+          if (bR) accR[warp][p][lane] += v;
+          count_eval<COUNT>(voigt, xv, y, nev, nnear, nmid, nsmall);
+          if (bL) {
+            const float xw = nx.x(jf + 1.0f);
+            float w = amp * (voigt ? voigt_K<false, true>(xw, y, kVoigtCells) : shape_f(R.shape, xw, y));
+            if (use_chi) w *= run ? cr.v * cr.ratio : ct.value(2 * p + 1, nx.absd(jf + 1.0f, s - 1));
+            accM[warp][p][lane] += w;
+            count_eval<COUNT>(voigt, xw, y, nev, nnear, nmid, nsmall);
+          }
+        }
+      } else {
+        // 32 pairs: the touched pairs only (not the gap inside a line's ring)
+        for (uint32_t tm = (uint32_t)(own | (own >> 1)); tm; tm &= tm - 1) {
+          const int p = __ffs((int)tm) - 1;
+          const bool bR = (own >> p) & MT(1), bL = (own >> (p + 1)) & MT(1);
+          const float cv = run ? cr.at(2 * (p - pa)) : 1.0f;
+          const float jf = (float)(2 * p);
+          const float xv = nx.x(jf);
+          float v = amp * (voigt ? voigt_K<false, true>(xv, y, kVoigtCells) : shape_f(R.shape, xv, y));
+          if (use_chi) v *= run ? cv : ct.value(2 * p, nx.absd(jf, s - 1));
+          if (bL) accL[warp][p][lane] += v;
+          if (bR) accR[warp][p][lane] += v;
+          count_eval<COUNT>(voigt, xv, y, nev, nnear, nmid, nsmall);
+          if (bL) {
+            const float xw = nx.x(jf + 1.0f);
+            float w = amp * (voigt ? voigt_K<false, true>(xw, y, kVoigtCells) : shape_f(R.shape, xw, y));
+            if (use_chi) w *= run ? cv * cr.ratio : ct.value(2 * p + 1, nx.absd(jf + 1.0f, s - 1));
+            accM[warp][p][lane] += w;
+            count_eval<COUNT>(voigt, xw, y, nev, nnear, nmid, nsmall);
+          }
         }
       }
     }
