@@ -19,14 +19,13 @@
 #include <type_traits>
 
 #include "marfa_internal.cuh"
+#include "ownership.cuh"
 #include "mlp.cuh"
 #include "voigt.cuh"
 
 namespace marfa {
 
 // ------------------------------------------------------------------ helpers
-__device__ __constant__ int64_t kChiBreakFx[3] = {3LL << kFixBits, 150LL << kFixBits,
-                                                  300LL << kFixBits};
 
 __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
   float y = v - c;
@@ -157,7 +156,7 @@ __device__ __forceinline__ int make_zones(int64_t A, int64_t B, int64_t Rc, int6
   zlo[nz] = A + cut - P; zhi[nz] = B + cut + P; ++nz;
   if (chi) {
     for (int b = 0; b < 3; ++b) {
-      const int64_t Bk = kChiBreakFx[b];
+      const int64_t Bk = chi_break_fx(b);
       if (Bk > cut + (B - A) + P) break;
       zlo[nz] = A - Bk - P; zhi[nz] = B - Bk + P; ++nz;
       zlo[nz] = A + Bk - P; zhi[nz] = B + Bk + P; ++nz;
@@ -171,76 +170,6 @@ __device__ __forceinline__ int mask_lowest(uint32_t m) { return __ffs((int)m) - 
 __device__ __forceinline__ int mask_lowest(uint64_t m) { return __ffsll((long long)m) - 1; }
 __device__ __forceinline__ int mask_highest(uint32_t m) { return 31 - __clz((int)m); }
 __device__ __forceinline__ int mask_highest(uint64_t m) { return 63 - __clzll((long long)m); }
-
-// Bits i = 0..nb-1 stand for panels base + i; set those in the closed interval [a, b].
-template <typename MT>
-__device__ __forceinline__ MT rmask(int64_t a, int64_t b, int64_t base, int nb) {
-  int64_t lo = a - base;
-  int64_t hi = b - base;
-  if (lo < 0) lo = 0;
-  if (hi > nb - 1) hi = nb - 1;
-  if (lo > hi) return MT(0);
-  return ((MT(2) << (int)hi) - MT(1)) & (~MT(0) << (int)lo);
-}
-
-// Panels of grid g accepted for a line, over panels [base, base + nb). With child set,
-// the accepted panels of grid g are mapped to their two children on grid g + 1 and
-// base/nb refer to grid g + 1.
-template <typename MT>
-__device__ __forceinline__ MT accept_mask(int g, int64_t c, int gst, bool chi, int64_t cut,
-                                          int R_w, int64_t base, int nb, bool child) {
-  const int s = panel_shift(g);
-  const int64_t k = child ? 1 : 0, f = child ? 2 : 1;  // panel a of grid g -> children [2a, 2a+1]
-  int64_t s_lo = cl_sh(c - cut, s), s_hi = fl_sh(c + cut, s) - 1;
-  MT m = rmask<MT>(s_lo * f, s_hi * f + k, base, nb);
-  if (!m) return MT(0);
-  // the span covered by the mask bits, in fixed point
-  const int sb = child ? s - 1 : s;
-  const int64_t xa = base << sb, xb = (base + nb) << sb;
-  const int64_t P = int64_t(1) << s;  // panel width of grid g: a gap or kink panel lies
-                                      // within one panel width of c +- R or c +- B
-  if (gst > g) {
-    const int64_t R = (int64_t)R_w * step_fx(g);
-    if (c + R + P >= xa && c - R - P <= xb) {
-      int64_t gl = fl_sh(c - R, s), gh = cl_sh(c + R, s) - 1;
-      m &= ~rmask<MT>(gl * f, gh * f + k, base, nb);
-    }
-  }
-  if (chi) {
-    // a panel holding a breakpoint beyond the cut-off already fails the support test
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const int64_t B = kChiBreakFx[b];
-      if (B > cut) break;
-      const int64_t s1 = c - B, s2 = c + B;
-      if (s1 >= xa - P && s1 <= xb + P)
-        m &= ~rmask<MT>((cl_sh(s1, s) - 1) * f, fl_sh(s1, s) * f + k, base, nb);
-      if (s2 >= xa - P && s2 <= xb + P)
-        m &= ~rmask<MT>((cl_sh(s2, s) - 1) * f, fl_sh(s2, s) * f + k, base, nb);
-    }
-  }
-  return m;
-}
-
-// Quick rejection for grids 2..10: with its core on a coarser grid (gst < g) a line
-// owns panels of grid g only where the parent panel holds its cut-off edge or a chi
-// breakpoint, i.e. within one panel width P of the child; if no edge or breakpoint lies
-// within P of the span [xa, xb] of the tile's panels, the line owns nothing there.
-__device__ __forceinline__ bool owns_nothing(int g, int64_t c, int gst, bool chi, int64_t cut,
-                                             int64_t xa, int64_t xb, int64_t P) {
-  if (gst >= g) return false;
-  const int64_t lo = xa - P, hi = xb + P;
-  if ((c - cut >= lo && c - cut <= hi) || (c + cut >= lo && c + cut <= hi)) return false;
-  if (chi) {
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const int64_t B = kChiBreakFx[b];
-      if (B > cut) break;
-      if ((c - B >= lo && c - B <= hi) || (c + B >= lo && c + B <= hi)) return false;
-    }
-  }
-  return true;
-}
 
 // Panels of grid g (1..10) owned by a line over [base, base + nb).
 __device__ __forceinline__ uint32_t owned_mask(int g, int64_t c, int gst, bool chi, int64_t cut,
@@ -258,12 +187,12 @@ __device__ __forceinline__ int clamp32(int64_t v) {
 struct ChiThr {
   int r3, r150, r300, l3, l150, l300;
   __device__ __forceinline__ void init(int64_t c, int64_t X0, int sh) {
-    r3 = clamp32(cl_sh(c + kChiBreakFx[0] - X0, sh));
-    r150 = clamp32(fl_sh(c + kChiBreakFx[1] - X0, sh));
-    r300 = clamp32(fl_sh(c + kChiBreakFx[2] - X0, sh));
-    l3 = clamp32(fl_sh(c - kChiBreakFx[0] - X0, sh));
-    l150 = clamp32(cl_sh(c - kChiBreakFx[1] - X0, sh));
-    l300 = clamp32(cl_sh(c - kChiBreakFx[2] - X0, sh));
+    r3 = clamp32(cl_sh(c + chi_break_fx(0) - X0, sh));
+    r150 = clamp32(fl_sh(c + chi_break_fx(1) - X0, sh));
+    r300 = clamp32(fl_sh(c + chi_break_fx(2) - X0, sh));
+    l3 = clamp32(fl_sh(c - chi_break_fx(0) - X0, sh));
+    l150 = clamp32(cl_sh(c - chi_break_fx(1) - X0, sh));
+    l300 = clamp32(cl_sh(c - chi_break_fx(2) - X0, sh));
   }
   __device__ __forceinline__ int branch(int j) const {
     return (j >= r3) + (j > r150) + (j > r300) + (j <= l3) + (j < l150) + (j < l300);
@@ -649,11 +578,11 @@ __global__ void __launch_bounds__(kG1Warps * 32)
       const float aC = amp * y * kInvSqrtPi;
       float aL = aC, aR = aC;
       if (chi && physical) {
-        jR = clamp32(cl_sh(c + kChiBreakFx[0] - X0, s - 1));
-        jL = clamp32(fl_sh(c - kChiBreakFx[0] - X0, s - 1));
-        if (cut > kChiBreakFx[1]) {  // owned nodes may lie beyond 150 cm^-1 (branches 2, 3)
-          const int jR150 = clamp32(fl_sh(c + kChiBreakFx[1] - X0, s - 1));
-          const int jL150 = clamp32(cl_sh(c - kChiBreakFx[1] - X0, s - 1));
+        jR = clamp32(cl_sh(c + chi_break_fx(0) - X0, s - 1));
+        jL = clamp32(fl_sh(c - chi_break_fx(0) - X0, s - 1));
+        if (cut > chi_break_fx(1)) {  // owned nodes may lie beyond 150 cm^-1 (branches 2, 3)
+          const int jR150 = clamp32(fl_sh(c + chi_break_fx(1) - X0, s - 1));
+          const int jL150 = clamp32(cl_sh(c - chi_break_fx(1) - X0, s - 1));
           if (jR150 < 2 * kG1Pairs - 1 || jL150 > 0) exact = true;
         }
         const float d0 = (nx.qf + nx.phi);  // offset of node 0 from the centre, cm^-1
@@ -801,8 +730,10 @@ void launch_g1(const ReqDev* reqs, const G1Item* items, int n_items, int64_t* co
 // the tile, evaluates the profile at the nodes of those panels only, and adds the
 // values into lane-private shared-memory slots (acc[pair][lane]); the slots are summed
 // over lanes and warps in a fixed order at the end.
+// Register budgets: 72 for the plain 16-pair variant (seven CTAs per SM), 128 for the
+// plain 32-pair one (four, as its 48 KB of slots allow), 168 with the surrogate.
 template <bool COUNT, bool SURR, int PAIRS>
-__global__ void __launch_bounds__(kLWarps * 32)
+__global__ void __launch_bounds__(kLWarps * 32, SURR ? 3 : (PAIRS == 16 ? 7 : 4))
     k_coarse_lm(const ReqDev* __restrict__ reqs, const CoarseItem* __restrict__ items,
              int64_t* __restrict__ counts) {
   extern __shared__ __align__(16) unsigned char dsm[];  // surrogate weights (SURR only)
@@ -826,6 +757,8 @@ __global__ void __launch_bounds__(kLWarps * 32)
   // panel masks of PAIRS + 1 bits: 32-bit words for 16 pairs
   using MT = typename std::conditional<(PAIRS < 32), uint32_t, uint64_t>::type;
   const MT win = rmask<MT>(m_first, m_last, base, nb);
+  PanelFrame fr;  // 32-bit ownership where the offsets are whole panels
+  fr.init(g, base, nb, cut, R.R_w);
   for (int p = 0; p < PAIRS; ++p) {
     accL[warp][p][lane] = 0.0f;
     accM[warp][p][lane] = 0.0f;
@@ -930,9 +863,17 @@ __global__ void __launch_bounds__(kLWarps * 32)
       const int64_t c = __ldg(R.c + lo_off + i);
       const int gst = __ldg(R.gstar + lo_off + i);
       const bool chi = __ldg(R.flags + lo_off + i) & 1;
-      if (owns_nothing(g, c, gst, chi, cut, xa_t, xb_t, P_t)) continue;
-      MT own = accept_mask<MT>(g, c, gst, chi, cut, R.R_w, base, nb, false) & win;
-      if (own) own &= ~accept_mask<MT>(g - 1, c, gst, chi, cut, R.R_w, base, nb, true);
+      MT own;
+      if (fr.ok) {
+        const PanelPos pp = fr.pos(c);
+        if (owns_nothing_frame(fr, pp, g, gst, chi)) continue;
+        own = accept_frame<MT>(fr, pp, g, gst, chi) & win;
+        if (own) own &= ~accept_parent_frame<MT>(fr, pp, g, gst, chi);
+      } else {
+        if (owns_nothing(g, c, gst, chi, cut, xa_t, xb_t, P_t)) continue;
+        own = accept_mask<MT>(g, c, gst, chi, cut, R.R_w, base, nb, false) & win;
+        if (own) own &= ~accept_mask<MT>(g - 1, c, gst, chi, cut, R.R_w, base, nb, true);
+      }
       if (!own) continue;
       const float amp = __ldg(R.amp + lo_off + i);
       const float sx = __ldg(R.sx + lo_off + i);
@@ -1088,6 +1029,8 @@ __global__ void __launch_bounds__(kCWarps * 32, SURR ? 3 : 6)
     const int64_t base = m0 - 1;  // mask bit b <-> panel m0 - 1 + b
     const int nb = kCPairs + 1;
     const uint64_t win = rmask<uint64_t>(m_first, m_last, base, nb);
+    PanelFrame fr;  // 32-bit ownership where the offsets are whole panels
+    fr.init(g, base, nb, cut, R.R_w);
     const LevelDev L = R.lev[lev];
     Bands bd;
     {
@@ -1132,7 +1075,13 @@ __global__ void __launch_bounds__(kCWarps * 32, SURR ? 3 : 6)
           c = __ldg(R.c + lo_off + i);
           const int gst = __ldg(R.gstar + lo_off + i);
           chi = __ldg(R.flags + lo_off + i) & 1;
-          if (!owns_nothing(g, c, gst, chi, cut, xa_t, xb_t, P_t)) {
+          if (fr.ok) {
+            const PanelPos pp = fr.pos(c);
+            if (!owns_nothing_frame(fr, pp, g, gst, chi)) {
+              own = accept_frame<uint64_t>(fr, pp, g, gst, chi) & win;
+              if (own) own &= ~accept_parent_frame<uint64_t>(fr, pp, g, gst, chi);
+            }
+          } else if (!owns_nothing(g, c, gst, chi, cut, xa_t, xb_t, P_t)) {
             own = accept_mask<uint64_t>(g, c, gst, chi, cut, R.R_w, base, nb, false) & win;
             if (own) own &= ~accept_mask<uint64_t>(g - 1, c, gst, chi, cut, R.R_w, base, nb, true);
           }

@@ -1,0 +1,220 @@
+// Exact panel ownership of a line on the coarse grids (rule R2 of Sec. 2.4 as read in
+// the oracle): which panels of grid g a line's profile is accumulated on, from its
+// fixed-point centre c, its core grid g*, the cut-off and the chi-factor breakpoints.
+// Host and device code, so that tests can compare the two forms on the CPU.
+//
+// Two forms give identical masks:
+//  * accept_mask / owns_nothing work on 64-bit fixed-point positions;
+//  * the PanelFrame forms work on 32-bit panel indices relative to the tile. They hold
+//    when the cut-off, R_w h_g, R_w h_(g-1) and the breakpoints within the cut-off are
+//    whole panels of grids g and g - 1 (PanelFrame::ok; true for whole-cm^-1 cut-offs,
+//    even R_w and g >= 3): then floor((c + o) / P) = floor(c / P) + o / P and
+//    ceil((c + o) / P) = floor(c / P) + o / P + [c not a multiple of P].
+#pragma once
+#include <cstdint>
+#include "marfa_internal.cuh"
+
+#define MARFA_HD __host__ __device__ __forceinline__
+
+namespace marfa {
+
+// chi-factor breakpoints of Eq. (10): 3, 150 and 300 cm^-1, fixed point
+MARFA_HD constexpr int64_t chi_break_fx(int b) {
+  return b == 0 ? (int64_t(3) << kFixBits) : (b == 1 ? (int64_t(150) << kFixBits) : (int64_t(300) << kFixBits));
+}
+
+// Bits i = 0..nb-1 stand for panels base + i; set those in the closed interval [a, b].
+template <typename MT>
+MARFA_HD MT rmask(int64_t a, int64_t b, int64_t base, int nb) {
+  int64_t lo = a - base;
+  int64_t hi = b - base;
+  if (lo < 0) lo = 0;
+  if (hi > nb - 1) hi = nb - 1;
+  if (lo > hi) return MT(0);
+  return ((MT(2) << (int)hi) - MT(1)) & (~MT(0) << (int)lo);
+}
+
+// The same with a and b already relative to base.
+template <typename MT>
+MARFA_HD MT rmask_rel(int lo, int hi, int nb) {
+  if (lo < 0) lo = 0;
+  if (hi > nb - 1) hi = nb - 1;
+  if (lo > hi) return MT(0);
+  return ((MT(2) << hi) - MT(1)) & (~MT(0) << lo);
+}
+
+// Panels of grid g accepted for a line, over panels [base, base + nb). With child set,
+// the accepted panels of grid g are mapped to their two children on grid g + 1 and
+// base/nb refer to grid g + 1.
+template <typename MT>
+MARFA_HD MT accept_mask(int g, int64_t c, int gst, bool chi, int64_t cut, int R_w, int64_t base, int nb,
+                        bool child) {
+  const int s = panel_shift(g);
+  const int64_t k = child ? 1 : 0, f = child ? 2 : 1;  // panel a of grid g -> children [2a, 2a+1]
+  int64_t s_lo = cl_sh(c - cut, s), s_hi = fl_sh(c + cut, s) - 1;
+  MT m = rmask<MT>(s_lo * f, s_hi * f + k, base, nb);
+  if (!m) return MT(0);
+  // the span covered by the mask bits, in fixed point
+  const int sb = child ? s - 1 : s;
+  const int64_t xa = base << sb, xb = (base + nb) << sb;
+  const int64_t P = int64_t(1) << s;  // panel width of grid g: a gap or kink panel lies
+                                      // within one panel width of c +- R or c +- B
+  if (gst > g) {
+    const int64_t R = (int64_t)R_w * step_fx(g);
+    if (c + R + P >= xa && c - R - P <= xb) {
+      int64_t gl = fl_sh(c - R, s), gh = cl_sh(c + R, s) - 1;
+      m &= ~rmask<MT>(gl * f, gh * f + k, base, nb);
+    }
+  }
+  if (chi) {
+    // a panel holding a breakpoint beyond the cut-off already fails the support test
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const int64_t B = chi_break_fx(b);
+      if (B > cut) break;
+      const int64_t s1 = c - B, s2 = c + B;
+      if (s1 >= xa - P && s1 <= xb + P)
+        m &= ~rmask<MT>((cl_sh(s1, s) - 1) * f, fl_sh(s1, s) * f + k, base, nb);
+      if (s2 >= xa - P && s2 <= xb + P)
+        m &= ~rmask<MT>((cl_sh(s2, s) - 1) * f, fl_sh(s2, s) * f + k, base, nb);
+    }
+  }
+  return m;
+}
+
+// Quick rejection for grids 2..10: with its core on a coarser grid (gst < g) a line
+// owns panels of grid g only where the parent panel holds its cut-off edge or a chi
+// breakpoint, i.e. within one panel width P of the child; if no edge or breakpoint lies
+// within P of the span [xa, xb] of the tile's panels, the line owns nothing there.
+MARFA_HD bool owns_nothing(int g, int64_t c, int gst, bool chi, int64_t cut, int64_t xa, int64_t xb,
+                           int64_t P) {
+  if (gst >= g) return false;
+  const int64_t lo = xa - P, hi = xb + P;
+  if ((c - cut >= lo && c - cut <= hi) || (c + cut >= lo && c + cut <= hi)) return false;
+  if (chi) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const int64_t B = chi_break_fx(b);
+      if (B > cut) break;
+      if ((c - B >= lo && c - B <= hi) || (c + B >= lo && c + B <= hi)) return false;
+    }
+  }
+  return true;
+}
+
+// ------------------------------------------------------------------ 32-bit panel frame
+// A line centre against a tile's panel frame: q0 = floor(c / P) - base and r0 = [P does
+// not divide c] for the panels P of grid g; q1, r1 the same for the parent grid's
+// panels 2P, relative to floor(base / 2).
+struct PanelPos {
+  int q0, r0, q1, r1;
+};
+
+// The tile's panels base .. base + nb - 1 of grid g (2..10) and the offsets in whole
+// panels; ok = false when an offset is not a whole panel (use the 64-bit form then).
+struct PanelFrame {
+  int s;            // panel shift of grid g
+  int64_t base;
+  int nb;
+  int e;            // base - 2 floor(base / 2)
+  int cut0, cut1;   // cut-off in panels of grid g, of grid g - 1
+  int R0, R1;       // R_w h_g in panels of grid g, R_w h_(g-1) in panels of grid g - 1
+  int nB;           // breakpoints within the cut-off
+  int B0[3], B1[3]; // those breakpoints in panels of grid g, of grid g - 1
+  bool ok;
+
+  MARFA_HD void init(int g, int64_t base_, int nb_, int64_t cut, int R_w) {
+    s = panel_shift(g);
+    base = base_;
+    nb = nb_;
+    e = (int)(base - 2 * fl_sh(base, 1));
+    const int64_t P = int64_t(1) << s, P1 = P << 1;
+    const int64_t Rg = (int64_t)R_w * step_fx(g), Rg1 = (int64_t)R_w * step_fx(g - 1);
+    ok = g >= 2 && cut >= 0 && cut % P1 == 0 && Rg % P == 0 && Rg1 % P1 == 0 &&
+         (cut >> s) < (int64_t(1) << 24) && (Rg1 >> s) < (int64_t(1) << 24);
+    cut0 = (int)(cut >> s);
+    cut1 = (int)(cut >> (s + 1));
+    R0 = (int)(Rg >> s);
+    R1 = (int)(Rg1 >> (s + 1));
+    nB = 0;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const int64_t B = chi_break_fx(b);
+      B0[b] = B1[b] = 0;
+      if (B > cut) continue;
+      if (B % P1 != 0) ok = false;
+      B0[b] = (int)(B >> s);
+      B1[b] = (int)(B >> (s + 1));
+      nB = b + 1;
+    }
+  }
+  // c must lie within 2^30 panels of the tile
+  MARFA_HD PanelPos pos(int64_t c) const {
+    PanelPos p;
+    p.q0 = (int)(fl_sh(c, s) - base);
+    p.r0 = (c & ((int64_t(1) << s) - 1)) != 0;
+    p.q1 = (int)(fl_sh(c, s + 1) - fl_sh(base, 1));
+    p.r1 = (c & ((int64_t(1) << (s + 1)) - 1)) != 0;
+    return p;
+  }
+};
+
+// accept_mask(g, ...) over the frame's panels, from the frame (ok) and the line's PanelPos.
+template <typename MT>
+MARFA_HD MT accept_frame(const PanelFrame& F, const PanelPos& p, int g, int gst, bool chi) {
+  MT m = rmask_rel<MT>(p.q0 - F.cut0 + p.r0, p.q0 + F.cut0 - 1, F.nb);
+  if (!m) return MT(0);
+  if (gst > g && p.q0 + F.R0 + 1 >= 0 && p.q0 + p.r0 - F.R0 - 1 <= F.nb)
+    m &= ~rmask_rel<MT>(p.q0 - F.R0, p.q0 + F.R0 + p.r0 - 1, F.nb);
+  if (chi) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      if (b >= F.nB) break;
+      const int a1 = p.q0 - F.B0[b], a2 = p.q0 + F.B0[b];
+      if (a1 >= -1 && a1 + p.r0 <= F.nb + 1) m &= ~rmask_rel<MT>(a1 + p.r0 - 1, a1, F.nb);
+      if (a2 >= -1 && a2 + p.r0 <= F.nb + 1) m &= ~rmask_rel<MT>(a2 + p.r0 - 1, a2, F.nb);
+    }
+  }
+  return m;
+}
+
+// accept_mask(g - 1, ..., child = true) over the frame's panels of grid g.
+template <typename MT>
+MARFA_HD MT accept_parent_frame(const PanelFrame& F, const PanelPos& p, int g, int gst, bool chi) {
+  // parent panel a (relative to floor(base / 2)) -> children 2a - e, 2a + 1 - e
+  MT m = rmask_rel<MT>(2 * (p.q1 - F.cut1 + p.r1) - F.e, 2 * (p.q1 + F.cut1 - 1) + 1 - F.e, F.nb);
+  if (!m) return MT(0);
+  if (gst > g - 1 && p.q0 + 2 * F.R1 + 2 >= 0 && p.q0 + p.r0 - 2 * F.R1 - 2 <= F.nb)
+    m &= ~rmask_rel<MT>(2 * (p.q1 - F.R1) - F.e, 2 * (p.q1 + F.R1 + p.r1 - 1) + 1 - F.e, F.nb);
+  if (chi) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      if (b >= F.nB) break;
+      const int c1 = p.q0 - F.B0[b], c2 = p.q0 + F.B0[b];  // in panels of grid g
+      if (c1 >= -2 && c1 + p.r0 <= F.nb + 2) {
+        const int a = p.q1 - F.B1[b];
+        m &= ~rmask_rel<MT>(2 * (a + p.r1 - 1) - F.e, 2 * a + 1 - F.e, F.nb);
+      }
+      if (c2 >= -2 && c2 + p.r0 <= F.nb + 2) {
+        const int a = p.q1 + F.B1[b];
+        m &= ~rmask_rel<MT>(2 * (a + p.r1 - 1) - F.e, 2 * a + 1 - F.e, F.nb);
+      }
+    }
+  }
+  return m;
+}
+
+// owns_nothing(g, ...) for the frame's span (xa = base P, xb = (base + nb) P).
+MARFA_HD bool owns_nothing_frame(const PanelFrame& F, const PanelPos& p, int g, int gst, bool chi) {
+  if (gst >= g) return false;
+  auto near = [&](int a) { return a >= -1 && a + p.r0 <= F.nb + 1; };
+  if (near(p.q0 - F.cut0) || near(p.q0 + F.cut0)) return false;
+  if (chi) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+      if (b < F.nB && (near(p.q0 - F.B0[b]) || near(p.q0 + F.B0[b]))) return false;
+  }
+  return true;
+}
+
+}  // namespace marfa
