@@ -125,7 +125,9 @@ int64_t marfa_num_points(double nu_lo, double nu_hi);
  *            marfa_num_points(nu_lo, nu_hi); caller-owned;
  *   stream : cudaStream_t to run on (NULL = legacy default stream). With a device
  *            k_out the call is asynchronous on that stream; with a host k_out it
- *            returns after the copy back.
+ *            returns when the result is there: page-locked host memory
+ *            (cudaHostAlloc / cudaHostRegister) is written by the kernels directly,
+ *            pageable memory through a device buffer and a copy back.
  * The line list must cover [nu_lo - cutoff, nu_hi + cutoff] for the sum to be complete;
  * lines outside cannot contribute. The value at a given nu does not depend on the
  * window or on other requests. Errors: MARFA_E_INVAL (window, cut-off, R_w/R_c, enum
@@ -162,7 +164,7 @@ int marfa_absorption_batch(int32_t n_req, const marfa_lines_t* const* lines,
  *              kernels (line-major: a thread per candidate line over 32 or over 16 node
  *              pairs; two-phase: warps of 32 node pairs that stage 32 lines at a time)
  *              on this batch's own work and keep the fastest (otherwise grids 2..7
- *              line-major over 32 pairs, 8..10 two-phase); MARFA_PLAN_SERIAL: capture
+ *              line-major over 16 pairs, 8..10 two-phase); MARFA_PLAN_SERIAL: capture
  *              grids 1..10 one after the
  *              other (otherwise they are parallel branches of the graph, which the GPU
  *              runs concurrently, and per-kernel times overlap);

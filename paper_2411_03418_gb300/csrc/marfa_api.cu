@@ -163,6 +163,46 @@ extern "C" void marfa_free_lines(marfa_lines_t* L) {
 
 static int64_t rint_fix(double v) { return (int64_t)std::nearbyint(v * kFix); }
 
+// order = the positions of the lines stably sorted by nu0: an LSD radix sort (11-bit
+// digits, stable) of the fixed-point keys rint(nu0 2^43), which are monotone in nu0, then
+// each run of equal keys stably re-sorted by nu0 itself.
+static void sort_by_nu0(const marfa_line_t* lines, int64_t n, std::vector<int64_t>& order) {
+  std::vector<uint64_t> k(n), k2(n);
+  std::vector<uint32_t> id(n), id2(n);
+  int64_t kmin = INT64_MAX;
+  for (int64_t i = 0; i < n; ++i) kmin = std::min(kmin, rint_fix(lines[i].nu0));
+  uint64_t kmax = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    k[i] = (uint64_t)(rint_fix(lines[i].nu0) - kmin);
+    kmax = std::max(kmax, k[i]);
+    id[i] = (uint32_t)i;
+  }
+  int bits = 0;
+  while (bits < 64 && (kmax >> bits)) ++bits;
+  std::vector<size_t> cnt(2049);
+  for (int sh = 0; sh < bits; sh += 11) {
+    std::fill(cnt.begin(), cnt.end(), 0);
+    for (int64_t i = 0; i < n; ++i) ++cnt[((k[i] >> sh) & 2047) + 1];
+    for (int d = 0; d < 2048; ++d) cnt[d + 1] += cnt[d];
+    for (int64_t i = 0; i < n; ++i) {
+      const size_t pos = cnt[(k[i] >> sh) & 2047]++;
+      k2[pos] = k[i];
+      id2[pos] = id[i];
+    }
+    k.swap(k2);
+    id.swap(id2);
+  }
+  for (int64_t i = 0; i < n; ++i) order[i] = id[i];
+  for (int64_t a = 0; a < n;) {  // runs of equal keys (nu0 closer than 2^-43 cm^-1)
+    int64_t b = a + 1;
+    while (b < n && k[b] == k[a]) ++b;
+    if (b - a > 1)
+      std::stable_sort(order.begin() + a, order.begin() + b,
+                       [&](int64_t x, int64_t y) { return lines[x].nu0 < lines[y].nu0; });
+    a = b;
+  }
+}
+
 extern "C" int marfa_prepare_lines(const marfa_line_t* lines, int64_t n, const marfa_species_t* sp,
                                    int32_t n_sp, marfa_lines_t** out) {
   if (!out) return fail(MARFA_E_INVAL, "out is NULL");
@@ -177,20 +217,31 @@ extern "C" int marfa_prepare_lines(const marfa_line_t* lines, int64_t n, const m
       return fail(MARFA_E_INVAL, "species %d: mass must be > 0 and q finite", sp[s].mol_iso);
     code[sp[s].mol_iso] = s;
   }
-  std::vector<int64_t> order(n);
+  // validate, resolve species codes (looked up once per run of equal species) and check
+  // whether the lines already come ordered by nu0 (line lists usually do)
+  std::vector<int16_t> code_of(n);
+  bool sorted = true;
+  int32_t last_iso = 0;
+  int last_code = -1;
   for (int64_t i = 0; i < n; ++i) {
     const marfa_line_t& l = lines[i];
     if (!std::isfinite(l.nu0) || l.nu0 < 0 || l.nu0 > 1e5)
       return fail(MARFA_E_INVAL, "line %lld: nu0 must be in [0, 1e5]", (long long)i);
-    if (!code.count(l.mol_iso))
-      return fail(MARFA_E_INVAL, "line %lld: unknown species %d", (long long)i, l.mol_iso);
+    if (last_code < 0 || l.mol_iso != last_iso) {
+      const auto it = code.find(l.mol_iso);
+      if (it == code.end()) return fail(MARFA_E_INVAL, "line %lld: unknown species %d", (long long)i, l.mol_iso);
+      last_iso = l.mol_iso;
+      last_code = it->second;
+    }
+    code_of[i] = (int16_t)last_code;
     if (!std::isfinite(l.S296) || !std::isfinite(l.gamma_air) || !std::isfinite(l.gamma_self) ||
         !std::isfinite(l.E_lower) || !std::isfinite(l.n_air) || !std::isfinite(l.delta_air))
       return fail(MARFA_E_INVAL, "line %lld: non-finite parameter", (long long)i);
-    order[i] = i;
+    if (i > 0 && l.nu0 < lines[i - 1].nu0) sorted = false;
   }
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int64_t a, int64_t b) { return lines[a].nu0 < lines[b].nu0; });
+  std::vector<int64_t> order(n);
+  for (int64_t i = 0; i < n; ++i) order[i] = i;
+  if (!sorted) sort_by_nu0(lines, n, order);
 
   marfa_lines_t* L = new (std::nothrow) marfa_lines_t();
   if (!L) return fail(MARFA_E_NOMEM, "host allocation failed");
@@ -198,10 +249,44 @@ extern "C" int marfa_prepare_lines(const marfa_line_t* lines, int64_t n, const m
   L->n = n;
   L->species.assign(sp, sp + n_sp);
   L->perm.assign(n, 0);
-  std::vector<int64_t> key(n);
-  std::vector<double> nu0(n);
-  std::vector<float> S(n), ga(n), gs(n), E(n), na(n), da(n);
-  std::vector<int16_t> spi(n);
+  // bucket index over the sorted keys: about one line per two buckets on average, at
+  // most 2^26 buckets
+  const int64_t key_first = rint_fix(lines[order[0]].nu0), key_last = rint_fix(lines[order[n - 1]].nu0);
+  const int64_t span = std::max<int64_t>(key_last - key_first, 1);
+  int bs = 20;
+  while (bs < 50 && (((int64_t)1 << (bs + 1)) * 2 * n <= span || (span >> bs) > ((int64_t)1 << 26))) ++bs;
+  L->bshift = bs;
+  L->key_base = (key_first >> bs) << bs;
+  const int64_t nb64 = ((key_last - L->key_base) >> bs) + 1;
+  if (nb64 > (int64_t)1 << 30) {
+    delete L;
+    return fail(MARFA_E_INVAL, "line list too sparse for the bucket index");
+  }
+  L->nbuck = (int32_t)nb64;
+  // one device block for all arrays (256-byte aligned sub-arrays), filled in a host
+  // staging block of the same layout and copied at once
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t sz_key = al(8 * n), sz_nu = al(8 * n), sz_f = al(4 * n), sz_sp = al(2 * n),
+               sz_b = al(4 * (L->nbuck + 1));
+  const size_t total = sz_key + sz_nu + 6 * sz_f + sz_sp + sz_b;
+  std::vector<unsigned char> hb;
+  try {
+    hb.assign(total, 0);
+  } catch (...) {
+    delete L;
+    return fail(MARFA_E_NOMEM, "host allocation failed");
+  }
+  size_t off = 0;
+  auto carve = [&](size_t sz) { const size_t o = off; off += sz; return o; };
+  const size_t o_key = carve(sz_key), o_nu = carve(sz_nu), o_S = carve(sz_f), o_ga = carve(sz_f),
+               o_gs = carve(sz_f), o_E = carve(sz_f), o_na = carve(sz_f), o_da = carve(sz_f),
+               o_sp = carve(sz_sp), o_b = carve(sz_b);
+  int64_t* key = (int64_t*)(hb.data() + o_key);
+  double* nu0 = (double*)(hb.data() + o_nu);
+  float *S = (float*)(hb.data() + o_S), *ga = (float*)(hb.data() + o_ga), *gs = (float*)(hb.data() + o_gs),
+        *E = (float*)(hb.data() + o_E), *na = (float*)(hb.data() + o_na), *da = (float*)(hb.data() + o_da);
+  int16_t* spi = (int16_t*)(hb.data() + o_sp);
+  int32_t* bfirst = (int32_t*)(hb.data() + o_b);
   double dmin = 1e300, dmax = -1e300;
   for (int64_t j = 0; j < n; ++j) {
     const marfa_line_t& l = lines[order[j]];
@@ -214,25 +299,12 @@ extern "C" int marfa_prepare_lines(const marfa_line_t* lines, int64_t n, const m
     E[j] = l.E_lower;
     na[j] = l.n_air;
     da[j] = l.delta_air;
-    spi[j] = (int16_t)code[l.mol_iso];
+    spi[j] = code_of[order[j]];
     dmin = std::min(dmin, (double)l.delta_air);
     dmax = std::max(dmax, (double)l.delta_air);
   }
   L->delta_min = dmin;
   L->delta_max = dmax;
-  // bucket index: about one line per two buckets on average, at most 2^26 buckets
-  const int64_t span = std::max<int64_t>(key[n - 1] - key[0], 1);
-  int bs = 20;
-  while (bs < 50 && (((int64_t)1 << (bs + 1)) * 2 * n <= span || (span >> bs) > ((int64_t)1 << 26))) ++bs;
-  L->bshift = bs;
-  L->key_base = (key[0] >> bs) << bs;
-  const int64_t nb64 = ((key[n - 1] - L->key_base) >> bs) + 1;
-  if (nb64 > (int64_t)1 << 30) {
-    delete L;
-    return fail(MARFA_E_INVAL, "line list too sparse for the bucket index");
-  }
-  L->nbuck = (int32_t)nb64;
-  std::vector<int32_t> bfirst(L->nbuck + 1);
   {
     int64_t i = 0;
     for (int64_t b = 0; b <= L->nbuck; ++b) {
@@ -241,11 +313,6 @@ extern "C" int marfa_prepare_lines(const marfa_line_t* lines, int64_t n, const m
       bfirst[b] = (int32_t)i;
     }
   }
-  // one device block for all arrays (256-byte aligned sub-arrays)
-  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-  const size_t sz_key = al(8 * n), sz_nu = al(8 * n), sz_f = al(4 * n), sz_sp = al(2 * n),
-               sz_b = al(4 * (L->nbuck + 1));
-  const size_t total = sz_key + sz_nu + 6 * sz_f + sz_sp + sz_b;
   cudaError_t e = cudaMalloc(&L->block, total);
   if (e != cudaSuccess) {
     L->block = nullptr;
@@ -253,28 +320,20 @@ extern "C" int marfa_prepare_lines(const marfa_line_t* lines, int64_t n, const m
     return fail(MARFA_E_NOMEM, "cudaMalloc(%zu) failed: %s", total, cudaGetErrorString(e));
   }
   char* p = (char*)L->block;
-  L->key = (int64_t*)p; p += sz_key;
-  L->nu0 = (double*)p; p += sz_nu;
-  L->S296 = (float*)p; p += sz_f;
-  L->ga = (float*)p; p += sz_f;
-  L->gs = (float*)p; p += sz_f;
-  L->E = (float*)p; p += sz_f;
-  L->na = (float*)p; p += sz_f;
-  L->da = (float*)p; p += sz_f;
-  L->sp = (int16_t*)p; p += sz_sp;
-  L->bfirst = (int32_t*)p;
-  struct Cp { void* d; const void* h; size_t b; } cps[] = {
-      {L->key, key.data(), 8 * (size_t)n}, {L->nu0, nu0.data(), 8 * (size_t)n},
-      {L->S296, S.data(), 4 * (size_t)n},  {L->ga, ga.data(), 4 * (size_t)n},
-      {L->gs, gs.data(), 4 * (size_t)n},   {L->E, E.data(), 4 * (size_t)n},
-      {L->na, na.data(), 4 * (size_t)n},   {L->da, da.data(), 4 * (size_t)n},
-      {L->sp, spi.data(), 2 * (size_t)n},  {L->bfirst, bfirst.data(), 4 * bfirst.size()}};
-  for (auto& c : cps) {
-    e = cudaMemcpy(c.d, c.h, c.b, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-      marfa_free_lines(L);
-      return fail(MARFA_E_CUDA, "cudaMemcpy failed: %s", cudaGetErrorString(e));
-    }
+  L->key = (int64_t*)(p + o_key);
+  L->nu0 = (double*)(p + o_nu);
+  L->S296 = (float*)(p + o_S);
+  L->ga = (float*)(p + o_ga);
+  L->gs = (float*)(p + o_gs);
+  L->E = (float*)(p + o_E);
+  L->na = (float*)(p + o_na);
+  L->da = (float*)(p + o_da);
+  L->sp = (int16_t*)(p + o_sp);
+  L->bfirst = (int32_t*)(p + o_b);
+  e = cudaMemcpy(L->block, hb.data(), total, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    marfa_free_lines(L);
+    return fail(MARFA_E_CUDA, "cudaMemcpy failed: %s", cudaGetErrorString(e));
   }
   *out = L;
   return MARFA_OK;
@@ -305,6 +364,7 @@ struct Plan {
   void* dbuf = nullptr;       // per-level line data + slots + tables
   float* dout = nullptr;      // output (own buffer when the caller's is on the host)
   bool own_out = false;
+  bool host_direct = false;  // dout is the device view of a page-locked host k_out
   float* user_out = nullptr;
 };
 
@@ -466,13 +526,25 @@ static bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// The device address of page-locked host memory (cudaHostAlloc / cudaHostRegister, mapped
+// into the device's address space), or null for any other memory.
+static void* pinned_host_view(void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 // Kernel variants of grids 2..10: 0 = line-major (k_coarse_lm, kLPairs node pairs per
 // CTA), 1 = two-phase (k_coarse, kCWarps x kCPairs node pairs per CTA), 2 = line-major
 // with 16 node pairs per CTA (half the shared memory, narrower tiles). Without tuning,
-// grids 2..kLastLM take the line-major kernel (few lines own a panel there, so a thread
-// per line wastes little) and the finer grids the two-phase one.
+// grids 2..kLastLM take the 16-pair line-major kernel (few lines own a panel there, so a
+// thread per line wastes little; the autotuner picks it there on every workload
+// measured) and the finer grids the two-phase one.
 constexpr int kNVariants = 3;
-static int default_variant(int g) { return g <= kLastLM ? 0 : 1; }
+static int default_variant(int g) { return g <= kLastLM ? 2 : 1; }
 static int64_t variant_pairs(int v) {
   return v == 0 ? (int64_t)kLPairs : (v == 1 ? (int64_t)kCPairs * kCWarps : (int64_t)16);
 }
@@ -529,9 +601,16 @@ static int upload(Plan& P, float* k_out, cudaStream_t st) {
   CK(cudaMemcpyAsync(dlev, P.lev.data(), sizeof(LevelDev) * nl, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(dls, P.ls.data(), sizeof(LevelSpeciesDev) * nl * ns, cudaMemcpyHostToDevice, st));
   P.user_out = k_out;
+  void* pinned = k_out && !is_device_ptr(k_out) ? pinned_host_view(k_out) : nullptr;
   if (k_out && is_device_ptr(k_out)) {
     P.dout = k_out;
     P.own_out = false;
+  } else if (pinned) {
+    // the finest-grid kernel stores the result straight into the page-locked host
+    // buffer (no device buffer, no copy back); the call still returns when it is there
+    P.dout = (float*)pinned;
+    P.own_out = false;
+    P.host_direct = true;
   } else {
     r = dev_alloc((void**)&P.dout, 4 * (size_t)P.npts * nl, st);
     if (r) return r;
@@ -727,6 +806,7 @@ static int finish_outputs(std::vector<Plan>& plans, cudaStream_t st) {
       CK(cudaMemcpyAsync(P.user_out, P.dout, 4 * (size_t)P.npts * P.n_levels, cudaMemcpyDeviceToHost, st));
       any_host = true;
     }
+    if (P.host_direct) any_host = true;
   }
   for (auto& P : plans) release(P, st);
   if (any_host) CK(cudaStreamSynchronize(st));
@@ -1162,10 +1242,11 @@ extern "C" int marfa_absorption_noalloc(const marfa_lines_t* lines, const marfa_
   for (int g = 2; g <= kNGrid; ++g) {  // coarse is ordered by grid
     size_t k1 = k;
     while (k1 < coarse.size() && coarse[k1].grid == g) ++k1;
-    if (default_variant(g) == 0)
-      launch_coarse_lm(drd, dci + k, (int)(k1 - k), nullptr, surr, kLPairs, st);
-    else
+    const int v = default_variant(g);
+    if (v == 1)
       launch_coarse(drd, dci + k, (int)(k1 - k), nullptr, surr, st);
+    else
+      launch_coarse_lm(drd, dci + k, (int)(k1 - k), nullptr, surr, v == 2 ? 16 : kLPairs, st);
     k = k1;
   }
   launch_fine(drd, dfi, (int)P.fine.size(), nullptr, surr, st);
