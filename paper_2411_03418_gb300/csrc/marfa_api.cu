@@ -163,43 +163,49 @@ extern "C" void marfa_free_lines(marfa_lines_t* L) {
 
 static int64_t rint_fix(double v) { return (int64_t)std::nearbyint(v * kFix); }
 
-// order = the positions of the lines stably sorted by nu0: an LSD radix sort (11-bit
-// digits, stable) of the fixed-point keys rint(nu0 2^43), which are monotone in nu0, then
-// each run of equal keys stably re-sorted by nu0 itself.
+// order = the positions of the lines stably sorted by nu0: one counting-sort pass on the
+// leading bits of the fixed-point keys rint(nu0 2^43) (monotone in nu0; about one line
+// per bucket), then each bucket stably sorted by nu0 itself (insertion sort; a library
+// stable sort for the rare crowded bucket).
 static void sort_by_nu0(const marfa_line_t* lines, int64_t n, std::vector<int64_t>& order) {
-  std::vector<uint64_t> k(n), k2(n);
-  std::vector<uint32_t> id(n), id2(n);
-  int64_t kmin = INT64_MAX;
-  for (int64_t i = 0; i < n; ++i) kmin = std::min(kmin, rint_fix(lines[i].nu0));
-  uint64_t kmax = 0;
+  std::vector<int64_t> key(n);
+  int64_t kmin = INT64_MAX, kmax = INT64_MIN;
   for (int64_t i = 0; i < n; ++i) {
-    k[i] = (uint64_t)(rint_fix(lines[i].nu0) - kmin);
-    kmax = std::max(kmax, k[i]);
-    id[i] = (uint32_t)i;
+    key[i] = rint_fix(lines[i].nu0);
+    kmin = std::min(kmin, key[i]);
+    kmax = std::max(kmax, key[i]);
   }
+  const uint64_t span = (uint64_t)(kmax - kmin);
   int bits = 0;
-  while (bits < 64 && (kmax >> bits)) ++bits;
-  std::vector<size_t> cnt(2049);
-  for (int sh = 0; sh < bits; sh += 11) {
-    std::fill(cnt.begin(), cnt.end(), 0);
-    for (int64_t i = 0; i < n; ++i) ++cnt[((k[i] >> sh) & 2047) + 1];
-    for (int d = 0; d < 2048; ++d) cnt[d + 1] += cnt[d];
-    for (int64_t i = 0; i < n; ++i) {
-      const size_t pos = cnt[(k[i] >> sh) & 2047]++;
-      k2[pos] = k[i];
-      id2[pos] = id[i];
-    }
-    k.swap(k2);
-    id.swap(id2);
+  while (bits < 64 && (span >> bits)) ++bits;
+  int kb = 1;
+  while (kb < 24 && ((int64_t)1 << kb) < n) ++kb;
+  const int shift = bits > kb ? bits - kb : 0;
+  const int64_t nbk = (int64_t)(span >> shift) + 1;
+  std::vector<int64_t> start(nbk + 1, 0);
+  for (int64_t i = 0; i < n; ++i) ++start[((uint64_t)(key[i] - kmin) >> shift) + 1];
+  for (int64_t b = 0; b < nbk; ++b) start[b + 1] += start[b];
+  {
+    std::vector<int64_t> pos(start.begin(), start.end() - 1);
+    for (int64_t i = 0; i < n; ++i) order[pos[(uint64_t)(key[i] - kmin) >> shift]++] = i;
   }
-  for (int64_t i = 0; i < n; ++i) order[i] = id[i];
-  for (int64_t a = 0; a < n;) {  // runs of equal keys (nu0 closer than 2^-43 cm^-1)
-    int64_t b = a + 1;
-    while (b < n && k[b] == k[a]) ++b;
-    if (b - a > 1)
-      std::stable_sort(order.begin() + a, order.begin() + b,
-                       [&](int64_t x, int64_t y) { return lines[x].nu0 < lines[y].nu0; });
-    a = b;
+  auto less = [&](int64_t x, int64_t y) { return lines[x].nu0 < lines[y].nu0; };
+  for (int64_t b = 0; b < nbk; ++b) {
+    const int64_t a0 = start[b], a1 = start[b + 1];
+    if (a1 - a0 < 2) continue;
+    if (a1 - a0 > 32) {
+      std::stable_sort(order.begin() + a0, order.begin() + a1, less);
+      continue;
+    }
+    for (int64_t i = a0 + 1; i < a1; ++i) {  // stable insertion sort
+      const int64_t v = order[i];
+      int64_t j = i - 1;
+      while (j >= a0 && less(v, order[j])) {
+        order[j + 1] = order[j];
+        --j;
+      }
+      order[j + 1] = v;
+    }
   }
 }
 
