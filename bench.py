@@ -43,6 +43,14 @@ UNIT = "pts*levels/s"
 # series, 6/15-term asymptotic series (the 6-term count is used for both), 9 x 9
 # polynomial cell plus the Gaussian term, small-y cell (6 x 4 terms) plus the Gaussian term.
 FLOPS_FAR, FLOPS_MID, FLOPS_NEAR, FLOPS_SMALL = 20.0, 70.0, 200.0, 90.0
+
+# DRAM bytes (read + write) per launch of the dominant kernel of each workload's full
+# window, from single-pass ncu captures of the timed replay (dram__bytes_read.sum +
+# dram__bytes_write.sum; command and figures in profiles/traffic_dominant_kernels.md).
+# They belong to the kernels as built when captured; other windows report null.
+TRAFFIC_BYTES = {("venus", "finest"): 651.62e6 + 614.90e6,
+                 ("earth", "finest"): 2.92e9 + 1.03e9,
+                 ("batch", "grid1"): 4.22e9 + 24.30e6}
 N_SM = 152
 FP32_LANES = 128
 
@@ -411,7 +419,9 @@ def main():
                      "variants": "0 line-major 32 pairs, 1 two-phase, 2 line-major 16 pairs"},
             "kernel_ms_per_step_serial": {n: float(kms[i] / args.steps) for i, n in enumerate(names)},
             "roofline": {"bound": "alu", "kernel": names[dom], "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": (TRAFFIC_BYTES.get((args.workload, names[dom]))
+                                     if args.nu_lo is None and args.nu_hi is None else None),
                          "flops_per_eval": {"far": FLOPS_FAR, "asymptotic": FLOPS_MID, "poly_cell": FLOPS_NEAR,
                                             "small_y_cell": FLOPS_SMALL},
                          "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz ({src} max clock)"},
