@@ -184,14 +184,15 @@ def chi_tonkov(d_fx) -> np.ndarray:
 
 
 QUAD_COEF = (1.0, 0.25, 0.0625)  # test shape f = amp (1 + d/4 + d^2/16), d in cm^-1
+QUART_COEF = (1.0, 0.25, 0.0625, 0.015625, 0.00390625)  # f = amp sum_j (d/4)^j, j <= 4
 
 
 def profile(shape: str, d_fx, amp, gamma_L, alpha_D, chi_on):
     """amp * f(d) * chi(|d|) at offsets d (fixed point) from the shifted centre.
 
     f: 'lorentz' Eq. (4); 'doppler' Eq. (5); 'voigt' Eqs. (7)-(8); test shapes
-    'const' (f = 1, no amplitude, no chi: k counts lines) and 'quad'
-    (f = 1 + d/4 + d^2/16, no chi).
+    'const' (f = 1, no amplitude, no chi: k counts lines), 'quad'
+    (f = 1 + d/4 + d^2/16, no chi) and 'quart' (f = sum_{j<=4} (d/4)^j, no chi).
     """
     d = np.asarray(d_fx, dtype=np.int64).astype(np.float64) / FIX
     if shape == "const":
@@ -199,6 +200,9 @@ def profile(shape: str, d_fx, amp, gamma_L, alpha_D, chi_on):
     if shape == "quad":
         a0, a1, a2 = QUAD_COEF
         return amp * (a0 + a1 * d + a2 * d * d)
+    if shape == "quart":
+        a0, a1, a2, a3, a4 = QUART_COEF
+        return amp * (a0 + d * (a1 + d * (a2 + d * (a3 + d * a4))))
     if shape == "lorentz":
         f = gamma_L / (np.pi * (gamma_L * gamma_L + d * d))
     elif shape == "doppler":
@@ -244,9 +248,11 @@ def brute_force(wl, lev: int, k_nodes=None) -> np.ndarray:
 
 
 # ---------------------------------------------------------------- Sec. 2.4 eleven-grid partition
-def accept(g: int, m, c, gs, chi_on, cut: int, R_w: int):
+def accept(g: int, m, c, gs, chi_on, cut: int, R_w: int, wide: bool = False):
     """Whether grid g (1..10) may carry a line on panel m: the closed interval
-    [m P, (m+1) P], P = 2 h_g, with its three nodes at 0, h_g, 2 h_g.
+    [m P, (m+1) P], P = 2 h_g, with its three nodes at 0, h_g, 2 h_g (wide: P = 4 h_g
+    and five nodes, the 5-point variant of Sec. 2.4; the same criteria on the wider
+    panels).
 
     Reading of Sec. 2.4 (centre on the finest grid, wings on ever coarser grids):
       support  : the whole panel lies within the cut-off, d_far <= cut-off;
@@ -259,7 +265,7 @@ def accept(g: int, m, c, gs, chi_on, cut: int, R_w: int):
     """
     m = np.asarray(m, dtype=np.int64)
     c = np.asarray(c, dtype=np.int64)
-    s = panel_shift(g)
+    s = panel_shift(g) + (1 if wide else 0)
     a = m << s
     b = a + (np.int64(1) << s)
     da = np.abs(a - c)
@@ -280,29 +286,53 @@ def accept(g: int, m, c, gs, chi_on, cut: int, R_w: int):
     return ok
 
 
-def owned(g: int, m, c, gs, chi_on, cut: int, R_w: int):
+def owned(g: int, m, c, gs, chi_on, cut: int, R_w: int, wide: bool = False):
     """Grid g owns panel m for a line when it accepts it and the parent panel on grid
-    g-1 (panel m >> 1) is not accepted; grid 1 owns what it accepts."""
-    ok = accept(g, m, c, gs, chi_on, cut, R_w)
+    g-1 (panel m >> 1, panels of the same number of steps) is not accepted; grid 1 owns
+    what it accepts."""
+    ok = accept(g, m, c, gs, chi_on, cut, R_w, wide)
     if g > 1:
-        ok &= ~accept(g - 1, np.asarray(m, dtype=np.int64) >> 1, c, gs, chi_on, cut, R_w)
+        ok &= ~accept(g - 1, np.asarray(m, dtype=np.int64) >> 1, c, gs, chi_on, cut, R_w, wide)
     return ok
 
 
-def fine_owned(k, c, gs, chi_on, cut: int, R_w: int):
+def fine_owned(k, c, gs, chi_on, cut: int, R_w: int, wide: bool = False):
     """The finest grid evaluates node k itself when |x_k - c| <= cut-off and grid 10
-    does not accept the panel containing x_k (half-open panels [a, a+2h))."""
+    does not accept the panel containing x_k (half-open panels [a, a+P))."""
     k = np.asarray(k, dtype=np.int64)
     X = k << fine_shift()
     within = np.abs(X - np.asarray(c, dtype=np.int64)) <= cut
-    m10 = X >> panel_shift(NGRID)
-    return within & ~accept(NGRID, m10, c, gs, chi_on, cut, R_w)
+    m10 = X >> (panel_shift(NGRID) + (1 if wide else 0))
+    return within & ~accept(NGRID, m10, c, gs, chi_on, cut, R_w, wide)
 
 
 def lagrange3(t):
     """Quadratic Lagrange weights for nodes at 0, 1, 2 evaluated at t."""
     t = np.asarray(t, dtype=np.float64)
     return (t - 1.0) * (t - 2.0) * 0.5, t * (2.0 - t), t * (t - 1.0) * 0.5
+
+
+def lagrange5(t):
+    """Quartic Lagrange weights for nodes at 0, 1, 2, 3, 4 evaluated at t: node j gets
+    prod_{i != j} (t - i) / (j - i)."""
+    t = np.asarray(t, dtype=np.float64)
+    out = []
+    for j in range(5):
+        w = np.ones_like(t)
+        for i in range(5):
+            if i != j:
+                w = w * (t - i) / (j - i)
+        out.append(w)
+    return tuple(out)
+
+
+def stencil_of(wl) -> int:
+    """Interpolation points per panel: 3 (the paper's quadratic) or 5 (quartic on panels
+    of four steps)."""
+    st = int(getattr(wl, "stencil", 3))
+    if st not in (3, 5):
+        raise ValueError(f"stencil {st}")
+    return st
 
 
 def _line_chunks(n, size):
@@ -331,6 +361,8 @@ def eleven_grid(wl, lev: int, stats: dict | None = None, dump: dict | None = Non
     gs = gstar(W, wl.R_c)
     chi_on = P["chi_on"]
     cut = int(round(wl.cutoff * FIX))
+    npn = stencil_of(wl)          # nodes per panel
+    wide = npn == 5
     k_lo, k_hi = window_nodes(wl.nu_lo, wl.nu_hi)
     npts = k_hi - k_lo + 1
     X_lo = k_lo << fine_shift()
@@ -348,13 +380,11 @@ def eleven_grid(wl, lev: int, stats: dict | None = None, dump: dict | None = Non
                        chi_on[sel])
 
     for g in range(1, NGRID + 1):
-        s = panel_shift(g)
+        s = panel_shift(g) + (1 if wide else 0)
         m_first = X_lo >> s
         m_last = X_hi >> s
         npan = m_last - m_first + 1
-        L = np.zeros(npan)
-        M = np.zeros(npan)
-        R = np.zeros(npan)
+        V = [np.zeros(npan) for _ in range(npn)]  # the panel's node values, left to right
         n_eval = 0
         dl, dm = [], []
         per = max(1, chunk_pairs // max(npan, 1))
@@ -363,7 +393,7 @@ def eleven_grid(wl, lev: int, stats: dict | None = None, dump: dict | None = Non
             mm = np.arange(m_first, m_last + 1, dtype=np.int64)
             li = np.repeat(idx, npan)
             mi = np.tile(mm, len(idx))
-            own = owned(g, mi, c[li], gs[li], chi_on[li], cut, wl.R_w)
+            own = owned(g, mi, c[li], gs[li], chi_on[li], cut, wl.R_w, wide)
             li = li[own]
             mi = mi[own]
             if len(li) == 0:
@@ -371,24 +401,25 @@ def eleven_grid(wl, lev: int, stats: dict | None = None, dump: dict | None = Non
             if dump is not None:
                 dl.append(li)
                 dm.append(mi)
-            # distinct nodes: odd node 2m+1 once per owned panel; even nodes 2m and
-            # 2m+2 shared by neighbouring owned panels of the same line.
+            # distinct nodes: the npn - 2 inner nodes once per owned panel; the end nodes
+            # shared by neighbouring owned panels of the same line.
             own2 = own.reshape(len(idx), npan)
             left_even = own2.copy()
             left_even[:, 1:] |= own2[:, :-1]
-            n_eval += int(own2.sum()) + int(left_even.sum()) + int(own2[:, -1].sum())
+            n_eval += (npn - 2) * int(own2.sum()) + int(left_even.sum()) + int(own2[:, -1].sum())
             a = mi << s
-            h = np.int64(1) << (s - 1)
+            h = np.int64(1) << (s - (npn - 1).bit_length() + 1)  # the grid step h_g
             slot = mi - m_first
-            L += np.bincount(slot, weights=f_at(li, a), minlength=npan)
-            M += np.bincount(slot, weights=f_at(li, a + h), minlength=npan)
-            R += np.bincount(slot, weights=f_at(li, a + 2 * h), minlength=npan)
+            for q in range(npn):
+                V[q] += np.bincount(slot, weights=f_at(li, a + q * h), minlength=npan)
         # interpolate this grid's panels onto the finest nodes
         mp = Xn >> s
-        t = (Xn - (mp << s)).astype(np.float64) / float(np.int64(1) << (s - 1))
-        w0, w1, w2 = lagrange3(t)
+        h = np.int64(1) << (s - (npn - 1).bit_length() + 1)
+        t = (Xn - (mp << s)).astype(np.float64) / float(h)
+        w = lagrange5(t) if wide else lagrange3(t)
         j = mp - m_first
-        out += L[j] * w0 + M[j] * w1 + R[j] * w2
+        for q in range(npn):
+            out += V[q][j] * w[q]
         if stats is not None:
             stats[g] = n_eval
         if dump is not None:
@@ -403,7 +434,7 @@ def eleven_grid(wl, lev: int, stats: dict | None = None, dump: dict | None = Non
         idx = np.arange(sl.start, sl.stop)
         li = np.repeat(idx, npts)
         ki = np.tile(knodes, len(idx))
-        own = fine_owned(ki, c[li], gs[li], chi_on[li], cut, wl.R_w)
+        own = fine_owned(ki, c[li], gs[li], chi_on[li], cut, wl.R_w, wide)
         li = li[own]
         ki = ki[own]
         if len(li) == 0:
@@ -438,6 +469,8 @@ def eleven_grid_at(wl, lev: int, k_nodes, line_block: int = 1 << 16) -> np.ndarr
     gs_all = gstar(W, wl.R_c)
     chi_all = P["chi_on"]
     cut = int(round(wl.cutoff * FIX))
+    npn = stencil_of(wl)
+    wide = npn == 5
     order = np.argsort(c_all, kind="stable")
     cs = c_all[order]
     res = np.zeros(len(k_nodes))
@@ -454,19 +487,19 @@ def eleven_grid_at(wl, lev: int, k_nodes, line_block: int = 1 << 16) -> np.ndarr
             ch = chi_all[sel]
             done = np.zeros(len(sel), dtype=bool)
             for g in range(1, NGRID + 1):
-                s = panel_shift(g)
+                s = panel_shift(g) + (1 if wide else 0)
                 m = np.full(len(sel), X >> s, dtype=np.int64)
-                acc = accept(g, m, c, gs, ch, cut, wl.R_w) & ~done
+                acc = accept(g, m, c, gs, ch, cut, wl.R_w, wide) & ~done
                 if np.any(acc):
                     j = np.nonzero(acc)[0]
                     a = m[j] << s
-                    h = np.int64(1) << (s - 1)
+                    h = np.int64(1) << (s - (npn - 1).bit_length() + 1)
                     t = float(X - (int(X >> s) << s)) / float(h)
-                    w0, w1, w2 = lagrange3(t)
+                    w = lagrange5(t) if wide else lagrange3(t)
                     sj = sel[j]
                     fv = [profile(wl.shape, a + q * h - c[j], P["amp"][sj], P["gamma_L"][sj],
-                                  P["alpha_D"][sj], ch[j]) for q in range(3)]
-                    parts.append(fv[0] * w0 + fv[1] * w1 + fv[2] * w2)
+                                  P["alpha_D"][sj], ch[j]) for q in range(npn)]
+                    parts.append(sum(fv[q] * w[q] for q in range(npn)))
                     done |= acc
             rest = np.nonzero(~done)[0]
             if len(rest):

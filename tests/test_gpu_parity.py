@@ -179,6 +179,9 @@ PARITY_CASES = [
          chi="tonkov", chi_species=1),
     dict(seed=57, n=200, lo=1000.0, hi=1000.0 + 1.0 / 2048, cut=3.5, T=(296.0,), p=(1.0,),
          chi="tonkov", chi_species=1),
+    # cut-off 400 cm^-1: lines on all three chi branches of Eq. (10) (3-150, 150-300, > 300)
+    dict(seed=58, n=400, lo=2000.0, hi=2001.5, cut=400.0, T=(500.0, 250.0), p=(10.0, 0.05),
+         chi="tonkov", chi_species=1),
 ]
 
 

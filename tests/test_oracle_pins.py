@@ -243,6 +243,86 @@ def test_quadratic_shape_eleven_grid_equals_brute_force(case):
     assert np.abs(k - kb).max() <= 1e-12 * np.abs(kb).max()
 
 
+# ------------------------------------------------------------ 5-point variant (quartic panels)
+def test_lagrange5_reproduces_quartics():
+    t = np.linspace(0.0, 4.0, 33)
+    w = O.lagrange5(t)
+    for p in range(5):
+        got = sum(w[j] * float(j) ** p for j in range(5))
+        assert np.allclose(got, t ** p, rtol=0, atol=1e-12 * max(1.0, 4.0 ** p))
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_five_point_quartic_shape_equals_brute_force(case):
+    """Quartic interpolation on panels of four steps reproduces a quartic exactly, so
+    eleven-grid == brute force to round-off proves that the 5-point partition counts
+    every finest node once (cut-off edges and chi kinks included)."""
+    T, p, chi, cut, Rw, Rc, (lo, hi) = case
+    wl = tiny_workload(13, 250, lo, hi, cut, T=T, p=p, shape="quart", chi=chi, chi_species=1,
+                       R_w=Rw, R_c=Rc, stencil=5)
+    k = O.eleven_grid(wl, 0)
+    kb = O.brute_force(wl, 0)
+    assert np.abs(k - kb).max() <= 1e-11 * np.abs(kb).max()
+
+
+def test_three_point_is_not_exact_on_quartics():
+    T, p, chi, cut, Rw, Rc, (lo, hi) = CASES[0]
+    wl = tiny_workload(13, 250, lo, hi, cut, T=T, p=p, shape="quart", chi=chi, R_w=Rw, R_c=Rc)
+    k = O.eleven_grid(wl, 0)
+    kb = O.brute_force(wl, 0)
+    assert np.abs(k - kb).max() > 1e-6 * np.abs(kb).max()
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_five_point_constant_shape_counts_lines(case):
+    T, p, chi, cut, Rw, Rc, (lo, hi) = case
+    wl = tiny_workload(11, 250, lo, hi, cut, T=T, p=p, shape="const", chi=chi, chi_species=1,
+                       R_w=Rw, R_c=Rc, stencil=5)
+    k = O.eleven_grid(wl, 0)
+    P = O.level_params(wl, 0)
+    c = O.centre_fixed(P["nu_shift"])
+    k_lo, k_hi = O.window_nodes(lo, hi)
+    X = np.arange(k_lo, k_hi + 1, dtype=np.int64) << O.fine_shift()
+    count = (np.abs(X[:, None] - c[None, :]) <= int(round(cut * O.FIX))).sum(axis=1)
+    assert np.abs(k - count).max() < 1e-9 * max(1, count.max())
+
+
+def test_five_point_pointwise_form_agrees(c0):
+    c5 = c0.with_(stencil=5)
+    k = O.eleven_grid(c5, 0)
+    k_lo, _ = O.window_nodes(c5.nu_lo, c5.nu_hi)
+    idx = np.array([0, 1, 7, 8, 15, 16, 1023, 4096, 10000, 20479, 20480])
+    assert np.allclose(O.eleven_grid_at(c5, 0, k_lo + idx), k[idx], rtol=1e-12, atol=0)
+
+
+def test_five_point_voigt_error_is_smaller(c0):
+    """Sec. 2.4 uses 3-point interpolation; the 5-point variant on four-step panels (same
+    partition rules) cuts the interpolation error several-fold at the same R_w, R_c."""
+    k_lo, _ = O.window_nodes(c0.nu_lo, c0.nu_hi)
+    idx = np.arange(0, 20481, 37)
+    kb = O.brute_force(c0, 0, k_lo + idx)
+    e3 = np.abs(O.eleven_grid(c0, 0)[idx] / kb - 1).max()
+    e5 = np.abs(O.eleven_grid(c0.with_(stencil=5), 0)[idx] / kb - 1).max()
+    assert e5 < e3 / 3
+
+
+def test_five_point_planted_mistake_fails(monkeypatch):
+    T, p, chi, cut, Rw, Rc, (lo, hi) = CASES[1]
+    wl = tiny_workload(13, 120, lo, hi, cut, T=T, p=p, shape="quart", chi=chi, chi_species=1,
+                       R_w=Rw, R_c=Rc, stencil=5)
+
+    def holds():
+        k = O.eleven_grid(wl, 0)
+        kb = O.brute_force(wl, 0)
+        return np.abs(k - kb).max() <= 1e-11 * np.abs(kb).max()
+
+    assert holds()
+    with monkeypatch.context() as m:
+        orig = O.lagrange5
+        m.setattr(O, "lagrange5", lambda t: tuple(reversed(orig(t))))
+        assert not holds()
+
+
 def test_pointwise_form_agrees_with_grid_form(c0):
     k = O.eleven_grid(c0, 0)
     k_lo, _ = O.window_nodes(c0.nu_lo, c0.nu_hi)
@@ -311,7 +391,7 @@ def test_planted_mistakes_fail_a_pin(monkeypatch):
         assert not _quad_pin_holds(wl)
     # 2. ownership that forgets the parent test (double counting)
     with monkeypatch.context() as m:
-        m.setattr(O, "owned", lambda g, mm, c, gs, ch, cut, Rw: O.accept(g, mm, c, gs, ch, cut, Rw))
+        m.setattr(O, "owned", lambda g, mm, c, gs, ch, cut, Rw, wide=False: O.accept(g, mm, c, gs, ch, cut, Rw, wide))
         assert not _quad_pin_holds(wl)
     # 3. a wrong sign in the pressure shift breaks the Lorentz single-line pin
     with monkeypatch.context() as m:
@@ -329,8 +409,8 @@ def test_planted_mistakes_fail_a_pin(monkeypatch):
     with monkeypatch.context() as m:
         orig_acc = O.accept
 
-        def acc(g, mm, c, gs, ch, cut, Rw):
-            return orig_acc(g, mm, c, gs, ch, cut + (1 << O.panel_shift(g)), Rw)
+        def acc(g, mm, c, gs, ch, cut, Rw, wide=False):
+            return orig_acc(g, mm, c, gs, ch, cut + (1 << O.panel_shift(g)), Rw, wide)
         m.setattr(O, "accept", acc)
         with pytest.raises(AssertionError):
             test_constant_shape_counts_lines_within_cutoff(CASES[3])

@@ -67,6 +67,7 @@ class Workload:
     R_w: int = 8
     R_c: int = 8
     surrogate: int = 0
+    stencil: int = 3   # interpolation points per coarse panel: 3 (Sec. 2.4) or 5
     meta: dict = field(default_factory=dict)
 
     @property
@@ -228,7 +229,8 @@ def config3_earth(seed: int = 3, n_lines: int = 1_200_000, n_levels: int = 50) -
 
 def tiny_workload(seed: int, n_lines: int, nu_lo: float, nu_hi: float, cutoff: float,
                   T=(296.0,), p=(1.0,), shape="voigt", chi="none", units="k_cm1",
-                  spread: float | None = None, chi_species: int = 0, R_w: int = 8, R_c: int = 8) -> Workload:
+                  spread: float | None = None, chi_species: int = 0, R_w: int = 8, R_c: int = 8,
+                  stencil: int = 3) -> Workload:
     """A small seeded request: n_lines CO2-like lines spread over window +- spread."""
     rng = np.random.Generator(np.random.PCG64(1000 + seed))
     s = cutoff if spread is None else spread
@@ -240,5 +242,5 @@ def tiny_workload(seed: int, n_lines: int, nu_lo: float, nu_hi: float, cutoff: f
     return Workload(
         name=f"small seed {seed}", lines=lines, species=sp, T=T, p=p,
         vmr=np.full((len(T), 1), 0.965), nu_lo=nu_lo, nu_hi=nu_hi, cutoff=cutoff,
-        shape=shape, chi=chi, units=units, R_w=R_w, R_c=R_c,
+        shape=shape, chi=chi, units=units, R_w=R_w, R_c=R_c, stencil=stencil,
     )
