@@ -234,6 +234,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer steps")
     ap.add_argument("--no-count", action="store_true", help="skip the evaluation-counting call")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-Voigt leg")
+    ap.add_argument("--stencil", type=int, choices=[3, 5], default=3,
+                    help="interpolation points per coarse panel: 3 (the paper's) or 5 (quartic)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -241,6 +243,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
     wls, wname = load_workloads(args.workload)
+    if args.stencil != 3:
+        wls = [w.with_(stencil=args.stencil) for w in wls]
     if args.nu_lo is not None or args.nu_hi is not None:
         wls = [w.with_(nu_lo=args.nu_lo if args.nu_lo is not None else w.nu_lo,
                        nu_hi=args.nu_hi if args.nu_hi is not None else w.nu_hi) for w in wls]
@@ -391,7 +395,7 @@ def main():
     if rank == 0:
         cfg = {"workload": wname, "requests": len(wls), "lines": int(sum(len(w.lines) for w in wls)),
                "levels": int(sum(w.n_levels for w in wls)), "points_x_levels_per_step": int(units // world),
-               "l2": "flushed between steps (256 MB write)"}
+               "l2": "flushed between steps (256 MB write)", "stencil": args.stencil}
         if len(wls) == 1:
             cfg["npts_per_level"] = npts[0]
         line = {
@@ -421,7 +425,8 @@ def main():
             "roofline": {"bound": "alu", "kernel": names[dom], "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": (TRAFFIC_BYTES.get((args.workload, names[dom]))
-                                     if args.nu_lo is None and args.nu_hi is None else None),
+                                     if args.nu_lo is None and args.nu_hi is None and args.stencil == 3
+                                     else None),
                          "flops_per_eval": {"far": FLOPS_FAR, "asymptotic": FLOPS_MID, "poly_cell": FLOPS_NEAR,
                                             "small_y_cell": FLOPS_SMALL},
                          "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz ({src} max clock)"},

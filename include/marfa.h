@@ -39,13 +39,15 @@ extern "C" {
 /* line shapes (Sec. 2.2); the TEST shapes exist to pin the grid bookkeeping:
  * TEST_CONST adds exactly 1 per line within the cut-off (k counts lines),
  * TEST_QUAD adds S(T)[n](1 + d/4 + d^2/16), d = nu - nu~0 in cm^-1, which the 3-point
- * interpolation reproduces exactly. Neither applies the chi-factor. */
+ * interpolation reproduces exactly; TEST_QUART adds S(T)[n] sum_{j<=4} (d/4)^j, which the
+ * 5-point interpolation reproduces exactly. None applies the chi-factor. */
 enum {
   MARFA_SHAPE_LORENTZ = 0,    /* Eq. (4)                                      */
   MARFA_SHAPE_VOIGT = 1,      /* Eqs. (7)-(8), the default of the paper        */
   MARFA_SHAPE_DOPPLER = 2,    /* Eq. (5)                                      */
   MARFA_SHAPE_TEST_CONST = 100,
-  MARFA_SHAPE_TEST_QUAD = 101
+  MARFA_SHAPE_TEST_QUAD = 101,
+  MARFA_SHAPE_TEST_QUART = 102
 };
 enum { MARFA_CHI_NONE = 0, MARFA_CHI_TONKOV = 1 };          /* Eq. (10)          */
 enum { MARFA_UNITS_SIGMA = 0,   /* cm^2/molecule, Eq. (3)                      */
@@ -92,6 +94,10 @@ typedef struct {
   int32_t R_w;         /* wing distance, in steps of a grid, below which that grid
                           refines (1..64; 8 is the default preset)                    */
   int32_t R_c;         /* a grid resolves a core when its step <= W / R_c (1..64)      */
+  int32_t stencil;     /* interpolation points per coarse-grid panel: 3 (Sec. 2.4: panels
+                          of two steps, quadratic; 0 means 3) or 5 (panels of four steps,
+                          quartic; the same partition rules on the wider panels).
+                          Not in the paper (its Sec. 2.4 mentions the option).      */
 } marfa_request_t;
 
 /* Opaque prepared line list, resident on the device it was prepared on. */

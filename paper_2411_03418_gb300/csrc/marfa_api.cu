@@ -403,7 +403,7 @@ static int validate_request(const marfa_request_t* rq, int64_t* npts) {
     return fail(MARFA_E_INVAL, "cut-off must be in (0, 1000] cm^-1");
   const int s = rq->shape;
   if (!(s == MARFA_SHAPE_LORENTZ || s == MARFA_SHAPE_VOIGT || s == MARFA_SHAPE_DOPPLER ||
-        s == MARFA_SHAPE_TEST_CONST || s == MARFA_SHAPE_TEST_QUAD))
+        s == MARFA_SHAPE_TEST_CONST || s == MARFA_SHAPE_TEST_QUAD || s == MARFA_SHAPE_TEST_QUART))
     return fail(MARFA_E_INVAL, "unknown shape %d", s);
   if (rq->chi != MARFA_CHI_NONE && rq->chi != MARFA_CHI_TONKOV)
     return fail(MARFA_E_INVAL, "unknown chi %d", rq->chi);
@@ -414,6 +414,8 @@ static int validate_request(const marfa_request_t* rq, int64_t* npts) {
     return fail(MARFA_E_INVAL, "the surrogate stands in for the Voigt profile only");
   if (rq->R_w < 1 || rq->R_w > 64 || rq->R_c < 1 || rq->R_c > 64)
     return fail(MARFA_E_INVAL, "R_w and R_c must be in 1..64");
+  if (rq->stencil != 0 && rq->stencil != 3 && rq->stencil != 5)
+    return fail(MARFA_E_INVAL, "stencil must be 3 or 5 (0: 3)");
   *npts = np;
   return MARFA_OK;
 }
@@ -491,10 +493,16 @@ static int build_plan(Plan& P, const marfa_lines_t* L, const marfa_level_t* leve
   const int64_t X_lo = R.k_lo << kFineShift, X_hi = R.k_hi << kFineShift;
   int64_t off = 0;
   R.m_first[0] = R.npan[0] = R.slot_off[0] = 0;
+  R.wide = rq->stencil == 5 ? 1 : 0;
   for (int g = 1; g <= kNGrid; ++g) {
     const int s = panel_shift(g);
-    R.m_first[g] = X_lo >> s;
-    R.npan[g] = (X_hi >> s) - R.m_first[g] + 1;
+    if (R.wide) {  // whole four-step panels: both halves of every panel the window touches
+      R.m_first[g] = (X_lo >> (s + 1)) << 1;
+      R.npan[g] = (((X_hi >> (s + 1)) << 1) + 1) - R.m_first[g] + 1;
+    } else {
+      R.m_first[g] = X_lo >> s;
+      R.npan[g] = (X_hi >> s) - R.m_first[g] + 1;
+    }
     R.slot_off[g] = off;
     off += 3 * R.npan[g] * (g == 1 ? kG1Split : 1);
   }
@@ -654,6 +662,7 @@ struct WorkSet {
   std::vector<FineItem> fi;
   int variant[kNGrid + 1] = {0};
   bool surr = false;                       // some request uses the surrogate
+  bool wide = false;                       // the requests use the 5-point partition
   bool surr_grid[kNGrid + 2] = {false};    // surrogate-capable kernels for grid 1..10, 11 finest
   size_t cw = 8 * kCountFields;            // count bytes per item
   void* buf = nullptr;
@@ -677,6 +686,10 @@ static int build_work(std::vector<Plan>& plans, const int* variant, bool count, 
                       cudaStream_t st) {
   for (auto& P : plans) W.rds.push_back(P.rd);
   for (auto& R : W.rds) W.surr = W.surr || R.mlp != nullptr;
+  W.wide = !W.rds.empty() && W.rds[0].wide != 0;
+  for (auto& R : W.rds)
+    if ((R.wide != 0) != W.wide)
+      return fail(MARFA_E_INVAL, "the requests of one call or plan must share one stencil");
   for (int g = 1; g <= kNGrid + 1; ++g) W.surr_grid[g] = W.surr;
   for (auto& P : plans) W.gi.insert(W.gi.end(), P.g1.begin(), P.g1.end());
   for (int g = 2; g <= kNGrid; ++g) {
@@ -736,15 +749,16 @@ static int build_work(std::vector<Plan>& plans, const int* variant, bool count, 
 static void launch_grid(const WorkSet& W, int g, cudaStream_t st) {
   const int n = (int)W.ci[g].size();
   if (W.variant[g] == 1)
-    launch_coarse(W.drd, W.dci[g], n, W.dcc[g], W.surr_grid[g], st);
+    launch_coarse(W.drd, W.dci[g], n, W.dcc[g], W.surr_grid[g], W.wide, st);
   else
-    launch_coarse_lm(W.drd, W.dci[g], n, W.dcc[g], W.surr_grid[g], W.variant[g] == 2 ? 16 : kLPairs, st);
+    launch_coarse_lm(W.drd, W.dci[g], n, W.dcc[g], W.surr_grid[g], W.variant[g] == 2 ? 16 : kLPairs, W.wide,
+                     st);
 }
 
 // Every summation launch of a work set: grid 1, grids 2..10, finest grid + cascade.
 static int launch_work(const WorkSet& W, cudaStream_t st, bool timed) {
   cudaEvent_t ev = timed ? timing_begin(st) : nullptr;
-  launch_g1(W.drd, W.dgi, (int)W.gi.size(), W.dgc, W.surr_grid[1], st);
+  launch_g1(W.drd, W.dgi, (int)W.gi.size(), W.dgc, W.surr_grid[1], W.wide, st);
   timing_end(ev, 1, st);
   cudaError_t e;
   if ((e = cudaGetLastError())) return fail(MARFA_E_CUDA, "grid-1 kernel: %s", cudaGetErrorString(e));
@@ -755,7 +769,7 @@ static int launch_work(const WorkSet& W, cudaStream_t st, bool timed) {
   }
   if ((e = cudaGetLastError())) return fail(MARFA_E_CUDA, "coarse-grid kernel: %s", cudaGetErrorString(e));
   ev = timed ? timing_begin(st) : nullptr;
-  launch_fine(W.drd, W.dfi, (int)W.fi.size(), W.dfc, W.surr_grid[kNGrid + 1], st);
+  launch_fine(W.drd, W.dfi, (int)W.fi.size(), W.dfc, W.surr_grid[kNGrid + 1], W.wide, st);
   timing_end(ev, kNGrid + 1, st);
   if ((e = cudaGetLastError())) return fail(MARFA_E_CUDA, "fine kernel: %s", cudaGetErrorString(e));
   return MARFA_OK;
@@ -959,7 +973,7 @@ static int plan_launch_all(marfa_plan_t* X, cudaStream_t st, bool capture) {
     for (int i = 0; i < kSide; ++i) cudaStreamWaitEvent(X->side[i], X->fork, 0);
   }
   rec(2, br[1]);
-  launch_g1(W.drd, W.dgi, (int)W.gi.size(), nullptr, W.surr_grid[1], br[1]);
+  launch_g1(W.drd, W.dgi, (int)W.gi.size(), nullptr, W.surr_grid[1], W.wide, br[1]);
   rec(3, br[1]);
   for (int g = kNGrid; g >= 2; --g) {  // the finer grids carry more work: start them first
     rec(2 * g, br[g]);
@@ -972,7 +986,7 @@ static int plan_launch_all(marfa_plan_t* X, cudaStream_t st, bool capture) {
       cudaStreamWaitEvent(st, X->join[i], 0);
     }
   rec(2 * (kNGrid + 1), st);
-  launch_fine(W.drd, W.dfi, (int)W.fi.size(), nullptr, W.surr_grid[kNGrid + 1], st);
+  launch_fine(W.drd, W.dfi, (int)W.fi.size(), nullptr, W.surr_grid[kNGrid + 1], W.wide, st);
   rec(2 * (kNGrid + 1) + 1, st);
   cudaError_t e = cudaGetLastError();
   if (e) return fail(MARFA_E_CUDA, "plan launches: %s", cudaGetErrorString(e));
@@ -1243,19 +1257,20 @@ extern "C" int marfa_absorption_noalloc(const marfa_lines_t* lines, const marfa_
   // nothing left in the scratch by an earlier call needs clearing.
   launch_level_prep(a, (int)nl, st);
   const bool surr = R.mlp != nullptr;
-  launch_g1(drd, dgi, (int)P.g1.size(), nullptr, surr, st);
+  const bool wide = P.rd.wide != 0;
+  launch_g1(drd, dgi, (int)P.g1.size(), nullptr, surr, wide, st);
   size_t k = 0;
   for (int g = 2; g <= kNGrid; ++g) {  // coarse is ordered by grid
     size_t k1 = k;
     while (k1 < coarse.size() && coarse[k1].grid == g) ++k1;
     const int v = default_variant(g);
     if (v == 1)
-      launch_coarse(drd, dci + k, (int)(k1 - k), nullptr, surr, st);
+      launch_coarse(drd, dci + k, (int)(k1 - k), nullptr, surr, wide, st);
     else
-      launch_coarse_lm(drd, dci + k, (int)(k1 - k), nullptr, surr, v == 2 ? 16 : kLPairs, st);
+      launch_coarse_lm(drd, dci + k, (int)(k1 - k), nullptr, surr, v == 2 ? 16 : kLPairs, wide, st);
     k = k1;
   }
-  launch_fine(drd, dfi, (int)P.fine.size(), nullptr, surr, st);
+  launch_fine(drd, dfi, (int)P.fine.size(), nullptr, surr, wide, st);
   CK(cudaGetLastError());
   return MARFA_OK;
 }

@@ -23,7 +23,7 @@ __host__ __device__ __forceinline__ int64_t fl_sh(int64_t a, int s) { return a >
 __host__ __device__ __forceinline__ int64_t cl_sh(int64_t a, int s) { return -((-a) >> s); }
 
 constexpr int kShapeLorentz = 0, kShapeVoigt = 1, kShapeDoppler = 2, kShapeConst = 100,
-              kShapeQuad = 101;
+              kShapeQuad = 101, kShapeQuart = 102;
 
 // Per level (host-computed in double precision).
 struct LevelDev {
@@ -98,6 +98,7 @@ struct ReqDev {
   float* slots;             // [n_levels][slots_per_level]
   int64_t cut_fx;           // cut-off, fixed point
   int32_t R_w;
+  int32_t wide;             // 5-point variant: ownership on panels of four steps, quartic cascade
   int32_t shape;
   int32_t chi_req;          // request asks for the chi-factor
   const MlpWeights* mlp;    // surrogate weights and guard, null for the plain path
@@ -162,14 +163,16 @@ struct PrepArgs {
 // in the asymptotic series and in small-y cells (voigt_class 2, 1 and 3).
 constexpr int kCountFields = 5;
 void launch_level_prep(const PrepArgs& a, int n_levels, cudaStream_t st);
+// wide: every request of the launch uses the 5-point partition (the plain kernels are
+// compiled for one partition; the counting and surrogate variants read it per request).
 void launch_g1(const ReqDev* reqs, const G1Item* items, int n_items, int64_t* counts, bool surr,
-               cudaStream_t st);
+               bool wide, cudaStream_t st);
 void launch_coarse(const ReqDev* reqs, const CoarseItem* items, int n_items, int64_t* counts,
-                   bool surr, cudaStream_t st);
+                   bool surr, bool wide, cudaStream_t st);
 void launch_coarse_lm(const ReqDev* reqs, const CoarseItem* items, int n_items, int64_t* counts,
-                      bool surr, int pairs, cudaStream_t st);
+                      bool surr, int pairs, bool wide, cudaStream_t st);
 void launch_fine(const ReqDev* reqs, const FineItem* items, int n_items, int64_t* counts, bool surr,
-                 cudaStream_t st);
+                 bool wide, cudaStream_t st);
 void launch_diag_voigt(const float* x, const float* y, float* out, int64_t n, cudaStream_t st);
 void launch_diag_owned(const ReqDev* req, int64_t n_lines, int level, int grid, int64_t first,
                        int count, uint8_t* out, cudaStream_t st);

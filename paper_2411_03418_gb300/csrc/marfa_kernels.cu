@@ -171,14 +171,6 @@ __device__ __forceinline__ int mask_lowest(uint64_t m) { return __ffsll((long lo
 __device__ __forceinline__ int mask_highest(uint32_t m) { return 31 - __clz((int)m); }
 __device__ __forceinline__ int mask_highest(uint64_t m) { return 63 - __clzll((long long)m); }
 
-// Panels of grid g (1..10) owned by a line over [base, base + nb).
-__device__ __forceinline__ uint32_t owned_mask(int g, int64_t c, int gst, bool chi, int64_t cut,
-                                               int R_w, int64_t base, int nb) {
-  uint32_t m = accept_mask<uint32_t>(g, c, gst, chi, cut, R_w, base, nb, false);
-  if (g > 1 && m) m &= ~accept_mask<uint32_t>(g - 1, c, gst, chi, cut, R_w, base, nb, true);
-  return m;
-}
-
 __device__ __forceinline__ int clamp32(int64_t v) {
   return (int)max(min(v, (int64_t)(1 << 30)), (int64_t)-(1 << 30));
 }
@@ -266,6 +258,7 @@ __device__ __forceinline__ float shape_f(int shape, float x, float y) {
     case kShapeLorentz: return 1.0f / fmaf(x, x, 1.0f);
     case kShapeDoppler: return expf(-x * x);
     case kShapeConst: return 1.0f;
+    case kShapeQuart: return fmaf(x, fmaf(x, fmaf(x, fmaf(x, 0.00390625f, 0.015625f), 0.0625f), 0.25f), 1.0f);
     default: return fmaf(x, fmaf(x, 0.0625f, 0.25f), 1.0f);  // kShapeQuad
   }
 }
@@ -498,7 +491,9 @@ __device__ __forceinline__ void comp_merge(float& s, float& c, float s2, float c
   c = (c + c2) + e;
 }
 
-template <bool COUNT, bool SURR>
+// WIDE: 0 the paper's 3-point partition, 1 the 5-point variant, 2 either, per request
+// (counting and surrogate variants).
+template <bool COUNT, bool SURR, int WIDE>
 __global__ void __launch_bounds__(kG1Warps * 32)
     k_g1(const ReqDev* __restrict__ reqs, const G1Item* __restrict__ items,
          int64_t* __restrict__ counts) {
@@ -512,6 +507,7 @@ __global__ void __launch_bounds__(kG1Warps * 32)
   __shared__ int64_t sCnt[kCountFields][kG1Warps];
   const G1Item it = items[blockIdx.x];
   const ReqDev& R = reqs[it.req];
+  const bool wide = WIDE == 2 ? R.wide != 0 : WIDE == 1;  // 5-point partition
   const bool use_mlp = SURR && R.mlp != nullptr;  // block-uniform
   if (use_mlp) mlp_load_smem(S, R.mlp);  // made visible by the first barrier below
   const int lev = it.level;
@@ -527,7 +523,8 @@ __global__ void __launch_bounds__(kG1Warps * 32)
   const LevelDev L = R.lev[lev];
   Bands bd;
   {
-    const int64_t zlo = (base << s) - cut, zhi = ((m0 + kG1Pairs) << s) + cut;
+    const int64_t Pw = wide ? (int64_t(1) << (s + 1)) : 0;  // a four-step panel may overhang the tile
+    const int64_t zlo = (base << s) - cut - Pw, zhi = ((m0 + kG1Pairs) << s) + cut + Pw;
     bd.lookup(R, L, &zlo, &zhi, 1);
   }
   // this CTA's share of the candidate lines
@@ -554,7 +551,8 @@ __global__ void __launch_bounds__(kG1Warps * 32)
       const int64_t c = __ldg(R.c + o);
       const int gst = __ldg(R.gstar + o);
       const bool chi = __ldg(R.flags + o) & 1;
-      const uint64_t msk = accept_mask<uint64_t>(1, c, gst, chi, cut, R.R_w, base, nb, false) & win;
+      // acceptance panels: two steps of grid 1, or four in the 5-point variant
+      const uint64_t msk = accept_mask_s<uint64_t>(1, c, gst, chi, cut, R.R_w, base, nb, s + wide, s) & win;
       const float amp = __ldg(R.amp + o), sx = __ldg(R.sx + o), y = __ldg(R.yv + o);
       NodeX nx;
       nx.init(X0 - c, s - 1, sx);
@@ -710,17 +708,19 @@ __global__ void __launch_bounds__(kG1Warps * 32)
 }
 
 void launch_g1(const ReqDev* reqs, const G1Item* items, int n_items, int64_t* counts, bool surr,
-               cudaStream_t st) {
+               bool wide, cudaStream_t st) {
   if (n_items <= 0) return;
   if (surr) {
     if (counts)
-      launch_surr(k_g1<true, true>, n_items, kG1Warps * 32, st, reqs, items, counts);
+      launch_surr(k_g1<true, true, 2>, n_items, kG1Warps * 32, st, reqs, items, counts);
     else
-      launch_surr(k_g1<false, true>, n_items, kG1Warps * 32, st, reqs, items, counts);
+      launch_surr(k_g1<false, true, 2>, n_items, kG1Warps * 32, st, reqs, items, counts);
   } else if (counts) {
-    k_g1<true, false><<<n_items, kG1Warps * 32, 0, st>>>(reqs, items, counts);
+    k_g1<true, false, 2><<<n_items, kG1Warps * 32, 0, st>>>(reqs, items, counts);
+  } else if (wide) {
+    k_g1<false, false, 1><<<n_items, kG1Warps * 32, 0, st>>>(reqs, items, counts);
   } else {
-    k_g1<false, false><<<n_items, kG1Warps * 32, 0, st>>>(reqs, items, counts);
+    k_g1<false, false, 0><<<n_items, kG1Warps * 32, 0, st>>>(reqs, items, counts);
   }
 }
 
@@ -732,7 +732,7 @@ void launch_g1(const ReqDev* reqs, const G1Item* items, int n_items, int64_t* co
 // over lanes and warps in a fixed order at the end.
 // Register budgets: 72 for the plain 16-pair variant (seven CTAs per SM), 128 for the
 // plain 32-pair one (four, as its 48 KB of slots allow), 168 with the surrogate.
-template <bool COUNT, bool SURR, int PAIRS>
+template <bool COUNT, bool SURR, int PAIRS, int WIDE>
 __global__ void __launch_bounds__(kLWarps * 32, SURR ? 3 : (PAIRS == 16 ? 7 : 4))
     k_coarse_lm(const ReqDev* __restrict__ reqs, const CoarseItem* __restrict__ items,
              int64_t* __restrict__ counts) {
@@ -744,6 +744,7 @@ __global__ void __launch_bounds__(kLWarps * 32, SURR ? 3 : (PAIRS == 16 ? 7 : 4)
   __shared__ int64_t sCnt[kCountFields][kLWarps];
   const CoarseItem it = items[blockIdx.x];
   const ReqDev& R = reqs[it.req];
+  const bool wide = WIDE == 2 ? R.wide != 0 : WIDE == 1;  // 5-point partition
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = it.grid;
   const int lev = it.level;
@@ -759,6 +760,7 @@ __global__ void __launch_bounds__(kLWarps * 32, SURR ? 3 : (PAIRS == 16 ? 7 : 4)
   const MT win = rmask<MT>(m_first, m_last, base, nb);
   PanelFrame fr;  // 32-bit ownership where the offsets are whole panels
   fr.init(g, base, nb, cut, R.R_w);
+  if (wide) fr.ok = false;
   for (int p = 0; p < PAIRS; ++p) {
     accL[warp][p][lane] = 0.0f;
     accM[warp][p][lane] = 0.0f;
@@ -767,16 +769,19 @@ __global__ void __launch_bounds__(kLWarps * 32, SURR ? 3 : (PAIRS == 16 ? 7 : 4)
   const LevelDev L = R.lev[lev];
   Bands bd;
   {
-    const int64_t P = int64_t(1) << s;
-    const int64_t A = (base >> 1) << (s + 1);
-    const int64_t B = (((base + nb - 1) >> 1) + 1) << (s + 1);
+    // the span of the parent grid's panels over the tile, widened by one of them
+    const int al = wide ? s + 2 : s + 1;  // parent panels: two (four) steps of grid g - 1
+    const int64_t P = int64_t(1) << (wide ? s + 2 : s);
+    const int64_t A = fl_sh(base << s, al) << al;
+    const int64_t B = (fl_sh((base + nb - 1) << s, al) + 1) << al;
     int64_t zlo[9], zhi[9];
     const int nz = make_zones(A, B, (int64_t)R.R_w * step_fx(g - 1), cut, P, R.chi_req, zlo, zhi);
     bd.lookup(R, L, zlo, zhi, nz);
   }
   const int64_t lo_off = (int64_t)lev * R.n_lines;
   const int64_t X0 = m0 << s;  // position of node 2 m0 (j = 0)
-  const int64_t xa_t = base << s, xb_t = (base + nb) << s, P_t = int64_t(1) << s;  // span of the mask's panels
+  const int64_t xa_t = base << s, xb_t = (base + nb) << s;  // span of the mask's panels
+  const int64_t P_t = int64_t(1) << (wide ? s + 2 : s);  // one parent panel (5-point: four steps of g - 1)
   const bool physical = R.shape < kShapeConst;
   const bool voigt = R.shape == kShapeVoigt;
   int64_t nev = 0, nmlp = 0, nnear = 0, nmid = 0, nsmall = 0;
@@ -813,8 +818,7 @@ __global__ void __launch_bounds__(kLWarps * 32, SURR ? 3 : (PAIRS == 16 ? 7 : 4)
           c = __ldg(R.c + lo_off + i);
           const int gst = __ldg(R.gstar + lo_off + i);
           chi = __ldg(R.flags + lo_off + i) & 1;
-          own = accept_mask<MT>(g, c, gst, chi, cut, R.R_w, base, nb, false) & win;
-          if (own) own &= ~accept_mask<MT>(g - 1, c, gst, chi, cut, R.R_w, base, nb, true);
+          own = owned_any<MT>(wide, g, c, gst, chi, cut, R.R_w, base, nb) & win;
         }
         float amp = 0.0f, y = 1.0f;
         NodeX nx;
@@ -871,8 +875,7 @@ __global__ void __launch_bounds__(kLWarps * 32, SURR ? 3 : (PAIRS == 16 ? 7 : 4)
         if (own) own &= ~accept_parent_frame<MT>(fr, pp, g, gst, chi);
       } else {
         if (owns_nothing(g, c, gst, chi, cut, xa_t, xb_t, P_t)) continue;
-        own = accept_mask<MT>(g, c, gst, chi, cut, R.R_w, base, nb, false) & win;
-        if (own) own &= ~accept_mask<MT>(g - 1, c, gst, chi, cut, R.R_w, base, nb, true);
+        own = owned_any<MT>(wide, g, c, gst, chi, cut, R.R_w, base, nb) & win;
       }
       if (!own) continue;
       const float amp = __ldg(R.amp + lo_off + i);
@@ -964,31 +967,35 @@ __global__ void __launch_bounds__(kLWarps * 32, SURR ? 3 : (PAIRS == 16 ? 7 : 4)
 }
 
 void launch_coarse_lm(const ReqDev* reqs, const CoarseItem* items, int n_items, int64_t* counts,
-                      bool surr, int pairs, cudaStream_t st) {
+                      bool surr, int pairs, bool wide, cudaStream_t st) {
   if (n_items <= 0) return;
   const int T = kLWarps * 32;
   if (pairs == 16) {
     if (surr) {
       if (counts)
-        launch_surr(k_coarse_lm<true, true, 16>, n_items, T, st, reqs, items, counts);
+        launch_surr(k_coarse_lm<true, true, 16, 2>, n_items, T, st, reqs, items, counts);
       else
-        launch_surr(k_coarse_lm<false, true, 16>, n_items, T, st, reqs, items, counts);
+        launch_surr(k_coarse_lm<false, true, 16, 2>, n_items, T, st, reqs, items, counts);
     } else if (counts) {
-      k_coarse_lm<true, false, 16><<<n_items, T, 0, st>>>(reqs, items, counts);
+      k_coarse_lm<true, false, 16, 2><<<n_items, T, 0, st>>>(reqs, items, counts);
+    } else if (wide) {
+      k_coarse_lm<false, false, 16, 1><<<n_items, T, 0, st>>>(reqs, items, counts);
     } else {
-      k_coarse_lm<false, false, 16><<<n_items, T, 0, st>>>(reqs, items, counts);
+      k_coarse_lm<false, false, 16, 0><<<n_items, T, 0, st>>>(reqs, items, counts);
     }
     return;
   }
   if (surr) {
     if (counts)
-      launch_surr(k_coarse_lm<true, true, 32>, n_items, T, st, reqs, items, counts);
+      launch_surr(k_coarse_lm<true, true, 32, 2>, n_items, T, st, reqs, items, counts);
     else
-      launch_surr(k_coarse_lm<false, true, 32>, n_items, T, st, reqs, items, counts);
+      launch_surr(k_coarse_lm<false, true, 32, 2>, n_items, T, st, reqs, items, counts);
   } else if (counts) {
-    k_coarse_lm<true, false, 32><<<n_items, T, 0, st>>>(reqs, items, counts);
+    k_coarse_lm<true, false, 32, 2><<<n_items, T, 0, st>>>(reqs, items, counts);
+  } else if (wide) {
+    k_coarse_lm<false, false, 32, 1><<<n_items, T, 0, st>>>(reqs, items, counts);
   } else {
-    k_coarse_lm<false, false, 32><<<n_items, T, 0, st>>>(reqs, items, counts);
+    k_coarse_lm<false, false, 32, 0><<<n_items, T, 0, st>>>(reqs, items, counts);
   }
 }
 
@@ -1001,7 +1008,7 @@ void launch_coarse_lm(const ReqDev* reqs, const CoarseItem* items, int n_items, 
 // buffered values of the lines owning its panels into compensated register sums.
 // At most 80 registers a thread in the plain variants (168 with the surrogate): with the
 // Voigt tables read through the read-only cache (no shared copy), six CTAs fit on an SM.
-template <bool COUNT, bool SURR>
+template <bool COUNT, bool SURR, int WIDE>
 __global__ void __launch_bounds__(kCWarps * 32, SURR ? 3 : 6)
     k_coarse(const ReqDev* __restrict__ reqs, const CoarseItem* __restrict__ items,
              int64_t* __restrict__ counts) {
@@ -1013,6 +1020,7 @@ __global__ void __launch_bounds__(kCWarps * 32, SURR ? 3 : 6)
   __shared__ int64_t sCnt[kCountFields][kCWarps];
   const CoarseItem it = items[blockIdx.x];
   const ReqDev& R = reqs[it.req];
+  const bool wide = WIDE == 2 ? R.wide != 0 : WIDE == 1;  // 5-point partition
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = it.grid;
   const int lev = it.level;
@@ -1031,19 +1039,23 @@ __global__ void __launch_bounds__(kCWarps * 32, SURR ? 3 : 6)
     const uint64_t win = rmask<uint64_t>(m_first, m_last, base, nb);
     PanelFrame fr;  // 32-bit ownership where the offsets are whole panels
     fr.init(g, base, nb, cut, R.R_w);
+    if (wide) fr.ok = false;
     const LevelDev L = R.lev[lev];
     Bands bd;
     {
-      const int64_t P = int64_t(1) << s;
-      const int64_t A = (base >> 1) << (s + 1);
-      const int64_t B = (((base + nb - 1) >> 1) + 1) << (s + 1);
+      // the span of the parent grid's panels over the tile, widened by one of them
+      const int al = wide ? s + 2 : s + 1;  // parent panels: two (four) steps of grid g - 1
+      const int64_t P = int64_t(1) << (wide ? s + 2 : s);
+      const int64_t A = fl_sh(base << s, al) << al;
+      const int64_t B = (fl_sh((base + nb - 1) << s, al) + 1) << al;
       int64_t zlo[9], zhi[9];
       const int nz = make_zones(A, B, (int64_t)R.R_w * step_fx(g - 1), cut, P, R.chi_req, zlo, zhi);
       bd.lookup(R, L, zlo, zhi, nz);
     }
     const int64_t lo_off = (int64_t)lev * R.n_lines;
     const int64_t X0 = m0 << s;  // position of node 2 m0 (j = 0)
-    const int64_t xa_t = base << s, xb_t = (base + nb) << s, P_t = int64_t(1) << s;  // span of the mask's panels
+    const int64_t xa_t = base << s, xb_t = (base + nb) << s;  // span of the mask's panels
+    const int64_t P_t = int64_t(1) << (wide ? s + 2 : s);  // one parent panel (5-point: four steps of g - 1)
     const bool physical = R.shape < kShapeConst;
     const bool voigt = R.shape == kShapeVoigt;
     const int p = lane;
@@ -1082,8 +1094,7 @@ __global__ void __launch_bounds__(kCWarps * 32, SURR ? 3 : 6)
               if (own) own &= ~accept_parent_frame<uint64_t>(fr, pp, g, gst, chi);
             }
           } else if (!owns_nothing(g, c, gst, chi, cut, xa_t, xb_t, P_t)) {
-            own = accept_mask<uint64_t>(g, c, gst, chi, cut, R.R_w, base, nb, false) & win;
-            if (own) own &= ~accept_mask<uint64_t>(g - 1, c, gst, chi, cut, R.R_w, base, nb, true);
+            own = owned_any<uint64_t>(wide, g, c, gst, chi, cut, R.R_w, base, nb) & win;
           }
         }
         const uint32_t any = __ballot_sync(0xffffffffu, own != 0);
@@ -1210,18 +1221,20 @@ __global__ void __launch_bounds__(kCWarps * 32, SURR ? 3 : 6)
 }
 
 void launch_coarse(const ReqDev* reqs, const CoarseItem* items, int n_items, int64_t* counts,
-                   bool surr, cudaStream_t st) {
+                   bool surr, bool wide, cudaStream_t st) {
   if (n_items <= 0) return;
   const int T = kCWarps * 32;
   if (surr) {
     if (counts)
-      launch_surr(k_coarse<true, true>, n_items, T, st, reqs, items, counts);
+      launch_surr(k_coarse<true, true, 2>, n_items, T, st, reqs, items, counts);
     else
-      launch_surr(k_coarse<false, true>, n_items, T, st, reqs, items, counts);
+      launch_surr(k_coarse<false, true, 2>, n_items, T, st, reqs, items, counts);
   } else if (counts) {
-    k_coarse<true, false><<<n_items, T, 0, st>>>(reqs, items, counts);
+    k_coarse<true, false, 2><<<n_items, T, 0, st>>>(reqs, items, counts);
+  } else if (wide) {
+    k_coarse<false, false, 1><<<n_items, T, 0, st>>>(reqs, items, counts);
   } else {
-    k_coarse<false, false><<<n_items, T, 0, st>>>(reqs, items, counts);
+    k_coarse<false, false, 0><<<n_items, T, 0, st>>>(reqs, items, counts);
   }
 }
 
@@ -1247,7 +1260,7 @@ struct __align__(16) FineChi {
   int on, pad;                          // chi-factor applies
 };
 
-template <bool COUNT, bool SURR>
+template <bool COUNT, bool SURR, int WIDE>
 __global__ void __launch_bounds__(kFineThreads)
     k_fine(const ReqDev* __restrict__ reqs, const FineItem* __restrict__ items,
            int64_t* __restrict__ counts) {
@@ -1263,6 +1276,7 @@ __global__ void __launch_bounds__(kFineThreads)
   __shared__ int64_t red[kCountFields][NW];
   const FineItem it = items[blockIdx.x];
   const ReqDev& R = reqs[it.req];
+  const bool wide = WIDE == 2 ? R.wide != 0 : WIDE == 1;  // 5-point partition
   const int lev = it.level;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool use_mlp = SURR && R.mlp != nullptr;  // block-uniform
@@ -1287,7 +1301,8 @@ __global__ void __launch_bounds__(kFineThreads)
     Bands bd;
     {
       int64_t zlo[9], zhi[9];
-      const int nz = make_zones(Xa, Xb, (int64_t)R.R_w * step_fx(kNGrid), cut, P10, R.chi_req, zlo, zhi);
+      const int nz = make_zones(Xa, Xb, (int64_t)R.R_w * step_fx(kNGrid), cut, wide ? P10 << 1 : P10,
+                                R.chi_req, zlo, zhi);
       bd.lookup(R, L, zlo, zhi, nz);
     }
     const int64_t pbase = kw >> 3;  // first G10 panel of the warp
@@ -1311,7 +1326,8 @@ __global__ void __launch_bounds__(kFineThreads)
         klo = (int)max(cl_sh(c - cut, kFineShift) - kw, (int64_t)wlo);
         khi = (int)min(fl_sh(c + cut, kFineShift) - kw, (int64_t)whi);
         if (klo <= khi) {
-          pm = ~accept_mask<uint32_t>(kNGrid, c, gst, chi, cut, R.R_w, pbase, 16, false) &
+          const int s10 = panel_shift(kNGrid);  // acceptance panels of grid 10: two (four) steps
+          pm = ~accept_mask_s<uint32_t>(kNGrid, c, gst, chi, cut, R.R_w, pbase, 16, s10 + wide, s10) &
                rmask<uint32_t>(klo >> 3, khi >> 3, 0, 16);
         }
       }
@@ -1424,10 +1440,44 @@ __global__ void __launch_bounds__(kFineThreads)
 #pragma unroll
     for (int g = 1; g <= kNGrid; ++g) {
       const int sh = 13 - g;  // finest nodes per panel of grid g: 2^(13-g)
-      const int64_t m = k0 >> sh;
-      const int64_t idx = m - R.m_first[g];
       const int64_t np = R.npan[g];
       const float* gp = sl + R.slot_off[g];
+      if (wide) {
+        // 5-point: the four-step panel M4 is two-step panels 2 M4, 2 M4 + 1 (m_first is
+        // even); its nodes are L, M, R of the first and M, R of the second
+        const int64_t M4 = k0 >> (sh + 1);
+        const int64_t i0 = 2 * M4 - R.m_first[g];
+        float v0 = __ldg(gp + i0), v1 = __ldg(gp + np + i0), v2 = __ldg(gp + 2 * np + i0);
+        float v3 = __ldg(gp + np + i0 + 1), v4 = __ldg(gp + 2 * np + i0 + 1);
+        if (g == 1) {  // the kG1Split partial copies of grid 1, summed in part order
+#pragma unroll
+          for (int part = 1; part < kG1Split; ++part) {
+            const float* gq = gp + 3 * np * part;
+            v0 += __ldg(gq + i0);
+            v1 += __ldg(gq + np + i0);
+            v2 += __ldg(gq + 2 * np + i0);
+            v3 += __ldg(gq + np + i0 + 1);
+            v4 += __ldg(gq + 2 * np + i0 + 1);
+          }
+        }
+        const int off0 = (int)(k0 - (M4 << (sh + 1)));
+        const float inv_h = ldexpf(1.0f, 1 - sh);
+#pragma unroll
+        for (int q = 0; q < kFinePerThread; ++q) {
+          const float t = (float)(off0 + q) * inv_h;  // position in steps of h_g, [0, 4)
+          const float d1 = t - 1.0f, d2 = t - 2.0f, d3 = t - 3.0f, d4 = t - 4.0f;
+          // quartic Lagrange weights of the nodes 0..4
+          const float w0 = (d1 * d2) * (d3 * d4) * (1.0f / 24.0f);
+          const float w1 = -(t * d2) * (d3 * d4) * (1.0f / 6.0f);
+          const float w2 = (t * d1) * (d3 * d4) * 0.25f;
+          const float w3 = -(t * d1) * (d2 * d4) * (1.0f / 6.0f);
+          const float w4 = (t * d1) * (d2 * d3) * (1.0f / 24.0f);
+          out[q] += fmaf(v0, w0, fmaf(v1, w1, fmaf(v2, w2, fmaf(v3, w3, v4 * w4))));
+        }
+        continue;
+      }
+      const int64_t m = k0 >> sh;
+      const int64_t idx = m - R.m_first[g];
       float vL = __ldg(gp + idx), vM = __ldg(gp + np + idx), vR = __ldg(gp + 2 * np + idx);
       if (g == 1) {  // the kG1Split partial copies of grid 1, summed in part order
 #pragma unroll
@@ -1477,17 +1527,19 @@ __global__ void __launch_bounds__(kFineThreads)
 }
 
 void launch_fine(const ReqDev* reqs, const FineItem* items, int n_items, int64_t* counts, bool surr,
-                 cudaStream_t st) {
+                 bool wide, cudaStream_t st) {
   if (n_items <= 0) return;
   if (surr) {
     if (counts)
-      launch_surr(k_fine<true, true>, n_items, kFineThreads, st, reqs, items, counts);
+      launch_surr(k_fine<true, true, 2>, n_items, kFineThreads, st, reqs, items, counts);
     else
-      launch_surr(k_fine<false, true>, n_items, kFineThreads, st, reqs, items, counts);
+      launch_surr(k_fine<false, true, 2>, n_items, kFineThreads, st, reqs, items, counts);
   } else if (counts) {
-    k_fine<true, false><<<n_items, kFineThreads, 0, st>>>(reqs, items, counts);
+    k_fine<true, false, 2><<<n_items, kFineThreads, 0, st>>>(reqs, items, counts);
+  } else if (wide) {
+    k_fine<false, false, 1><<<n_items, kFineThreads, 0, st>>>(reqs, items, counts);
   } else {
-    k_fine<false, false><<<n_items, kFineThreads, 0, st>>>(reqs, items, counts);
+    k_fine<false, false, 0><<<n_items, kFineThreads, 0, st>>>(reqs, items, counts);
   }
 }
 
@@ -1514,12 +1566,15 @@ __global__ void k_diag_owned(const ReqDev* __restrict__ req, int lev, int grid, 
   const bool chi = R.flags[o] & 1;
   uint8_t v;
   if (grid <= kNGrid) {
-    v = owned_mask(grid, c, gst, chi, R.cut_fx, R.R_w, first + i, 1) & 1u;
+    const int sg = panel_shift(grid);
+    v = grid == 1 ? accept_mask_s<uint32_t>(1, c, gst, chi, R.cut_fx, R.R_w, first + i, 1, sg + R.wide, sg) & 1u
+                  : owned_any<uint32_t>(R.wide, grid, c, gst, chi, R.cut_fx, R.R_w, first + i, 1) & 1u;
   } else {
     const int64_t k = first + i;
     const int64_t d = (k << kFineShift) - c;
     const bool within = (d < 0 ? -d : d) <= R.cut_fx;
-    v = within && !accept_mask<uint32_t>(kNGrid, c, gst, chi, R.cut_fx, R.R_w, k >> 3, 1, false);
+    const int s10 = panel_shift(kNGrid);
+    v = within && !accept_mask_s<uint32_t>(kNGrid, c, gst, chi, R.cut_fx, R.R_w, k >> 3, 1, s10 + R.wide, s10);
   }
   out[line * (int64_t)count + i] = v;
 }

@@ -43,21 +43,20 @@ MARFA_HD MT rmask_rel(int lo, int hi, int nb) {
   return ((MT(2) << hi) - MT(1)) & (~MT(0) << lo);
 }
 
-// Panels of grid g accepted for a line, over panels [base, base + nb). With child set,
-// the accepted panels of grid g are mapped to their two children on grid g + 1 and
-// base/nb refer to grid g + 1.
+// Panels of grid g accepted for a line: the acceptance panels are 2^s fixed-point units
+// wide (s = panel_shift(g): two steps of grid g; one more for the 5-point variant's four
+// steps), and each is mapped onto the mask bits, panels of 2^sb units (sb <= s) over
+// [base, base + nb): acceptance panel a covers bits a f .. a f + f - 1, f = 2^(s - sb).
 template <typename MT>
-MARFA_HD MT accept_mask(int g, int64_t c, int gst, bool chi, int64_t cut, int R_w, int64_t base, int nb,
-                        bool child) {
-  const int s = panel_shift(g);
-  const int64_t k = child ? 1 : 0, f = child ? 2 : 1;  // panel a of grid g -> children [2a, 2a+1]
+MARFA_HD MT accept_mask_s(int g, int64_t c, int gst, bool chi, int64_t cut, int R_w, int64_t base, int nb,
+                          int s, int sb) {
+  const int64_t f = int64_t(1) << (s - sb), k = f - 1;
   int64_t s_lo = cl_sh(c - cut, s), s_hi = fl_sh(c + cut, s) - 1;
   MT m = rmask<MT>(s_lo * f, s_hi * f + k, base, nb);
   if (!m) return MT(0);
   // the span covered by the mask bits, in fixed point
-  const int sb = child ? s - 1 : s;
   const int64_t xa = base << sb, xb = (base + nb) << sb;
-  const int64_t P = int64_t(1) << s;  // panel width of grid g: a gap or kink panel lies
+  const int64_t P = int64_t(1) << s;  // acceptance panel width: a gap or kink panel lies
                                       // within one panel width of c +- R or c +- B
   if (gst > g) {
     const int64_t R = (int64_t)R_w * step_fx(g);
@@ -79,6 +78,28 @@ MARFA_HD MT accept_mask(int g, int64_t c, int gst, bool chi, int64_t cut, int R_
         m &= ~rmask<MT>((cl_sh(s2, s) - 1) * f, fl_sh(s2, s) * f + k, base, nb);
     }
   }
+  return m;
+}
+
+// Panels of grid g accepted for a line, over panels [base, base + nb). With child set,
+// the accepted panels of grid g are mapped to their two children on grid g + 1 and
+// base/nb refer to grid g + 1.
+template <typename MT>
+MARFA_HD MT accept_mask(int g, int64_t c, int gst, bool chi, int64_t cut, int R_w, int64_t base, int nb,
+                        bool child) {
+  const int s = panel_shift(g);
+  return accept_mask_s<MT>(g, c, gst, chi, cut, R_w, base, nb, s, child ? s - 1 : s);
+}
+
+// Panels of grid g (2..10) a line owns over the two-step panels [base, base + nb): the
+// panels grid g accepts and its parent grid does not; wide selects the 5-point variant
+// (acceptance on four-step panels). One code path for both: the shifts are arguments.
+template <typename MT>
+MARFA_HD MT owned_any(bool wide, int g, int64_t c, int gst, bool chi, int64_t cut, int R_w, int64_t base,
+                      int nb) {
+  const int sb = panel_shift(g), w = wide ? 1 : 0;
+  MT m = accept_mask_s<MT>(g, c, gst, chi, cut, R_w, base, nb, sb + w, sb);
+  if (m) m &= ~accept_mask_s<MT>(g - 1, c, gst, chi, cut, R_w, base, nb, sb + 1 + w, sb);
   return m;
 }
 

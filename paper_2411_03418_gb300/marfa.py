@@ -19,7 +19,7 @@ LINE_DTYPE = np.dtype([("nu0", "<f8"), ("S296", "<f4"), ("gamma_air", "<f4"), ("
 SPECIES_DTYPE = np.dtype([("mol_iso", "<i4"), ("chi_enabled", "<i4"), ("mass_amu", "<f8"), ("q_exp", "<f8")])
 LEVEL_DTYPE = np.dtype([("T_K", "<f8"), ("p_atm", "<f8")])
 
-SHAPES = {"lorentz": 0, "voigt": 1, "doppler": 2, "const": 100, "quad": 101}
+SHAPES = {"lorentz": 0, "voigt": 1, "doppler": 2, "const": 100, "quad": 101, "quart": 102}
 CHI = {"none": 0, "tonkov": 1}
 UNITS = {"sigma": 0, "k_cm1": 1, "k_km1": 2}
 ERRORS = {-1: "MARFA_E_INVAL", -2: "MARFA_E_NOMEM", -3: "MARFA_E_CUDA", -4: "MARFA_E_IO",
@@ -35,7 +35,8 @@ class MarfaError(RuntimeError):
 class marfa_request_t(C.Structure):
     _fields_ = [("nu_lo", C.c_double), ("nu_hi", C.c_double), ("cutoff", C.c_double),
                 ("shape", C.c_int32), ("chi", C.c_int32), ("units", C.c_int32),
-                ("surrogate", C.c_int32), ("R_w", C.c_int32), ("R_c", C.c_int32)]
+                ("surrogate", C.c_int32), ("R_w", C.c_int32), ("R_c", C.c_int32),
+                ("stencil", C.c_int32)]
 
 
 _LIB = None
@@ -160,9 +161,9 @@ def marfa_num_points(nu_lo: float, nu_hi: float) -> int:
 
 
 def make_request(nu_lo, nu_hi, cutoff, shape="voigt", chi="none", units="k_cm1", surrogate=0,
-                 R_w=8, R_c=8) -> marfa_request_t:
+                 R_w=8, R_c=8, stencil=3) -> marfa_request_t:
     return marfa_request_t(float(nu_lo), float(nu_hi), float(cutoff), SHAPES[shape], CHI[chi],
-                           UNITS[units], int(surrogate), int(R_w), int(R_c))
+                           UNITS[units], int(surrogate), int(R_w), int(R_c), int(stencil))
 
 
 def make_levels(T, p) -> np.ndarray:
@@ -396,7 +397,7 @@ def marfa_diag_kernel_timing(enable: bool):
 # ------------------------------------------------------------------ workload marshalling
 def request_of(wl) -> marfa_request_t:
     return make_request(wl.nu_lo, wl.nu_hi, wl.cutoff, wl.shape, wl.chi, wl.units, wl.surrogate,
-                        wl.R_w, wl.R_c)
+                        wl.R_w, wl.R_c, getattr(wl, "stencil", 3))
 
 
 def levels_of(wl) -> np.ndarray:

@@ -38,7 +38,7 @@ def test_header_and_library_exports_agree(M):
 def test_struct_layouts(M):
     assert M.LINE_DTYPE.itemsize == 36
     assert M.SPECIES_DTYPE.itemsize == 24
-    assert ctypes.sizeof(M.marfa_request_t) == 48
+    assert ctypes.sizeof(M.marfa_request_t) == 56
 
 
 def test_num_points_matches_oracle(M):

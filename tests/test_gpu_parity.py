@@ -194,6 +194,28 @@ def test_absorption_parity(M, kw):
         assert_parity(got[lev], O.eleven_grid(wl, lev), what=f"level {lev}")
 
 
+# the 5-point variant (quartic interpolation on panels of four steps)
+PARITY_CASES_5 = [
+    dict(seed=71, n=400, lo=1500.0, hi=1504.7, cut=25.0, T=(296.0,), p=(1.0,)),
+    dict(seed=72, n=600, lo=2000.0, hi=2003.01, cut=125.0, T=(735.0, 400.0, 170.0), p=(92.0, 0.3, 1e-5),
+         chi="tonkov", chi_species=1),
+    dict(seed=73, n=300, lo=700.37, hi=701.9, cut=10.0, T=(250.0,), p=(0.02,), shape="lorentz"),
+    dict(seed=74, n=300, lo=1000.0, hi=1002.0, cut=20.0, T=(300.0, 200.0), p=(2.0, 1e-4), shape="quart",
+         chi="tonkov", chi_species=1),
+    dict(seed=75, n=250, lo=999.13, hi=1001.0, cut=160.0, T=(500.0,), p=(3.0,), shape="const", chi="tonkov",
+         chi_species=1, R_w=4, R_c=16),
+]
+
+
+@pytest.mark.parametrize("kw", PARITY_CASES_5)
+def test_absorption_parity_five_point(M, kw):
+    kw = dict(kw)
+    wl = tiny_workload(kw.pop("seed"), kw.pop("n"), kw.pop("lo"), kw.pop("hi"), kw.pop("cut"), stencil=5, **kw)
+    got = run_gpu(M, wl)
+    for lev in range(wl.n_levels):
+        assert_parity(got[lev], O.eleven_grid(wl, lev), what=f"level {lev}")
+
+
 def test_host_output_equals_device_output(M):
     wl = tiny_workload(61, 300, 2000.0, 2001.5, 25.0, T=(296.0, 200.0), p=(1.0, 1e-3))
     a = run_gpu(M, wl, device_out=True)

@@ -78,6 +78,31 @@ def test_plan_matches_batch_and_replays(M):
     M.marfa_plan_destroy(plan)
 
 
+def test_five_point_plan_matches_batch(M):
+    """The 5-point variant through a captured plan equals marfa_absorption_batch."""
+    import torch
+    wls = [w.with_(stencil=5) for w in SMALL]
+    plan, ref, outs = _batch_and_plan(M, wls, autotune=False)
+    M.marfa_plan_execute(plan)
+    torch.cuda.synchronize()
+    for r, o in zip(ref, outs):
+        assert np.array_equal(o.cpu().numpy(), r)
+    M.marfa_plan_destroy(plan)
+
+
+def test_mixed_stencils_rejected(M):
+    """The plain kernels are compiled for one partition: a call mixing 3- and 5-point
+    requests is refused."""
+    import torch
+    wls = [SMALL[0], SMALL[1].with_(stencil=5)]
+    lines = [M.marfa_prepare_lines(w.lines, w.species) for w in wls]
+    outs = [torch.empty((w.n_levels, M.marfa_num_points(w.nu_lo, w.nu_hi)), dtype=torch.float32, device="cuda")
+            for w in wls]
+    with pytest.raises(M.MarfaError, match="stencil"):
+        M.marfa_absorption_batch(lines, [M.levels_of(w) for w in wls], [w.vmr for w in wls],
+                                 [M.request_of(w) for w in wls], outs)
+
+
 def test_autotuned_plan_parity(M):
     import torch
     plan, ref, outs = _batch_and_plan(M, SMALL, autotune=True)
