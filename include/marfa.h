@@ -218,6 +218,24 @@ int marfa_write_pt_table(const char* dir, int32_t level_number, double nu_lo,
                          double nu_hi, const float* k, int64_t npts);
 
 /*
+ * Appendix B: line records from the text of a HITRAN .par file (the conversion the
+ * paper's utility performs before a run). Records are the 160-column fixed-width lines
+ * of the HITRAN 2004+ format; the fields used are molecule (columns 1-2), isotopologue
+ * (3: '1'..'9', '0' for 10, 'A', 'B', ... for 11, 12, ...), nu (4-15), S (16-25),
+ * gamma_air (36-40), gamma_self (41-45), E'' (46-55), n_air (56-59) and delta_air
+ * (60-67); the rest of a record is not read. jointMolIso, whose layout the paper leaves
+ * to its documentation, is 100 * molecule + isotopologue.
+ *   text, len : host, the file contents; records end with '\n' (a '\r' before it is
+ *               dropped); blank lines are skipped; each record needs its first 67 columns;
+ *   out, cap  : host, room for cap records (out may be NULL when cap is 0: count only);
+ *   n_out     : receives the number of records in text (also when cap is too small).
+ * Records keep the file's order. Errors: MARFA_E_INVAL for a malformed or short record
+ * (marfa_last_error names its line) and when cap is smaller than the record count
+ * (nothing is written then).
+ */
+int marfa_read_par(const char* text, int64_t len, marfa_line_t* out, int64_t cap, int64_t* n_out);
+
+/*
  * marfa_absorption without any device allocation, for callers that cannot allocate
  * device memory: a host model that has given all free device memory to its own pool
  * (so cudaMalloc would fail or fragment it), or a pipeline that must not let an

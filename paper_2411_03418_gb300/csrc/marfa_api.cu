@@ -8,6 +8,7 @@
 #include <unistd.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cerrno>
 #include <cmath>
 #include <cstdarg>
@@ -1124,6 +1125,77 @@ extern "C" int marfa_plan_info(const marfa_plan_t* X, int32_t* variant, float* t
 }
 
 // ------------------------------------------------------------------ PT-table (Appendix A)
+// One fixed-width numeric field of a .par record: columns [c0, c0 + w) (0-based), blank-
+// padded; false when it is empty or not a number.
+static bool par_field(const char* rec, int c0, int w, double* v) {
+  char buf[32];
+  int n = 0;
+  for (int i = 0; i < w; ++i) {
+    const char ch = rec[c0 + i];
+    if (ch != ' ') buf[n++] = ch;
+  }
+  buf[n] = 0;
+  if (n == 0) return false;
+  char* end = nullptr;
+  *v = std::strtod(buf, &end);
+  return end == buf + n && std::isfinite(*v);
+}
+
+extern "C" int marfa_read_par(const char* text, int64_t len, marfa_line_t* out, int64_t cap,
+                              int64_t* n_out) {
+  if (!text || len < 0 || !n_out || cap < 0 || (cap > 0 && !out))
+    return fail(MARFA_E_INVAL, "bad arguments");
+  // pass 1 counts and checks the records, pass 2 writes them
+  for (int pass = 0; pass < 2; ++pass) {
+    int64_t n = 0, line_no = 0;
+    for (int64_t pos = 0; pos < len;) {
+      int64_t end = pos;
+      while (end < len && text[end] != '\n') ++end;
+      const int64_t next = end + 1;
+      int64_t e = end;
+      if (e > pos && text[e - 1] == '\r') --e;
+      ++line_no;
+      bool blank = true;
+      for (int64_t i = pos; i < e && blank; ++i) blank = text[i] == ' ' || text[i] == '\t';
+      if (!blank) {
+        if (e - pos < 67) return fail(MARFA_E_INVAL, "line %lld: shorter than 67 columns", (long long)line_no);
+        const char* rec = text + pos;
+        double mol, nu, S, ga, gs, E, na, da;
+        const char ic = rec[2];
+        int iso = -1;
+        if (ic >= '1' && ic <= '9') iso = ic - '0';
+        else if (ic == '0') iso = 10;
+        else if (ic >= 'A' && ic <= 'Z') iso = 11 + (ic - 'A');
+        if (!par_field(rec, 0, 2, &mol) || mol < 1 || mol > 999 || mol != std::floor(mol) || iso < 0 ||
+            !par_field(rec, 3, 12, &nu) || !par_field(rec, 15, 10, &S) || !par_field(rec, 35, 5, &ga) ||
+            !par_field(rec, 40, 5, &gs) || !par_field(rec, 45, 10, &E) || !par_field(rec, 55, 4, &na) ||
+            !par_field(rec, 59, 8, &da))
+          return fail(MARFA_E_INVAL, "line %lld: malformed .par record", (long long)line_no);
+        if (pass == 1) {
+          marfa_line_t& L = out[n];
+          L.nu0 = nu;
+          L.S296 = (float)S;
+          L.gamma_air = (float)ga;
+          L.gamma_self = (float)gs;
+          L.E_lower = (float)E;
+          L.n_air = (float)na;
+          L.mol_iso = 100 * (int32_t)mol + iso;
+          L.delta_air = (float)da;
+        }
+        ++n;
+      }
+      pos = next;
+    }
+    if (pass == 0) {
+      *n_out = n;
+      if (cap == 0 && !out) return MARFA_OK;
+      if (cap < n) return fail(MARFA_E_INVAL, "room for %lld records, the text holds %lld", (long long)cap,
+                               (long long)n);
+    }
+  }
+  return MARFA_OK;
+}
+
 extern "C" int marfa_write_pt_table(const char* dir, int32_t level_number, double nu_lo,
                                     double nu_hi, const float* k, int64_t npts) {
   const int64_t NT = 20481;

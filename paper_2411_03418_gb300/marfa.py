@@ -46,7 +46,7 @@ EXPORTS = ["marfa_prepare_lines", "marfa_free_lines", "marfa_num_points", "marfa
            "marfa_diag_kernel_timing", "marfa_absorption_noalloc", "marfa_mlp_loss_grad",
            "marfa_mlp_train", "marfa_surrogate_load", "marfa_surrogate_unload", "marfa_surrogate_eval",
            "marfa_diag_absorption_counted_surrogate", "marfa_plan_create", "marfa_plan_execute",
-           "marfa_plan_info", "marfa_plan_destroy", "marfa_diag_absorption_counts"]
+           "marfa_plan_info", "marfa_plan_destroy", "marfa_diag_absorption_counts", "marfa_read_par"]
 
 MLP_PARAMS = 8577
 MLP_MAX_BATCH = 65536
@@ -79,6 +79,7 @@ def load(path: str | None = None):
         "marfa_absorption": (C.c_int, [vp, vp, vp, i32, vp, vp, vp]),
         "marfa_absorption_batch": (C.c_int, [i32, vp, vp, vp, vp, vp, vp, vp]),
         "marfa_write_pt_table": (C.c_int, [C.c_char_p, i32, dbl, dbl, vp, i64]),
+        "marfa_read_par": (C.c_int, [C.c_char_p, i64, vp, i64, C.POINTER(C.c_int64)]),
         "marfa_last_error": (C.c_char_p, []),
         "marfa_diag_voigt": (C.c_int, [vp, vp, vp, i64]),
         "marfa_diag_level_lines": (C.c_int, [vp, vp, vp, i32, vp, vp, vp, vp]),
@@ -258,6 +259,17 @@ def marfa_plan_destroy(plan: Plan) -> None:
     if plan.handle:
         load().marfa_plan_destroy(plan.handle)
         plan.handle = None
+
+
+def marfa_read_par(text: bytes) -> np.ndarray:
+    """Appendix B records (LINE_DTYPE) from the text of a HITRAN .par file."""
+    lib = load()
+    n = C.c_int64(0)
+    _check(lib.marfa_read_par(text, len(text), None, 0, C.byref(n)))
+    out = np.zeros(n.value, dtype=LINE_DTYPE)
+    if n.value:
+        _check(lib.marfa_read_par(text, len(text), _ptr(out), n.value, C.byref(n)))
+    return out
 
 
 def marfa_write_pt_table(directory: str, level_number: int, nu_lo: float, nu_hi: float, k: np.ndarray) -> None:
