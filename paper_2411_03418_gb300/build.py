@@ -20,9 +20,9 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmarfa.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["marfa_api.cu", "marfa_kernels.cu", "marfa_mlp.cu"]
-DEPS = SOURCES + ["marfa_internal.cuh", "mlp.cuh", "voigt.cuh", "voigt_tables.inc"]
+DEPS = SOURCES + ["marfa_internal.cuh", "mlp.cuh", "ownership.cuh", "voigt.cuh", "voigt_tables.inc"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off", "-I", INCLUDE]
+FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off,-pthread", "-I", INCLUDE]
 
 
 def _nvcc() -> str:
@@ -65,7 +65,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with ThreadPoolExecutor(len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + ".tmp"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
+    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")

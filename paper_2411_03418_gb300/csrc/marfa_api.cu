@@ -8,6 +8,7 @@
 #include <unistd.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <cerrno>
 #include <cmath>
@@ -15,10 +16,11 @@
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <string>
-#include <unordered_map>
+#include <thread>
 #include <vector>
 
 #include "../../include/marfa.h"
@@ -162,53 +164,194 @@ extern "C" void marfa_free_lines(marfa_lines_t* L) {
   delete L;
 }
 
+// ---------------------------------------------------------------- host line preparation
+// The host work of marfa_prepare_lines (validation, fixed-point keys, the stable sort by
+// nu0, the sorted arrays and the bucket index) runs over contiguous chunks on up to
+// kHostThreads threads; every result, errors included, is independent of their number.
+constexpr int kHostThreads = 16;
+
+static int host_threads(int64_t work, int64_t min_per_thread) {
+  const unsigned hc = std::thread::hardware_concurrency();
+  int64_t nt = std::min<int64_t>(hc ? (int64_t)hc : 1, kHostThreads);
+  nt = std::min<int64_t>(nt, std::max<int64_t>(1, work / min_per_thread));
+  return (int)nt;
+}
+
+// f(lo, hi, t) on the nt contiguous chunks of [0, n), chunk t on thread t; chunk 0, and any
+// chunk whose thread cannot be started, runs on the calling thread. f must not throw.
+template <class F>
+static void par_chunks(int nt, int64_t n, const F& f) {
+  std::vector<std::thread> th;
+  try {
+    th.reserve(nt);
+  } catch (...) {
+  }
+  for (int t = 1; t < nt; ++t) {
+    const int64_t lo = n * t / nt, hi = n * (t + 1) / nt;
+    bool started = false;
+    try {
+      th.emplace_back([&f, lo, hi, t] { f(lo, hi, t); });
+      started = true;
+    } catch (...) {
+    }
+    if (!started) f(lo, hi, t);
+  }
+  f(0, n / nt, 0);
+  for (auto& x : th) x.join();
+}
+
+// mol_iso -> species code: open addressing over a power-of-two table (read-only once built,
+// so the threads share it)
+struct SpeciesIndex {
+  std::vector<int32_t> iso;
+  std::vector<int16_t> code;  // -1 = empty slot
+  int lg = 0;
+  uint32_t slot(int32_t m) const { return ((uint32_t)m * 2654435761u) >> (32 - lg); }
+  // returns false if m is already present
+  bool insert(int32_t m, int16_t c) {
+    const uint32_t mask = (1u << lg) - 1;
+    for (uint32_t h = slot(m);; h = (h + 1) & mask) {
+      if (code[h] < 0) {
+        iso[h] = m;
+        code[h] = c;
+        return true;
+      }
+      if (iso[h] == m) return false;
+    }
+  }
+  int find(int32_t m) const {
+    const uint32_t mask = (1u << lg) - 1;
+    for (uint32_t h = slot(m);; h = (h + 1) & mask) {
+      if (code[h] < 0) return -1;
+      if (iso[h] == m) return code[h];
+    }
+  }
+  void init(int n_sp) {
+    lg = 2;
+    while ((1 << lg) < 2 * n_sp) ++lg;
+    iso.assign((size_t)1 << lg, 0);
+    code.assign((size_t)1 << lg, (int16_t)-1);
+  }
+};
+
 static int64_t rint_fix(double v) { return (int64_t)std::nearbyint(v * kFix); }
 
-// order = the positions of the lines stably sorted by nu0: one counting-sort pass on the
-// leading bits of the fixed-point keys rint(nu0 2^43) (monotone in nu0; about one line
-// per bucket), then each bucket stably sorted by nu0 itself (insertion sort; a library
-// stable sort for the rare crowded bucket).
-static void sort_by_nu0(const marfa_line_t* lines, int64_t n, std::vector<int64_t>& order) {
-  std::vector<int64_t> key(n);
+// Sorts idx[0..m) (line indices in input order, fixed-point keys key[]) stably by nu0: a
+// counting pass on the leading bits of the keys, which are monotone in nu0 (about one line
+// per bucket), then each bucket stably by nu0 itself (insertion sort; a library stable sort
+// for the rare crowded bucket). tmp and start are scratch.
+static void sort_run(const marfa_line_t* lines, const int64_t* key, int64_t* idx, int64_t m,
+                     std::vector<int64_t>& tmp, std::vector<int64_t>& start) {
+  auto less = [&](int64_t x, int64_t y) { return lines[x].nu0 < lines[y].nu0; };
+  auto insertion = [&](int64_t* a, int64_t len) {
+    for (int64_t i = 1; i < len; ++i) {
+      const int64_t v = a[i];
+      int64_t j = i - 1;
+      while (j >= 0 && less(v, a[j])) {
+        a[j + 1] = a[j];
+        --j;
+      }
+      a[j + 1] = v;
+    }
+  };
+  if (m <= 32) {
+    insertion(idx, m);
+    return;
+  }
   int64_t kmin = INT64_MAX, kmax = INT64_MIN;
-  for (int64_t i = 0; i < n; ++i) {
-    key[i] = rint_fix(lines[i].nu0);
-    kmin = std::min(kmin, key[i]);
-    kmax = std::max(kmax, key[i]);
+  for (int64_t i = 0; i < m; ++i) {
+    kmin = std::min(kmin, key[idx[i]]);
+    kmax = std::max(kmax, key[idx[i]]);
   }
   const uint64_t span = (uint64_t)(kmax - kmin);
   int bits = 0;
   while (bits < 64 && (span >> bits)) ++bits;
   int kb = 1;
-  while (kb < 24 && ((int64_t)1 << kb) < n) ++kb;
+  while (kb < 24 && ((int64_t)1 << kb) < m) ++kb;
   const int shift = bits > kb ? bits - kb : 0;
   const int64_t nbk = (int64_t)(span >> shift) + 1;
-  std::vector<int64_t> start(nbk + 1, 0);
-  for (int64_t i = 0; i < n; ++i) ++start[((uint64_t)(key[i] - kmin) >> shift) + 1];
+  start.assign(nbk + 1, 0);
+  tmp.resize(m);
+  for (int64_t i = 0; i < m; ++i) ++start[((uint64_t)(key[idx[i]] - kmin) >> shift) + 1];
   for (int64_t b = 0; b < nbk; ++b) start[b + 1] += start[b];
-  {
-    std::vector<int64_t> pos(start.begin(), start.end() - 1);
-    for (int64_t i = 0; i < n; ++i) order[pos[(uint64_t)(key[i] - kmin) >> shift]++] = i;
-  }
-  auto less = [&](int64_t x, int64_t y) { return lines[x].nu0 < lines[y].nu0; };
+  for (int64_t i = 0; i < m; ++i) tmp[start[(uint64_t)(key[idx[i]] - kmin) >> shift]++] = idx[i];
+  // start[b] now holds the end of bucket b
+  int64_t a0 = 0;
   for (int64_t b = 0; b < nbk; ++b) {
-    const int64_t a0 = start[b], a1 = start[b + 1];
-    if (a1 - a0 < 2) continue;
-    if (a1 - a0 > 32) {
-      std::stable_sort(order.begin() + a0, order.begin() + a1, less);
-      continue;
-    }
-    for (int64_t i = a0 + 1; i < a1; ++i) {  // stable insertion sort
-      const int64_t v = order[i];
-      int64_t j = i - 1;
-      while (j >= a0 && less(v, order[j])) {
-        order[j + 1] = order[j];
-        --j;
-      }
-      order[j + 1] = v;
+    const int64_t a1 = start[b];
+    if (a1 - a0 > 32)
+      std::stable_sort(tmp.begin() + a0, tmp.begin() + a1, less);
+    else if (a1 - a0 > 1)
+      insertion(tmp.data() + a0, a1 - a0);
+    a0 = a1;
+  }
+  std::copy(tmp.begin(), tmp.begin() + m, idx);
+}
+
+// order = the positions of the lines stably sorted by nu0 (what std::stable_sort gives):
+// a counting pass on the leading bits of key - kmin, each thread over its chunk of the input
+// in order, splits the lines into coarse buckets; the threads then take the coarse buckets
+// one at a time and sort each with sort_run. Returns false if scratch memory ran out.
+static bool sort_by_nu0(const marfa_line_t* lines, const int64_t* key, int64_t n, int64_t kmin,
+                        int64_t kmax, int64_t* order) {
+  const uint64_t span = (uint64_t)(kmax - kmin);
+  int bits = 0;
+  while (bits < 64 && (span >> bits)) ++bits;
+  int cb = 1;
+  while (cb < 12 && ((int64_t)64 << cb) < n) ++cb;
+  const int shift = bits > cb ? bits - cb : 0;
+  const int64_t C = (int64_t)(span >> shift) + 1;
+  const int nt = host_threads(n, 16384);
+  std::vector<int64_t> hist;
+  try {
+    hist.assign((size_t)nt * C, 0);
+  } catch (...) {
+    return false;
+  }
+  auto coarse = [&](int64_t i) { return (int64_t)((uint64_t)(key[i] - kmin) >> shift); };
+  par_chunks(nt, n, [&](int64_t lo, int64_t hi, int t) {
+    int64_t* h = hist.data() + (size_t)t * C;
+    for (int64_t i = lo; i < hi; ++i) ++h[coarse(i)];
+  });
+  std::vector<int64_t> bstart(C + 1);
+  int64_t run = 0;
+  for (int64_t c = 0; c < C; ++c) {
+    bstart[c] = run;
+    for (int t = 0; t < nt; ++t) {
+      const int64_t k = hist[(size_t)t * C + c];
+      hist[(size_t)t * C + c] = run;
+      run += k;
     }
   }
+  bstart[C] = run;
+  par_chunks(nt, n, [&](int64_t lo, int64_t hi, int t) {
+    int64_t* pos = hist.data() + (size_t)t * C;
+    for (int64_t i = lo; i < hi; ++i) order[pos[coarse(i)]++] = i;
+  });
+  std::atomic<int64_t> next{0};
+  std::atomic<bool> oom{false};
+  par_chunks(nt, nt, [&](int64_t, int64_t, int) {
+    try {
+      std::vector<int64_t> tmp, start;
+      for (int64_t c; (c = next.fetch_add(1)) < C;)
+        if (bstart[c + 1] - bstart[c] > 1)
+          sort_run(lines, key, order + bstart[c], bstart[c + 1] - bstart[c], tmp, start);
+    } catch (...) {
+      oom = true;
+    }
+  });
+  return !oom;
 }
+
+// what the validation of one chunk of lines found
+struct ChunkScan {
+  int64_t bad = INT64_MAX;  // first invalid line of the chunk
+  int why = 0;              // 1 nu0 out of range, 2 unknown species, 3 non-finite parameter
+  int32_t iso = 0;          // the unknown species
+  bool sorted = true;       // the chunk is ordered by nu0
+  int64_t kmin = INT64_MAX, kmax = INT64_MIN;
+  double dmin = 1e300, dmax = -1e300;
+};
 
 extern "C" int marfa_prepare_lines(const marfa_line_t* lines, int64_t n, const marfa_species_t* sp,
                                    int32_t n_sp, marfa_lines_t** out) {
@@ -217,48 +360,90 @@ extern "C" int marfa_prepare_lines(const marfa_line_t* lines, int64_t n, const m
   if (!lines || n < 1) return fail(MARFA_E_INVAL, "need at least one line");
   if (n > (int64_t)1 << 31) return fail(MARFA_E_INVAL, "at most 2^31 lines");
   if (!sp || n_sp < 1 || n_sp > 32767) return fail(MARFA_E_INVAL, "need 1..32767 species");
-  std::unordered_map<int32_t, int> code;
+  SpeciesIndex code;
+  std::vector<int16_t> code_of;
+  std::vector<int64_t> keyin, order;
+  try {
+    code.init(n_sp);
+    code_of.resize(n);
+    keyin.resize(n);
+  } catch (...) {
+    return fail(MARFA_E_NOMEM, "host allocation failed");
+  }
   for (int s = 0; s < n_sp; ++s) {
-    if (code.count(sp[s].mol_iso)) return fail(MARFA_E_INVAL, "duplicate species %d", sp[s].mol_iso);
+    if (!code.insert(sp[s].mol_iso, (int16_t)s)) return fail(MARFA_E_INVAL, "duplicate species %d", sp[s].mol_iso);
     if (!(sp[s].mass_amu > 0) || !std::isfinite(sp[s].mass_amu) || !std::isfinite(sp[s].q_exp))
       return fail(MARFA_E_INVAL, "species %d: mass must be > 0 and q finite", sp[s].mol_iso);
-    code[sp[s].mol_iso] = s;
   }
-  // validate, resolve species codes (looked up once per run of equal species) and check
-  // whether the lines already come ordered by nu0 (line lists usually do)
-  std::vector<int16_t> code_of(n);
-  bool sorted = true;
-  int32_t last_iso = 0;
-  int last_code = -1;
-  for (int64_t i = 0; i < n; ++i) {
-    const marfa_line_t& l = lines[i];
-    if (!std::isfinite(l.nu0) || l.nu0 < 0 || l.nu0 > 1e5)
-      return fail(MARFA_E_INVAL, "line %lld: nu0 must be in [0, 1e5]", (long long)i);
-    if (last_code < 0 || l.mol_iso != last_iso) {
-      const auto it = code.find(l.mol_iso);
-      if (it == code.end()) return fail(MARFA_E_INVAL, "line %lld: unknown species %d", (long long)i, l.mol_iso);
-      last_iso = l.mol_iso;
-      last_code = it->second;
+  // validate, resolve species codes (looked up once per run of equal species), take the
+  // fixed-point keys and check whether the lines already come ordered by nu0 (line lists
+  // usually do); each chunk stops at its first invalid line, and the first over all chunks
+  // is the one reported
+  const int nt = host_threads(n, 8192);
+  std::vector<ChunkScan> scan(nt);
+  par_chunks(nt, n, [&](int64_t lo, int64_t hi, int t) {
+    ChunkScan& S = scan[t];
+    int32_t last_iso = 0;
+    int last_code = -1;
+    for (int64_t i = lo; i < hi; ++i) {
+      const marfa_line_t& l = lines[i];
+      if (!std::isfinite(l.nu0) || l.nu0 < 0 || l.nu0 > 1e5) {
+        S.bad = i, S.why = 1;
+        return;
+      }
+      if (last_code < 0 || l.mol_iso != last_iso) {
+        last_code = code.find(l.mol_iso);
+        if (last_code < 0) {
+          S.bad = i, S.why = 2, S.iso = l.mol_iso;
+          return;
+        }
+        last_iso = l.mol_iso;
+      }
+      code_of[i] = (int16_t)last_code;
+      if (!std::isfinite(l.S296) || !std::isfinite(l.gamma_air) || !std::isfinite(l.gamma_self) ||
+          !std::isfinite(l.E_lower) || !std::isfinite(l.n_air) || !std::isfinite(l.delta_air)) {
+        S.bad = i, S.why = 3;
+        return;
+      }
+      if (i > 0 && l.nu0 < lines[i - 1].nu0) S.sorted = false;
+      const int64_t k = rint_fix(l.nu0);
+      keyin[i] = k;
+      S.kmin = std::min(S.kmin, k);
+      S.kmax = std::max(S.kmax, k);
+      S.dmin = std::min(S.dmin, (double)l.delta_air);
+      S.dmax = std::max(S.dmax, (double)l.delta_air);
     }
-    code_of[i] = (int16_t)last_code;
-    if (!std::isfinite(l.S296) || !std::isfinite(l.gamma_air) || !std::isfinite(l.gamma_self) ||
-        !std::isfinite(l.E_lower) || !std::isfinite(l.n_air) || !std::isfinite(l.delta_air))
-      return fail(MARFA_E_INVAL, "line %lld: non-finite parameter", (long long)i);
-    if (i > 0 && l.nu0 < lines[i - 1].nu0) sorted = false;
+  });
+  bool sorted = true;
+  int64_t key_first = INT64_MAX, key_last = INT64_MIN;
+  double dmin = 1e300, dmax = -1e300;
+  for (const ChunkScan& S : scan) {
+    if (S.why == 1) return fail(MARFA_E_INVAL, "line %lld: nu0 must be in [0, 1e5]", (long long)S.bad);
+    if (S.why == 2) return fail(MARFA_E_INVAL, "line %lld: unknown species %d", (long long)S.bad, S.iso);
+    if (S.why == 3) return fail(MARFA_E_INVAL, "line %lld: non-finite parameter", (long long)S.bad);
+    sorted = sorted && S.sorted;
+    key_first = std::min(key_first, S.kmin);
+    key_last = std::max(key_last, S.kmax);
+    dmin = std::min(dmin, S.dmin);
+    dmax = std::max(dmax, S.dmax);
   }
-  std::vector<int64_t> order(n);
-  for (int64_t i = 0; i < n; ++i) order[i] = i;
-  if (!sorted) sort_by_nu0(lines, n, order);
+  if (!sorted) {
+    try {
+      order.resize(n);
+    } catch (...) {
+      return fail(MARFA_E_NOMEM, "host allocation failed");
+    }
+    if (!sort_by_nu0(lines, keyin.data(), n, key_first, key_last, order.data()))
+      return fail(MARFA_E_NOMEM, "host allocation failed");
+  }
+  auto src = [&](int64_t j) { return sorted ? j : order[j]; };
 
   marfa_lines_t* L = new (std::nothrow) marfa_lines_t();
   if (!L) return fail(MARFA_E_NOMEM, "host allocation failed");
   cudaGetDevice(&L->device);
   L->n = n;
-  L->species.assign(sp, sp + n_sp);
-  L->perm.assign(n, 0);
   // bucket index over the sorted keys: about one line per two buckets on average, at
   // most 2^26 buckets
-  const int64_t key_first = rint_fix(lines[order[0]].nu0), key_last = rint_fix(lines[order[n - 1]].nu0);
   const int64_t span = std::max<int64_t>(key_last - key_first, 1);
   int bs = 20;
   while (bs < 50 && (((int64_t)1 << (bs + 1)) * 2 * n <= span || (span >> bs) > ((int64_t)1 << 26))) ++bs;
@@ -276,50 +461,61 @@ extern "C" int marfa_prepare_lines(const marfa_line_t* lines, int64_t n, const m
   const size_t sz_key = al(8 * n), sz_nu = al(8 * n), sz_f = al(4 * n), sz_sp = al(2 * n),
                sz_b = al(4 * (L->nbuck + 1));
   const size_t total = sz_key + sz_nu + 6 * sz_f + sz_sp + sz_b;
-  std::vector<unsigned char> hb;
+  std::unique_ptr<unsigned char[]> hb;
   try {
-    hb.assign(total, 0);
+    L->species.assign(sp, sp + n_sp);
+    L->perm.resize(n);
+    hb.reset(new unsigned char[total]);
   } catch (...) {
     delete L;
     return fail(MARFA_E_NOMEM, "host allocation failed");
   }
   size_t off = 0;
-  auto carve = [&](size_t sz) { const size_t o = off; off += sz; return o; };
-  const size_t o_key = carve(sz_key), o_nu = carve(sz_nu), o_S = carve(sz_f), o_ga = carve(sz_f),
-               o_gs = carve(sz_f), o_E = carve(sz_f), o_na = carve(sz_f), o_da = carve(sz_f),
-               o_sp = carve(sz_sp), o_b = carve(sz_b);
-  int64_t* key = (int64_t*)(hb.data() + o_key);
-  double* nu0 = (double*)(hb.data() + o_nu);
-  float *S = (float*)(hb.data() + o_S), *ga = (float*)(hb.data() + o_ga), *gs = (float*)(hb.data() + o_gs),
-        *E = (float*)(hb.data() + o_E), *na = (float*)(hb.data() + o_na), *da = (float*)(hb.data() + o_da);
-  int16_t* spi = (int16_t*)(hb.data() + o_sp);
-  int32_t* bfirst = (int32_t*)(hb.data() + o_b);
-  double dmin = 1e300, dmax = -1e300;
-  for (int64_t j = 0; j < n; ++j) {
-    const marfa_line_t& l = lines[order[j]];
-    L->perm[order[j]] = j;
-    nu0[j] = l.nu0;
-    key[j] = rint_fix(l.nu0);
-    S[j] = l.S296;
-    ga[j] = l.gamma_air;
-    gs[j] = l.gamma_self;
-    E[j] = l.E_lower;
-    na[j] = l.n_air;
-    da[j] = l.delta_air;
-    spi[j] = code_of[order[j]];
-    dmin = std::min(dmin, (double)l.delta_air);
-    dmax = std::max(dmax, (double)l.delta_air);
-  }
+  // a sub-array of `used` bytes in a slot of sz bytes; the padding is zeroed
+  auto carve = [&](size_t sz, size_t used) {
+    const size_t o = off;
+    off += sz;
+    std::memset(hb.get() + o + used, 0, sz - used);
+    return o;
+  };
+  const size_t o_key = carve(sz_key, 8 * n), o_nu = carve(sz_nu, 8 * n), o_S = carve(sz_f, 4 * n),
+               o_ga = carve(sz_f, 4 * n), o_gs = carve(sz_f, 4 * n), o_E = carve(sz_f, 4 * n),
+               o_na = carve(sz_f, 4 * n), o_da = carve(sz_f, 4 * n), o_sp = carve(sz_sp, 2 * n),
+               o_b = carve(sz_b, 4 * ((size_t)L->nbuck + 1));
+  int64_t* key = (int64_t*)(hb.get() + o_key);
+  double* nu0 = (double*)(hb.get() + o_nu);
+  float *S = (float*)(hb.get() + o_S), *ga = (float*)(hb.get() + o_ga), *gs = (float*)(hb.get() + o_gs),
+        *E = (float*)(hb.get() + o_E), *na = (float*)(hb.get() + o_na), *da = (float*)(hb.get() + o_da);
+  int16_t* spi = (int16_t*)(hb.get() + o_sp);
+  int32_t* bfirst = (int32_t*)(hb.get() + o_b);
+  int64_t* perm = L->perm.data();
+  par_chunks(host_threads(n, 8192), n, [&](int64_t lo, int64_t hi, int) {
+    for (int64_t j = lo; j < hi; ++j) {
+      const int64_t i = src(j);
+      const marfa_line_t& l = lines[i];
+      perm[i] = j;
+      nu0[j] = l.nu0;
+      key[j] = keyin[i];
+      S[j] = l.S296;
+      ga[j] = l.gamma_air;
+      gs[j] = l.gamma_self;
+      E[j] = l.E_lower;
+      na[j] = l.n_air;
+      da[j] = l.delta_air;
+      spi[j] = code_of[i];
+    }
+  });
   L->delta_min = dmin;
   L->delta_max = dmax;
-  {
-    int64_t i = 0;
-    for (int64_t b = 0; b <= L->nbuck; ++b) {
+  // bfirst[b] = the first sorted line whose key is >= the start of bucket b
+  par_chunks(host_threads(L->nbuck + 1, 16384), L->nbuck + 1, [&](int64_t b0, int64_t b1, int) {
+    int64_t i = std::lower_bound(key, key + n, L->key_base + (b0 << bs)) - key;
+    for (int64_t b = b0; b < b1; ++b) {
       const int64_t K = L->key_base + (b << bs);
       while (i < n && key[i] < K) ++i;
       bfirst[b] = (int32_t)i;
     }
-  }
+  });
   cudaError_t e = cudaMalloc(&L->block, total);
   if (e != cudaSuccess) {
     L->block = nullptr;
@@ -337,7 +533,7 @@ extern "C" int marfa_prepare_lines(const marfa_line_t* lines, int64_t n, const m
   L->da = (float*)(p + o_da);
   L->sp = (int16_t*)(p + o_sp);
   L->bfirst = (int32_t*)(p + o_b);
-  e = cudaMemcpy(L->block, hb.data(), total, cudaMemcpyHostToDevice);
+  e = cudaMemcpy(L->block, hb.get(), total, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     marfa_free_lines(L);
     return fail(MARFA_E_CUDA, "cudaMemcpy failed: %s", cudaGetErrorString(e));

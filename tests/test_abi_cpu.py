@@ -93,3 +93,28 @@ def test_prepare_lines_validation_before_any_device_call(M):
     assert "duplicate" in str(e.value)
     with pytest.raises(M.MarfaError):
         M.marfa_prepare_lines(wl.lines[:0], wl.species)
+
+
+def test_prepare_lines_reports_first_invalid_line(M):
+    """Validation runs over chunks of the line list on several host threads; the error
+    names the first invalid line whatever chunk it falls in."""
+    from workloads import config0_tiny
+    wl = config0_tiny()
+    big = np.resize(wl.lines, 200_003)
+    bad = big.copy()
+    bad["nu0"][150_001] = -1.0
+    bad["mol_iso"][170_000] = 99
+    bad["S296"][199_999] = np.inf
+    for first, what in [(150_001, "nu0"), (170_000, "unknown species"), (199_999, "non-finite")]:
+        with pytest.raises(M.MarfaError) as e:
+            M.marfa_prepare_lines(bad, wl.species)
+        assert e.value.code == -1 and f"line {first}:" in str(e.value) and what in str(e.value)
+        bad["nu0"][150_001] = 1.0
+        if first >= 170_000:
+            bad["mol_iso"][170_000] = wl.lines["mol_iso"][0]
+    bad2 = big.copy()
+    bad2["gamma_air"][7] = np.nan
+    bad2["nu0"][100_000] = np.nan
+    with pytest.raises(M.MarfaError) as e:
+        M.marfa_prepare_lines(bad2, wl.species)
+    assert "line 7:" in str(e.value)

@@ -270,6 +270,25 @@ def test_batch_equals_single_bit_identical(M):
         assert np.array_equal(s, o.cpu().numpy())
 
 
+def test_prepared_order_is_the_stable_sort_by_nu0(M):
+    """The host-side sort (chunks on several threads) gives exactly the order of a stable
+    sort by nu0: ties, values closer than one fixed-point unit, a crowded band, shuffled."""
+    wl = tiny_workload(97, 50, 1000.0, 1003.0, 25.0, T=(296.0,), p=(1.0,))
+    rng = np.random.default_rng(5)
+    n = 300_001
+    big = np.resize(wl.lines, n)
+    nu = np.concatenate([
+        1000.0 + np.floor(rng.random(n // 3) * 64) / 16,          # many exact ties
+        1001.5 + 1e-13 * np.floor(rng.random(n // 3) * 500),       # below one 2^-43 unit apart
+        990.0 + 25.0 * rng.random(n - 2 * (n // 3)),              # spread
+    ])
+    big["nu0"] = nu[rng.permutation(n)]
+    lines = M.marfa_prepare_lines(big, wl.species)
+    _, _, perm = M.marfa_diag_level_lines(lines, M.levels_of(wl), wl.vmr, M.request_of(wl))
+    order = np.argsort(big["nu0"], kind="stable")
+    assert np.array_equal(perm[order], np.arange(n))
+
+
 def test_window_and_permutation_invariance(M):
     wl = tiny_workload(80, 400, 1000.0, 1003.0, 25.0, T=(296.0,), p=(1.0,))
     a = run_gpu(M, wl)[0]
