@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <condition_variable>
 #include <cstdlib>
 #include <cerrno>
 #include <cmath>
@@ -16,6 +17,7 @@
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <memory>
 #include <mutex>
 #include <new>
@@ -170,34 +172,89 @@ extern "C" void marfa_free_lines(marfa_lines_t* L) {
 // kHostThreads threads; every result, errors included, is independent of their number.
 constexpr int kHostThreads = 16;
 
+// Persistent host threads for those chunked loops (starting and joining 15 threads costs
+// about as much as one loop over 200k lines). The pool starts on first use, and again in a
+// child process after fork (which inherits no threads); it runs one job at a time and is
+// never torn down: its threads sleep on a condition variable until the process ends.
+class HostPool {
+ public:
+  // the pool of this process, or nullptr if it cannot be made (then loops run serially)
+  static HostPool* get() {
+    static std::mutex create_mu;
+    static HostPool* pool = nullptr;
+    std::lock_guard<std::mutex> g(create_mu);
+    if (!pool || pool->pid_ != getpid()) pool = new (std::nothrow) HostPool();
+    return pool;
+  }
+  int size() const { return 1 + nworkers_; }
+  // f(t) for t in [0, nt), nt <= size(); t = 0 runs on the calling thread. f must not throw.
+  void run(int nt, const std::function<void(int)>& f) {
+    std::lock_guard<std::mutex> job(job_mu_);
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      fn_ = &f;
+      want_ = nt;
+      pending_ = nt - 1;
+      ++gen_;
+    }
+    cv_start_.notify_all();
+    f(0);
+    std::unique_lock<std::mutex> lk(mu_);
+    cv_done_.wait(lk, [&] { return pending_ == 0; });
+  }
+
+ private:
+  HostPool() : pid_(getpid()) {
+    const unsigned hc = std::thread::hardware_concurrency();
+    const int nw = (int)std::min<unsigned>(hc ? hc : 1, kHostThreads) - 1;
+    for (int i = 1; i <= nw; ++i) {
+      try {
+        std::thread([this, i] { loop(i); }).detach();
+      } catch (...) {
+        break;
+      }
+      nworkers_ = i;
+    }
+  }
+  void loop(int id) {
+    uint64_t seen = 0;
+    std::unique_lock<std::mutex> lk(mu_);
+    for (;;) {
+      cv_start_.wait(lk, [&] { return gen_ != seen; });
+      seen = gen_;
+      if (id >= want_) continue;  // not part of this job
+      const std::function<void(int)>* f = fn_;
+      lk.unlock();
+      (*f)(id);
+      lk.lock();
+      if (--pending_ == 0) cv_done_.notify_one();
+    }
+  }
+  const pid_t pid_;
+  int nworkers_ = 0;
+  std::mutex job_mu_, mu_;
+  std::condition_variable cv_start_, cv_done_;
+  const std::function<void(int)>* fn_ = nullptr;
+  uint64_t gen_ = 0;
+  int want_ = 0, pending_ = 0;
+};
+
 static int host_threads(int64_t work, int64_t min_per_thread) {
-  const unsigned hc = std::thread::hardware_concurrency();
-  int64_t nt = std::min<int64_t>(hc ? (int64_t)hc : 1, kHostThreads);
-  nt = std::min<int64_t>(nt, std::max<int64_t>(1, work / min_per_thread));
+  const HostPool* pool = HostPool::get();
+  const int64_t nt = std::min<int64_t>(pool ? pool->size() : 1, std::max<int64_t>(1, work / min_per_thread));
   return (int)nt;
 }
 
-// f(lo, hi, t) on the nt contiguous chunks of [0, n), chunk t on thread t; chunk 0, and any
-// chunk whose thread cannot be started, runs on the calling thread. f must not throw.
+// f(lo, hi, t) on the nt contiguous chunks of [0, n), chunk t on pool thread t (chunk 0 on
+// the calling thread); nt comes from host_threads. f must not throw.
 template <class F>
 static void par_chunks(int nt, int64_t n, const F& f) {
-  std::vector<std::thread> th;
-  try {
-    th.reserve(nt);
-  } catch (...) {
+  HostPool* pool = nt > 1 ? HostPool::get() : nullptr;
+  if (!pool || nt > pool->size()) {
+    for (int t = 0; t < nt; ++t) f(n * t / nt, n * (t + 1) / nt, t);
+    return;
   }
-  for (int t = 1; t < nt; ++t) {
-    const int64_t lo = n * t / nt, hi = n * (t + 1) / nt;
-    bool started = false;
-    try {
-      th.emplace_back([&f, lo, hi, t] { f(lo, hi, t); });
-      started = true;
-    } catch (...) {
-    }
-    if (!started) f(lo, hi, t);
-  }
-  f(0, n / nt, 0);
-  for (auto& x : th) x.join();
+  pool->run(nt, [&](int t) { f(n * t / nt, n * (t + 1) / nt, t); });
 }
 
 // mol_iso -> species code: open addressing over a power-of-two table (read-only once built,
