@@ -26,6 +26,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import queue
 import subprocess
 import sys
 import tempfile
@@ -94,47 +95,92 @@ def read_clocks(path, dev_index):
             "samples": len(rows)}
 
 
-def cpu_baseline_sample(wl, seconds_hint=15.0):
-    """Time the FP64 oracle (as it stands) on a bounded sample of the workload: the
-    eleven-grid result of one mid-profile level on a window of 0.25 cm^-1, with the
-    line list cut to the lines that can reach it (others contribute nothing)."""
-    from oracle import marfa_oracle as O
-    lev = 30
-    lo, hi = 2500.0, 2500.25
+def _oracle_sample(wl, lev, lo, hi):
+    """The workload cut to one level, the window [lo, hi] and the lines that can reach it
+    (the others contribute nothing)."""
     keep = np.abs(wl.lines["nu0"] - 0.5 * (lo + hi)) <= wl.cutoff + 2.0
-    sub = wl.with_(lines=wl.lines[keep], nu_lo=lo, nu_hi=hi).level_subset([lev])
+    return wl.with_(lines=wl.lines[keep], nu_lo=lo, nu_hi=hi).level_subset([lev]), int(keep.sum())
+
+
+def _oracle_worker(sub, barrier, q):
+    """One process of the all-cores oracle run (spawn start): waits for the others, then
+    runs the eleven-grid oracle on its sample and reports its start and end times."""
+    from oracle import marfa_oracle as O
+    barrier.wait(timeout=600.0)
+    t0 = time.monotonic()
+    O.eleven_grid(sub, 0)
+    q.put((t0, time.monotonic()))
+
+
+def oracle_all_cores(wl, lev, lo, width, nproc):
+    """The FP64 oracle (as it stands) on nproc adjacent windows of the given width at one
+    level, one process per host core, all started together: (points per second over the
+    whole run, points, seconds)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    barrier, q = ctx.Barrier(nproc), ctx.Queue()
+    subs = [_oracle_sample(wl, lev, lo + i * width, lo + (i + 1) * width)[0] for i in range(nproc)]
+    procs = [ctx.Process(target=_oracle_worker, args=(s, barrier, q)) for s in subs]
+    for p in procs:
+        p.start()
+    spans, deadline = [], time.monotonic() + 900.0
+    try:
+        while len(spans) < nproc:
+            try:
+                spans.append(q.get(timeout=1.0))
+            except queue.Empty:
+                if any(p.exitcode not in (None, 0) for p in procs) or time.monotonic() > deadline:
+                    raise RuntimeError("an oracle worker process failed or timed out")
+    finally:
+        for p in procs:
+            p.join(timeout=30.0)
+            if p.is_alive():
+                p.kill()
+    from oracle import marfa_oracle as O
+    pts = sum(O.num_points(s.nu_lo, s.nu_hi) for s in subs)
+    dt = max(b for _, b in spans) - min(a for a, _ in spans)
+    return pts / dt, pts, dt
+
+
+def cpu_baseline_sample(wl):
+    """Time the FP64 oracle (as it stands) on a bounded sample of the workload: the
+    eleven-grid result of one mid-profile level on windows of 0.25 cm^-1, once on one
+    core and then on every host core at once (one window per process)."""
+    from oracle import marfa_oracle as O
+    lev, lo, width = 30, 2500.0, 0.25
+    sub, nin = _oracle_sample(wl, lev, lo, lo + width)
     t = time.perf_counter()
     O.eleven_grid(sub, 0)
-    dt = time.perf_counter() - t
-    pts = O.num_points(lo, hi)
-    return {"value": pts / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"level {lev}, {lo}-{hi} cm^-1 ({pts} points), {int(keep.sum())} lines in reach, "
-                      f"{dt:.1f} s single-threaded numpy/scipy FP64"}
+    dt1 = time.perf_counter() - t
+    pts1 = O.num_points(lo, lo + width)
+    nproc = os.cpu_count() or 1
+    v, pts, dt = oracle_all_cores(wl, lev, lo, width, nproc)
+    return {"value": v, "unit": UNIT, "cores": nproc, "kind": "oracle",
+            "single_core_value": pts1 / dt1,
+            "sample": f"level {lev}, {nproc} adjacent windows of {width} cm^-1 from {lo} cm^-1 "
+                      f"({pts} points, one process per core, {dt:.1f} s); single core: {lo}-{lo + width} "
+                      f"cm^-1 ({pts1} points, {nin} lines in reach, {dt1:.1f} s); numpy/scipy FP64"}
 
 
 def run_reference(args, wl, rank, world):
     if rank != 0:
         return
-    from oracle import marfa_oracle as O
-    times = []
-    lev = 30
-    lo, hi = 2500.0, 2500.125
-    keep = np.abs(wl.lines["nu0"] - 0.5 * (lo + hi)) <= wl.cutoff + 2.0
-    sub = wl.with_(lines=wl.lines[keep], nu_lo=lo, nu_hi=hi).level_subset([lev])
-    pts = O.num_points(lo, hi)
+    nproc = os.cpu_count() or 1
+    lev, lo, width = 30, 2500.0, 0.125
+    times, pts = [], 0
     for i in range(args.warmup + args.steps):
-        t = time.perf_counter()
-        O.eleven_grid(sub, 0)
+        _, pts, dt = oracle_all_cores(wl, lev, lo, width, nproc)
         if i >= args.warmup:
-            times.append(time.perf_counter() - t)
+            times.append(dt)
     dt = float(np.mean(times))
     v = pts / dt
+    sample = (f"level {lev}, {nproc} adjacent windows of {width} cm^-1 from {lo} cm^-1 per step "
+              f"({pts} points, one process per core)")
     line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl.name, "sample": f"level {lev}, {lo}-{hi} cm^-1 per step"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"level {lev}, {lo}-{hi} cm^-1 ({pts} points), {int(keep.sum())} lines"},
+            "config": {"workload": wl.name, "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": nproc, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

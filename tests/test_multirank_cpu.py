@@ -48,3 +48,13 @@ def test_single_rank_is_identity():
     import bench
     assert bench.max_over_ranks(3.5, None, "cpu") == 3.5
     assert bench.job_throughput(10, 1, 2, 4.0) == 5.0
+
+
+def test_oracle_all_cores_runs_and_counts_points():
+    """The all-cores oracle baseline: one spawned process per window, all points counted."""
+    import bench
+    from oracle import marfa_oracle as O
+    from workloads import config0_tiny
+    wl = config0_tiny()
+    v, pts, dt = bench.oracle_all_cores(wl, 0, 4000.0, 0.03125, 2)
+    assert pts == 2 * O.num_points(4000.0, 4000.03125) and dt > 0 and v == pts / dt
