@@ -1269,7 +1269,7 @@ __global__ void __launch_bounds__(kFineThreads)
   extern __shared__ __align__(16) unsigned char dsm[];  // surrogate weights (SURR only)
   MlpWeights& S = *reinterpret_cast<MlpWeights*>(dsm);
   __shared__ float tile[kFineTile];
-  __shared__ float stab[kVoigtTableFloats];
+  __shared__ __align__(16) float stab[kVoigtTableFloats];
   __shared__ FineLine sL[NW][32];  // staged lines, one per lane of each warp
   __shared__ FineChi sC[NW][32];
   __shared__ __align__(16) float sAcc[NW][kWarpNodes], sCmp[NW][kWarpNodes];

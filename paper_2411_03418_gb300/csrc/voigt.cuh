@@ -69,9 +69,34 @@ __device__ __forceinline__ float voigt_asym(float x, float y) {
 
 // One bivariate cell; tab is the coefficient table, either the global copy (read
 // through the read-only cache) or a copy a kernel placed in shared memory (SMEM).
+// In a shared copy the cells are padded to an even number of floats (81 -> 82) and read
+// as float2.
+constexpr int kVoigtCellFloats = (VOIGT_DEG + 1) * (VOIGT_DEG + 1);
+constexpr int kVoigtCellStride = (kVoigtCellFloats + 1) & ~1;
+
 template <bool SMEM>
 __device__ __forceinline__ float voigt_cell(const float* tab, int cell, float u, float v) {
-  const float* c = tab + cell * (VOIGT_DEG + 1) * (VOIGT_DEG + 1);
+  if (SMEM) {
+    const float2* c2 = reinterpret_cast<const float2*>(tab + cell * kVoigtCellStride);
+    float acc = 0.0f, r = 0.0f;
+    // coefficient k = p (DEG + 1) + q, taken from k = 80 down to 0, two at a time
+#pragma unroll
+    for (int i = kVoigtCellStride / 2 - 1; i >= 0; --i) {
+      const float2 t = c2[i];
+#pragma unroll
+      for (int h = 1; h >= 0; --h) {
+        const int k = 2 * i + h;
+        if (k >= kVoigtCellFloats) continue;
+        r = fmaf(r, v, h ? t.y : t.x);
+        if (k % (VOIGT_DEG + 1) == 0) {  // q = 0: row p done
+          acc = fmaf(acc, u, r);
+          r = 0.0f;
+        }
+      }
+    }
+    return acc;
+  }
+  const float* c = tab + cell * kVoigtCellFloats;
   float acc = 0.0f;
 #pragma unroll
   for (int p = VOIGT_DEG; p >= 0; --p) {
@@ -79,7 +104,7 @@ __device__ __forceinline__ float voigt_cell(const float* tab, int cell, float u,
 #pragma unroll
     for (int q = VOIGT_DEG; q >= 0; --q) {
       const int k = p * (VOIGT_DEG + 1) + q;
-      r = fmaf(r, v, SMEM ? c[k] : __ldg(c + k));
+      r = fmaf(r, v, __ldg(c + k));
     }
     acc = fmaf(acc, u, r);
   }
@@ -91,6 +116,16 @@ template <bool SMEM>
 __device__ __forceinline__ float voigt_cell_small(const float* tab, int cell, float u, float v) {
   constexpr int NQ = VOIGT_SMALL_DV + 1;
   const float* c = tab + cell * (VOIGT_SMALL_DX + 1) * NQ;
+  if (SMEM && NQ == 4) {  // shared copy: two float2 per power of u
+    float acc = 0.0f;
+#pragma unroll
+    for (int p = VOIGT_SMALL_DX; p >= 0; --p) {
+      const float2 hi = reinterpret_cast<const float2*>(c)[2 * p + 1];
+      const float2 lo = reinterpret_cast<const float2*>(c)[2 * p];
+      acc = fmaf(acc, u, fmaf(fmaf(fmaf(hi.y, v, hi.x), v, lo.y), v, lo.x));
+    }
+    return acc;
+  }
   float acc = 0.0f;
 #pragma unroll
   for (int p = VOIGT_SMALL_DX; p >= 0; --p) {
@@ -103,7 +138,7 @@ __device__ __forceinline__ float voigt_cell_small(const float* tab, int cell, fl
 }
 
 // Floats of the large table; the small-y table follows it in a kernel's shared copy.
-constexpr int kVoigtBigFloats = VOIGT_NCELL * (VOIGT_DEG + 1) * (VOIGT_DEG + 1);
+constexpr int kVoigtBigFloats = VOIGT_NCELL * kVoigtCellStride;  // in a shared copy
 
 // Far-wing form (|z| >= 100): two terms of the series, K = y/(sqrt(pi) r^2) (1 + (3x^2 - y^2)/(2 r^4)).
 __device__ __forceinline__ float voigt_far(float x, float y) {
@@ -183,8 +218,11 @@ constexpr int kVoigtTableFloats = kVoigtBigFloats + kVoigtSmallFloats;
 
 // Copy both coefficient tables into shared memory (all threads of the block take part).
 __device__ __forceinline__ void voigt_table_to_smem(float* dst) {
-  for (int i = threadIdx.x; i < kVoigtTableFloats; i += blockDim.x)
-    dst[i] = i < kVoigtBigFloats ? kVoigtCells[i] : kVoigtSmall[i - kVoigtBigFloats];
+  for (int i = threadIdx.x; i < kVoigtTableFloats; i += blockDim.x) {
+    const int cell = i / kVoigtCellStride, k = i - cell * kVoigtCellStride;
+    dst[i] = i >= kVoigtBigFloats ? kVoigtSmall[i - kVoigtBigFloats]
+                                  : (k < kVoigtCellFloats ? kVoigtCells[cell * kVoigtCellFloats + k] : 0.0f);
+  }
 }
 
 }  // namespace marfa
