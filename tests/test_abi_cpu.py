@@ -118,3 +118,73 @@ def test_prepare_lines_reports_first_invalid_line(M):
     with pytest.raises(M.MarfaError) as e:
         M.marfa_prepare_lines(bad2, wl.species)
     assert "line 7:" in str(e.value)
+
+
+def _prepare_error(M, lines, species):
+    try:
+        M.marfa_prepare_lines(lines, species)
+    except M.MarfaError as e:
+        return str(e)
+    return None
+
+
+def test_prepare_lines_concurrent_callers_share_the_host_pool(M):
+    """Two host threads validating large line lists at once: the worker pool runs one
+    job at a time, and each caller gets the error of its own input."""
+    import threading
+    from workloads import config0_tiny
+    wl = config0_tiny()
+    big = np.resize(wl.lines, 150_000)
+    bad = [big.copy() for _ in range(4)]
+    for k, b in enumerate(bad):
+        b["nu0"][20_000 * (k + 1) + k] = np.nan
+    got = [None] * len(bad)
+
+    def run(k):
+        for _ in range(5):
+            got[k] = _prepare_error(M, bad[k], wl.species)
+
+    th = [threading.Thread(target=run, args=(k,)) for k in range(len(bad))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join(timeout=120)
+        assert not t.is_alive()
+    for k in range(len(bad)):
+        assert got[k] is not None and f"line {20_000 * (k + 1) + k}:" in got[k]
+
+
+def _child_prepare(conn):
+    from paper_2411_03418_gb300 import marfa as M
+    from workloads import config0_tiny
+    wl = config0_tiny()
+    bad = np.resize(wl.lines, 120_000)
+    bad["nu0"][99_999] = -5.0
+    conn.send(_prepare_error(M, bad, wl.species))
+    conn.close()
+
+
+@pytest.mark.filterwarnings("ignore:This process .* is multi-threaded")
+def test_prepare_lines_after_fork(M):
+    """A child forked after the host pool started (it inherits no pool threads) starts a
+    pool of its own instead of waiting on the parent's."""
+    import multiprocessing as mp
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("forking after CUDA initialisation is not supported")
+    from workloads import config0_tiny
+    wl = config0_tiny()
+    first = np.resize(wl.lines, 120_000)
+    first["nu0"][50_000] = -1.0
+    assert "line 50000:" in _prepare_error(M, first, wl.species)  # the parent's pool is up
+    ctx = mp.get_context("fork")
+    a, b = ctx.Pipe()
+    p = ctx.Process(target=_child_prepare, args=(b,))
+    p.start()
+    ok = a.poll(120)
+    p.join(timeout=30)
+    if p.is_alive():
+        p.kill()
+    assert ok, "the forked child did not finish its line preparation"
+    msg = a.recv()
+    assert msg is not None and "line 99999:" in msg
