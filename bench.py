@@ -430,6 +430,11 @@ def main():
     achieved = dom_flops / (dom_ms * 1e-3) / 1e12
     mhz, src = peaks()
     peak = N_SM * FP32_LANES * 2 * mhz * 1e6 / 1e12
+    # measured issue rates beside the derived peak: FP32 FMA and the MUFU kinds the
+    # Voigt branches use (ex2 in exp, rcp in the divisions, cos in the Gaussian core)
+    probes = {"fp32_fma_tflops": 2.0 * M.marfa_diag_pipe_rate("fma") / 1e12}
+    for k in ("ex2", "rcp", "cos"):
+        probes[f"mufu_{k}_gops"] = M.marfa_diag_pipe_rate(k) / 1e9
 
     surr = None
     wpath = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2411_03418_gb300",
@@ -475,7 +480,8 @@ def main():
                                      else None),
                          "flops_per_eval": {"far": FLOPS_FAR, "asymptotic": FLOPS_MID, "poly_cell": FLOPS_NEAR,
                                             "small_y_cell": FLOPS_SMALL},
-                         "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz ({src} max clock)"},
+                         "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz ({src} max clock)",
+                         "probes": probes},
             "clocks": clocks,
         }
         if surr is not None:

@@ -375,6 +375,13 @@ int marfa_diag_absorption_counted_surrogate(const marfa_lines_t* lines,
                                             float* k_out, int64_t* counts,
                                             int64_t* surrogate_counts);
 
+/* Issue rate of one instruction kind on this device, for the roofline denominators:
+ * pipe 0 FP32 FMA, 1 MUFU ex2.approx, 2 MUFU rcp.approx, 3 MUFU cos.approx. Eight
+ * 256-thread CTAs per SM run eight independent dependency chains a thread; five timed
+ * launches after one warm-up, CUDA events on the default stream. Writes instructions per
+ * second (an FMA counts once) to *ops_per_s. */
+int marfa_diag_pipe_rate(int32_t pipe, double* ops_per_s);
+
 /* Per-kernel device time: enable = 1 clears the totals and starts recording CUDA events
  * around every kernel launch of this library (on the launch stream); enable = 0 stops,
  * waits for the recorded events and writes, for the twelve kernel launches of a call

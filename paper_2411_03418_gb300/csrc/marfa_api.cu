@@ -1621,6 +1621,39 @@ extern "C" int marfa_diag_voigt(const float* x, const float* y, float* out, int6
   return MARFA_OK;
 }
 
+extern "C" int marfa_diag_pipe_rate(int32_t pipe, double* ops_per_s) {
+  if (pipe < 0 || pipe > 3 || !ops_per_s) return fail(MARFA_E_INVAL, "pipe must be 0..3 and ops_per_s non-NULL");
+  int dev = 0, nsm = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int blocks = 8 * nsm;  // 2048 threads on every SM
+  const int iters = pipe == 0 ? 8192 : 1024;
+  const int reps = 5;
+  float* out = nullptr;
+  CK(cudaMalloc(&out, (size_t)blocks * 256 * sizeof(float)));
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  cudaError_t e = cudaEventCreate(&ev[0]);
+  if (!e) e = cudaEventCreate(&ev[1]);
+  int64_t n = 0;
+  float ms = 0.0f;
+  if (!e) {
+    launch_diag_pipe(pipe, out, blocks, iters, 0);  // warm-up
+    e = cudaEventRecord(ev[0], 0);
+    for (int r = 0; r < reps && !e; ++r) n += launch_diag_pipe(pipe, out, blocks, iters, 0);
+    if (!e) e = cudaEventRecord(ev[1], 0);
+    if (!e) e = cudaEventSynchronize(ev[1]);
+    if (!e) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    if (!e) e = cudaGetLastError();
+  }
+  for (cudaEvent_t x : ev)
+    if (x) cudaEventDestroy(x);
+  cudaFree(out);
+  if (e) return fail(MARFA_E_CUDA, "pipe probe: %s", cudaGetErrorString(e));
+  if (!(ms > 0.0f)) return fail(MARFA_E_CUDA, "pipe probe: no elapsed time");
+  *ops_per_s = (double)n / (ms * 1e-3);
+  return MARFA_OK;
+}
+
 extern "C" int marfa_diag_level_lines(const marfa_lines_t* lines, const marfa_level_t* levels,
                                       const double* vmr, int32_t n_levels, const marfa_request_t* rq,
                                       int64_t* c_out, int8_t* gstar_out, int64_t* perm) {

@@ -174,6 +174,8 @@ void launch_coarse_lm(const ReqDev* reqs, const CoarseItem* items, int n_items, 
 void launch_fine(const ReqDev* reqs, const FineItem* items, int n_items, int64_t* counts, bool surr,
                  bool wide, cudaStream_t st);
 void launch_diag_voigt(const float* x, const float* y, float* out, int64_t n, cudaStream_t st);
+// instructions issued by one probe launch (out: blocks x 256 floats)
+int64_t launch_diag_pipe(int pipe, float* out, int blocks, int iters, cudaStream_t st);
 void launch_diag_owned(const ReqDev* req, int64_t n_lines, int level, int grid, int64_t first,
                        int count, uint8_t* out, cudaStream_t st);
 

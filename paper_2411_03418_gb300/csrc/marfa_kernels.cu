@@ -1554,6 +1554,52 @@ void launch_diag_voigt(const float* x, const float* y, float* out, int64_t n, cu
   k_diag_voigt<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, y, out, n);
 }
 
+// Issue-rate probes for the roofline denominators: every thread runs kPipeChains
+// independent dependency chains of one instruction kind. PIPE 0: FP32 FMA; 1: MUFU
+// ex2.approx; 2: MUFU rcp.approx; 3: MUFU cos.approx (__cosf). The chains stay in range
+// (FMA: a fixed point near 1e-3; ex2 of -a: (0, 1]; rcp of 1 + a: [1/2, 1]; cos of a:
+// [cos 1, 1]), and their sum is stored so that none is dropped.
+constexpr int kPipeChains = 8;
+
+template <int PIPE>
+__global__ void __launch_bounds__(256) k_diag_pipe(float* out, int iters) {
+  float a[kPipeChains];
+#pragma unroll
+  for (int k = 0; k < kPipeChains; ++k) a[k] = 1e-3f * (float)((threadIdx.x + k) & 7);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < kPipeChains; ++k) {
+      if (PIPE == 0) {
+        a[k] = fmaf(a[k], 0.999f, 1e-6f);
+      } else if (PIPE == 1) {
+        float r;
+        asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(-a[k]));
+        a[k] = r;
+      } else if (PIPE == 2) {
+        float r;
+        asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(1.0f + a[k]));
+        a[k] = r;
+      } else {
+        a[k] = __cosf(a[k]);
+      }
+    }
+  }
+  float t = 0.0f;
+#pragma unroll
+  for (int k = 0; k < kPipeChains; ++k) t += a[k];
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = t;
+}
+
+int64_t launch_diag_pipe(int pipe, float* out, int blocks, int iters, cudaStream_t st) {
+  switch (pipe) {
+    case 0: k_diag_pipe<0><<<blocks, 256, 0, st>>>(out, iters); break;
+    case 1: k_diag_pipe<1><<<blocks, 256, 0, st>>>(out, iters); break;
+    case 2: k_diag_pipe<2><<<blocks, 256, 0, st>>>(out, iters); break;
+    default: k_diag_pipe<3><<<blocks, 256, 0, st>>>(out, iters); break;
+  }
+  return (int64_t)blocks * 256 * iters * kPipeChains;  // instructions of the probed kind
+}
+
 __global__ void k_diag_owned(const ReqDev* __restrict__ req, int lev, int grid, int64_t first,
                              int count, uint8_t* out) {
   const ReqDev& R = *req;

@@ -46,7 +46,8 @@ EXPORTS = ["marfa_prepare_lines", "marfa_free_lines", "marfa_num_points", "marfa
            "marfa_diag_kernel_timing", "marfa_absorption_noalloc", "marfa_mlp_loss_grad",
            "marfa_mlp_train", "marfa_surrogate_load", "marfa_surrogate_unload", "marfa_surrogate_eval",
            "marfa_diag_absorption_counted_surrogate", "marfa_plan_create", "marfa_plan_execute",
-           "marfa_plan_info", "marfa_plan_destroy", "marfa_diag_absorption_counts", "marfa_read_par"]
+           "marfa_plan_info", "marfa_plan_destroy", "marfa_diag_absorption_counts", "marfa_read_par",
+           "marfa_diag_pipe_rate"]
 
 MLP_PARAMS = 8577
 MLP_MAX_BATCH = 65536
@@ -86,6 +87,7 @@ def load(path: str | None = None):
         "marfa_diag_owned": (C.c_int, [vp, vp, vp, i32, vp, i32, i32, i64, i32, vp]),
         "marfa_diag_absorption_counted": (C.c_int, [vp, vp, vp, i32, vp, vp, vp]),
         "marfa_diag_kernel_timing": (C.c_int, [i32, vp, vp]),
+        "marfa_diag_pipe_rate": (C.c_int, [i32, vp]),
         "marfa_absorption_noalloc": (C.c_int, [vp, vp, vp, i32, vp, vp, vp]),
         "marfa_mlp_loss_grad": (C.c_int, [vp, vp, vp, vp, i64, i32, vp, vp]),
         "marfa_mlp_train": (C.c_int, [vp, vp, vp, vp, i64, vp, vp]),
@@ -404,6 +406,16 @@ def marfa_diag_kernel_timing(enable: bool):
     n = np.zeros(12, dtype=np.int64)
     _check(load().marfa_diag_kernel_timing(1 if enable else 0, _ptr(ms), _ptr(n)))
     return ms, n
+
+
+PIPES = {"fma": 0, "ex2": 1, "rcp": 2, "cos": 3}
+
+
+def marfa_diag_pipe_rate(pipe: str) -> float:
+    """Measured issue rate (instructions/s) of FP32 FMA or a MUFU kind on this device."""
+    r = C.c_double(0.0)
+    _check(load().marfa_diag_pipe_rate(PIPES[pipe], C.byref(r)))
+    return r.value
 
 
 # ------------------------------------------------------------------ workload marshalling

@@ -188,3 +188,12 @@ def test_prepare_lines_after_fork(M):
     assert ok, "the forked child did not finish its line preparation"
     msg = a.recv()
     assert msg is not None and "line 99999:" in msg
+
+
+def test_pipe_rate_rejects_bad_arguments(M):
+    import ctypes
+    r = ctypes.c_double(0.0)
+    for pipe, out in [(7, ctypes.byref(r)), (-1, ctypes.byref(r)), (0, None)]:
+        with pytest.raises(M.MarfaError) as e:
+            M._check(M.load().marfa_diag_pipe_rate(pipe, out))
+        assert e.value.code == -1

@@ -246,3 +246,15 @@ def test_config3_earth_precision(M):
     for r in report:
         print(f"  {r[0]:2d} {r[1]:8.2f} {r[2]:.3e} {r[3]:.3e}")
     M.marfa_plan_destroy(plan)
+
+
+def test_pipe_rate_probes(M):
+    """The issue-rate probes behind the roofline: FP32 FMA near 128 a clock per SM, the
+    MUFU kinds well below it."""
+    import torch
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    fma = M.marfa_diag_pipe_rate("fma")
+    assert 0.3e9 * nsm * 128 < fma < 2.2e9 * nsm * 128 * 1.05
+    for k in ("ex2", "rcp", "cos"):
+        r = M.marfa_diag_pipe_rate(k)
+        assert 0.0 < r < fma / 2
