@@ -999,6 +999,20 @@ void launch_coarse_lm(const ReqDev* reqs, const CoarseItem* items, int n_items, 
   }
 }
 
+// 32 x 32 bit-matrix transpose across a warp: lane t holds row t; returns column `lane`
+// (bit t = bit lane of row t). Five stages swap the off-diagonal blocks of width 16, 8,
+// 4, 2 and 1 between lanes t and t ^ j.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
+  constexpr uint32_t kM[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const int j = 16 >> k;
+    const uint32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+    x = (lane & j) ? ((x & ~kM[k]) | ((y & ~kM[k]) >> j)) : ((x & kM[k]) | ((y & kM[k]) << j));
+  }
+  return x;
+}
+
 // ------------------------------------------------------------------ grids 2..10
 // Warp w of a CTA owns kCPairs consecutive node pairs of grid g of one level (lane p
 // holds pair p: even node 2m, odd node 2m+1). The warp takes 32 candidate lines at a
@@ -1187,12 +1201,9 @@ __global__ void __launch_bounds__(kCWarps * 32, SURR ? 3 : 6)
         }
         mk[lane] = own;
         __syncwarp();
-        // phase 2: the staged lines owning panel m0+p-1 (bit p) or m0+p (bit p+1)
-        uint32_t mine = 0;
-        for (uint32_t rem = any; rem; rem &= rem - 1) {
-          const int t = __ffs(rem) - 1;
-          mine |= (((mk[t] >> p) & 3ull) ? 1u : 0u) << t;
-        }
+        // phase 2: the staged lines owning panel m0+p-1 (bit p) or m0+p (bit p+1): bit t
+        // of lane p's mask = bit p of lane t's (own | own >> 1), a 32 x 32 bit transpose
+        uint32_t mine = warp_transpose32((uint32_t)(own | (own >> 1)), lane);
         while (mine) {
           const int t = __ffs(mine) - 1;
           mine &= mine - 1;
