@@ -1370,15 +1370,12 @@ __global__ void __launch_bounds__(kFineThreads)
         sC[warp][lane] = fc;
       }
       __syncwarp();
+      // lane q < 16: the staged lines owning panel q (a 32 x 32 bit transpose of the masks)
+      const uint32_t pcol = warp_transpose32(pm, lane);
 #pragma unroll 1
       for (int s = 0; s < kFinePerThread; ++s) {
         // the staged lines owning this group's panel 4 s + gi
-        uint32_t mine = 0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const uint32_t b = __ballot_sync(0xffffffffu, (pm >> (4 * s + k)) & 1u);
-          if (k == gi) mine = b;
-        }
+        uint32_t mine = __shfl_sync(0xffffffffu, pcol, 4 * s + gi);
         if (!__any_sync(0xffffffffu, mine != 0)) continue;
         const int j = 32 * s + lane;
         const float jf = (float)j;

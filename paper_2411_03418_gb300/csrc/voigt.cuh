@@ -216,13 +216,18 @@ __device__ __forceinline__ int voigt_class(float x, float y) {
 constexpr int kVoigtSmallFloats = VOIGT_SMALL_NX * (VOIGT_SMALL_DX + 1) * (VOIGT_SMALL_DV + 1);
 constexpr int kVoigtTableFloats = kVoigtBigFloats + kVoigtSmallFloats;
 
-// Copy both coefficient tables into shared memory (all threads of the block take part).
+// Copy both coefficient tables into shared memory, the large one with padded cells (all
+// threads of the block take part: warp w copies cells w, w + nwarps, ..., lane by lane;
+// then the small-y table). dst: 16-byte aligned.
 __device__ __forceinline__ void voigt_table_to_smem(float* dst) {
-  for (int i = threadIdx.x; i < kVoigtTableFloats; i += blockDim.x) {
-    const int cell = i / kVoigtCellStride, k = i - cell * kVoigtCellStride;
-    dst[i] = i >= kVoigtBigFloats ? kVoigtSmall[i - kVoigtBigFloats]
-                                  : (k < kVoigtCellFloats ? kVoigtCells[cell * kVoigtCellFloats + k] : 0.0f);
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int cell = threadIdx.x >> 5; cell < VOIGT_NCELL; cell += nw) {
+    const float* src = kVoigtCells + cell * kVoigtCellFloats;
+    float* d = dst + cell * kVoigtCellStride;
+#pragma unroll
+    for (int k = lane; k < kVoigtCellStride; k += 32) d[k] = k < kVoigtCellFloats ? src[k] : 0.0f;
   }
+  for (int i = threadIdx.x; i < kVoigtSmallFloats; i += blockDim.x) dst[kVoigtBigFloats + i] = kVoigtSmall[i];
 }
 
 }  // namespace marfa
