@@ -89,12 +89,16 @@ def main():
     with open(out, "w") as f:
         f.write("// Generated by gen_voigt_tables.py: bivariate polynomial cells of the FP32 Voigt.\n")
         f.write(f"// {CORE_NX} core cells (Psi = Im F(x+iy)/y over x-width {CORE_W}, y^2 in [0,1]),\n")
-        f.write(f"// then {G_NX}x{G_NY} cells of K for y >= 1 ({G_WX} x {G_WY}), row-major [ix][iy].\n")
+        f.write(f"// then {G_NX}x{G_NY} cells of K for y >= 1 ({G_WX} x {G_WY}), row-major [ix][iy]; each cell padded\n"
+                "// with one zero to VOIGT_CELL_STRIDE floats (8-byte aligned rows).\n")
         f.write(f"// The includer defines MARFA_VOIGT_QUAL (storage qualifiers of the table).\n")
         f.write(f"#define VOIGT_DEG {DEG}\n#define VOIGT_NCELL {len(cells)}\n#define VOIGT_NPSI {CORE_NX}\n")
-        f.write("MARFA_VOIGT_QUAL float kVoigtCells[VOIGT_NCELL * (VOIGT_DEG + 1) * (VOIGT_DEG + 1)] = {\n")
+        stride = ((DEG + 1) ** 2 + 1) // 2 * 2
+        f.write(f"#define VOIGT_CELL_STRIDE {stride}\n")
+        f.write("MARFA_VOIGT_QUAL float kVoigtCells[VOIGT_NCELL * VOIGT_CELL_STRIDE] = {\n")
         for c in cells:
-            f.write("  " + ", ".join(f"{float(np.float32(v))!r}f" for v in c.ravel()) + ",\n")
+            pad = ", 0.0f" * (stride - (DEG + 1) ** 2)
+            f.write("  " + ", ".join(f"{float(np.float32(v))!r}f" for v in c.ravel()) + pad + ",\n")
         f.write("};\n")
         f.write(f"// {SMALL_NX} small-y cells (Psi over x-width {SMALL_W}, y^2 in [0, {SMALL_ETA}]),\n")
         f.write(f"// degree {SMALL_DX} in u and {SMALL_DV} in v = 2 y^2 / {SMALL_ETA} - 1, c[p][q] row-major.\n")

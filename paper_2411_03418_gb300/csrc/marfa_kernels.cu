@@ -1295,27 +1295,30 @@ __global__ void __launch_bounds__(kFineThreads)
   if (use_mlp) mlp_load_smem(S, R.mlp);
 #pragma unroll
   for (int q = 0; q < kFinePerThread; ++q) sAcc[warp][32 * q + lane] = sCmp[warp][32 * q + lane] = 0.0f;
-  __syncthreads();
   const int64_t kw = it.k0 + (int64_t)kWarpNodes * warp;  // first node of the warp
   const int64_t k0 = kw + kFinePerThread * lane;           // first node of the lane's output
   const int64_t cut = R.cut_fx;
   const LevelDev L = R.lev[lev];
+  const int wlo = (int)max(R.k_lo - kw, (int64_t)0);
+  const int whi = (int)min(R.k_hi - kw, (int64_t)(kWarpNodes - 1));
+  const int64_t Xa = kw << kFineShift, Xb = (kw + kWarpNodes - 1) << kFineShift;
+  // the warp's candidate bands, looked up before the barrier (global loads only), so
+  // that their latency overlaps the table copy
+  Bands bd;
+  bd.n = 0;
+  if (wlo <= whi) {  // warp-uniform
+    const int64_t P10 = int64_t(1) << panel_shift(kNGrid);
+    int64_t zlo[9], zhi[9];
+    const int nz = make_zones(Xa, Xb, (int64_t)R.R_w * step_fx(kNGrid), cut, wide ? P10 << 1 : P10,
+                              R.chi_req, zlo, zhi);
+    bd.lookup(R, L, zlo, zhi, nz);
+  }
+  __syncthreads();
   int64_t nev = 0, nmlp = 0, nnear = 0, nmid = 0, nsmall = 0;
   int qn = 0;  // entries in this warp's surrogate queue (warp-uniform)
   // surrogate results: the tag is the warp node
   auto fine_apply = [&](int tag, float v) { kahan_add(sAcc[warp][tag], sCmp[warp][tag], v); };
-  const int wlo = (int)max(R.k_lo - kw, (int64_t)0);
-  const int whi = (int)min(R.k_hi - kw, (int64_t)(kWarpNodes - 1));
   if (wlo <= whi) {  // warp-uniform
-    const int64_t Xa = kw << kFineShift, Xb = (kw + kWarpNodes - 1) << kFineShift;
-    const int64_t P10 = int64_t(1) << panel_shift(kNGrid);
-    Bands bd;
-    {
-      int64_t zlo[9], zhi[9];
-      const int nz = make_zones(Xa, Xb, (int64_t)R.R_w * step_fx(kNGrid), cut, wide ? P10 << 1 : P10,
-                                R.chi_req, zlo, zhi);
-      bd.lookup(R, L, zlo, zhi, nz);
-    }
     const int64_t pbase = kw >> 3;  // first G10 panel of the warp
     const int64_t lo_off = (int64_t)lev * R.n_lines;
     const bool physical = R.shape < kShapeConst;

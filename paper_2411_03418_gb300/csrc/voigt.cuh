@@ -17,7 +17,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
-#define MARFA_VOIGT_QUAL static __device__ const
+#define MARFA_VOIGT_QUAL static __device__ const __align__(16)
 #include "voigt_tables.inc"
 #undef MARFA_VOIGT_QUAL
 
@@ -68,77 +68,77 @@ __device__ __forceinline__ float voigt_asym(float x, float y) {
 }
 
 // One bivariate cell; tab is the coefficient table, either the global copy (read
-// through the read-only cache) or a copy a kernel placed in shared memory (SMEM).
-// In a shared copy the cells are padded to an even number of floats (81 -> 82) and read
-// as float2.
+// through the read-only cache) or a copy a kernel placed in shared memory (SMEM). Cells
+// are padded to an even number of floats (81 -> 82); the shared copy is read as float2
+// (vector loads through the read-only cache cost the global readers registers).
 constexpr int kVoigtCellFloats = (VOIGT_DEG + 1) * (VOIGT_DEG + 1);
-constexpr int kVoigtCellStride = (kVoigtCellFloats + 1) & ~1;
+constexpr int kVoigtCellStride = VOIGT_CELL_STRIDE;
+static_assert(kVoigtCellStride % 2 == 0 && kVoigtCellStride >= kVoigtCellFloats, "cell padding");
 
 template <bool SMEM>
 __device__ __forceinline__ float voigt_cell(const float* tab, int cell, float u, float v) {
-  if (SMEM) {
-    const float2* c2 = reinterpret_cast<const float2*>(tab + cell * kVoigtCellStride);
-    float acc = 0.0f, r = 0.0f;
-    // coefficient k = p (DEG + 1) + q, taken from k = 80 down to 0, two at a time
+  if (!SMEM) {  // global copy: scalar loads through the read-only cache
+    const float* c = tab + cell * kVoigtCellStride;
+    float acc = 0.0f;
 #pragma unroll
-    for (int i = kVoigtCellStride / 2 - 1; i >= 0; --i) {
-      const float2 t = c2[i];
+    for (int p = VOIGT_DEG; p >= 0; --p) {
+      float r = 0.0f;
 #pragma unroll
-      for (int h = 1; h >= 0; --h) {
-        const int k = 2 * i + h;
-        if (k >= kVoigtCellFloats) continue;
-        r = fmaf(r, v, h ? t.y : t.x);
-        if (k % (VOIGT_DEG + 1) == 0) {  // q = 0: row p done
-          acc = fmaf(acc, u, r);
-          r = 0.0f;
-        }
-      }
+      for (int q = VOIGT_DEG; q >= 0; --q) r = fmaf(r, v, __ldg(c + p * (VOIGT_DEG + 1) + q));
+      acc = fmaf(acc, u, r);
     }
     return acc;
   }
-  const float* c = tab + cell * kVoigtCellFloats;
-  float acc = 0.0f;
+  const float2* c2 = reinterpret_cast<const float2*>(tab + cell * kVoigtCellStride);
+  float acc = 0.0f, r = 0.0f;
+  // coefficient k = p (DEG + 1) + q of u^p v^q, taken from k = 80 down to 0, two at a time
 #pragma unroll
-  for (int p = VOIGT_DEG; p >= 0; --p) {
-    float r = 0.0f;
+  for (int i = kVoigtCellStride / 2 - 1; i >= 0; --i) {
+    const float2 t = c2[i];
 #pragma unroll
-    for (int q = VOIGT_DEG; q >= 0; --q) {
-      const int k = p * (VOIGT_DEG + 1) + q;
-      r = fmaf(r, v, __ldg(c + k));
+    for (int h = 1; h >= 0; --h) {
+      const int k = 2 * i + h;
+      if (k >= kVoigtCellFloats) continue;
+      r = fmaf(r, v, h ? t.y : t.x);
+      if (k % (VOIGT_DEG + 1) == 0) {  // q = 0: row p done
+        acc = fmaf(acc, u, r);
+        r = 0.0f;
+      }
     }
-    acc = fmaf(acc, u, r);
   }
   return acc;
 }
 
-// One small-y cell (degree VOIGT_SMALL_DX in u, VOIGT_SMALL_DV in v).
+// One small-y cell (degree VOIGT_SMALL_DX in u, VOIGT_SMALL_DV = 3 in v: one row of four
+// coefficients per power of u, read from a shared copy as two float2).
 template <bool SMEM>
 __device__ __forceinline__ float voigt_cell_small(const float* tab, int cell, float u, float v) {
-  constexpr int NQ = VOIGT_SMALL_DV + 1;
-  const float* c = tab + cell * (VOIGT_SMALL_DX + 1) * NQ;
-  if (SMEM && NQ == 4) {  // shared copy: two float2 per power of u
+  static_assert(VOIGT_SMALL_DV == 3, "four coefficients per row");
+  if (!SMEM) {  // global copy: scalar loads through the read-only cache
+    const float* c = tab + cell * (VOIGT_SMALL_DX + 1) * 4;
     float acc = 0.0f;
 #pragma unroll
     for (int p = VOIGT_SMALL_DX; p >= 0; --p) {
-      const float2 hi = reinterpret_cast<const float2*>(c)[2 * p + 1];
-      const float2 lo = reinterpret_cast<const float2*>(c)[2 * p];
-      acc = fmaf(acc, u, fmaf(fmaf(fmaf(hi.y, v, hi.x), v, lo.y), v, lo.x));
+      float r = 0.0f;
+#pragma unroll
+      for (int q = 3; q >= 0; --q) r = fmaf(r, v, __ldg(c + p * 4 + q));
+      acc = fmaf(acc, u, r);
     }
     return acc;
   }
+  const float2* c2 = reinterpret_cast<const float2*>(tab + cell * (VOIGT_SMALL_DX + 1) * 4);
   float acc = 0.0f;
 #pragma unroll
   for (int p = VOIGT_SMALL_DX; p >= 0; --p) {
-    float r = 0.0f;
-#pragma unroll
-    for (int q = VOIGT_SMALL_DV; q >= 0; --q) r = fmaf(r, v, SMEM ? c[p * NQ + q] : __ldg(c + p * NQ + q));
-    acc = fmaf(acc, u, r);
+    const float2 hi = c2[2 * p + 1];
+    const float2 lo = c2[2 * p];
+    acc = fmaf(acc, u, fmaf(fmaf(fmaf(hi.y, v, hi.x), v, lo.y), v, lo.x));
   }
   return acc;
 }
 
 // Floats of the large table; the small-y table follows it in a kernel's shared copy.
-constexpr int kVoigtBigFloats = VOIGT_NCELL * kVoigtCellStride;  // in a shared copy
+constexpr int kVoigtBigFloats = VOIGT_NCELL * kVoigtCellStride;
 
 // Far-wing form (|z| >= 100): two terms of the series, K = y/(sqrt(pi) r^2) (1 + (3x^2 - y^2)/(2 r^4)).
 __device__ __forceinline__ float voigt_far(float x, float y) {
@@ -216,16 +216,16 @@ __device__ __forceinline__ int voigt_class(float x, float y) {
 constexpr int kVoigtSmallFloats = VOIGT_SMALL_NX * (VOIGT_SMALL_DX + 1) * (VOIGT_SMALL_DV + 1);
 constexpr int kVoigtTableFloats = kVoigtBigFloats + kVoigtSmallFloats;
 
-// Copy both coefficient tables into shared memory, the large one with padded cells (all
-// threads of the block take part: warp w copies cells w, w + nwarps, ..., lane by lane;
-// then the small-y table). dst: 16-byte aligned.
+// Copy both coefficient tables into shared memory, in the global layout (all threads of
+// the block take part: warp w copies cells w, w + nwarps, ..., lane by lane; then the
+// small-y table). dst: 16-byte aligned.
 __device__ __forceinline__ void voigt_table_to_smem(float* dst) {
   const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int cell = threadIdx.x >> 5; cell < VOIGT_NCELL; cell += nw) {
-    const float* src = kVoigtCells + cell * kVoigtCellFloats;
+    const float* src = kVoigtCells + cell * kVoigtCellStride;
     float* d = dst + cell * kVoigtCellStride;
 #pragma unroll
-    for (int k = lane; k < kVoigtCellStride; k += 32) d[k] = k < kVoigtCellFloats ? src[k] : 0.0f;
+    for (int k = lane; k < kVoigtCellStride; k += 32) d[k] = src[k];
   }
   for (int i = threadIdx.x; i < kVoigtSmallFloats; i += blockDim.x) dst[kVoigtBigFloats + i] = kVoigtSmall[i];
 }
