@@ -49,7 +49,7 @@ FLOPS_FAR, FLOPS_MID, FLOPS_NEAR, FLOPS_SMALL = 20.0, 70.0, 200.0, 90.0
 # window, from single-pass ncu captures of the timed replay (dram__bytes_read.sum +
 # dram__bytes_write.sum; command and figures in profiles/traffic_dominant_kernels.md).
 # They belong to the kernels as built when captured; other windows report null.
-TRAFFIC_BYTES = {("venus", "finest"): 652.15e6 + 616.38e6,
+TRAFFIC_BYTES = {("venus", "finest"): 651.52e6 + 614.07e6,
                  ("earth", "finest"): 2.92e9 + 1.03e9,
                  ("batch", "grid1"): 4.22e9 + 24.49e6}
 N_SM = 152
