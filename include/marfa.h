@@ -375,6 +375,12 @@ int marfa_diag_absorption_counted_surrogate(const marfa_lines_t* lines,
                                             float* k_out, int64_t* counts,
                                             int64_t* surrogate_counts);
 
+/* The order marfa_prepare_lines gives the lines (host only, no device call): order[j] =
+ * the input index of the j-th line of a stable sort by nu0 (host array [n]; the identity
+ * when the input is already ordered). Errors: MARFA_E_INVAL (nu0 outside [0, 1e5]),
+ * MARFA_E_NOMEM. */
+int marfa_diag_line_order(const marfa_line_t* lines, int64_t n, int64_t* order);
+
 /* Issue rate of one instruction kind on this device, for the roofline denominators:
  * pipe 0 FP32 FMA, 1 MUFU ex2.approx, 2 MUFU rcp.approx, 3 MUFU cos.approx. Eight
  * 256-thread CTAs per SM run eight independent dependency chains a thread; five timed

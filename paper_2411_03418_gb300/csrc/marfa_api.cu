@@ -599,6 +599,33 @@ extern "C" int marfa_prepare_lines(const marfa_line_t* lines, int64_t n, const m
   return MARFA_OK;
 }
 
+extern "C" int marfa_diag_line_order(const marfa_line_t* lines, int64_t n, int64_t* order) {
+  if (!lines || !order || n < 1 || n > (int64_t)1 << 31) return fail(MARFA_E_INVAL, "bad arguments");
+  std::vector<int64_t> key;
+  try {
+    key.resize(n);
+  } catch (...) {
+    return fail(MARFA_E_NOMEM, "host allocation failed");
+  }
+  int64_t kmin = INT64_MAX, kmax = INT64_MIN;
+  bool sorted = true;
+  for (int64_t i = 0; i < n; ++i) {
+    const double v = lines[i].nu0;
+    if (!std::isfinite(v) || v < 0 || v > 1e5)
+      return fail(MARFA_E_INVAL, "line %lld: nu0 must be in [0, 1e5]", (long long)i);
+    key[i] = rint_fix(v);
+    kmin = std::min(kmin, key[i]);
+    kmax = std::max(kmax, key[i]);
+    if (i > 0 && v < lines[i - 1].nu0) sorted = false;
+  }
+  if (sorted) {
+    for (int64_t i = 0; i < n; ++i) order[i] = i;
+    return MARFA_OK;
+  }
+  if (!sort_by_nu0(lines, key.data(), n, kmin, kmax, order)) return fail(MARFA_E_NOMEM, "host allocation failed");
+  return MARFA_OK;
+}
+
 extern "C" int64_t marfa_num_points(double nu_lo, double nu_hi) {
   if (!std::isfinite(nu_lo) || !std::isfinite(nu_hi) || nu_lo < 0 || nu_hi < 0 || nu_hi > 1e5)
     return MARFA_E_INVAL;

@@ -47,7 +47,7 @@ EXPORTS = ["marfa_prepare_lines", "marfa_free_lines", "marfa_num_points", "marfa
            "marfa_mlp_train", "marfa_surrogate_load", "marfa_surrogate_unload", "marfa_surrogate_eval",
            "marfa_diag_absorption_counted_surrogate", "marfa_plan_create", "marfa_plan_execute",
            "marfa_plan_info", "marfa_plan_destroy", "marfa_diag_absorption_counts", "marfa_read_par",
-           "marfa_diag_pipe_rate"]
+           "marfa_diag_pipe_rate", "marfa_diag_line_order"]
 
 MLP_PARAMS = 8577
 MLP_MAX_BATCH = 65536
@@ -88,6 +88,7 @@ def load(path: str | None = None):
         "marfa_diag_absorption_counted": (C.c_int, [vp, vp, vp, i32, vp, vp, vp]),
         "marfa_diag_kernel_timing": (C.c_int, [i32, vp, vp]),
         "marfa_diag_pipe_rate": (C.c_int, [i32, vp]),
+        "marfa_diag_line_order": (C.c_int, [vp, i64, vp]),
         "marfa_absorption_noalloc": (C.c_int, [vp, vp, vp, i32, vp, vp, vp]),
         "marfa_mlp_loss_grad": (C.c_int, [vp, vp, vp, vp, i64, i32, vp, vp]),
         "marfa_mlp_train": (C.c_int, [vp, vp, vp, vp, i64, vp, vp]),
@@ -409,6 +410,14 @@ def marfa_diag_kernel_timing(enable: bool):
 
 
 PIPES = {"fma": 0, "ex2": 1, "rcp": 2, "cos": 3}
+
+
+def marfa_diag_line_order(lines: np.ndarray) -> np.ndarray:
+    """The prepared order of a line list (input index of each sorted line), host only."""
+    lines = np.ascontiguousarray(lines, dtype=LINE_DTYPE)
+    order = np.empty(len(lines), dtype=np.int64)
+    _check(load().marfa_diag_line_order(_ptr(lines), len(lines), _ptr(order)))
+    return order
 
 
 def marfa_diag_pipe_rate(pipe: str) -> float:

@@ -197,3 +197,24 @@ def test_pipe_rate_rejects_bad_arguments(M):
         with pytest.raises(M.MarfaError) as e:
             M._check(M.load().marfa_diag_pipe_rate(pipe, out))
         assert e.value.code == -1
+
+
+@pytest.mark.parametrize("kind", ["uniform", "ties", "sub_unit", "crowded", "extremes", "sorted", "reversed"])
+def test_line_order_is_the_stable_sort_by_nu0(M, kind):
+    """The host sort behind marfa_prepare_lines (chunked on the worker pool) equals a
+    stable sort by nu0, on inputs that stress its buckets."""
+    rng = np.random.default_rng(11)
+    n = 300_007
+    nu = {
+        "uniform": 500.0 + 9000.0 * rng.random(n),
+        "ties": 2000.0 + np.floor(rng.random(n) * 40) / 8,
+        "sub_unit": 1000.0 + 1e-13 * np.floor(rng.random(n) * 300),   # closer than 2^-43 cm^-1
+        "crowded": np.where(rng.random(n) < 0.9, 2300.0 + 1e-3 * rng.random(n), 100.0 + 9e4 * rng.random(n)),
+        "extremes": rng.choice(np.array([0.0, -0.0, 1e5, 5e4]), n),
+        "sorted": np.sort(500.0 + 9000.0 * rng.random(n)),
+        "reversed": np.sort(500.0 + 9000.0 * rng.random(n))[::-1].copy(),
+    }[kind]
+    lines = np.zeros(n, dtype=M.LINE_DTYPE)
+    lines["nu0"] = nu
+    order = M.marfa_diag_line_order(lines)
+    assert np.array_equal(order, np.argsort(nu, kind="stable"))
