@@ -768,15 +768,18 @@ __global__ void __launch_bounds__(kLWarps * 32, SURR ? 3 : (PAIRS == 16 ? 7 : 4)
   }
   const LevelDev L = R.lev[lev];
   Bands bd;
+  bd.n = 0;
   {
-    // the span of the parent grid's panels over the tile, widened by one of them
+    // the span of the parent grid's panels over the tile's panels inside the window,
+    // widened by one of them
+    const int64_t pa = max(base, m_first), pb = min(base + nb - 1, m_last);
     const int al = wide ? s + 2 : s + 1;  // parent panels: two (four) steps of grid g - 1
     const int64_t P = int64_t(1) << (wide ? s + 2 : s);
-    const int64_t A = fl_sh(base << s, al) << al;
-    const int64_t B = (fl_sh((base + nb - 1) << s, al) + 1) << al;
+    const int64_t A = fl_sh(pa << s, al) << al;
+    const int64_t B = (fl_sh(pb << s, al) + 1) << al;
     int64_t zlo[9], zhi[9];
     const int nz = make_zones(A, B, (int64_t)R.R_w * step_fx(g - 1), cut, P, R.chi_req, zlo, zhi);
-    bd.lookup(R, L, zlo, zhi, nz);
+    if (pa <= pb) bd.lookup(R, L, zlo, zhi, nz);
   }
   const int64_t lo_off = (int64_t)lev * R.n_lines;
   const int64_t X0 = m0 << s;  // position of node 2 m0 (j = 0)
@@ -1056,15 +1059,18 @@ __global__ void __launch_bounds__(kCWarps * 32, SURR ? 3 : 6)
     if (wide) fr.ok = false;
     const LevelDev L = R.lev[lev];
     Bands bd;
+    bd.n = 0;
     {
-      // the span of the parent grid's panels over the tile, widened by one of them
+      // the span of the parent grid's panels over the tile's panels inside the window,
+      // widened by one of them
+      const int64_t pa = max(base, m_first), pb = min(base + nb - 1, m_last);
       const int al = wide ? s + 2 : s + 1;  // parent panels: two (four) steps of grid g - 1
       const int64_t P = int64_t(1) << (wide ? s + 2 : s);
-      const int64_t A = fl_sh(base << s, al) << al;
-      const int64_t B = (fl_sh((base + nb - 1) << s, al) + 1) << al;
+      const int64_t A = fl_sh(pa << s, al) << al;
+      const int64_t B = (fl_sh(pb << s, al) + 1) << al;
       int64_t zlo[9], zhi[9];
       const int nz = make_zones(A, B, (int64_t)R.R_w * step_fx(g - 1), cut, P, R.chi_req, zlo, zhi);
-      bd.lookup(R, L, zlo, zhi, nz);
+      if (pa <= pb) bd.lookup(R, L, zlo, zhi, nz);
     }
     const int64_t lo_off = (int64_t)lev * R.n_lines;
     const int64_t X0 = m0 << s;  // position of node 2 m0 (j = 0)
@@ -1307,10 +1313,11 @@ __global__ void __launch_bounds__(kFineThreads)
   Bands bd;
   bd.n = 0;
   if (wlo <= whi) {  // warp-uniform
+    // the span of the warp's nodes inside the window
     const int64_t P10 = int64_t(1) << panel_shift(kNGrid);
     int64_t zlo[9], zhi[9];
-    const int nz = make_zones(Xa, Xb, (int64_t)R.R_w * step_fx(kNGrid), cut, wide ? P10 << 1 : P10,
-                              R.chi_req, zlo, zhi);
+    const int nz = make_zones((kw + wlo) << kFineShift, (kw + whi) << kFineShift, (int64_t)R.R_w * step_fx(kNGrid),
+                              cut, wide ? P10 << 1 : P10, R.chi_req, zlo, zhi);
     bd.lookup(R, L, zlo, zhi, nz);
   }
   __syncthreads();
