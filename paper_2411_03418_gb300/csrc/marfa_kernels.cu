@@ -534,153 +534,197 @@ __global__ void __launch_bounds__(kG1Warps * 32)
   const bool voigt = R.shape == kShapeVoigt;
   const bool physical = R.shape < kShapeConst;
 
-  const int p = lane, j0 = 2 * p;
-  const float f0 = (float)j0, f1 = (float)(j0 + 1);
-  const float rR0 = expf(-0.027f * f0), rR1 = expf(-0.027f * f1);
-  const float rL0 = expf(0.027f * f0), rL1 = expf(0.027f * f1);
+  // Lane mapping. Normally lane = pair and a warp takes one staged line at a time. A
+  // request whose window covers at most 8 pairs of the tile (the rest of the lanes would
+  // idle) takes 4 lines at a time instead: lane = (line slot lane / 8, pair pw0 + lane % 8);
+  // the four slots' sums are merged before the per-warp reduction.
+  const int64_t bw0 = max(m_first - base, (int64_t)0), bw1 = min(m_last - base, (int64_t)(nb - 1));
+  const int pw0 = (int)max(bw0 - 1, (int64_t)0), pw1 = (int)min(bw1, (int64_t)(kG1Pairs - 1));
+  const bool narrow = !use_mlp && pw1 - pw0 < 8;  // block-uniform
   float eS = 0.f, eC = 0.f, lS = 0.f, lC = 0.f, rS = 0.f, rC = 0.f, mS = 0.f, mC = 0.f;
   int64_t nev = 0, nmlp = 0, nnear = 0, nmid = 0, nsmall = 0;
   if (use_mlp) __syncthreads();
   int qn = 0;  // entries in this warp's surrogate queue (warp-uniform)
 
-  for (int64_t b0 = i_lo; b0 < i_hi; b0 += kG1Batch) {
-    const int nbat = (int)min((int64_t)kG1Batch, i_hi - b0);
-    __syncthreads();
-    for (int k = tid; k < nbat; k += kG1Warps * 32) {
-      const int64_t o = off + b0 + k;
-      const int64_t c = __ldg(R.c + o);
-      const int gst = __ldg(R.gstar + o);
-      const bool chi = __ldg(R.flags + o) & 1;
-      // acceptance panels: two steps of grid 1, or four in the 5-point variant
-      const uint64_t msk = accept_mask_s<uint64_t>(1, c, gst, chi, cut, R.R_w, base, nb, s + wide, s) & win;
-      const float amp = __ldg(R.amp + o), sx = __ldg(R.sx + o), y = __ldg(R.yv + o);
-      NodeX nx;
-      nx.init(X0 - c, s - 1, sx);
-      // distance from the centre to the nearest node of the owned panels (bit b <-> panel
-      // base + b, nodes 2(base + b) .. 2(base + b) + 2): the owned panels nearest to c
-      // below and above it bound it from below
-      int64_t dn = 0;
-      if (msk) {
-        const int64_t pc = fl_sh(c, s) - base;  // panel holding c, relative to base
-        const uint64_t below = pc <= 0 ? 0ull : (pc >= nb ? msk : msk & ((1ull << pc) - 1ull));
-        const uint64_t above = pc < 0 ? msk : (pc >= nb - 1 ? 0ull : msk & ~((2ull << pc) - 1ull));
-        const bool inside = pc >= 0 && pc < nb && ((msk >> pc) & 1ull);
-        int64_t d1 = INT64_MAX, d2 = INT64_MAX;
-        if (below) d1 = c - ((base + (63 - __clzll((long long)below)) + 1) << s);  // end of that panel
-        if (above) d2 = ((base + (__ffsll((long long)above) - 1)) << s) - c;       // start of that panel
-        dn = inside ? 0 : min(d1, d2);
-      }
-      const bool far = voigt && (__ll2float_rn(dn) * ldexpf(1.0f, -kFixBits) * sx >= 100.0f || y >= 100.0f);
-      int jL = -(1 << 30), jR = 1 << 30;
-      bool exact = !far;
-      const float aC = amp * y * kInvSqrtPi;
-      float aL = aC, aR = aC;
-      if (chi && physical) {
-        jR = clamp32(cl_sh(c + chi_break_fx(0) - X0, s - 1));
-        jL = clamp32(fl_sh(c - chi_break_fx(0) - X0, s - 1));
-        if (cut > chi_break_fx(1)) {  // owned nodes may lie beyond 150 cm^-1 (branches 2, 3)
-          const int jR150 = clamp32(fl_sh(c + chi_break_fx(1) - X0, s - 1));
-          const int jL150 = clamp32(cl_sh(c - chi_break_fx(1) - X0, s - 1));
-          if (jR150 < 2 * kG1Pairs - 1 || jL150 > 0) exact = true;
+  // the sums over the candidate lines, compiled once for each lane mapping
+  auto sum_lines = [&](auto narrow_tag) {
+    constexpr bool NARROW = decltype(narrow_tag)::value;
+    constexpr int n_slot = NARROW ? 4 : 1;
+    const int slot = NARROW ? lane >> 3 : 0;
+    const int p = NARROW ? pw0 + (lane & 7) : lane, j0 = 2 * p;
+    const float f0 = (float)j0, f1 = (float)(j0 + 1);
+    const float rR0 = expf(-0.027f * f0), rR1 = expf(-0.027f * f1);
+    const float rL0 = expf(0.027f * f0), rL1 = expf(0.027f * f1);
+    for (int64_t b0 = i_lo; b0 < i_hi; b0 += kG1Batch) {
+      const int nbat = (int)min((int64_t)kG1Batch, i_hi - b0);
+      __syncthreads();
+      for (int k = tid; k < nbat; k += kG1Warps * 32) {
+        const int64_t o = off + b0 + k;
+        const int64_t c = __ldg(R.c + o);
+        const int gst = __ldg(R.gstar + o);
+        const bool chi = __ldg(R.flags + o) & 1;
+        // acceptance panels: two steps of grid 1, or four in the 5-point variant
+        const uint64_t msk = accept_mask_s<uint64_t>(1, c, gst, chi, cut, R.R_w, base, nb, s + wide, s) & win;
+        const float amp = __ldg(R.amp + o), sx = __ldg(R.sx + o), y = __ldg(R.yv + o);
+        NodeX nx;
+        nx.init(X0 - c, s - 1, sx);
+        // distance from the centre to the nearest node of the owned panels (bit b <-> panel
+        // base + b, nodes 2(base + b) .. 2(base + b) + 2): the owned panels nearest to c
+        // below and above it bound it from below
+        int64_t dn = 0;
+        if (msk) {
+          const int64_t pc = fl_sh(c, s) - base;  // panel holding c, relative to base
+          const uint64_t below = pc <= 0 ? 0ull : (pc >= nb ? msk : msk & ((1ull << pc) - 1ull));
+          const uint64_t above = pc < 0 ? msk : (pc >= nb - 1 ? 0ull : msk & ~((2ull << pc) - 1ull));
+          const bool inside = pc >= 0 && pc < nb && ((msk >> pc) & 1ull);
+          int64_t d1 = INT64_MAX, d2 = INT64_MAX;
+          if (below) d1 = c - ((base + (63 - __clzll((long long)below)) + 1) << s);  // end of that panel
+          if (above) d2 = ((base + (__ffsll((long long)above) - 1)) << s) - c;       // start of that panel
+          dn = inside ? 0 : min(d1, d2);
         }
-        const float d0 = (nx.qf + nx.phi);  // offset of node 0 from the centre, cm^-1
-        aR = aC * 1.084f * expf(-0.027f * d0);
-        aL = aC * 1.084f * expf(0.027f * d0);
-      }
-      // fast-path flags: bit 0 exact path; bit 1 the line owns every panel of the tile;
-      // bits 2-3 the chi side of all evaluated nodes (1 left, 2 right, 0 centre/mixed)
-      int fl = exact ? 1 : 0;
-      if (jL >= 2 * kG1Pairs - 1) fl |= 4;        // every node at d <= -3
-      else if (jR <= 0) fl |= 8;                  // every node at d >= 3
-      const bool one_side = !(chi && physical) || (fl & 12);
-      if (msk == full_tile && one_side) fl |= 2;
-      sA[k] = make_float4(nx.qf, nx.hs, nx.phs, y * y);
-      sB[k] = make_float4(aC, aL, aR, -0.5f * y * y);
-      sM[k] = msk;
-      sC[k] = make_int4(jL, jR, fl, 0);
-    }
-    __syncthreads();
-    float pe = 0.f, pl = 0.f, pr = 0.f, pm = 0.f;
-    // surrogate results: tag bit 0 odd node; bits 1, 2 the even node's L and R slots
-    auto g1_apply = [&](int tag, float v) {
-      if (tag & 1) pm += v;
-      else if ((tag & 6) == 6) pe += v;
-      else if (tag & 2) pl += v;
-      else pr += v;
-    };
-    for (int k = warp; k < nbat; k += kG1Warps) {
-      const int4 C = sC[k];
-      if ((C.z & 3) == 2) {
-        // the line owns the whole tile through the far wing, on one chi side or with no chi
-        const float4 a = sA[k], b = sB[k];
-        const bool right = C.z & 8, left = C.z & 4;
-        const float a0 = right ? b.z * rR0 : (left ? b.y * rL0 : b.x);
-        const float a1 = right ? b.z * rR1 : (left ? b.y * rL1 : b.x);
-        const float x0 = fmaf(f0 + a.x, a.y, a.z), x02 = x0 * x0;
-        const float i0 = __fdividef(1.0f, x02 + a.w);
-        const float x1 = fmaf(f1 + a.x, a.y, a.z), x12 = x1 * x1;
-        const float i1 = __fdividef(1.0f, x12 + a.w);
-        pe += a0 * i0 * fmaf(fmaf(1.5f, x02, b.w), i0 * i0, 1.0f);
-        pm += a1 * i1 * fmaf(fmaf(1.5f, x12, b.w), i1 * i1, 1.0f);
-        if (COUNT) nev += 2;
-        continue;
-      }
-      const uint64_t msk = sM[k];
-      const bool bL = (msk >> (p + 1)) & 1ull;  // panel m0+p: L of node 2m, M of node 2m+1
-      const bool bR = (msk >> p) & 1ull;        // panel m0+p-1: R of node 2m
-      if (SURR && use_mlp && (C.z & 1)) {  // exact path, warp-uniform: every lane takes part
-        if (qn > kQCap - 64) q_flush(warp_queue(dsm), qn, S, g1_apply);
-        const G1Nodes nd = g1_exact_nodes(R, off + b0 + k, X0, j0);
-        const bool a0 = bL || bR, a1 = bL;
-        const bool u0 = a0 && mlp_guard(S, nd.x0, nd.y), u1 = a1 && mlp_guard(S, nd.x1, nd.y);
-        q_push(warp_queue(dsm), qn, u0, nd.x0, nd.y, nd.w0, (bL ? 2 : 0) | (bR ? 4 : 0));
-        q_push(warp_queue(dsm), qn, u1, nd.x1, nd.y, nd.w1, 1);
-        if (a0 && !u0) g1_apply((bL ? 2 : 0) | (bR ? 4 : 0), nd.w0 * voigt_K(nd.x0, nd.y));
-        if (a1 && !u1) g1_apply(1, nd.w1 * voigt_K(nd.x1, nd.y));
-        if (a0) count_eval<COUNT>(true, nd.x0, nd.y, nev, nnear, nmid, nsmall);
-        if (a1) count_eval<COUNT>(true, nd.x1, nd.y, nev, nnear, nmid, nsmall);
-        if (COUNT) nmlp += (u0 ? 1 : 0) + (u1 ? 1 : 0);
-        continue;
-      }
-      if (!(bL || bR)) continue;
-      float v0, v1;
-      if (!(C.z & 1)) {
-        const float4 a = sA[k], b = sB[k];
-        const float x0 = fmaf(f0 + a.x, a.y, a.z), x02 = x0 * x0;
-        const float i0 = __fdividef(1.0f, x02 + a.w);
-        const float s0 = fmaf(fmaf(1.5f, x02, b.w), i0 * i0, 1.0f);
-        const float am0 = j0 >= C.y ? b.z * rR0 : (j0 <= C.x ? b.y * rL0 : b.x);
-        v0 = am0 * i0 * s0;
-        const float x1 = fmaf(f1 + a.x, a.y, a.z), x12 = x1 * x1;
-        const float i1 = __fdividef(1.0f, x12 + a.w);
-        const float s1 = fmaf(fmaf(1.5f, x12, b.w), i1 * i1, 1.0f);
-        const float am1 = j0 + 1 >= C.y ? b.z * rR1 : (j0 + 1 <= C.x ? b.y * rL1 : b.x);
-        v1 = bL ? am1 * i1 * s1 : 0.0f;
-      } else {
-        int nn = 0, nm = 0, ns = 0;
-        const float2 v = g1_exact_pair(R, off + b0 + k, X0, j0, true, bL, nn, nm, ns);
-        v0 = v.x;
-        v1 = v.y;
-        if (COUNT) {
-          nnear += nn;
-          nmid += nm;
-          nsmall += ns;
+        const bool far = voigt && (__ll2float_rn(dn) * ldexpf(1.0f, -kFixBits) * sx >= 100.0f || y >= 100.0f);
+        int jL = -(1 << 30), jR = 1 << 30;
+        bool exact = !far;
+        const float aC = amp * y * kInvSqrtPi;
+        float aL = aC, aR = aC;
+        if (chi && physical) {
+          jR = clamp32(cl_sh(c + chi_break_fx(0) - X0, s - 1));
+          jL = clamp32(fl_sh(c - chi_break_fx(0) - X0, s - 1));
+          if (cut > chi_break_fx(1)) {  // owned nodes may lie beyond 150 cm^-1 (branches 2, 3)
+            const int jR150 = clamp32(fl_sh(c + chi_break_fx(1) - X0, s - 1));
+            const int jL150 = clamp32(cl_sh(c - chi_break_fx(1) - X0, s - 1));
+            if (jR150 < 2 * kG1Pairs - 1 || jL150 > 0) exact = true;
+          }
+          const float d0 = (nx.qf + nx.phi);  // offset of node 0 from the centre, cm^-1
+          aR = aC * 1.084f * expf(-0.027f * d0);
+          aL = aC * 1.084f * expf(0.027f * d0);
         }
+        // fast-path flags: bit 0 exact path; bit 1 the line owns every panel of the tile;
+        // bits 2-3 the chi side of all evaluated nodes (1 left, 2 right, 0 centre/mixed)
+        int fl = exact ? 1 : 0;
+        if (jL >= 2 * kG1Pairs - 1) fl |= 4;        // every node at d <= -3
+        else if (jR <= 0) fl |= 8;                  // every node at d >= 3
+        const bool one_side = !(chi && physical) || (fl & 12);
+        if (msk == full_tile && one_side) fl |= 2;
+        sA[k] = make_float4(nx.qf, nx.hs, nx.phs, y * y);
+        sB[k] = make_float4(aC, aL, aR, -0.5f * y * y);
+        sM[k] = msk;
+        sC[k] = make_int4(jL, jR, fl, 0);
       }
-      if (bL && bR) pe += v0; else if (bL) pl += v0; else pr += v0;
-      pm += v1;
-      if (COUNT) nev += 1 + (bL ? 1 : 0);
+      __syncthreads();
+      float pe = 0.f, pl = 0.f, pr = 0.f, pm = 0.f;
+      // surrogate results: tag bit 0 odd node; bits 1, 2 the even node's L and R slots
+      auto g1_apply = [&](int tag, float v) {
+        if (tag & 1) pm += v;
+        else if ((tag & 6) == 6) pe += v;
+        else if (tag & 2) pl += v;
+        else pr += v;
+      };
+      for (int k = warp * n_slot + slot; k < nbat; k += kG1Warps * n_slot) {
+        const int4 C = sC[k];
+        if ((C.z & 3) == 2) {
+          // the line owns the whole tile through the far wing, on one chi side or with no chi
+          const float4 a = sA[k], b = sB[k];
+          const bool right = C.z & 8, left = C.z & 4;
+          const float a0 = right ? b.z * rR0 : (left ? b.y * rL0 : b.x);
+          const float a1 = right ? b.z * rR1 : (left ? b.y * rL1 : b.x);
+          const float x0 = fmaf(f0 + a.x, a.y, a.z), x02 = x0 * x0;
+          const float i0 = __fdividef(1.0f, x02 + a.w);
+          const float x1 = fmaf(f1 + a.x, a.y, a.z), x12 = x1 * x1;
+          const float i1 = __fdividef(1.0f, x12 + a.w);
+          pe += a0 * i0 * fmaf(fmaf(1.5f, x02, b.w), i0 * i0, 1.0f);
+          pm += a1 * i1 * fmaf(fmaf(1.5f, x12, b.w), i1 * i1, 1.0f);
+          if (COUNT) nev += 2;
+          continue;
+        }
+        const uint64_t msk = sM[k];
+        const bool bL = (msk >> (p + 1)) & 1ull;  // panel m0+p: L of node 2m, M of node 2m+1
+        const bool bR = (msk >> p) & 1ull;        // panel m0+p-1: R of node 2m
+        if (SURR && use_mlp && (C.z & 1)) {  // exact path, warp-uniform: every lane takes part
+          if (qn > kQCap - 64) q_flush(warp_queue(dsm), qn, S, g1_apply);
+          const G1Nodes nd = g1_exact_nodes(R, off + b0 + k, X0, j0);
+          const bool a0 = bL || bR, a1 = bL;
+          const bool u0 = a0 && mlp_guard(S, nd.x0, nd.y), u1 = a1 && mlp_guard(S, nd.x1, nd.y);
+          q_push(warp_queue(dsm), qn, u0, nd.x0, nd.y, nd.w0, (bL ? 2 : 0) | (bR ? 4 : 0));
+          q_push(warp_queue(dsm), qn, u1, nd.x1, nd.y, nd.w1, 1);
+          if (a0 && !u0) g1_apply((bL ? 2 : 0) | (bR ? 4 : 0), nd.w0 * voigt_K(nd.x0, nd.y));
+          if (a1 && !u1) g1_apply(1, nd.w1 * voigt_K(nd.x1, nd.y));
+          if (a0) count_eval<COUNT>(true, nd.x0, nd.y, nev, nnear, nmid, nsmall);
+          if (a1) count_eval<COUNT>(true, nd.x1, nd.y, nev, nnear, nmid, nsmall);
+          if (COUNT) nmlp += (u0 ? 1 : 0) + (u1 ? 1 : 0);
+          continue;
+        }
+        if (!(bL || bR)) continue;
+        float v0, v1;
+        if (!(C.z & 1)) {
+          const float4 a = sA[k], b = sB[k];
+          const float x0 = fmaf(f0 + a.x, a.y, a.z), x02 = x0 * x0;
+          const float i0 = __fdividef(1.0f, x02 + a.w);
+          const float s0 = fmaf(fmaf(1.5f, x02, b.w), i0 * i0, 1.0f);
+          const float am0 = j0 >= C.y ? b.z * rR0 : (j0 <= C.x ? b.y * rL0 : b.x);
+          v0 = am0 * i0 * s0;
+          const float x1 = fmaf(f1 + a.x, a.y, a.z), x12 = x1 * x1;
+          const float i1 = __fdividef(1.0f, x12 + a.w);
+          const float s1 = fmaf(fmaf(1.5f, x12, b.w), i1 * i1, 1.0f);
+          const float am1 = j0 + 1 >= C.y ? b.z * rR1 : (j0 + 1 <= C.x ? b.y * rL1 : b.x);
+          v1 = bL ? am1 * i1 * s1 : 0.0f;
+        } else {
+          int nn = 0, nm = 0, ns = 0;
+          const float2 v = g1_exact_pair(R, off + b0 + k, X0, j0, true, bL, nn, nm, ns);
+          v0 = v.x;
+          v1 = v.y;
+          if (COUNT) {
+            nnear += nn;
+            nmid += nm;
+            nsmall += ns;
+          }
+        }
+        if (bL && bR) pe += v0; else if (bL) pl += v0; else pr += v0;
+        pm += v1;
+        if (COUNT) nev += 1 + (bL ? 1 : 0);
+      }
+      if (SURR && use_mlp) q_flush(warp_queue(dsm), qn, S, g1_apply);
+      kahan_add(eS, eC, pe);
+      kahan_add(lS, lC, pl);
+      kahan_add(rS, rC, pr);
+      kahan_add(mS, mC, pm);
     }
-    if (SURR && use_mlp) q_flush(warp_queue(dsm), qn, S, g1_apply);
-    kahan_add(eS, eC, pe);
-    kahan_add(lS, lC, pl);
-    kahan_add(rS, rC, pr);
-    kahan_add(mS, mC, pm);
+  };
+  if (narrow)
+    sum_lines(std::true_type{});
+  else
+    sum_lines(std::false_type{});
+  const int slot = narrow ? lane >> 3 : 0;
+  const int p = narrow ? pw0 + (lane & 7) : lane;
+  if (narrow) {
+    // merge the four line slots of each pair (slots 0 + 1 and 2 + 3, then the two), and
+    // leave the pairs' sums at their own lanes
+#pragma unroll
+    for (int d = 8; d <= 16; d <<= 1) {
+      float o0 = __shfl_xor_sync(0xffffffffu, eS, d), o1 = __shfl_xor_sync(0xffffffffu, eC, d);
+      comp_merge(eS, eC, o0, o1);
+      o0 = __shfl_xor_sync(0xffffffffu, lS, d), o1 = __shfl_xor_sync(0xffffffffu, lC, d);
+      comp_merge(lS, lC, o0, o1);
+      o0 = __shfl_xor_sync(0xffffffffu, rS, d), o1 = __shfl_xor_sync(0xffffffffu, rC, d);
+      comp_merge(rS, rC, o0, o1);
+      o0 = __shfl_xor_sync(0xffffffffu, mS, d), o1 = __shfl_xor_sync(0xffffffffu, mC, d);
+      comp_merge(mS, mC, o0, o1);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) sRed[warp][q][lane] = 0.0f;
+    __syncwarp();
+    if (slot == 0 && p <= pw1) {
+      sRed[warp][0][p] = eS; sRed[warp][1][p] = eC;
+      sRed[warp][2][p] = lS; sRed[warp][3][p] = lC;
+      sRed[warp][4][p] = rS; sRed[warp][5][p] = rC;
+      sRed[warp][6][p] = mS; sRed[warp][7][p] = mC;
+    }
+  } else {
+    sRed[warp][0][lane] = eS; sRed[warp][1][lane] = eC;
+    sRed[warp][2][lane] = lS; sRed[warp][3][lane] = lC;
+    sRed[warp][4][lane] = rS; sRed[warp][5][lane] = rC;
+    sRed[warp][6][lane] = mS; sRed[warp][7][lane] = mC;
   }
-  sRed[warp][0][lane] = eS; sRed[warp][1][lane] = eC;
-  sRed[warp][2][lane] = lS; sRed[warp][3][lane] = lC;
-  sRed[warp][4][lane] = rS; sRed[warp][5][lane] = rC;
-  sRed[warp][6][lane] = mS; sRed[warp][7][lane] = mC;
   __syncthreads();
   if (warp == 0) {
     float a[8];
@@ -697,7 +741,7 @@ __global__ void __launch_bounds__(kG1Warps * 32)
     comp_merge(rs, rc, a[4], a[5]);
     const int64_t np = R.npan[1];
     float* gp = R.slots + (int64_t)lev * R.slots_per_level + R.slot_off[1] + 3 * np * it.part;
-    const int64_t m = m0 + p;
+    const int64_t m = m0 + lane;  // this lane's pair
     if (m <= m_last) {
       gp[m - m_first] = ls + lc;
       gp[np + (m - m_first)] = a[6] + a[7];
