@@ -49,9 +49,9 @@ FLOPS_FAR, FLOPS_MID, FLOPS_NEAR, FLOPS_SMALL = 20.0, 70.0, 200.0, 90.0
 # window, from single-pass ncu captures of the timed replay (dram__bytes_read.sum +
 # dram__bytes_write.sum; command and figures in profiles/traffic_dominant_kernels.md).
 # They belong to the kernels as built when captured; other windows report null.
-TRAFFIC_BYTES = {("venus", "finest"): 651.52e6 + 614.07e6,
+TRAFFIC_BYTES = {("venus", "finest"): 652.63e6 + 614.32e6,
                  ("earth", "finest"): 2.92e9 + 1.03e9,
-                 ("batch", "grid1"): 4.22e9 + 24.49e6}
+                 ("batch", "finest"): 1.95e9 + 1.24e9}
 N_SM = 152
 FP32_LANES = 128
 
