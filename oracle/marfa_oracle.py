@@ -13,6 +13,8 @@ What it computes, in the paper's order and notation:
   HITRAN's definitions; written out in ``level_params``).
 * Sec. 2.2, Eqs. (4)-(8): Lorentz, Gauss and Voigt shapes; K(x, y) = Re w(x + iy)
   with w the Faddeeva function (``scipy.special.wofz`` serves as the library step).
+* Appendix C: the paper's own fast Voigt (Lorentz wing beyond |x| = 15, a region-4
+  asymptote, Humlicek's rational approximations elsewhere), ``voigt_K_paper``.
 * Sec. 2.3, Eqs. (9)-(10): the Tonkov chi-factor.
 * Sec. 2.4: the eleven-grid scheme (10 coarse grids + the 2^-11 cm^-1 finest grid,
   quadratic 3-point interpolation onto the finest grid), under the partition reading
@@ -183,6 +185,43 @@ def chi_tonkov(d_fx) -> np.ndarray:
     return out
 
 
+# Humlicek (1982) rational approximations of w(z) = exp(-z^2) erfc(-iz) in t = y - i x, for
+# regions I (|x| + y >= 15), II (5.5 <= |x| + y < 15) and III (|x| + y < 5.5); Kuntz (1997)
+# evaluates the same rational functions' real parts in real arithmetic.
+def _humlicek_w(region: int, t):
+    if region == 1:
+        return t * 0.5641896 / (0.5 + t * t)
+    if region == 2:
+        u = t * t
+        return t * (1.410474 + u * 0.5641896) / (0.75 + u * (3.0 + u))
+    num = 16.4955 + t * (20.20933 + t * (11.96482 + t * (3.778987 + t * 0.5642236)))
+    den = 16.4955 + t * (38.82363 + t * (39.27121 + t * (21.69274 + t * (6.699398 + t))))
+    return num / den
+
+
+def voigt_K_paper(x, y):
+    """K(x, y) as the paper's Appendix C computes it (its "fast" Voigt): the Lorentz wing
+    y / (sqrt(pi) (x^2 + y^2)) for |x| > 15; in region 4 = {y < 0.02, 1 < |x| < 5.5} the
+    asymptote exp(-x^2) + y / (sqrt(pi) x^2) (1 + 3 / (2 x^2)) (the Lorentz-wing expansion
+    of Appendix C plus the Gaussian core it sits on); elsewhere Re of Humlicek's rational
+    approximation of the region |x| + y falls in (I >= 15 > II >= 5.5 > III). The region is
+    chosen in FP32, the precision of the paper's code; the values are FP64."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    ax = np.abs(x)
+    ax32, y32 = ax.astype(np.float32), y.astype(np.float32)
+    s32 = (ax32 + y32).astype(np.float32)
+    t = y - 1j * ax
+    out = np.where(s32 >= np.float32(15.0), _humlicek_w(1, t).real,
+                   np.where(s32 >= np.float32(5.5), _humlicek_w(2, t).real, _humlicek_w(3, t).real))
+    r4 = (y32 < np.float32(0.02)) & (ax32 > np.float32(1.0)) & (ax32 < np.float32(5.5))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        k4 = np.exp(-ax * ax) + y / (math.sqrt(np.pi) * ax * ax) * (1.0 + 1.5 / (ax * ax))
+        lor = y / (math.sqrt(np.pi) * (ax * ax + y * y))
+    out = np.where(r4, k4, out)
+    return np.where(ax32 > np.float32(15.0), lor, out)
+
+
 QUAD_COEF = (1.0, 0.25, 0.0625)  # test shape f = amp (1 + d/4 + d^2/16), d in cm^-1
 QUART_COEF = (1.0, 0.25, 0.0625, 0.015625, 0.00390625)  # f = amp sum_j (d/4)^j, j <= 4
 
@@ -190,7 +229,8 @@ QUART_COEF = (1.0, 0.25, 0.0625, 0.015625, 0.00390625)  # f = amp sum_j (d/4)^j,
 def profile(shape: str, d_fx, amp, gamma_L, alpha_D, chi_on):
     """amp * f(d) * chi(|d|) at offsets d (fixed point) from the shifted centre.
 
-    f: 'lorentz' Eq. (4); 'doppler' Eq. (5); 'voigt' Eqs. (7)-(8); test shapes
+    f: 'lorentz' Eq. (4); 'doppler' Eq. (5); 'voigt' Eqs. (7)-(8) ('voigt_paper': with
+    K computed as Appendix C does, voigt_K_paper); test shapes
     'const' (f = 1, no amplitude, no chi: k counts lines), 'quad'
     (f = 1 + d/4 + d^2/16, no chi) and 'quart' (f = sum_{j<=4} (d/4)^j, no chi).
     """
@@ -207,10 +247,11 @@ def profile(shape: str, d_fx, amp, gamma_L, alpha_D, chi_on):
         f = gamma_L / (np.pi * (gamma_L * gamma_L + d * d))
     elif shape == "doppler":
         f = math.sqrt(LN2 / np.pi) / alpha_D * np.exp(-d * d * LN2 / (alpha_D * alpha_D))
-    elif shape == "voigt":
+    elif shape in ("voigt", "voigt_paper"):
         x = math.sqrt(LN2) * d / alpha_D
         y = math.sqrt(LN2) * gamma_L / alpha_D
-        f = math.sqrt(LN2 / np.pi) / alpha_D * voigt_K(x, y)
+        K = voigt_K(x, y) if shape == "voigt" else voigt_K_paper(x, y)
+        f = math.sqrt(LN2 / np.pi) / alpha_D * K
     else:
         raise ValueError(shape)
     f = amp * f

@@ -414,3 +414,52 @@ def test_planted_mistakes_fail_a_pin(monkeypatch):
         m.setattr(O, "accept", acc)
         with pytest.raises(AssertionError):
             test_constant_shape_counts_lines_within_cutoff(CASES[3])
+
+
+# ---------------------------------------------------------------- Appendix C: the paper's fast Voigt
+def _plane():
+    x, y = np.meshgrid(np.linspace(0.0, 40.0, 1601), np.logspace(-4, 2, 97))
+    return x.ravel(), y.ravel()
+
+
+def test_paper_voigt_humlicek_regions_match_faddeeva():
+    """Regions I-III (Humlicek's rational approximations), away from the paper's
+    substitutions, agree with the Faddeeva function to Humlicek's 1e-4."""
+    from scipy.special import wofz
+    x, y = _plane()
+    keep = (x <= 15) & ~((y < 0.02) & (x > 1) & (x < 5.5)) & ~((x + y < 5.5) & (y < 0.195 * x - 0.176))
+    ref = wofz(x[keep] + 1j * y[keep]).real
+    got = O.voigt_K_paper(x[keep], y[keep])
+    assert np.max(np.abs(got - ref) / ref) < 1e-4
+
+
+def test_paper_voigt_substitutions():
+    """|x| > 15: the Lorentz wing, exactly, within the paper's 1 % of K; region 4: the
+    Appendix C asymptote on the Gaussian core, exactly (its error to K, up to about 9 %,
+    is the paper's, reported rather than pinned); the rest of Humlicek's region IV (now
+    region III's formula) within about 1 % (1.06 % at worst on this grid)."""
+    from scipy.special import wofz
+    x, y = _plane()
+    ref = wofz(x + 1j * y).real
+    got = O.voigt_K_paper(x, y)
+    far = x > 15
+    assert np.allclose(got[far], y[far] / (np.sqrt(np.pi) * (x[far] ** 2 + y[far] ** 2)), rtol=1e-14, atol=0)
+    assert np.max(np.abs(got[far] - ref[far]) / ref[far]) < 0.01
+    r4 = (y < 0.02) & (x > 1) & (x < 5.5)
+    k4 = np.exp(-x[r4] ** 2) + y[r4] / (np.sqrt(np.pi) * x[r4] ** 2) * (1 + 1.5 / x[r4] ** 2)
+    assert np.allclose(got[r4], k4, rtol=1e-14, atol=0)
+    assert 0.05 < np.max(np.abs(got[r4] - ref[r4]) / ref[r4]) < 0.09
+    iv = (x + y < 5.5) & (y < 0.195 * x - 0.176) & ~r4
+    assert np.max(np.abs(got[iv] - ref[iv]) / ref[iv]) < 0.015
+    assert np.array_equal(O.voigt_K_paper(-x, y), got)  # even in x
+
+
+def test_paper_voigt_profile_normalisation():
+    """The 'voigt_paper' shape integrates to 1 like the Voigt profile (to the accuracy of
+    its substitutions), by trapezoid on a fine grid out to 400 Doppler widths."""
+    gL, aD = 0.003, 0.002
+    d = np.linspace(-400 * aD, 400 * aD, 800_001)
+    d_fx = np.rint(d * O.FIX).astype(np.int64)
+    f = O.profile("voigt_paper", d_fx, 1.0, gL, aD, False)
+    g = O.profile("voigt", d_fx, 1.0, gL, aD, False)
+    assert abs(np.trapezoid(f, d) / np.trapezoid(g, d) - 1) < 2e-3
