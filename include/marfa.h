@@ -45,6 +45,10 @@ enum {
   MARFA_SHAPE_LORENTZ = 0,    /* Eq. (4)                                      */
   MARFA_SHAPE_VOIGT = 1,      /* Eqs. (7)-(8), the default of the paper        */
   MARFA_SHAPE_DOPPLER = 2,    /* Eq. (5)                                      */
+  MARFA_SHAPE_VOIGT_PAPER = 3, /* Eqs. (7)-(8) with K as Appendix C computes it:
+                                  the Lorentz wing for |x| > 15, the region-4
+                                  asymptote for y < 0.02, 1 < |x| < 5.5,
+                                  Humlicek's rational approximations elsewhere */
   MARFA_SHAPE_TEST_CONST = 100,
   MARFA_SHAPE_TEST_QUAD = 101,
   MARFA_SHAPE_TEST_QUART = 102
@@ -374,6 +378,10 @@ int marfa_diag_absorption_counted_surrogate(const marfa_lines_t* lines,
                                             int32_t n_levels, const marfa_request_t* rq,
                                             float* k_out, int64_t* counts,
                                             int64_t* surrogate_counts);
+
+/* The line shape K(x, y) (or f(x) for the non-Voigt shapes, y ignored) as the kernels
+ * evaluate it, for shape = MARFA_SHAPE_* at n points (host arrays x, y, out). */
+int marfa_diag_shape(int32_t shape, const float* x, const float* y, float* out, int64_t n);
 
 /* The order marfa_prepare_lines gives the lines (host only, no device call): order[j] =
  * the input index of the j-th line of a stable sort by nu0 (host array [n]; the identity

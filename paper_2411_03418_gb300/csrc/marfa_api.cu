@@ -684,7 +684,8 @@ static int validate_request(const marfa_request_t* rq, int64_t* npts) {
     return fail(MARFA_E_INVAL, "cut-off must be in (0, 1000] cm^-1");
   const int s = rq->shape;
   if (!(s == MARFA_SHAPE_LORENTZ || s == MARFA_SHAPE_VOIGT || s == MARFA_SHAPE_DOPPLER ||
-        s == MARFA_SHAPE_TEST_CONST || s == MARFA_SHAPE_TEST_QUAD || s == MARFA_SHAPE_TEST_QUART))
+        s == MARFA_SHAPE_VOIGT_PAPER || s == MARFA_SHAPE_TEST_CONST || s == MARFA_SHAPE_TEST_QUAD ||
+        s == MARFA_SHAPE_TEST_QUART))
     return fail(MARFA_E_INVAL, "unknown shape %d", s);
   if (rq->chi != MARFA_CHI_NONE && rq->chi != MARFA_CHI_TONKOV)
     return fail(MARFA_E_INVAL, "unknown chi %d", rq->chi);
@@ -1678,6 +1679,28 @@ extern "C" int marfa_diag_pipe_rate(int32_t pipe, double* ops_per_s) {
   if (e) return fail(MARFA_E_CUDA, "pipe probe: %s", cudaGetErrorString(e));
   if (!(ms > 0.0f)) return fail(MARFA_E_CUDA, "pipe probe: no elapsed time");
   *ops_per_s = (double)n / (ms * 1e-3);
+  return MARFA_OK;
+}
+
+extern "C" int marfa_diag_shape(int32_t shape, const float* x, const float* y, float* out, int64_t n) {
+  if (!(shape == MARFA_SHAPE_LORENTZ || shape == MARFA_SHAPE_VOIGT || shape == MARFA_SHAPE_DOPPLER ||
+        shape == MARFA_SHAPE_VOIGT_PAPER || shape == MARFA_SHAPE_TEST_CONST || shape == MARFA_SHAPE_TEST_QUAD ||
+        shape == MARFA_SHAPE_TEST_QUART))
+    return fail(MARFA_E_INVAL, "unknown shape %d", shape);
+  if (n < 0 || (n > 0 && (!x || !y || !out))) return fail(MARFA_E_INVAL, "bad arguments");
+  if (n == 0) return MARFA_OK;
+  float* dx;
+  CK(cudaMalloc(&dx, 12 * (size_t)n));
+  float *dy = dx + n, *dz = dy + n;
+  cudaError_t e;
+  if ((e = cudaMemcpy(dx, x, 4 * n, cudaMemcpyHostToDevice)) || (e = cudaMemcpy(dy, y, 4 * n, cudaMemcpyHostToDevice))) {
+    cudaFree(dx);
+    return fail(MARFA_E_CUDA, "copy failed: %s", cudaGetErrorString(e));
+  }
+  launch_diag_shape(shape, dx, dy, dz, n, 0);
+  e = cudaMemcpy(out, dz, 4 * n, cudaMemcpyDeviceToHost);
+  cudaFree(dx);
+  if (e) return fail(MARFA_E_CUDA, "shape kernel: %s", cudaGetErrorString(e));
   return MARFA_OK;
 }
 

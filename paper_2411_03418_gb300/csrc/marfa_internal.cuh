@@ -22,8 +22,8 @@ __host__ __device__ constexpr int64_t step_fx(int g) { return int64_t(1) << (kFi
 __host__ __device__ __forceinline__ int64_t fl_sh(int64_t a, int s) { return a >> s; }
 __host__ __device__ __forceinline__ int64_t cl_sh(int64_t a, int s) { return -((-a) >> s); }
 
-constexpr int kShapeLorentz = 0, kShapeVoigt = 1, kShapeDoppler = 2, kShapeConst = 100,
-              kShapeQuad = 101, kShapeQuart = 102;
+constexpr int kShapeLorentz = 0, kShapeVoigt = 1, kShapeDoppler = 2, kShapeVoigtPaper = 3,
+              kShapeConst = 100, kShapeQuad = 101, kShapeQuart = 102;
 
 // Per level (host-computed in double precision).
 struct LevelDev {
@@ -174,6 +174,7 @@ void launch_coarse_lm(const ReqDev* reqs, const CoarseItem* items, int n_items, 
 void launch_fine(const ReqDev* reqs, const FineItem* items, int n_items, int64_t* counts, bool surr,
                  bool wide, cudaStream_t st);
 void launch_diag_voigt(const float* x, const float* y, float* out, int64_t n, cudaStream_t st);
+void launch_diag_shape(int shape, const float* x, const float* y, float* out, int64_t n, cudaStream_t st);
 // instructions issued by one probe launch (out: blocks x 256 floats)
 int64_t launch_diag_pipe(int pipe, float* out, int blocks, int iters, cudaStream_t st);
 void launch_diag_owned(const ReqDev* req, int64_t n_lines, int level, int grid, int64_t first,

@@ -255,6 +255,7 @@ struct NodeX {
 __device__ __forceinline__ float shape_f(int shape, float x, float y) {
   switch (shape) {
     case kShapeVoigt: return voigt_K(x, y);
+    case kShapeVoigtPaper: return voigt_K_paper_call(x, y);
     case kShapeLorentz: return 1.0f / fmaf(x, x, 1.0f);
     case kShapeDoppler: return expf(-x * x);
     case kShapeConst: return 1.0f;
@@ -372,12 +373,14 @@ __global__ void __launch_bounds__(256) k_level_prep(PrepArgs a) {
       sx = kSqrtLn2 / aD;
       W = aD;
       break;
-    default:
-      amp = (a.shape == kShapeVoigt) ? S * kSqrtLn2Pi / aD : (a.shape == kShapeConst ? 1.0f : S);
-      sx = (a.shape == kShapeVoigt) ? kSqrtLn2 / aD : 1.0f;
+    default: {
+      const bool vgt = a.shape == kShapeVoigt || a.shape == kShapeVoigtPaper;
+      amp = vgt ? S * kSqrtLn2Pi / aD : (a.shape == kShapeConst ? 1.0f : S);
+      sx = vgt ? kSqrtLn2 / aD : 1.0f;
       y = kSqrtLn2 * gL / aD;
       W = fmaf(0.5346f, gL, sqrtf(fmaf(0.2166f * gL, gL, aD * aD)));
-      if (a.shape != kShapeVoigt) y = 0.0f;
+      if (!vgt) y = 0.0f;
+    }
   }
   // g*: coarsest grid with h_g <= W / R_c. Decided in FP32 unless W lies within 1e-5
   // of a threshold, then in FP64 with the operations in the same order as the FP64
@@ -1351,7 +1354,7 @@ __global__ void __launch_bounds__(kFineThreads)
   const LevelDev L = R.lev[lev];
   const int wlo = (int)max(R.k_lo - kw, (int64_t)0);
   const int whi = (int)min(R.k_hi - kw, (int64_t)(kWarpNodes - 1));
-  const int64_t Xa = kw << kFineShift, Xb = (kw + kWarpNodes - 1) << kFineShift;
+  const int64_t Xa = kw << kFineShift;  // position of the warp's first node
   // the warp's candidate bands, looked up before the barrier (global loads only), so
   // that their latency overlaps the table copy
   Bands bd;
@@ -1614,6 +1617,16 @@ __global__ void k_diag_voigt(const float* x, const float* y, float* out, int64_t
 void launch_diag_voigt(const float* x, const float* y, float* out, int64_t n, cudaStream_t st) {
   if (n <= 0) return;
   k_diag_voigt<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, y, out, n);
+}
+
+__global__ void k_diag_shape(int shape, const float* x, const float* y, float* out, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = shape_f(shape, x[i], y[i]);
+}
+
+void launch_diag_shape(int shape, const float* x, const float* y, float* out, int64_t n, cudaStream_t st) {
+  if (n <= 0) return;
+  k_diag_shape<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(shape, x, y, out, n);
 }
 
 // Issue-rate probes for the roofline denominators: every thread runs kPipeChains

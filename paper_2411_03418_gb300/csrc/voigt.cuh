@@ -201,6 +201,72 @@ __device__ __forceinline__ float voigt_K(float x, float y, const float* tab) {
 
 __device__ __forceinline__ float voigt_K(float x, float y) { return voigt_K<false>(x, y, kVoigtCells); }
 
+// K(x, y) as the paper's Appendix C computes it, in FP32 like the paper's code: the
+// Lorentz wing y / (sqrt(pi) (x^2 + y^2)) beyond |x| = 15; in region 4 (y < 0.02,
+// 1 < |x| < 5.5) the asymptote exp(-x^2) + y / (sqrt(pi) x^2) (1 + 3 / (2 x^2)); elsewhere
+// Re of Humlicek's (1982) rational approximation of w in t = y - i|x| for the region
+// |x| + y falls in (I: >= 15, II: >= 5.5, III: below). Accurate to Humlicek's 1e-4 in
+// regions I-III, about 1 % in the Lorentz wing and the rest of Humlicek's region IV, and
+// several per cent in region 4 (the paper's choices).
+__device__ __forceinline__ float voigt_K_paper(float x, float y) {
+  const float ax = fabsf(x);
+  if (ax > 15.0f) return y * kInvSqrtPi / fmaf(ax, ax, y * y);
+  if (y < 0.02f && ax > 1.0f && ax < 5.5f) {
+    const float ix2 = 1.0f / (ax * ax);
+    return expf(-ax * ax) + y * kInvSqrtPi * ix2 * fmaf(1.5f, ix2, 1.0f);
+  }
+  const float tr = y, ti = -ax;  // t = y - i|x|
+  auto mul = [](float& ar, float& ai, float br, float bi) {
+    const float r = ar * br - ai * bi;
+    ai = ar * bi + ai * br;
+    ar = r;
+  };
+  float nr, ni, dr, di;  // w = (nr + i ni) / (dr + i di)
+  const float s = ax + y;
+  if (s >= 5.5f) {
+    float ur = tr, ui = ti;  // u = t^2
+    mul(ur, ui, tr, ti);
+    if (s >= 15.0f) {  // region I: 0.5641896 t / (0.5 + u)
+      nr = 0.5641896f * tr;
+      ni = 0.5641896f * ti;
+      dr = 0.5f + ur;
+      di = ui;
+    } else {  // region II: t (1.410474 + 0.5641896 u) / (0.75 + u (3 + u))
+      nr = 1.410474f + 0.5641896f * ur;
+      ni = 0.5641896f * ui;
+      mul(nr, ni, tr, ti);
+      dr = 3.0f + ur;
+      di = ui;
+      mul(dr, di, ur, ui);
+      dr += 0.75f;
+    }
+  } else {  // region III: quartic over quintic in t
+    nr = 0.5642236f * tr;
+    ni = 0.5642236f * ti;
+    nr += 3.778987f;
+    mul(nr, ni, tr, ti);
+    nr += 11.96482f;
+    mul(nr, ni, tr, ti);
+    nr += 20.20933f;
+    mul(nr, ni, tr, ti);
+    nr += 16.4955f;
+    dr = tr + 6.699398f;
+    di = ti;
+    mul(dr, di, tr, ti);
+    dr += 21.69274f;
+    mul(dr, di, tr, ti);
+    dr += 39.27121f;
+    mul(dr, di, tr, ti);
+    dr += 38.82363f;
+    mul(dr, di, tr, ti);
+    dr += 16.4955f;
+  }
+  return __fdividef(fmaf(nr, dr, ni * di), fmaf(dr, dr, di * di));
+}
+
+// The same out of line, for the generic shape switch (keeps its callers' registers).
+static __device__ __noinline__ float voigt_K_paper_call(float x, float y) { return voigt_K_paper(x, y); }
+
 // Cost class of one voigt_K evaluation, for operation counts: 0 the far-wing two-term
 // series, 1 the 6- or 15-term asymptotic series, 2 a 9 x 9 polynomial cell (Dawson or K
 // table), 3 a small-y cell.

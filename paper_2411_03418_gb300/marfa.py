@@ -19,7 +19,7 @@ LINE_DTYPE = np.dtype([("nu0", "<f8"), ("S296", "<f4"), ("gamma_air", "<f4"), ("
 SPECIES_DTYPE = np.dtype([("mol_iso", "<i4"), ("chi_enabled", "<i4"), ("mass_amu", "<f8"), ("q_exp", "<f8")])
 LEVEL_DTYPE = np.dtype([("T_K", "<f8"), ("p_atm", "<f8")])
 
-SHAPES = {"lorentz": 0, "voigt": 1, "doppler": 2, "const": 100, "quad": 101, "quart": 102}
+SHAPES = {"lorentz": 0, "voigt": 1, "doppler": 2, "voigt_paper": 3, "const": 100, "quad": 101, "quart": 102}
 CHI = {"none": 0, "tonkov": 1}
 UNITS = {"sigma": 0, "k_cm1": 1, "k_km1": 2}
 ERRORS = {-1: "MARFA_E_INVAL", -2: "MARFA_E_NOMEM", -3: "MARFA_E_CUDA", -4: "MARFA_E_IO",
@@ -47,7 +47,7 @@ EXPORTS = ["marfa_prepare_lines", "marfa_free_lines", "marfa_num_points", "marfa
            "marfa_mlp_train", "marfa_surrogate_load", "marfa_surrogate_unload", "marfa_surrogate_eval",
            "marfa_diag_absorption_counted_surrogate", "marfa_plan_create", "marfa_plan_execute",
            "marfa_plan_info", "marfa_plan_destroy", "marfa_diag_absorption_counts", "marfa_read_par",
-           "marfa_diag_pipe_rate", "marfa_diag_line_order"]
+           "marfa_diag_pipe_rate", "marfa_diag_line_order", "marfa_diag_shape"]
 
 MLP_PARAMS = 8577
 MLP_MAX_BATCH = 65536
@@ -89,6 +89,7 @@ def load(path: str | None = None):
         "marfa_diag_kernel_timing": (C.c_int, [i32, vp, vp]),
         "marfa_diag_pipe_rate": (C.c_int, [i32, vp]),
         "marfa_diag_line_order": (C.c_int, [vp, i64, vp]),
+        "marfa_diag_shape": (C.c_int, [i32, vp, vp, vp, i64]),
         "marfa_absorption_noalloc": (C.c_int, [vp, vp, vp, i32, vp, vp, vp]),
         "marfa_mlp_loss_grad": (C.c_int, [vp, vp, vp, vp, i64, i32, vp, vp]),
         "marfa_mlp_train": (C.c_int, [vp, vp, vp, vp, i64, vp, vp]),
@@ -410,6 +411,15 @@ def marfa_diag_kernel_timing(enable: bool):
 
 
 PIPES = {"fma": 0, "ex2": 1, "rcp": 2, "cos": 3}
+
+
+def marfa_diag_shape(shape: str, x, y) -> np.ndarray:
+    """The kernels' line shape (K(x, y) for the Voigt shapes) at float32 points x, y."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    out = np.empty_like(x)
+    _check(load().marfa_diag_shape(SHAPES[shape], _ptr(x), _ptr(y), _ptr(out), len(x)))
+    return out
 
 
 def marfa_diag_line_order(lines: np.ndarray) -> np.ndarray:

@@ -194,6 +194,39 @@ def test_absorption_parity(M, kw):
         assert_parity(got[lev], O.eleven_grid(wl, lev), what=f"level {lev}")
 
 
+# ------------------------------------------------------------ Appendix C: the paper's fast Voigt
+def test_paper_voigt_shape_elementwise(M):
+    """The kernels' FP32 paper-mode Voigt against the oracle's FP64 one at the same float32
+    points (both choose the region in FP32), every region and its boundaries included.
+    Bound: FP32 round-off, largest in region III near the real axis where Re w is a few
+    hundred times smaller than |w| (about 5e-5)."""
+    xs = np.concatenate([np.linspace(0.0, 40.0, 4001), [1.0, 5.5, 15.0], np.nextafter(np.float32([1.0, 5.5, 15.0]), 0),
+                         np.nextafter(np.float32([1.0, 5.5, 15.0]), 100)]).astype(np.float32)
+    ys = np.concatenate([np.logspace(-5, 2, 141), [0.02], np.nextafter(np.float32([0.02]), 0)]).astype(np.float32)
+    x, y = (a.ravel() for a in np.meshgrid(xs, ys))
+    x = np.concatenate([x, -x[:1000]])
+    y = np.concatenate([y, y[:1000]])
+    got = M.marfa_diag_shape("voigt_paper", x, y).astype(np.float64)
+    ref = O.voigt_K_paper(x.astype(np.float64), y.astype(np.float64))
+    rel = np.abs(got / ref - 1.0)
+    assert rel.max() < 1.5e-4 and np.median(rel) < 1e-6
+
+
+def test_paper_voigt_absorption(M):
+    """The 'voigt_paper' shape through the whole path against the oracle's eleven-grid sum
+    with the same shape. A node's x is computed in FP32 on the GPU and FP64 in the oracle,
+    so an evaluation within round-off of a region boundary (|x| = 1, 5.5, 15, y = 0.02)
+    can take the neighbouring region's formula, which differs by up to the 8 % step of the
+    region-4 asymptote: nearly all nodes meet the 1e-4 bar, all of them a 2 % one."""
+    wl = tiny_workload(81, 500, 2000.0, 2003.01, 125.0, T=(735.0, 296.0, 170.0), p=(92.0, 1.0, 1e-5),
+                       chi="tonkov", chi_species=1, shape="voigt_paper")
+    got = run_gpu(M, wl)
+    for lev in range(wl.n_levels):
+        ref = O.eleven_grid(wl, lev)
+        rel = np.abs(got[lev] / ref - 1.0)
+        assert np.mean(rel < RTOL) > 0.999 and rel.max() < 0.02, (lev, rel.max())
+
+
 # the 5-point variant (quartic interpolation on panels of four steps)
 PARITY_CASES_5 = [
     dict(seed=71, n=400, lo=1500.0, hi=1504.7, cut=25.0, T=(296.0,), p=(1.0,)),
