@@ -45,13 +45,12 @@ UNIT = "pts*levels/s"
 # polynomial cell plus the Gaussian term, small-y cell (6 x 4 terms) plus the Gaussian term.
 FLOPS_FAR, FLOPS_MID, FLOPS_NEAR, FLOPS_SMALL = 20.0, 70.0, 200.0, 90.0
 
-# DRAM bytes (read + write) per launch of the dominant kernel of each workload's full
-# window, from single-pass ncu captures of the timed replay (dram__bytes_read.sum +
+# DRAM bytes (read + write) per launch of the dominant kernel of the Venus workload's
+# full window, from a single-pass ncu capture of the timed replay (dram__bytes_read.sum +
 # dram__bytes_write.sum; command and figures in profiles/traffic_dominant_kernels.md).
-# They belong to the kernels as built when captured; other windows report null.
-TRAFFIC_BYTES = {("venus", "finest"): 652.63e6 + 614.32e6,
-                 ("earth", "finest"): 2.92e9 + 1.03e9,
-                 ("batch", "finest"): 1.95e9 + 1.24e9}
+# They belong to the kernels as built when captured; other workloads and windows report
+# null.
+TRAFFIC_BYTES = {("venus", "finest"): 651.35e6 + 614.03e6}
 N_SM = 152
 FP32_LANES = 128
 
