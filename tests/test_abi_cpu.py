@@ -218,3 +218,13 @@ def test_line_order_is_the_stable_sort_by_nu0(M, kind):
     lines["nu0"] = nu
     order = M.marfa_diag_line_order(lines)
     assert np.array_equal(order, np.argsort(nu, kind="stable"))
+
+
+def test_line_order_small_inputs(M):
+    """Short line lists (below one worker chunk, and around the 32-line insertion-sort
+    limit) with ties, in the order of a stable sort by nu0."""
+    rng = np.random.default_rng(3)
+    for n in list(range(1, 70)) + [127, 128, 129, 1000, 8191, 8193, 16385]:
+        lines = np.zeros(n, dtype=M.LINE_DTYPE)
+        lines["nu0"] = np.floor(rng.random(n) * max(2, n // 3)) * 0.5 + 1000.0
+        assert np.array_equal(M.marfa_diag_line_order(lines), np.argsort(lines["nu0"], kind="stable")), n
