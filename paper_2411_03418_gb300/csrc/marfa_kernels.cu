@@ -427,7 +427,8 @@ void launch_level_prep(const PrepArgs& a, int n_levels, cudaStream_t st) {
 // ------------------------------------------------------------------ grid 1
 // Grid 1 (1 cm^-1 step) carries the long cut-off tails of every line and most of the
 // profile evaluations. A CTA owns kG1Pairs consecutive node pairs of one level: lane p
-// of every warp holds pair p (even node 2m, odd node 2m+1), and the 8 warps split the
+// of every warp holds pair p (even node 2m, odd node 2m+1; a tile the window covers only
+// in part may fold four lines onto the lanes instead, see k_g1), and the 8 warps split the
 // candidate lines, which are staged in shared memory and read by broadcast. For a line
 // whose tile nodes are all in the far Voigt wing (|z| >= 100) the profile is the two-term
 // series y/(sqrt(pi) r^2)(1 + (3x^2 - y^2)/(2 r^4)), and the chi-factor of branch 1 is a
@@ -537,10 +538,10 @@ __global__ void __launch_bounds__(kG1Warps * 32)
   const bool voigt = R.shape == kShapeVoigt;
   const bool physical = R.shape < kShapeConst;
 
-  // Lane mapping. Normally lane = pair and a warp takes one staged line at a time. A
-  // request whose window covers at most 8 pairs of the tile (the rest of the lanes would
-  // idle) takes 4 lines at a time instead: lane = (line slot lane / 8, pair pw0 + lane % 8);
-  // the four slots' sums are merged before the per-warp reduction.
+  // Lane mapping. Normally lane = pair and a warp takes one staged line at a time. A tile
+  // of which the window covers at most 8 pairs, pw0 .. pw1 (the other lanes would idle),
+  // takes 4 lines at a time instead: lane = (line slot lane / 8, pair pw0 + lane % 8); the
+  // four slots' sums are merged before the per-warp reduction.
   const int64_t bw0 = max(m_first - base, (int64_t)0), bw1 = min(m_last - base, (int64_t)(nb - 1));
   const int pw0 = (int)max(bw0 - 1, (int64_t)0), pw1 = (int)min(bw1, (int64_t)(kG1Pairs - 1));
   const bool narrow = !use_mlp && pw1 - pw0 < 8;  // block-uniform
