@@ -446,7 +446,8 @@ def test_paper_voigt_substitutions():
     far = x > float(g["voigt_lorentz_x"])
     assert np.allclose(got[far], y[far] / (np.sqrt(np.pi) * (x[far] ** 2 + y[far] ** 2)), rtol=1e-14, atol=0)
     assert np.max(np.abs(got[far] - ref[far]) / ref[far]) < float(g["voigt_asymptote_tolerance"])
-    r4 = (y < 0.02) & (x > 1) & (x < 5.5)
+    r4 = ((y < float(g["voigt_region4_y_max"])) & (x > float(g["voigt_region4_x_min"]))
+          & (x < float(g["voigt_region4_x_max"])))
     k4 = np.exp(-x[r4] ** 2) + y[r4] / (np.sqrt(np.pi) * x[r4] ** 2) * (1 + 1.5 / x[r4] ** 2)
     assert np.allclose(got[r4], k4, rtol=1e-14, atol=0)
     assert 0.05 < np.max(np.abs(got[r4] - ref[r4]) / ref[r4]) < 0.09
