@@ -955,6 +955,12 @@ struct WorkSet {
   int64_t* dgc = nullptr;
   int64_t* dcc[kNGrid + 1] = {nullptr};
   int64_t* dfc = nullptr;
+  // every request's level preparation as one launch: the requests' arguments and the
+  // prefix sums of their blocks
+  std::vector<PrepArgs> prep;
+  std::vector<int64_t> prep_first;
+  PrepArgs* dprep = nullptr;
+  int64_t* dprep_first = nullptr;
 };
 
 static void free_work(WorkSet& W, cudaStream_t st) {
@@ -979,6 +985,12 @@ static int build_work(std::vector<Plan>& plans, const int* variant, bool count, 
     for (auto& P : plans) coarse_items(P, g, W.variant[g], W.ci[g]);
   }
   for (auto& P : plans) W.fi.insert(W.fi.end(), P.fine.begin(), P.fine.end());
+  W.prep_first.push_back(0);
+  for (auto& P : plans) {
+    W.prep.push_back(P.prep);
+    W.prep_first.push_back(W.prep_first.back() + (P.prep.n + 255) / 256 * P.n_levels);
+  }
+  if (W.prep_first.back() > 0x7fffffff) return fail(MARFA_E_INVAL, "too many (level, line) pairs in one call");
   size_t total_items = W.gi.size() + W.fi.size();
   for (int g = 2; g <= kNGrid; ++g) total_items += W.ci[g].size();
   if (W.gi.size() > 0x7fffffffu || W.fi.size() > 0x7fffffffu || total_items > ((size_t)1 << 34))
@@ -990,6 +1002,7 @@ static int build_work(std::vector<Plan>& plans, const int* variant, bool count, 
   size_t sz = al(sizeof(ReqDev) * W.rds.size()) + al(sizeof(G1Item) * W.gi.size()) +
               al(sizeof(FineItem) * W.fi.size()) + al(cw * W.gi.size()) + al(cw * W.fi.size());
   for (int g = 2; g <= kNGrid; ++g) sz += al(sizeof(CoarseItem) * W.ci[g].size()) + al(cw * W.ci[g].size());
+  sz += al(sizeof(PrepArgs) * W.prep.size()) + al(sizeof(int64_t) * W.prep_first.size());
   int r = dev_alloc(&W.buf, sz, st);
   if (r) return r;
   char* p = (char*)W.buf;
@@ -1002,6 +1015,8 @@ static int build_work(std::vector<Plan>& plans, const int* variant, bool count, 
   W.dgi = (G1Item*)take(sizeof(G1Item) * W.gi.size());
   W.dfi = (FineItem*)take(sizeof(FineItem) * W.fi.size());
   for (int g = 2; g <= kNGrid; ++g) W.dci[g] = (CoarseItem*)take(sizeof(CoarseItem) * W.ci[g].size());
+  W.dprep = (PrepArgs*)take(sizeof(PrepArgs) * W.prep.size());
+  W.dprep_first = (int64_t*)take(sizeof(int64_t) * W.prep_first.size());
   if (count) {
     W.dgc = (int64_t*)take(cw * W.gi.size());
     W.dfc = (int64_t*)take(cw * W.fi.size());
@@ -1015,6 +1030,8 @@ static int build_work(std::vector<Plan>& plans, const int* variant, bool count, 
   up(W.dgi, W.gi.data(), sizeof(G1Item) * W.gi.size());
   up(W.dfi, W.fi.data(), sizeof(FineItem) * W.fi.size());
   for (int g = 2; g <= kNGrid; ++g) up(W.dci[g], W.ci[g].data(), sizeof(CoarseItem) * W.ci[g].size());
+  up(W.dprep, W.prep.data(), sizeof(PrepArgs) * W.prep.size());
+  up(W.dprep_first, W.prep_first.data(), sizeof(int64_t) * W.prep_first.size());
   if (!e && count) {
     e = cudaMemsetAsync(W.dgc, 0, cw * W.gi.size(), st);
     if (!e) e = cudaMemsetAsync(W.dfc, 0, cw * W.fi.size(), st);
@@ -1244,9 +1261,12 @@ static int plan_launch_all(marfa_plan_t* X, cudaStream_t st, bool capture) {
   };
   const bool branches = capture && !X->serial;
   rec(0, st);
-  for (auto& P : X->plans) launch_prep(P, st, false);
-  rec(1, st);
   const WorkSet& W = X->W;
+  if (X->plans.size() > 1)  // one launch for all requests (each alone would fill the GPU poorly)
+    launch_level_prep_batch(W.dprep, W.dprep_first, (int)X->plans.size(), W.prep_first.back(), st);
+  else
+    for (auto& P : X->plans) launch_prep(P, st, false);
+  rec(1, st);
   // grid g runs on branch stream br[g] (capture) or on st
   cudaStream_t br[kNGrid + 1];
   for (int g = 1; g <= kNGrid; ++g) br[g] = branches ? X->side[(g == 1 ? 0 : 1 + (kNGrid - g)) % kSide] : st;

@@ -163,6 +163,10 @@ struct PrepArgs {
 // in the asymptotic series and in small-y cells (voigt_class 2, 1 and 3).
 constexpr int kCountFields = 5;
 void launch_level_prep(const PrepArgs& a, int n_levels, cudaStream_t st);
+// every request's level preparation in one launch: args[n_req] (device), first[n_req + 1]
+// (device) the prefix sums of the requests' blocks, ceil(n / 256) x n_levels each
+void launch_level_prep_batch(const PrepArgs* args, const int64_t* first, int n_req, int64_t blocks,
+                             cudaStream_t st);
 // wide: every request of the launch uses the 5-point partition (the plain kernels are
 // compiled for one partition; the counting and surrogate variants read it per request).
 void launch_g1(const ReqDev* reqs, const G1Item* items, int n_items, int64_t* counts, bool surr,

@@ -334,10 +334,8 @@ static void launch_surr(void (*k)(KA...), int n_items, int threads, cudaStream_t
 }
 
 // ------------------------------------------------------------------ K1: level prep
-__global__ void __launch_bounds__(256) k_level_prep(PrepArgs a) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int lev = blockIdx.y;
-  if (i >= a.n) return;
+// The per-(level, line) data of line i at level lev.
+__device__ __forceinline__ void level_prep_pair(const PrepArgs& a, int64_t i, int lev) {
   const LevelDev L = a.lev[lev];
   const int s = a.species[i];
   const LevelSpeciesDev LS = a.ls[(int64_t)lev * a.n_species + s];
@@ -419,9 +417,38 @@ __global__ void __launch_bounds__(256) k_level_prep(PrepArgs a) {
   a.flags[o] = (uint8_t)(LS.chi ? 1 : 0);
 }
 
+__global__ void __launch_bounds__(256) k_level_prep(PrepArgs a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < a.n) level_prep_pair(a, i, blockIdx.y);
+}
+
+// All requests of a batch in one launch: block b belongs to the last request r with
+// first[r] <= b, whose blocks run over its levels (outer) and 256-line chunks (inner).
+__global__ void __launch_bounds__(256) k_level_prep_batch(const PrepArgs* __restrict__ args,
+                                                          const int64_t* __restrict__ first, int n_req) {
+  const int64_t b = blockIdx.x;
+  int lo = 0, hi = n_req - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  const PrepArgs a = args[lo];
+  const int64_t local = b - first[lo], nb = (a.n + 255) / 256;
+  const int lev = (int)(local / nb);
+  const int64_t i = (local - lev * nb) * 256 + threadIdx.x;
+  if (i < a.n) level_prep_pair(a, i, lev);
+}
+
 void launch_level_prep(const PrepArgs& a, int n_levels, cudaStream_t st) {
   dim3 grid((unsigned)((a.n + 255) / 256), (unsigned)n_levels);
   k_level_prep<<<grid, 256, 0, st>>>(a);
+}
+
+void launch_level_prep_batch(const PrepArgs* args, const int64_t* first, int n_req, int64_t blocks,
+                             cudaStream_t st) {
+  if (n_req <= 0 || blocks <= 0) return;
+  k_level_prep_batch<<<(unsigned)blocks, 256, 0, st>>>(args, first, n_req);
 }
 
 // ------------------------------------------------------------------ grid 1
