@@ -345,12 +345,14 @@ static void sort_run(const marfa_line_t* lines, const int64_t* key, int64_t* idx
   std::copy(tmp.begin(), tmp.begin() + m, idx);
 }
 
-// order = the positions of the lines stably sorted by nu0 (what std::stable_sort gives):
-// a counting pass on the leading bits of key - kmin, each thread over its chunk of the input
-// in order, splits the lines into coarse buckets; the threads then take the coarse buckets
-// one at a time and sort each with sort_run. Returns false if scratch memory ran out.
-static bool sort_by_nu0(const marfa_line_t* lines, const int64_t* key, int64_t n, int64_t kmin,
-                        int64_t kmax, int64_t* order) {
+// order = the line indices src[0..n) (the identity 0..n-1 when src is NULL) stably sorted
+// by nu0 (what std::stable_sort gives): a counting pass on the leading bits of key - kmin,
+// each thread over its chunk of the input in order, splits the lines into coarse buckets;
+// a bucket holding more than its share of the lines is split again the same way (once),
+// and the threads then take the remaining buckets one at a time and sort each with
+// sort_run. Returns false if scratch memory ran out.
+static bool split_sort(const marfa_line_t* lines, const int64_t* key, const int64_t* src, int64_t n,
+                       int64_t kmin, int64_t kmax, int64_t* order, bool top) {
   const uint64_t span = (uint64_t)(kmax - kmin);
   int bits = 0;
   while (bits < 64 && (span >> bits)) ++bits;
@@ -365,7 +367,8 @@ static bool sort_by_nu0(const marfa_line_t* lines, const int64_t* key, int64_t n
   } catch (...) {
     return false;
   }
-  auto coarse = [&](int64_t i) { return (int64_t)((uint64_t)(key[i] - kmin) >> shift); };
+  auto line = [&](int64_t i) { return src ? src[i] : i; };
+  auto coarse = [&](int64_t i) { return (int64_t)((uint64_t)(key[line(i)] - kmin) >> shift); };
   par_chunks(nt, n, [&](int64_t lo, int64_t hi, int t) {
     int64_t* h = hist.data() + (size_t)t * C;
     for (int64_t i = lo; i < hi; ++i) ++h[coarse(i)];
@@ -383,21 +386,48 @@ static bool sort_by_nu0(const marfa_line_t* lines, const int64_t* key, int64_t n
   bstart[C] = run;
   par_chunks(nt, n, [&](int64_t lo, int64_t hi, int t) {
     int64_t* pos = hist.data() + (size_t)t * C;
-    for (int64_t i = lo; i < hi; ++i) order[pos[coarse(i)]++] = i;
+    for (int64_t i = lo; i < hi; ++i) order[pos[coarse(i)]++] = line(i);
   });
+  // crowded buckets (a dense band in a wide key range): split again on all threads
+  std::vector<char> done(C, 0);
+  if (top && nt > 1) {
+    const int64_t big = std::max<int64_t>(2 * n / nt, 1 << 15);
+    for (int64_t c = 0; c < C; ++c) {
+      const int64_t m = bstart[c + 1] - bstart[c];
+      if (m <= big) continue;
+      std::vector<int64_t> sub;
+      try {
+        sub.assign(order + bstart[c], order + bstart[c + 1]);
+      } catch (...) {
+        return false;
+      }
+      int64_t lo = INT64_MAX, hi = INT64_MIN;
+      for (const int64_t i : sub) {
+        lo = std::min(lo, key[i]);
+        hi = std::max(hi, key[i]);
+      }
+      if (!split_sort(lines, key, sub.data(), m, lo, hi, order + bstart[c], false)) return false;
+      done[c] = 1;
+    }
+  }
   std::atomic<int64_t> next{0};
   std::atomic<bool> oom{false};
   par_chunks(nt, nt, [&](int64_t, int64_t, int) {
     try {
       std::vector<int64_t> tmp, start;
       for (int64_t c; (c = next.fetch_add(1)) < C;)
-        if (bstart[c + 1] - bstart[c] > 1)
+        if (!done[c] && bstart[c + 1] - bstart[c] > 1)
           sort_run(lines, key, order + bstart[c], bstart[c + 1] - bstart[c], tmp, start);
     } catch (...) {
       oom = true;
     }
   });
   return !oom;
+}
+
+static bool sort_by_nu0(const marfa_line_t* lines, const int64_t* key, int64_t n, int64_t kmin,
+                        int64_t kmax, int64_t* order) {
+  return split_sort(lines, key, nullptr, n, kmin, kmax, order, true);
 }
 
 // what the validation of one chunk of lines found
