@@ -25,6 +25,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import queue
 import subprocess
@@ -101,6 +102,16 @@ def _oracle_sample(wl, lev, lo, hi):
     return wl.with_(lines=wl.lines[keep], nu_lo=lo, nu_hi=hi).level_subset([lev]), int(keep.sum())
 
 
+def _sample_place(wl, width, count):
+    """The middle level of the workload and the start (a multiple of 2^-11 cm^-1) of
+    `count` adjacent windows of `width` cm^-1 centred in its window (Venus: level 30 of 60,
+    16 windows of 0.125 cm^-1 from 2499 cm^-1)."""
+    lev = wl.n_levels // 2
+    lo = 0.5 * (wl.nu_lo + wl.nu_hi) - 0.5 * width * count
+    lo = max(wl.nu_lo, min(lo, wl.nu_hi - width * count))
+    return lev, math.floor(lo * 2048.0) / 2048.0
+
+
 def _oracle_worker(sub, barrier, q):
     """One process of the all-cores oracle run (spawn start): waits for the others, then
     runs the eleven-grid oracle on its sample and reports its start and end times."""
@@ -146,13 +157,14 @@ def cpu_baseline_sample(wl):
     eleven-grid result of one mid-profile level on windows of 0.25 cm^-1, once on one
     core and then on every host core at once (one window per process)."""
     from oracle import marfa_oracle as O
-    lev, lo, width = 30, 2500.0, 0.25
+    width = 0.25
+    nproc = os.cpu_count() or 1
+    lev, lo = _sample_place(wl, width, nproc)
     sub, nin = _oracle_sample(wl, lev, lo, lo + width)
     t = time.perf_counter()
     O.eleven_grid(sub, 0)
     dt1 = time.perf_counter() - t
     pts1 = O.num_points(lo, lo + width)
-    nproc = os.cpu_count() or 1
     v, pts, dt = oracle_all_cores(wl, lev, lo, width, nproc)
     return {"value": v, "unit": UNIT, "cores": nproc, "kind": "oracle",
             "single_core_value": pts1 / dt1,
@@ -165,7 +177,8 @@ def run_reference(args, wl, rank, world):
     if rank != 0:
         return
     nproc = os.cpu_count() or 1
-    lev, lo, width = 30, 2500.0, 0.125
+    width = 0.125
+    lev, lo = _sample_place(wl, width, nproc)
     times, pts = [], 0
     for i in range(args.warmup + args.steps):
         _, pts, dt = oracle_all_cores(wl, lev, lo, width, nproc)

@@ -58,3 +58,18 @@ def test_oracle_all_cores_runs_and_counts_points():
     wl = config0_tiny()
     v, pts, dt = bench.oracle_all_cores(wl, 0, 4000.0, 0.03125, 2)
     assert pts == 2 * O.num_points(4000.0, 4000.03125) and dt > 0 and v == pts / dt
+
+
+def test_reference_arm_line_on_a_small_workload():
+    """`bench.py --impl reference` prints the contract's JSON line (the oracle on every
+    host core), here on the small one-level workload."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--workload",
+                        "tiny", "--steps", "1", "--warmup", "0"], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "pts*levels/s"
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["cores"] >= 1
