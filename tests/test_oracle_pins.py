@@ -207,6 +207,106 @@ def test_gstar_thresholds():
     assert O.gstar(np.array([1e3]), 8)[0] == 1
 
 
+# ------------------------------------------------------------ the core width W that sets g*
+def _voigt_hwhm_by_bisection(gL, aD):
+    """Half width at half maximum of the Voigt profile, found by root bracketing on
+    scipy's own ``voigt_profile`` (Gaussian sigma = alpha_D / sqrt(2 ln 2), Lorentz HWHM
+    gamma_L): a route that shares nothing with the oracle's width formula."""
+    from scipy.optimize import brentq
+    sigma = aD / math.sqrt(2.0 * math.log(2.0))
+    half = 0.5 * special.voigt_profile(0.0, sigma, gL)
+    top = gL + aD  # the Voigt HWHM never exceeds the sum of the two half widths
+    return brentq(lambda d: special.voigt_profile(d, sigma, gL) - half, 0.0, top,
+                  xtol=1e-14 * top, rtol=1e-13)
+
+
+# Olivero & Longbothum (1977) give their width formula to about 0.02 %; over gamma_L /
+# alpha_D in [1e-3, 1e3] its largest deviation from the exact half width is 2.36e-4.
+HWHM_BAR = 2.5e-4
+
+
+def test_shape_hwhm_limits():
+    """Both limits of the Voigt width are exact forms: no Doppler width leaves the
+    Lorentz half width (0.5346 + sqrt(0.2166) = 1.000003), no Lorentz width the Doppler
+    half width; the pure shapes take their own half widths."""
+    for gL in (1e-4, 0.07, 3.4, 40.0):
+        assert float(O.shape_hwhm("voigt", gL, 0.0)) == pytest.approx(gL, rel=1e-5)
+        assert float(O.shape_hwhm("lorentz", gL, 0.002)) == gL
+    for aD in (1e-4, 2.2e-3, 0.05):
+        assert float(O.shape_hwhm("voigt", 0.0, aD)) == aD
+        assert float(O.shape_hwhm("doppler", 0.3, aD)) == aD
+
+
+def test_shape_hwhm_matches_voigt_half_maximum():
+    """Between the limits W is the half width of the Voigt profile to the formula's
+    published accuracy, over the width ratios of the workloads (Doppler-dominated upper
+    levels to collision-dominated lower ones)."""
+    for aD in (1e-3, 2.2e-3, 0.05):
+        for ratio in np.logspace(-3, 3, 25):
+            gL = float(ratio) * aD
+            W = float(O.shape_hwhm("voigt", gL, aD))
+            ref = _voigt_hwhm_by_bisection(gL, aD)
+            assert abs(W / ref - 1.0) <= HWHM_BAR, (gL, aD, W, ref)
+
+
+def test_shape_hwhm_planted_mistakes_fail(monkeypatch):
+    """A mistyped constant or a dropped square in the width formula fails a pin."""
+    def planted(a, b, square):
+        def W(shape, gL, aD):
+            if shape == "lorentz":
+                return np.asarray(gL, dtype=np.float64)
+            if shape == "doppler":
+                return np.asarray(aD, dtype=np.float64)
+            d2 = aD * aD if square else aD
+            return a * gL + np.sqrt(b * gL * gL + d2)
+        return W
+
+    for bad in (planted(0.5436, 0.2166, True), planted(0.5346, 0.2616, True),
+                planted(0.5346, 0.2166, False), planted(0.5, 0.25, True)):
+        with monkeypatch.context() as m:
+            m.setattr(O, "shape_hwhm", bad)
+            failed = 0
+            for pin in (test_shape_hwhm_limits, test_shape_hwhm_matches_voigt_half_maximum):
+                try:
+                    pin()
+                except AssertionError:
+                    failed += 1
+            assert failed >= 1
+
+
+# ------------------------------------------------------------ the fixed-point centre
+def test_centre_fixed_rounds_half_to_even():
+    """c = rint(nu~0 2^43) rounds a tie to the even neighbour. Near 100 cm^-1 the FP64
+    spacing is 2^-46 cm^-1, so centres that fall exactly half-way between two
+    fixed-point units exist; the expected integers come from exact rational arithmetic
+    (Python's round() of a Fraction rounds half to even)."""
+    from fractions import Fraction
+    u = 2.0 ** -46
+    offs = [4, 12, -4, 20, -12, 1, 3, 5, -5, 0]  # in units of 2^-46: 4 = half a fixed-point unit
+    vals = np.array([100.0 + k * u for k in offs], dtype=np.float64)
+    want = np.array([round(Fraction(float(v)) * (1 << O.FIX_BITS)) for v in vals], dtype=np.int64)
+    got = O.centre_fixed(vals)
+    assert np.array_equal(got, want)
+    base = 100 << O.FIX_BITS
+    # the ties explicitly: +0.5 -> 0, +1.5 -> 2, -0.5 -> 0, +2.5 -> 2, -1.5 -> -2
+    assert list(got[:5] - base) == [0, 2, 0, 2, -2]
+    # and the same through the pressure shift of a record (nu0 + delta p, Sec. 2.2)
+    wl = _wl_one(296.0, 1.0, nu0=100.0, d=3 * 2.0 ** -44)
+    c = O.centre_fixed(O.level_params(wl, 0)["nu_shift"])
+    assert int(c[0]) - base == 2
+
+
+def test_centre_fixed_planted_rounding_fails(monkeypatch):
+    """Rounding down, or rounding ties away from zero, fails the tie pin."""
+    F = float(1 << O.FIX_BITS)
+    for bad in (lambda v: np.floor(np.asarray(v) * F).astype(np.int64),
+                lambda v: (np.sign(np.asarray(v)) * np.floor(np.abs(np.asarray(v)) * F + 0.5)).astype(np.int64)):
+        with monkeypatch.context() as m:
+            m.setattr(O, "centre_fixed", bad)
+            with pytest.raises(AssertionError):
+                test_centre_fixed_rounds_half_to_even()
+
+
 # ------------------------------------------------------------ eleven-grid bookkeeping
 CASES = [
     # T, p, chi, cut-off, R_w, R_c, window
