@@ -245,22 +245,26 @@ int marfa_read_par(const char* text, int64_t len, marfa_line_t* out, int64_t cap
  * (so cudaMalloc would fail or fragment it), or a pipeline that must not let an
  * allocation or a free synchronise the device while its other streams run. The paper
  * has no counterpart of this call; it computes the same k(nu) as marfa_absorption.
- *   - Scratch: a file-scope __device__ array of 32 MiB (MARFA_NOALLOC_SCRATCH_BYTES)
- *     that every GPU loading the library holds until the process exits. A request
- *     whose per-level line data, grid slots and work lists exceed it is rejected with
- *     MARFA_E_INVAL (for example: one level of 200,000 lines on a 1000 cm^-1 window
- *     fits; sixty such levels do not).
+ *   - Scratch: a file-scope __device__ array of 32 MiB (MARFA_NOALLOC_SCRATCH_BYTES).
+ *     A device commits it when marfa_prepare_lines first runs there: that call looks
+ *     up the array's device address (cudaGetSymbolAddress, with the device current),
+ *     which loads the part of the library holding it, and fails with MARFA_E_NOMEM if
+ *     the 32 MiB cannot be had. From then on the device holds the array until the
+ *     process exits, and marfa_absorption_noalloc itself allocates nothing. The set-up
+ *     call (marfa_prepare_lines) must come before any stream capture, like any call
+ *     that allocates. A request whose per-level line data, grid slots and work lists
+ *     exceed the array is rejected with MARFA_E_INVAL (for example: one level of
+ *     200,000 lines on a 1000 cm^-1 window fits; sixty such levels do not).
  *   - k_out must be device memory ([n_levels][npts] float32); host outputs are
  *     rejected with MARFA_E_INVAL. lines comes from marfa_prepare_lines.
- *   - The first call on a device looks up the scratch's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call before
- *     any stream capture.
  *   - Every call reuses the same scratch and leaves its contents there; the kernels
  *     write every value they read, so nothing needs clearing between calls. Calls
  *     whose work overlaps on the GPU (other streams, other host threads) race on the
  *     scratch: serialise them.
- *   - Asynchronous on stream (NULL = legacy default stream); the copies of the level
- *     tables and work lists come from pageable host memory into the scratch.
+ *   - Asynchronous on stream (NULL = legacy default stream); the level tables and work
+ *     lists are copied into the scratch from the call's own pageable host memory. A
+ *     stream in capture is refused with MARFA_E_INVAL, since those copies would be
+ *     recorded from host memory freed when the call returns.
  */
 #define MARFA_NOALLOC_SCRATCH_BYTES (32u << 20)
 int marfa_absorption_noalloc(const marfa_lines_t* lines, const marfa_level_t* levels,

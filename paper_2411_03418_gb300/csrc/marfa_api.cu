@@ -87,6 +87,28 @@ static int dev_alloc(void** p, size_t bytes, cudaStream_t st) {
   return MARFA_OK;
 }
 
+// ------------------------------------------------------------------ absorption without allocation
+// The scratch of marfa_absorption_noalloc (declared here, where marfa_prepare_lines can
+// reach it; the entry point itself is at the end of the file).
+static constexpr size_t kNoAllocBytes = (size_t)32 << 20;  // 32 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Device address of g_noalloc_scratch on the current device (in host code the symbol is
+// only a host-side stand-in). Looked up on every call, so that a context torn down and
+// made again by the host application never leaves a stale address behind. The first
+// lookup on a device loads the module holding the array, which commits its 32 MiB:
+// marfa_prepare_lines makes that lookup, so the memory is taken by a call that
+// allocates anyway, before any marfa_absorption_noalloc on that device.
+static int noalloc_scratch(char** out) {
+  void* ptr = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+  if (e != cudaSuccess || !ptr)
+    return fail(e == cudaErrorMemoryAllocation ? MARFA_E_NOMEM : MARFA_E_CUDA,
+                "cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
+  *out = (char*)ptr;
+  return MARFA_OK;
+}
+
 // ------------------------------------------------------------------ kernel timing
 // Optional event pairs around each launch (marfa_diag_kernel_timing).
 namespace {
@@ -624,6 +646,13 @@ extern "C" int marfa_prepare_lines(const marfa_line_t* lines, int64_t n, const m
   if (e != cudaSuccess) {
     marfa_free_lines(L);
     return fail(MARFA_E_CUDA, "cudaMemcpy failed: %s", cudaGetErrorString(e));
+  }
+  // commit marfa_absorption_noalloc's scratch on this device now (see noalloc_scratch)
+  char* scratch = nullptr;
+  const int rs = noalloc_scratch(&scratch);
+  if (rs) {
+    marfa_free_lines(L);
+    return rs;
   }
   *out = L;
   return MARFA_OK;
@@ -1571,35 +1600,18 @@ extern "C" int marfa_write_pt_table(const char* dir, int32_t level_number, doubl
 // Callers that cannot allocate device memory (a host model that has handed all free
 // device memory to its own pool, so that cudaMalloc fails or fragments it, or a
 // pipeline that must not let an allocation or a free synchronise the device while
-// other streams run) use marfa_absorption_noalloc. Its scratch is this file-scope
-// array: every GPU that loads the library holds it until the process exits.
-static constexpr size_t kNoAllocBytes = (size_t)32 << 20;  // 32 MiB
-static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
-
-// Device address of g_noalloc_scratch, looked up once per device with that device
-// current (in host code the symbol is only a host-side stand-in).
-static int noalloc_scratch(char** out) {
-  static std::mutex mu;
-  static void* addr[64] = {nullptr};
-  int dev = 0;
-  CK(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) return fail(MARFA_E_INVAL, "device %d out of range", dev);
-  std::lock_guard<std::mutex> lk(mu);
-  if (!addr[dev]) {
-    void* ptr = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess || !ptr)
-      return fail(MARFA_E_CUDA, "cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
-    addr[dev] = ptr;
-  }
-  *out = (char*)addr[dev];
-  return MARFA_OK;
-}
-
+// other streams run) use marfa_absorption_noalloc. Its scratch is g_noalloc_scratch:
+// every GPU on which marfa_prepare_lines has run holds it until the process exits.
 extern "C" int marfa_absorption_noalloc(const marfa_lines_t* lines, const marfa_level_t* levels,
                                         const double* vmr, int32_t n_levels,
                                         const marfa_request_t* rq, float* k_out, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
+  // The level tables and work lists are copied from this call's own host memory, which
+  // is gone when it returns: a stream in capture would record copies of freed memory.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(st, &cap));
+  if (cap != cudaStreamCaptureStatusNone)
+    return fail(MARFA_E_INVAL, "marfa_absorption_noalloc refuses a stream in capture (use marfa_plan_* for graphs)");
   Plan P;
   int r = build_plan(P, lines, levels, vmr, n_levels, rq, 0);
   if (r) return r;
