@@ -481,9 +481,11 @@ def main():
             "gpu_launches": int(klaunch.sum()),
             "plan": {"graph": "one CUDA graph per step (12 kernel launches; grids 1-10 as parallel branches)",
                      "create_s": plan_s_create, "serial_ms_per_step": serial_ms,
-                     "variant_grids_1_10": [int(v) for v in variant],
+                     "variant_grids_1_10_finest": [int(v) for v in variant],
                      "autotune_ms_per_launch": [[round(float(a), 3) for a in row] for row in tune_ms],
-                     "variants": "0 line-major 32 pairs, 1 two-phase, 2 line-major 16 pairs"},
+                     "variants": "grids 2-10: 0 line-major 32 pairs, 1 two-phase, 2 line-major 16 pairs, "
+                                 "3 flattened, 4 by mechanism; finest: 0 groups per panel, 1 flattened jobs, "
+                                 "2 flattened jobs by mechanism"},
             "kernel_ms_per_step_serial": {n: float(kms[i] / args.steps) for i, n in enumerate(names)},
             "roofline": {"bound": "alu", "kernel": names[dom], "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak,

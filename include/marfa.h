@@ -170,11 +170,18 @@ int marfa_absorption_batch(int32_t n_req, const marfa_lines_t* const* lines,
  *              caller and kept by the plan: every execution rewrites them;
  *   lines    : must stay alive until marfa_plan_destroy; levels, vmr and rq are copied,
  *              and so is the loaded surrogate for requests with surrogate = 1;
- *   flags    : MARFA_PLAN_AUTOTUNE: for each of grids 2..10, time the three summation
+ *   flags    : MARFA_PLAN_AUTOTUNE: for each of grids 2..10, time the four summation
  *              kernels (line-major: a thread per candidate line over 32 or over 16 node
- *              pairs; two-phase: warps of 32 node pairs that stage 32 lines at a time)
- *              on this batch's own work and keep the fastest (otherwise grids 2..7
- *              line-major over 16 pairs, 8..10 two-phase); MARFA_PLAN_SERIAL: capture
+ *              pairs; two-phase: warps of 32 node pairs that stage 32 lines at a time;
+ *              flattened: the two-phase tiles with the evaluations spread evenly over
+ *              the lanes and grouped by Voigt branch; by mechanism: the two-phase tiles
+ *              with candidates taken per centre, cut-off edge and chi breakpoint, each
+ *              with closed-form ownership, where those lie far enough apart), and for
+ *              the finest grid its three
+ *              kernels (8-lane groups per G10 panel; flattened (line, panel) jobs, with
+ *              general or closed-form ownership), on
+ *              this batch's own work and keep the fastest (otherwise the defaults of
+ *              marfa_diag_variants); MARFA_PLAN_SERIAL: capture
  *              grids 1..10 one after the
  *              other (otherwise they are parallel branches of the graph, which the GPU
  *              runs concurrently, and per-kernel times overlap);
@@ -198,13 +205,29 @@ int marfa_plan_create(int32_t n_req, const marfa_lines_t* const* lines,
  * current device must be the plan's. */
 int marfa_plan_execute(marfa_plan_t* plan, void* stream);
 
-/* Kernel choice and timings (host arrays, each may be NULL): variant[10] for grids
- * 1..10 (-1 grid 1, 0 line-major over 32 pairs, 1 two-phase, 2 line-major over 16
- * pairs); tune_ms[10][3] the autotuner's time per launch of each variant (-1 when not
- * tuned); kernel_ms[12] device time of the last
+/* Kernel choice and timings (host arrays, each may be NULL): variant[MARFA_PLAN_KINDS]
+ * for grids 1..10 and the finest grid (grid 1: -1, its one kernel; grids 2..10: 0
+ * line-major over 32 pairs, 1 two-phase, 2 line-major over 16 pairs, 3 flattened, 4 by
+ * mechanism (closed-form ownership; the launch takes 1 where it does not apply); finest
+ * grid: 0 groups per panel, 1 flattened jobs, 2 flattened jobs by mechanism (1 where it
+ * does not apply)); tune_ms[MARFA_PLAN_KINDS][MARFA_PLAN_VARIANTS]
+ * the autotuner's time per launch of each variant (-1 when not tuned or not a variant of
+ * that kind); kernel_ms[12] device time of the last
  * execution per kernel kind (0 level preparation, 1..10 grids, 11 finest grid; waits for
  * that execution; MARFA_E_CUDA before the first execution). */
+#define MARFA_PLAN_KINDS 11
+#define MARFA_PLAN_VARIANTS 5
 int marfa_plan_info(const marfa_plan_t* plan, int32_t* variant, float* tune_ms, double* kernel_ms);
+
+/* Test and tuning hook: the process-wide kernel variants that calls without autotuning
+ * use (marfa_absorption, marfa_absorption_batch, marfa_absorption_noalloc and plans
+ * created without MARFA_PLAN_AUTOTUNE), in the layout of marfa_plan_info's variant
+ * array (entry 0, grid 1, is ignored on set and -1 on get). set (may be NULL): the new
+ * defaults, each checked against its kind's range (MARFA_E_INVAL, nothing changed);
+ * get (may be NULL): receives the defaults after the call. Every variant computes the
+ * same partition; they differ only in the order of the sums (the same tolerance to the
+ * oracle). Calls already running keep the variants they started with. */
+int marfa_diag_variants(const int32_t* set, int32_t* get);
 
 /* Free the plan's graph and device buffers (waits for the device). */
 void marfa_plan_destroy(marfa_plan_t* plan);

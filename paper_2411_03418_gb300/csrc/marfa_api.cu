@@ -27,6 +27,7 @@
 
 #include "../../include/marfa.h"
 #include "marfa_internal.cuh"
+#include "ownership.cuh"
 
 using namespace marfa;
 
@@ -852,6 +853,12 @@ static int build_plan(Plan& P, const marfa_lines_t* L, const marfa_level_t* leve
   R.R_w = rq->R_w;
   R.shape = rq->shape;
   R.chi_req = rq->chi == MARFA_CHI_TONKOV ? 1 : 0;
+  R.mech = 0;
+  if (!R.wide) {
+    for (int g = 2; g <= kNGrid; ++g)
+      if (mech_ok(g, R.cut_fx, R.R_w, R.chi_req != 0)) R.mech |= 1 << g;
+    if (mech_fine_ok(R.cut_fx, R.R_w, R.chi_req != 0)) R.mech |= 1 << (kNGrid + 1);
+  }
   R.mlp = nullptr;
   if (rq->surrogate) {
     r = surrogate_for_current_device(&R.mlp);
@@ -894,14 +901,24 @@ static void* pinned_host_view(void* p) {
 
 // Kernel variants of grids 2..10: 0 = line-major (k_coarse_lm, kLPairs node pairs per
 // CTA), 1 = two-phase (k_coarse, kCWarps x kCPairs node pairs per CTA), 2 = line-major
-// with 16 node pairs per CTA (half the shared memory, narrower tiles). Without tuning,
-// grids 2..kLastLM take the 16-pair line-major kernel (few lines own a panel there, so a
-// thread per line wastes little; the autotuner picks it there on every workload
-// measured) and the finer grids the two-phase one.
-constexpr int kNVariants = 3;
-static int default_variant(int g) { return g <= kLastLM ? 2 : 1; }
+// with 16 node pairs per CTA (half the shared memory, narrower tiles), 3 = flattened
+// (k_coarse_jobs: the two-phase tiles with phase 1 spread evenly over the lanes and
+// grouped by Voigt branch), 4 = by mechanism (k_coarse_mech: the two-phase tiles with
+// closed-form ownership, where every request of the launch has its mech bit for the
+// grid; otherwise the launch takes variant 1). Finest grid (kind kFineKind): 0 = k_fine (an 8-lane group per
+// G10 panel), 1 = k_fine_jobs ((line, panel) jobs spread evenly over the groups), 2 = the
+// same with closed-form ownership (mech bit of every request; otherwise variant 1).
+// Surrogate-capable launches always take variant 1 on grids 2..10 (when 3 is chosen)
+// and k_fine. Calls without tuning take the process-wide defaults (marfa_diag_variants).
+constexpr int kNVariants = 5;
+constexpr int kFineKind = kNGrid + 1;
+constexpr int kNFineVariants = 3;
+// Defaults measured on the Venus workload (line-major over 16 pairs on grids 2..7, the
+// mechanism kernel on 8..10, flattened jobs on the finest grid).
+static std::atomic<int> g_default_variant[kNGrid + 2] = {{-1}, {-1}, {2}, {2}, {2}, {2}, {2}, {2}, {4}, {4}, {4}, {1}};
+static int default_variant(int g) { return g_default_variant[g].load(std::memory_order_relaxed); }
 static int64_t variant_pairs(int v) {
-  return v == 0 ? (int64_t)kLPairs : (v == 1 ? (int64_t)kCPairs * kCWarps : (int64_t)16);
+  return v == 0 ? (int64_t)kLPairs : (v == 2 ? (int64_t)16 : (int64_t)kCPairs * kCWarps);
 }
 
 static void coarse_items(const Plan& P, int g, int v, std::vector<CoarseItem>& out) {
@@ -1001,7 +1018,7 @@ struct WorkSet {
   std::vector<G1Item> gi;
   std::vector<CoarseItem> ci[kNGrid + 1];  // grids 2..10
   std::vector<FineItem> fi;
-  int variant[kNGrid + 1] = {0};
+  int variant[kNGrid + 2] = {0};             // kernel variant per grid 2..10 and the finest grid
   bool surr = false;                       // some request uses the surrogate
   bool wide = false;                       // the requests use the 5-point partition
   bool surr_grid[kNGrid + 2] = {false};    // surrogate-capable kernels for grid 1..10, 11 finest
@@ -1043,6 +1060,7 @@ static int build_work(std::vector<Plan>& plans, const int* variant, bool count, 
     W.variant[g] = variant ? variant[g] : default_variant(g);
     for (auto& P : plans) coarse_items(P, g, W.variant[g], W.ci[g]);
   }
+  W.variant[kFineKind] = variant ? variant[kFineKind] : default_variant(kFineKind);
   for (auto& P : plans) W.fi.insert(W.fi.end(), P.fine.begin(), P.fine.end());
   W.prep_first.push_back(0);
   for (auto& P : plans) {
@@ -1106,11 +1124,28 @@ static int build_work(std::vector<Plan>& plans, const int* variant, bool count, 
 // Grid g of a work set with kernel variant v.
 static void launch_grid(const WorkSet& W, int g, cudaStream_t st) {
   const int n = (int)W.ci[g].size();
-  if (W.variant[g] == 1)
+  bool mech = W.variant[g] == 4 && !W.surr_grid[g] && !W.wide;
+  for (const auto& R : W.rds) mech = mech && ((R.mech >> g) & 1);
+  if (mech)
+    launch_coarse_mech(W.drd, W.dci[g], n, W.dcc[g], st);
+  else if (W.variant[g] == 3 && !W.surr_grid[g])
+    launch_coarse_jobs(W.drd, W.dci[g], n, W.dcc[g], W.wide, st);
+  else if (W.variant[g] == 1 || W.variant[g] >= 3)
     launch_coarse(W.drd, W.dci[g], n, W.dcc[g], W.surr_grid[g], W.wide, st);
   else
     launch_coarse_lm(W.drd, W.dci[g], n, W.dcc[g], W.surr_grid[g], W.variant[g] == 2 ? 16 : kLPairs, W.wide,
                      st);
+}
+
+// The finest grid + cascade of a work set with its kernel variant.
+static void launch_finest(const WorkSet& W, cudaStream_t st) {
+  const int n = (int)W.fi.size();
+  bool mech = W.variant[kFineKind] == 2 && !W.wide;
+  for (const auto& R : W.rds) mech = mech && ((R.mech >> (kNGrid + 1)) & 1);
+  if (W.variant[kFineKind] >= 1 && !W.surr_grid[kNGrid + 1])
+    launch_fine_jobs(W.drd, W.dfi, n, W.dfc, W.wide, mech, st);
+  else
+    launch_fine(W.drd, W.dfi, n, W.dfc, W.surr_grid[kNGrid + 1], W.wide, st);
 }
 
 // Every summation launch of a work set: grid 1, grids 2..10, finest grid + cascade.
@@ -1127,7 +1162,7 @@ static int launch_work(const WorkSet& W, cudaStream_t st, bool timed) {
   }
   if ((e = cudaGetLastError())) return fail(MARFA_E_CUDA, "coarse-grid kernel: %s", cudaGetErrorString(e));
   ev = timed ? timing_begin(st) : nullptr;
-  launch_fine(W.drd, W.dfi, (int)W.fi.size(), W.dfc, W.surr_grid[kNGrid + 1], W.wide, st);
+  launch_finest(W, st);
   timing_end(ev, kNGrid + 1, st);
   if ((e = cudaGetLastError())) return fail(MARFA_E_CUDA, "fine kernel: %s", cudaGetErrorString(e));
   return MARFA_OK;
@@ -1246,7 +1281,7 @@ struct marfa_plan {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t ev[2 * kKinds] = {nullptr};
-  float tune_ms[kNGrid + 1][kNVariants] = {};
+  float tune_ms[kNGrid + 2][kNVariants] = {};
   bool tuned = false;
   MlpWeights* mlp = nullptr;  // the plan's own copy of the surrogate (if any request uses it)
   bool serial = false;        // capture the coarse grids one after the other
@@ -1277,35 +1312,49 @@ extern "C" void marfa_plan_destroy(marfa_plan_t* X) {
   delete X;
 }
 
-// Time grid g's launch with each kernel variant on the plan's own work (two timed
-// launches after one warm-up each) and keep the fastest.
+// Time each kernel variant of grids 2..10 and of the finest grid on the plan's own work
+// (two timed launches after one warm-up each) and keep the fastest.
 static int plan_autotune(marfa_plan_t* X, cudaStream_t st, int* chosen) {
   WorkSet A[kNVariants];
-  int all[kNVariants][kNGrid + 1];
-  for (int v = 0; v < kNVariants; ++v)
+  int all[kNVariants][kNGrid + 2];
+  for (int v = 0; v < kNVariants; ++v) {
     for (int g = 0; g <= kNGrid; ++g) all[v][g] = v;
+    all[v][kFineKind] = v < kNFineVariants ? v : 0;
+  }
   int r = MARFA_OK;
   for (int v = 0; v < kNVariants && !r; ++v) r = build_work(X->plans, all[v], false, A[v], st);
   cudaEvent_t a = nullptr, b = nullptr;
   cudaError_t e = cudaSuccess;
   if (!r && ((e = cudaEventCreate(&a)) || (e = cudaEventCreate(&b))))
     r = fail(MARFA_E_CUDA, "autotune events: %s", cudaGetErrorString(e));
+  for (int g = 0; g <= kNGrid + 1; ++g)
+    for (int v = 0; v < kNVariants; ++v) X->tune_ms[g][v] = -1.0f;
+  auto time3 = [&](const std::function<void()>& launch, float* out) {
+    launch();
+    cudaEventRecord(a, st);
+    launch();
+    launch();
+    cudaEventRecord(b, st);
+    float ms = 0;
+    if ((e = cudaEventSynchronize(b)) || (e = cudaEventElapsedTime(&ms, a, b)))
+      return fail(MARFA_E_CUDA, "autotune: %s", cudaGetErrorString(e));
+    *out = 0.5f * ms;
+    return MARFA_OK;
+  };
   for (int g = 2; g <= kNGrid && !r; ++g) {
-    for (int v = 0; v < kNVariants && !r; ++v) {
-      launch_grid(A[v], g, st);
-      cudaEventRecord(a, st);
-      launch_grid(A[v], g, st);
-      launch_grid(A[v], g, st);
-      cudaEventRecord(b, st);
-      float ms = 0;
-      if ((e = cudaEventSynchronize(b)) || (e = cudaEventElapsedTime(&ms, a, b)))
-        r = fail(MARFA_E_CUDA, "autotune of grid %d: %s", g, cudaGetErrorString(e));
-      X->tune_ms[g][v] = 0.5f * ms;
-    }
+    for (int v = 0; v < kNVariants && !r; ++v) r = time3([&] { launch_grid(A[v], g, st); }, &X->tune_ms[g][v]);
     int best = 0;
     for (int v = 1; v < kNVariants; ++v)
       if (X->tune_ms[g][v] < X->tune_ms[g][best]) best = v;
     chosen[g] = best;
+  }
+  // the finest grid reads the coarse grids' slots (already filled by the runs above)
+  for (int v = 0; v < kNFineVariants && !r; ++v) r = time3([&] { launch_finest(A[v], st); }, &X->tune_ms[kFineKind][v]);
+  if (!r) {
+    int best = 0;
+    for (int v = 1; v < kNFineVariants; ++v)
+      if (X->tune_ms[kFineKind][v] < X->tune_ms[kFineKind][best]) best = v;
+    chosen[kFineKind] = best;
   }
   if (a) cudaEventDestroy(a);
   if (b) cudaEventDestroy(b);
@@ -1347,7 +1396,7 @@ static int plan_launch_all(marfa_plan_t* X, cudaStream_t st, bool capture) {
       cudaStreamWaitEvent(st, X->join[i], 0);
     }
   rec(2 * (kNGrid + 1), st);
-  launch_fine(W.drd, W.dfi, (int)W.fi.size(), nullptr, W.surr_grid[kNGrid + 1], W.wide, st);
+  launch_finest(W, st);
   rec(2 * (kNGrid + 1) + 1, st);
   cudaError_t e = cudaGetLastError();
   if (e) return fail(MARFA_E_CUDA, "plan launches: %s", cudaGetErrorString(e));
@@ -1389,8 +1438,8 @@ extern "C" int marfa_plan_create(int32_t n_req, const marfa_lines_t* const* line
     for (auto& P : X->plans)
       if (P.rd.mlp) P.rd.mlp = X->mlp;
   }
-  int chosen[kNGrid + 1];
-  for (int g = 0; g <= kNGrid; ++g) chosen[g] = default_variant(g);
+  int chosen[kNGrid + 2];
+  for (int g = 0; g <= kNGrid + 1; ++g) chosen[g] = default_variant(g);
   if (!r && autotune) {
     for (auto& P : X->plans) launch_prep(P, st, false);
     r = plan_autotune(X, st, chosen);
@@ -1464,11 +1513,11 @@ extern "C" int marfa_plan_execute(marfa_plan_t* X, void* stream) {
 extern "C" int marfa_plan_info(const marfa_plan_t* X, int32_t* variant, float* tune_ms, double* kernel_ms) {
   if (!X) return fail(MARFA_E_INVAL, "plan is NULL");
   if (variant)
-    for (int g = 1; g <= kNGrid; ++g) variant[g - 1] = g == 1 ? -1 : X->W.variant[g];
+    for (int g = 1; g <= kFineKind; ++g) variant[g - 1] = g == 1 ? -1 : X->W.variant[g];
   if (tune_ms)
-    for (int g = 1; g <= kNGrid; ++g)
+    for (int g = 1; g <= kFineKind; ++g)
       for (int v = 0; v < kNVariants; ++v)
-        tune_ms[kNVariants * (g - 1) + v] = (X->tuned && g > 1) ? X->tune_ms[g][v] : -1.0f;
+        tune_ms[kNVariants * (g - 1) + v] = X->tuned ? X->tune_ms[g][v] : -1.0f;
   if (kernel_ms) {
     for (int k = 0; k < kKinds; ++k) {
       float ms = 0;
@@ -1481,6 +1530,20 @@ extern "C" int marfa_plan_info(const marfa_plan_t* X, int32_t* variant, float* t
       kernel_ms[k] = ms;
     }
   }
+  return MARFA_OK;
+}
+
+extern "C" int marfa_diag_variants(const int32_t* set, int32_t* get) {
+  if (set) {
+    for (int g = 2; g <= kFineKind; ++g) {
+      const int v = set[g - 1];
+      const int nv = g == kFineKind ? kNFineVariants : kNVariants;
+      if (v < 0 || v >= nv) return fail(MARFA_E_INVAL, "variant %d of kind %d out of range", v, g);
+    }
+    for (int g = 2; g <= kFineKind; ++g) g_default_variant[g].store(set[g - 1], std::memory_order_relaxed);
+  }
+  if (get)
+    for (int g = 1; g <= kFineKind; ++g) get[g - 1] = g == 1 ? -1 : default_variant(g);
   return MARFA_OK;
 }
 
@@ -1625,8 +1688,10 @@ extern "C" int marfa_absorption_noalloc(const marfa_lines_t* lines, const marfa_
   const size_t sz_c = al(8 * pairs), sz_f = al(4 * pairs), sz_b = al(pairs);
   const size_t sz_slots = al(4 * (size_t)P.rd.slots_per_level * nl);
   const size_t sz_lev = al(sizeof(LevelDev) * nl), sz_ls = al(sizeof(LevelSpeciesDev) * nl * ns);
-  std::vector<CoarseItem> coarse;  // grids 2..10 in order, default kernel variants
-  for (int g = 2; g <= kNGrid; ++g) coarse_items(P, g, default_variant(g), coarse);
+  int var[kNGrid + 2];  // the default kernel variants, read once
+  for (int g = 0; g <= kNGrid + 1; ++g) var[g] = default_variant(g);
+  std::vector<CoarseItem> coarse;  // grids 2..10 in order
+  for (int g = 2; g <= kNGrid; ++g) coarse_items(P, g, var[g], coarse);
   const size_t sz_r = al(sizeof(ReqDev)), sz_gi = al(sizeof(G1Item) * P.g1.size()),
                sz_ci = al(sizeof(CoarseItem) * coarse.size()), sz_fi = al(sizeof(FineItem) * P.fine.size());
   const size_t total = sz_c + 3 * sz_f + 2 * sz_b + sz_slots + sz_lev + sz_ls + sz_r + sz_gi + sz_ci + sz_fi;
@@ -1678,14 +1743,22 @@ extern "C" int marfa_absorption_noalloc(const marfa_lines_t* lines, const marfa_
   for (int g = 2; g <= kNGrid; ++g) {  // coarse is ordered by grid
     size_t k1 = k;
     while (k1 < coarse.size() && coarse[k1].grid == g) ++k1;
-    const int v = default_variant(g);
-    if (v == 1)
+    const int v = var[g];
+    if (v == 4 && !surr && !wide && ((R.mech >> g) & 1))
+      launch_coarse_mech(drd, dci + k, (int)(k1 - k), nullptr, st);
+    else if (v == 3 && !surr)
+      launch_coarse_jobs(drd, dci + k, (int)(k1 - k), nullptr, wide, st);
+    else if (v == 1 || v >= 3)
       launch_coarse(drd, dci + k, (int)(k1 - k), nullptr, surr, wide, st);
     else
       launch_coarse_lm(drd, dci + k, (int)(k1 - k), nullptr, surr, v == 2 ? 16 : kLPairs, wide, st);
     k = k1;
   }
-  launch_fine(drd, dfi, (int)P.fine.size(), nullptr, surr, wide, st);
+  if (var[kFineKind] >= 1 && !surr)
+    launch_fine_jobs(drd, dfi, (int)P.fine.size(), nullptr, wide,
+                     var[kFineKind] == 2 && !wide && ((R.mech >> (kNGrid + 1)) & 1), st);
+  else
+    launch_fine(drd, dfi, (int)P.fine.size(), nullptr, surr, wide, st);
   CK(cudaGetLastError());
   return MARFA_OK;
 }

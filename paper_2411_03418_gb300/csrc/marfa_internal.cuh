@@ -101,6 +101,7 @@ struct ReqDev {
   int32_t wide;             // 5-point variant: ownership on panels of four steps, quartic cascade
   int32_t shape;
   int32_t chi_req;          // request asks for the chi-factor
+  int32_t mech;             // bit g (2..10): mech_ok on grid g; bit 11: mech_fine_ok (3-point only)
   const MlpWeights* mlp;    // surrogate weights and guard, null for the plain path
   float out_scale;          // inverse internal scale
   float* out;               // [n_levels][npts]
@@ -134,7 +135,6 @@ constexpr int kG1Warps = 8;          // warps of a G1 CTA, each takes every 8th 
 constexpr int kG1Batch = 512;        // lines staged in shared memory at a time
 constexpr int kLPairs = 32;          // node pairs per CTA of the line-major kernel (or 16)
 constexpr int kLWarps = 4;
-constexpr int kLastLM = 7;           // grids 2..7 line-major, 8..10 two-phase
 constexpr int kCPairs = 32;          // node pairs per warp tile of the two-phase kernel
 constexpr int kCWarps = 4;           // warps (tiles) of a grids-2..10 CTA
 constexpr int kFineThreads = 256;
@@ -177,6 +177,19 @@ void launch_coarse_lm(const ReqDev* reqs, const CoarseItem* items, int n_items, 
                       bool surr, int pairs, bool wide, cudaStream_t st);
 void launch_fine(const ReqDev* reqs, const FineItem* items, int n_items, int64_t* counts, bool surr,
                  bool wide, cudaStream_t st);
+// The flattened variants (plain path only): grids 2..10 over the two-phase tiles with
+// phase 1 spread evenly over the lanes and grouped by Voigt branch (k_coarse_jobs), and
+// the finest grid with (line, G10 panel) jobs spread evenly over 8-lane groups
+// (k_fine_jobs).
+// Grids 2..10 and the finest grid with ownership by mechanism (centre, cut-off edges,
+// chi breakpoints in separate candidate passes, closed forms of ownership.cuh); only for
+// requests whose mech bit of the grid is set (3-point, plain path).
+void launch_coarse_mech(const ReqDev* reqs, const CoarseItem* items, int n_items, int64_t* counts,
+                        cudaStream_t st);
+void launch_coarse_jobs(const ReqDev* reqs, const CoarseItem* items, int n_items, int64_t* counts, bool wide,
+                        cudaStream_t st);
+void launch_fine_jobs(const ReqDev* reqs, const FineItem* items, int n_items, int64_t* counts, bool wide,
+                      bool mech, cudaStream_t st);
 void launch_diag_voigt(const float* x, const float* y, float* out, int64_t n, cudaStream_t st);
 void launch_diag_shape(int shape, const float* x, const float* y, float* out, int64_t n, cudaStream_t st);
 // instructions issued by one probe launch (out: blocks x 256 floats)

@@ -165,6 +165,10 @@ __device__ __forceinline__ int make_zones(int64_t A, int64_t B, int64_t Rc, int6
   return nz;
 }
 
+// A node index relative to a tile, clamped to int16 (comparisons with indices 0..4095 keep
+// their outcome).
+__device__ __forceinline__ int16_t clamp_node16(int v) { return (int16_t)max(min(v, 4096), -4096); }
+
 // Lowest and highest set bit of a non-zero panel mask.
 __device__ __forceinline__ int mask_lowest(uint32_t m) { return __ffs((int)m) - 1; }
 __device__ __forceinline__ int mask_lowest(uint64_t m) { return __ffsll((long long)m) - 1; }
@@ -1330,6 +1334,461 @@ void launch_coarse(const ReqDev* reqs, const CoarseItem* items, int n_items, int
   }
 }
 
+// ------------------------------------------------------------------ grids 2..10 by mechanism
+// Where a line's centre region, cut-off edges and chi breakpoints act on disjoint panels
+// of grid g (mech_ok), its owned panels are the union of closed forms (ownership.cuh).
+// Each warp (32 node pairs of grid g, as in k_coarse) then takes its candidates in
+// separate passes, one per mechanism, each over the lines whose centre, edge or
+// breakpoint position falls near the tile: the centre pass gives a line its ring (or
+// core) as at most two runs of panels, an edge pass at most one panel, a breakpoint
+// pass at most two. A pass decides ownership with a few shifts instead of the general
+// masks, and the lanes of one pass carry similar work (a ring, or one panel's three
+// nodes). The chi-factor is 1 in the centre region (it lies inside the first breakpoint),
+// one branch of Eq. (10) along an edge panel, and decided per node near a breakpoint.
+// Values go through the per-line buffers and phase 2 of k_coarse (pair sums in line
+// order within a pass, passes in a fixed order): results are deterministic.
+template <bool COUNT>
+__global__ void __launch_bounds__(kCWarps * 32, 6)
+    k_coarse_mech(const ReqDev* __restrict__ reqs, const CoarseItem* __restrict__ items,
+                  int64_t* __restrict__ counts) {
+  __shared__ float bufE[kCWarps][32][kCPairs + 1];
+  __shared__ float bufO[kCWarps][32][kCPairs + 1];
+  __shared__ unsigned long long smsk[kCWarps][32];
+  __shared__ int64_t sCnt[kCountFields][kCWarps];
+  const CoarseItem it = items[blockIdx.x];
+  const ReqDev& R = reqs[it.req];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = it.grid;
+  const int lev = it.level;
+  const int64_t m_first = R.m_first[g];
+  const int64_t m_last = m_first + R.npan[g] - 1;
+  const int64_t m0 = it.m0 + (int64_t)kCPairs * warp;
+  int64_t nev = 0, nnear = 0, nmid = 0, nsmall = 0;
+  if (m0 <= m_last + 1) {  // warp-uniform
+    const int s = panel_shift(g);
+    const int64_t P = int64_t(1) << s;
+    const int64_t cut = R.cut_fx;
+    const int64_t base = m0 - 1;
+    const int nb = kCPairs + 1;
+    const uint64_t win = rmask<uint64_t>(m_first, m_last, base, nb);
+    const int64_t xa = base << s, xb = (base + nb) << s;  // span of the mask's panels
+    const int64_t X0 = m0 << s;                            // node j = 0
+    const int64_t R2 = (int64_t)R.R_w * step_fx(g - 1);
+    const LevelDev L = R.lev[lev];
+    const int64_t lo_off = (int64_t)lev * R.n_lines;
+    const bool physical = R.shape < kShapeConst;
+    const bool voigt = R.shape == kShapeVoigt;
+    const float hnode = ldexpf(1.0f, s - 1 - kFixBits);
+    // chi branch along the cut-off edges (no breakpoint lies within two panels of it)
+    const int eb = (cut >= chi_break_fx(0)) + (cut > chi_break_fx(1)) + (cut > chi_break_fx(2));
+    const float eC = eb == 1 ? 1.084f : (eb == 2 ? 0.208f : 0.025f);
+    const float er = eb == 1 ? 0.027f : (eb == 2 ? 0.016f : 0.009f);
+    int nB = 0;
+    if (R.chi_req)
+      for (int b = 0; b < 3 && chi_break_fx(b) <= cut; ++b) nB = b + 1;
+    const int npass = 3 + 2 * nB;
+    float (*bE)[kCPairs + 1] = bufE[warp];
+    float (*bO)[kCPairs + 1] = bufO[warp];
+    unsigned long long* mk = smsk[warp];
+    const int p = lane;
+    float sL = 0.f, cL = 0.f, sR = 0.f, cR = 0.f, sM = 0.f, cM = 0.f;
+    for (int pass = 0; pass < npass; ++pass) {  // warp-uniform
+      // 0 centre; 1, 2 the right and left cut-off edges; then the right and left
+      // positions of each breakpoint. The mechanism sits at c + off.
+      const int64_t off = pass == 0 ? 0
+                        : pass == 1 ? cut
+                        : pass == 2 ? -cut
+                        : ((pass & 1) ? chi_break_fx((pass - 3) >> 1) : -chi_break_fx((pass - 3) >> 1));
+      // positions of c + off that can give panels of the tile
+      const int64_t reach = pass == 0 ? R2 + 2 * P : 2 * P;
+      Bands bd;
+      bd.n = 0;
+      {
+        const int64_t zlo = xa - reach - off, zhi = xb + reach - off;
+        bd.lookup(R, L, &zlo, &zhi, 1);
+      }
+      const int64_t n_cand = bd.total();
+      BandCursor cur;
+      for (int64_t t0 = 0; t0 < n_cand; t0 += 32) {  // warp-uniform
+        const bool valid = t0 + lane < n_cand;
+        const int64_t i = valid ? cur.line(bd, t0 + lane) : 0;
+        uint64_t own = 0;
+        int64_t c = 0;
+        bool chi = false;
+        if (valid) {
+          c = __ldg(R.c + lo_off + i);
+          if (pass == 0) {
+            const int gst = __ldg(R.gstar + lo_off + i);
+            if (gst >= g) {
+              int64_t a1, b1, a2, b2;
+              mech_centre(g, c, gst, R.R_w, a1, b1, a2, b2);
+              own = (rmask<uint64_t>(a1, b1, base, nb) | rmask<uint64_t>(a2, b2, base, nb)) & win;
+            }
+          } else if (pass <= 2) {
+            const int64_t q = pass == 1 ? mech_edge_right(g, c + cut) : mech_edge_left(g, c - cut);
+            if (q != -1) own = rmask<uint64_t>(q, q, base, nb) & win;
+            chi = __ldg(R.flags + lo_off + i) & 1;
+          } else {
+            chi = __ldg(R.flags + lo_off + i) & 1;
+            if (chi) {
+              int64_t q0, q1;
+              mech_kink(g, c + off, q0, q1);
+              if (q0 != -1) own |= rmask<uint64_t>(q0, q0, base, nb);
+              if (q1 != -1) own |= rmask<uint64_t>(q1, q1, base, nb);
+              own &= win;
+            }
+          }
+        }
+        const uint32_t tev = (uint32_t)(own | (own >> 1));
+        if (!__ballot_sync(0xffffffffu, tev != 0)) continue;
+        if (tev) {
+          const float amp = __ldg(R.amp + lo_off + i);
+          const float sx = __ldg(R.sx + lo_off + i);
+          const float y = __ldg(R.yv + lo_off + i);
+          NodeX nx;
+          nx.init(X0 - c, s - 1, sx);
+          const bool use_chi = chi && physical;
+          ChiThr ct;
+          if (use_chi && pass > 2) ct.init(c, X0, s - 1);
+          // runs of owned panels: bits [ba, be] give nodes [2 ba - 2, 2 be] of the tile
+          for (uint64_t rest = own; rest;) {
+            const int ba = __ffsll((long long)rest) - 1;
+            const uint64_t above = ~rest & (~0ull << ba);
+            const int be = above ? __ffsll((long long)above) - 2 : 63;
+            rest &= be >= 63 ? 0ull : (~0ull << (be + 1));
+            const int ja = max(2 * ba - 2, 0), jb = min(2 * be, 2 * kCPairs - 1);
+            for (int j = ja; j <= jb; ++j) {
+              const float jf = (float)j;
+              const float xv = nx.x(jf);
+              float v = amp * (voigt ? voigt_K<false, false, true>(xv, y, kVoigtCells) : shape_f(R.shape, xv, y));
+              if (use_chi) {
+                if (pass > 2)
+                  v *= ct.value(j, nx.absd(jf, s - 1));
+                else if (pass > 0 && eb > 0)
+                  v *= eC * __expf(-er * nx.absd(jf, s - 1));
+              }
+              if (j & 1) bO[lane][j >> 1] = v;
+              else bE[lane][j >> 1] = v;
+              count_eval<COUNT>(voigt, xv, y, nev, nnear, nmid, nsmall);
+            }
+          }
+        }
+        mk[lane] = own;
+        __syncwarp();
+        uint32_t mine = warp_transpose32(tev, lane);
+        while (mine) {
+          const int t = __ffs(mine) - 1;
+          mine &= mine - 1;
+          const uint64_t m2 = mk[t];
+          const float v0 = bE[t][p];
+          if ((m2 >> (p + 1)) & 1ull) {
+            kahan_add(sL, cL, v0);
+            kahan_add(sM, cM, bO[t][p]);
+          }
+          if ((m2 >> p) & 1ull) kahan_add(sR, cR, v0);
+        }
+        __syncwarp();
+      }
+    }
+    float* gp = R.slots + (int64_t)lev * R.slots_per_level + R.slot_off[g];
+    const int64_t np = R.npan[g];
+    const int64_t m = m0 + p;
+    if (m <= m_last) {
+      gp[m - m_first] = sL + cL;
+      gp[np + (m - m_first)] = sM + cM;
+    }
+    if (m - 1 >= m_first && m - 1 <= m_last) gp[2 * np + (m - 1 - m_first)] = sR + cR;
+  }
+  if (COUNT) block_counts<kCWarps>(nev, 0, nnear, nmid, nsmall, sCnt, counts);
+}
+
+void launch_coarse_mech(const ReqDev* reqs, const CoarseItem* items, int n_items, int64_t* counts,
+                        cudaStream_t st) {
+  if (n_items <= 0) return;
+  const int T = kCWarps * 32;
+  if (counts)
+    k_coarse_mech<true><<<n_items, T, 0, st>>>(reqs, items, counts);
+  else
+    k_coarse_mech<false><<<n_items, T, 0, st>>>(reqs, items, counts);
+}
+
+// ------------------------------------------------------------------ grids 2..10, flattened
+// The two-phase tiles (warp = 32 node pairs of grid g, 32 staged candidate lines per
+// round) with phase 1 spread evenly over the lanes. Each owned node of a staged line is
+// one entry (line, node); the round's entries are grouped by the branch of the Voigt
+// function their node falls in (far wing, 6-term series, 15-term series, small-y
+// cell, 9 x 9 cell; found per line from the node ranges between the branches'
+// |x| boundaries), and the warp walks the grouped list 32 entries at a time, so that a
+// line owning twenty nodes no longer holds 31 lanes idle and the lanes of a step take
+// one branch. Values land in the per-line buffers of the two-phase kernel and phase 2
+// sums them per pair in line order, as there: results are deterministic.
+struct __align__(16) JobLine {
+  float qf, hs, phs, amp;   // NodeX of the line relative to the tile's node 0, amplitude
+  float y, phi, cv, clr;    // Voigt y; chi run: chi(j) = cv 2^(clr (j - cja))
+  int16_t mode, cja;        // chi: 0 none, 1 run, 2 by thresholds
+  int16_t r3, r150, r300, l3, l150, l300;  // ChiThr relative to node 0, clamped
+};
+
+// Pairs p of a 32-pair tile whose even node 2p (odd: 2p + 1) satisfies |j + o| hs >= T,
+// j the node index, o = q + phi the centre's offset: j >= ceil(T / hs - o) or
+// j <= floor(-T / hs - o).
+__device__ __forceinline__ void far_side_pairs(float T, float hs, float o, uint32_t& ev, uint32_t& od) {
+  const float tr = fminf(fmaxf(T / hs - o, -1.0e6f), 1.0e6f);
+  const float tl = fminf(fmaxf(-T / hs - o, -1.0e6f), 1.0e6f);
+  const int jr = (int)ceilf(tr), jl = (int)floorf(tl);
+  // even: 2p >= jr <=> p >= ceil(jr / 2); 2p <= jl <=> p <= floor(jl / 2)
+  const int er = (jr + 1) >> 1, el = jl >> 1;
+  // odd: 2p + 1 >= jr <=> p >= ceil((jr - 1) / 2) = jr >> 1; 2p + 1 <= jl <=> p <= floor((jl - 1) / 2)
+  const int orr = jr >> 1, ol = (jl - 1) >> 1;
+  ev = rmask_rel<uint32_t>(er, 31, 32) | rmask_rel<uint32_t>(0, el, 32);
+  od = rmask_rel<uint32_t>(orr, 31, 32) | rmask_rel<uint32_t>(0, ol, 32);
+}
+
+template <bool COUNT, int WIDE>
+__global__ void __launch_bounds__(kCWarps * 32)
+    k_coarse_jobs(const ReqDev* __restrict__ reqs, const CoarseItem* __restrict__ items,
+                  int64_t* __restrict__ counts) {
+  constexpr int kEntCap = 512;  // entries of a round evaluated per chunk
+  __shared__ float bufE[kCWarps][32][kCPairs + 1];
+  __shared__ float bufO[kCWarps][32][kCPairs + 1];
+  __shared__ unsigned long long smsk[kCWarps][32];
+  __shared__ JobLine sJL[kCWarps][32];
+  __shared__ uint16_t sEnt[kCWarps][kEntCap];
+  __shared__ int64_t sCnt[kCountFields][kCWarps];
+  const CoarseItem it = items[blockIdx.x];
+  const ReqDev& R = reqs[it.req];
+  const bool wide = WIDE == 1;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = it.grid;
+  const int lev = it.level;
+  const int64_t m_first = R.m_first[g];
+  const int64_t m_last = m_first + R.npan[g] - 1;
+  const int64_t m0 = it.m0 + (int64_t)kCPairs * warp;
+  int64_t nev = 0, nnear = 0, nmid = 0, nsmall = 0;
+  if (m0 <= m_last + 1) {  // warp-uniform
+    const int s = panel_shift(g);
+    const int64_t cut = R.cut_fx;
+    const int64_t base = m0 - 1;
+    const int nb = kCPairs + 1;
+    const uint64_t win = rmask<uint64_t>(m_first, m_last, base, nb);
+    PanelFrame fr;
+    fr.init(g, base, nb, cut, R.R_w);
+    if (wide) fr.ok = false;
+    const LevelDev L = R.lev[lev];
+    Bands bd;
+    bd.n = 0;
+    {
+      const int64_t pa = max(base, m_first), pb = min(base + nb - 1, m_last);
+      const int al = wide ? s + 2 : s + 1;
+      const int64_t P = int64_t(1) << (wide ? s + 2 : s);
+      const int64_t A = fl_sh(pa << s, al) << al;
+      const int64_t B = (fl_sh(pb << s, al) + 1) << al;
+      int64_t zlo[9], zhi[9];
+      const int nz = make_zones(A, B, (int64_t)R.R_w * step_fx(g - 1), cut, P, R.chi_req, zlo, zhi);
+      if (pa <= pb) bd.lookup(R, L, zlo, zhi, nz);
+    }
+    const int64_t lo_off = (int64_t)lev * R.n_lines;
+    const int64_t X0 = m0 << s;
+    const int64_t xa_t = base << s, xb_t = (base + nb) << s;
+    const int64_t P_t = int64_t(1) << (wide ? s + 2 : s);
+    const bool physical = R.shape < kShapeConst;
+    const bool voigt = R.shape == kShapeVoigt;
+    const int p = lane;
+    float (*bE)[kCPairs + 1] = bufE[warp];
+    float (*bO)[kCPairs + 1] = bufO[warp];
+    unsigned long long* mk = smsk[warp];
+    JobLine* jl = sJL[warp];
+    uint16_t* ent = sEnt[warp];
+    const float hnode = ldexpf(1.0f, s - 1 - kFixBits);  // node step, cm^-1
+    float sL = 0.f, cL = 0.f, sR = 0.f, cR = 0.f, sM = 0.f, cM = 0.f;
+    const int64_t n_cand = bd.total();
+    BandCursor cur;
+    for (int64_t t0 = 0; t0 < n_cand; t0 += 32) {  // warp-uniform
+      const bool valid = t0 + lane < n_cand;
+      const int64_t i = valid ? cur.line(bd, t0 + lane) : 0;
+      uint64_t own = 0;
+      int64_t c = 0;
+      bool chi = false;
+      if (valid) {
+        c = __ldg(R.c + lo_off + i);
+        const int gst = __ldg(R.gstar + lo_off + i);
+        chi = __ldg(R.flags + lo_off + i) & 1;
+        if (fr.ok) {
+          const PanelPos pp = fr.pos(c);
+          if (!owns_nothing_frame(fr, pp, g, gst, chi)) {
+            own = accept_frame<uint64_t>(fr, pp, g, gst, chi) & win;
+            if (own) own &= ~accept_parent_frame<uint64_t>(fr, pp, g, gst, chi);
+          }
+        } else if (!owns_nothing(g, c, gst, chi, cut, xa_t, xb_t, P_t)) {
+          own = owned_any<uint64_t>(wide, g, c, gst, chi, cut, R.R_w, base, nb) & win;
+        }
+      }
+      if (!__ballot_sync(0xffffffffu, own != 0)) continue;
+      // even nodes 2p of the touched pairs, odd nodes 2p + 1 of the owned panels m0 + p
+      const uint32_t tev = (uint32_t)(own | (own >> 1)), tod = (uint32_t)(own >> 1);
+      // per branch (0 far, 1 6-term, 2 15-term, 3 small-y cell, 4 9 x 9 cell) the nodes
+      uint32_t ce0 = 0, ce1 = 0, ce2 = 0, ce3 = 0, ce4 = 0, co0 = 0, co1 = 0, co2 = 0, co3 = 0, co4 = 0;
+      if (own) {
+        const float amp = __ldg(R.amp + lo_off + i);
+        const float sx = __ldg(R.sx + lo_off + i);
+        const float y = __ldg(R.yv + lo_off + i);
+        NodeX nx;
+        nx.init(X0 - c, s - 1, sx);
+        JobLine J;
+        J.qf = nx.qf; J.hs = nx.hs; J.phs = nx.phs; J.amp = amp;
+        J.y = y; J.phi = nx.phi; J.cv = 1.0f; J.clr = 0.0f;
+        J.mode = 0; J.cja = 0;
+        J.r3 = J.r150 = J.r300 = J.l3 = J.l150 = J.l300 = 0;
+        if (chi && physical) {
+          ChiThr ct;
+          ct.init(c, X0, s - 1);
+          const int ja = max(__ffsll((long long)own) - 2, 0) * 2;
+          const int jb = min(63 - __clzll((long long)own), kCPairs - 1) * 2 + 1;
+          if (ct.uniform(ja, jb)) {
+            ChiRun cr;
+            cr.init(ct, ja, nx.absd((float)ja, s - 1), s - 1);
+            J.mode = 1; J.cja = (int16_t)ja; J.cv = cr.v; J.clr = cr.lr;
+          } else {
+            J.mode = 2;
+            J.r3 = clamp_node16(ct.r3); J.r150 = clamp_node16(ct.r150); J.r300 = clamp_node16(ct.r300);
+            J.l3 = clamp_node16(ct.l3); J.l150 = clamp_node16(ct.l150); J.l300 = clamp_node16(ct.l300);
+          }
+        }
+        jl[lane] = J;
+        if (voigt) {
+          // |x| boundaries T1 <= T2 <= T3 of the branches: below T1 a cell (small-y for
+          // y < 1/4), T1..T2 the 15-term series (empty for y < 1), T2..T3 the 6-term
+          // series, from T3 on the far wing
+          const float y2 = y * y;
+          const float T3 = sqrtf(fmaxf(1.0e4f - y2, 0.0f));
+          const bool narrow = y < 1.0f;
+          const float T1 = narrow ? 12.0f : sqrtf(fmaxf(20.25f - y2, 0.0f));
+          const float T2 = narrow ? 12.0f : sqrtf(fmaxf(64.0f - y2, 0.0f));
+          const float o = nx.qf + nx.phi;
+          uint32_t e1, o1, e2, o2, e3, o3;
+          far_side_pairs(T1, nx.hs, o, e1, o1);
+          far_side_pairs(T2, nx.hs, o, e2, o2);
+          far_side_pairs(T3, nx.hs, o, e3, o3);
+          ce0 = tev & e3;       co0 = tod & o3;
+          ce1 = tev & e2 & ~e3; co1 = tod & o2 & ~o3;
+          ce2 = tev & e1 & ~e2; co2 = tod & o1 & ~o2;
+          const uint32_t le = tev & ~e1, lo = tod & ~o1;
+          const bool small = y < 0.25f;
+          ce3 = small ? le : 0u; co3 = small ? lo : 0u;
+          ce4 = small ? 0u : le; co4 = small ? 0u : lo;
+        } else {
+          ce0 = tev;
+          co0 = tod;
+        }
+      }
+      mk[lane] = own;
+      // entries grouped by branch, each group in line (lane) order: inclusive scans of
+      // the five counts, two 16-bit fields per word
+      const int n0 = __popc(ce0) + __popc(co0), n1 = __popc(ce1) + __popc(co1), n2 = __popc(ce2) + __popc(co2),
+                n3 = __popc(ce3) + __popc(co3), n4 = __popc(ce4) + __popc(co4);
+      int a01 = n0 | (n1 << 16), a23 = n2 | (n3 << 16), a4 = n4;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v01 = __shfl_up_sync(0xffffffffu, a01, o);
+        const int v23 = __shfl_up_sync(0xffffffffu, a23, o);
+        const int v4 = __shfl_up_sync(0xffffffffu, a4, o);
+        if (lane >= o) {
+          a01 += v01;
+          a23 += v23;
+          a4 += v4;
+        }
+      }
+      const int t01 = __shfl_sync(0xffffffffu, a01, 31), t23 = __shfl_sync(0xffffffffu, a23, 31);
+      const int t4 = __shfl_sync(0xffffffffu, a4, 31);
+      // this lane's first entry in each group
+      const int b0 = (a01 & 0xffff) - n0;
+      const int b1 = (t01 & 0xffff) + (a01 >> 16) - n1;
+      const int b2 = (t01 & 0xffff) + (t01 >> 16) + (a23 & 0xffff) - n2;
+      const int b3 = (t01 & 0xffff) + (t01 >> 16) + (t23 & 0xffff) + (a23 >> 16) - n3;
+      const int b4 = (t01 & 0xffff) + (t01 >> 16) + (t23 & 0xffff) + (t23 >> 16) + a4 - n4;
+      const int total = (t01 & 0xffff) + (t01 >> 16) + (t23 & 0xffff) + (t23 >> 16) + t4;
+      // the list in chunks of kEntCap entries: each lane writes its entries that fall in
+      // the chunk, then the warp evaluates the chunk, 32 entries per step
+      for (int c0 = 0; c0 < total; c0 += kEntCap) {  // warp-uniform
+        const int c1 = c0 + kEntCap;
+        auto put = [&](int w, uint32_t me, uint32_t mo) {
+          for (uint32_t m = me; m; m &= m - 1, ++w)
+            if (w >= c0 && w < c1) ent[w - c0] = (uint16_t)((lane << 6) | (2 * (__ffs(m) - 1)));
+          for (uint32_t m = mo; m; m &= m - 1, ++w)
+            if (w >= c0 && w < c1) ent[w - c0] = (uint16_t)((lane << 6) | (2 * (__ffs(m) - 1) + 1));
+        };
+        put(b0, ce0, co0);
+        put(b1, ce1, co1);
+        put(b2, ce2, co2);
+        put(b3, ce3, co3);
+        put(b4, ce4, co4);
+        __syncwarp();
+        const int nc = min(total - c0, kEntCap);
+#pragma unroll 1
+        for (int e0 = 0; e0 < nc; e0 += 32) {  // warp-uniform
+          const int e = e0 + lane;
+          if (e >= nc) continue;
+          const int en = ent[e];
+          const int li = en >> 6, j = en & 63;
+          const JobLine J = jl[li];
+          const float jf = (float)j;
+          const float xv = fmaf(jf + J.qf, J.hs, J.phs);
+          float v = J.amp * (voigt ? voigt_K<false, false, true>(xv, J.y, kVoigtCells) : shape_f(R.shape, xv, J.y));
+          if (J.mode == 1) {
+            v *= J.clr != 0.0f ? J.cv * exp2f(J.clr * (float)(j - J.cja)) : J.cv;
+          } else if (J.mode == 2) {
+            const ChiThr ct{J.r3, J.r150, J.r300, J.l3, J.l150, J.l300};
+            v *= ct.value(j, fabsf((jf + J.qf) + J.phi) * hnode);
+          }
+          if (j & 1) bO[li][j >> 1] = v;
+          else bE[li][j >> 1] = v;
+          count_eval<COUNT>(voigt, xv, J.y, nev, nnear, nmid, nsmall);
+        }
+        __syncwarp();
+      }
+      // phase 2 (as in k_coarse): the staged lines owning pair p's panels, in line order
+      uint32_t mine = warp_transpose32(tev, lane);
+      while (mine) {
+        const int t = __ffs(mine) - 1;
+        mine &= mine - 1;
+        const uint64_t m2 = mk[t];
+        const float v0 = bE[t][p];
+        if ((m2 >> (p + 1)) & 1ull) {
+          kahan_add(sL, cL, v0);
+          kahan_add(sM, cM, bO[t][p]);
+        }
+        if ((m2 >> p) & 1ull) kahan_add(sR, cR, v0);
+      }
+      __syncwarp();
+    }
+    float* gp = R.slots + (int64_t)lev * R.slots_per_level + R.slot_off[g];
+    const int64_t np = R.npan[g];
+    const int64_t m = m0 + p;
+    if (m <= m_last) {
+      gp[m - m_first] = sL + cL;
+      gp[np + (m - m_first)] = sM + cM;
+    }
+    if (m - 1 >= m_first && m - 1 <= m_last) gp[2 * np + (m - 1 - m_first)] = sR + cR;
+  }
+  if (COUNT) block_counts<kCWarps>(nev, 0, nnear, nmid, nsmall, sCnt, counts);
+}
+
+void launch_coarse_jobs(const ReqDev* reqs, const CoarseItem* items, int n_items, int64_t* counts, bool wide,
+                        cudaStream_t st) {
+  if (n_items <= 0) return;
+  const int T = kCWarps * 32;
+  if (counts) {
+    if (wide)
+      k_coarse_jobs<true, 1><<<n_items, T, 0, st>>>(reqs, items, counts);
+    else
+      k_coarse_jobs<true, 0><<<n_items, T, 0, st>>>(reqs, items, counts);
+  } else if (wide) {
+    k_coarse_jobs<false, 1><<<n_items, T, 0, st>>>(reqs, items, counts);
+  } else {
+    k_coarse_jobs<false, 0><<<n_items, T, 0, st>>>(reqs, items, counts);
+  }
+}
+
 // ------------------------------------------------------------------ finest grid + cascade
 // A CTA owns 1024 consecutive finest nodes of one level; warp w owns 128 of them
 // (16 G10 panels of 8 nodes). Each warp loads 32 candidate lines at a time; the loading
@@ -1351,6 +1810,109 @@ struct __align__(16) FineChi {
   int r3, r150, r300, l3, l150, l300;  // ChiThr relative to the warp's first node
   int on, pad;                          // chi-factor applies
 };
+
+// The finest-grid epilogue shared by the finest-grid kernels: node k0 + q of this thread
+// holds out[q] (its finest-grid sum); add the quadratic (quartic: 5-point variant)
+// through the panel-local slots of every coarse grid, scale, and write the CTA's tile
+// [it.k0, it.k0 + kFineTile) of level lev to the output with aligned vector stores.
+// Every thread of the CTA calls it (it ends with a CTA barrier and the stores).
+__device__ __forceinline__ void fine_cascade_store(const ReqDev& R, const FineItem& it, int lev, bool wide,
+                                                   int64_t k0, float (&out)[kFinePerThread], float* tile) {
+  const int tid = threadIdx.x;
+  uint32_t valid = 0;
+#pragma unroll
+  for (int q = 0; q < kFinePerThread; ++q)
+    if (k0 + q >= R.k_lo && k0 + q <= R.k_hi) valid |= 1u << q;
+  if (valid) {
+    // cascade: quadratic through the panel-local L, M, R of every coarse grid
+    const float* sl = R.slots + (int64_t)lev * R.slots_per_level;
+#pragma unroll
+    for (int g = 1; g <= kNGrid; ++g) {
+      const int sh = 13 - g;  // finest nodes per panel of grid g: 2^(13-g)
+      const int64_t np = R.npan[g];
+      const float* gp = sl + R.slot_off[g];
+      if (wide) {
+        // 5-point: the four-step panel M4 is two-step panels 2 M4, 2 M4 + 1 (m_first is
+        // even); its nodes are L, M, R of the first and M, R of the second
+        const int64_t M4 = k0 >> (sh + 1);
+        const int64_t i0 = 2 * M4 - R.m_first[g];
+        float v0 = __ldg(gp + i0), v1 = __ldg(gp + np + i0), v2 = __ldg(gp + 2 * np + i0);
+        float v3 = __ldg(gp + np + i0 + 1), v4 = __ldg(gp + 2 * np + i0 + 1);
+        if (g == 1) {  // the kG1Split partial copies of grid 1, summed in part order
+#pragma unroll
+          for (int part = 1; part < kG1Split; ++part) {
+            const float* gq = gp + 3 * np * part;
+            v0 += __ldg(gq + i0);
+            v1 += __ldg(gq + np + i0);
+            v2 += __ldg(gq + 2 * np + i0);
+            v3 += __ldg(gq + np + i0 + 1);
+            v4 += __ldg(gq + 2 * np + i0 + 1);
+          }
+        }
+        const int off0 = (int)(k0 - (M4 << (sh + 1)));
+        const float inv_h = ldexpf(1.0f, 1 - sh);
+#pragma unroll
+        for (int q = 0; q < kFinePerThread; ++q) {
+          const float t = (float)(off0 + q) * inv_h;  // position in steps of h_g, [0, 4)
+          const float d1 = t - 1.0f, d2 = t - 2.0f, d3 = t - 3.0f, d4 = t - 4.0f;
+          // quartic Lagrange weights of the nodes 0..4
+          const float w0 = (d1 * d2) * (d3 * d4) * (1.0f / 24.0f);
+          const float w1 = -(t * d2) * (d3 * d4) * (1.0f / 6.0f);
+          const float w2 = (t * d1) * (d3 * d4) * 0.25f;
+          const float w3 = -(t * d1) * (d2 * d4) * (1.0f / 6.0f);
+          const float w4 = (t * d1) * (d2 * d3) * (1.0f / 24.0f);
+          out[q] += fmaf(v0, w0, fmaf(v1, w1, fmaf(v2, w2, fmaf(v3, w3, v4 * w4))));
+        }
+        continue;
+      }
+      const int64_t m = k0 >> sh;
+      const int64_t idx = m - R.m_first[g];
+      float vL = __ldg(gp + idx), vM = __ldg(gp + np + idx), vR = __ldg(gp + 2 * np + idx);
+      if (g == 1) {  // the kG1Split partial copies of grid 1, summed in part order
+#pragma unroll
+        for (int part = 1; part < kG1Split; ++part) {
+          const float* gq = gp + 3 * np * part;
+          vL += __ldg(gq + idx);
+          vM += __ldg(gq + np + idx);
+          vR += __ldg(gq + 2 * np + idx);
+        }
+      }
+      const int off0 = (int)(k0 - (m << sh));
+      const float inv_h = ldexpf(1.0f, 1 - sh);
+#pragma unroll
+      for (int q = 0; q < kFinePerThread; ++q) {
+        const float t = (float)(off0 + q) * inv_h;  // position in steps of h_g, [0, 2)
+        const float w0 = (t - 1.0f) * (t - 2.0f) * 0.5f;
+        const float w1 = t * (2.0f - t);
+        const float w2 = t * (t - 1.0f) * 0.5f;
+        out[q] += fmaf(vL, w0, fmaf(vM, w1, vR * w2));
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kFinePerThread; ++q) tile[kFinePerThread * tid + q] = out[q] * R.out_scale;
+  }
+  __syncthreads();
+  // write the valid part [a, b] of the tile
+  const int64_t a = max(it.k0, R.k_lo), b = min(it.k0 + kFineTile - 1, R.k_hi);
+  if (a <= b) {
+    float* row = R.out + (int64_t)lev * R.npts;
+    const int64_t i0 = a - R.k_lo;           // first output index
+    const int n = (int)(b - a + 1);
+    const int t0 = (int)(a - it.k0);         // its position in the tile
+    float* dst = row + i0;
+    int head = (int)((16 - ((uintptr_t)dst & 15)) & 15) / 4;
+    if (head > n) head = n;
+    if (tid < head) dst[tid] = tile[t0 + tid];
+    const int nv = (n - head) / 4;
+    float4* d4 = reinterpret_cast<float4*>(dst + head);
+    for (int v = tid; v < nv; v += kFineThreads) {
+      const int e = t0 + head + 4 * v;
+      d4[v] = make_float4(tile[e], tile[e + 1], tile[e + 2], tile[e + 3]);
+    }
+    const int done = head + 4 * nv;
+    if (tid < n - done) dst[done + tid] = tile[t0 + done + tid];
+  }
+}
 
 template <bool COUNT, bool SURR, int WIDE>
 __global__ void __launch_bounds__(kFineThreads)
@@ -1519,104 +2081,247 @@ __global__ void __launch_bounds__(kFineThreads)
   }
   if (SURR && use_mlp) q_flush(warp_queue(dsm), qn, S, fine_apply);  // warp-uniform
   __syncwarp();
-  uint32_t valid = 0;
-#pragma unroll
-  for (int q = 0; q < kFinePerThread; ++q)
-    if (k0 + q >= R.k_lo && k0 + q <= R.k_hi) valid |= 1u << q;
-  if (valid) {
-    // cascade: quadratic through the panel-local L, M, R of every coarse grid
-    const float* sl = R.slots + (int64_t)lev * R.slots_per_level;
+  {
     float out[kFinePerThread];
 #pragma unroll
     for (int q = 0; q < kFinePerThread; ++q)
       out[q] = sAcc[warp][kFinePerThread * lane + q] + sCmp[warp][kFinePerThread * lane + q];
-#pragma unroll
-    for (int g = 1; g <= kNGrid; ++g) {
-      const int sh = 13 - g;  // finest nodes per panel of grid g: 2^(13-g)
-      const int64_t np = R.npan[g];
-      const float* gp = sl + R.slot_off[g];
-      if (wide) {
-        // 5-point: the four-step panel M4 is two-step panels 2 M4, 2 M4 + 1 (m_first is
-        // even); its nodes are L, M, R of the first and M, R of the second
-        const int64_t M4 = k0 >> (sh + 1);
-        const int64_t i0 = 2 * M4 - R.m_first[g];
-        float v0 = __ldg(gp + i0), v1 = __ldg(gp + np + i0), v2 = __ldg(gp + 2 * np + i0);
-        float v3 = __ldg(gp + np + i0 + 1), v4 = __ldg(gp + 2 * np + i0 + 1);
-        if (g == 1) {  // the kG1Split partial copies of grid 1, summed in part order
-#pragma unroll
-          for (int part = 1; part < kG1Split; ++part) {
-            const float* gq = gp + 3 * np * part;
-            v0 += __ldg(gq + i0);
-            v1 += __ldg(gq + np + i0);
-            v2 += __ldg(gq + 2 * np + i0);
-            v3 += __ldg(gq + np + i0 + 1);
-            v4 += __ldg(gq + 2 * np + i0 + 1);
-          }
-        }
-        const int off0 = (int)(k0 - (M4 << (sh + 1)));
-        const float inv_h = ldexpf(1.0f, 1 - sh);
-#pragma unroll
-        for (int q = 0; q < kFinePerThread; ++q) {
-          const float t = (float)(off0 + q) * inv_h;  // position in steps of h_g, [0, 4)
-          const float d1 = t - 1.0f, d2 = t - 2.0f, d3 = t - 3.0f, d4 = t - 4.0f;
-          // quartic Lagrange weights of the nodes 0..4
-          const float w0 = (d1 * d2) * (d3 * d4) * (1.0f / 24.0f);
-          const float w1 = -(t * d2) * (d3 * d4) * (1.0f / 6.0f);
-          const float w2 = (t * d1) * (d3 * d4) * 0.25f;
-          const float w3 = -(t * d1) * (d2 * d4) * (1.0f / 6.0f);
-          const float w4 = (t * d1) * (d2 * d3) * (1.0f / 24.0f);
-          out[q] += fmaf(v0, w0, fmaf(v1, w1, fmaf(v2, w2, fmaf(v3, w3, v4 * w4))));
-        }
-        continue;
-      }
-      const int64_t m = k0 >> sh;
-      const int64_t idx = m - R.m_first[g];
-      float vL = __ldg(gp + idx), vM = __ldg(gp + np + idx), vR = __ldg(gp + 2 * np + idx);
-      if (g == 1) {  // the kG1Split partial copies of grid 1, summed in part order
-#pragma unroll
-        for (int part = 1; part < kG1Split; ++part) {
-          const float* gq = gp + 3 * np * part;
-          vL += __ldg(gq + idx);
-          vM += __ldg(gq + np + idx);
-          vR += __ldg(gq + 2 * np + idx);
-        }
-      }
-      const int off0 = (int)(k0 - (m << sh));
-      const float inv_h = ldexpf(1.0f, 1 - sh);
-#pragma unroll
-      for (int q = 0; q < kFinePerThread; ++q) {
-        const float t = (float)(off0 + q) * inv_h;  // position in steps of h_g, [0, 2)
-        const float w0 = (t - 1.0f) * (t - 2.0f) * 0.5f;
-        const float w1 = t * (2.0f - t);
-        const float w2 = t * (t - 1.0f) * 0.5f;
-        out[q] += fmaf(vL, w0, fmaf(vM, w1, vR * w2));
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < kFinePerThread; ++q) tile[kFinePerThread * tid + q] = out[q] * R.out_scale;
-  }
-  __syncthreads();
-  // write the valid part [a, b] of the tile
-  const int64_t a = max(it.k0, R.k_lo), b = min(it.k0 + kFineTile - 1, R.k_hi);
-  if (a <= b) {
-    float* row = R.out + (int64_t)lev * R.npts;
-    const int64_t i0 = a - R.k_lo;           // first output index
-    const int n = (int)(b - a + 1);
-    const int t0 = (int)(a - it.k0);         // its position in the tile
-    float* dst = row + i0;
-    int head = (int)((16 - ((uintptr_t)dst & 15)) & 15) / 4;
-    if (head > n) head = n;
-    if (tid < head) dst[tid] = tile[t0 + tid];
-    const int nv = (n - head) / 4;
-    float4* d4 = reinterpret_cast<float4*>(dst + head);
-    for (int v = tid; v < nv; v += kFineThreads) {
-      const int e = t0 + head + 4 * v;
-      d4[v] = make_float4(tile[e], tile[e + 1], tile[e + 2], tile[e + 3]);
-    }
-    const int done = head + 4 * nv;
-    if (tid < n - done) dst[done + tid] = tile[t0 + done + tid];
+    fine_cascade_store(R, it, lev, wide, k0, out, tile);
   }
   if (COUNT) block_counts<NW>(nev, nmlp, nnear, nmid, nsmall, red, counts);
+}
+
+// The finest grid with flattened jobs. The tiles, candidate bands and staged lines are
+// those of k_fine; what differs is how a warp spreads the evaluations over its lanes.
+// A job is one staged line on one of the warp's 16 G10 panels (eight nodes, one per
+// lane of an 8-lane group). The round's jobs form one list, far-wing jobs first (the
+// two-term series, at the panel's centre |z| >= 100), then the others, each part in line
+// order, so that the four groups of a warp step mostly evaluate the same line on
+// neighbouring panels (one branch of the Voigt function) and no group waits for another
+// group's longer list. Group gi of a step adds into its own accumulator row (plain FP32;
+// the four rows of a node are merged with TwoSum in the epilogue), so the order of every
+// sum is fixed by the job list: results are deterministic.
+struct __align__(16) FineChi16 {
+  int16_t r3, r150, r300, l3, l150, l300;  // ChiThr relative to the warp's first node, clamped
+  int16_t on, pad;
+};
+
+// MECH: where the centre region, cut-off edges and chi breakpoints lie apart
+// (mech_fine_ok), the candidates come in one pass per mechanism, each with its node range
+// in closed form (mech_fine_*): the centre pass takes the lines with g* = 11 (chi = 1
+// there: the region lies inside the first breakpoint), the edge and breakpoint passes
+// the lines whose edge or breakpoint falls near the warp's nodes.
+template <bool COUNT, int WIDE, bool MECH>
+__global__ void __launch_bounds__(kFineThreads, 4)
+    k_fine_jobs(const ReqDev* __restrict__ reqs, const FineItem* __restrict__ items,
+                int64_t* __restrict__ counts) {
+  constexpr int NW = kFineThreads / 32;
+  constexpr int kWarpNodes = kFinePerThread * 32;  // 128 nodes = 16 G10 panels
+  __shared__ __align__(16) float stab[kVoigtTableFloats];
+  __shared__ FineLine sL[NW][32];
+  __shared__ FineChi16 sC[NW][32];
+  // per job group gi a row over the CTA's nodes (dynamic shared memory, kFineJobsDyn
+  // bytes); row 0 doubles as the output tile (a lane reads its four nodes of every row
+  // before it overwrites them in row 0)
+  extern __shared__ __align__(16) unsigned char dsm[];
+  float (*sAcc)[NW * kWarpNodes] = reinterpret_cast<float (*)[NW * kWarpNodes]>(dsm);
+  __shared__ uint16_t sJob[NW][32 * 16];
+  __shared__ int64_t red[kCountFields][NW];
+  const FineItem it = items[blockIdx.x];
+  const ReqDev& R = reqs[it.req];
+  const bool wide = WIDE == 1;
+  const int lev = it.level;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  voigt_table_to_smem(stab);
+#pragma unroll
+  for (int g = 0; g < 4; ++g)
+#pragma unroll
+    for (int q = 0; q < kFinePerThread; ++q) sAcc[g][kWarpNodes * warp + 32 * q + lane] = 0.0f;
+  const int64_t kw = it.k0 + (int64_t)kWarpNodes * warp;  // first node of the warp
+  const int64_t k0 = kw + kFinePerThread * lane;           // first node of the lane's output
+  const int64_t cut = R.cut_fx;
+  const LevelDev L = R.lev[lev];
+  const int wlo = (int)max(R.k_lo - kw, (int64_t)0);
+  const int whi = (int)min(R.k_hi - kw, (int64_t)(kWarpNodes - 1));
+  const int64_t Xa = kw << kFineShift;
+  const int64_t P10 = int64_t(1) << panel_shift(kNGrid);
+  Bands bd;
+  bd.n = 0;
+  if (!MECH && wlo <= whi) {
+    int64_t zlo[9], zhi[9];
+    const int nz = make_zones((kw + wlo) << kFineShift, (kw + whi) << kFineShift, (int64_t)R.R_w * step_fx(kNGrid),
+                              cut, wide ? P10 << 1 : P10, R.chi_req, zlo, zhi);
+    bd.lookup(R, L, zlo, zhi, nz);
+  }
+  __syncthreads();
+  int64_t nev = 0, nnear = 0, nmid = 0, nsmall = 0;
+  int nB = 0;
+  if (MECH && R.chi_req)
+    for (int b = 0; b < 3 && chi_break_fx(b) <= cut; ++b) nB = b + 1;
+  const int npass = MECH ? 3 + 2 * nB : 1;
+  for (int pass = 0; pass < npass && wlo <= whi; ++pass) {  // warp-uniform
+    // the mechanism of this pass sits at c + off (MECH only)
+    const int64_t off = pass == 0 ? 0
+                      : pass == 1 ? cut
+                      : pass == 2 ? -cut
+                      : ((pass & 1) ? chi_break_fx((pass - 3) >> 1) : -chi_break_fx((pass - 3) >> 1));
+    if (MECH) {
+      const int64_t reach = (pass == 0 ? (int64_t)R.R_w * step_fx(kNGrid) : 0) + P10 + 1;
+      const int64_t zlo = ((kw + wlo) << kFineShift) - reach - off, zhi = ((kw + whi) << kFineShift) + reach - off;
+      bd.lookup(R, L, &zlo, &zhi, 1);
+    }
+    const int64_t pbase = kw >> 3;
+    const int64_t lo_off = (int64_t)lev * R.n_lines;
+    const bool physical = R.shape < kShapeConst;
+    const bool voigt = R.shape == kShapeVoigt;
+    const int gi = lane >> 3, t8 = lane & 7;
+    const int64_t n_cand = bd.total();
+    BandCursor cur;
+    uint16_t* jobs = sJob[warp];
+    for (int64_t t0 = 0; t0 < n_cand; t0 += 32) {  // warp-uniform
+      const bool valid = t0 + lane < n_cand;
+      const int64_t i = valid ? cur.line(bd, t0 + lane) : 0;
+      uint32_t pm = 0;
+      int klo = 0, khi = -1;
+      int64_t c = 0;
+      bool chi = false;
+      if (valid && MECH) {
+        c = __ldg(R.c + lo_off + i);
+        int64_t a = 1, b = 0;
+        if (pass == 0) {
+          mech_fine_centre(c, __ldg(R.gstar + lo_off + i), R.R_w, a, b);
+        } else {
+          chi = __ldg(R.flags + lo_off + i) & 1;
+          if (pass == 1) mech_fine_edge_right(c + cut, a, b);
+          else if (pass == 2) mech_fine_edge_left(c - cut, a, b);
+          else if (chi) mech_fine_kink(c + off, a, b);
+        }
+        klo = (int)max(min(a - kw, (int64_t)kWarpNodes), (int64_t)wlo);
+        khi = (int)min(max(b - kw, (int64_t)-1), (int64_t)whi);
+        if (klo <= khi) pm = rmask<uint32_t>(klo >> 3, khi >> 3, 0, 16);
+      } else if (valid) {
+        c = __ldg(R.c + lo_off + i);
+        const int gst = __ldg(R.gstar + lo_off + i);
+        chi = __ldg(R.flags + lo_off + i) & 1;
+        klo = (int)max(cl_sh(c - cut, kFineShift) - kw, (int64_t)wlo);
+        khi = (int)min(fl_sh(c + cut, kFineShift) - kw, (int64_t)whi);
+        if (klo <= khi) {
+          const int s10 = panel_shift(kNGrid);
+          pm = ~accept_mask_s<uint32_t>(kNGrid, c, gst, chi, cut, R.R_w, pbase, 16, s10 + wide, s10) &
+               rmask<uint32_t>(klo >> 3, khi >> 3, 0, 16);
+        }
+      }
+      if (!__ballot_sync(0xffffffffu, pm != 0)) continue;
+      __syncwarp();  // the previous round's jobs are done with the staged lines
+      uint32_t far = 0;
+      if (pm) {
+        NodeX nx;
+        nx.init(Xa - c, kFineShift, __ldg(R.sx + lo_off + i));
+        FineLine fl;
+        fl.klo = klo;
+        fl.khi = khi;
+        fl.amp = __ldg(R.amp + lo_off + i);
+        fl.y = __ldg(R.yv + lo_off + i);
+        fl.qf = nx.qf;
+        fl.hs = nx.hs;
+        fl.phs = nx.phs;
+        fl.phi = nx.phi;
+        sL[warp][lane] = fl;
+        FineChi16 fc;
+        fc.on = chi && physical && !(MECH && pass == 0);
+        fc.pad = 0;
+        if (fc.on) {
+          ChiThr ct;
+          ct.init(c, Xa, kFineShift);
+          fc.r3 = clamp_node16(ct.r3); fc.r150 = clamp_node16(ct.r150); fc.r300 = clamp_node16(ct.r300);
+          fc.l3 = clamp_node16(ct.l3); fc.l150 = clamp_node16(ct.l150); fc.l300 = clamp_node16(ct.l300);
+          if (ct.uniform(klo, khi) && ct.branch(klo) == 0) fc.on = 0;
+        }
+        sC[warp][lane] = fc;
+        if (voigt) {
+          // panels whose centre node lies in the far wing |z| >= 100: |j + q + phi| hs >= X
+          const float X = sqrtf(fmaxf(1.0e4f - fl.y * fl.y, 0.0f));
+          const float t = fminf(X / fl.hs, 1.0e6f);
+          const float off = 3.5f + nx.qf + nx.phi;  // centre node of panel p is 8 p + 3.5
+          const int pr = (int)ceilf(fmaxf((t - off) * 0.125f, -1.0f));    // first far panel right of c
+          const int pl = (int)floorf(fminf((-t - off) * 0.125f, 17.0f));  // last far panel left of c
+          far = (rmask<uint32_t>(pr, 15, 0, 16) | rmask<uint32_t>(0, pl, 0, 16)) & pm;
+        }
+      }
+      // job list: far jobs, then the rest, each in line order (lane order, then panel)
+      const int nf = __popc(far), nn = __popc(pm & ~far);
+      int pre = nf | (nn << 16);  // inclusive scan of both counts at once
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, pre, o);
+        if (lane >= o) pre += v;
+      }
+      const int tot = __shfl_sync(0xffffffffu, pre, 31);
+      const int F = tot & 0xffff, J = F + (tot >> 16);
+      int pf = (pre & 0xffff) - nf, pn = F + (pre >> 16) - nn;
+      for (uint32_t m = far; m; m &= m - 1) jobs[pf++] = (uint16_t)((lane << 4) | (__ffs(m) - 1));
+      for (uint32_t m = pm & ~far; m; m &= m - 1) jobs[pn++] = (uint16_t)((lane << 4) | (__ffs(m) - 1));
+      __syncwarp();
+      float* acc = &sAcc[gi][kWarpNodes * warp];
+#pragma unroll 1
+      for (int e0 = 0; e0 < J; e0 += 4) {  // warp-uniform
+        const int e = e0 + gi;
+        if (e >= J) continue;
+        const int job = jobs[e];
+        const int li = job >> 4;
+        const int j = 8 * (job & 15) + t8;
+        const FineLine fl = sL[warp][li];
+        if (j < fl.klo || j > fl.khi) continue;
+        const float jf = (float)j;
+        const float xv = fmaf(jf + fl.qf, fl.hs, fl.phs);
+        float v = fl.amp * (voigt ? voigt_K<true, false, true>(xv, fl.y, stab) : shape_f(R.shape, xv, fl.y));
+        const FineChi16 fc = sC[warp][li];
+        if (fc.on) {
+          const ChiThr ct{fc.r3, fc.r150, fc.r300, fc.l3, fc.l150, fc.l300};
+          v *= ct.value(j, fabsf((jf + fl.qf) + fl.phi) * ldexpf(1.0f, -kFineBits));
+        }
+        acc[j] += v;
+        count_eval<COUNT>(voigt, xv, fl.y, nev, nnear, nmid, nsmall);
+      }
+      __syncwarp();
+    }
+  }
+  __syncwarp();
+  float out[kFinePerThread];
+#pragma unroll
+  for (int q = 0; q < kFinePerThread; ++q) {
+    const int n = kFinePerThread * tid + q;
+    float s_ = sAcc[0][n], c_ = 0.0f;
+    comp_merge(s_, c_, sAcc[1][n], 0.0f);
+    comp_merge(s_, c_, sAcc[2][n], 0.0f);
+    comp_merge(s_, c_, sAcc[3][n], 0.0f);
+    out[q] = s_ + c_;
+  }
+  fine_cascade_store(R, it, lev, wide, k0, out, sAcc[0]);
+  if (COUNT) block_counts<NW>(nev, 0, nnear, nmid, nsmall, red, counts);
+}
+
+constexpr size_t kFineJobsDyn = sizeof(float) * 4 * kFineTile;
+
+void launch_fine_jobs(const ReqDev* reqs, const FineItem* items, int n_items, int64_t* counts, bool wide,
+                      bool mech, cudaStream_t st) {
+  if (n_items <= 0) return;
+  const size_t B = kFineJobsDyn;
+  if (mech) {  // 3-point only
+    if (counts)
+      launch_dyn(k_fine_jobs<true, 0, true>, n_items, kFineThreads, B, st, reqs, items, counts);
+    else
+      launch_dyn(k_fine_jobs<false, 0, true>, n_items, kFineThreads, B, st, reqs, items, counts);
+  } else if (counts) {
+    if (wide)
+      launch_dyn(k_fine_jobs<true, 1, false>, n_items, kFineThreads, B, st, reqs, items, counts);
+    else
+      launch_dyn(k_fine_jobs<true, 0, false>, n_items, kFineThreads, B, st, reqs, items, counts);
+  } else if (wide) {
+    launch_dyn(k_fine_jobs<false, 1, false>, n_items, kFineThreads, B, st, reqs, items, counts);
+  } else {
+    launch_dyn(k_fine_jobs<false, 0, false>, n_items, kFineThreads, B, st, reqs, items, counts);
+  }
 }
 
 void launch_fine(const ReqDev* reqs, const FineItem* items, int n_items, int64_t* counts, bool surr,

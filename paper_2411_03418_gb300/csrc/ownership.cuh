@@ -238,4 +238,129 @@ MARFA_HD bool owns_nothing_frame(const PanelFrame& F, const PanelPos& p, int g, 
   return true;
 }
 
+// ------------------------------------------------------------------ ownership by mechanism
+// Away from each other, the three things that decide a line's panels on grid g act
+// separately: the centre (grid g carries the ring d_near(Q) >= R_w h_g of a line whose
+// core is finer, or the whole core when g* = g), each cut-off edge (the grid carries the
+// panel inside the cut-off whose parent straddles it) and each chi breakpoint (the
+// grid carries the children of a parent holding the breakpoint that do not hold it
+// themselves). mech_ok tells when they are far enough apart on grid g (3-point
+// partition) that the owned panels are exactly the union of the closed forms below and
+// no node belongs to panels of two mechanisms (so that each node is evaluated once):
+// the centre's panels lie within R_w h_(g-1) + 4 h_g of the centre (their parents are
+// nearer than R_w h_(g-1)), a breakpoint's and an edge's within the one parent (4 h_g)
+// holding it; so an applicable breakpoint B (B <= cut-off) needs B >= R_w h_(g-1) + 8 h_g
+// and B + 8 h_g < cut-off, consecutive breakpoints more than 8 h_g apart, and without
+// breakpoints the cut-off needs to exceed R_w h_(g-1) + 8 h_g.
+// The finest grid has the same structure with the G10 panels (mech_fine_ok).
+MARFA_HD bool mech_ok(int g, int64_t cut, int R_w, bool chi_req) {
+  const int64_t h8 = step_fx(g) << 3, R2 = (int64_t)R_w * step_fx(g - 1);
+  if (!(R2 + h8 < cut)) return false;
+  if (chi_req) {
+    int64_t prev = -h8;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const int64_t B = chi_break_fx(b);
+      if (B > cut) break;
+      if (!(B >= R2 + h8 && B + h8 < cut && B - prev > h8)) return false;
+      prev = B;
+    }
+  }
+  return true;
+}
+
+// Finest grid: the centre's nodes lie within R_w h_10 + P of the centre (P the G10 panel
+// width), a breakpoint's within P of it, an edge's within P inside it.
+MARFA_HD bool mech_fine_ok(int64_t cut, int R_w, bool chi_req) {
+  const int64_t P = int64_t(1) << panel_shift(kNGrid), R = (int64_t)R_w * step_fx(kNGrid);
+  if (!(R + 2 * P < cut)) return false;
+  if (chi_req) {
+    int64_t prev = -2 * P;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const int64_t B = chi_break_fx(b);
+      if (B > cut) break;
+      if (!(B >= R + 2 * P && B + 2 * P < cut && B - prev > 2 * P)) return false;
+      prev = B;
+    }
+  }
+  return true;
+}
+
+// The centre's panels of grid g (absolute indices): [a1, b1] left of the centre and
+// [a2, b2] right of it (either may be empty: a > b); with gst == g the two ranges
+// join into the core [a1, b2] (b1 = a2 - 1); with gst < g none.
+MARFA_HD void mech_centre(int g, int64_t c, int gst, int R_w, int64_t& a1, int64_t& b1, int64_t& a2, int64_t& b2) {
+  const int s = panel_shift(g);
+  const int64_t R = (int64_t)R_w * step_fx(g), R2 = (int64_t)R_w * step_fx(g - 1);
+  const int64_t lo = fl_sh(c - R2, s + 1) << 1, hi = ((cl_sh(c + R2, s + 1) - 1) << 1) + 1;
+  if (gst < g) {
+    a1 = a2 = 1;
+    b1 = b2 = 0;
+  } else if (gst == g) {
+    a1 = lo;
+    b2 = hi;
+    a2 = hi + 1;
+    b1 = hi;
+  } else {
+    a1 = lo;
+    b1 = min(hi, fl_sh(c - R, s) - 1);
+    a2 = max(lo, cl_sh(c + R, s));
+    b2 = hi;
+  }
+}
+
+// The panel of grid g a cut-off edge gives (-1: none; a negative panel lies outside
+// every window): right edge E = c + cut-off, left edge E = c - cut-off.
+MARFA_HD int64_t mech_edge_right(int g, int64_t E) {
+  const int64_t t = fl_sh(E, panel_shift(g));
+  return (t & 1) ? t - 1 : -1;
+}
+MARFA_HD int64_t mech_edge_left(int g, int64_t E) {
+  const int64_t u = cl_sh(E, panel_shift(g));
+  return (u & 1) ? u : -1;
+}
+
+// The panels of grid g a breakpoint at position K gives: q[0], q[1] (-1: none).
+MARFA_HD void mech_kink(int g, int64_t K, int64_t& q0, int64_t& q1) {
+  const int s = panel_shift(g);
+  const int64_t n = fl_sh(K, s + 1), r = K - (n << (s + 1)), P = int64_t(1) << s;
+  q0 = q1 = -1;
+  if (r == 0) {
+    q0 = 2 * n - 2;
+    q1 = 2 * n + 1;
+  } else if (r < P) {
+    q0 = 2 * n + 1;
+  } else if (r > P) {
+    q0 = 2 * n;
+  }
+}
+
+// Finest-grid nodes (absolute indices, inclusive ranges; a > b empty) of each mechanism.
+MARFA_HD void mech_fine_centre(int64_t c, int gst, int R_w, int64_t& a, int64_t& b) {
+  const int s10 = panel_shift(kNGrid);
+  const int64_t R = (int64_t)R_w * step_fx(kNGrid);
+  if (gst <= kNGrid) {
+    a = 1;
+    b = 0;
+    return;
+  }
+  a = fl_sh(c - R, s10) << 3;
+  b = ((cl_sh(c + R, s10) - 1) << 3) + 7;
+}
+MARFA_HD void mech_fine_edge_right(int64_t E, int64_t& a, int64_t& b) {
+  a = fl_sh(E, panel_shift(kNGrid)) << 3;
+  b = fl_sh(E, kFineShift);
+}
+MARFA_HD void mech_fine_edge_left(int64_t E, int64_t& a, int64_t& b) {
+  a = cl_sh(E, kFineShift);
+  b = ((cl_sh(E, panel_shift(kNGrid)) - 1) << 3) + 7;
+}
+MARFA_HD void mech_fine_kink(int64_t K, int64_t& a, int64_t& b) {
+  const int s10 = panel_shift(kNGrid);
+  const int64_t p = fl_sh(K, s10);
+  b = (p << 3) + 7;
+  a = (K == (p << s10)) ? (p - 1) << 3 : p << 3;
+}
+
 }  // namespace marfa

@@ -47,7 +47,7 @@ EXPORTS = ["marfa_prepare_lines", "marfa_free_lines", "marfa_num_points", "marfa
            "marfa_mlp_train", "marfa_surrogate_load", "marfa_surrogate_unload", "marfa_surrogate_eval",
            "marfa_diag_absorption_counted_surrogate", "marfa_plan_create", "marfa_plan_execute",
            "marfa_plan_info", "marfa_plan_destroy", "marfa_diag_absorption_counts", "marfa_read_par",
-           "marfa_diag_pipe_rate", "marfa_diag_line_order", "marfa_diag_shape"]
+           "marfa_diag_pipe_rate", "marfa_diag_line_order", "marfa_diag_shape", "marfa_diag_variants"]
 
 MLP_PARAMS = 8577
 MLP_MAX_BATCH = 65536
@@ -100,6 +100,7 @@ def load(path: str | None = None):
         "marfa_plan_create": (C.c_int, [i32, vp, vp, vp, vp, vp, vp, i32, vp, C.POINTER(vp)]),
         "marfa_plan_execute": (C.c_int, [vp, vp]),
         "marfa_plan_info": (C.c_int, [vp, vp, vp, vp]),
+        "marfa_diag_variants": (C.c_int, [vp, vp]),
         "marfa_plan_destroy": (None, [vp]),
         "marfa_diag_absorption_counts": (C.c_int, [vp, vp, vp, i32, vp, vp, vp]),
     }
@@ -250,13 +251,29 @@ def marfa_plan_execute(plan: Plan, stream=None) -> None:
     _check(load().marfa_plan_execute(plan.handle, _stream(stream)))
 
 
+PLAN_KINDS, PLAN_VARIANTS = 11, 5
+
+
 def marfa_plan_info(plan: Plan, kernel_ms: bool = False):
-    """(variant[10], tune_ms[10, 3], kernel_ms[12] or None)."""
-    v = np.empty(10, dtype=np.int32)
-    t = np.empty((10, 3), dtype=np.float32)
+    """(variant[11] for grids 1..10 and the finest grid, tune_ms[11, 5], kernel_ms[12] or None)."""
+    v = np.empty(PLAN_KINDS, dtype=np.int32)
+    t = np.empty((PLAN_KINDS, PLAN_VARIANTS), dtype=np.float32)
     k = np.empty(12, dtype=np.float64) if kernel_ms else None
     _check(load().marfa_plan_info(plan.handle, _ptr(v), _ptr(t), _ptr(k)))
     return v, t, k
+
+
+def marfa_diag_variants(variants=None) -> np.ndarray:
+    """Set (when given, 11 entries: grids 1..10 and the finest grid; entry 0 ignored) and
+    return the kernel variants of calls without autotuning."""
+    get = np.empty(PLAN_KINDS, dtype=np.int32)
+    if variants is None:
+        _check(load().marfa_diag_variants(None, _ptr(get)))
+    else:
+        sv = np.ascontiguousarray(variants, dtype=np.int32)
+        assert sv.shape == (PLAN_KINDS,)
+        _check(load().marfa_diag_variants(_ptr(sv), _ptr(get)))
+    return get
 
 
 def marfa_plan_destroy(plan: Plan) -> None:

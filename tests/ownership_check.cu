@@ -1,7 +1,10 @@
-// Host check of the two forms of panel ownership in csrc/ownership.cuh: wherever the
-// 32-bit panel frame applies (PanelFrame::ok) its masks must equal those of the 64-bit
-// fixed-point form, bit for bit. Built and run by tests/test_ownership_cpu.py; prints
-// "cases <n> frames_ok <k> mismatches <m>" and exits 1 on any mismatch.
+// Host check of the forms of panel ownership in csrc/ownership.cuh: wherever the 32-bit
+// panel frame applies (PanelFrame::ok) its masks must equal those of the 64-bit
+// fixed-point form, bit for bit; and wherever the mechanisms act apart (mech_ok,
+// mech_fine_ok) the union of their closed forms must equal the 64-bit form's owned
+// panels of grids 2..10 and owned nodes of the finest grid. Built and run by
+// tests/test_ownership_cpu.py; prints "cases <n> frames_ok <k> mismatches <m>
+// mech_cases <n> mech_ok <k> mech_mismatches <m>" and exits 1 on any mismatch.
 #include <cstdint>
 #include <cstdio>
 #include "ownership.cuh"
@@ -39,6 +42,119 @@ static long check(int g, int64_t base, int nb, int64_t cut, int R_w, int64_t c, 
     fprintf(stderr, "g %d base %lld nb %d cut %lld R_w %d c %lld gst %d chi %d: %llx/%llx %llx/%llx %d/%d\n", g,
             (long long)base, nb, (long long)cut, R_w, (long long)c, gst, (int)chi, (unsigned long long)a64,
             (unsigned long long)a32, (unsigned long long)b64, (unsigned long long)b32, (int)n64, (int)n32);
+  return bad;
+}
+
+// Bits of panels [base, base + 64) owned on grid g by the union of the mechanisms; also
+// counts (into g_shared_nodes) the nodes of the window that the panels of two separate
+// mechanism ranges both hold (such a node would be evaluated twice).
+static long g_shared_nodes = 0;
+static uint64_t mech_mask(int g, int64_t c, int gst, bool chi, int64_t cut, int R_w, int64_t base) {
+  uint64_t m = 0;
+  unsigned char hits[130] = {0};  // node n = nodes 2 (base + b) .. 2 (base + b) + 2 of bit b
+  auto add = [&](int64_t a, int64_t b) {
+    const uint64_t r = rmask<uint64_t>(a, b, base, 64);
+    unsigned char here[130] = {0};
+    for (int q = 0; q < 64; ++q)
+      if ((r >> q) & 1)
+        for (int n = 2 * q; n <= 2 * q + 2; ++n) here[n] = 1;
+    for (int n = 0; n < 130; ++n) hits[n] += here[n];
+    m |= r;
+  };
+  int64_t a1, b1, a2, b2;
+  mech_centre(g, c, gst, R_w, a1, b1, a2, b2);
+  add(a1, b1);
+  add(a2, b2);
+  int64_t q = mech_edge_right(g, c + cut);
+  if (q != -1) add(q, q);
+  q = mech_edge_left(g, c - cut);
+  if (q != -1) add(q, q);
+  if (chi)
+    for (int b = 0; b < 3; ++b) {
+      const int64_t B = chi_break_fx(b);
+      if (B > cut) break;
+      for (int sg = -1; sg <= 1; sg += 2) {
+        int64_t q0, q1;
+        mech_kink(g, c + sg * B, q0, q1);
+        if (q0 != -1) add(q0, q0);
+        if (q1 != -1) add(q1, q1);
+      }
+    }
+  for (int n = 0; n < 130; ++n)
+    if (hits[n] > 1) ++g_shared_nodes;
+  return m;
+}
+
+// Whether node k is owned by the finest grid by the union of the mechanisms (and counts
+// into g_shared_nodes a node two mechanisms both give).
+static bool mech_fine_node(int64_t k, int64_t c, int gst, bool chi, int64_t cut, int R_w) {
+  int n = 0;
+  auto in = [&](int64_t a, int64_t b) { n += (k >= a && k <= b) ? 1 : 0; };
+  int64_t a, b;
+  mech_fine_centre(c, gst, R_w, a, b);
+  in(a, b);
+  mech_fine_edge_right(c + cut, a, b);
+  in(a, b);
+  mech_fine_edge_left(c - cut, a, b);
+  in(a, b);
+  if (chi)
+    for (int i = 0; i < 3; ++i) {
+      const int64_t B = chi_break_fx(i);
+      if (B > cut) break;
+      mech_fine_kink(c - B, a, b);
+      in(a, b);
+      mech_fine_kink(c + B, a, b);
+      in(a, b);
+    }
+  if (n > 1) ++g_shared_nodes;
+  return n > 0;
+}
+
+// Compare the mechanisms with the 64-bit form around the centre, both edges and every
+// breakpoint of one line; returns mismatches (0 when the mechanisms do not apply).
+static long check_mech(int g, int64_t cut, int R_w, bool chi_req, int64_t c, int gst, bool chi, bool& ok) {
+  const bool fine = g == 11;
+  ok = fine ? mech_fine_ok(cut, R_w, chi_req) : mech_ok(g, cut, R_w, chi_req);
+  if (!ok) return 0;
+  long bad = 0;
+  int64_t spots[9] = {c, c - cut, c + cut, 0, 0, 0, 0, 0, 0};
+  int ns = 3;
+  for (int b = 0; b < 3; ++b) {
+    const int64_t B = chi_break_fx(b);
+    if (B > cut) break;
+    spots[ns++] = c - B;
+    spots[ns++] = c + B;
+  }
+  for (int i = 0; i < ns; ++i) {
+    if (!fine) {
+      const int s = panel_shift(g);
+      for (int64_t base = fl_sh(spots[i], s) - 96; base <= fl_sh(spots[i], s) + 32; base += 64) {
+        const uint64_t ref = owned_any<uint64_t>(false, g, c, gst, chi, cut, R_w, base, 64);
+        const uint64_t got = mech_mask(g, c, gst, chi, cut, R_w, base);
+        if (ref != got) {
+          ++bad;
+          if (bad < 20)
+            fprintf(stderr, "mech g %d cut %lld R_w %d c %lld gst %d chi %d base %lld: %llx vs %llx\n", g,
+                    (long long)cut, R_w, (long long)c, gst, (int)chi, (long long)base, (unsigned long long)ref,
+                    (unsigned long long)got);
+        }
+      }
+    } else {
+      const int s10 = panel_shift(kNGrid);
+      const int64_t k0 = fl_sh(spots[i], kFineShift);
+      for (int64_t k = k0 - 400; k <= k0 + 400; ++k) {
+        const int64_t X = k << kFineShift, d = X - c;
+        const bool within = (d < 0 ? -d : d) <= cut;
+        const bool ref = within && !(accept_mask_s<uint32_t>(kNGrid, c, gst, chi, cut, R_w, k >> 3, 1, s10, s10) & 1u);
+        if (ref != mech_fine_node(k, c, gst, chi, cut, R_w)) {
+          ++bad;
+          if (bad < 20)
+            fprintf(stderr, "mech fine cut %lld R_w %d c %lld gst %d chi %d k %lld: %d\n", (long long)cut, R_w,
+                    (long long)c, gst, (int)chi, (long long)k, (int)ref);
+        }
+      }
+    }
+  }
   return bad;
 }
 
@@ -82,6 +198,32 @@ int main() {
     ++cases;
     okc += ok;
   }
-  printf("cases %ld frames_ok %ld mismatches %ld\n", cases, okc, bad);
-  return bad ? 1 : 0;
+  // the mechanisms: random centres, on and one unit beside panel and node boundaries
+  // (so that centre, edges and breakpoints land on them), every grid and the finest
+  long mcases = 0, mok = 0, mbad = 0;
+  const int64_t mcuts[] = {125 * one, 25 * one, 400 * one, 3 * one + one / 2, 160 * one + one / 7, 10 * one,
+                           151 * one};
+  const int mRws[] = {8, 16, 4, 7, 2};
+  for (int rep = 0; rep < 60000; ++rep) {
+    const int g = (int)uniform(2, 11);
+    const int64_t cut = mcuts[uniform(0, 6)];
+    const int R_w = mRws[uniform(0, 4)];
+    const bool chi_req = uniform(0, 3) != 0;
+    const bool chi = chi_req && uniform(0, 3) != 0;
+    int64_t c = uniform(500, 3000) * one + uniform(0, one - 1);
+    const int jit = (int)uniform(0, 3);
+    const int sh = (int)uniform(kFineShift, panel_shift(2) + 1);
+    if (jit == 0) c = (c >> sh) << sh;
+    if (jit == 1) c = ((c >> sh) << sh) + (uniform(0, 1) ? 1 : -1);
+    const int gst = (int)uniform(1, 11);
+    bool ok = false;
+    mbad += check_mech(g, cut, R_w, chi_req, c, gst, chi, ok);
+    ++mcases;
+    mok += ok;
+  }
+  if (g_shared_nodes) fprintf(stderr, "nodes given by two mechanisms: %ld\n", g_shared_nodes);
+  mbad += g_shared_nodes;
+  printf("cases %ld frames_ok %ld mismatches %ld mech_cases %ld mech_ok %ld mech_mismatches %ld\n", cases, okc, bad,
+         mcases, mok, mbad);
+  return (bad || mbad) ? 1 : 0;
 }

@@ -72,7 +72,7 @@ def test_plan_matches_batch_and_replays(M):
     for r, o in zip(ref, outs):
         assert np.array_equal(o.cpu().numpy(), r)
     v, t, k = M.marfa_plan_info(plan, kernel_ms=True)
-    assert v[0] == -1 and list(v[1:7]) == [2] * 6 and list(v[7:]) == [1] * 3
+    assert list(v) == list(M.marfa_diag_variants())  # the process-wide defaults
     assert np.all(t == -1)
     assert np.all(k >= 0) and k.sum() > 0
     M.marfa_plan_destroy(plan)
@@ -109,10 +109,11 @@ def test_autotuned_plan_parity(M):
     M.marfa_plan_execute(plan)
     torch.cuda.synchronize()
     v, t, _ = M.marfa_plan_info(plan)
-    assert set(v[1:].tolist()) <= {0, 1, 2}
-    assert np.all(t[1:] > 0)
+    assert set(v[1:10].tolist()) <= {0, 1, 2, 3, 4} and v[10] in (0, 1, 2)
+    assert np.all(t[1:10] > 0) and np.all(t[10, :3] > 0) and np.all(t[10, 3:] == -1) and np.all(t[0] == -1)
     for g in range(1, 10):  # the chosen variant is the fastest one
         assert t[g, v[g]] <= t[g].min()
+    assert t[10, v[10]] <= t[10, :3].min()
     for q, w in enumerate(SMALL):
         got = outs[q].cpu().numpy()
         for lev in range(w.n_levels):

@@ -203,6 +203,10 @@ def test_surrogate_absorption_vs_oracle(M, loaded, case):
 
 
 def test_surrogate_batch_matches_single(M, loaded):
+    """A batch holding a surrogate request runs every request through the
+    surrogate-capable kernels: the surrogate request's result is the same bit for bit as
+    alone; the plain request takes, alone, the plain kernels, whose sums run in another
+    order (within FP32 rounding of the batch result)."""
     a = SURR_CASES[0].with_(surrogate=1)
     b = SURR_CASES[1]
     ka, kb = _run(M, a), _run(M, b)
@@ -212,7 +216,9 @@ def test_surrogate_batch_matches_single(M, loaded):
     ob = np.empty_like(kb)
     M.marfa_absorption_batch([la, lb], [M.levels_of(a), M.levels_of(b)], [a.vmr, b.vmr],
                              [M.request_of(a), M.request_of(b)], [oa, ob])
-    assert np.array_equal(oa, ka) and np.array_equal(ob, kb)
+    assert np.array_equal(oa, ka)
+    for lev in range(b.n_levels):
+        _assert_close(ob[lev], kb[lev], 1e-5, f"plain request in a surrogate batch, level {lev}")
 
 
 def test_surrogate_plan_matches_call(M, loaded):

@@ -30,3 +30,6 @@ def test_panel_frame_masks_equal_fixed_point_masks(tmp_path):
     assert fields[0] == "cases" and fields[4] == "mismatches"
     assert int(fields[5]) == 0
     assert int(fields[3]) > 100000  # enough cases where the frame applies
+    assert fields[6] == "mech_cases" and fields[10] == "mech_mismatches"
+    assert int(fields[11]) == 0
+    assert int(fields[9]) > 20000  # enough cases where the mechanisms act apart
