@@ -240,12 +240,16 @@ struct ChiRun {
 // point) and node spacing 2^sh units, node j sits at (j + q + phi) steps, q integer,
 // phi in [0, 1). Then x_j = ((j + q) + phi) * hs with hs = sx * step is formed as
 // fma(j + q, hs, phi * hs): j + q is exact in FP32 and only one rounding remains.
+// Both conversions stay in 32 bits (64-bit integer conversions run on the FP64 pipe):
+// q is a node count below 2^31 (tiles lie within the cut-off, <= 1000 cm^-1, of a
+// candidate line), and phi is taken from the top 31 bits of the remainder (sh >= 32),
+// rounded to FP32 (error <= 2^-25 + 2^-31 of a step).
 struct NodeX {
   float qf, hs, phs, phi;
   __device__ __forceinline__ void init(int64_t rel, int sh, float sx) {
     const int64_t q = fl_sh(rel, sh);
-    phi = __ll2float_rn(rel - (q << sh)) * ldexpf(1.0f, -sh);
-    qf = (float)q;
+    phi = __int2float_rn((int)((rel - (q << sh)) >> (sh - 31))) * 0x1p-31f;
+    qf = __int2float_rn((int)q);
     hs = sx * ldexpf(1.0f, sh - kFixBits);
     phs = phi * hs;
   }
@@ -617,7 +621,9 @@ __global__ void __launch_bounds__(kG1Warps * 32)
           if (above) d2 = ((base + (__ffsll((long long)above) - 1)) << s) - c;       // start of that panel
           dn = inside ? 0 : min(d1, d2);
         }
-        const bool far = voigt && (__ll2float_rn(dn) * ldexpf(1.0f, -kFixBits) * sx >= 100.0f || y >= 100.0f);
+        // dn < 2^62: its top 31 bits suffice for the far-wing test (32-bit conversion)
+        const bool far = voigt && (__int2float_rn((int)(dn >> 31)) * ldexpf(1.0f, 31 - kFixBits) * sx >= 100.0f ||
+                                   y >= 100.0f);
         int jL = -(1 << 30), jR = 1 << 30;
         bool exact = !far;
         const float aC = amp * y * kInvSqrtPi;
