@@ -15,7 +15,8 @@ configurations the same way (batch: 256 uneven requests in one plan; earth: 1.2M
 x 50 levels; tiny: 2,000 lines x 1 level).
 
 Prints one JSON line. ``value`` is fine-grid points x levels per second over all
-ranks; ``line_evals_per_s`` counts the (line, node) profile evaluations the scheme
+ranks (with N > 1 ranks the levels, or a batch's requests, are split over them:
+strong scaling, no data-path collective); ``line_evals_per_s`` counts the (line, node) profile evaluations the scheme
 defines. ``e2e`` is the same metric through the public call with host buffers
 (line records and levels from pinned host memory in, k(nu) back to pinned host
 memory, every step). ``--impl reference`` times the FP64 CPU oracle on a bounded
@@ -259,10 +260,25 @@ def max_over_ranks(t, dist, dev):
     return float(tt.item())
 
 
+def marfa_points(w):
+    """Finest-grid nodes of a workload's window (k 2^-11 in [nu_lo, nu_hi])."""
+    return int(math.floor(w.nu_hi * 2048.0) - math.ceil(w.nu_lo * 2048.0) + 1)
+
+
+def sum_over_ranks(x, dist, dev):
+    """The sum of the ranks' values of x (an integer), or x itself on one rank."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([int(x)], dtype=torch.int64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return int(t.item())
+
+
 def job_throughput(units_per_rank, world, steps, t_max):
-    """Whole-job rate: every rank processes the same workload (weak scaling, one
-    replica per GPU), so the job's units per second are world x units x steps over the
-    slowest rank's time."""
+    """Whole-job rate over the slowest rank's time: world x units x steps / t_max, where
+    each of `world` ranks processes `units_per_rank` per step (a replica per rank, weak
+    scaling; for a job split over the ranks pass the job's units and world = 1)."""
     return units_per_rank * world * steps / t_max
 
 
@@ -292,6 +308,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer steps")
     ap.add_argument("--no-count", action="store_true", help="skip the evaluation-counting call")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-Voigt leg")
+    ap.add_argument("--shard", choices=["auto", "levels", "requests", "none"], default="auto",
+                    help="with N > 1 ranks: split the levels (one request) or the requests (a batch) "
+                         "over the ranks (strong scaling; auto), or run a replica per rank (none)")
     ap.add_argument("--stencil", type=int, choices=[3, 5], default=3,
                     help="interpolation points per coarse panel: 3 (the paper's) or 5 (quartic)")
     args = ap.parse_args()
@@ -314,6 +333,25 @@ def main():
     if args.impl == "reference":
         run_reference(args, wl, rank, world)
         return
+
+    # the whole job's work, then this rank's share of it (levels are independent, and so
+    # are the requests of a batch: no exchange step between the ranks)
+    units_job = sum(w.n_levels * marfa_points(w) for w in wls)
+    shard = args.shard
+    if shard == "auto":
+        shard = "none" if world == 1 else ("levels" if len(wls) == 1 else "requests")
+    if world > 1 and shard != "none":
+        from paper_2411_03418_gb300.shard import level_shards, request_shards
+        if shard == "levels":
+            if any(w.n_levels < world for w in wls):
+                raise SystemExit("fewer levels than ranks: use --shard requests or none")
+            wls = [w.level_subset(level_shards(w.n_levels, world)[rank]) for w in wls]
+        else:
+            if len(wls) < world:
+                raise SystemExit("fewer requests than ranks: use --shard levels or none")
+            wls = [wls[i] for i in request_shards(len(wls), world)[rank]]
+    else:
+        units_job *= world  # a replica of the workload per rank
 
     import torch
     dist = None
@@ -403,9 +441,9 @@ def main():
     serial_ms = float(sum(a.elapsed_time(b) for a, b in ev_s)) / args.steps
     M.marfa_plan_destroy(plan_s)
     units_rank = sum(w.n_levels * n for w, n in zip(wls, npts))
-    units = units_rank * world
-    value = job_throughput(units_rank, world, args.steps, t_total)
-    evals_s = job_throughput(evals_per_step, world, args.steps, t_total)
+    evals_job = int(sum_over_ranks(evals_per_step, dist, dev))
+    value = job_throughput(units_job, 1, args.steps, t_total)
+    evals_s = job_throughput(evals_job, 1, args.steps, t_total)
 
     # end to end through the public call with host buffers (pinned): line records in,
     # prepare, absorption (batch call for several requests), k(nu) back, every step
@@ -432,7 +470,7 @@ def main():
             e2e_step()
         torch.cuda.synchronize()
         t_e2e = max_over_ranks(time.perf_counter() - t0, dist, dev)
-    e2e_value = job_throughput(units_rank, world, args.steps, t_e2e)
+    e2e_value = job_throughput(units_job, 1, args.steps, t_e2e)
 
     # roofline of the dominant kernel (FP32 pipe, algorithmic flops per evaluation)
     names = ["level_prep"] + [f"grid{g}" for g in range(1, 11)] + ["finest"]
@@ -457,14 +495,15 @@ def main():
 
     if rank == 0:
         cfg = {"workload": wname, "requests": len(wls), "lines": int(sum(len(w.lines) for w in wls)),
-               "levels": int(sum(w.n_levels for w in wls)), "points_x_levels_per_step": int(units // world),
+               "levels": int(sum(w.n_levels for w in wls)), "points_x_levels_per_step": int(units_job),
                "l2": "flushed between steps (256 MB write)", "stencil": args.stencil}
         if len(wls) == 1:
             cfg["npts_per_level"] = npts[0]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak" if (world == 1 or shard == "none") else "strong", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
             "config": cfg,
             "line_evals_per_s": evals_s, "line_evals_per_step": evals_per_step,
             "line_evals_per_grid": [int(v) for v in counts_grid],
