@@ -431,6 +431,35 @@ int marfa_diag_pipe_rate(int32_t pipe, double* ops_per_s);
  * may be NULL). */
 int marfa_diag_kernel_timing(int32_t enable, double* ms, int64_t* launches);
 
+/* Error-path testing (no counterpart in the paper): make the nth allocation from now on
+ * fail as if memory were exhausted (nth >= 1; 0 disarms). Counted allocations: the
+ * stream-ordered device buffers of calls and plans, the line list's device block, host
+ * staging buffer and object, plan objects and the surrogate's device buffers. The entry
+ * point that meets the failure returns MARFA_E_NOMEM after freeing what it had
+ * allocated; the injector then disarms itself. The environment variable
+ * MARFA_FAIL_ALLOC=n arms it when the library loads. left (may be NULL) receives the
+ * allocations the previous arming still had to let through plus one (0: not armed).
+ * Errors: MARFA_E_INVAL for nth < 0. */
+int marfa_diag_fail_alloc(int64_t nth, int64_t* left);
+
+/* Device memory in use, for leak checks: after synchronising the current device,
+ * pool_used receives the bytes allocated from its default memory pool (the library's
+ * stream-ordered buffers) and device_free the free device memory (cudaMemGetInfo); each
+ * may be NULL. Errors: MARFA_E_CUDA. */
+int marfa_diag_device_memory(int64_t* pool_used, int64_t* device_free);
+
+/* Device-side checks (no counterpart in the paper). A library built with MARFA_DEBUG
+ * guards its kernels' indexed shared and global accesses with range checks that, when
+ * one fails, skip the access and record a code in a device status word instead of
+ * trapping; every call (and plan execution) then waits for the device and returns
+ * MARFA_E_INTERNAL naming the first failed check (the word is cleared). An ordinary
+ * build has no checks. This entry point runs a probe kernel that makes a store at
+ * index of a 32-entry array only when the index is in range: in a MARFA_DEBUG build an
+ * index outside 0..31 records check 901 and the call returns MARFA_E_INTERNAL; an
+ * ordinary build returns MARFA_OK. debug_build (may be NULL) receives 1 for a
+ * MARFA_DEBUG build. */
+int marfa_diag_check(int32_t index, int32_t* debug_build);
+
 #ifdef __cplusplus
 }
 #endif

@@ -55,6 +55,16 @@ static int fail(int code, const char* fmt, ...) {
 
 extern "C" const char* marfa_last_error(void) { return g_err.c_str(); }
 
+// MARFA_DEBUG builds: after a call's kernels, the device-side checks' status word (the
+// call waits for the device); a failed check is reported as MARFA_E_INTERNAL and cleared.
+static int debug_checks() {
+  if (!kDebugBuild) return 0;
+  unsigned code = 0;
+  if (marfa::device_check_status(&code, true)) return fail(MARFA_E_CUDA, "device synchronisation failed");
+  if (code) return fail(MARFA_E_INTERNAL, "device-side check %u failed", code);
+  return 0;
+}
+
 // ------------------------------------------------------------------ physical constants
 static const double kTref = 296.0;
 static const double kC2 = 1.438776877;     // cm K
@@ -63,6 +73,36 @@ static const double kNA = 6.02214076e23;   // 1/mol
 static const double kC = 2.99792458e8;     // m/s
 static const double kAtm = 101325.0;       // Pa
 static const double kSigmaScale = 18446744073709551616.0;  // 2^64: keeps sigma sums normal
+
+// ------------------------------------------------------------------ allocation-failure injection
+// For tests of the error paths: armed with n >= 1, the n-th allocation from then on
+// fails as if the memory were exhausted (device allocations of dev_alloc, the line
+// list's device block, host staging buffer and object, plan objects, the surrogate's
+// buffers), and the injector disarms itself. MARFA_FAIL_ALLOC=n in the environment arms
+// it when the library loads; marfa_diag_fail_alloc re-arms it.
+static std::atomic<int64_t> g_fail_left{-1};  // allocations to let through before the failure; < 0: off
+static int64_t fail_alloc_env() {
+  const char* v = std::getenv("MARFA_FAIL_ALLOC");
+  const long long n = v ? std::atoll(v) : 0;
+  return n >= 1 ? n - 1 : -1;
+}
+static const bool g_fail_env_read = (g_fail_left.store(fail_alloc_env()), true);
+
+// True when this allocation is the one to fail.
+static bool alloc_fails() {
+  int64_t v = g_fail_left.load();
+  while (v >= 0)
+    if (g_fail_left.compare_exchange_weak(v, v - 1)) return v == 0;
+  return false;
+}
+
+extern "C" int marfa_diag_fail_alloc(int64_t nth, int64_t* left) {
+  (void)g_fail_env_read;
+  if (left) *left = g_fail_left.load() >= 0 ? g_fail_left.load() + 1 : 0;
+  if (nth < 0) return fail(MARFA_E_INVAL, "nth must be >= 0 (0: off)");
+  g_fail_left.store(nth >= 1 ? nth - 1 : -1);
+  return MARFA_OK;
+}
 
 // ------------------------------------------------------------------ device memory
 // Stream-ordered allocations from the device's default pool, kept cached between calls.
@@ -84,7 +124,27 @@ static int dev_alloc(void** p, size_t bytes, cudaStream_t st) {
   }
   *p = nullptr;
   if (bytes == 0) bytes = 16;
+  if (alloc_fails()) return fail(MARFA_E_NOMEM, "device allocation of %zu bytes failed (injected)", bytes);
   CK(cudaMallocAsync(p, bytes, st));
+  return MARFA_OK;
+}
+
+extern "C" int marfa_diag_device_memory(int64_t* pool_used, int64_t* device_free) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceSynchronize());
+  if (pool_used) {
+    cudaMemPool_t pool;
+    uint64_t used = 0;
+    CK(cudaDeviceGetDefaultMemPool(&pool, dev));
+    CK(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
+    *pool_used = (int64_t)used;
+  }
+  if (device_free) {
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    *device_free = (int64_t)fr;
+  }
   return MARFA_OK;
 }
 
@@ -548,7 +608,7 @@ extern "C" int marfa_prepare_lines(const marfa_line_t* lines, int64_t n, const m
   }
   auto src = [&](int64_t j) { return sorted ? j : order[j]; };
 
-  marfa_lines_t* L = new (std::nothrow) marfa_lines_t();
+  marfa_lines_t* L = alloc_fails() ? nullptr : new (std::nothrow) marfa_lines_t();
   if (!L) return fail(MARFA_E_NOMEM, "host allocation failed");
   cudaGetDevice(&L->device);
   L->n = n;
@@ -575,6 +635,7 @@ extern "C" int marfa_prepare_lines(const marfa_line_t* lines, int64_t n, const m
   try {
     L->species.assign(sp, sp + n_sp);
     L->perm.resize(n);
+    if (alloc_fails()) throw std::bad_alloc();
     hb.reset(new unsigned char[total]);
   } catch (...) {
     delete L;
@@ -626,7 +687,7 @@ extern "C" int marfa_prepare_lines(const marfa_line_t* lines, int64_t n, const m
       bfirst[b] = (int32_t)i;
     }
   });
-  cudaError_t e = cudaMalloc(&L->block, total);
+  cudaError_t e = alloc_fails() ? cudaErrorMemoryAllocation : cudaMalloc(&L->block, total);
   if (e != cudaSuccess) {
     L->block = nullptr;
     delete L;
@@ -1250,7 +1311,8 @@ static int absorption_impl(int32_t n_req, const marfa_lines_t* const* lines,
     for (auto& P : plans) release(P, st);
     return r;
   }
-  return finish_outputs(plans, st);
+  r = finish_outputs(plans, st);
+  return r ? r : debug_checks();
 }
 
 extern "C" int marfa_absorption(const marfa_lines_t* lines, const marfa_level_t* levels,
@@ -1417,7 +1479,7 @@ extern "C" int marfa_plan_create(int32_t n_req, const marfa_lines_t* const* line
     if (!k_out[q] || !is_device_ptr(k_out[q]))
       return fail(MARFA_E_INVAL, "k_out[%d] must be device memory for a captured plan", q);
   cudaStream_t st = (cudaStream_t)stream;
-  marfa_plan_t* X = new (std::nothrow) marfa_plan_t();
+  marfa_plan_t* X = alloc_fails() ? nullptr : new (std::nothrow) marfa_plan_t();
   if (!X) return fail(MARFA_E_NOMEM, "host allocation failed");
   cudaGetDevice(&X->device);
   X->serial = flags & MARFA_PLAN_SERIAL;
@@ -1477,6 +1539,7 @@ extern "C" int marfa_plan_create(int32_t n_req, const marfa_lines_t* const* line
   // one ordinary run first: checks every launch outside capture and leaves the output valid
   if (!r) r = plan_launch_all(X, st, false);
   if (!r && (e = cudaStreamSynchronize(st))) r = fail(MARFA_E_CUDA, "plan run: %s", cudaGetErrorString(e));
+  if (!r) r = debug_checks();
   cudaStream_t cs = nullptr;
   if (!r && (e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)))
     r = fail(MARFA_E_CUDA, "capture stream: %s", cudaGetErrorString(e));
@@ -1507,7 +1570,7 @@ extern "C" int marfa_plan_execute(marfa_plan_t* X, void* stream) {
   CK(cudaGetDevice(&dev));
   if (dev != X->device) return fail(MARFA_E_INVAL, "plan belongs to device %d, current is %d", X->device, dev);
   CK(cudaGraphLaunch(X->exec, (cudaStream_t)stream));
-  return MARFA_OK;
+  return debug_checks();
 }
 
 extern "C" int marfa_plan_info(const marfa_plan_t* X, int32_t* variant, float* tune_ms, double* kernel_ms) {
@@ -1760,7 +1823,15 @@ extern "C" int marfa_absorption_noalloc(const marfa_lines_t* lines, const marfa_
   else
     launch_fine(drd, dfi, (int)P.fine.size(), nullptr, surr, wide, st);
   CK(cudaGetLastError());
-  return MARFA_OK;
+  return debug_checks();
+}
+
+extern "C" int marfa_diag_check(int32_t index, int32_t* debug_build) {
+  if (debug_build) *debug_build = kDebugBuild ? 1 : 0;
+  launch_diag_check(index, 0);
+  CK(cudaGetLastError());
+  CK(cudaDeviceSynchronize());
+  return debug_checks();
 }
 
 // ------------------------------------------------------------------ diagnostics
@@ -2072,8 +2143,8 @@ extern "C" int marfa_surrogate_load(const float* params, float budget, int32_t s
   float *dp = nullptr, *derr = nullptr;
   const int cells = kGuardNx * kGuardNy;
   cudaError_t e;
-  if ((e = cudaMalloc(&w, sizeof(MlpWeights))) || (e = cudaMalloc(&dp, 4 * kMlpParams)) ||
-      (e = cudaMalloc(&derr, 4 * cells))) {
+  if ((e = alloc_fails() ? cudaErrorMemoryAllocation : cudaMalloc(&w, sizeof(MlpWeights))) ||
+      (e = cudaMalloc(&dp, 4 * kMlpParams)) || (e = cudaMalloc(&derr, 4 * cells))) {
     cudaFree(w);
     cudaFree(dp);
     cudaFree(derr);

@@ -156,6 +156,30 @@ struct PrepArgs {
   uint8_t* flags;
 };
 
+// ------------------------------------------------------------------ device-side checks
+// In a MARFA_DEBUG build, MARFA_DCHECK(cond, code) is cond, and when cond is false it also
+// records code in the library's device status word (the first failure wins); callers
+// skip the guarded access when it is false, so a failed check never faults. In an
+// ordinary build it is `true` and costs nothing. Codes: 1xx grids 2..10, 2xx the finest
+// grid, 3xx grid 1, 4xx candidate bands, 9xx the diagnostic probe.
+#ifdef MARFA_DEBUG
+__device__ bool marfa_dcheck_fail(unsigned code);
+#define MARFA_DCHECK(cond, code) ((cond) || marfa_dcheck_fail(code))
+#else
+#define MARFA_DCHECK(cond, code) true
+#endif
+// The status word (0: no check failed), optionally cleared; MARFA_OK in ordinary builds
+// (always 0). Synchronises the current device.
+int device_check_status(unsigned* code, bool clear);
+constexpr bool kDebugBuild =
+#ifdef MARFA_DEBUG
+    true;
+#else
+    false;
+#endif
+// launches the diagnostic probe: a guarded store at index i of a 32-entry array
+void launch_diag_check(int i, cudaStream_t st);
+
 // kernels (marfa_kernels.cu). With surr set, the surrogate-capable variants run (requests
 // with mlp != null use the surrogate under its guard). counts, when given, selects the
 // counting variants and receives kCountFields entries per item: all profile evaluations,

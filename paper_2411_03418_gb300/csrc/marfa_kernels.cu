@@ -25,6 +25,44 @@
 
 namespace marfa {
 
+// ------------------------------------------------------------------ device-side checks
+#ifdef MARFA_DEBUG
+static __device__ unsigned g_marfa_status = 0;
+__device__ bool marfa_dcheck_fail(unsigned code) {
+  atomicCAS(&g_marfa_status, 0u, code);
+  return false;
+}
+#endif
+
+int device_check_status(unsigned* code, bool clear) {
+  *code = 0;
+  if (cudaDeviceSynchronize() != cudaSuccess) return -3;  // MARFA_E_CUDA
+#ifdef MARFA_DEBUG
+  if (cudaMemcpyFromSymbol(code, g_marfa_status, sizeof(unsigned)) != cudaSuccess) return -3;
+  if (clear && *code) {
+    const unsigned zero = 0;
+    if (cudaMemcpyToSymbol(g_marfa_status, &zero, sizeof(unsigned)) != cudaSuccess) return -3;
+  }
+#else
+  (void)clear;
+#endif
+  return 0;
+}
+
+// The probe of the checks: a store at index i of a 32-entry shared array, made only when
+// i is in range (in a MARFA_DEBUG build an index out of range records code 901).
+__global__ void k_diag_check(int i, int* sink) {
+  __shared__ int a[32];
+  a[threadIdx.x] = 0;
+  __syncwarp();
+  if (i >= 0 && i < 32 && MARFA_DCHECK(true, 901)) a[i] = 1;
+  else MARFA_DCHECK(false, 901);
+  __syncwarp();
+  if (a[threadIdx.x] && sink) *sink = 1;
+}
+
+void launch_diag_check(int i, cudaStream_t st) { k_diag_check<<<1, 32, 0, st>>>(i, nullptr); }
+
 // ------------------------------------------------------------------ helpers
 
 __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
@@ -96,6 +134,10 @@ struct Bands {
       }
     }
     merge();
+#ifdef MARFA_DEBUG
+    for (int r = 0; r < n; ++r)
+      if (!MARFA_DCHECK(lo[r] >= 0 && lo[r] <= hi[r] && hi[r] <= R.n_lines, 401)) n = 0;
+#endif
   }
   // All candidates of the bands as one sequence 0 .. total-1, so that a loop over them
   // by a block or a warp leaves idle lanes only in its last round.
@@ -783,7 +825,7 @@ __global__ void __launch_bounds__(kG1Warps * 32)
     const int64_t np = R.npan[1];
     float* gp = R.slots + (int64_t)lev * R.slots_per_level + R.slot_off[1] + 3 * np * it.part;
     const int64_t m = m0 + lane;  // this lane's pair
-    if (m <= m_last) {
+    if (m <= m_last && MARFA_DCHECK(m >= m_first, 301)) {
       gp[m - m_first] = ls + lc;
       gp[np + (m - m_first)] = a[6] + a[7];
     }
@@ -991,6 +1033,7 @@ __global__ void __launch_bounds__(kLWarps * 32, SURR ? 3 : (PAIRS == 16 ? 7 : 4)
           const float xv = nx.x(jf);
           float v = amp * (voigt ? voigt_K<false, true>(xv, y, kVoigtCells) : shape_f(R.shape, xv, y));
           if (use_chi) v *= run ? cr.v : ct.value(2 * p, nx.absd(jf, s - 1));
+          if (!MARFA_DCHECK(p >= 0 && p < PAIRS, 106)) continue;
           if (bL) accL[warp][p][lane] += v;
           if (bR) accR[warp][p][lane] += v;
           count_eval<COUNT>(voigt, xv, y, nev, nnear, nmid, nsmall);
@@ -1012,6 +1055,7 @@ __global__ void __launch_bounds__(kLWarps * 32, SURR ? 3 : (PAIRS == 16 ? 7 : 4)
           const float xv = nx.x(jf);
           float v = amp * (voigt ? voigt_K<false, true>(xv, y, kVoigtCells) : shape_f(R.shape, xv, y));
           if (use_chi) v *= run ? cv : ct.value(2 * p, nx.absd(jf, s - 1));
+          if (!MARFA_DCHECK(p >= 0 && p < PAIRS, 106)) continue;
           if (bL) accL[warp][p][lane] += v;
           if (bR) accR[warp][p][lane] += v;
           count_eval<COUNT>(voigt, xv, y, nev, nnear, nmid, nsmall);
@@ -1047,7 +1091,7 @@ __global__ void __launch_bounds__(kLWarps * 32, SURR ? 3 : (PAIRS == 16 ? 7 : 4)
     float* gp = R.slots + (int64_t)lev * R.slots_per_level + R.slot_off[g];
     const int64_t np = R.npan[g];
     const int64_t m = m0 + p;
-    if (kind == 0 && m <= m_last) gp[m - m_first] = v;
+    if (kind == 0 && m <= m_last && MARFA_DCHECK(m >= m_first, 105)) gp[m - m_first] = v;
     if (kind == 1 && m <= m_last) gp[np + (m - m_first)] = v;
     if (kind == 2 && m - 1 >= m_first && m - 1 <= m_last) gp[2 * np + (m - 1 - m_first)] = v;
   }
@@ -1241,7 +1285,7 @@ __global__ void __launch_bounds__(kCWarps * 32, SURR ? 3 : 6)
                 v = amp * voigt_K(xv, y);
                 if (use_chi) v *= ce;
               }
-              bE[lane][q] = v;
+              if (MARFA_DCHECK(q >= 0 && q < kCPairs, 101)) bE[lane][q] = v;
             }
             if (ao) {
               float w = 0.0f;
@@ -1249,7 +1293,7 @@ __global__ void __launch_bounds__(kCWarps * 32, SURR ? 3 : 6)
                 w = amp * voigt_K(xw, y);
                 if (use_chi) w *= co;
               }
-              bO[lane][q] = w;
+              if (MARFA_DCHECK(q >= 0 && q < kCPairs, 101)) bO[lane][q] = w;
             }
             if (ae) count_eval<COUNT>(true, xv, y, nev, nnear, nmid, nsmall);
             if (ao) count_eval<COUNT>(true, xw, y, nev, nnear, nmid, nsmall);
@@ -1279,13 +1323,13 @@ __global__ void __launch_bounds__(kCWarps * 32, SURR ? 3 : 6)
             const float xv = nx.x(jf);
             float v = amp * (voigt ? voigt_K<false, false, true>(xv, y, kVoigtCells) : shape_f(R.shape, xv, y));
             if (use_chi) v *= run ? cv : ct.value(2 * q, nx.absd(jf, s - 1));
-            bE[lane][q] = v;
+            if (MARFA_DCHECK(q >= 0 && q < kCPairs, 101)) bE[lane][q] = v;
             count_eval<COUNT>(voigt, xv, y, nev, nnear, nmid, nsmall);
             if (bL) {
               const float xw = nx.x(jf + 1.0f);
               float w = amp * (voigt ? voigt_K<false, false, true>(xw, y, kVoigtCells) : shape_f(R.shape, xw, y));
               if (use_chi) w *= run ? cv * cr.ratio : ct.value(2 * q + 1, nx.absd(jf + 1.0f, s - 1));
-              bO[lane][q] = w;
+              if (MARFA_DCHECK(q >= 0 && q < kCPairs, 101)) bO[lane][q] = w;
               count_eval<COUNT>(voigt, xw, y, nev, nnear, nmid, nsmall);
             }
           }
@@ -1313,7 +1357,7 @@ __global__ void __launch_bounds__(kCWarps * 32, SURR ? 3 : 6)
     float* gp = R.slots + (int64_t)lev * R.slots_per_level + R.slot_off[g];
     const int64_t np = R.npan[g];
     const int64_t m = m0 + p;
-    if (m <= m_last) {
+    if (m <= m_last && MARFA_DCHECK(m >= m_first, 104)) {
       gp[m - m_first] = sL + cL;
       gp[np + (m - m_first)] = sM + cM;
     }
@@ -1473,6 +1517,7 @@ __global__ void __launch_bounds__(kCWarps * 32, 6)
                 else if (pass > 0 && eb > 0)
                   v *= eC * __expf(-er * nx.absd(jf, s - 1));
               }
+              if (!MARFA_DCHECK(j >= 0 && j < 2 * kCPairs, 102)) continue;
               if (j & 1) bO[lane][j >> 1] = v;
               else bE[lane][j >> 1] = v;
               count_eval<COUNT>(voigt, xv, y, nev, nnear, nmid, nsmall);
@@ -1499,7 +1544,7 @@ __global__ void __launch_bounds__(kCWarps * 32, 6)
     float* gp = R.slots + (int64_t)lev * R.slots_per_level + R.slot_off[g];
     const int64_t np = R.npan[g];
     const int64_t m = m0 + p;
-    if (m <= m_last) {
+    if (m <= m_last && MARFA_DCHECK(m >= m_first, 104)) {
       gp[m - m_first] = sL + cL;
       gp[np + (m - m_first)] = sM + cM;
     }
@@ -1746,6 +1791,7 @@ __global__ void __launch_bounds__(kCWarps * 32)
             const ChiThr ct{J.r3, J.r150, J.r300, J.l3, J.l150, J.l300};
             v *= ct.value(j, fabsf((jf + J.qf) + J.phi) * hnode);
           }
+          if (!MARFA_DCHECK(li < 32 && j < 2 * kCPairs, 103)) continue;
           if (j & 1) bO[li][j >> 1] = v;
           else bE[li][j >> 1] = v;
           count_eval<COUNT>(voigt, xv, J.y, nev, nnear, nmid, nsmall);
@@ -1770,7 +1816,7 @@ __global__ void __launch_bounds__(kCWarps * 32)
     float* gp = R.slots + (int64_t)lev * R.slots_per_level + R.slot_off[g];
     const int64_t np = R.npan[g];
     const int64_t m = m0 + p;
-    if (m <= m_last) {
+    if (m <= m_last && MARFA_DCHECK(m >= m_first, 104)) {
       gp[m - m_first] = sL + cL;
       gp[np + (m - m_first)] = sM + cM;
     }
@@ -1900,7 +1946,7 @@ __device__ __forceinline__ void fine_cascade_store(const ReqDev& R, const FineIt
   __syncthreads();
   // write the valid part [a, b] of the tile
   const int64_t a = max(it.k0, R.k_lo), b = min(it.k0 + kFineTile - 1, R.k_hi);
-  if (a <= b) {
+  if (a <= b && MARFA_DCHECK(a - R.k_lo >= 0 && b - R.k_lo < R.npts, 203)) {
     float* row = R.out + (int64_t)lev * R.npts;
     const int64_t i0 = a - R.k_lo;           // first output index
     const int n = (int)(b - a + 1);
@@ -2265,8 +2311,10 @@ __global__ void __launch_bounds__(kFineThreads, 4)
       const int tot = __shfl_sync(0xffffffffu, pre, 31);
       const int F = tot & 0xffff, J = F + (tot >> 16);
       int pf = (pre & 0xffff) - nf, pn = F + (pre >> 16) - nn;
-      for (uint32_t m = far; m; m &= m - 1) jobs[pf++] = (uint16_t)((lane << 4) | (__ffs(m) - 1));
-      for (uint32_t m = pm & ~far; m; m &= m - 1) jobs[pn++] = (uint16_t)((lane << 4) | (__ffs(m) - 1));
+      for (uint32_t m = far; m; m &= m - 1)
+        if (MARFA_DCHECK(pf < 32 * 16, 201)) jobs[pf++] = (uint16_t)((lane << 4) | (__ffs(m) - 1));
+      for (uint32_t m = pm & ~far; m; m &= m - 1)
+        if (MARFA_DCHECK(pn < 32 * 16, 201)) jobs[pn++] = (uint16_t)((lane << 4) | (__ffs(m) - 1));
       __syncwarp();
       float* acc = &sAcc[gi][kWarpNodes * warp];
 #pragma unroll 1
@@ -2286,7 +2334,7 @@ __global__ void __launch_bounds__(kFineThreads, 4)
           const ChiThr ct{fc.r3, fc.r150, fc.r300, fc.l3, fc.l150, fc.l300};
           v *= ct.value(j, fabsf((jf + fl.qf) + fl.phi) * ldexpf(1.0f, -kFineBits));
         }
-        acc[j] += v;
+        if (MARFA_DCHECK(j >= 0 && j < kWarpNodes, 202)) acc[j] += v;
         count_eval<COUNT>(voigt, xv, fl.y, nev, nnear, nmid, nsmall);
       }
       __syncwarp();

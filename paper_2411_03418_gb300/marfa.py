@@ -47,7 +47,8 @@ EXPORTS = ["marfa_prepare_lines", "marfa_free_lines", "marfa_num_points", "marfa
            "marfa_mlp_train", "marfa_surrogate_load", "marfa_surrogate_unload", "marfa_surrogate_eval",
            "marfa_diag_absorption_counted_surrogate", "marfa_plan_create", "marfa_plan_execute",
            "marfa_plan_info", "marfa_plan_destroy", "marfa_diag_absorption_counts", "marfa_read_par",
-           "marfa_diag_pipe_rate", "marfa_diag_line_order", "marfa_diag_shape", "marfa_diag_variants"]
+           "marfa_diag_pipe_rate", "marfa_diag_line_order", "marfa_diag_shape", "marfa_diag_variants",
+           "marfa_diag_fail_alloc", "marfa_diag_device_memory", "marfa_diag_check"]
 
 MLP_PARAMS = 8577
 MLP_MAX_BATCH = 65536
@@ -101,6 +102,9 @@ def load(path: str | None = None):
         "marfa_plan_execute": (C.c_int, [vp, vp]),
         "marfa_plan_info": (C.c_int, [vp, vp, vp, vp]),
         "marfa_diag_variants": (C.c_int, [vp, vp]),
+        "marfa_diag_fail_alloc": (C.c_int, [C.c_int64, vp]),
+        "marfa_diag_device_memory": (C.c_int, [vp, vp]),
+        "marfa_diag_check": (C.c_int, [C.c_int32, vp]),
         "marfa_plan_destroy": (None, [vp]),
         "marfa_diag_absorption_counts": (C.c_int, [vp, vp, vp, i32, vp, vp, vp]),
     }
@@ -261,6 +265,29 @@ def marfa_plan_info(plan: Plan, kernel_ms: bool = False):
     k = np.empty(12, dtype=np.float64) if kernel_ms else None
     _check(load().marfa_plan_info(plan.handle, _ptr(v), _ptr(t), _ptr(k)))
     return v, t, k
+
+
+def marfa_diag_fail_alloc(nth: int) -> int:
+    """Make the nth allocation from now on fail (0 disarms); returns what the previous
+    arming still had to let through plus one (0: it was not armed)."""
+    left = C.c_int64(0)
+    _check(load().marfa_diag_fail_alloc(int(nth), C.byref(left)))
+    return left.value
+
+
+def marfa_diag_check(index: int) -> bool:
+    """Run the device-check probe at index; returns whether the library is a MARFA_DEBUG
+    build (raises MarfaError MARFA_E_INTERNAL when the probe's check fails there)."""
+    dbg = C.c_int32(0)
+    _check(load().marfa_diag_check(int(index), C.byref(dbg)))
+    return bool(dbg.value)
+
+
+def marfa_diag_device_memory():
+    """(bytes in use from the device's default memory pool, free device memory)."""
+    used, free = C.c_int64(0), C.c_int64(0)
+    _check(load().marfa_diag_device_memory(C.byref(used), C.byref(free)))
+    return used.value, free.value
 
 
 def marfa_diag_variants(variants=None) -> np.ndarray:

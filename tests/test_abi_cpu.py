@@ -228,3 +228,18 @@ def test_line_order_small_inputs(M):
         lines = np.zeros(n, dtype=M.LINE_DTYPE)
         lines["nu0"] = np.floor(rng.random(n) * max(2, n // 3)) * 0.5 + 1000.0
         assert np.array_equal(M.marfa_diag_line_order(lines), np.argsort(lines["nu0"], kind="stable")), n
+
+
+def test_fail_alloc_environment_arms_the_injector():
+    """MARFA_FAIL_ALLOC=n arms the allocation-failure injector when the library loads
+    (checked in a fresh process; no GPU call is made)."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_2411_03418_gb300 import marfa as M\n"
+            "M.load(); print(M.marfa_diag_fail_alloc(0), M.marfa_diag_fail_alloc(0))" % root)
+    env = dict(os.environ, MARFA_FAIL_ALLOC="7")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.split() == ["7", "0"]
