@@ -523,8 +523,8 @@ def main():
                      "variant_grids_1_10_finest": [int(v) for v in variant],
                      "autotune_ms_per_launch": [[round(float(a), 3) for a in row] for row in tune_ms],
                      "variants": "grids 2-10: 0 line-major 32 pairs, 1 two-phase, 2 line-major 16 pairs, "
-                                 "3 flattened, 4 by mechanism; finest: 0 groups per panel, 1 flattened jobs, "
-                                 "2 flattened jobs by mechanism"},
+                                 "3 flattened, 4 by mechanism, 5 by mechanism merged; finest: 0 groups per panel, "
+                                 "1 flattened jobs, 2 flattened jobs by mechanism, 3 the same merged"},
             "kernel_ms_per_step_serial": {n: float(kms[i] / args.steps) for i, n in enumerate(names)},
             "roofline": {"bound": "alu", "kernel": names[dom], "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak,

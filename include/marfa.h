@@ -176,8 +176,8 @@ int marfa_absorption_batch(int32_t n_req, const marfa_lines_t* const* lines,
  *              flattened: the two-phase tiles with the evaluations spread evenly over
  *              the lanes and grouped by Voigt branch; by mechanism: the two-phase tiles
  *              with candidates taken per centre, cut-off edge and chi breakpoint, each
- *              with closed-form ownership, where those lie far enough apart), and for
- *              the finest grid its three
+ *              with closed-form ownership, where those lie far enough apart, in a
+ *              pass per mechanism or one merged pass), and for the finest grid its four
  *              kernels (8-lane groups per G10 panel; flattened (line, panel) jobs, with
  *              general or closed-form ownership), on
  *              this batch's own work and keep the fastest (otherwise the defaults of
@@ -208,15 +208,16 @@ int marfa_plan_execute(marfa_plan_t* plan, void* stream);
 /* Kernel choice and timings (host arrays, each may be NULL): variant[MARFA_PLAN_KINDS]
  * for grids 1..10 and the finest grid (grid 1: -1, its one kernel; grids 2..10: 0
  * line-major over 32 pairs, 1 two-phase, 2 line-major over 16 pairs, 3 flattened, 4 by
- * mechanism (closed-form ownership; the launch takes 1 where it does not apply); finest
+ * mechanism (closed-form ownership, a pass per mechanism; the launch takes 1 where it
+ * does not apply), 5 by mechanism in one merged pass; finest
  * grid: 0 groups per panel, 1 flattened jobs, 2 flattened jobs by mechanism (1 where it
- * does not apply)); tune_ms[MARFA_PLAN_KINDS][MARFA_PLAN_VARIANTS]
+ * does not apply), 3 the same in one merged pass); tune_ms[MARFA_PLAN_KINDS][MARFA_PLAN_VARIANTS]
  * the autotuner's time per launch of each variant (-1 when not tuned or not a variant of
  * that kind); kernel_ms[12] device time of the last
  * execution per kernel kind (0 level preparation, 1..10 grids, 11 finest grid; waits for
  * that execution; MARFA_E_CUDA before the first execution). */
 #define MARFA_PLAN_KINDS 11
-#define MARFA_PLAN_VARIANTS 5
+#define MARFA_PLAN_VARIANTS 6
 int marfa_plan_info(const marfa_plan_t* plan, int32_t* variant, float* tune_ms, double* kernel_ms);
 
 /* Test and tuning hook: the process-wide kernel variants that calls without autotuning

@@ -965,18 +965,20 @@ static void* pinned_host_view(void* p) {
 // with 16 node pairs per CTA (half the shared memory, narrower tiles), 3 = flattened
 // (k_coarse_jobs: the two-phase tiles with phase 1 spread evenly over the lanes and
 // grouped by Voigt branch), 4 = by mechanism (k_coarse_mech: the two-phase tiles with
-// closed-form ownership, where every request of the launch has its mech bit for the
-// grid; otherwise the launch takes variant 1). Finest grid (kind kFineKind): 0 = k_fine (an 8-lane group per
+// closed-form ownership, one candidate pass per mechanism, where every request of the
+// launch has its mech bit for the grid; otherwise the launch takes variant 1), 5 = the
+// same in one merged pass. Finest grid (kind kFineKind): 0 = k_fine (an 8-lane group per
 // G10 panel), 1 = k_fine_jobs ((line, panel) jobs spread evenly over the groups), 2 = the
-// same with closed-form ownership (mech bit of every request; otherwise variant 1).
+// same with closed-form ownership, one pass per mechanism (mech bit of every request;
+// otherwise variant 1), 3 = the same in one merged pass.
 // Surrogate-capable launches always take variant 1 on grids 2..10 (when 3 is chosen)
 // and k_fine. Calls without tuning take the process-wide defaults (marfa_diag_variants).
-constexpr int kNVariants = 5;
+constexpr int kNVariants = 6;
 constexpr int kFineKind = kNGrid + 1;
-constexpr int kNFineVariants = 3;
+constexpr int kNFineVariants = 4;
 // Defaults measured on the Venus workload (line-major over 16 pairs on grids 2..7, the
-// mechanism kernel on 8..10, flattened jobs on the finest grid).
-static std::atomic<int> g_default_variant[kNGrid + 2] = {{-1}, {-1}, {2}, {2}, {2}, {2}, {2}, {2}, {4}, {4}, {4}, {1}};
+// mechanism kernel on 8..10, flattened jobs by mechanism on the finest grid).
+static std::atomic<int> g_default_variant[kNGrid + 2] = {{-1}, {-1}, {2}, {2}, {2}, {2}, {2}, {2}, {4}, {4}, {4}, {2}};
 static int default_variant(int g) { return g_default_variant[g].load(std::memory_order_relaxed); }
 static int64_t variant_pairs(int v) {
   return v == 0 ? (int64_t)kLPairs : (v == 2 ? (int64_t)16 : (int64_t)kCPairs * kCWarps);
@@ -1185,10 +1187,10 @@ static int build_work(std::vector<Plan>& plans, const int* variant, bool count, 
 // Grid g of a work set with kernel variant v.
 static void launch_grid(const WorkSet& W, int g, cudaStream_t st) {
   const int n = (int)W.ci[g].size();
-  bool mech = W.variant[g] == 4 && !W.surr_grid[g] && !W.wide;
+  bool mech = (W.variant[g] == 4 || W.variant[g] == 5) && !W.surr_grid[g] && !W.wide;
   for (const auto& R : W.rds) mech = mech && ((R.mech >> g) & 1);
   if (mech)
-    launch_coarse_mech(W.drd, W.dci[g], n, W.dcc[g], st);
+    launch_coarse_mech(W.drd, W.dci[g], n, W.dcc[g], W.variant[g] == 5, st);
   else if (W.variant[g] == 3 && !W.surr_grid[g])
     launch_coarse_jobs(W.drd, W.dci[g], n, W.dcc[g], W.wide, st);
   else if (W.variant[g] == 1 || W.variant[g] >= 3)
@@ -1201,10 +1203,10 @@ static void launch_grid(const WorkSet& W, int g, cudaStream_t st) {
 // The finest grid + cascade of a work set with its kernel variant.
 static void launch_finest(const WorkSet& W, cudaStream_t st) {
   const int n = (int)W.fi.size();
-  bool mech = W.variant[kFineKind] == 2 && !W.wide;
+  bool mech = W.variant[kFineKind] >= 2 && !W.wide;
   for (const auto& R : W.rds) mech = mech && ((R.mech >> (kNGrid + 1)) & 1);
   if (W.variant[kFineKind] >= 1 && !W.surr_grid[kNGrid + 1])
-    launch_fine_jobs(W.drd, W.dfi, n, W.dfc, W.wide, mech, st);
+    launch_fine_jobs(W.drd, W.dfi, n, W.dfc, W.wide, mech ? W.variant[kFineKind] - 1 : 0, st);
   else
     launch_fine(W.drd, W.dfi, n, W.dfc, W.surr_grid[kNGrid + 1], W.wide, st);
 }
@@ -1807,8 +1809,8 @@ extern "C" int marfa_absorption_noalloc(const marfa_lines_t* lines, const marfa_
     size_t k1 = k;
     while (k1 < coarse.size() && coarse[k1].grid == g) ++k1;
     const int v = var[g];
-    if (v == 4 && !surr && !wide && ((R.mech >> g) & 1))
-      launch_coarse_mech(drd, dci + k, (int)(k1 - k), nullptr, st);
+    if ((v == 4 || v == 5) && !surr && !wide && ((R.mech >> g) & 1))
+      launch_coarse_mech(drd, dci + k, (int)(k1 - k), nullptr, v == 5, st);
     else if (v == 3 && !surr)
       launch_coarse_jobs(drd, dci + k, (int)(k1 - k), nullptr, wide, st);
     else if (v == 1 || v >= 3)
@@ -1819,7 +1821,7 @@ extern "C" int marfa_absorption_noalloc(const marfa_lines_t* lines, const marfa_
   }
   if (var[kFineKind] >= 1 && !surr)
     launch_fine_jobs(drd, dfi, (int)P.fine.size(), nullptr, wide,
-                     var[kFineKind] == 2 && !wide && ((R.mech >> (kNGrid + 1)) & 1), st);
+                     (var[kFineKind] >= 2 && !wide && ((R.mech >> (kNGrid + 1)) & 1)) ? var[kFineKind] - 1 : 0, st);
   else
     launch_fine(drd, dfi, (int)P.fine.size(), nullptr, surr, wide, st);
   CK(cudaGetLastError());

@@ -208,12 +208,14 @@ void launch_fine(const ReqDev* reqs, const FineItem* items, int n_items, int64_t
 // Grids 2..10 and the finest grid with ownership by mechanism (centre, cut-off edges,
 // chi breakpoints in separate candidate passes, closed forms of ownership.cuh); only for
 // requests whose mech bit of the grid is set (3-point, plain path).
-void launch_coarse_mech(const ReqDev* reqs, const CoarseItem* items, int n_items, int64_t* counts,
+void launch_coarse_mech(const ReqDev* reqs, const CoarseItem* items, int n_items, int64_t* counts, bool merged,
                         cudaStream_t st);
 void launch_coarse_jobs(const ReqDev* reqs, const CoarseItem* items, int n_items, int64_t* counts, bool wide,
                         cudaStream_t st);
+// mech: 0 general ownership, 1 closed forms in one pass per mechanism, 2 closed forms
+// in one merged pass (1, 2: 3-point requests with the mech bit of the finest grid)
 void launch_fine_jobs(const ReqDev* reqs, const FineItem* items, int n_items, int64_t* counts, bool wide,
-                      bool mech, cudaStream_t st);
+                      int mech, cudaStream_t st);
 void launch_diag_voigt(const float* x, const float* y, float* out, int64_t n, cudaStream_t st);
 void launch_diag_shape(int shape, const float* x, const float* y, float* out, int64_t n, cudaStream_t st);
 // instructions issued by one probe launch (out: blocks x 256 floats)

@@ -56,7 +56,7 @@ __global__ void k_diag_check(int i, int* sink) {
   a[threadIdx.x] = 0;
   __syncwarp();
   if (i >= 0 && i < 32 && MARFA_DCHECK(true, 901)) a[i] = 1;
-  else MARFA_DCHECK(false, 901);
+  else (void)MARFA_DCHECK(false, 901);
   __syncwarp();
   if (a[threadIdx.x] && sink) *sink = 1;
 }
@@ -1397,7 +1397,11 @@ void launch_coarse(const ReqDev* reqs, const CoarseItem* items, int n_items, int
 // one branch of Eq. (10) along an edge panel, and decided per node near a breakpoint.
 // Values go through the per-line buffers and phase 2 of k_coarse (pair sums in line
 // order within a pass, passes in a fixed order): results are deterministic.
-template <bool COUNT>
+// MERGED: one pass over the merged position zones of all mechanisms instead of one pass
+// per mechanism (fewer band lookups and rounds; a candidate's panels are then the union
+// of its mechanisms' closed forms, and the chi-factor of a run of panels is 1 when the
+// run lies in the centre region, else decided per node).
+template <bool COUNT, bool MERGED>
 __global__ void __launch_bounds__(kCWarps * 32, 6)
     k_coarse_mech(const ReqDev* __restrict__ reqs, const CoarseItem* __restrict__ items,
                   int64_t* __restrict__ counts) {
@@ -1436,26 +1440,55 @@ __global__ void __launch_bounds__(kCWarps * 32, 6)
     int nB = 0;
     if (R.chi_req)
       for (int b = 0; b < 3 && chi_break_fx(b) <= cut; ++b) nB = b + 1;
-    const int npass = 3 + 2 * nB;
+    const int npass = MERGED ? 1 : 3 + 2 * nB;
+    // the centre region ends before the first breakpoint's region begins (mech_ok)
+    const float centre_end = 3.0f - 4.0f * ldexpf(1.0f, s - 1 - kFixBits);
     float (*bE)[kCPairs + 1] = bufE[warp];
     float (*bO)[kCPairs + 1] = bufO[warp];
     unsigned long long* mk = smsk[warp];
     const int p = lane;
     float sL = 0.f, cL = 0.f, sR = 0.f, cR = 0.f, sM = 0.f, cM = 0.f;
+    // pass 0 centre; 1, 2 the right and left cut-off edges; then the right and left
+    // positions of each breakpoint. The mechanism sits at c + off; positions of c + off
+    // within reach of the tile can give panels of it.
+    auto pass_off = [&](int q) {
+      return q == 0 ? (int64_t)0
+           : q == 1 ? cut
+           : q == 2 ? -cut
+           : ((q & 1) ? chi_break_fx((q - 3) >> 1) : -chi_break_fx((q - 3) >> 1));
+    };
+    // every pass's candidate range at once (lane 2q: the first line of pass q, lane
+    // 2q + 1: its end), so that the lookups' global loads overlap
+    int64_t range_v = 0;
+    if (!MERGED && lane < 2 * npass) {
+      const int q = lane >> 1;
+      const int64_t off = pass_off(q), reach = q == 0 ? R2 + 2 * P : 2 * P;
+      range_v = (lane & 1) ? upper_idx(R, xb + reach - off - L.smin) : lower_idx(R, xa - reach - off - L.smax);
+    }
     for (int pass = 0; pass < npass; ++pass) {  // warp-uniform
-      // 0 centre; 1, 2 the right and left cut-off edges; then the right and left
-      // positions of each breakpoint. The mechanism sits at c + off.
-      const int64_t off = pass == 0 ? 0
-                        : pass == 1 ? cut
-                        : pass == 2 ? -cut
-                        : ((pass & 1) ? chi_break_fx((pass - 3) >> 1) : -chi_break_fx((pass - 3) >> 1));
-      // positions of c + off that can give panels of the tile
-      const int64_t reach = pass == 0 ? R2 + 2 * P : 2 * P;
+      const int64_t off = pass_off(pass);
       Bands bd;
       bd.n = 0;
-      {
-        const int64_t zlo = xa - reach - off, zhi = xb + reach - off;
-        bd.lookup(R, L, &zlo, &zhi, 1);
+      if (!MERGED) {
+        const int64_t a = __shfl_sync(0xffffffffu, range_v, 2 * pass);
+        const int64_t b = __shfl_sync(0xffffffffu, range_v, 2 * pass + 1);
+        if (a < b) {
+          bd.lo[0] = a;
+          bd.hi[0] = b;
+          bd.n = 1;
+        }
+      } else {
+        int64_t zlo[9], zhi[9];
+        int nz = 0;
+        zlo[nz] = xa - R2 - 2 * P; zhi[nz] = xb + R2 + 2 * P; ++nz;
+        zlo[nz] = xa - 2 * P - cut; zhi[nz] = xb + 2 * P - cut; ++nz;
+        zlo[nz] = xa - 2 * P + cut; zhi[nz] = xb + 2 * P + cut; ++nz;
+        for (int b = 0; b < nB; ++b) {
+          const int64_t B = chi_break_fx(b);
+          zlo[nz] = xa - 2 * P - B; zhi[nz] = xb + 2 * P - B; ++nz;
+          zlo[nz] = xa - 2 * P + B; zhi[nz] = xb + 2 * P + B; ++nz;
+        }
+        bd.lookup(R, L, zlo, zhi, nz);
       }
       const int64_t n_cand = bd.total();
       BandCursor cur;
@@ -1465,8 +1498,37 @@ __global__ void __launch_bounds__(kCWarps * 32, 6)
         uint64_t own = 0;
         int64_t c = 0;
         bool chi = false;
-        if (valid) {
+        float amp_p = 0.0f, sx_p = 1.0f, y_p = 0.0f;
+        if (valid && MERGED) {
           c = __ldg(R.c + lo_off + i);
+          const int gst = __ldg(R.gstar + lo_off + i);
+          chi = __ldg(R.flags + lo_off + i) & 1;
+          if (gst >= g) {
+            int64_t a1, b1, a2, b2;
+            mech_centre(g, c, gst, R.R_w, a1, b1, a2, b2);
+            own = rmask<uint64_t>(a1, b1, base, nb) | rmask<uint64_t>(a2, b2, base, nb);
+          }
+          int64_t q = mech_edge_right(g, c + cut);
+          if (q != -1) own |= rmask<uint64_t>(q, q, base, nb);
+          q = mech_edge_left(g, c - cut);
+          if (q != -1) own |= rmask<uint64_t>(q, q, base, nb);
+          if (chi)
+            for (int b = 0; b < nB; ++b) {
+              int64_t q0, q1;
+              mech_kink(g, c + chi_break_fx(b), q0, q1);
+              if (q0 != -1) own |= rmask<uint64_t>(q0, q0, base, nb);
+              if (q1 != -1) own |= rmask<uint64_t>(q1, q1, base, nb);
+              mech_kink(g, c - chi_break_fx(b), q0, q1);
+              if (q0 != -1) own |= rmask<uint64_t>(q0, q0, base, nb);
+              if (q1 != -1) own |= rmask<uint64_t>(q1, q1, base, nb);
+            }
+          own &= win;
+        } else if (valid) {
+          c = __ldg(R.c + lo_off + i);
+          // the evaluation's line data with the candidate's (one round trip)
+          amp_p = __ldg(R.amp + lo_off + i);
+          sx_p = __ldg(R.sx + lo_off + i);
+          y_p = __ldg(R.yv + lo_off + i);
           if (pass == 0) {
             const int gst = __ldg(R.gstar + lo_off + i);
             if (gst >= g) {
@@ -1492,14 +1554,14 @@ __global__ void __launch_bounds__(kCWarps * 32, 6)
         const uint32_t tev = (uint32_t)(own | (own >> 1));
         if (!__ballot_sync(0xffffffffu, tev != 0)) continue;
         if (tev) {
-          const float amp = __ldg(R.amp + lo_off + i);
-          const float sx = __ldg(R.sx + lo_off + i);
-          const float y = __ldg(R.yv + lo_off + i);
+          const float amp = MERGED ? __ldg(R.amp + lo_off + i) : amp_p;
+          const float sx = MERGED ? __ldg(R.sx + lo_off + i) : sx_p;
+          const float y = MERGED ? __ldg(R.yv + lo_off + i) : y_p;
           NodeX nx;
           nx.init(X0 - c, s - 1, sx);
           const bool use_chi = chi && physical;
           ChiThr ct;
-          if (use_chi && pass > 2) ct.init(c, X0, s - 1);
+          if (use_chi && (MERGED || pass > 2)) ct.init(c, X0, s - 1);
           // runs of owned panels: bits [ba, be] give nodes [2 ba - 2, 2 be] of the tile
           for (uint64_t rest = own; rest;) {
             const int ba = __ffsll((long long)rest) - 1;
@@ -1507,11 +1569,16 @@ __global__ void __launch_bounds__(kCWarps * 32, 6)
             const int be = above ? __ffsll((long long)above) - 2 : 63;
             rest &= be >= 63 ? 0ull : (~0ull << (be + 1));
             const int ja = max(2 * ba - 2, 0), jb = min(2 * be, 2 * kCPairs - 1);
+            // merged: a run in the centre region has chi = 1, any other run takes the
+            // general per-node rule (an edge run or a breakpoint run)
+            const bool run_chi = MERGED && use_chi && nx.absd((float)ja, s - 1) >= centre_end;
             for (int j = ja; j <= jb; ++j) {
               const float jf = (float)j;
               const float xv = nx.x(jf);
               float v = amp * (voigt ? voigt_K<false, false, true>(xv, y, kVoigtCells) : shape_f(R.shape, xv, y));
-              if (use_chi) {
+              if (MERGED) {
+                if (run_chi) v *= ct.value(j, nx.absd(jf, s - 1));
+              } else if (use_chi) {
                 if (pass > 2)
                   v *= ct.value(j, nx.absd(jf, s - 1));
                 else if (pass > 0 && eb > 0)
@@ -1553,14 +1620,20 @@ __global__ void __launch_bounds__(kCWarps * 32, 6)
   if (COUNT) block_counts<kCWarps>(nev, 0, nnear, nmid, nsmall, sCnt, counts);
 }
 
-void launch_coarse_mech(const ReqDev* reqs, const CoarseItem* items, int n_items, int64_t* counts,
+void launch_coarse_mech(const ReqDev* reqs, const CoarseItem* items, int n_items, int64_t* counts, bool merged,
                         cudaStream_t st) {
   if (n_items <= 0) return;
   const int T = kCWarps * 32;
-  if (counts)
-    k_coarse_mech<true><<<n_items, T, 0, st>>>(reqs, items, counts);
-  else
-    k_coarse_mech<false><<<n_items, T, 0, st>>>(reqs, items, counts);
+  if (merged) {
+    if (counts)
+      k_coarse_mech<true, true><<<n_items, T, 0, st>>>(reqs, items, counts);
+    else
+      k_coarse_mech<false, true><<<n_items, T, 0, st>>>(reqs, items, counts);
+  } else if (counts) {
+    k_coarse_mech<true, false><<<n_items, T, 0, st>>>(reqs, items, counts);
+  } else {
+    k_coarse_mech<false, false><<<n_items, T, 0, st>>>(reqs, items, counts);
+  }
 }
 
 // ------------------------------------------------------------------ grids 2..10, flattened
@@ -2158,12 +2231,14 @@ struct __align__(16) FineChi16 {
   int16_t on, pad;
 };
 
-// MECH: where the centre region, cut-off edges and chi breakpoints lie apart
-// (mech_fine_ok), the candidates come in one pass per mechanism, each with its node range
-// in closed form (mech_fine_*): the centre pass takes the lines with g* = 11 (chi = 1
-// there: the region lies inside the first breakpoint), the edge and breakpoint passes
-// the lines whose edge or breakpoint falls near the warp's nodes.
-template <bool COUNT, int WIDE, bool MECH>
+// MECH (1 or 2): where the centre region, cut-off edges and chi breakpoints lie apart
+// (mech_fine_ok), a candidate's nodes come in closed form (mech_fine_*). With MECH = 1
+// the candidates come in one pass per mechanism: the centre pass takes the lines with
+// g* = 11 (chi = 1 there: the region lies inside the first breakpoint), the edge and
+// breakpoint passes the lines whose edge or breakpoint falls near the warp's nodes. With
+// MECH = 2 one pass takes the merged zones; a candidate's nodes in the warp then come from
+// one mechanism at most (the warp spans 1/16 cm^-1, the mechanisms lie >= 3 cm^-1 apart).
+template <bool COUNT, int WIDE, int MECH>
 __global__ void __launch_bounds__(kFineThreads, 4)
     k_fine_jobs(const ReqDev* __restrict__ reqs, const FineItem* __restrict__ items,
                 int64_t* __restrict__ counts) {
@@ -2199,7 +2274,7 @@ __global__ void __launch_bounds__(kFineThreads, 4)
   const int64_t P10 = int64_t(1) << panel_shift(kNGrid);
   Bands bd;
   bd.n = 0;
-  if (!MECH && wlo <= whi) {
+  if (MECH == 0 && wlo <= whi) {
     int64_t zlo[9], zhi[9];
     const int nz = make_zones((kw + wlo) << kFineShift, (kw + whi) << kFineShift, (int64_t)R.R_w * step_fx(kNGrid),
                               cut, wide ? P10 << 1 : P10, R.chi_req, zlo, zhi);
@@ -2210,17 +2285,48 @@ __global__ void __launch_bounds__(kFineThreads, 4)
   int nB = 0;
   if (MECH && R.chi_req)
     for (int b = 0; b < 3 && chi_break_fx(b) <= cut; ++b) nB = b + 1;
-  const int npass = MECH ? 3 + 2 * nB : 1;
+  const int npass = MECH == 1 ? 3 + 2 * nB : 1;
+  // the mechanism of pass q sits at c + off(q) (MECH only)
+  auto pass_off = [&](int q) {
+    return q == 0 ? (int64_t)0
+         : q == 1 ? cut
+         : q == 2 ? -cut
+         : ((q & 1) ? chi_break_fx((q - 3) >> 1) : -chi_break_fx((q - 3) >> 1));
+  };
+  // MECH == 1: every pass's candidate range at once (lane 2q: first line, 2q + 1: end)
+  int64_t range_v = 0;
+  if (MECH == 1 && wlo <= whi && lane < 2 * npass) {
+    const int q = lane >> 1;
+    const int64_t off = pass_off(q);
+    const int64_t reach = (q == 0 ? (int64_t)R.R_w * step_fx(kNGrid) : 0) + P10 + 1;
+    range_v = (lane & 1) ? upper_idx(R, ((kw + whi) << kFineShift) + reach - off - L.smin)
+                         : lower_idx(R, ((kw + wlo) << kFineShift) - reach - off - L.smax);
+  }
   for (int pass = 0; pass < npass && wlo <= whi; ++pass) {  // warp-uniform
-    // the mechanism of this pass sits at c + off (MECH only)
-    const int64_t off = pass == 0 ? 0
-                      : pass == 1 ? cut
-                      : pass == 2 ? -cut
-                      : ((pass & 1) ? chi_break_fx((pass - 3) >> 1) : -chi_break_fx((pass - 3) >> 1));
-    if (MECH) {
-      const int64_t reach = (pass == 0 ? (int64_t)R.R_w * step_fx(kNGrid) : 0) + P10 + 1;
-      const int64_t zlo = ((kw + wlo) << kFineShift) - reach - off, zhi = ((kw + whi) << kFineShift) + reach - off;
-      bd.lookup(R, L, &zlo, &zhi, 1);
+    const int64_t off = pass_off(pass);
+    if (MECH == 1) {
+      const int64_t a = __shfl_sync(0xffffffffu, range_v, 2 * pass);
+      const int64_t b = __shfl_sync(0xffffffffu, range_v, 2 * pass + 1);
+      bd.n = 0;
+      if (a < b) {
+        bd.lo[0] = a;
+        bd.hi[0] = b;
+        bd.n = 1;
+      }
+    } else if (MECH == 2) {
+      const int64_t Xlo = (kw + wlo) << kFineShift, Xhi = (kw + whi) << kFineShift;
+      const int64_t rc = (int64_t)R.R_w * step_fx(kNGrid) + P10 + 1, re = P10 + 1;
+      int64_t zlo[9], zhi[9];
+      int nz = 0;
+      zlo[nz] = Xlo - rc; zhi[nz] = Xhi + rc; ++nz;
+      zlo[nz] = Xlo - re - cut; zhi[nz] = Xhi + re - cut; ++nz;
+      zlo[nz] = Xlo - re + cut; zhi[nz] = Xhi + re + cut; ++nz;
+      for (int b = 0; b < nB; ++b) {
+        const int64_t B = chi_break_fx(b);
+        zlo[nz] = Xlo - re - B; zhi[nz] = Xhi + re - B; ++nz;
+        zlo[nz] = Xlo - re + B; zhi[nz] = Xhi + re + B; ++nz;
+      }
+      bd.lookup(R, L, zlo, zhi, nz);
     }
     const int64_t pbase = kw >> 3;
     const int64_t lo_off = (int64_t)lev * R.n_lines;
@@ -2237,7 +2343,42 @@ __global__ void __launch_bounds__(kFineThreads, 4)
       int klo = 0, khi = -1;
       int64_t c = 0;
       bool chi = false;
-      if (valid && MECH) {
+      bool centre = false;  // MECH == 2: the nodes are the centre's (chi = 1)
+      if (valid && MECH == 2) {
+        c = __ldg(R.c + lo_off + i);
+        chi = __ldg(R.flags + lo_off + i) & 1;
+        const int64_t lo = kw + wlo, hi = kw + whi;
+        int64_t a = 1, b = 0, a2, b2;
+        int found = 0;
+        auto take = [&](int64_t x, int64_t y, bool ctr) {
+          x = max(x, lo);
+          y = min(y, hi);
+          if (x <= y) {
+            a = x;
+            b = y;
+            centre = ctr;
+            ++found;
+          }
+        };
+        mech_fine_centre(c, __ldg(R.gstar + lo_off + i), R.R_w, a2, b2);
+        take(a2, b2, true);
+        mech_fine_edge_right(c + cut, a2, b2);
+        take(a2, b2, false);
+        mech_fine_edge_left(c - cut, a2, b2);
+        take(a2, b2, false);
+        if (chi)
+          for (int q = 0; q < nB; ++q) {
+            mech_fine_kink(c + chi_break_fx(q), a2, b2);
+            take(a2, b2, false);
+            mech_fine_kink(c - chi_break_fx(q), a2, b2);
+            take(a2, b2, false);
+          }
+        if (found && MARFA_DCHECK(found == 1, 204)) {
+          klo = (int)(a - kw);
+          khi = (int)(b - kw);
+          pm = rmask<uint32_t>(klo >> 3, khi >> 3, 0, 16);
+        }
+      } else if (valid && MECH == 1) {
         c = __ldg(R.c + lo_off + i);
         int64_t a = 1, b = 0;
         if (pass == 0) {
@@ -2280,7 +2421,7 @@ __global__ void __launch_bounds__(kFineThreads, 4)
         fl.phi = nx.phi;
         sL[warp][lane] = fl;
         FineChi16 fc;
-        fc.on = chi && physical && !(MECH && pass == 0);
+        fc.on = chi && physical && !(MECH == 1 && pass == 0) && !(MECH == 2 && centre);
         fc.pad = 0;
         if (fc.on) {
           ChiThr ct;
@@ -2358,23 +2499,28 @@ __global__ void __launch_bounds__(kFineThreads, 4)
 constexpr size_t kFineJobsDyn = sizeof(float) * 4 * kFineTile;
 
 void launch_fine_jobs(const ReqDev* reqs, const FineItem* items, int n_items, int64_t* counts, bool wide,
-                      bool mech, cudaStream_t st) {
+                      int mech, cudaStream_t st) {
   if (n_items <= 0) return;
   const size_t B = kFineJobsDyn;
-  if (mech) {  // 3-point only
+  if (mech == 1) {  // 3-point only
     if (counts)
-      launch_dyn(k_fine_jobs<true, 0, true>, n_items, kFineThreads, B, st, reqs, items, counts);
+      launch_dyn(k_fine_jobs<true, 0, 1>, n_items, kFineThreads, B, st, reqs, items, counts);
     else
-      launch_dyn(k_fine_jobs<false, 0, true>, n_items, kFineThreads, B, st, reqs, items, counts);
+      launch_dyn(k_fine_jobs<false, 0, 1>, n_items, kFineThreads, B, st, reqs, items, counts);
+  } else if (mech == 2) {
+    if (counts)
+      launch_dyn(k_fine_jobs<true, 0, 2>, n_items, kFineThreads, B, st, reqs, items, counts);
+    else
+      launch_dyn(k_fine_jobs<false, 0, 2>, n_items, kFineThreads, B, st, reqs, items, counts);
   } else if (counts) {
     if (wide)
-      launch_dyn(k_fine_jobs<true, 1, false>, n_items, kFineThreads, B, st, reqs, items, counts);
+      launch_dyn(k_fine_jobs<true, 1, 0>, n_items, kFineThreads, B, st, reqs, items, counts);
     else
-      launch_dyn(k_fine_jobs<true, 0, false>, n_items, kFineThreads, B, st, reqs, items, counts);
+      launch_dyn(k_fine_jobs<true, 0, 0>, n_items, kFineThreads, B, st, reqs, items, counts);
   } else if (wide) {
-    launch_dyn(k_fine_jobs<false, 1, false>, n_items, kFineThreads, B, st, reqs, items, counts);
+    launch_dyn(k_fine_jobs<false, 1, 0>, n_items, kFineThreads, B, st, reqs, items, counts);
   } else {
-    launch_dyn(k_fine_jobs<false, 0, false>, n_items, kFineThreads, B, st, reqs, items, counts);
+    launch_dyn(k_fine_jobs<false, 0, 0>, n_items, kFineThreads, B, st, reqs, items, counts);
   }
 }
 

@@ -255,11 +255,11 @@ def marfa_plan_execute(plan: Plan, stream=None) -> None:
     _check(load().marfa_plan_execute(plan.handle, _stream(stream)))
 
 
-PLAN_KINDS, PLAN_VARIANTS = 11, 5
+PLAN_KINDS, PLAN_VARIANTS = 11, 6
 
 
 def marfa_plan_info(plan: Plan, kernel_ms: bool = False):
-    """(variant[11] for grids 1..10 and the finest grid, tune_ms[11, 5], kernel_ms[12] or None)."""
+    """(variant[11] for grids 1..10 and the finest grid, tune_ms[11, 6], kernel_ms[12] or None)."""
     v = np.empty(PLAN_KINDS, dtype=np.int32)
     t = np.empty((PLAN_KINDS, PLAN_VARIANTS), dtype=np.float32)
     k = np.empty(12, dtype=np.float64) if kernel_ms else None

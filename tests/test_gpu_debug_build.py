@@ -42,8 +42,8 @@ cases = [
                   chi_species=1, stencil=5),
 ]
 refs = [[O.eleven_grid(w, l) for l in range(w.n_levels)] for w in cases]
-for coarse in range(5):
-    for fine in range(3):
+for coarse in range(6):
+    for fine in range(4):
         v = np.full(11, coarse, np.int32); v[0] = -1; v[10] = fine
         M.marfa_diag_variants(v)
         for w, ref in zip(cases, refs):

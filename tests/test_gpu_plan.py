@@ -109,11 +109,11 @@ def test_autotuned_plan_parity(M):
     M.marfa_plan_execute(plan)
     torch.cuda.synchronize()
     v, t, _ = M.marfa_plan_info(plan)
-    assert set(v[1:10].tolist()) <= {0, 1, 2, 3, 4} and v[10] in (0, 1, 2)
-    assert np.all(t[1:10] > 0) and np.all(t[10, :3] > 0) and np.all(t[10, 3:] == -1) and np.all(t[0] == -1)
+    assert set(v[1:10].tolist()) <= {0, 1, 2, 3, 4, 5} and v[10] in (0, 1, 2, 3)
+    assert np.all(t[1:10] > 0) and np.all(t[10, :4] > 0) and np.all(t[10, 4:] == -1) and np.all(t[0] == -1)
     for g in range(1, 10):  # the chosen variant is the fastest one
         assert t[g, v[g]] <= t[g].min()
-    assert t[10, v[10]] <= t[10, :3].min()
+    assert t[10, v[10]] <= t[10, :4].min()
     for q, w in enumerate(SMALL):
         got = outs[q].cpu().numpy()
         for lev in range(w.n_levels):

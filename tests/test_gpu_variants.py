@@ -1,8 +1,9 @@
 """Every summation-kernel variant against the FP64 oracle (GPU).
 
-Grids 2..10 have five kernels (line-major over 32 or 16 node pairs, two-phase,
-flattened, by mechanism) and the finest grid three (8-lane groups per G10 panel,
-flattened jobs, flattened jobs by mechanism); a captured plan's autotuner picks one per
+Grids 2..10 have six kernels (line-major over 32 or 16 node pairs, two-phase,
+flattened, by mechanism in a pass per mechanism or one merged pass) and the finest grid
+four (8-lane groups per G10 panel, flattened jobs, flattened jobs by mechanism in passes
+or merged); a captured plan's autotuner picks one per
 grid. The mechanism kernels apply where centre, edges and breakpoints lie apart (the
 5-point case below falls back to the general kernels). Each computes the same partition in its
 own summation order, so each is held to the same bars: the exact evaluation count per
@@ -80,8 +81,8 @@ def _oracle(ci, lev):
     return _ORACLE[(ci, lev)]
 
 
-@pytest.mark.parametrize("coarse", [0, 1, 2, 3, 4])
-@pytest.mark.parametrize("fine", [0, 1, 2])
+@pytest.mark.parametrize("coarse", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("fine", [0, 1, 2, 3])
 def test_variant_counts_and_parity(M, coarse, fine):
     _force(M, coarse, fine)
     for ci, wl in enumerate(CASES):
@@ -106,8 +107,8 @@ def test_variant_constant_shape_counts_lines(M):
     k_lo, k_hi = O.window_nodes(wl.nu_lo, wl.nu_hi)
     X = np.arange(k_lo, k_hi + 1, dtype=np.int64) << O.fine_shift()
     cut_fx = int(round(wl.cutoff * O.FIX))
-    for coarse in range(5):
-        for fine in range(3):
+    for coarse in range(6):
+        for fine in range(4):
             _force(M, coarse, fine)
             out = np.empty((wl.n_levels, len(X)), np.float32)
             M.marfa_absorption(lines, M.levels_of(wl), wl.vmr, M.request_of(wl), out)
@@ -125,6 +126,6 @@ def test_variants_refuse_out_of_range(M):
         M.marfa_diag_variants(bad)
     assert np.array_equal(M.marfa_diag_variants(), v)
     bad = v.copy()
-    bad[10] = 3
+    bad[10] = 4
     with pytest.raises(M.MarfaError):
         M.marfa_diag_variants(bad)
