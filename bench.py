@@ -394,6 +394,7 @@ def main():
     plan = M.marfa_plan_create(lines, levels, [w.vmr for w in wls], rqs, outs, autotune=True, stream=stream)
     plan_s_create = time.perf_counter() - t0
     variant, tune_ms, _ = M.marfa_plan_info(plan)
+    req_class, class_choice, _ = M.marfa_plan_classes(plan, len(wls))
 
     def step():
         M.marfa_plan_execute(plan, stream)
@@ -522,6 +523,10 @@ def main():
                      "create_s": plan_s_create, "serial_ms_per_step": serial_ms,
                      "variant_grids_1_10_finest": [int(v) for v in variant],
                      "autotune_ms_per_launch": [[round(float(a), 3) for a in row] for row in tune_ms],
+                     "size_classes": {"requests_per_class": [int((req_class == c).sum()) for c in range(2)],
+                                      "choice_per_class": [[int(x) for x in row] for row in class_choice],
+                                      "choice_layout": "[grid-1 split, variant of grids 2..10, finest variant]; "
+                                                       "class 0: windows <= 16 cm-1, 1: wider; -1: no request"},
                      "variants": "grids 2-10: 0 line-major 32 pairs, 1 two-phase, 2 line-major 16 pairs, "
                                  "3 flattened, 4 by mechanism, 5 by mechanism merged; finest: 0 groups per panel, "
                                  "1 flattened jobs, 2 flattened jobs by mechanism, 3 the same merged"},

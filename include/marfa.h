@@ -170,7 +170,9 @@ int marfa_absorption_batch(int32_t n_req, const marfa_lines_t* const* lines,
  *              caller and kept by the plan: every execution rewrites them;
  *   lines    : must stay alive until marfa_plan_destroy; levels, vmr and rq are copied,
  *              and so is the loaded surrogate for requests with surrogate = 1;
- *   flags    : MARFA_PLAN_AUTOTUNE: for each of grids 2..10, time the four summation
+ *   flags    : MARFA_PLAN_AUTOTUNE: for each size class of the batch (marfa_plan_classes):
+ *              the grid-1 split (1, 2, 3 or 6 CTAs per tile), and for each of grids
+ *              2..10 the six summation
  *              kernels (line-major: a thread per candidate line over 32 or over 16 node
  *              pairs; two-phase: warps of 32 node pairs that stage 32 lines at a time;
  *              flattened: the two-phase tiles with the evaluations spread evenly over
@@ -218,7 +220,21 @@ int marfa_plan_execute(marfa_plan_t* plan, void* stream);
  * that execution; MARFA_E_CUDA before the first execution). */
 #define MARFA_PLAN_KINDS 11
 #define MARFA_PLAN_VARIANTS 6
+/* These report the kernel choice of request 0's size class (marfa_plan_classes). */
 int marfa_plan_info(const marfa_plan_t* plan, int32_t* variant, float* tune_ms, double* kernel_ms);
+
+/* Size classes of a plan: the autotuner treats narrow requests (windows of at most
+ * 16 cm^-1, 32769 points) and wider ones apart, since their tiles and candidate counts
+ * differ. Host arrays, each may be NULL: req_class[n_req] receives each request's class
+ * (0 narrow, 1 wide); choice[2][MARFA_PLAN_KINDS] the choice per class (entry 0: the
+ * grid-1 split, the number of CTAs that share a grid-1 tile's candidate lines, 1, 2, 3 or
+ * 6; entries 1..10: the variants of marfa_plan_info's layout), -1 for a class with no
+ * request; tune_ms[2][MARFA_PLAN_KINDS][MARFA_PLAN_VARIANTS] the autotuner's time per
+ * launch of each choice (entry 0: of the splits 1, 2, 3, 6), -1 where not timed. Without
+ * MARFA_PLAN_AUTOTUNE every class takes split 6 and the marfa_diag_variants defaults.
+ * Errors: MARFA_E_INVAL for a NULL plan. */
+#define MARFA_PLAN_CLASSES 2
+int marfa_plan_classes(const marfa_plan_t* plan, int32_t* req_class, int32_t* choice, float* tune_ms);
 
 /* Test and tuning hook: the process-wide kernel variants that calls without autotuning
  * use (marfa_absorption, marfa_absorption_batch, marfa_absorption_noalloc and plans

@@ -756,6 +756,13 @@ extern "C" int64_t marfa_num_points(double nu_lo, double nu_hi) {
 }
 
 // ------------------------------------------------------------------ request plans
+// Size classes of a batch's requests, tuned apart: windows up to 16 cm^-1 (narrow) and
+// wider ones. Per class: the grid-1 split (entry 1 of a choice row), the kernel variant of
+// grids 2..10 (entries 2..10) and of the finest grid (entry 11).
+constexpr int kNClasses = 2;
+constexpr int64_t kNarrowPts = 16 * 2048 + 1;
+constexpr int kG1Splits[4] = {1, 2, 3, 6};
+
 struct Plan {
   const marfa_lines_t* lines = nullptr;
   marfa_request_t rq{};
@@ -765,8 +772,9 @@ struct Plan {
   ReqDev rd{};
   int64_t npts = 0;
   int req_idx = 0;
-  std::vector<G1Item> g1;
+  std::vector<G1Item> g1;     // grid-1 items with kG1Split parts (the no-alloc path's)
   std::vector<FineItem> fine;
+  int cls = 0;                // size class: 0 narrow window, 1 wide (kernel choices per class)
   PrepArgs prep{};            // level-preparation launch, filled by upload()
   // device buffers
   void* dbuf = nullptr;       // per-level line data + slots + tables
@@ -927,6 +935,8 @@ static int build_plan(Plan& P, const marfa_lines_t* L, const marfa_level_t* leve
   }
   R.out_scale = (float)(1.0 / scale);
   R.npts = P.npts;
+  R.g1_split = kG1Split;
+  P.cls = P.npts <= kNarrowPts ? 0 : 1;
   (void)physical;
   // work lists: grid 1 in tiles of kG1Pairs pairs and the finest grid in tiles of
   // kFineTile nodes; grids 2..10 follow the kernel variant chosen per grid (coarse_items)
@@ -1078,10 +1088,13 @@ static void release(Plan& P, cudaStream_t st) {
 // grids 2..10 with their kernel variants, finest grid) and their device copies.
 struct WorkSet {
   std::vector<ReqDev> rds;
+  // items of each kind (1 grid 1, 2..10 grids, 11 finest), class 0 first then class 1:
+  // kind k's class-c items are first[k][c] .. first[k][c + 1] - 1
   std::vector<G1Item> gi;
   std::vector<CoarseItem> ci[kNGrid + 1];  // grids 2..10
   std::vector<FineItem> fi;
-  int variant[kNGrid + 2] = {0};             // kernel variant per grid 2..10 and the finest grid
+  size_t first[kNGrid + 2][kNClasses + 1] = {};
+  int tune[kNClasses][kNGrid + 2] = {};    // per class: [1] grid-1 split, [2..10] variants, [11] finest
   bool surr = false;                       // some request uses the surrogate
   bool wide = false;                       // the requests use the 5-point partition
   bool surr_grid[kNGrid + 2] = {false};    // surrogate-capable kernels for grid 1..10, 11 finest
@@ -1107,24 +1120,41 @@ static void free_work(WorkSet& W, cudaStream_t st) {
   W.buf = nullptr;
 }
 
-// Build the work lists of plans with kernel variant variant[g] for grid g (NULL: the
-// defaults), allocate their device copies (plus count buffers when count) and upload.
-static int build_work(std::vector<Plan>& plans, const int* variant, bool count, WorkSet& W,
+// Build the work lists of plans with the kernel choices tune[class] (NULL: the defaults
+// for every class: grid-1 split kG1Split), allocate their device copies (plus count
+// buffers when count) and upload.
+static int build_work(std::vector<Plan>& plans, const int (*tune)[kNGrid + 2], bool count, WorkSet& W,
                       cudaStream_t st) {
-  for (auto& P : plans) W.rds.push_back(P.rd);
+  for (int c = 0; c < kNClasses; ++c)
+    for (int k = 1; k <= kNGrid + 1; ++k)
+      W.tune[c][k] = tune ? tune[c][k] : (k == 1 ? kG1Split : default_variant(k));
+  for (auto& P : plans) {
+    W.rds.push_back(P.rd);
+    W.rds.back().g1_split = W.tune[P.cls][1];
+  }
   for (auto& R : W.rds) W.surr = W.surr || R.mlp != nullptr;
   W.wide = !W.rds.empty() && W.rds[0].wide != 0;
   for (auto& R : W.rds)
     if ((R.wide != 0) != W.wide)
       return fail(MARFA_E_INVAL, "the requests of one call or plan must share one stencil");
   for (int g = 1; g <= kNGrid + 1; ++g) W.surr_grid[g] = W.surr;
-  for (auto& P : plans) W.gi.insert(W.gi.end(), P.g1.begin(), P.g1.end());
-  for (int g = 2; g <= kNGrid; ++g) {
-    W.variant[g] = variant ? variant[g] : default_variant(g);
-    for (auto& P : plans) coarse_items(P, g, W.variant[g], W.ci[g]);
+  for (int c = 0; c < kNClasses; ++c) {
+    W.first[1][c] = W.gi.size();
+    for (int g = 2; g <= kNGrid; ++g) W.first[g][c] = W.ci[g].size();
+    W.first[kNGrid + 1][c] = W.fi.size();
+    for (auto& P : plans) {
+      if (P.cls != c) continue;
+      const ReqDev& R = P.rd;
+      for (int l = 0; l < P.n_levels; ++l)
+        for (int64_t m0 = R.m_first[1]; m0 <= R.m_first[1] + R.npan[1]; m0 += kG1Pairs)
+          for (int part = 0; part < W.tune[c][1]; ++part) W.gi.push_back(G1Item{P.req_idx, l, m0, part, 0});
+      for (int g = 2; g <= kNGrid; ++g) coarse_items(P, g, W.tune[c][g], W.ci[g]);
+      W.fi.insert(W.fi.end(), P.fine.begin(), P.fine.end());
+    }
   }
-  W.variant[kFineKind] = variant ? variant[kFineKind] : default_variant(kFineKind);
-  for (auto& P : plans) W.fi.insert(W.fi.end(), P.fine.begin(), P.fine.end());
+  W.first[1][kNClasses] = W.gi.size();
+  for (int g = 2; g <= kNGrid; ++g) W.first[g][kNClasses] = W.ci[g].size();
+  W.first[kNGrid + 1][kNClasses] = W.fi.size();
   W.prep_first.push_back(0);
   for (auto& P : plans) {
     W.prep.push_back(P.prep);
@@ -1184,37 +1214,63 @@ static int build_work(std::vector<Plan>& plans, const int* variant, bool count, 
   return MARFA_OK;
 }
 
-// Grid g of a work set with kernel variant v.
-static void launch_grid(const WorkSet& W, int g, cudaStream_t st) {
-  const int n = (int)W.ci[g].size();
-  bool mech = (W.variant[g] == 4 || W.variant[g] == 5) && !W.surr_grid[g] && !W.wide;
+// Grid g (2..10) of a work set, the items of class c, with that class's kernel variant.
+static void launch_grid(const WorkSet& W, int g, int c, cudaStream_t st) {
+  const size_t f0 = W.first[g][c];
+  const int n = (int)(W.first[g][c + 1] - f0);
+  if (n <= 0) return;
+  const int v = W.tune[c][g];
+  const CoarseItem* items = W.dci[g] + f0;
+  int64_t* counts = W.dcc[g] ? W.dcc[g] + f0 * kCountFields : nullptr;
+  bool mech = (v == 4 || v == 5) && !W.surr_grid[g] && !W.wide;
   for (const auto& R : W.rds) mech = mech && ((R.mech >> g) & 1);
   if (mech)
-    launch_coarse_mech(W.drd, W.dci[g], n, W.dcc[g], W.variant[g] == 5, st);
-  else if (W.variant[g] == 3 && !W.surr_grid[g])
-    launch_coarse_jobs(W.drd, W.dci[g], n, W.dcc[g], W.wide, st);
-  else if (W.variant[g] == 1 || W.variant[g] >= 3)
-    launch_coarse(W.drd, W.dci[g], n, W.dcc[g], W.surr_grid[g], W.wide, st);
+    launch_coarse_mech(W.drd, items, n, counts, v == 5, st);
+  else if (v == 3 && !W.surr_grid[g])
+    launch_coarse_jobs(W.drd, items, n, counts, W.wide, st);
+  else if (v == 1 || v >= 3)
+    launch_coarse(W.drd, items, n, counts, W.surr_grid[g], W.wide, st);
   else
-    launch_coarse_lm(W.drd, W.dci[g], n, W.dcc[g], W.surr_grid[g], W.variant[g] == 2 ? 16 : kLPairs, W.wide,
-                     st);
+    launch_coarse_lm(W.drd, items, n, counts, W.surr_grid[g], v == 2 ? 16 : kLPairs, W.wide, st);
+}
+static void launch_grid(const WorkSet& W, int g, cudaStream_t st) {
+  for (int c = 0; c < kNClasses; ++c) launch_grid(W, g, c, st);
 }
 
-// The finest grid + cascade of a work set with its kernel variant.
-static void launch_finest(const WorkSet& W, cudaStream_t st) {
-  const int n = (int)W.fi.size();
-  bool mech = W.variant[kFineKind] >= 2 && !W.wide;
+// The finest grid + cascade of a work set, the items of class c, with that class's variant.
+static void launch_finest(const WorkSet& W, int c, cudaStream_t st) {
+  const size_t f0 = W.first[kNGrid + 1][c];
+  const int n = (int)(W.first[kNGrid + 1][c + 1] - f0);
+  if (n <= 0) return;
+  const int v = W.tune[c][kFineKind];
+  const FineItem* items = W.dfi + f0;
+  int64_t* counts = W.dfc ? W.dfc + f0 * kCountFields : nullptr;
+  bool mech = v >= 2 && !W.wide;
   for (const auto& R : W.rds) mech = mech && ((R.mech >> (kNGrid + 1)) & 1);
-  if (W.variant[kFineKind] >= 1 && !W.surr_grid[kNGrid + 1])
-    launch_fine_jobs(W.drd, W.dfi, n, W.dfc, W.wide, mech ? W.variant[kFineKind] - 1 : 0, st);
+  if (v >= 1 && !W.surr_grid[kNGrid + 1])
+    launch_fine_jobs(W.drd, items, n, counts, W.wide, mech ? v - 1 : 0, st);
   else
-    launch_fine(W.drd, W.dfi, n, W.dfc, W.surr_grid[kNGrid + 1], W.wide, st);
+    launch_fine(W.drd, items, n, counts, W.surr_grid[kNGrid + 1], W.wide, st);
+}
+static void launch_finest(const WorkSet& W, cudaStream_t st) {
+  for (int c = 0; c < kNClasses; ++c) launch_finest(W, c, st);
+}
+
+// Grid 1 of a work set, the items of class c (their requests' g1_split parts).
+static void launch_grid1(const WorkSet& W, int c, cudaStream_t st) {
+  const size_t f0 = W.first[1][c];
+  const int n = (int)(W.first[1][c + 1] - f0);
+  if (n <= 0) return;
+  launch_g1(W.drd, W.dgi + f0, n, W.dgc ? W.dgc + f0 * kCountFields : nullptr, W.surr_grid[1], W.wide, st);
+}
+static void launch_grid1(const WorkSet& W, cudaStream_t st) {
+  for (int c = 0; c < kNClasses; ++c) launch_grid1(W, c, st);
 }
 
 // Every summation launch of a work set: grid 1, grids 2..10, finest grid + cascade.
 static int launch_work(const WorkSet& W, cudaStream_t st, bool timed) {
   cudaEvent_t ev = timed ? timing_begin(st) : nullptr;
-  launch_g1(W.drd, W.dgi, (int)W.gi.size(), W.dgc, W.surr_grid[1], W.wide, st);
+  launch_grid1(W, st);
   timing_end(ev, 1, st);
   cudaError_t e;
   if ((e = cudaGetLastError())) return fail(MARFA_E_CUDA, "grid-1 kernel: %s", cudaGetErrorString(e));
@@ -1345,7 +1401,9 @@ struct marfa_plan {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t ev[2 * kKinds] = {nullptr};
-  float tune_ms[kNGrid + 2][kNVariants] = {};
+  // per class: the autotuner's time per launch of each variant ([1]: of each grid-1
+  // split, kG1Splits order), -1 where not timed
+  float tune_ms[kNClasses][kNGrid + 2][kNVariants] = {};
   bool tuned = false;
   MlpWeights* mlp = nullptr;  // the plan's own copy of the surrogate (if any request uses it)
   bool serial = false;        // capture the coarse grids one after the other
@@ -1376,23 +1434,38 @@ extern "C" void marfa_plan_destroy(marfa_plan_t* X) {
   delete X;
 }
 
-// Time each kernel variant of grids 2..10 and of the finest grid on the plan's own work
-// (two timed launches after one warm-up each) and keep the fastest.
-static int plan_autotune(marfa_plan_t* X, cudaStream_t st, int* chosen) {
-  WorkSet A[kNVariants];
-  int all[kNVariants][kNGrid + 2];
-  for (int v = 0; v < kNVariants; ++v) {
-    for (int g = 0; g <= kNGrid; ++g) all[v][g] = v;
-    all[v][kFineKind] = v < kNFineVariants ? v : 0;
-  }
+// Time, for each size class present, each grid-1 split and each kernel variant of grids
+// 2..10 and of the finest grid on the class's own work (two timed launches after one
+// warm-up each) and keep the fastest: chosen[class][kind] as WorkSet::tune.
+static int plan_autotune(marfa_plan_t* X, cudaStream_t st, int (*chosen)[kNGrid + 2]) {
+  constexpr int NS = 4;  // grid-1 splits tried (kG1Splits)
+  WorkSet A[kNVariants], B[NS];
+  int all[kNClasses][kNGrid + 2];
+  bool present[kNClasses] = {false, false};
+  for (auto& P : X->plans) present[P.cls] = true;
   int r = MARFA_OK;
-  for (int v = 0; v < kNVariants && !r; ++v) r = build_work(X->plans, all[v], false, A[v], st);
+  for (int v = 0; v < kNVariants && !r; ++v) {
+    for (int c = 0; c < kNClasses; ++c) {
+      for (int g = 2; g <= kNGrid; ++g) all[c][g] = v;
+      all[c][1] = kG1Split;
+      all[c][kFineKind] = v < kNFineVariants ? v : 0;
+    }
+    r = build_work(X->plans, all, false, A[v], st);
+  }
+  for (int k = 0; k < NS && !r; ++k) {
+    for (int c = 0; c < kNClasses; ++c) {
+      for (int g = 2; g <= kNGrid + 1; ++g) all[c][g] = default_variant(g);
+      all[c][1] = kG1Splits[k];
+    }
+    r = build_work(X->plans, all, false, B[k], st);
+  }
   cudaEvent_t a = nullptr, b = nullptr;
   cudaError_t e = cudaSuccess;
   if (!r && ((e = cudaEventCreate(&a)) || (e = cudaEventCreate(&b))))
     r = fail(MARFA_E_CUDA, "autotune events: %s", cudaGetErrorString(e));
-  for (int g = 0; g <= kNGrid + 1; ++g)
-    for (int v = 0; v < kNVariants; ++v) X->tune_ms[g][v] = -1.0f;
+  for (int c = 0; c < kNClasses; ++c)
+    for (int g = 0; g <= kNGrid + 1; ++g)
+      for (int v = 0; v < kNVariants; ++v) X->tune_ms[c][g][v] = -1.0f;
   auto time3 = [&](const std::function<void()>& launch, float* out) {
     launch();
     cudaEventRecord(a, st);
@@ -1405,24 +1478,33 @@ static int plan_autotune(marfa_plan_t* X, cudaStream_t st, int* chosen) {
     *out = 0.5f * ms;
     return MARFA_OK;
   };
-  for (int g = 2; g <= kNGrid && !r; ++g) {
-    for (int v = 0; v < kNVariants && !r; ++v) r = time3([&] { launch_grid(A[v], g, st); }, &X->tune_ms[g][v]);
+  auto best_of = [](const float* t, int n) {
     int best = 0;
-    for (int v = 1; v < kNVariants; ++v)
-      if (X->tune_ms[g][v] < X->tune_ms[g][best]) best = v;
-    chosen[g] = best;
-  }
-  // the finest grid reads the coarse grids' slots (already filled by the runs above)
-  for (int v = 0; v < kNFineVariants && !r; ++v) r = time3([&] { launch_finest(A[v], st); }, &X->tune_ms[kFineKind][v]);
-  if (!r) {
-    int best = 0;
-    for (int v = 1; v < kNFineVariants; ++v)
-      if (X->tune_ms[kFineKind][v] < X->tune_ms[kFineKind][best]) best = v;
-    chosen[kFineKind] = best;
+    for (int v = 1; v < n; ++v)
+      if (t[v] < t[best]) best = v;
+    return best;
+  };
+  for (int c = 0; c < kNClasses && !r; ++c) {
+    if (!present[c]) {
+      for (int k = 1; k <= kNGrid + 1; ++k) chosen[c][k] = k == 1 ? kG1Split : default_variant(k);
+      continue;
+    }
+    for (int k = 0; k < NS && !r; ++k) r = time3([&] { launch_grid1(B[k], c, st); }, &X->tune_ms[c][1][k]);
+    if (!r) chosen[c][1] = kG1Splits[best_of(X->tune_ms[c][1], NS)];
+    for (int g = 2; g <= kNGrid && !r; ++g) {
+      for (int v = 0; v < kNVariants && !r; ++v)
+        r = time3([&] { launch_grid(A[v], g, c, st); }, &X->tune_ms[c][g][v]);
+      if (!r) chosen[c][g] = best_of(X->tune_ms[c][g], kNVariants);
+    }
+    // the finest grid reads the coarse grids' slots (already filled by the runs above)
+    for (int v = 0; v < kNFineVariants && !r; ++v)
+      r = time3([&] { launch_finest(A[v], c, st); }, &X->tune_ms[c][kFineKind][v]);
+    if (!r) chosen[c][kFineKind] = best_of(X->tune_ms[c][kFineKind], kNFineVariants);
   }
   if (a) cudaEventDestroy(a);
   if (b) cudaEventDestroy(b);
   for (int v = 0; v < kNVariants; ++v) free_work(A[v], st);
+  for (int k = 0; k < NS; ++k) free_work(B[k], st);
   X->tuned = !r;
   return r;
 }
@@ -1447,7 +1529,7 @@ static int plan_launch_all(marfa_plan_t* X, cudaStream_t st, bool capture) {
     for (int i = 0; i < kSide; ++i) cudaStreamWaitEvent(X->side[i], X->fork, 0);
   }
   rec(2, br[1]);
-  launch_g1(W.drd, W.dgi, (int)W.gi.size(), nullptr, W.surr_grid[1], W.wide, br[1]);
+  launch_grid1(W, br[1]);
   rec(3, br[1]);
   for (int g = kNGrid; g >= 2; --g) {  // the finer grids carry more work: start them first
     rec(2 * g, br[g]);
@@ -1502,8 +1584,9 @@ extern "C" int marfa_plan_create(int32_t n_req, const marfa_lines_t* const* line
     for (auto& P : X->plans)
       if (P.rd.mlp) P.rd.mlp = X->mlp;
   }
-  int chosen[kNGrid + 2];
-  for (int g = 0; g <= kNGrid + 1; ++g) chosen[g] = default_variant(g);
+  int chosen[kNClasses][kNGrid + 2];
+  for (int c = 0; c < kNClasses; ++c)
+    for (int g = 0; g <= kNGrid + 1; ++g) chosen[c][g] = g == 1 ? kG1Split : default_variant(g);
   if (!r && autotune) {
     for (auto& P : X->plans) launch_prep(P, st, false);
     r = plan_autotune(X, st, chosen);
@@ -1577,12 +1660,13 @@ extern "C" int marfa_plan_execute(marfa_plan_t* X, void* stream) {
 
 extern "C" int marfa_plan_info(const marfa_plan_t* X, int32_t* variant, float* tune_ms, double* kernel_ms) {
   if (!X) return fail(MARFA_E_INVAL, "plan is NULL");
+  const int c = X->plans.empty() ? 0 : X->plans[0].cls;  // the class of request 0
   if (variant)
-    for (int g = 1; g <= kFineKind; ++g) variant[g - 1] = g == 1 ? -1 : X->W.variant[g];
+    for (int g = 1; g <= kFineKind; ++g) variant[g - 1] = g == 1 ? -1 : X->W.tune[c][g];
   if (tune_ms)
     for (int g = 1; g <= kFineKind; ++g)
       for (int v = 0; v < kNVariants; ++v)
-        tune_ms[kNVariants * (g - 1) + v] = X->tuned ? X->tune_ms[g][v] : -1.0f;
+        tune_ms[kNVariants * (g - 1) + v] = (X->tuned && g > 1) ? X->tune_ms[c][g][v] : -1.0f;
   if (kernel_ms) {
     for (int k = 0; k < kKinds; ++k) {
       float ms = 0;
@@ -1594,6 +1678,24 @@ extern "C" int marfa_plan_info(const marfa_plan_t* X, int32_t* variant, float* t
       }
       kernel_ms[k] = ms;
     }
+  }
+  return MARFA_OK;
+}
+
+extern "C" int marfa_plan_classes(const marfa_plan_t* X, int32_t* req_class, int32_t* choice, float* tune_ms) {
+  if (!X) return fail(MARFA_E_INVAL, "plan is NULL");
+  bool present[kNClasses] = {false, false};
+  for (size_t q = 0; q < X->plans.size(); ++q) {
+    present[X->plans[q].cls] = true;
+    if (req_class) req_class[q] = X->plans[q].cls;
+  }
+  for (int c = 0; c < kNClasses; ++c) {
+    if (choice)
+      for (int g = 1; g <= kFineKind; ++g) choice[c * kFineKind + g - 1] = present[c] ? X->W.tune[c][g] : -1;
+    if (tune_ms)
+      for (int g = 1; g <= kFineKind; ++g)
+        for (int v = 0; v < kNVariants; ++v)
+          tune_ms[(c * kFineKind + g - 1) * kNVariants + v] = (X->tuned && present[c]) ? X->tune_ms[c][g][v] : -1.0f;
   }
   return MARFA_OK;
 }

@@ -93,7 +93,7 @@ struct ReqDev {
   int64_t m_first[kNGrid + 1];  // per grid 1..10: first panel of the window
   int64_t npan[kNGrid + 1];     // per grid: panels of the window
   int64_t slot_off[kNGrid + 1]; // per grid: offset of its L|M|R arrays in a level's slots
-                                // (grid 1: kG1Split copies, [part][L|M|R][npan])
+                                // (grid 1: room for kG1Split copies, [part][L|M|R][npan])
   int64_t slots_per_level;
   float* slots;             // [n_levels][slots_per_level]
   int64_t cut_fx;           // cut-off, fixed point
@@ -102,6 +102,7 @@ struct ReqDev {
   int32_t shape;
   int32_t chi_req;          // request asks for the chi-factor
   int32_t mech;             // bit g (2..10): mech_ok on grid g; bit 11: mech_fine_ok (3-point only)
+  int32_t g1_split;         // CTAs sharing a grid-1 tile's candidate lines (1..kG1Split)
   const MlpWeights* mlp;    // surrogate weights and guard, null for the plain path
   float out_scale;          // inverse internal scale
   float* out;               // [n_levels][npts]
@@ -121,7 +122,7 @@ struct FineItem {
 };
 
 // One CTA of the G1 kernel: kG1Pairs consecutive node pairs of grid 1 of one level, and
-// part `part` of kG1Split equal shares of the tile's candidate lines.
+// part `part` of the request's g1_split equal shares of the tile's candidate lines.
 struct G1Item {
   int32_t req, level;
   int64_t m0;  // first pair
@@ -129,8 +130,9 @@ struct G1Item {
 };
 
 constexpr int kG1Pairs = 32;         // node pairs per G1 tile (one per lane)
-constexpr int kG1Split = 6;          // CTAs sharing one G1 tile's candidate lines; each
-                                     // writes its own copy of the tile's slots
+constexpr int kG1Split = 6;          // at most this many CTAs share one G1 tile's candidate
+                                     // lines (ReqDev::g1_split, tuned); each writes its own
+                                     // copy of the tile's slots
 constexpr int kG1Warps = 8;          // warps of a G1 CTA, each takes every 8th staged line
 constexpr int kG1Batch = 512;        // lines staged in shared memory at a time
 constexpr int kLPairs = 32;          // node pairs per CTA of the line-major kernel (or 16)

@@ -610,7 +610,7 @@ __global__ void __launch_bounds__(kG1Warps * 32)
   }
   // this CTA's share of the candidate lines
   const int64_t c_lo = bd.n ? bd.lo[0] : 0, c_n = bd.n ? bd.hi[0] - c_lo : 0;
-  const int64_t i_lo = c_lo + c_n * it.part / kG1Split, i_hi = c_lo + c_n * (it.part + 1) / kG1Split;
+  const int64_t i_lo = c_lo + c_n * it.part / R.g1_split, i_hi = c_lo + c_n * (it.part + 1) / R.g1_split;
   const int64_t off = (int64_t)lev * R.n_lines;
   const bool voigt = R.shape == kShapeVoigt;
   const bool physical = R.shape < kShapeConst;
@@ -1963,9 +1963,8 @@ __device__ __forceinline__ void fine_cascade_store(const ReqDev& R, const FineIt
         const int64_t i0 = 2 * M4 - R.m_first[g];
         float v0 = __ldg(gp + i0), v1 = __ldg(gp + np + i0), v2 = __ldg(gp + 2 * np + i0);
         float v3 = __ldg(gp + np + i0 + 1), v4 = __ldg(gp + 2 * np + i0 + 1);
-        if (g == 1) {  // the kG1Split partial copies of grid 1, summed in part order
-#pragma unroll
-          for (int part = 1; part < kG1Split; ++part) {
+        if (g == 1) {  // the g1_split partial copies of grid 1, summed in part order
+          for (int part = 1; part < R.g1_split; ++part) {
             const float* gq = gp + 3 * np * part;
             v0 += __ldg(gq + i0);
             v1 += __ldg(gq + np + i0);
@@ -1993,9 +1992,8 @@ __device__ __forceinline__ void fine_cascade_store(const ReqDev& R, const FineIt
       const int64_t m = k0 >> sh;
       const int64_t idx = m - R.m_first[g];
       float vL = __ldg(gp + idx), vM = __ldg(gp + np + idx), vR = __ldg(gp + 2 * np + idx);
-      if (g == 1) {  // the kG1Split partial copies of grid 1, summed in part order
-#pragma unroll
-        for (int part = 1; part < kG1Split; ++part) {
+      if (g == 1) {  // the g1_split partial copies of grid 1, summed in part order
+        for (int part = 1; part < R.g1_split; ++part) {
           const float* gq = gp + 3 * np * part;
           vL += __ldg(gq + idx);
           vM += __ldg(gq + np + idx);

@@ -48,7 +48,8 @@ EXPORTS = ["marfa_prepare_lines", "marfa_free_lines", "marfa_num_points", "marfa
            "marfa_diag_absorption_counted_surrogate", "marfa_plan_create", "marfa_plan_execute",
            "marfa_plan_info", "marfa_plan_destroy", "marfa_diag_absorption_counts", "marfa_read_par",
            "marfa_diag_pipe_rate", "marfa_diag_line_order", "marfa_diag_shape", "marfa_diag_variants",
-           "marfa_diag_fail_alloc", "marfa_diag_device_memory", "marfa_diag_check"]
+           "marfa_diag_fail_alloc", "marfa_diag_device_memory", "marfa_diag_check",
+           "marfa_plan_classes"]
 
 MLP_PARAMS = 8577
 MLP_MAX_BATCH = 65536
@@ -102,6 +103,7 @@ def load(path: str | None = None):
         "marfa_plan_execute": (C.c_int, [vp, vp]),
         "marfa_plan_info": (C.c_int, [vp, vp, vp, vp]),
         "marfa_diag_variants": (C.c_int, [vp, vp]),
+        "marfa_plan_classes": (C.c_int, [vp, vp, vp, vp]),
         "marfa_diag_fail_alloc": (C.c_int, [C.c_int64, vp]),
         "marfa_diag_device_memory": (C.c_int, [vp, vp]),
         "marfa_diag_check": (C.c_int, [C.c_int32, vp]),
@@ -265,6 +267,18 @@ def marfa_plan_info(plan: Plan, kernel_ms: bool = False):
     k = np.empty(12, dtype=np.float64) if kernel_ms else None
     _check(load().marfa_plan_info(plan.handle, _ptr(v), _ptr(t), _ptr(k)))
     return v, t, k
+
+
+PLAN_CLASSES = 2
+
+
+def marfa_plan_classes(plan: Plan, n_req: int):
+    """(req_class[n_req], choice[2, 11] (column 0: the grid-1 split), tune_ms[2, 11, 6])."""
+    rc = np.empty(n_req, dtype=np.int32)
+    ch = np.empty((PLAN_CLASSES, PLAN_KINDS), dtype=np.int32)
+    t = np.empty((PLAN_CLASSES, PLAN_KINDS, PLAN_VARIANTS), dtype=np.float32)
+    _check(load().marfa_plan_classes(plan.handle, _ptr(rc), _ptr(ch), _ptr(t)))
+    return rc, ch, t
 
 
 def marfa_diag_fail_alloc(nth: int) -> int:

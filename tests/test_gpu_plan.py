@@ -259,3 +259,36 @@ def test_pipe_rate_probes(M):
     for k in ("ex2", "rcp", "cos"):
         r = M.marfa_diag_pipe_rate(k)
         assert 0.0 < r < fma / 2
+
+
+def test_size_classes_tuned_apart(M):
+    """A batch of narrow (<= 16 cm^-1) and wide windows: each request gets its size class,
+    each class its own grid-1 split and kernel variants (the fastest of the autotuner's
+    timings on that class's work), and the plan stays within FP32 rounding of the
+    untuned batch and within 1e-4 of the oracle."""
+    import torch
+    wls = [tiny_workload(44, 300, 2000.0, 2003.0, 25.0, T=(400.0, 200.0), p=(5.0, 1e-3), chi="tonkov",
+                         chi_species=1),
+           tiny_workload(45, 400, 3000.0, 3020.5, 25.0, T=(296.0,), p=(0.1,)),
+           tiny_workload(46, 200, 1200.0, 1201.0, 10.0, T=(250.0,), p=(0.05,))]
+    plan, ref, outs = _batch_and_plan(M, wls, autotune=True)
+    M.marfa_plan_execute(plan)
+    torch.cuda.synchronize()
+    rc, ch, t = M.marfa_plan_classes(plan, len(wls))
+    assert list(rc) == [0, 1, 0]
+    splits = [1, 2, 3, 6]
+    for c in (0, 1):
+        assert ch[c, 0] in splits
+        assert ch[c, 0] == splits[int(np.argmin(t[c, 0, :4]))]
+        assert np.all(t[c, 0, :4] > 0) and np.all(t[c, 0, 4:] == -1)
+        for g in range(1, 10):
+            assert 0 <= ch[c, g] <= 5 and t[c, g, ch[c, g]] <= t[c, g].min()
+        assert 0 <= ch[c, 10] <= 3 and t[c, 10, ch[c, 10]] <= t[c, 10, :4].min()
+    v, _, _ = M.marfa_plan_info(plan)
+    assert list(v[1:]) == list(ch[rc[0], 1:])  # plan_info reports request 0's class
+    for q, w in enumerate(wls):
+        got = outs[q].cpu().numpy()
+        for lev in range(w.n_levels):
+            check(got[lev], ref[q][lev], np.abs(got[lev]).max(), f"request {q} level {lev} vs batch")
+            check(got[lev], O.eleven_grid(w, lev), np.abs(got[lev]).max(), f"request {q} level {lev}")
+    M.marfa_plan_destroy(plan)
