@@ -45,6 +45,8 @@ enum {
   MARFA_SHAPE_LORENTZ = 0,    /* Eq. (4)                                      */
   MARFA_SHAPE_VOIGT = 1,      /* Eqs. (7)-(8), the default of the paper        */
   MARFA_SHAPE_DOPPLER = 2,    /* Eq. (5)                                      */
+  MARFA_SHAPE_USER = 4,       /* the user's shape of marfa_shape_user_set (Sec. 2.2: the
+                                 shape is whatever function the user points it to) */
   MARFA_SHAPE_VOIGT_PAPER = 3, /* Eqs. (7)-(8) with K as Appendix C computes it:
                                   the Lorentz wing for |x| > 15, the region-4
                                   asymptote for y < 0.02, 1 < |x| < 5.5,
@@ -222,6 +224,20 @@ int marfa_plan_execute(marfa_plan_t* plan, void* stream);
 #define MARFA_PLAN_VARIANTS 6
 /* These report the kernel choice of request 0's size class (marfa_plan_classes). */
 int marfa_plan_info(const marfa_plan_t* plan, int32_t* variant, float* tune_ms, double* kernel_ms);
+
+/*
+ * A user-defined line shape (Sec. 2.2: the code calls the shape through a pointer the
+ * user may redirect to any function; here a table the library interpolates). g holds n
+ * samples (2..4096, finite, >= 0, host array) of a symmetric g(x) at x = k x_max /
+ * (n - 1), k = 0..n-1; the shape is g linear between samples and g(x_max) (x_max/|x|)^2
+ * beyond x_max, on the Lorentz scaling: x = (nu - nu~0) / gamma_L and
+ * f = S / (pi gamma_L) g(x), so that g = 1/(1 + x^2) gives Eq. (4); its half width for
+ * the grid choice (g*) is gamma_L. Requests with shape MARFA_SHAPE_USER take it (on the
+ * current device; every device needs its own call; a later call replaces the table for
+ * later calls and plans). The chi-factor and the cut-off apply as for every shape.
+ * Errors: MARFA_E_INVAL (sizes, x_max outside (0, 1e6], bad samples), MARFA_E_CUDA.
+ */
+int marfa_shape_user_set(const float* g, int32_t n, double x_max);
 
 /* Size classes of a plan: the autotuner treats narrow requests (windows of at most
  * 16 cm^-1, 32769 points) and wider ones apart, since their tiles and candidate counts

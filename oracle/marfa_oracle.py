@@ -141,7 +141,7 @@ def shape_hwhm(shape: str, gamma_L, alpha_D):
     Lorentz: gamma_L; Gauss: alpha_D; test shapes use the Voigt width so that they
     exercise the same partition as the Voigt profile.
     """
-    if shape == "lorentz":
+    if shape in ("lorentz", "user"):
         return np.asarray(gamma_L, dtype=np.float64)
     if shape == "doppler":
         return np.asarray(alpha_D, dtype=np.float64)
@@ -226,11 +226,30 @@ QUAD_COEF = (1.0, 0.25, 0.0625)  # test shape f = amp (1 + d/4 + d^2/16), d in c
 QUART_COEF = (1.0, 0.25, 0.0625, 0.015625, 0.00390625)  # f = amp sum_j (d/4)^j, j <= 4
 
 
-def profile(shape: str, d_fx, amp, gamma_L, alpha_D, chi_on):
+def user_g(x, table, x_max):
+    """The user-defined shape of Sec. 2.2's redirectable shape function, as the library
+    defines it: g(|x|) linear between the samples table[k] at x = k x_max / (n - 1), and
+    g(x_max) (x_max / |x|)^2 beyond x_max."""
+    ax = np.abs(np.asarray(x, dtype=np.float64))
+    t = np.asarray(table, dtype=np.float64)
+    xs = np.linspace(0.0, float(x_max), len(t))
+    inside = np.interp(np.minimum(ax, x_max), xs, t)
+    tail = t[-1] * (float(x_max) / np.maximum(ax, float(x_max))) ** 2
+    return np.where(ax < x_max, inside, tail)
+
+
+def user_of(wl):
+    """The (table, x_max) of a workload's user-defined shape, or None."""
+    t = getattr(wl, "user_shape", None)
+    return None if t is None else (t, wl.user_xmax)
+
+
+def profile(shape: str, d_fx, amp, gamma_L, alpha_D, chi_on, user=None):
     """amp * f(d) * chi(|d|) at offsets d (fixed point) from the shifted centre.
 
     f: 'lorentz' Eq. (4); 'doppler' Eq. (5); 'voigt' Eqs. (7)-(8) ('voigt_paper': with
-    K computed as Appendix C does, voigt_K_paper); test shapes
+    K computed as Appendix C does, voigt_K_paper); 'user' the user's tabulated g on the
+    Lorentz scaling, f = g(d / gamma_L) / (pi gamma_L) (user = (table, x_max)); test shapes
     'const' (f = 1, no amplitude, no chi: k counts lines), 'quad'
     (f = 1 + d/4 + d^2/16, no chi) and 'quart' (f = sum_{j<=4} (d/4)^j, no chi).
     """
@@ -245,6 +264,8 @@ def profile(shape: str, d_fx, amp, gamma_L, alpha_D, chi_on):
         return amp * (a0 + d * (a1 + d * (a2 + d * (a3 + d * a4))))
     if shape == "lorentz":
         f = gamma_L / (np.pi * (gamma_L * gamma_L + d * d))
+    elif shape == "user":
+        f = user_g(d / gamma_L, user[0], user[1]) / (np.pi * gamma_L)
     elif shape == "doppler":
         f = math.sqrt(LN2 / np.pi) / alpha_D * np.exp(-d * d * LN2 / (alpha_D * alpha_D))
     elif shape in ("voigt", "voigt_paper"):
@@ -283,7 +304,7 @@ def brute_force(wl, lev: int, k_nodes=None) -> np.ndarray:
         if len(sel) == 0:
             continue
         v = profile(wl.shape, x - c[sel], P["amp"][sel], P["gamma_L"][sel], P["alpha_D"][sel],
-                    P["chi_on"][sel])
+                    P["chi_on"][sel], user=user_of(wl))
         out[i] = math.fsum(v)
     return out
 
@@ -418,7 +439,7 @@ def eleven_grid(wl, lev: int, stats: dict | None = None, dump: dict | None = Non
 
     def f_at(sel, Xv):
         return profile(wl.shape, Xv - c[sel], P["amp"][sel], P["gamma_L"][sel], P["alpha_D"][sel],
-                       chi_on[sel])
+                       chi_on[sel], user=user_of(wl))
 
     for g in range(1, NGRID + 1):
         s = panel_shift(g) + (1 if wide else 0)
@@ -539,14 +560,14 @@ def eleven_grid_at(wl, lev: int, k_nodes, line_block: int = 1 << 16) -> np.ndarr
                     w = lagrange5(t) if wide else lagrange3(t)
                     sj = sel[j]
                     fv = [profile(wl.shape, a + q * h - c[j], P["amp"][sj], P["gamma_L"][sj],
-                                  P["alpha_D"][sj], ch[j]) for q in range(npn)]
+                                  P["alpha_D"][sj], ch[j], user=user_of(wl)) for q in range(npn)]
                     parts.append(sum(fv[q] * w[q] for q in range(npn)))
                     done |= acc
             rest = np.nonzero(~done)[0]
             if len(rest):
                 sj = sel[rest]
                 parts.append(profile(wl.shape, X - c[rest], P["amp"][sj], P["gamma_L"][sj],
-                                     P["alpha_D"][sj], ch[rest]))
+                                     P["alpha_D"][sj], ch[rest], user=user_of(wl)))
         res[ii] = math.fsum(np.concatenate(parts)) if parts else 0.0
     return res
 

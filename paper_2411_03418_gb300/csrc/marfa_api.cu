@@ -802,6 +802,33 @@ static int surrogate_for_current_device(const MlpWeights** out) {
   return MARFA_OK;
 }
 
+// ------------------------------------------------------------------ user-defined shape
+// The devices on which marfa_shape_user_set has put a table.
+static std::mutex g_user_mu;
+static uint64_t g_user_devs = 0;
+static bool user_shape_set_here() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+  std::lock_guard<std::mutex> lk(g_user_mu);
+  return (g_user_devs >> dev) & 1;
+}
+
+extern "C" int marfa_shape_user_set(const float* g, int32_t n, double x_max) {
+  if (!g || n < 2 || n > kUserShapeMax) return fail(MARFA_E_INVAL, "need 2..%d samples", kUserShapeMax);
+  if (!std::isfinite(x_max) || !(x_max > 0) || x_max > 1e6) return fail(MARFA_E_INVAL, "x_max must be in (0, 1e6]");
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(g[i]) || g[i] < 0) return fail(MARFA_E_INVAL, "sample %d is negative or not finite", i);
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(MARFA_E_INVAL, "device %d out of range", dev);
+  const int e = set_user_shape(g, n, (float)x_max);
+  if (e) return fail(MARFA_E_CUDA, "user shape upload: %s", cudaGetErrorString((cudaError_t)e));
+  CK(cudaDeviceSynchronize());
+  std::lock_guard<std::mutex> lk(g_user_mu);
+  g_user_devs |= uint64_t(1) << dev;
+  return MARFA_OK;
+}
+
 static int validate_request(const marfa_request_t* rq, int64_t* npts) {
   if (!rq) return fail(MARFA_E_INVAL, "request is NULL");
   const int64_t np = marfa_num_points(rq->nu_lo, rq->nu_hi);
@@ -813,9 +840,11 @@ static int validate_request(const marfa_request_t* rq, int64_t* npts) {
     return fail(MARFA_E_INVAL, "cut-off must be in (0, 1000] cm^-1");
   const int s = rq->shape;
   if (!(s == MARFA_SHAPE_LORENTZ || s == MARFA_SHAPE_VOIGT || s == MARFA_SHAPE_DOPPLER ||
-        s == MARFA_SHAPE_VOIGT_PAPER || s == MARFA_SHAPE_TEST_CONST || s == MARFA_SHAPE_TEST_QUAD ||
-        s == MARFA_SHAPE_TEST_QUART))
+        s == MARFA_SHAPE_VOIGT_PAPER || s == MARFA_SHAPE_USER || s == MARFA_SHAPE_TEST_CONST ||
+        s == MARFA_SHAPE_TEST_QUAD || s == MARFA_SHAPE_TEST_QUART))
     return fail(MARFA_E_INVAL, "unknown shape %d", s);
+  if (s == MARFA_SHAPE_USER && !user_shape_set_here())
+    return fail(MARFA_E_INVAL, "shape USER requested but no user shape is set on this device (marfa_shape_user_set)");
   if (rq->chi != MARFA_CHI_NONE && rq->chi != MARFA_CHI_TONKOV)
     return fail(MARFA_E_INVAL, "unknown chi %d", rq->chi);
   if (rq->units < MARFA_UNITS_SIGMA || rq->units > MARFA_UNITS_K_KM1)
@@ -1994,9 +2023,11 @@ extern "C" int marfa_diag_pipe_rate(int32_t pipe, double* ops_per_s) {
 
 extern "C" int marfa_diag_shape(int32_t shape, const float* x, const float* y, float* out, int64_t n) {
   if (!(shape == MARFA_SHAPE_LORENTZ || shape == MARFA_SHAPE_VOIGT || shape == MARFA_SHAPE_DOPPLER ||
-        shape == MARFA_SHAPE_VOIGT_PAPER || shape == MARFA_SHAPE_TEST_CONST || shape == MARFA_SHAPE_TEST_QUAD ||
-        shape == MARFA_SHAPE_TEST_QUART))
+        shape == MARFA_SHAPE_VOIGT_PAPER || shape == MARFA_SHAPE_USER || shape == MARFA_SHAPE_TEST_CONST ||
+        shape == MARFA_SHAPE_TEST_QUAD || shape == MARFA_SHAPE_TEST_QUART))
     return fail(MARFA_E_INVAL, "unknown shape %d", shape);
+  if (shape == MARFA_SHAPE_USER && !user_shape_set_here())
+    return fail(MARFA_E_INVAL, "no user shape is set on this device");
   if (n < 0 || (n > 0 && (!x || !y || !out))) return fail(MARFA_E_INVAL, "bad arguments");
   if (n == 0) return MARFA_OK;
   float* dx;

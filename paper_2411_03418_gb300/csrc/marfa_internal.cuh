@@ -22,8 +22,10 @@ __host__ __device__ constexpr int64_t step_fx(int g) { return int64_t(1) << (kFi
 __host__ __device__ __forceinline__ int64_t fl_sh(int64_t a, int s) { return a >> s; }
 __host__ __device__ __forceinline__ int64_t cl_sh(int64_t a, int s) { return -((-a) >> s); }
 
-constexpr int kShapeLorentz = 0, kShapeVoigt = 1, kShapeDoppler = 2, kShapeVoigtPaper = 3,
+constexpr int kShapeLorentz = 0, kShapeVoigt = 1, kShapeDoppler = 2, kShapeVoigtPaper = 3, kShapeUser = 4,
               kShapeConst = 100, kShapeQuad = 101, kShapeQuart = 102;
+constexpr int kNPhysShapes = 5;    // physical shapes 0..4: the entries of the device shape table
+constexpr int kUserShapeMax = 4096;  // samples of a user-defined shape
 
 // Per level (host-computed in double precision).
 struct LevelDev {
@@ -181,6 +183,9 @@ constexpr bool kDebugBuild =
 #endif
 // launches the diagnostic probe: a guarded store at index i of a 32-entry array
 void launch_diag_check(int i, cudaStream_t st);
+// the user-defined shape of the current device: g(x) at n samples over [0, x_max]
+// (marfa_kernels.cu); MARFA_OK or a CUDA error code
+int set_user_shape(const float* g, int n, float x_max);
 
 // kernels (marfa_kernels.cu). With surr set, the surrogate-capable variants run (requests
 // with mlp != null use the surrogate under its guard). counts, when given, selects the

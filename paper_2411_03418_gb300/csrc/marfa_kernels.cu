@@ -302,16 +302,60 @@ struct NodeX {
   }
 };
 
+// ------------------------------------------------------------------ line shapes
+// The paper lets a user redirect the line shape to any function (its procedure-pointer
+// hook, Sec. 2.2). Here the physical shapes are entries of a device function table
+// indexed by the request's shape code, each g(x, y) in the shape's own scaled variable
+// x (the level preparation sets the amplitude and the x scale per shape): Lorentz
+// 1/(1 + x^2), Voigt K(x, y), Doppler exp(-x^2), the paper's fast Voigt, and the user's
+// shape. The user's shape g(x) is given as n samples over [0, x_max] (symmetric in x),
+// linear between samples and g(x_max) (x_max / x)^2 beyond, on the Lorentz scaling
+// x = (nu - nu~0) / gamma_L with the Lorentz amplitude S / (pi gamma_L) (the Lorentz
+// itself is g = 1/(1 + x^2)). The Voigt kernels evaluate K inline; the table serves the
+// other shapes.
+__device__ float g_user_tab[kUserShapeMax];
+__device__ int g_user_n = 0;
+__device__ float g_user_xmax = 1.0f, g_user_scale = 1.0f;  // scale = (n - 1) / x_max
+
+static __device__ __noinline__ float shape_lorentz(float x, float) { return 1.0f / fmaf(x, x, 1.0f); }
+static __device__ __noinline__ float shape_voigt(float x, float y) { return voigt_K(x, y); }
+static __device__ __noinline__ float shape_doppler(float x, float) { return expf(-x * x); }
+static __device__ __noinline__ float shape_voigt_paper(float x, float y) { return voigt_K_paper(x, y); }
+static __device__ __noinline__ float shape_user(float x, float) {
+  const float ax = fabsf(x);
+  const int n = g_user_n;
+  if (ax >= g_user_xmax) {
+    const float r = g_user_xmax / ax;
+    return g_user_tab[n - 1] * r * r;
+  }
+  const float t = ax * g_user_scale;
+  const int i = min((int)t, n - 2);
+  const float f = t - (float)i;
+  return fmaf(f, g_user_tab[i + 1] - g_user_tab[i], g_user_tab[i]);
+}
+
+typedef float (*ShapeFn)(float, float);
+__device__ ShapeFn const g_shape_table[kNPhysShapes] = {shape_lorentz, shape_voigt, shape_doppler,
+                                                         shape_voigt_paper, shape_user};
+
 __device__ __forceinline__ float shape_f(int shape, float x, float y) {
+  if (shape < kNPhysShapes) return g_shape_table[shape](x, y);
   switch (shape) {
-    case kShapeVoigt: return voigt_K(x, y);
-    case kShapeVoigtPaper: return voigt_K_paper_call(x, y);
-    case kShapeLorentz: return 1.0f / fmaf(x, x, 1.0f);
-    case kShapeDoppler: return expf(-x * x);
     case kShapeConst: return 1.0f;
     case kShapeQuart: return fmaf(x, fmaf(x, fmaf(x, fmaf(x, 0.00390625f, 0.015625f), 0.0625f), 0.25f), 1.0f);
     default: return fmaf(x, fmaf(x, 0.0625f, 0.25f), 1.0f);  // kShapeQuad
   }
+}
+
+int set_user_shape(const float* g, int n, float x_max) {
+  const float scale = (float)(n - 1) / x_max;
+  cudaError_t e;
+  if ((e = cudaMemcpyToSymbol(g_user_tab, g, sizeof(float) * n)) ||
+      (e = cudaMemcpyToSymbol(g_user_n, &n, sizeof(int))) ||
+      (e = cudaMemcpyToSymbol(g_user_xmax, &x_max, sizeof(float))) ||
+      (e = cudaMemcpyToSymbol(g_user_scale, &scale, sizeof(float))))
+    return (int)e;
+  return 0;
 }
 
 // Per-CTA evaluation counts, kCountFields per block: all profile evaluations, those the
@@ -412,6 +456,7 @@ __device__ __forceinline__ void level_prep_pair(const PrepArgs& a, int64_t i, in
   const float kSqrtLn2 = 0.83255461115769776f, kSqrtLn2Pi = 0.46971863934982566f;
   switch (a.shape) {
     case kShapeLorentz:
+    case kShapeUser:  // the user's shape on the Lorentz scaling
       amp = S * 0.31830988618379067f / gL;
       sx = 1.0f / gL;
       W = gL;
@@ -449,7 +494,7 @@ __device__ __forceinline__ void level_prep_pair(const PrepArgs& a, int64_t i, in
                                             __dmul_rn((double)gs, LS.ps_d)));
     const double aD64 = __dmul_rn(__ddiv_rn(nu0, 2.99792458e8), LS.sqrtv);
     double W64;
-    if (a.shape == kShapeLorentz)
+    if (a.shape == kShapeLorentz || a.shape == kShapeUser)
       W64 = gL64;
     else if (a.shape == kShapeDoppler)
       W64 = aD64;

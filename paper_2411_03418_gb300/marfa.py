@@ -19,7 +19,8 @@ LINE_DTYPE = np.dtype([("nu0", "<f8"), ("S296", "<f4"), ("gamma_air", "<f4"), ("
 SPECIES_DTYPE = np.dtype([("mol_iso", "<i4"), ("chi_enabled", "<i4"), ("mass_amu", "<f8"), ("q_exp", "<f8")])
 LEVEL_DTYPE = np.dtype([("T_K", "<f8"), ("p_atm", "<f8")])
 
-SHAPES = {"lorentz": 0, "voigt": 1, "doppler": 2, "voigt_paper": 3, "const": 100, "quad": 101, "quart": 102}
+SHAPES = {"lorentz": 0, "voigt": 1, "doppler": 2, "voigt_paper": 3, "user": 4, "const": 100, "quad": 101,
+          "quart": 102}
 CHI = {"none": 0, "tonkov": 1}
 UNITS = {"sigma": 0, "k_cm1": 1, "k_km1": 2}
 ERRORS = {-1: "MARFA_E_INVAL", -2: "MARFA_E_NOMEM", -3: "MARFA_E_CUDA", -4: "MARFA_E_IO",
@@ -49,7 +50,7 @@ EXPORTS = ["marfa_prepare_lines", "marfa_free_lines", "marfa_num_points", "marfa
            "marfa_plan_info", "marfa_plan_destroy", "marfa_diag_absorption_counts", "marfa_read_par",
            "marfa_diag_pipe_rate", "marfa_diag_line_order", "marfa_diag_shape", "marfa_diag_variants",
            "marfa_diag_fail_alloc", "marfa_diag_device_memory", "marfa_diag_check",
-           "marfa_plan_classes"]
+           "marfa_plan_classes", "marfa_shape_user_set"]
 
 MLP_PARAMS = 8577
 MLP_MAX_BATCH = 65536
@@ -104,6 +105,7 @@ def load(path: str | None = None):
         "marfa_plan_info": (C.c_int, [vp, vp, vp, vp]),
         "marfa_diag_variants": (C.c_int, [vp, vp]),
         "marfa_plan_classes": (C.c_int, [vp, vp, vp, vp]),
+        "marfa_shape_user_set": (C.c_int, [vp, C.c_int32, C.c_double]),
         "marfa_diag_fail_alloc": (C.c_int, [C.c_int64, vp]),
         "marfa_diag_device_memory": (C.c_int, [vp, vp]),
         "marfa_diag_check": (C.c_int, [C.c_int32, vp]),
@@ -267,6 +269,14 @@ def marfa_plan_info(plan: Plan, kernel_ms: bool = False):
     k = np.empty(12, dtype=np.float64) if kernel_ms else None
     _check(load().marfa_plan_info(plan.handle, _ptr(v), _ptr(t), _ptr(k)))
     return v, t, k
+
+
+def marfa_shape_user_set(g, x_max: float) -> None:
+    """The user-defined line shape of the current device: g(x) sampled at
+    x = k x_max / (n - 1) (linear between samples, g(x_max) (x_max/x)^2 beyond), on the
+    Lorentz scaling x = (nu - nu~0) / gamma_L, f = S / (pi gamma_L) g(x)."""
+    g = np.ascontiguousarray(g, dtype=np.float32)
+    _check(load().marfa_shape_user_set(_ptr(g), len(g), float(x_max)))
 
 
 PLAN_CLASSES = 2

@@ -388,3 +388,39 @@ def test_wide_window_full_tiles_parity(M):
     got = run_gpu(M, wl)
     for lev in range(wl.n_levels):
         assert_parity(got[lev], O.eleven_grid(wl, lev), what=f"wide window level {lev}")
+
+
+# ------------------------------------------------------------ Sec. 2.2: a user-defined shape
+def test_user_shape_parity(M):
+    """The user's tabulated shape (here a sub-Lorentzian g = exp(-x/40) / (1 + x^2), given
+    as 4001 samples over [0, 400]) through the device shape table, with the chi-factor
+    and two levels, against the oracle's eleven-grid sum with the same definition; and
+    the table sampled from 1/(1 + x^2) against the built-in Lorentz shape."""
+    x = np.linspace(0.0, 400.0, 4001)
+    g = (np.exp(-x / 40.0) / (1.0 + x * x)).astype(np.float32)
+    M.marfa_shape_user_set(g, 400.0)
+    wl = tiny_workload(97, 300, 1500.0, 1502.3, 25.0, T=(296.0, 200.0), p=(1.0, 0.05), shape="user",
+                       chi="tonkov", chi_species=1).with_(user_shape=g, user_xmax=400.0)
+    got = run_gpu(M, wl)
+    for lev in range(wl.n_levels):
+        assert_parity(got[lev], O.eleven_grid(wl, lev), what=f"user shape level {lev}")
+    xs = M.marfa_diag_shape("user", np.linspace(0, 500, 101).astype(np.float32), np.zeros(101, np.float32))
+    assert np.allclose(xs, O.user_g(np.linspace(0, 500, 101).astype(np.float32), g, 400.0), rtol=2e-6, atol=1e-12)
+    # 4096 samples of 1/(1 + x^2) over [0, 64]: linear interpolation within dx^2/4 = 6e-5
+    # near the centre, the (64/x)^2 tail within 1/64^2 = 2.4e-4 of the Lorentz wing
+    xl = np.linspace(0.0, 64.0, 4096)
+    M.marfa_shape_user_set((1.0 / (1.0 + xl * xl)).astype(np.float32), 64.0)
+    lor = tiny_workload(98, 200, 1000.0, 1001.0, 10.0, T=(250.0,), p=(0.05,), shape="lorentz")
+    a = run_gpu(M, lor)
+    b = run_gpu(M, lor.with_(shape="user"))
+    assert_parity(b[0], a[0].astype(np.float64), rtol=5e-4, what="user table of the Lorentz vs Lorentz")
+
+
+def test_user_shape_requires_a_table(M):
+    """A shape outside the library's range or a bad table is refused."""
+    with pytest.raises(M.MarfaError):
+        M.marfa_shape_user_set(np.array([1.0], np.float32), 1.0)
+    with pytest.raises(M.MarfaError):
+        M.marfa_shape_user_set(np.array([1.0, -1.0], np.float32), 1.0)
+    with pytest.raises(M.MarfaError):
+        M.marfa_shape_user_set(np.array([1.0, 0.5], np.float32), 0.0)

@@ -565,3 +565,46 @@ def test_paper_voigt_profile_normalisation():
     f = O.profile("voigt_paper", d_fx, 1.0, gL, aD, False)
     g = O.profile("voigt", d_fx, 1.0, gL, aD, False)
     assert abs(np.trapezoid(f, d) / np.trapezoid(g, d) - 1) < 2e-3
+
+
+# ---------------------------------------------------------------- Sec. 2.2: a user-defined shape
+def _lorentz_table(n=200001, x_max=1000.0):
+    x = np.linspace(0.0, x_max, n)
+    return (1.0 / (1.0 + x * x)).astype(np.float32), x_max
+
+
+def test_user_shape_of_a_sampled_lorentz_is_the_lorentz_profile():
+    """The user's shape g sampled from 1/(1 + x^2) gives Eq. (4) back, within the linear
+    interpolation bound max|g''| dx^2 / 8 = dx^2 / 4 near the centre, the float32 rounding
+    of the samples, and the (x_max/x)^2 tail's relative error 1/x_max^2 beyond x_max."""
+    table, x_max = _lorentz_table()
+    dx = x_max / (len(table) - 1)
+    gL = 0.07
+    d = np.concatenate([np.linspace(0.0, 3.0, 3001), np.linspace(3.0, 200.0, 2001)])
+    d_fx = np.round(d * O.FIX).astype(np.int64)
+    got = O.profile("user", d_fx, 1.0, gL, 0.002, False, user=(table, x_max))
+    ref = O.profile("lorentz", d_fx, 1.0, gL, 0.002, False)
+    rel = np.abs(got / ref - 1.0)
+    x = d / gL
+    bound = (dx * dx / 4.0) * (1.0 + x * x) + 1.2e-7 + np.where(x > x_max, 1.0 / x_max ** 2, 0.0)
+    assert np.all(rel <= bound), rel.max()
+    # the tail: exactly g(x_max) (x_max / x)^2
+    xt = np.array([1500.0, 4000.0])
+    assert np.allclose(O.user_g(xt, table, x_max), float(table[-1]) * (x_max / xt) ** 2, rtol=1e-15)
+
+
+def test_user_shape_interpolates_linearly_and_is_symmetric():
+    table = np.array([1.0, 0.5, 0.25, 0.0], np.float32)
+    x_max = 3.0
+    assert np.allclose(O.user_g([0.0, 0.5, 1.0, 2.5, -2.5], table, x_max), [1.0, 0.75, 0.5, 0.125, 0.125])
+    assert O.user_g([3.0], table, x_max)[0] == 0.0
+
+
+def test_user_shape_planted_scaling_mistake_fails():
+    """Scaling the user's g by gamma_L the wrong way (x = d gamma_L) fails the Lorentz pin."""
+    table, x_max = _lorentz_table(20001, 100.0)
+    d_fx = np.round(np.linspace(0.0, 2.0, 201) * O.FIX).astype(np.int64)
+    gL = 0.07
+    ref = O.profile("lorentz", d_fx, 1.0, gL, 0.002, False)
+    bad = O.user_g(d_fx / O.FIX * gL, table, x_max) / (np.pi * gL)
+    assert np.abs(bad / ref - 1.0).max() > 0.5

@@ -68,6 +68,9 @@ class Workload:
     R_c: int = 8
     surrogate: int = 0
     stencil: int = 3   # interpolation points per coarse panel: 3 (Sec. 2.4) or 5
+    # shape 'user': g(x) sampled at x = k user_xmax / (n - 1) on the Lorentz scaling
+    user_shape: np.ndarray | None = None
+    user_xmax: float = 0.0
     meta: dict = field(default_factory=dict)
 
     @property
