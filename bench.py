@@ -48,11 +48,14 @@ UNIT = "pts*levels/s"
 FLOPS_FAR, FLOPS_MID, FLOPS_NEAR, FLOPS_SMALL = 20.0, 70.0, 200.0, 90.0
 
 # DRAM bytes (read + write) per launch of the dominant kernel of the Venus workload's
-# full window, from a single-pass ncu capture of the timed replay (dram__bytes_read.sum +
-# dram__bytes_write.sum; command and figures in profiles/traffic_dominant_kernels.md).
-# They belong to the kernels as built when captured; other workloads and windows report
-# null.
-TRAFFIC_BYTES = {("venus", "finest"): 651.35e6 + 614.03e6}
+# full window, by the variant the plan chose, from a single-pass ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum; command and figures in
+# profiles/traffic_dominant_kernels.md). Finest-grid variants: 1 flattened jobs, 2 the
+# same by mechanism, 3 by mechanism merged. They belong to the kernels as built when
+# captured; other workloads, windows and variants report null.
+TRAFFIC_BYTES = {("venus", "finest", 1): 663.5e6 + 808.7e6,
+                 ("venus", "finest", 2): 650.5e6 + 467.8e6,
+                 ("venus", "finest", 3): 663.7e6 + 854.0e6}
 N_SM = 152
 FP32_LANES = 128
 
@@ -533,7 +536,7 @@ def main():
             "kernel_ms_per_step_serial": {n: float(kms[i] / args.steps) for i, n in enumerate(names)},
             "roofline": {"bound": "alu", "kernel": names[dom], "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak,
-                         "traffic": (TRAFFIC_BYTES.get((args.workload, names[dom]))
+                         "traffic": (TRAFFIC_BYTES.get((args.workload, names[dom], int(variant[dom - 1]) if dom > 0 else -1))
                                      if args.nu_lo is None and args.nu_hi is None and args.stencil == 3
                                      else None),
                          "flops_per_eval": {"far": FLOPS_FAR, "asymptotic": FLOPS_MID, "poly_cell": FLOPS_NEAR,

@@ -24,7 +24,6 @@ __host__ __device__ __forceinline__ int64_t cl_sh(int64_t a, int s) { return -((
 
 constexpr int kShapeLorentz = 0, kShapeVoigt = 1, kShapeDoppler = 2, kShapeVoigtPaper = 3, kShapeUser = 4,
               kShapeConst = 100, kShapeQuad = 101, kShapeQuart = 102;
-constexpr int kNPhysShapes = 5;    // physical shapes 0..4: the entries of the device shape table
 constexpr int kUserShapeMax = 4096;  // samples of a user-defined shape
 
 // Per level (host-computed in double precision).

@@ -304,24 +304,21 @@ struct NodeX {
 
 // ------------------------------------------------------------------ line shapes
 // The paper lets a user redirect the line shape to any function (its procedure-pointer
-// hook, Sec. 2.2). Here the physical shapes are entries of a device function table
-// indexed by the request's shape code, each g(x, y) in the shape's own scaled variable
-// x (the level preparation sets the amplitude and the x scale per shape): Lorentz
-// 1/(1 + x^2), Voigt K(x, y), Doppler exp(-x^2), the paper's fast Voigt, and the user's
-// shape. The user's shape g(x) is given as n samples over [0, x_max] (symmetric in x),
-// linear between samples and g(x_max) (x_max / x)^2 beyond, on the Lorentz scaling
+// hook, Sec. 2.2). Here every shape is g(x, y) in the shape's own scaled variable x (the
+// level preparation sets the amplitude and the x scale per shape): Lorentz 1/(1 + x^2),
+// Voigt K(x, y), Doppler exp(-x^2), the paper's fast Voigt, and the user's shape. The
+// user's shape g(x) is given as n samples over [0, x_max] (symmetric in x), linear
+// between samples and g(x_max) (x_max / x)^2 beyond, on the Lorentz scaling
 // x = (nu - nu~0) / gamma_L with the Lorentz amplitude S / (pi gamma_L) (the Lorentz
-// itself is g = 1/(1 + x^2)). The Voigt kernels evaluate K inline; the table serves the
-// other shapes.
+// itself is g = 1/(1 + x^2)). The kernels evaluate K inline and reach the other shapes
+// through shape_f, a switch over direct calls: a table of device function pointers
+// would serve as well, but an indirect call site makes ptxas budget the kernel for any
+// target (grid 1's kernel went from 80 to 177 registers, a third of its occupancy).
 __device__ float g_user_tab[kUserShapeMax];
 __device__ int g_user_n = 0;
 __device__ float g_user_xmax = 1.0f, g_user_scale = 1.0f;  // scale = (n - 1) / x_max
 
-static __device__ __noinline__ float shape_lorentz(float x, float) { return 1.0f / fmaf(x, x, 1.0f); }
-static __device__ __noinline__ float shape_voigt(float x, float y) { return voigt_K(x, y); }
-static __device__ __noinline__ float shape_doppler(float x, float) { return expf(-x * x); }
-static __device__ __noinline__ float shape_voigt_paper(float x, float y) { return voigt_K_paper(x, y); }
-static __device__ __noinline__ float shape_user(float x, float) {
+static __device__ __noinline__ float shape_user(float x) {
   const float ax = fabsf(x);
   const int n = g_user_n;
   if (ax >= g_user_xmax) {
@@ -334,13 +331,13 @@ static __device__ __noinline__ float shape_user(float x, float) {
   return fmaf(f, g_user_tab[i + 1] - g_user_tab[i], g_user_tab[i]);
 }
 
-typedef float (*ShapeFn)(float, float);
-__device__ ShapeFn const g_shape_table[kNPhysShapes] = {shape_lorentz, shape_voigt, shape_doppler,
-                                                         shape_voigt_paper, shape_user};
-
 __device__ __forceinline__ float shape_f(int shape, float x, float y) {
-  if (shape < kNPhysShapes) return g_shape_table[shape](x, y);
   switch (shape) {
+    case kShapeVoigt: return voigt_K(x, y);
+    case kShapeVoigtPaper: return voigt_K_paper_call(x, y);
+    case kShapeLorentz: return 1.0f / fmaf(x, x, 1.0f);
+    case kShapeDoppler: return expf(-x * x);
+    case kShapeUser: return shape_user(x);
     case kShapeConst: return 1.0f;
     case kShapeQuart: return fmaf(x, fmaf(x, fmaf(x, fmaf(x, 0.00390625f, 0.015625f), 0.0625f), 0.25f), 1.0f);
     default: return fmaf(x, fmaf(x, 0.0625f, 0.25f), 1.0f);  // kShapeQuad
