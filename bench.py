@@ -53,9 +53,7 @@ FLOPS_FAR, FLOPS_MID, FLOPS_NEAR, FLOPS_SMALL = 20.0, 70.0, 200.0, 90.0
 # profiles/traffic_dominant_kernels.md). Finest-grid variants: 1 flattened jobs, 2 the
 # same by mechanism, 3 by mechanism merged. They belong to the kernels as built when
 # captured; other workloads, windows and variants report null.
-TRAFFIC_BYTES = {("venus", "finest", 1): 663.5e6 + 808.7e6,
-                 ("venus", "finest", 2): 650.5e6 + 467.8e6,
-                 ("venus", "finest", 3): 663.7e6 + 854.0e6}
+TRAFFIC_BYTES = {}
 N_SM = 152
 FP32_LANES = 128
 

@@ -956,6 +956,8 @@ static int build_plan(Plan& P, const marfa_lines_t* L, const marfa_level_t* leve
     for (int g = 2; g <= kNGrid; ++g)
       if (mech_ok(g, R.cut_fx, R.R_w, R.chi_req != 0)) R.mech |= 1 << g;
     if (mech_fine_ok(R.cut_fx, R.R_w, R.chi_req != 0)) R.mech |= 1 << (kNGrid + 1);
+    if (mech_fine_merge_ok(R.cut_fx, R.R_w, R.chi_req != 0, (int64_t)kFineWarpNodes << kFineShift))
+      R.mech |= 1 << (kNGrid + 2);
   }
   R.mlp = nullptr;
   if (rq->surrogate) {
@@ -1274,10 +1276,13 @@ static void launch_finest(const WorkSet& W, int c, cudaStream_t st) {
   const int v = W.tune[c][kFineKind];
   const FineItem* items = W.dfi + f0;
   int64_t* counts = W.dfc ? W.dfc + f0 * kCountFields : nullptr;
-  bool mech = v >= 2 && !W.wide;
-  for (const auto& R : W.rds) mech = mech && ((R.mech >> (kNGrid + 1)) & 1);
+  bool mech = v >= 2 && !W.wide, merge = v == 3;
+  for (const auto& R : W.rds) {
+    mech = mech && ((R.mech >> (kNGrid + 1)) & 1);
+    merge = merge && ((R.mech >> (kNGrid + 2)) & 1);
+  }
   if (v >= 1 && !W.surr_grid[kNGrid + 1])
-    launch_fine_jobs(W.drd, items, n, counts, W.wide, mech ? v - 1 : 0, st);
+    launch_fine_jobs(W.drd, items, n, counts, W.wide, mech ? (merge ? 2 : 1) : 0, st);
   else
     launch_fine(W.drd, items, n, counts, W.surr_grid[kNGrid + 1], W.wide, st);
 }
@@ -1950,9 +1955,11 @@ extern "C" int marfa_absorption_noalloc(const marfa_lines_t* lines, const marfa_
       launch_coarse_lm(drd, dci + k, (int)(k1 - k), nullptr, surr, v == 2 ? 16 : kLPairs, wide, st);
     k = k1;
   }
-  if (var[kFineKind] >= 1 && !surr)
-    launch_fine_jobs(drd, dfi, (int)P.fine.size(), nullptr, wide,
-                     (var[kFineKind] >= 2 && !wide && ((R.mech >> (kNGrid + 1)) & 1)) ? var[kFineKind] - 1 : 0, st);
+  if (var[kFineKind] >= 1 && !surr) {
+    const bool mech = var[kFineKind] >= 2 && !wide && ((R.mech >> (kNGrid + 1)) & 1);
+    const bool merge = var[kFineKind] == 3 && ((R.mech >> (kNGrid + 2)) & 1);
+    launch_fine_jobs(drd, dfi, (int)P.fine.size(), nullptr, wide, mech ? (merge ? 2 : 1) : 0, st);
+  }
   else
     launch_fine(drd, dfi, (int)P.fine.size(), nullptr, surr, wide, st);
   CK(cudaGetLastError());

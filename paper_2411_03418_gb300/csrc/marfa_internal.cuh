@@ -102,7 +102,8 @@ struct ReqDev {
   int32_t wide;             // 5-point variant: ownership on panels of four steps, quartic cascade
   int32_t shape;
   int32_t chi_req;          // request asks for the chi-factor
-  int32_t mech;             // bit g (2..10): mech_ok on grid g; bit 11: mech_fine_ok (3-point only)
+  int32_t mech;             // bit g (2..10): mech_ok on grid g; bit 11: mech_fine_ok; bit 12:
+                            // mech_fine_merge_ok (3-point only)
   int32_t g1_split;         // CTAs sharing a grid-1 tile's candidate lines (1..kG1Split)
   const MlpWeights* mlp;    // surrogate weights and guard, null for the plain path
   float out_scale;          // inverse internal scale
@@ -143,6 +144,7 @@ constexpr int kCWarps = 4;           // warps (tiles) of a grids-2..10 CTA
 constexpr int kFineThreads = 256;
 constexpr int kFinePerThread = 4;
 constexpr int kFineTile = kFineThreads * kFinePerThread;
+constexpr int kFineWarpNodes = kFinePerThread * 32;  // finest nodes of one warp
 
 struct PrepArgs {
   int64_t n;

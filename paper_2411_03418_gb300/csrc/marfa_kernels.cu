@@ -1039,6 +1039,11 @@ __global__ void __launch_bounds__(kLWarps * 32, SURR ? 3 : (PAIRS == 16 ? 7 : 4)
       const int64_t c = __ldg(R.c + lo_off + i);
       const int gst = __ldg(R.gstar + lo_off + i);
       const bool chi = __ldg(R.flags + lo_off + i) & 1;
+      // the line's data with its position (consecutive lines across the threads:
+      // coalesced), so that a candidate costs one round trip to memory
+      const float amp = __ldg(R.amp + lo_off + i);
+      const float sx = __ldg(R.sx + lo_off + i);
+      const float y = __ldg(R.yv + lo_off + i);
       MT own;
       if (fr.ok) {
         const PanelPos pp = fr.pos(c);
@@ -1050,9 +1055,6 @@ __global__ void __launch_bounds__(kLWarps * 32, SURR ? 3 : (PAIRS == 16 ? 7 : 4)
         own = owned_any<MT>(wide, g, c, gst, chi, cut, R.R_w, base, nb) & win;
       }
       if (!own) continue;
-      const float amp = __ldg(R.amp + lo_off + i);
-      const float sx = __ldg(R.sx + lo_off + i);
-      const float y = __ldg(R.yv + lo_off + i);
       NodeX nx;
       nx.init(X0 - c, s - 1, sx);
       ChiThr ct;
@@ -1978,29 +1980,76 @@ struct __align__(16) FineChi {
   int on, pad;                          // chi-factor applies
 };
 
+// The 3-point cascade at the four nodes k0 + q of a thread: the quadratic through
+// (0, vL), (1, vM), (2, vR) of a coarse grid's panel, in t (steps of h_g from the
+// panel's left node), is vL + t (c1 + t c2); the nodes sit at t0 + q dt, so it is
+// a + q (b + q c) there, and the ten grids' a, b, c add up. Only for threads with a
+// node inside the window (the slots exist there).
+struct Cascade3 {
+  float a, b, c;
+};
+
+__device__ __forceinline__ Cascade3 cascade3(const ReqDev& R, int lev, int64_t k0) {
+  Cascade3 r{0.0f, 0.0f, 0.0f};
+  const float* sl = R.slots + (int64_t)lev * R.slots_per_level;
+#pragma unroll
+  for (int g = 1; g <= kNGrid; ++g) {
+    const int sh = 13 - g;  // finest nodes per panel of grid g: 2^(13-g)
+    const int64_t np = R.npan[g];
+    const float* gp = sl + R.slot_off[g];
+    const int64_t m = k0 >> sh;
+    const int64_t idx = m - R.m_first[g];
+    float vL = __ldg(gp + idx), vM = __ldg(gp + np + idx), vR = __ldg(gp + 2 * np + idx);
+    if (g == 1) {  // the g1_split partial copies of grid 1, summed in part order
+#pragma unroll
+      for (int part = 1; part < kG1Split; ++part)
+        if (part < R.g1_split) {  // loads issued together, not one round trip per part
+          const float* gq = gp + 3 * np * part;
+          vL += __ldg(gq + idx);
+          vM += __ldg(gq + np + idx);
+          vR += __ldg(gq + 2 * np + idx);
+        }
+    }
+    const float c1 = 0.5f * fmaf(-3.0f, vL, fmaf(4.0f, vM, -vR));
+    const float c2 = 0.5f * fmaf(-2.0f, vM, vL + vR);
+    const float dt = ldexpf(1.0f, 1 - sh);
+    const float t0 = (float)(int)(k0 - (m << sh)) * dt;
+    r.a += fmaf(t0, fmaf(t0, c2, c1), vL);
+    r.b += dt * fmaf(2.0f * t0, c2, c1);
+    r.c += (dt * dt) * c2;
+  }
+  return r;
+}
+
+// Whether any of the thread's nodes k0 .. k0 + 3 lies inside the window.
+__device__ __forceinline__ bool fine_lane_valid(const ReqDev& R, int64_t k0) {
+  return k0 + kFinePerThread - 1 >= R.k_lo && k0 <= R.k_hi;
+}
+
 // The finest-grid epilogue shared by the finest-grid kernels: node k0 + q of this thread
 // holds out[q] (its finest-grid sum); add the quadratic (quartic: 5-point variant)
 // through the panel-local slots of every coarse grid, scale, and write the CTA's tile
 // [it.k0, it.k0 + kFineTile) of level lev to the output with aligned vector stores.
-// Every thread of the CTA calls it (it ends with a CTA barrier and the stores).
+// Every thread of the CTA calls it (it ends with a CTA barrier and the stores). pre: the
+// 3-point cascade when the caller computed it already (cascade3), else null.
 __device__ __forceinline__ void fine_cascade_store(const ReqDev& R, const FineItem& it, int lev, bool wide,
-                                                   int64_t k0, float (&out)[kFinePerThread], float* tile) {
+                                                   int64_t k0, float (&out)[kFinePerThread], float* tile,
+                                                   const Cascade3* pre = nullptr) {
   const int tid = threadIdx.x;
-  uint32_t valid = 0;
+  if (fine_lane_valid(R, k0)) {
+    if (!wide) {
+      const Cascade3 cc = pre ? *pre : cascade3(R, lev, k0);
 #pragma unroll
-  for (int q = 0; q < kFinePerThread; ++q)
-    if (k0 + q >= R.k_lo && k0 + q <= R.k_hi) valid |= 1u << q;
-  if (valid) {
-    // cascade: quadratic through the panel-local L, M, R of every coarse grid
-    const float* sl = R.slots + (int64_t)lev * R.slots_per_level;
+      for (int q = 0; q < kFinePerThread; ++q) out[q] += fmaf((float)q, fmaf((float)q, cc.c, cc.b), cc.a);
+    } else {
+      // 5-point: the four-step panel M4 is two-step panels 2 M4, 2 M4 + 1 (m_first is
+      // even); its nodes are L, M, R of the first and M, R of the second
+      const float* sl = R.slots + (int64_t)lev * R.slots_per_level;
 #pragma unroll
-    for (int g = 1; g <= kNGrid; ++g) {
-      const int sh = 13 - g;  // finest nodes per panel of grid g: 2^(13-g)
-      const int64_t np = R.npan[g];
-      const float* gp = sl + R.slot_off[g];
-      if (wide) {
-        // 5-point: the four-step panel M4 is two-step panels 2 M4, 2 M4 + 1 (m_first is
-        // even); its nodes are L, M, R of the first and M, R of the second
+      for (int g = 1; g <= kNGrid; ++g) {
+        const int sh = 13 - g;  // finest nodes per panel of grid g: 2^(13-g)
+        const int64_t np = R.npan[g];
+        const float* gp = sl + R.slot_off[g];
         const int64_t M4 = k0 >> (sh + 1);
         const int64_t i0 = 2 * M4 - R.m_first[g];
         float v0 = __ldg(gp + i0), v1 = __ldg(gp + np + i0), v2 = __ldg(gp + 2 * np + i0);
@@ -2029,28 +2078,6 @@ __device__ __forceinline__ void fine_cascade_store(const ReqDev& R, const FineIt
           const float w4 = (t * d1) * (d2 * d3) * (1.0f / 24.0f);
           out[q] += fmaf(v0, w0, fmaf(v1, w1, fmaf(v2, w2, fmaf(v3, w3, v4 * w4))));
         }
-        continue;
-      }
-      const int64_t m = k0 >> sh;
-      const int64_t idx = m - R.m_first[g];
-      float vL = __ldg(gp + idx), vM = __ldg(gp + np + idx), vR = __ldg(gp + 2 * np + idx);
-      if (g == 1) {  // the g1_split partial copies of grid 1, summed in part order
-        for (int part = 1; part < R.g1_split; ++part) {
-          const float* gq = gp + 3 * np * part;
-          vL += __ldg(gq + idx);
-          vM += __ldg(gq + np + idx);
-          vR += __ldg(gq + 2 * np + idx);
-        }
-      }
-      const int off0 = (int)(k0 - (m << sh));
-      const float inv_h = ldexpf(1.0f, 1 - sh);
-#pragma unroll
-      for (int q = 0; q < kFinePerThread; ++q) {
-        const float t = (float)(off0 + q) * inv_h;  // position in steps of h_g, [0, 2)
-        const float w0 = (t - 1.0f) * (t - 2.0f) * 0.5f;
-        const float w1 = t * (2.0f - t);
-        const float w2 = t * (t - 1.0f) * 0.5f;
-        out[q] += fmaf(vL, w0, fmaf(vM, w1, vR * w2));
       }
     }
 #pragma unroll
@@ -2276,8 +2303,9 @@ struct __align__(16) FineChi16 {
 // the candidates come in one pass per mechanism: the centre pass takes the lines with
 // g* = 11 (chi = 1 there: the region lies inside the first breakpoint), the edge and
 // breakpoint passes the lines whose edge or breakpoint falls near the warp's nodes. With
-// MECH = 2 one pass takes the merged zones; a candidate's nodes in the warp then come from
-// one mechanism at most (the warp spans 1/16 cm^-1, the mechanisms lie >= 3 cm^-1 apart).
+// MECH = 2 the centre pass is followed by one pass over the merged ranges of all edges
+// and breakpoints (fewer rounds of staging); a candidate's nodes in the warp then come
+// from one mechanism (mech_fine_merge_ok: they lie more than a warp's span apart).
 template <bool COUNT, int WIDE, int MECH>
 __global__ void __launch_bounds__(kFineThreads, 4)
     k_fine_jobs(const ReqDev* __restrict__ reqs, const FineItem* __restrict__ items,
@@ -2320,12 +2348,17 @@ __global__ void __launch_bounds__(kFineThreads, 4)
                               cut, wide ? P10 << 1 : P10, R.chi_req, zlo, zhi);
     bd.lookup(R, L, zlo, zhi, nz);
   }
+  // the coarse grids' cascade (3-point), loaded now so that its latency overlaps the
+  // summation instead of the end of the CTA
+  Cascade3 cc{0.0f, 0.0f, 0.0f};
+  if (!wide && fine_lane_valid(R, k0)) cc = cascade3(R, lev, k0);
   __syncthreads();
   int64_t nev = 0, nnear = 0, nmid = 0, nsmall = 0;
   int nB = 0;
   if (MECH && R.chi_req)
     for (int b = 0; b < 3 && chi_break_fx(b) <= cut; ++b) nB = b + 1;
-  const int npass = MECH == 1 ? 3 + 2 * nB : 1;
+  const int nmech = 3 + 2 * nB;  // centre, two cut-off edges, two per breakpoint
+  const int npass = MECH == 1 ? nmech : (MECH == 2 ? 2 : 1);
   // the mechanism of pass q sits at c + off(q) (MECH only)
   auto pass_off = [&](int q) {
     return q == 0 ? (int64_t)0
@@ -2333,9 +2366,9 @@ __global__ void __launch_bounds__(kFineThreads, 4)
          : q == 2 ? -cut
          : ((q & 1) ? chi_break_fx((q - 3) >> 1) : -chi_break_fx((q - 3) >> 1));
   };
-  // MECH == 1: every pass's candidate range at once (lane 2q: first line, 2q + 1: end)
+  // MECH: every mechanism's candidate range at once (lane 2q: first line, 2q + 1: end)
   int64_t range_v = 0;
-  if (MECH == 1 && wlo <= whi && lane < 2 * npass) {
+  if (MECH && wlo <= whi && lane < 2 * nmech) {
     const int q = lane >> 1;
     const int64_t off = pass_off(q);
     const int64_t reach = (q == 0 ? (int64_t)R.R_w * step_fx(kNGrid) : 0) + P10 + 1;
@@ -2344,7 +2377,7 @@ __global__ void __launch_bounds__(kFineThreads, 4)
   }
   for (int pass = 0; pass < npass && wlo <= whi; ++pass) {  // warp-uniform
     const int64_t off = pass_off(pass);
-    if (MECH == 1) {
+    if (MECH == 1 || (MECH == 2 && pass == 0)) {
       const int64_t a = __shfl_sync(0xffffffffu, range_v, 2 * pass);
       const int64_t b = __shfl_sync(0xffffffffu, range_v, 2 * pass + 1);
       bd.n = 0;
@@ -2353,20 +2386,18 @@ __global__ void __launch_bounds__(kFineThreads, 4)
         bd.hi[0] = b;
         bd.n = 1;
       }
-    } else if (MECH == 2) {
-      const int64_t Xlo = (kw + wlo) << kFineShift, Xhi = (kw + whi) << kFineShift;
-      const int64_t rc = (int64_t)R.R_w * step_fx(kNGrid) + P10 + 1, re = P10 + 1;
-      int64_t zlo[9], zhi[9];
-      int nz = 0;
-      zlo[nz] = Xlo - rc; zhi[nz] = Xhi + rc; ++nz;
-      zlo[nz] = Xlo - re - cut; zhi[nz] = Xhi + re - cut; ++nz;
-      zlo[nz] = Xlo - re + cut; zhi[nz] = Xhi + re + cut; ++nz;
-      for (int b = 0; b < nB; ++b) {
-        const int64_t B = chi_break_fx(b);
-        zlo[nz] = Xlo - re - B; zhi[nz] = Xhi + re - B; ++nz;
-        zlo[nz] = Xlo - re + B; zhi[nz] = Xhi + re + B; ++nz;
+    } else if (MECH == 2) {  // the edges' and breakpoints' ranges, merged
+      bd.n = 0;
+      for (int q = 1; q < nmech; ++q) {
+        const int64_t a = __shfl_sync(0xffffffffu, range_v, 2 * q);
+        const int64_t b = __shfl_sync(0xffffffffu, range_v, 2 * q + 1);
+        if (a < b) {
+          bd.lo[bd.n] = a;
+          bd.hi[bd.n] = b;
+          ++bd.n;
+        }
       }
-      bd.lookup(R, L, zlo, zhi, nz);
+      bd.merge();
     }
     const int64_t pbase = kw >> 3;
     const int64_t lo_off = (int64_t)lev * R.n_lines;
@@ -2379,46 +2410,50 @@ __global__ void __launch_bounds__(kFineThreads, 4)
     for (int64_t t0 = 0; t0 < n_cand; t0 += 32) {  // warp-uniform
       const bool valid = t0 + lane < n_cand;
       const int64_t i = valid ? cur.line(bd, t0 + lane) : 0;
+      // the line's data with its position (consecutive lines: coalesced), so that a
+      // candidate costs one round trip to memory
+      float amp_p = 0.0f, sx_p = 0.0f, y_p = 0.0f;
+      if (valid) {
+        amp_p = __ldg(R.amp + lo_off + i);
+        sx_p = __ldg(R.sx + lo_off + i);
+        y_p = __ldg(R.yv + lo_off + i);
+      }
       uint32_t pm = 0;
       int klo = 0, khi = -1;
       int64_t c = 0;
       bool chi = false;
-      bool centre = false;  // MECH == 2: the nodes are the centre's (chi = 1)
-      if (valid && MECH == 2) {
+      if (valid && MECH == 2 && pass == 1) {
         c = __ldg(R.c + lo_off + i);
         chi = __ldg(R.flags + lo_off + i) & 1;
         const int64_t lo = kw + wlo, hi = kw + whi;
         int64_t a = 1, b = 0, a2, b2;
         int found = 0;
-        auto take = [&](int64_t x, int64_t y, bool ctr) {
+        auto take = [&](int64_t x, int64_t y) {
           x = max(x, lo);
           y = min(y, hi);
           if (x <= y) {
             a = x;
             b = y;
-            centre = ctr;
             ++found;
           }
         };
-        mech_fine_centre(c, __ldg(R.gstar + lo_off + i), R.R_w, a2, b2);
-        take(a2, b2, true);
         mech_fine_edge_right(c + cut, a2, b2);
-        take(a2, b2, false);
+        take(a2, b2);
         mech_fine_edge_left(c - cut, a2, b2);
-        take(a2, b2, false);
+        take(a2, b2);
         if (chi)
           for (int q = 0; q < nB; ++q) {
             mech_fine_kink(c + chi_break_fx(q), a2, b2);
-            take(a2, b2, false);
+            take(a2, b2);
             mech_fine_kink(c - chi_break_fx(q), a2, b2);
-            take(a2, b2, false);
+            take(a2, b2);
           }
         if (found && MARFA_DCHECK(found == 1, 204)) {
           klo = (int)(a - kw);
           khi = (int)(b - kw);
           pm = rmask<uint32_t>(klo >> 3, khi >> 3, 0, 16);
         }
-      } else if (valid && MECH == 1) {
+      } else if (valid && MECH) {  // one mechanism: pass 0 the centre
         c = __ldg(R.c + lo_off + i);
         int64_t a = 1, b = 0;
         if (pass == 0) {
@@ -2449,19 +2484,19 @@ __global__ void __launch_bounds__(kFineThreads, 4)
       uint32_t far = 0;
       if (pm) {
         NodeX nx;
-        nx.init(Xa - c, kFineShift, __ldg(R.sx + lo_off + i));
+        nx.init(Xa - c, kFineShift, sx_p);
         FineLine fl;
         fl.klo = klo;
         fl.khi = khi;
-        fl.amp = __ldg(R.amp + lo_off + i);
-        fl.y = __ldg(R.yv + lo_off + i);
+        fl.amp = amp_p;
+        fl.y = y_p;
         fl.qf = nx.qf;
         fl.hs = nx.hs;
         fl.phs = nx.phs;
         fl.phi = nx.phi;
         sL[warp][lane] = fl;
         FineChi16 fc;
-        fc.on = chi && physical && !(MECH == 1 && pass == 0) && !(MECH == 2 && centre);
+        fc.on = chi && physical && !(MECH && pass == 0);
         fc.pad = 0;
         if (fc.on) {
           ChiThr ct;
@@ -2510,10 +2545,12 @@ __global__ void __launch_bounds__(kFineThreads, 4)
         const float jf = (float)j;
         const float xv = fmaf(jf + fl.qf, fl.hs, fl.phs);
         float v = fl.amp * (voigt ? voigt_K<true, false, true>(xv, fl.y, stab) : shape_f(R.shape, xv, fl.y));
-        const FineChi16 fc = sC[warp][li];
-        if (fc.on) {
-          const ChiThr ct{fc.r3, fc.r150, fc.r300, fc.l3, fc.l150, fc.l300};
-          v *= ct.value(j, fabsf((jf + fl.qf) + fl.phi) * ldexpf(1.0f, -kFineBits));
+        if (!(MECH && pass == 0)) {  // chi = 1 in the centre region
+          const FineChi16 fc = sC[warp][li];
+          if (fc.on) {
+            const ChiThr ct{fc.r3, fc.r150, fc.r300, fc.l3, fc.l150, fc.l300};
+            v *= ct.value(j, fabsf((jf + fl.qf) + fl.phi) * ldexpf(1.0f, -kFineBits));
+          }
         }
         if (MARFA_DCHECK(j >= 0 && j < kWarpNodes, 202)) acc[j] += v;
         count_eval<COUNT>(voigt, xv, fl.y, nev, nnear, nmid, nsmall);
@@ -2532,7 +2569,7 @@ __global__ void __launch_bounds__(kFineThreads, 4)
     comp_merge(s_, c_, sAcc[3][n], 0.0f);
     out[q] = s_ + c_;
   }
-  fine_cascade_store(R, it, lev, wide, k0, out, sAcc[0]);
+  fine_cascade_store(R, it, lev, wide, k0, out, sAcc[0], &cc);
   if (COUNT) block_counts<NW>(nev, 0, nnear, nmid, nsmall, red, counts);
 }
 

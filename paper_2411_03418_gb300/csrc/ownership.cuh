@@ -287,6 +287,26 @@ MARFA_HD bool mech_fine_ok(int64_t cut, int R_w, bool chi_req) {
   return true;
 }
 
+// The finest grid's merged pass takes every cut-off edge and chi breakpoint of a line in
+// one pass and gives a candidate the nodes of one mechanism in a span of `span` units
+// (a warp's nodes): that needs the edge and the applicable breakpoints on one side of
+// the centre to lie more than the span plus two G10 panels apart (mech_fine_ok alone
+// allows two G10 panels).
+MARFA_HD bool mech_fine_merge_ok(int64_t cut, int R_w, bool chi_req, int64_t span) {
+  if (!mech_fine_ok(cut, R_w, chi_req)) return false;
+  if (!chi_req) return true;
+  const int64_t gap = span + (int64_t(2) << panel_shift(kNGrid));
+  int64_t prev = -1;
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    const int64_t B = chi_break_fx(b);
+    if (B > cut) break;
+    if (cut - B <= gap || (prev >= 0 && B - prev <= gap)) return false;
+    prev = B;
+  }
+  return true;
+}
+
 // The centre's panels of grid g (absolute indices): [a1, b1] left of the centre and
 // [a2, b2] right of it (either may be empty: a > b); with gst == g the two ranges
 // join into the core [a1, b2] (b1 = a2 - 1); with gst < g none.

@@ -110,6 +110,36 @@ static bool mech_fine_node(int64_t k, int64_t c, int gst, bool chi, int64_t cut,
   return n > 0;
 }
 
+// The finest grid's merged pass (mech_fine_merge_ok): within any warp-aligned span of
+// kFineWarpNodes nodes at most one of a line's edges and breakpoints gives nodes.
+static long g_merge_cases = 0, g_merge_bad = 0;
+static void check_merge(int64_t c, bool chi, int64_t cut, const int64_t* spots, int ns) {
+  for (int i = 1; i < ns; ++i) {
+    const int64_t k0 = fl_sh(spots[i], kFineShift);
+    for (int64_t kw = ((k0 / kFineWarpNodes) - 2) * kFineWarpNodes; kw <= k0 + 2 * kFineWarpNodes;
+         kw += kFineWarpNodes) {
+      int n = 0;
+      auto in = [&](int64_t a, int64_t b) { n += (a <= kw + kFineWarpNodes - 1 && b >= kw && a <= b) ? 1 : 0; };
+      int64_t a, b;
+      mech_fine_edge_right(c + cut, a, b);
+      in(a, b);
+      mech_fine_edge_left(c - cut, a, b);
+      in(a, b);
+      if (chi)
+        for (int q = 0; q < 3; ++q) {
+          const int64_t B = chi_break_fx(q);
+          if (B > cut) break;
+          mech_fine_kink(c - B, a, b);
+          in(a, b);
+          mech_fine_kink(c + B, a, b);
+          in(a, b);
+        }
+      ++g_merge_cases;
+      if (n > 1) ++g_merge_bad;
+    }
+  }
+}
+
 // Compare the mechanisms with the 64-bit form around the centre, both edges and every
 // breakpoint of one line; returns mismatches (0 when the mechanisms do not apply).
 static long check_mech(int g, int64_t cut, int R_w, bool chi_req, int64_t c, int gst, bool chi, bool& ok) {
@@ -125,6 +155,8 @@ static long check_mech(int g, int64_t cut, int R_w, bool chi_req, int64_t c, int
     spots[ns++] = c - B;
     spots[ns++] = c + B;
   }
+  if (fine && mech_fine_merge_ok(cut, R_w, chi_req, (int64_t)kFineWarpNodes << kFineShift))
+    check_merge(c, chi, cut, spots, ns);
   for (int i = 0; i < ns; ++i) {
     if (!fine) {
       const int s = panel_shift(g);
@@ -202,11 +234,11 @@ int main() {
   // (so that centre, edges and breakpoints land on them), every grid and the finest
   long mcases = 0, mok = 0, mbad = 0;
   const int64_t mcuts[] = {125 * one, 25 * one, 400 * one, 3 * one + one / 2, 160 * one + one / 7, 10 * one,
-                           151 * one};
+                           151 * one, 150 * one + one / 64};
   const int mRws[] = {8, 16, 4, 7, 2};
   for (int rep = 0; rep < 60000; ++rep) {
     const int g = (int)uniform(2, 11);
-    const int64_t cut = mcuts[uniform(0, 6)];
+    const int64_t cut = mcuts[uniform(0, 7)];
     const int R_w = mRws[uniform(0, 4)];
     const bool chi_req = uniform(0, 3) != 0;
     const bool chi = chi_req && uniform(0, 3) != 0;
@@ -223,7 +255,12 @@ int main() {
   }
   if (g_shared_nodes) fprintf(stderr, "nodes given by two mechanisms: %ld\n", g_shared_nodes);
   mbad += g_shared_nodes;
-  printf("cases %ld frames_ok %ld mismatches %ld mech_cases %ld mech_ok %ld mech_mismatches %ld\n", cases, okc, bad,
-         mcases, mok, mbad);
-  return (bad || mbad) ? 1 : 0;
+  // the condition is needed: an edge 1/64 cm^-1 beyond a breakpoint passes mech_fine_ok
+  // but puts both mechanisms in one warp
+  const bool planted = mech_fine_ok(150 * one + one / 64, 8, true) &&
+                       !mech_fine_merge_ok(150 * one + one / 64, 8, true, (int64_t)kFineWarpNodes << kFineShift);
+  printf("cases %ld frames_ok %ld mismatches %ld mech_cases %ld mech_ok %ld mech_mismatches %ld merge_cases %ld "
+         "merge_bad %ld planted %d\n",
+         cases, okc, bad, mcases, mok, mbad, g_merge_cases, g_merge_bad, (int)planted);
+  return (bad || mbad || g_merge_bad || !planted) ? 1 : 0;
 }

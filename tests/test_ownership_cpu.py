@@ -33,3 +33,8 @@ def test_panel_frame_masks_equal_fixed_point_masks(tmp_path):
     assert fields[6] == "mech_cases" and fields[10] == "mech_mismatches"
     assert int(fields[11]) == 0
     assert int(fields[9]) > 20000  # enough cases where the mechanisms act apart
+    # the finest grid's merged pass: one edge or breakpoint per warp span where
+    # mech_fine_merge_ok holds, and the condition rejects an edge beside a breakpoint
+    assert fields[12] == "merge_cases" and int(fields[13]) > 10000
+    assert fields[14] == "merge_bad" and int(fields[15]) == 0
+    assert fields[16] == "planted" and fields[17] == "1"
