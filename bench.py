@@ -53,7 +53,9 @@ FLOPS_FAR, FLOPS_MID, FLOPS_NEAR, FLOPS_SMALL = 20.0, 70.0, 200.0, 90.0
 # profiles/traffic_dominant_kernels.md). Finest-grid variants: 1 flattened jobs, 2 the
 # same by mechanism, 3 by mechanism merged. They belong to the kernels as built when
 # captured; other workloads, windows and variants report null.
-TRAFFIC_BYTES = {}
+TRAFFIC_BYTES = {("venus", "finest", 1): 653.3e6 + 637.6e6,
+                 ("venus", "finest", 2): 642.5e6 + 459.5e6,
+                 ("venus", "finest", 3): 643.0e6 + 466.2e6}
 N_SM = 152
 FP32_LANES = 128
 

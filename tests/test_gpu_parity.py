@@ -214,17 +214,16 @@ def test_paper_voigt_shape_elementwise(M):
 
 def test_paper_voigt_absorption(M):
     """The 'voigt_paper' shape through the whole path against the oracle's eleven-grid sum
-    with the same shape. A node's x is computed in FP32 on the GPU and FP64 in the oracle,
-    so an evaluation within round-off of a region boundary (|x| = 1, 5.5, 15, y = 0.02)
-    can take the neighbouring region's formula, which differs by up to the 8 % step of the
-    region-4 asymptote: nearly all nodes meet the 1e-4 bar, all of them a 2 % one."""
+    with the same shape, at the same 1e-4 bar as the default shape at every node. The
+    regions are chosen in FP32 on both sides; a node's x is FP32 on the GPU and FP64 in
+    the oracle, so an evaluation within a few roundings of a region boundary could take
+    the neighbouring formula; on this case none weighs enough there to move a node by
+    1e-4, and every node meets the bar (largest error about 2e-6)."""
     wl = tiny_workload(81, 500, 2000.0, 2003.01, 125.0, T=(735.0, 296.0, 170.0), p=(92.0, 1.0, 1e-5),
                        chi="tonkov", chi_species=1, shape="voigt_paper")
     got = run_gpu(M, wl)
     for lev in range(wl.n_levels):
-        ref = O.eleven_grid(wl, lev)
-        rel = np.abs(got[lev] / ref - 1.0)
-        assert np.mean(rel < RTOL) > 0.999 and rel.max() < 0.02, (lev, rel.max())
+        assert_parity(got[lev], O.eleven_grid(wl, lev), what=f"paper-mode Voigt level {lev}")
 
 
 # the 5-point variant (quartic interpolation on panels of four steps)
@@ -371,13 +370,20 @@ def test_config1_venus_full_size_sampled(M):
     rng = np.random.default_rng(5)
     k_lo, _ = O.window_nodes(wl.nu_lo, wl.nu_hi)
     for lev in (0, 17, 35, 50, 59):
-        idx = np.concatenate([[0, n - 1], rng.integers(0, n, 14)])
+        # the floor from the oracle alone: its largest value over the sampled nodes, which
+        # include the centre of the line with the highest peak (a lower bound of the
+        # level's maximum, so the floor can only be stricter than the definition's)
+        P = O.level_params(wl, lev)
+        inside = (P["nu_shift"] > wl.nu_lo) & (P["nu_shift"] < wl.nu_hi)
+        peak = np.where(inside, P["amp"] / np.maximum(P["alpha_D"], P["gamma_L"]), 0.0)
+        kc = int(np.rint(P["nu_shift"][int(np.argmax(peak))] * 2048)) - k_lo
+        idx = np.concatenate([[0, n - 1, kc], rng.integers(0, n, 14)])
         ref = O.eleven_grid_at(wl, lev, k_lo + idx)
         got = out[lev, torch.as_tensor(idx, device="cuda")].cpu().numpy()
-        rowmax = float(out[lev].max().cpu())
-        big = np.abs(ref) > FLOOR * rowmax
+        refmax = float(np.abs(ref).max())
+        big = np.abs(ref) > FLOOR * refmax
         assert np.all(np.abs(got[big] / ref[big] - 1) < RTOL), f"level {lev}"
-        assert np.all(np.abs(got[~big] - ref[~big]) <= RTOL * FLOOR * rowmax)
+        assert np.all(np.abs(got[~big] - ref[~big]) <= RTOL * FLOOR * refmax)
 
 
 def test_wide_window_full_tiles_parity(M):
@@ -393,7 +399,7 @@ def test_wide_window_full_tiles_parity(M):
 # ------------------------------------------------------------ Sec. 2.2: a user-defined shape
 def test_user_shape_parity(M):
     """The user's tabulated shape (here a sub-Lorentzian g = exp(-x/40) / (1 + x^2), given
-    as 4001 samples over [0, 400]) through the device shape table, with the chi-factor
+    as 4001 samples over [0, 400]) through the kernels' shape switch, with the chi-factor
     and two levels, against the oracle's eleven-grid sum with the same definition; and
     the table sampled from 1/(1 + x^2) against the built-in Lorentz shape."""
     x = np.linspace(0.0, 400.0, 4001)
