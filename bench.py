@@ -481,6 +481,7 @@ def main():
     dom = int(np.argmax(kms))
     dom_ms = kms[dom] / max(1, klaunch[dom])
     dom_flops = float(flops_grid[dom - 1]) if dom > 0 else 0.0
+    evals_dom = float(counts_grid[dom - 1]) if dom > 0 else 0.0
     achieved = dom_flops / (dom_ms * 1e-3) / 1e12
     mhz, src = peaks()
     peak = N_SM * FP32_LANES * 2 * mhz * 1e6 / 1e12
@@ -542,6 +543,13 @@ def main():
                          "flops_per_eval": {"far": FLOPS_FAR, "asymptotic": FLOPS_MID, "poly_cell": FLOPS_NEAR,
                                             "small_y_cell": FLOPS_SMALL},
                          "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz ({src} max clock)",
+                         "frac_of_fma_probe": achieved / probes["fp32_fma_tflops"],
+                         # the same launch with a flat 10 or 40 FP32 flops per evaluation (the
+                         # per-evaluation range of the hot-path budget) instead of the
+                         # implementation's counts by Voigt branch
+                         "flat_10_40_flops_per_eval": {
+                             "achieved": [evals_dom * f / (dom_ms * 1e-3) / 1e12 for f in (10.0, 40.0)],
+                             "frac": [evals_dom * f / (dom_ms * 1e-3) / 1e12 / peak for f in (10.0, 40.0)]},
                          "probes": probes},
             "clocks": clocks,
         }
