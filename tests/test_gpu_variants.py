@@ -129,3 +129,28 @@ def test_variants_refuse_out_of_range(M):
     bad[10] = 4
     with pytest.raises(M.MarfaError):
         M.marfa_diag_variants(bad)
+
+
+def test_merged_finest_pass_falls_back_where_an_edge_meets_a_breakpoint(M):
+    """A cut-off 1/64 cm^-1 beyond the 150 cm^-1 breakpoint: the mechanisms lie apart
+    (mech_fine_ok), but a line's edge and breakpoint fall among one warp's nodes, so the
+    finest grid's merged pass does not apply (mech_fine_merge_ok). Forced to the merged
+    variant, the library takes the per-mechanism passes and stays within 1e-4 of the
+    oracle. A third of the lines sit 150 cm^-1 below the window and a third above, so that
+    their edges and breakpoints fall inside it."""
+    cut = 150.0 + 1.0 / 64
+    base = tiny_workload(76, 600, 2000.0, 2000.5, cut, T=(296.0, 200.0), p=(1.0, 1e-3), chi="tonkov",
+                         chi_species=1, spread=0.5)
+    ln = base.lines.copy()
+    k = len(ln) // 3
+    ln["nu0"][:k] -= 150.0
+    ln["nu0"][k:2 * k] += 150.0
+    wl = base.with_(lines=ln)
+    lines = M.marfa_prepare_lines(wl.lines, wl.species)
+    refs = [O.eleven_grid(wl, lev) for lev in range(wl.n_levels)]
+    for coarse in (2, 4):
+        _force(M, coarse, 3)
+        out = np.empty((wl.n_levels, M.marfa_num_points(wl.nu_lo, wl.nu_hi)), np.float32)
+        M.marfa_absorption(lines, M.levels_of(wl), wl.vmr, M.request_of(wl), out)
+        for lev in range(wl.n_levels):
+            assert_parity(out[lev], refs[lev], f"coarse {coarse} level {lev}")
