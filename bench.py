@@ -533,7 +533,7 @@ def main():
                                                        "class 0: windows <= 16 cm-1, 1: wider; -1: no request"},
                      "variants": "grids 2-10: 0 line-major 32 pairs, 1 two-phase, 2 line-major 16 pairs, "
                                  "3 flattened, 4 by mechanism, 5 by mechanism merged; finest: 0 groups per panel, "
-                                 "1 flattened jobs, 2 flattened jobs by mechanism, 3 the same merged"},
+                                 "1 flattened jobs, 2 flattened jobs by mechanism, 3 the same with a merged edge/breakpoint pass"},
             "kernel_ms_per_step_serial": {n: float(kms[i] / args.steps) for i, n in enumerate(names)},
             "roofline": {"bound": "alu", "kernel": names[dom], "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak,

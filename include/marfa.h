@@ -183,7 +183,8 @@ int marfa_absorption_batch(int32_t n_req, const marfa_lines_t* const* lines,
  *              with closed-form ownership, where those lie far enough apart, in a
  *              pass per mechanism or one merged pass), and for the finest grid its four
  *              kernels (8-lane groups per G10 panel; flattened (line, panel) jobs, with
- *              general or closed-form ownership), on
+ *              general or closed-form ownership, the latter in a pass per mechanism or
+ *              a centre pass and one merged edge/breakpoint pass), on
  *              this batch's own work and keep the fastest (otherwise the defaults of
  *              marfa_diag_variants); MARFA_PLAN_SERIAL: capture
  *              grids 1..10 one after the
@@ -215,7 +216,9 @@ int marfa_plan_execute(marfa_plan_t* plan, void* stream);
  * mechanism (closed-form ownership, a pass per mechanism; the launch takes 1 where it
  * does not apply), 5 by mechanism in one merged pass; finest
  * grid: 0 groups per panel, 1 flattened jobs, 2 flattened jobs by mechanism (1 where it
- * does not apply), 3 the same in one merged pass); tune_ms[MARFA_PLAN_KINDS][MARFA_PLAN_VARIANTS]
+ * does not apply), 3 the same with a centre pass and one merged pass over the cut-off
+ * edges and breakpoints (2 where a line's edge and a breakpoint can share a warp's
+ * nodes)); tune_ms[MARFA_PLAN_KINDS][MARFA_PLAN_VARIANTS]
  * the autotuner's time per launch of each variant (-1 when not tuned or not a variant of
  * that kind); kernel_ms[12] device time of the last
  * execution per kernel kind (0 level preparation, 1..10 grids, 11 finest grid; waits for

@@ -1011,15 +1011,17 @@ static void* pinned_host_view(void* p) {
 // same in one merged pass. Finest grid (kind kFineKind): 0 = k_fine (an 8-lane group per
 // G10 panel), 1 = k_fine_jobs ((line, panel) jobs spread evenly over the groups), 2 = the
 // same with closed-form ownership, one pass per mechanism (mech bit of every request;
-// otherwise variant 1), 3 = the same in one merged pass.
+// otherwise variant 1), 3 = the same with a centre pass and one merged pass over the
+// edges and breakpoints (merge bit of every request; otherwise variant 2).
 // Surrogate-capable launches always take variant 1 on grids 2..10 (when 3 is chosen)
 // and k_fine. Calls without tuning take the process-wide defaults (marfa_diag_variants).
 constexpr int kNVariants = 6;
 constexpr int kFineKind = kNGrid + 1;
 constexpr int kNFineVariants = 4;
 // Defaults measured on the Venus workload (line-major over 16 pairs on grids 2..7, the
-// mechanism kernel on 8..10, flattened jobs by mechanism on the finest grid).
-static std::atomic<int> g_default_variant[kNGrid + 2] = {{-1}, {-1}, {2}, {2}, {2}, {2}, {2}, {2}, {4}, {4}, {4}, {2}};
+// mechanism kernel on 8..10, flattened jobs by mechanism with the merged edge and
+// breakpoint pass on the finest grid).
+static std::atomic<int> g_default_variant[kNGrid + 2] = {{-1}, {-1}, {2}, {2}, {2}, {2}, {2}, {2}, {4}, {4}, {4}, {3}};
 static int default_variant(int g) { return g_default_variant[g].load(std::memory_order_relaxed); }
 static int64_t variant_pairs(int v) {
   return v == 0 ? (int64_t)kLPairs : (v == 2 ? (int64_t)16 : (int64_t)kCPairs * kCWarps);
