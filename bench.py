@@ -449,16 +449,18 @@ def main():
     value = job_throughput(units_job, 1, args.steps, t_total)
     evals_s = job_throughput(evals_job, 1, args.steps, t_total)
 
-    # end to end through the public call with host buffers (pinned): line records in,
-    # prepare, absorption (batch call for several requests), k(nu) back, every step
+    # end to end through the public calls with host buffers (pinned): line records in,
+    # prepare (the batch preparation for several requests), absorption (the batch call
+    # for several requests), k(nu) back, every step
     rec_h = [torch.from_numpy(w.lines.view(np.uint8)).pin_memory().numpy().view(w.lines.dtype) for w in wls]
     out_h = [torch.empty((w.n_levels, n), dtype=torch.float32).pin_memory().numpy() for w, n in zip(wls, npts)]
 
     def e2e_step():
-        l2 = [M.marfa_prepare_lines(r, w.species) for r, w in zip(rec_h, wls)]
         if len(wls) == 1:
+            l2 = [M.marfa_prepare_lines(rec_h[0], wls[0].species)]
             M.marfa_absorption(l2[0], levels[0], wls[0].vmr, rqs[0], out_h[0], stream)
         else:
+            l2 = M.marfa_prepare_lines_batch(rec_h, [w.species for w in wls])
             M.marfa_absorption_batch(l2, levels, [w.vmr for w in wls], rqs, out_h, stream)
         for x in l2:
             M.marfa_free_lines(x)

@@ -121,7 +121,22 @@ int marfa_prepare_lines(const marfa_line_t* lines, int64_t n_lines,
                         const marfa_species_t* species, int32_t n_species,
                         marfa_lines_t** out);
 
-/* Release a handle from marfa_prepare_lines (NULL is ignored). */
+/*
+ * The line lists of n_req requests at once (the preparation step of a batch, App. B
+ * records per request): lines[q] (n[q] records), species[q] (n_species[q] entries), all
+ * host pointers; out[q] receives request q's handle, the same list marfa_prepare_lines
+ * would make. The host work of the requests runs in parallel on the library's host
+ * threads, the copies to the current device follow in one stream-ordered sequence. On
+ * any error no handle is returned (every out[q] NULL, nothing held) and the message
+ * names the first failing request. Errors: those of marfa_prepare_lines; MARFA_E_INVAL
+ * for n_req < 1 or a NULL array. Not in the paper (it prepares one list at a time).
+ */
+int marfa_prepare_lines_batch(int32_t n_req, const marfa_line_t* const* lines, const int64_t* n_lines,
+                              const marfa_species_t* const* species, const int32_t* n_species,
+                              marfa_lines_t** out);
+
+/* Release a handle from marfa_prepare_lines or marfa_prepare_lines_batch (NULL is
+ * ignored). Waits until the device has finished every use of the list. */
 void marfa_free_lines(marfa_lines_t* lines);
 
 /* Number of output points of a window: #{k : nu_lo <= k 2^-11 <= nu_hi}; 0 if empty,
@@ -250,7 +265,8 @@ int marfa_shape_user_set(const float* g, int32_t n, double x_max);
  * 6; entries 1..10: the variants of marfa_plan_info's layout), -1 for a class with no
  * request; tune_ms[2][MARFA_PLAN_KINDS][MARFA_PLAN_VARIANTS] the autotuner's time per
  * launch of each choice (entry 0: of the splits 1, 2, 3, 6), -1 where not timed. Without
- * MARFA_PLAN_AUTOTUNE every class takes split 6 and the marfa_diag_variants defaults.
+ * MARFA_PLAN_AUTOTUNE the narrow class takes split 2, the wide class split 6, and both
+ * the marfa_diag_variants defaults (as marfa_absorption and marfa_absorption_batch do).
  * Errors: MARFA_E_INVAL for a NULL plan. */
 #define MARFA_PLAN_CLASSES 2
 int marfa_plan_classes(const marfa_plan_t* plan, int32_t* req_class, int32_t* choice, float* tune_ms);

@@ -243,7 +243,8 @@ extern "C" void marfa_free_lines(marfa_lines_t* L) {
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(L->device);
-    cudaFree(L->block);
+    cudaDeviceSynchronize();  // every use of the list, on any stream, has finished
+    cudaFreeAsync(L->block, 0);  // back to the device's pool
     cudaSetDevice(cur);
   }
   delete L;
@@ -322,7 +323,9 @@ class HostPool {
   int want_ = 0, pending_ = 0;
 };
 
+static thread_local bool t_serial_loops = false;  // set on a thread that runs one job of a batch
 static int host_threads(int64_t work, int64_t min_per_thread) {
+  if (t_serial_loops) return 1;
   const HostPool* pool = HostPool::get();
   const int64_t nt = std::min<int64_t>(pool ? pool->size() : 1, std::max<int64_t>(1, work / min_per_thread));
   return (int)nt;
@@ -523,10 +526,19 @@ struct ChunkScan {
   double dmin = 1e300, dmax = -1e300;
 };
 
-extern "C" int marfa_prepare_lines(const marfa_line_t* lines, int64_t n, const marfa_species_t* sp,
-                                   int32_t n_sp, marfa_lines_t** out) {
-  if (!out) return fail(MARFA_E_INVAL, "out is NULL");
-  *out = nullptr;
+// A line list prepared on the host: the list object (no device block yet) and the host
+// staging block in the device block's layout, with the offsets of its sub-arrays.
+struct StagedLines {
+  marfa_lines_t* L = nullptr;
+  std::unique_ptr<unsigned char[]> hb;
+  size_t total = 0;
+  size_t o_key = 0, o_nu = 0, o_S = 0, o_ga = 0, o_gs = 0, o_E = 0, o_na = 0, o_da = 0, o_sp = 0, o_b = 0;
+};
+
+// Validation, order, per-field arrays and bucket index of one line list, on the host
+// (App. B records; the ordering and keys of the header's marfa_prepare_lines).
+static int prepare_host(const marfa_line_t* lines, int64_t n, const marfa_species_t* sp, int32_t n_sp,
+                        StagedLines& out) {
   if (!lines || n < 1) return fail(MARFA_E_INVAL, "need at least one line");
   if (n > (int64_t)1 << 31) return fail(MARFA_E_INVAL, "at most 2^31 lines");
   if (!sp || n_sp < 1 || n_sp > 32767) return fail(MARFA_E_INVAL, "need 1..32767 species");
@@ -610,7 +622,6 @@ extern "C" int marfa_prepare_lines(const marfa_line_t* lines, int64_t n, const m
 
   marfa_lines_t* L = alloc_fails() ? nullptr : new (std::nothrow) marfa_lines_t();
   if (!L) return fail(MARFA_E_NOMEM, "host allocation failed");
-  cudaGetDevice(&L->device);
   L->n = n;
   // bucket index over the sorted keys: about one line per two buckets on average, at
   // most 2^26 buckets
@@ -687,36 +698,103 @@ extern "C" int marfa_prepare_lines(const marfa_line_t* lines, int64_t n, const m
       bfirst[b] = (int32_t)i;
     }
   });
-  cudaError_t e = alloc_fails() ? cudaErrorMemoryAllocation : cudaMalloc(&L->block, total);
-  if (e != cudaSuccess) {
+  out.L = L;
+  out.hb = std::move(hb);
+  out.total = total;
+  out.o_key = o_key, out.o_nu = o_nu, out.o_S = o_S, out.o_ga = o_ga, out.o_gs = o_gs;
+  out.o_E = o_E, out.o_na = o_na, out.o_da = o_da, out.o_sp = o_sp, out.o_b = o_b;
+  return MARFA_OK;
+}
+
+// The device block of a staged list from the stream-ordered pool, filled by one copy on
+// the legacy default stream (a plain cudaMalloc per list costs more than the copy for the
+// small lists of a batch of requests); the caller synchronises that stream.
+static int upload_staged(StagedLines& st) {
+  marfa_lines_t* L = st.L;
+  CK(cudaGetDevice(&L->device));  // the calling thread's device
+  if (const int ra = dev_alloc(&L->block, st.total, 0)) {
     L->block = nullptr;
-    delete L;
-    return fail(MARFA_E_NOMEM, "cudaMalloc(%zu) failed: %s", total, cudaGetErrorString(e));
+    return ra;
   }
   char* p = (char*)L->block;
-  L->key = (int64_t*)(p + o_key);
-  L->nu0 = (double*)(p + o_nu);
-  L->S296 = (float*)(p + o_S);
-  L->ga = (float*)(p + o_ga);
-  L->gs = (float*)(p + o_gs);
-  L->E = (float*)(p + o_E);
-  L->na = (float*)(p + o_na);
-  L->da = (float*)(p + o_da);
-  L->sp = (int16_t*)(p + o_sp);
-  L->bfirst = (int32_t*)(p + o_b);
-  e = cudaMemcpy(L->block, hb.get(), total, cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) {
-    marfa_free_lines(L);
-    return fail(MARFA_E_CUDA, "cudaMemcpy failed: %s", cudaGetErrorString(e));
-  }
+  L->key = (int64_t*)(p + st.o_key);
+  L->nu0 = (double*)(p + st.o_nu);
+  L->S296 = (float*)(p + st.o_S);
+  L->ga = (float*)(p + st.o_ga);
+  L->gs = (float*)(p + st.o_gs);
+  L->E = (float*)(p + st.o_E);
+  L->na = (float*)(p + st.o_na);
+  L->da = (float*)(p + st.o_da);
+  L->sp = (int16_t*)(p + st.o_sp);
+  L->bfirst = (int32_t*)(p + st.o_b);
+  CK(cudaMemcpyAsync(L->block, st.hb.get(), st.total, cudaMemcpyHostToDevice, 0));
+  return MARFA_OK;
+}
+
+extern "C" int marfa_prepare_lines(const marfa_line_t* lines, int64_t n, const marfa_species_t* sp,
+                                   int32_t n_sp, marfa_lines_t** out) {
+  if (!out) return fail(MARFA_E_INVAL, "out is NULL");
+  *out = nullptr;
+  StagedLines st;
+  int r = prepare_host(lines, n, sp, n_sp, st);
+  if (r) return r;
+  r = upload_staged(st);
+  if (!r && cudaStreamSynchronize(0) != cudaSuccess) r = fail(MARFA_E_CUDA, "copying the line list failed");
   // commit marfa_absorption_noalloc's scratch on this device now (see noalloc_scratch)
   char* scratch = nullptr;
-  const int rs = noalloc_scratch(&scratch);
-  if (rs) {
-    marfa_free_lines(L);
-    return rs;
+  if (!r) r = noalloc_scratch(&scratch);
+  if (r) {
+    marfa_free_lines(st.L);
+    return r;
   }
-  *out = L;
+  *out = st.L;
+  return MARFA_OK;
+}
+
+// Several line lists at once: the host stages run in parallel on the host pool (one list
+// per thread, each list's own loops serial), then the device blocks are filled in order
+// on the legacy default stream and synchronised once.
+extern "C" int marfa_prepare_lines_batch(int32_t n_req, const marfa_line_t* const* lines, const int64_t* n,
+                                         const marfa_species_t* const* sp, const int32_t* n_sp,
+                                         marfa_lines_t** out) {
+  if (!out || !lines || !n || !sp || !n_sp || n_req < 1) return fail(MARFA_E_INVAL, "bad batch arguments");
+  for (int32_t q = 0; q < n_req; ++q) out[q] = nullptr;
+  std::vector<StagedLines> st;
+  std::vector<int> rc;
+  std::vector<std::string> msg;
+  try {
+    st.resize(n_req);
+    rc.assign(n_req, 0);
+    msg.resize(n_req);
+  } catch (...) {
+    return fail(MARFA_E_NOMEM, "host allocation failed");
+  }
+  std::atomic<int32_t> next{0};
+  const int nt = (int)std::min<int64_t>(host_threads((int64_t)n_req << 20, 1 << 20), n_req);
+  par_chunks(nt, nt, [&](int64_t, int64_t, int) {
+    const bool was = t_serial_loops;
+    t_serial_loops = true;
+    for (int32_t q; (q = next.fetch_add(1)) < n_req;) {
+      rc[q] = prepare_host(lines[q], n[q], sp[q], n_sp[q], st[q]);
+      if (rc[q]) msg[q] = g_err;
+    }
+    t_serial_loops = was;
+  });
+  int r = MARFA_OK;
+  for (int32_t q = 0; q < n_req && !r; ++q)
+    if (rc[q]) r = fail(rc[q], "request %d: %s", q, msg[q].c_str());
+  for (int32_t q = 0; q < n_req && !r; ++q) {
+    r = upload_staged(st[q]);
+    if (r) r = fail(r, "request %d: %s", q, g_err.c_str());
+  }
+  if (!r && cudaStreamSynchronize(0) != cudaSuccess) r = fail(MARFA_E_CUDA, "copying the line lists failed");
+  char* scratch = nullptr;
+  if (!r) r = noalloc_scratch(&scratch);
+  if (r) {
+    for (auto& x : st) marfa_free_lines(x.L);
+    return r;
+  }
+  for (int32_t q = 0; q < n_req; ++q) out[q] = st[q].L;
   return MARFA_OK;
 }
 
@@ -762,6 +840,9 @@ extern "C" int64_t marfa_num_points(double nu_lo, double nu_hi) {
 constexpr int kNClasses = 2;
 constexpr int64_t kNarrowPts = 16 * 2048 + 1;
 constexpr int kG1Splits[4] = {1, 2, 3, 6};
+// The grid-1 split of calls without tuning, per size class: what the autotuner chooses on
+// the uneven batch for its narrow requests (2) and on the Venus window (6).
+constexpr int kG1DefaultSplit[2] = {2, 6};
 
 struct Plan {
   const marfa_lines_t* lines = nullptr;
@@ -772,8 +853,6 @@ struct Plan {
   ReqDev rd{};
   int64_t npts = 0;
   int req_idx = 0;
-  std::vector<G1Item> g1;     // grid-1 items with kG1Split parts (the no-alloc path's)
-  std::vector<FineItem> fine;
   int cls = 0;                // size class: 0 narrow window, 1 wide (kernel choices per class)
   PrepArgs prep{};            // level-preparation launch, filled by upload()
   // device buffers
@@ -969,16 +1048,52 @@ static int build_plan(Plan& P, const marfa_lines_t* L, const marfa_level_t* leve
   R.g1_split = kG1Split;
   P.cls = P.npts <= kNarrowPts ? 0 : 1;
   (void)physical;
-  // work lists: grid 1 in tiles of kG1Pairs pairs and the finest grid in tiles of
-  // kFineTile nodes; grids 2..10 follow the kernel variant chosen per grid (coarse_items)
   P.req_idx = req_idx;
-  for (int l = 0; l < n_levels; ++l)
-    for (int64_t m0 = R.m_first[1]; m0 <= R.m_first[1] + R.npan[1]; m0 += kG1Pairs)
-      for (int part = 0; part < kG1Split; ++part) P.g1.push_back(G1Item{req_idx, l, m0, part, 0});
-  const int64_t kb0 = R.k_lo & ~(int64_t)7;  // tiles start on a G10 panel
-  for (int l = 0; l < n_levels; ++l)
-    for (int64_t k0 = kb0; k0 <= R.k_hi; k0 += kFineTile) P.fine.push_back(FineItem{req_idx, l, k0});
   return MARFA_OK;
+}
+
+// The work items of a plan: grid 1 in tiles of kG1Pairs pairs (each in `split` parts),
+// grids 2..10 in tiles of their kernel variant's pairs (variant_pairs), the finest grid in
+// tiles of kFineTile nodes starting on a G10 panel; every level, level-major. Each kind
+// as an ExpandDesc (base, step, tiles per level), written by the device or, for the
+// no-alloc path and the counting runs, by expand_on_host.
+static int64_t variant_pairs(int v);
+static ExpandDesc plan_desc(const Plan& P, int kind, int v_or_split) {
+  const ReqDev& R = P.rd;
+  ExpandDesc d{};
+  d.kind = kind;
+  d.req = P.req_idx;
+  d.n_levels = P.n_levels;
+  d.split = kind == 1 ? v_or_split : 1;
+  if (kind == 1) {
+    d.base = R.m_first[1];
+    d.step = kG1Pairs;
+    d.tiles = R.npan[1] / kG1Pairs + 1;
+  } else if (kind <= kNGrid) {
+    d.base = R.m_first[kind];
+    d.step = variant_pairs(v_or_split);
+    d.tiles = R.npan[kind] / d.step + 1;
+  } else {
+    d.base = R.k_lo & ~(int64_t)7;
+    d.step = kFineTile;
+    d.tiles = (R.k_hi - d.base) / kFineTile + 1;
+  }
+  return d;
+}
+static int64_t desc_count(const ExpandDesc& d) { return d.tiles * d.split * d.n_levels; }
+template <class Item>
+static void expand_on_host(const ExpandDesc& d, std::vector<Item>& out) {
+  for (int l = 0; l < d.n_levels; ++l)
+    for (int64_t t = 0; t < d.tiles; ++t)
+      for (int part = 0; part < d.split; ++part) {
+        const int64_t pos = d.base + t * d.step;
+        if constexpr (std::is_same<Item, G1Item>::value)
+          out.push_back(G1Item{d.req, l, pos, part, 0});
+        else if constexpr (std::is_same<Item, CoarseItem>::value)
+          out.push_back(CoarseItem{d.req, l, d.kind, 0, pos});
+        else
+          out.push_back(FineItem{d.req, l, pos});
+      }
 }
 
 static bool is_device_ptr(const void* p) {
@@ -1123,6 +1238,9 @@ struct WorkSet {
   std::vector<ReqDev> rds;
   // items of each kind (1 grid 1, 2..10 grids, 11 finest), class 0 first then class 1:
   // kind k's class-c items are first[k][c] .. first[k][c + 1] - 1
+  size_t n_gi = 0, n_ci[kNGrid + 1] = {}, n_fi = 0;  // items of grid 1, grids 2..10, the finest
+  std::vector<ExpandDesc> desc;  // the items, written on the device (launch_expand_items)
+  // host copies of the items, made for counting runs only (read_counts)
   std::vector<G1Item> gi;
   std::vector<CoarseItem> ci[kNGrid + 1];  // grids 2..10
   std::vector<FineItem> fi;
@@ -1154,13 +1272,13 @@ static void free_work(WorkSet& W, cudaStream_t st) {
 }
 
 // Build the work lists of plans with the kernel choices tune[class] (NULL: the defaults
-// for every class: grid-1 split kG1Split), allocate their device copies (plus count
-// buffers when count) and upload.
+// for every class: grid-1 split kG1DefaultSplit), allocate their device copies (plus
+// count buffers when count) and upload.
 static int build_work(std::vector<Plan>& plans, const int (*tune)[kNGrid + 2], bool count, WorkSet& W,
                       cudaStream_t st) {
   for (int c = 0; c < kNClasses; ++c)
     for (int k = 1; k <= kNGrid + 1; ++k)
-      W.tune[c][k] = tune ? tune[c][k] : (k == 1 ? kG1Split : default_variant(k));
+      W.tune[c][k] = tune ? tune[c][k] : (k == 1 ? kG1DefaultSplit[c] : default_variant(k));
   for (auto& P : plans) {
     W.rds.push_back(P.rd);
     W.rds.back().g1_split = W.tune[P.cls][1];
@@ -1171,40 +1289,48 @@ static int build_work(std::vector<Plan>& plans, const int (*tune)[kNGrid + 2], b
     if ((R.wide != 0) != W.wide)
       return fail(MARFA_E_INVAL, "the requests of one call or plan must share one stencil");
   for (int g = 1; g <= kNGrid + 1; ++g) W.surr_grid[g] = W.surr;
+  // items in order: class, then request, then kind; kind k's class-c items are
+  // first[k][c] .. first[k][c + 1] - 1
+  size_t at[kNGrid + 2] = {};
   for (int c = 0; c < kNClasses; ++c) {
-    W.first[1][c] = W.gi.size();
-    for (int g = 2; g <= kNGrid; ++g) W.first[g][c] = W.ci[g].size();
-    W.first[kNGrid + 1][c] = W.fi.size();
+    for (int k = 1; k <= kNGrid + 1; ++k) W.first[k][c] = at[k];
     for (auto& P : plans) {
       if (P.cls != c) continue;
-      const ReqDev& R = P.rd;
-      for (int l = 0; l < P.n_levels; ++l)
-        for (int64_t m0 = R.m_first[1]; m0 <= R.m_first[1] + R.npan[1]; m0 += kG1Pairs)
-          for (int part = 0; part < W.tune[c][1]; ++part) W.gi.push_back(G1Item{P.req_idx, l, m0, part, 0});
-      for (int g = 2; g <= kNGrid; ++g) coarse_items(P, g, W.tune[c][g], W.ci[g]);
-      W.fi.insert(W.fi.end(), P.fine.begin(), P.fine.end());
+      for (int k = 1; k <= kNGrid + 1; ++k) {
+        ExpandDesc d = plan_desc(P, k, k == kNGrid + 1 ? 0 : W.tune[c][k]);
+        d.dst = reinterpret_cast<void*>(at[k]);  // the item index for now; a pointer below
+        at[k] += (size_t)desc_count(d);
+        if (desc_count(d) > 0) W.desc.push_back(d);
+        if (count) {
+          if (k == 1) expand_on_host(d, W.gi);
+          else if (k <= kNGrid) expand_on_host(d, W.ci[k]);
+          else expand_on_host(d, W.fi);
+        }
+      }
     }
   }
-  W.first[1][kNClasses] = W.gi.size();
-  for (int g = 2; g <= kNGrid; ++g) W.first[g][kNClasses] = W.ci[g].size();
-  W.first[kNGrid + 1][kNClasses] = W.fi.size();
+  for (int k = 1; k <= kNGrid + 1; ++k) W.first[k][kNClasses] = at[k];
+  W.n_gi = at[1];
+  for (int g = 2; g <= kNGrid; ++g) W.n_ci[g] = at[g];
+  W.n_fi = at[kNGrid + 1];
   W.prep_first.push_back(0);
   for (auto& P : plans) {
     W.prep.push_back(P.prep);
     W.prep_first.push_back(W.prep_first.back() + (P.prep.n + 255) / 256 * P.n_levels);
   }
   if (W.prep_first.back() > 0x7fffffff) return fail(MARFA_E_INVAL, "too many (level, line) pairs in one call");
-  size_t total_items = W.gi.size() + W.fi.size();
-  for (int g = 2; g <= kNGrid; ++g) total_items += W.ci[g].size();
-  if (W.gi.size() > 0x7fffffffu || W.fi.size() > 0x7fffffffu || total_items > ((size_t)1 << 34))
+  size_t total_items = W.n_gi + W.n_fi;
+  for (int g = 2; g <= kNGrid; ++g) total_items += W.n_ci[g];
+  if (W.n_gi > 0x7fffffffu || W.n_fi > 0x7fffffffu || total_items > ((size_t)1 << 34) ||
+      W.desc.size() > 0x7fffffffu)
     return fail(MARFA_E_INVAL, "too much work in one call");
   for (int g = 2; g <= kNGrid; ++g)
-    if (W.ci[g].size() > 0x7fffffffu) return fail(MARFA_E_INVAL, "too much work in one call");
+    if (W.n_ci[g] > 0x7fffffffu) return fail(MARFA_E_INVAL, "too much work in one call");
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t cw = count ? W.cw : 0;
-  size_t sz = al(sizeof(ReqDev) * W.rds.size()) + al(sizeof(G1Item) * W.gi.size()) +
-              al(sizeof(FineItem) * W.fi.size()) + al(cw * W.gi.size()) + al(cw * W.fi.size());
-  for (int g = 2; g <= kNGrid; ++g) sz += al(sizeof(CoarseItem) * W.ci[g].size()) + al(cw * W.ci[g].size());
+  size_t sz = al(sizeof(ReqDev) * W.rds.size()) + al(sizeof(G1Item) * W.n_gi) + al(sizeof(FineItem) * W.n_fi) +
+              al(cw * W.n_gi) + al(cw * W.n_fi) + al(sizeof(ExpandDesc) * W.desc.size());
+  for (int g = 2; g <= kNGrid; ++g) sz += al(sizeof(CoarseItem) * W.n_ci[g]) + al(cw * W.n_ci[g]);
   sz += al(sizeof(PrepArgs) * W.prep.size()) + al(sizeof(int64_t) * W.prep_first.size());
   int r = dev_alloc(&W.buf, sz, st);
   if (r) return r;
@@ -1215,30 +1341,37 @@ static int build_work(std::vector<Plan>& plans, const int (*tune)[kNGrid + 2], b
     return q;
   };
   W.drd = (ReqDev*)take(sizeof(ReqDev) * W.rds.size());
-  W.dgi = (G1Item*)take(sizeof(G1Item) * W.gi.size());
-  W.dfi = (FineItem*)take(sizeof(FineItem) * W.fi.size());
-  for (int g = 2; g <= kNGrid; ++g) W.dci[g] = (CoarseItem*)take(sizeof(CoarseItem) * W.ci[g].size());
+  W.dgi = (G1Item*)take(sizeof(G1Item) * W.n_gi);
+  W.dfi = (FineItem*)take(sizeof(FineItem) * W.n_fi);
+  for (int g = 2; g <= kNGrid; ++g) W.dci[g] = (CoarseItem*)take(sizeof(CoarseItem) * W.n_ci[g]);
   W.dprep = (PrepArgs*)take(sizeof(PrepArgs) * W.prep.size());
   W.dprep_first = (int64_t*)take(sizeof(int64_t) * W.prep_first.size());
+  ExpandDesc* ddesc = (ExpandDesc*)take(sizeof(ExpandDesc) * W.desc.size());
   if (count) {
-    W.dgc = (int64_t*)take(cw * W.gi.size());
-    W.dfc = (int64_t*)take(cw * W.fi.size());
-    for (int g = 2; g <= kNGrid; ++g) W.dcc[g] = (int64_t*)take(cw * W.ci[g].size());
+    W.dgc = (int64_t*)take(cw * W.n_gi);
+    W.dfc = (int64_t*)take(cw * W.n_fi);
+    for (int g = 2; g <= kNGrid; ++g) W.dcc[g] = (int64_t*)take(cw * W.n_ci[g]);
+  }
+  for (auto& d : W.desc) {  // item index -> device address of the kind's array
+    const size_t i = reinterpret_cast<size_t>(d.dst);
+    d.dst = d.kind == 1 ? (void*)(W.dgi + i) : (d.kind <= kNGrid ? (void*)(W.dci[d.kind] + i) : (void*)(W.dfi + i));
   }
   cudaError_t e = cudaSuccess;
   auto up = [&](void* d, const void* h, size_t b) {
     if (!e && b) e = cudaMemcpyAsync(d, h, b, cudaMemcpyHostToDevice, st);
   };
   up(W.drd, W.rds.data(), sizeof(ReqDev) * W.rds.size());
-  up(W.dgi, W.gi.data(), sizeof(G1Item) * W.gi.size());
-  up(W.dfi, W.fi.data(), sizeof(FineItem) * W.fi.size());
-  for (int g = 2; g <= kNGrid; ++g) up(W.dci[g], W.ci[g].data(), sizeof(CoarseItem) * W.ci[g].size());
+  up(ddesc, W.desc.data(), sizeof(ExpandDesc) * W.desc.size());
   up(W.dprep, W.prep.data(), sizeof(PrepArgs) * W.prep.size());
   up(W.dprep_first, W.prep_first.data(), sizeof(int64_t) * W.prep_first.size());
+  if (!e) {
+    launch_expand_items(ddesc, (int)W.desc.size(), st);
+    e = cudaGetLastError();
+  }
   if (!e && count) {
-    e = cudaMemsetAsync(W.dgc, 0, cw * W.gi.size(), st);
-    if (!e) e = cudaMemsetAsync(W.dfc, 0, cw * W.fi.size(), st);
-    for (int g = 2; g <= kNGrid && !e; ++g) e = cudaMemsetAsync(W.dcc[g], 0, cw * W.ci[g].size(), st);
+    e = cudaMemsetAsync(W.dgc, 0, cw * W.n_gi, st);
+    if (!e) e = cudaMemsetAsync(W.dfc, 0, cw * W.n_fi, st);
+    for (int g = 2; g <= kNGrid && !e; ++g) e = cudaMemsetAsync(W.dcc[g], 0, cw * W.n_ci[g], st);
   }
   if (e) {
     free_work(W, st);
@@ -1361,6 +1494,15 @@ static int run_plans(std::vector<Plan>& plans, cudaStream_t st, std::vector<int6
   WorkSet W;
   int r = build_work(plans, nullptr, counts != nullptr, W, st);
   if (r) return r;
+  // the level preparation: one launch for all requests of a batch (each alone would fill
+  // the GPU poorly), the request's own for one
+  if (plans.size() > 1) {
+    cudaEvent_t ev = timing_begin(st);
+    launch_level_prep_batch(W.dprep, W.dprep_first, (int)plans.size(), W.prep_first.back(), st);
+    timing_end(ev, 0, st);
+  } else {
+    launch_prep(plans[0], st, true);
+  }
   r = launch_work(W, st, true);
   if (!r && counts) r = read_counts(W, plans, st, counts);
   free_work(W, st);
@@ -1394,7 +1536,7 @@ static int absorption_impl(int32_t n_req, const marfa_lines_t* const* lines,
     if (r) return r;
   }
   for (int q = 0; q < n_req; ++q) {
-    int r = upload_and_prep(plans[q], k_out[q], st);
+    int r = upload(plans[q], k_out[q], st);
     if (r) {
       for (auto& P : plans) release(P, st);
       return r;
@@ -1522,7 +1664,7 @@ static int plan_autotune(marfa_plan_t* X, cudaStream_t st, int (*chosen)[kNGrid 
   };
   for (int c = 0; c < kNClasses && !r; ++c) {
     if (!present[c]) {
-      for (int k = 1; k <= kNGrid + 1; ++k) chosen[c][k] = k == 1 ? kG1Split : default_variant(k);
+      for (int k = 1; k <= kNGrid + 1; ++k) chosen[c][k] = k == 1 ? kG1DefaultSplit[c] : default_variant(k);
       continue;
     }
     for (int k = 0; k < NS && !r; ++k) r = time3([&] { launch_grid1(B[k], c, st); }, &X->tune_ms[c][1][k]);
@@ -1622,7 +1764,7 @@ extern "C" int marfa_plan_create(int32_t n_req, const marfa_lines_t* const* line
   }
   int chosen[kNClasses][kNGrid + 2];
   for (int c = 0; c < kNClasses; ++c)
-    for (int g = 0; g <= kNGrid + 1; ++g) chosen[c][g] = g == 1 ? kG1Split : default_variant(g);
+    for (int g = 0; g <= kNGrid + 1; ++g) chosen[c][g] = g == 1 ? kG1DefaultSplit[c] : default_variant(g);
   if (!r && autotune) {
     for (auto& P : X->plans) launch_prep(P, st, false);
     r = plan_autotune(X, st, chosen);
@@ -1895,8 +2037,12 @@ extern "C" int marfa_absorption_noalloc(const marfa_lines_t* lines, const marfa_
   for (int g = 0; g <= kNGrid + 1; ++g) var[g] = default_variant(g);
   std::vector<CoarseItem> coarse;  // grids 2..10 in order
   for (int g = 2; g <= kNGrid; ++g) coarse_items(P, g, var[g], coarse);
-  const size_t sz_r = al(sizeof(ReqDev)), sz_gi = al(sizeof(G1Item) * P.g1.size()),
-               sz_ci = al(sizeof(CoarseItem) * coarse.size()), sz_fi = al(sizeof(FineItem) * P.fine.size());
+  std::vector<G1Item> g1items;  // grid 1 with kG1Split parts (R.g1_split), the finest grid
+  std::vector<FineItem> fine;
+  expand_on_host(plan_desc(P, 1, kG1Split), g1items);
+  expand_on_host(plan_desc(P, kNGrid + 1, 0), fine);
+  const size_t sz_r = al(sizeof(ReqDev)), sz_gi = al(sizeof(G1Item) * g1items.size()),
+               sz_ci = al(sizeof(CoarseItem) * coarse.size()), sz_fi = al(sizeof(FineItem) * fine.size());
   const size_t total = sz_c + 3 * sz_f + 2 * sz_b + sz_slots + sz_lev + sz_ls + sz_r + sz_gi + sz_ci + sz_fi;
   if (total > kNoAllocBytes)
     return fail(MARFA_E_INVAL, "request needs %zu bytes of scratch; marfa_absorption_noalloc holds %zu",
@@ -1923,9 +2069,9 @@ extern "C" int marfa_absorption_noalloc(const marfa_lines_t* lines, const marfa_
   CK(cudaMemcpyAsync(dlev, P.lev.data(), sizeof(LevelDev) * nl, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(dls, P.ls.data(), sizeof(LevelSpeciesDev) * nl * ns, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(drd, &R, sizeof(ReqDev), cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(dgi, P.g1.data(), sizeof(G1Item) * P.g1.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dgi, g1items.data(), sizeof(G1Item) * g1items.size(), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(dci, coarse.data(), sizeof(CoarseItem) * coarse.size(), cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(dfi, P.fine.data(), sizeof(FineItem) * P.fine.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dfi, fine.data(), sizeof(FineItem) * fine.size(), cudaMemcpyHostToDevice, st));
   PrepArgs a;
   a.n = n;
   a.nu0 = L->nu0; a.S296 = L->S296; a.ga = L->ga; a.gs = L->gs; a.E = L->E; a.na = L->na; a.da = L->da;
@@ -1941,7 +2087,7 @@ extern "C" int marfa_absorption_noalloc(const marfa_lines_t* lines, const marfa_
   launch_level_prep(a, (int)nl, st);
   const bool surr = R.mlp != nullptr;
   const bool wide = P.rd.wide != 0;
-  launch_g1(drd, dgi, (int)P.g1.size(), nullptr, surr, wide, st);
+  launch_g1(drd, dgi, (int)g1items.size(), nullptr, surr, wide, st);
   size_t k = 0;
   for (int g = 2; g <= kNGrid; ++g) {  // coarse is ordered by grid
     size_t k1 = k;
@@ -1960,10 +2106,10 @@ extern "C" int marfa_absorption_noalloc(const marfa_lines_t* lines, const marfa_
   if (var[kFineKind] >= 1 && !surr) {
     const bool mech = var[kFineKind] >= 2 && !wide && ((R.mech >> (kNGrid + 1)) & 1);
     const bool merge = var[kFineKind] == 3 && ((R.mech >> (kNGrid + 2)) & 1);
-    launch_fine_jobs(drd, dfi, (int)P.fine.size(), nullptr, wide, mech ? (merge ? 2 : 1) : 0, st);
+    launch_fine_jobs(drd, dfi, (int)fine.size(), nullptr, wide, mech ? (merge ? 2 : 1) : 0, st);
   }
   else
-    launch_fine(drd, dfi, (int)P.fine.size(), nullptr, surr, wide, st);
+    launch_fine(drd, dfi, (int)fine.size(), nullptr, surr, wide, st);
   CK(cudaGetLastError());
   return debug_checks();
 }

@@ -131,6 +131,18 @@ struct G1Item {
   int32_t part, pad;
 };
 
+// The work items of one (request, kind) for the device to write (launch_expand_items):
+// n_levels x tiles x split items, level-major, then tile, then part, the same order as
+// the host loops would write them. kind 1: G1Item (m0 = base + tile step, part);
+// 2..10: CoarseItem of that grid (m0 = base + tile step); 11: FineItem (k0 = base +
+// tile step).
+struct ExpandDesc {
+  int32_t kind, req, n_levels, split;
+  int64_t base, step, tiles;
+  void* dst;  // the first item
+};
+void launch_expand_items(const ExpandDesc* d, int n, cudaStream_t st);
+
 constexpr int kG1Pairs = 32;         // node pairs per G1 tile (one per lane)
 constexpr int kG1Split = 6;          // at most this many CTAs share one G1 tile's candidate
                                      // lines (ReqDev::g1_split, tuned); each writes its own

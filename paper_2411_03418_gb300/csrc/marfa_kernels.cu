@@ -2618,6 +2618,32 @@ void launch_fine(const ReqDev* reqs, const FineItem* items, int n_items, int64_t
   }
 }
 
+// ------------------------------------------------------------------ work lists
+// One CTA per descriptor writes its items (see ExpandDesc): the work lists of a call are
+// made on the device from a few descriptors per request instead of being built on the
+// host and copied.
+__global__ void __launch_bounds__(256) k_expand_items(const ExpandDesc* __restrict__ ds) {
+  const ExpandDesc d = ds[blockIdx.x];
+  const int64_t per_level = d.tiles * d.split, count = per_level * d.n_levels;
+  for (int64_t i = threadIdx.x; i < count; i += blockDim.x) {
+    const int l = (int)(i / per_level);
+    const int64_t r = i - (int64_t)l * per_level;
+    const int64_t t = r / d.split;
+    const int part = (int)(r - t * d.split);
+    const int64_t pos = d.base + t * d.step;
+    if (d.kind == 1)
+      static_cast<G1Item*>(d.dst)[i] = G1Item{d.req, l, pos, part, 0};
+    else if (d.kind <= kNGrid)
+      static_cast<CoarseItem*>(d.dst)[i] = CoarseItem{d.req, l, d.kind, 0, pos};
+    else
+      static_cast<FineItem*>(d.dst)[i] = FineItem{d.req, l, pos};
+  }
+}
+
+void launch_expand_items(const ExpandDesc* d, int n, cudaStream_t st) {
+  if (n > 0) k_expand_items<<<n, 256, 0, st>>>(d);
+}
+
 // ------------------------------------------------------------------ diagnostics
 __global__ void k_diag_voigt(const float* x, const float* y, float* out, int64_t n) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

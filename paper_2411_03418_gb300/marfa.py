@@ -50,7 +50,7 @@ EXPORTS = ["marfa_prepare_lines", "marfa_free_lines", "marfa_num_points", "marfa
            "marfa_plan_info", "marfa_plan_destroy", "marfa_diag_absorption_counts", "marfa_read_par",
            "marfa_diag_pipe_rate", "marfa_diag_line_order", "marfa_diag_shape", "marfa_diag_variants",
            "marfa_diag_fail_alloc", "marfa_diag_device_memory", "marfa_diag_check",
-           "marfa_plan_classes", "marfa_shape_user_set"]
+           "marfa_plan_classes", "marfa_shape_user_set", "marfa_prepare_lines_batch"]
 
 MLP_PARAMS = 8577
 MLP_MAX_BATCH = 65536
@@ -78,6 +78,7 @@ def load(path: str | None = None):
     vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
     sig = {
         "marfa_prepare_lines": (C.c_int, [vp, i64, vp, i32, C.POINTER(vp)]),
+        "marfa_prepare_lines_batch": (C.c_int, [i32, vp, vp, vp, vp, vp]),
         "marfa_free_lines": (None, [vp]),
         "marfa_num_points": (i64, [dbl, dbl]),
         "marfa_absorption": (C.c_int, [vp, vp, vp, i32, vp, vp, vp]),
@@ -162,6 +163,21 @@ def marfa_prepare_lines(lines: np.ndarray, species: np.ndarray) -> Lines:
     h = C.c_void_p()
     _check(load().marfa_prepare_lines(_ptr(lines), len(lines), _ptr(species), len(species), C.byref(h)))
     return Lines(h, len(lines), len(species))
+
+
+def marfa_prepare_lines_batch(line_lists, species_lists) -> list:
+    """Several line lists at once (marfa_prepare_lines_batch): one Lines per request."""
+    ls = [np.ascontiguousarray(x, dtype=LINE_DTYPE) for x in line_lists]
+    ss = [np.ascontiguousarray(x, dtype=SPECIES_DTYPE) for x in species_lists]
+    q = len(ls)
+    assert q == len(ss) and q >= 1
+    lp = (C.c_void_p * q)(*[x.ctypes.data for x in ls])
+    sp = (C.c_void_p * q)(*[x.ctypes.data for x in ss])
+    n = np.array([len(x) for x in ls], dtype=np.int64)
+    ns = np.array([len(x) for x in ss], dtype=np.int32)
+    out = (C.c_void_p * q)()
+    _check(load().marfa_prepare_lines_batch(q, lp, _ptr(n), sp, _ptr(ns), out))
+    return [Lines(C.c_void_p(out[i]), len(ls[i]), len(ss[i])) for i in range(q)]
 
 
 def marfa_free_lines(lines: Lines) -> None:

@@ -37,8 +37,9 @@ def _exhaust(M, call, what, device_free=False):
     """Arm the injector at n = 1, 2, ... until `call` succeeds; returns (allocations
     the call makes, its result). Every failing run must raise MARFA_E_NOMEM and leave
     the device pool's bytes in use as they were (and, with device_free, the free device
-    memory: for the line list's plain cudaMalloc; the pool keeps what it has reserved,
-    so the free memory is no leak measure for pool allocations)."""
+    memory too: for calls whose failing runs must not reserve device memory at all; the
+    pool keeps what it has reserved, so the free memory is no leak measure once a call
+    has taken pool memory)."""
     import gc
     gc.collect()
     used, free = M.marfa_diag_device_memory()
@@ -88,6 +89,13 @@ def test_every_entry_point_fails_cleanly_and_recovers(M):
     for out, name in ((dev, "device output"), (pageable, "pageable host output"), (pinned, "pinned host output")):
         k, got = _exhaust(M, lambda: _direct(M, lines, WL, out), f"marfa_absorption, {name}")
         assert k >= 2 and np.array_equal(got, ref), name
+    def prep_batch():
+        got = M.marfa_prepare_lines_batch([WL.lines, WL2.lines, WL.lines], [WL.species, WL2.species, WL.species])
+        assert len(got) == 3
+        return got
+    k, made = _exhaust(M, prep_batch, "marfa_prepare_lines_batch")
+    assert k >= 9  # three lists: object, host staging buffer, device block each
+    del made
     lines2 = M.marfa_prepare_lines(WL2.lines, WL2.species)
     outs = [np.empty((w.n_levels, M.marfa_num_points(w.nu_lo, w.nu_hi)), np.float32) for w in (WL, WL2)]
 

@@ -305,3 +305,27 @@ def test_size_classes_tuned_apart(M):
             check(got[lev], ref[q][lev], np.abs(got[lev]).max(), f"request {q} level {lev} vs batch")
             check(got[lev], O.eleven_grid(w, lev), np.abs(got[lev]).max(), f"request {q} level {lev}")
     M.marfa_plan_destroy(plan)
+
+
+def test_batch_preparation_equals_single_preparation(M):
+    """marfa_prepare_lines_batch gives every request the list marfa_prepare_lines makes:
+    the batch computed from either set of handles is the same bit for bit. A request with
+    an invalid record fails the whole call, naming that request, with nothing held."""
+    wls = [tiny_workload(300 + q, 150 + 40 * q, 1500.0 + 3 * q, 1501.2 + 3 * q, 25.0, T=(296.0, 200.0),
+                         p=(1.0, 1e-3), chi="tonkov", chi_species=1) for q in range(5)]
+    single = [M.marfa_prepare_lines(w.lines, w.species) for w in wls]
+    batch = M.marfa_prepare_lines_batch([w.lines for w in wls], [w.species for w in wls])
+    outs = []
+    for handles in (single, batch):
+        o = [np.empty((w.n_levels, M.marfa_num_points(w.nu_lo, w.nu_hi)), np.float32) for w in wls]
+        M.marfa_absorption_batch(handles, [M.levels_of(w) for w in wls], [w.vmr for w in wls],
+                                 [M.request_of(w) for w in wls], o)
+        outs.append(o)
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+    used0 = M.marfa_diag_device_memory()[0]
+    bad = wls[3].lines.copy()
+    bad["nu0"][7] = np.nan
+    with pytest.raises(M.MarfaError, match="request 3"):
+        M.marfa_prepare_lines_batch([w.lines for w in wls[:3]] + [bad, wls[4].lines], [w.species for w in wls])
+    assert M.marfa_diag_device_memory()[0] == used0
