@@ -1134,9 +1134,9 @@ constexpr int kNVariants = 6;
 constexpr int kFineKind = kNGrid + 1;
 constexpr int kNFineVariants = 4;
 // Defaults measured on the Venus workload (line-major over 16 pairs on grids 2..7, the
-// mechanism kernel on 8..10, flattened jobs by mechanism with the merged edge and
-// breakpoint pass on the finest grid).
-static std::atomic<int> g_default_variant[kNGrid + 2] = {{-1}, {-1}, {2}, {2}, {2}, {2}, {2}, {2}, {4}, {4}, {4}, {3}};
+// mechanism kernel on 8..10, flattened jobs by mechanism, a pass per mechanism, on the
+// finest grid).
+static std::atomic<int> g_default_variant[kNGrid + 2] = {{-1}, {-1}, {2}, {2}, {2}, {2}, {2}, {2}, {4}, {4}, {4}, {2}};
 static int default_variant(int g) { return g_default_variant[g].load(std::memory_order_relaxed); }
 static int64_t variant_pairs(int v) {
   return v == 0 ? (int64_t)kLPairs : (v == 2 ? (int64_t)16 : (int64_t)kCPairs * kCWarps);

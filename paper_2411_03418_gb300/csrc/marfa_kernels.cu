@@ -1511,16 +1511,14 @@ __global__ void __launch_bounds__(kCWarps * 32, 6)
     }
     for (int pass = 0; pass < npass; ++pass) {  // warp-uniform
       const int64_t off = pass_off(pass);
+      // a pass per mechanism: one range of candidates (first line r_lo), kept in
+      // registers; merged: the bands of all mechanisms
       Bands bd;
       bd.n = 0;
+      int64_t r_lo = 0, r_n = 0;
       if (!MERGED) {
-        const int64_t a = __shfl_sync(0xffffffffu, range_v, 2 * pass);
-        const int64_t b = __shfl_sync(0xffffffffu, range_v, 2 * pass + 1);
-        if (a < b) {
-          bd.lo[0] = a;
-          bd.hi[0] = b;
-          bd.n = 1;
-        }
+        r_lo = __shfl_sync(0xffffffffu, range_v, 2 * pass);
+        r_n = max(__shfl_sync(0xffffffffu, range_v, 2 * pass + 1) - r_lo, (int64_t)0);
       } else {
         int64_t zlo[9], zhi[9];
         int nz = 0;
@@ -1534,11 +1532,11 @@ __global__ void __launch_bounds__(kCWarps * 32, 6)
         }
         bd.lookup(R, L, zlo, zhi, nz);
       }
-      const int64_t n_cand = bd.total();
+      const int64_t n_cand = MERGED ? bd.total() : r_n;
       BandCursor cur;
       for (int64_t t0 = 0; t0 < n_cand; t0 += 32) {  // warp-uniform
         const bool valid = t0 + lane < n_cand;
-        const int64_t i = valid ? cur.line(bd, t0 + lane) : 0;
+        const int64_t i = valid ? (MERGED ? cur.line(bd, t0 + lane) : r_lo + t0 + lane) : 0;
         uint64_t own = 0;
         int64_t c = 0;
         bool chi = false;
@@ -2377,15 +2375,13 @@ __global__ void __launch_bounds__(kFineThreads, 4)
   }
   for (int pass = 0; pass < npass && wlo <= whi; ++pass) {  // warp-uniform
     const int64_t off = pass_off(pass);
-    if (MECH == 1 || (MECH == 2 && pass == 0)) {
-      const int64_t a = __shfl_sync(0xffffffffu, range_v, 2 * pass);
-      const int64_t b = __shfl_sync(0xffffffffu, range_v, 2 * pass + 1);
-      bd.n = 0;
-      if (a < b) {
-        bd.lo[0] = a;
-        bd.hi[0] = b;
-        bd.n = 1;
-      }
+    // one mechanism: one range of candidates (first line r_lo) kept in registers;
+    // otherwise the bands
+    const bool one_range = MECH == 1 || (MECH == 2 && pass == 0);
+    int64_t r_lo = 0, r_n = 0;
+    if (one_range) {
+      r_lo = __shfl_sync(0xffffffffu, range_v, 2 * pass);
+      r_n = max(__shfl_sync(0xffffffffu, range_v, 2 * pass + 1) - r_lo, (int64_t)0);
     } else if (MECH == 2) {  // the edges' and breakpoints' ranges, merged
       bd.n = 0;
       for (int q = 1; q < nmech; ++q) {
@@ -2404,12 +2400,12 @@ __global__ void __launch_bounds__(kFineThreads, 4)
     const bool physical = R.shape < kShapeConst;
     const bool voigt = R.shape == kShapeVoigt;
     const int gi = lane >> 3, t8 = lane & 7;
-    const int64_t n_cand = bd.total();
+    const int64_t n_cand = one_range ? r_n : bd.total();
     BandCursor cur;
     uint16_t* jobs = sJob[warp];
     for (int64_t t0 = 0; t0 < n_cand; t0 += 32) {  // warp-uniform
       const bool valid = t0 + lane < n_cand;
-      const int64_t i = valid ? cur.line(bd, t0 + lane) : 0;
+      const int64_t i = valid ? (one_range ? r_lo + t0 + lane : cur.line(bd, t0 + lane)) : 0;
       // the line's data with its position (consecutive lines: coalesced), so that a
       // candidate costs one round trip to memory
       float amp_p = 0.0f, sx_p = 0.0f, y_p = 0.0f;
