@@ -187,6 +187,29 @@ struct BandCursor {
   }
 };
 
+// The same walk over bands copied to shared memory (the CTA's copy, sb): the current
+// band's bounds stay in registers and only a band change reads shared memory, so the
+// per-candidate walk makes no local-memory access.
+struct SharedBandCursor {
+  int r = 0;
+  int64_t start = 0, blo = 0, blen = 0;
+  __device__ __forceinline__ void init(const int64_t* sb_lo, const int64_t* sb_hi, int n) {
+    if (n > 0) {
+      blo = sb_lo[0];
+      blen = sb_hi[0] - sb_lo[0];
+    }
+  }
+  __device__ __forceinline__ int64_t line(const int64_t* sb_lo, const int64_t* sb_hi, int64_t t) {
+    while (t - start >= blen) {
+      start += blen;
+      ++r;
+      blo = sb_lo[r];
+      blen = sb_hi[r] - sb_lo[r];
+    }
+    return blo + (t - start);
+  }
+};
+
 // Position zones where a line centre must lie for the line to own something in the
 // span [A, B]: within Rc of it (centre), at the cut-off distance (edges) or at a chi
 // breakpoint distance (kinks), each widened by the margin P.
@@ -950,6 +973,13 @@ __global__ void __launch_bounds__(kLWarps * 32, SURR ? 3 : (PAIRS == 16 ? 7 : 4)
     const int nz = make_zones(A, B, (int64_t)R.R_w * step_fx(g - 1), cut, P, R.chi_req, zlo, zhi);
     if (pa <= pb) bd.lookup(R, L, zlo, zhi, nz);
   }
+  // the bands in shared memory for the candidate walk (every warp looked them up alike)
+  __shared__ int64_t sb_lo[9], sb_hi[9];
+  if (tid < bd.n) {
+    sb_lo[tid] = bd.lo[tid];
+    sb_hi[tid] = bd.hi[tid];
+  }
+  __syncthreads();
   const int64_t lo_off = (int64_t)lev * R.n_lines;
   const int64_t X0 = m0 << s;  // position of node 2 m0 (j = 0)
   const int64_t xa_t = base << s, xb_t = (base + nb) << s;  // span of the mask's panels
@@ -975,11 +1005,12 @@ __global__ void __launch_bounds__(kLWarps * 32, SURR ? 3 : (PAIRS == 16 ? 7 : 4)
   };
   __syncwarp();
   const int64_t n_cand = bd.total();
-  BandCursor cur;
+  SharedBandCursor cur;
+  cur.init(sb_lo, sb_hi, bd.n);
   {
     for (int64_t t0 = 0; t0 < n_cand; t0 += kLWarps * 32) {  // block-uniform
       const bool valid = t0 + tid < n_cand;
-      const int64_t i = valid ? cur.line(bd, t0 + tid) : 0;
+      const int64_t i = valid ? cur.line(sb_lo, sb_hi, t0 + tid) : 0;
       if (SURR && use_mlp) {
         // all lanes step through the union of their pair ranges together; evaluations
         // that pass the guard go to the warp's queue
