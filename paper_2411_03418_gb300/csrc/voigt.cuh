@@ -109,6 +109,12 @@ __device__ __forceinline__ float voigt_cell(const float* tab, int cell, float u,
   return acc;
 }
 
+// A kernel's shared copy pads each small-y cell from 24 to 26 floats: cells a and b
+// then share a bank at the same coefficient only when a - b is a multiple of 16 (with
+// 24 floats, a multiple of 4), so the lane groups of a warp step that read different
+// cells rarely conflict.
+constexpr int kVoigtSmallCellSmem = 26;
+
 // One small-y cell (degree VOIGT_SMALL_DX in u, VOIGT_SMALL_DV = 3 in v: one row of four
 // coefficients per power of u, read from a shared copy as two float2).
 template <bool SMEM>
@@ -126,7 +132,7 @@ __device__ __forceinline__ float voigt_cell_small(const float* tab, int cell, fl
     }
     return acc;
   }
-  const float2* c2 = reinterpret_cast<const float2*>(tab + cell * (VOIGT_SMALL_DX + 1) * 4);
+  const float2* c2 = reinterpret_cast<const float2*>(tab + cell * kVoigtSmallCellSmem);
   float acc = 0.0f;
 #pragma unroll
   for (int p = VOIGT_SMALL_DX; p >= 0; --p) {
@@ -280,11 +286,12 @@ __device__ __forceinline__ int voigt_class(float x, float y) {
 }
 
 constexpr int kVoigtSmallFloats = VOIGT_SMALL_NX * (VOIGT_SMALL_DX + 1) * (VOIGT_SMALL_DV + 1);
-constexpr int kVoigtTableFloats = kVoigtBigFloats + kVoigtSmallFloats;
+constexpr int kVoigtTableFloats = kVoigtBigFloats + VOIGT_SMALL_NX * kVoigtSmallCellSmem;  // shared copy
+static_assert(kVoigtSmallCellSmem % 2 == 0 && kVoigtSmallCellSmem >= (VOIGT_SMALL_DX + 1) * 4, "small cell padding");
 
-// Copy both coefficient tables into shared memory, in the global layout (all threads of
-// the block take part: warp w copies cells w, w + nwarps, ..., lane by lane; then the
-// small-y table). dst: 16-byte aligned.
+// Copy both coefficient tables into shared memory (all threads of the block take part:
+// warp w copies cells w, w + nwarps, ..., lane by lane, in the global layout; then the
+// small-y cells, each padded to kVoigtSmallCellSmem floats). dst: 16-byte aligned.
 __device__ __forceinline__ void voigt_table_to_smem(float* dst) {
   const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int cell = threadIdx.x >> 5; cell < VOIGT_NCELL; cell += nw) {
@@ -293,7 +300,11 @@ __device__ __forceinline__ void voigt_table_to_smem(float* dst) {
 #pragma unroll
     for (int k = lane; k < kVoigtCellStride; k += 32) d[k] = src[k];
   }
-  for (int i = threadIdx.x; i < kVoigtSmallFloats; i += blockDim.x) dst[kVoigtBigFloats + i] = kVoigtSmall[i];
+  constexpr int cf = (VOIGT_SMALL_DX + 1) * 4;  // floats of a small-y cell
+  for (int i = threadIdx.x; i < VOIGT_SMALL_NX * kVoigtSmallCellSmem; i += blockDim.x) {
+    const int cell = i / kVoigtSmallCellSmem, k = i - cell * kVoigtSmallCellSmem;
+    dst[kVoigtBigFloats + i] = k < cf ? kVoigtSmall[cell * cf + k] : 0.0f;
+  }
 }
 
 }  // namespace marfa
