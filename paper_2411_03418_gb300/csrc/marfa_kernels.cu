@@ -273,6 +273,15 @@ struct ChiThr {
     const float r = b == 1 ? 0.027f : (b == 2 ? 0.016f : 0.009f);
     return C * __expf(-r * absd);
   }
+  // The same without a branch (the exponential always taken, 1 selected where the branch
+  // is 0): cheaper where the lanes of a warp fall on both sides of a breakpoint.
+  __device__ __forceinline__ float value_sel(int j, float absd) const {
+    const int b = branch(j);
+    const float C = b == 1 ? 1.084f : (b == 2 ? 0.208f : 0.025f);
+    const float r = b == 1 ? 0.027f : (b == 2 ? 0.016f : 0.009f);
+    const float e = C * __expf(-r * absd);
+    return b == 0 ? 1.0f : e;
+  }
 };
 
 // chi-factor along the nodes ja, ja + 1, ... of one line when its branch is the same at
@@ -802,21 +811,31 @@ __global__ void __launch_bounds__(kG1Warps * 32)
           if (COUNT) nmlp += (u0 ? 1 : 0) + (u1 ? 1 : 0);
           continue;
         }
-        if (!(bL || bR)) continue;
-        float v0, v1;
         if (!(C.z & 1)) {
+          // far wing, without branches: every lane evaluates both nodes and each sum
+          // takes a value only where the panels own the node (adding zero elsewhere
+          // leaves the sums as they were)
           const float4 a = sA[k], b = sB[k];
           const float x0 = fmaf(f0 + a.x, a.y, a.z), x02 = x0 * x0;
           const float i0 = __fdividef(1.0f, x02 + a.w);
           const float s0 = fmaf(fmaf(1.5f, x02, b.w), i0 * i0, 1.0f);
           const float am0 = j0 >= C.y ? b.z * rR0 : (j0 <= C.x ? b.y * rL0 : b.x);
-          v0 = am0 * i0 * s0;
+          const float v0 = am0 * i0 * s0;
           const float x1 = fmaf(f1 + a.x, a.y, a.z), x12 = x1 * x1;
           const float i1 = __fdividef(1.0f, x12 + a.w);
           const float s1 = fmaf(fmaf(1.5f, x12, b.w), i1 * i1, 1.0f);
           const float am1 = j0 + 1 >= C.y ? b.z * rR1 : (j0 + 1 <= C.x ? b.y * rL1 : b.x);
-          v1 = bL ? am1 * i1 * s1 : 0.0f;
-        } else {
+          const float v1 = am1 * i1 * s1;
+          pe += (bL && bR) ? v0 : 0.0f;
+          pl += (bL && !bR) ? v0 : 0.0f;
+          pr += (!bL && bR) ? v0 : 0.0f;
+          pm += bL ? v1 : 0.0f;
+          if (COUNT) nev += (bL || bR ? 1 : 0) + (bL ? 1 : 0);
+          continue;
+        }
+        if (!(bL || bR)) continue;
+        float v0, v1;
+        {
           int nn = 0, nm = 0, ns = 0;
           const float2 v = g1_exact_pair(R, off + b0 + k, X0, j0, true, bL, nn, nm, ns);
           v0 = v.x;
@@ -1522,7 +1541,7 @@ __global__ void __launch_bounds__(kCWarps * 32, 6)
     float (*bO)[kCPairs + 1] = bufO[warp];
     unsigned long long* mk = smsk[warp];
     const int p = lane;
-    float sL = 0.f, cL = 0.f, sR = 0.f, cR = 0.f, sM = 0.f, cM = 0.f;
+    float sL = 0.f, sR = 0.f, sM = 0.f;
     // pass 0 centre; 1, 2 the right and left cut-off edges; then the right and left
     // positions of each breakpoint. The mechanism sits at c + off; positions of c + off
     // within reach of the tile can give panels of it.
@@ -1653,7 +1672,7 @@ __global__ void __launch_bounds__(kCWarps * 32, 6)
                 if (run_chi) v *= ct.value(j, nx.absd(jf, s - 1));
               } else if (use_chi) {
                 if (pass > 2)
-                  v *= ct.value(j, nx.absd(jf, s - 1));
+                  v *= ct.value_sel(j, nx.absd(jf, s - 1));
                 else if (pass > 0 && eb > 0)
                   v *= eC * __expf(-er * nx.absd(jf, s - 1));
               }
@@ -1667,16 +1686,18 @@ __global__ void __launch_bounds__(kCWarps * 32, 6)
         mk[lane] = own;
         __syncwarp();
         uint32_t mine = warp_transpose32(tev, lane);
+        // plain FP32 sums: a pair of grids 8..10 gathers a few dozen values at most, so
+        // that the rounding error stays below 4e-6 relative
         while (mine) {
           const int t = __ffs(mine) - 1;
           mine &= mine - 1;
           const uint64_t m2 = mk[t];
           const float v0 = bE[t][p];
           if ((m2 >> (p + 1)) & 1ull) {
-            kahan_add(sL, cL, v0);
-            kahan_add(sM, cM, bO[t][p]);
+            sL += v0;
+            sM += bO[t][p];
           }
-          if ((m2 >> p) & 1ull) kahan_add(sR, cR, v0);
+          if ((m2 >> p) & 1ull) sR += v0;
         }
         __syncwarp();
       }
@@ -1685,10 +1706,10 @@ __global__ void __launch_bounds__(kCWarps * 32, 6)
     const int64_t np = R.npan[g];
     const int64_t m = m0 + p;
     if (m <= m_last && MARFA_DCHECK(m >= m_first, 104)) {
-      gp[m - m_first] = sL + cL;
-      gp[np + (m - m_first)] = sM + cM;
+      gp[m - m_first] = sL;
+      gp[np + (m - m_first)] = sM;
     }
-    if (m - 1 >= m_first && m - 1 <= m_last) gp[2 * np + (m - 1 - m_first)] = sR + cR;
+    if (m - 1 >= m_first && m - 1 <= m_last) gp[2 * np + (m - 1 - m_first)] = sR;
   }
   if (COUNT) block_counts<kCWarps>(nev, 0, nnear, nmid, nsmall, sCnt, counts);
 }
@@ -2566,9 +2587,12 @@ __global__ void __launch_bounds__(kFineThreads, 4)
         if (e >= J) continue;
         const int job = jobs[e];
         const int li = job >> 4;
-        const int j = 8 * (job & 15) + t8;
+        const int jn = 8 * (job & 15) + t8;
         const FineLine fl = sL[warp][li];
-        if (j < fl.klo || j > fl.khi) continue;
+        // a lane outside the line's nodes evaluates its group's nearest node (the same
+        // branch of the Voigt function: no divergence) and adds zero to its own node
+        const bool inr = jn >= fl.klo && jn <= fl.khi;
+        const int j = min(max(jn, fl.klo), fl.khi);
         const float jf = (float)j;
         const float xv = fmaf(jf + fl.qf, fl.hs, fl.phs);
         float v = fl.amp * (voigt ? voigt_K<true, false, true>(xv, fl.y, stab) : shape_f(R.shape, xv, fl.y));
@@ -2576,11 +2600,11 @@ __global__ void __launch_bounds__(kFineThreads, 4)
           const FineChi16 fc = sC[warp][li];
           if (fc.on) {
             const ChiThr ct{fc.r3, fc.r150, fc.r300, fc.l3, fc.l150, fc.l300};
-            v *= ct.value(j, fabsf((jf + fl.qf) + fl.phi) * ldexpf(1.0f, -kFineBits));
+            v *= ct.value_sel(j, fabsf((jf + fl.qf) + fl.phi) * ldexpf(1.0f, -kFineBits));
           }
         }
-        if (MARFA_DCHECK(j >= 0 && j < kWarpNodes, 202)) acc[j] += v;
-        count_eval<COUNT>(voigt, xv, fl.y, nev, nnear, nmid, nsmall);
+        if (MARFA_DCHECK(jn >= 0 && jn < kWarpNodes, 202)) acc[jn] += inr ? v : 0.0f;
+        if (inr) count_eval<COUNT>(voigt, xv, fl.y, nev, nnear, nmid, nsmall);
       }
       __syncwarp();
     }

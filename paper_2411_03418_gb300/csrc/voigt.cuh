@@ -70,7 +70,8 @@ __device__ __forceinline__ float voigt_asym(float x, float y) {
 // One bivariate cell; tab is the coefficient table, either the global copy (read
 // through the read-only cache) or a copy a kernel placed in shared memory (SMEM). Cells
 // are padded to an even number of floats (81 -> 82); the shared copy is read as float2
-// (vector loads through the read-only cache cost the global readers registers).
+// (vector loads through the read-only cache cost the global readers registers, and
+// float4 reads of these 81-term cells make the finest-grid kernels spill).
 constexpr int kVoigtCellFloats = (VOIGT_DEG + 1) * (VOIGT_DEG + 1);
 constexpr int kVoigtCellStride = VOIGT_CELL_STRIDE;
 static_assert(kVoigtCellStride % 2 == 0 && kVoigtCellStride >= kVoigtCellFloats, "cell padding");
@@ -109,14 +110,14 @@ __device__ __forceinline__ float voigt_cell(const float* tab, int cell, float u,
   return acc;
 }
 
-// A kernel's shared copy pads each small-y cell from 24 to 26 floats: cells a and b
-// then share a bank at the same coefficient only when a - b is a multiple of 16 (with
-// 24 floats, a multiple of 4), so the lane groups of a warp step that read different
-// cells rarely conflict.
-constexpr int kVoigtSmallCellSmem = 26;
+// A kernel's shared copy pads each small-y cell from 24 to 28 floats: every cell starts
+// on a 16-byte boundary (one float4 per row), and consecutive cells lie 28 banks apart,
+// so the cells that the eight lanes of one 128-bit load phase read (one lane group's
+// neighbouring nodes: up to eight consecutive cells) fall on disjoint banks.
+constexpr int kVoigtSmallCellSmem = 28;
 
 // One small-y cell (degree VOIGT_SMALL_DX in u, VOIGT_SMALL_DV = 3 in v: one row of four
-// coefficients per power of u, read from a shared copy as two float2).
+// coefficients per power of u, read from a shared copy as one float4).
 template <bool SMEM>
 __device__ __forceinline__ float voigt_cell_small(const float* tab, int cell, float u, float v) {
   static_assert(VOIGT_SMALL_DV == 3, "four coefficients per row");
@@ -132,19 +133,18 @@ __device__ __forceinline__ float voigt_cell_small(const float* tab, int cell, fl
     }
     return acc;
   }
-  const float2* c2 = reinterpret_cast<const float2*>(tab + cell * kVoigtSmallCellSmem);
+  const float4* c4 = reinterpret_cast<const float4*>(tab + cell * kVoigtSmallCellSmem);
   float acc = 0.0f;
 #pragma unroll
   for (int p = VOIGT_SMALL_DX; p >= 0; --p) {
-    const float2 hi = c2[2 * p + 1];
-    const float2 lo = c2[2 * p];
-    acc = fmaf(acc, u, fmaf(fmaf(fmaf(hi.y, v, hi.x), v, lo.y), v, lo.x));
+    const float4 t = c4[p];
+    acc = fmaf(acc, u, fmaf(fmaf(fmaf(t.w, v, t.z), v, t.y), v, t.x));
   }
   return acc;
 }
 
-// Floats of the large table; the small-y table follows it in a kernel's shared copy.
-constexpr int kVoigtBigFloats = VOIGT_NCELL * kVoigtCellStride;
+// Floats of the large table in a kernel's shared copy; the small-y table follows it.
+constexpr int kVoigtBigSmem = VOIGT_NCELL * kVoigtCellStride;
 
 // Far-wing form (|z| >= 100): two terms of the series, K = y/(sqrt(pi) r^2) (1 + (3x^2 - y^2)/(2 r^4)).
 __device__ __forceinline__ float voigt_far(float x, float y) {
@@ -163,7 +163,7 @@ __device__ __forceinline__ float voigt_near_body(float ax, float y, const float*
     const int ci = min((int)(ax * 4.0f), VOIGT_SMALL_NX - 1);
     const float u = (ax - (0.25f * ci + 0.125f)) * 8.0f;
     const float v = fmaf(32.0f * y, y, -1.0f);
-    const float ps = voigt_cell_small<SMEM>(SMEM ? tab + kVoigtBigFloats : kVoigtSmall, ci, u, v);
+    const float ps = voigt_cell_small<SMEM>(SMEM ? tab + kVoigtBigSmem : kVoigtSmall, ci, u, v);
     const float gt = ax < 6.5f ? gauss_term(ax, y) : 0.0f;
     return gt - kTwoOverSqrtPi * y * ps;
   }
@@ -286,8 +286,9 @@ __device__ __forceinline__ int voigt_class(float x, float y) {
 }
 
 constexpr int kVoigtSmallFloats = VOIGT_SMALL_NX * (VOIGT_SMALL_DX + 1) * (VOIGT_SMALL_DV + 1);
-constexpr int kVoigtTableFloats = kVoigtBigFloats + VOIGT_SMALL_NX * kVoigtSmallCellSmem;  // shared copy
-static_assert(kVoigtSmallCellSmem % 2 == 0 && kVoigtSmallCellSmem >= (VOIGT_SMALL_DX + 1) * 4, "small cell padding");
+constexpr int kVoigtTableFloats = kVoigtBigSmem + VOIGT_SMALL_NX * kVoigtSmallCellSmem;  // shared copy
+static_assert(kVoigtSmallCellSmem % 4 == 0 && kVoigtSmallCellSmem >= (VOIGT_SMALL_DX + 1) * 4, "small cell padding");
+static_assert(kVoigtBigSmem % 4 == 0, "the small-y table starts on a 16-byte boundary");
 
 // Copy both coefficient tables into shared memory (all threads of the block take part:
 // warp w copies cells w, w + nwarps, ..., lane by lane, in the global layout; then the
@@ -303,7 +304,7 @@ __device__ __forceinline__ void voigt_table_to_smem(float* dst) {
   constexpr int cf = (VOIGT_SMALL_DX + 1) * 4;  // floats of a small-y cell
   for (int i = threadIdx.x; i < VOIGT_SMALL_NX * kVoigtSmallCellSmem; i += blockDim.x) {
     const int cell = i / kVoigtSmallCellSmem, k = i - cell * kVoigtSmallCellSmem;
-    dst[kVoigtBigFloats + i] = k < cf ? kVoigtSmall[cell * cf + k] : 0.0f;
+    dst[kVoigtBigSmem + i] = k < cf ? kVoigtSmall[cell * cf + k] : 0.0f;
   }
 }
 
