@@ -2543,7 +2543,7 @@ __global__ void __launch_bounds__(kFineThreads, 4)
         fl.phs = nx.phs;
         fl.phi = nx.phi;
         sL[warp][lane] = fl;
-        FineChi16 fc;
+        FineChi16 fc{};  // thresholds 0 where chi is off (read, then not used)
         fc.on = chi && physical && !(MECH && pass == 0);
         fc.pad = 0;
         if (fc.on) {
@@ -2597,11 +2597,11 @@ __global__ void __launch_bounds__(kFineThreads, 4)
         const float xv = fmaf(jf + fl.qf, fl.hs, fl.phs);
         float v = fl.amp * (voigt ? voigt_K<true, false, true>(xv, fl.y, stab) : shape_f(R.shape, xv, fl.y));
         if (!(MECH && pass == 0)) {  // chi = 1 in the centre region
+          // the chi factor by select (the groups of a step take different lines)
           const FineChi16 fc = sC[warp][li];
-          if (fc.on) {
-            const ChiThr ct{fc.r3, fc.r150, fc.r300, fc.l3, fc.l150, fc.l300};
-            v *= ct.value_sel(j, fabsf((jf + fl.qf) + fl.phi) * ldexpf(1.0f, -kFineBits));
-          }
+          const ChiThr ct{fc.r3, fc.r150, fc.r300, fc.l3, fc.l150, fc.l300};
+          const float cv = ct.value_sel(j, fabsf((jf + fl.qf) + fl.phi) * ldexpf(1.0f, -kFineBits));
+          v *= fc.on ? cv : 1.0f;
         }
         if (MARFA_DCHECK(jn >= 0 && jn < kWarpNodes, 202)) acc[jn] += inr ? v : 0.0f;
         if (inr) count_eval<COUNT>(voigt, xv, fl.y, nev, nnear, nmid, nsmall);
