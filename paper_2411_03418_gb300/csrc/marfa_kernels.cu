@@ -1653,7 +1653,17 @@ __global__ void __launch_bounds__(kCWarps * 32, 6)
           nx.init(X0 - c, s - 1, sx);
           const bool use_chi = chi && physical;
           ChiThr ct;
-          if (use_chi && (MERGED || pass > 2)) ct.init(c, X0, s - 1);
+          if (use_chi && MERGED) ct.init(c, X0, s - 1);
+          // a breakpoint pass: near the lane's nodes the chi branch changes only at this
+          // breakpoint (kb, on the right of the centre when kr), so one threshold of
+          // ChiThr decides it (the same index and rounding)
+          const int kb = (pass - 3) >> 1;
+          const bool kr = pass & 1;
+          int kthr = 0;
+          if (!MERGED && use_chi && pass > 2) {
+            const int64_t rel = c + (kr ? chi_break_fx(kb) : -chi_break_fx(kb)) - X0;
+            kthr = clamp32((kr == (kb == 0)) ? cl_sh(rel, s - 1) : fl_sh(rel, s - 1));
+          }
           // runs of owned panels: bits [ba, be] give nodes [2 ba - 2, 2 be] of the tile
           for (uint64_t rest = own; rest;) {
             const int ba = __ffsll((long long)rest) - 1;
@@ -1671,8 +1681,14 @@ __global__ void __launch_bounds__(kCWarps * 32, 6)
               if (MERGED) {
                 if (run_chi) v *= ct.value(j, nx.absd(jf, s - 1));
               } else if (use_chi) {
-                if (pass > 2)
-                  v *= ct.value_sel(j, nx.absd(jf, s - 1));
+                if (pass > 2) {
+                  const bool beyond = kr ? (kb == 0 ? j >= kthr : j > kthr) : (kb == 0 ? j <= kthr : j < kthr);
+                  const int br = kb + (beyond ? 1 : 0);
+                  const float C = br == 1 ? 1.084f : (br == 2 ? 0.208f : 0.025f);
+                  const float r = br == 1 ? 0.027f : (br == 2 ? 0.016f : 0.009f);
+                  const float e = C * __expf(-r * nx.absd(jf, s - 1));
+                  v *= br == 0 ? 1.0f : e;
+                }
                 else if (pass > 0 && eb > 0)
                   v *= eC * __expf(-er * nx.absd(jf, s - 1));
               }
