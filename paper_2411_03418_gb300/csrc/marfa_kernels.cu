@@ -1677,7 +1677,7 @@ __global__ void __launch_bounds__(kCWarps * 32, 6)
             for (int j = ja; j <= jb; ++j) {
               const float jf = (float)j;
               const float xv = nx.x(jf);
-              float v = amp * (voigt ? voigt_K<false, false, true>(xv, y, kVoigtCells) : shape_f(R.shape, xv, y));
+              float v = amp * (voigt ? voigt_K<false, false, true, true>(xv, y, kVoigtCells) : shape_f(R.shape, xv, y));
               if (MERGED) {
                 if (run_chi) v *= ct.value(j, nx.absd(jf, s - 1));
               } else if (use_chi) {

@@ -76,9 +76,9 @@ constexpr int kVoigtCellFloats = (VOIGT_DEG + 1) * (VOIGT_DEG + 1);
 constexpr int kVoigtCellStride = VOIGT_CELL_STRIDE;
 static_assert(kVoigtCellStride % 2 == 0 && kVoigtCellStride >= kVoigtCellFloats, "cell padding");
 
-template <bool SMEM>
+template <bool SMEM, bool VEC = false>
 __device__ __forceinline__ float voigt_cell(const float* tab, int cell, float u, float v) {
-  if (!SMEM) {  // global copy: scalar loads through the read-only cache
+  if (!SMEM && !VEC) {  // global copy: scalar loads through the read-only cache
     const float* c = tab + cell * kVoigtCellStride;
     float acc = 0.0f;
 #pragma unroll
@@ -87,6 +87,25 @@ __device__ __forceinline__ float voigt_cell(const float* tab, int cell, float u,
 #pragma unroll
       for (int q = VOIGT_DEG; q >= 0; --q) r = fmaf(r, v, __ldg(c + p * (VOIGT_DEG + 1) + q));
       acc = fmaf(acc, u, r);
+    }
+    return acc;
+  }
+  if (!SMEM) {  // global copy, VEC: float2 loads through the read-only cache
+    const float2* c2 = reinterpret_cast<const float2*>(tab + cell * kVoigtCellStride);
+    float acc = 0.0f, r = 0.0f;
+#pragma unroll
+    for (int i = kVoigtCellStride / 2 - 1; i >= 0; --i) {
+      const float2 t = __ldg(c2 + i);
+#pragma unroll
+      for (int h = 1; h >= 0; --h) {
+        const int k = 2 * i + h;
+        if (k >= kVoigtCellFloats) continue;
+        r = fmaf(r, v, h ? t.y : t.x);
+        if (k % (VOIGT_DEG + 1) == 0) {  // q = 0: row p done
+          acc = fmaf(acc, u, r);
+          r = 0.0f;
+        }
+      }
     }
     return acc;
   }
@@ -118,10 +137,10 @@ constexpr int kVoigtSmallCellSmem = 28;
 
 // One small-y cell (degree VOIGT_SMALL_DX in u, VOIGT_SMALL_DV = 3 in v: one row of four
 // coefficients per power of u, read from a shared copy as one float4).
-template <bool SMEM>
+template <bool SMEM, bool VEC = false>
 __device__ __forceinline__ float voigt_cell_small(const float* tab, int cell, float u, float v) {
   static_assert(VOIGT_SMALL_DV == 3, "four coefficients per row");
-  if (!SMEM) {  // global copy: scalar loads through the read-only cache
+  if (!SMEM && !VEC) {  // global copy: scalar loads through the read-only cache
     const float* c = tab + cell * (VOIGT_SMALL_DX + 1) * 4;
     float acc = 0.0f;
 #pragma unroll
@@ -130,6 +149,16 @@ __device__ __forceinline__ float voigt_cell_small(const float* tab, int cell, fl
 #pragma unroll
       for (int q = 3; q >= 0; --q) r = fmaf(r, v, __ldg(c + p * 4 + q));
       acc = fmaf(acc, u, r);
+    }
+    return acc;
+  }
+  if (!SMEM) {  // global copy, VEC: one float4 per row through the read-only cache
+    const float4* c4 = reinterpret_cast<const float4*>(tab + cell * (VOIGT_SMALL_DX + 1) * 4);
+    float acc = 0.0f;
+#pragma unroll
+    for (int p = VOIGT_SMALL_DX; p >= 0; --p) {
+      const float4 t = __ldg(c4 + p);
+      acc = fmaf(acc, u, fmaf(fmaf(fmaf(t.w, v, t.z), v, t.y), v, t.x));
     }
     return acc;
   }
@@ -157,13 +186,13 @@ __device__ __forceinline__ float voigt_far(float x, float y) {
 // Everything but the far wing. The Dawson-table branch covers the whole near wing of
 // narrow lines (y < 1, |x| < 12) so that one line's nodes on the fine grids take a
 // single code path.
-template <bool SMEM>
+template <bool SMEM, bool VEC = false>
 __device__ __forceinline__ float voigt_near_body(float ax, float y, const float* tab) {
   if (y < 0.25f && ax < 12.0f) {
     const int ci = min((int)(ax * 4.0f), VOIGT_SMALL_NX - 1);
     const float u = (ax - (0.25f * ci + 0.125f)) * 8.0f;
     const float v = fmaf(32.0f * y, y, -1.0f);
-    const float ps = voigt_cell_small<SMEM>(SMEM ? tab + kVoigtBigSmem : kVoigtSmall, ci, u, v);
+    const float ps = voigt_cell_small<SMEM, VEC>(SMEM ? tab + kVoigtBigSmem : kVoigtSmall, ci, u, v);
     const float gt = ax < 6.5f ? gauss_term(ax, y) : 0.0f;
     return gt - kTwoOverSqrtPi * y * ps;
   }
@@ -171,7 +200,7 @@ __device__ __forceinline__ float voigt_near_body(float ax, float y, const float*
     int ci = min((int)(ax * 2.0f), VOIGT_NPSI - 1);
     float u = (ax - (0.5f * ci + 0.25f)) * 4.0f;
     float v = 2.0f * y * y - 1.0f;
-    float ps = voigt_cell<SMEM>(tab, ci, u, v);
+    float ps = voigt_cell<SMEM, VEC>(tab, ci, u, v);
     float gt = ax < 6.5f ? gauss_term(ax, y) : 0.0f;
     return gt - kTwoOverSqrtPi * y * ps;
   }
@@ -182,7 +211,7 @@ __device__ __forceinline__ float voigt_near_body(float ax, float y, const float*
   int iy = min((int)((y - 1.0f) * (1.0f / 1.75f)), 1);
   float u = (ax - (0.9f * ix + 0.45f)) * (1.0f / 0.45f);
   float v = (y - (1.0f + 1.75f * iy + 0.875f)) * (1.0f / 0.875f);
-  return voigt_cell<SMEM>(tab, VOIGT_NPSI + ix * 2 + iy, u, v);
+  return voigt_cell<SMEM, VEC>(tab, VOIGT_NPSI + ix * 2 + iy, u, v);
 }
 
 // The same out of line, so that callers with several evaluation sites stay small.
@@ -196,13 +225,15 @@ __device__ __noinline__ float voigt_K_near(float ax, float y, const float* tab) 
 // axis) instead of the six terms of voigt_K_near; it pays where most evaluations lie in
 // the mid wing (grids 2..8) and costs registers and branches elsewhere. INL: the near
 // wing inline (one evaluation site in the caller's loop) instead of a call.
-template <bool SMEM, bool MID3 = false, bool INL = false>
+// VEC (global tables only): vector loads of the cells, for a caller with the registers
+// to spare (they raise the register count of most kernels).
+template <bool SMEM, bool MID3 = false, bool INL = false, bool VEC = false>
 __device__ __forceinline__ float voigt_K(float x, float y, const float* tab) {
   float ax = fabsf(x);
   float r2 = fmaf(ax, ax, y * y);
   if (r2 >= 1.0e4f) return voigt_far(ax, y);
   if (MID3 && r2 >= 506.25f) return voigt_asym<2>(ax, y);
-  return INL ? voigt_near_body<SMEM>(ax, y, tab) : voigt_K_near<SMEM>(ax, y, tab);
+  return INL ? voigt_near_body<SMEM, VEC>(ax, y, tab) : voigt_K_near<SMEM>(ax, y, tab);
 }
 
 __device__ __forceinline__ float voigt_K(float x, float y) { return voigt_K<false>(x, y, kVoigtCells); }
