@@ -247,11 +247,20 @@ __device__ __forceinline__ int clamp32(int64_t v) {
 // chi-factor piece thresholds in node units relative to position X0, node spacing 2^sh.
 struct ChiThr {
   int r3, r150, r300, l3, l150, l300;
-  __device__ __forceinline__ void init(int64_t c, int64_t X0, int sh) {
+  // cut: the request's cut-off. The nodes a line is evaluated at lie within its cut-off
+  // (plus at most a four-step panel of grid 1); when that stays 8 cm^-1 short of the
+  // 150 cm^-1 breakpoint, the two outer thresholds on each side are never crossed and
+  // are set out of reach instead of computed.
+  __device__ __forceinline__ void init(int64_t c, int64_t X0, int sh, int64_t cut) {
     r3 = clamp32(cl_sh(c + chi_break_fx(0) - X0, sh));
+    l3 = clamp32(fl_sh(c - chi_break_fx(0) - X0, sh));
+    if (cut + (int64_t(8) << kFixBits) <= chi_break_fx(1)) {
+      r150 = r300 = 1 << 30;
+      l150 = l300 = -(1 << 30);
+      return;
+    }
     r150 = clamp32(fl_sh(c + chi_break_fx(1) - X0, sh));
     r300 = clamp32(fl_sh(c + chi_break_fx(2) - X0, sh));
-    l3 = clamp32(fl_sh(c - chi_break_fx(0) - X0, sh));
     l150 = clamp32(cl_sh(c - chi_break_fx(1) - X0, sh));
     l300 = clamp32(cl_sh(c - chi_break_fx(2) - X0, sh));
   }
@@ -594,7 +603,7 @@ __device__ __noinline__ float2 g1_exact_pair(const ReqDev& R, int64_t o, int64_t
   NodeX nx;
   nx.init(X0 - c, sh, sx);
   ChiThr ct;
-  if (use_chi) ct.init(c, X0, sh);
+  if (use_chi) ct.init(c, X0, sh, R.cut_fx);
   float v[2] = {0.0f, 0.0f};
   for (int q = 0; q < 2; ++q) {
     if (!(q ? need1 : need0)) continue;
@@ -631,7 +640,7 @@ __device__ __noinline__ G1Nodes g1_exact_nodes(const ReqDev& R, int64_t o, int64
   r.w0 = r.w1 = amp;
   if (use_chi) {
     ChiThr ct;
-    ct.init(c, X0, sh);
+    ct.init(c, X0, sh, R.cut_fx);
     r.w0 = amp * ct.value(j0, nx.absd((float)j0, sh));
     r.w1 = amp * ct.value(j0 + 1, nx.absd((float)(j0 + 1), sh));
   }
@@ -1052,7 +1061,7 @@ __global__ void __launch_bounds__(kLWarps * 32, SURR ? 3 : (PAIRS == 16 ? 7 : 4)
           amp = __ldg(R.amp + lo_off + i);
           y = __ldg(R.yv + lo_off + i);
           nx.init(X0 - c, s - 1, __ldg(R.sx + lo_off + i));
-          if (use_chi) ct.init(c, X0, s - 1);
+          if (use_chi) ct.init(c, X0, s - 1, R.cut_fx);
           pa = max(mask_lowest(own) - 1, 0);
           pb = min(mask_highest(own), PAIRS - 1);
         }
@@ -1109,7 +1118,7 @@ __global__ void __launch_bounds__(kLWarps * 32, SURR ? 3 : (PAIRS == 16 ? 7 : 4)
       nx.init(X0 - c, s - 1, sx);
       ChiThr ct;
       const bool use_chi = chi && physical;
-      if (use_chi) ct.init(c, X0, s - 1);
+      if (use_chi) ct.init(c, X0, s - 1, R.cut_fx);
       // pair p uses bits p (R slot of node 2p) and p + 1 (L of node 2p, M of node 2p+1)
       const int pa = max(mask_lowest(own) - 1, 0);
       const int pb = min(mask_highest(own), PAIRS - 1);
@@ -1356,7 +1365,7 @@ __global__ void __launch_bounds__(kCWarps * 32, SURR ? 3 : 6)
             amp = __ldg(R.amp + lo_off + i);
             y = __ldg(R.yv + lo_off + i);
             nx.init(X0 - c, s - 1, __ldg(R.sx + lo_off + i));
-            if (use_chi) ct.init(c, X0, s - 1);
+            if (use_chi) ct.init(c, X0, s - 1, R.cut_fx);
             pa = max(__ffsll((long long)own) - 2, 0);
             pb = min(63 - __clzll((long long)own), kCPairs - 1);
           }
@@ -1401,7 +1410,7 @@ __global__ void __launch_bounds__(kCWarps * 32, SURR ? 3 : 6)
           nx.init(X0 - c, s - 1, sx);
           ChiThr ct;
           const bool use_chi = chi && physical;
-          if (use_chi) ct.init(c, X0, s - 1);
+          if (use_chi) ct.init(c, X0, s - 1, R.cut_fx);
           const int pa = max(__ffsll((long long)own) - 2, 0);
           const int pb = min(63 - __clzll((long long)own), kCPairs - 1);
           // a chi branch common to all nodes 2pa .. 2pb + 1: one exponential per line
@@ -1653,7 +1662,7 @@ __global__ void __launch_bounds__(kCWarps * 32, 6)
           nx.init(X0 - c, s - 1, sx);
           const bool use_chi = chi && physical;
           ChiThr ct;
-          if (use_chi && MERGED) ct.init(c, X0, s - 1);
+          if (use_chi && MERGED) ct.init(c, X0, s - 1, R.cut_fx);
           // a breakpoint pass: near the lane's nodes the chi branch changes only at this
           // breakpoint (kb, on the right of the centre when kr), so one threshold of
           // ChiThr decides it (the same index and rounding)
@@ -1875,7 +1884,7 @@ __global__ void __launch_bounds__(kCWarps * 32)
         J.r3 = J.r150 = J.r300 = J.l3 = J.l150 = J.l300 = 0;
         if (chi && physical) {
           ChiThr ct;
-          ct.init(c, X0, s - 1);
+          ct.init(c, X0, s - 1, R.cut_fx);
           const int ja = max(__ffsll((long long)own) - 2, 0) * 2;
           const int jb = min(63 - __clzll((long long)own), kCPairs - 1) * 2 + 1;
           if (ct.uniform(ja, jb)) {
@@ -2266,7 +2275,7 @@ __global__ void __launch_bounds__(kFineThreads)
         fc.on = chi && physical;
         if (fc.on) {
           ChiThr ct;
-          ct.init(c, Xa, kFineShift);
+          ct.init(c, Xa, kFineShift, R.cut_fx);
           fc.r3 = ct.r3; fc.r150 = ct.r150; fc.r300 = ct.r300;
           fc.l3 = ct.l3; fc.l150 = ct.l150; fc.l300 = ct.l300;
           // within 3 cm^-1 of the centre at all its nodes of the warp: chi = 1 exactly
@@ -2564,7 +2573,7 @@ __global__ void __launch_bounds__(kFineThreads, 4)
         fc.pad = 0;
         if (fc.on) {
           ChiThr ct;
-          ct.init(c, Xa, kFineShift);
+          ct.init(c, Xa, kFineShift, R.cut_fx);
           fc.r3 = clamp_node16(ct.r3); fc.r150 = clamp_node16(ct.r150); fc.r300 = clamp_node16(ct.r300);
           fc.l3 = clamp_node16(ct.l3); fc.l150 = clamp_node16(ct.l150); fc.l300 = clamp_node16(ct.l300);
           if (ct.uniform(klo, khi) && ct.branch(klo) == 0) fc.on = 0;
