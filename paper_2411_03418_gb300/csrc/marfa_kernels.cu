@@ -2581,8 +2581,9 @@ __global__ void __launch_bounds__(kFineThreads, 4)
         sC[warp][lane] = fc;
         if (voigt) {
           // panels whose centre node lies in the far wing |z| >= 100: |j + q + phi| hs >= X
-          const float X = sqrtf(fmaxf(1.0e4f - fl.y * fl.y, 0.0f));
-          const float t = fminf(X / fl.hs, 1.0e6f);
+          // (the order of the job list only: approximate square root and division)
+          const float X2 = fmaxf(1.0e4f - fl.y * fl.y, 1.0e-30f);
+          const float t = fminf(__fdividef(X2 * rsqrtf(X2), fl.hs), 1.0e6f);
           const float off = 3.5f + nx.qf + nx.phi;  // centre node of panel p is 8 p + 3.5
           const int pr = (int)ceilf(fmaxf((t - off) * 0.125f, -1.0f));    // first far panel right of c
           const int pl = (int)floorf(fminf((-t - off) * 0.125f, 17.0f));  // last far panel left of c
