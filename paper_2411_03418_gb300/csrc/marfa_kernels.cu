@@ -2473,6 +2473,13 @@ __global__ void __launch_bounds__(kFineThreads, 4)
       bd.merge();
     }
     const int64_t pbase = kw >> 3;
+    // MECH = 1: the chi branch along an edge (eb), and the breakpoint of a breakpoint
+    // pass (kb, on the right of the centre when kr)
+    const int eb = (cut >= chi_break_fx(0)) + (cut > chi_break_fx(1)) + (cut > chi_break_fx(2));
+    const float eC = eb == 1 ? 1.084f : (eb == 2 ? 0.208f : 0.025f);
+    const float er = eb == 1 ? 0.027f : (eb == 2 ? 0.016f : 0.009f);
+    const int kb = (pass - 3) >> 1;
+    const bool kr = pass & 1;
     const int64_t lo_off = (int64_t)lev * R.n_lines;
     const bool physical = R.shape < kShapeConst;
     const bool voigt = R.shape == kShapeVoigt;
@@ -2571,7 +2578,13 @@ __global__ void __launch_bounds__(kFineThreads, 4)
         FineChi16 fc{};  // thresholds 0 where chi is off (read, then not used)
         fc.on = chi && physical && !(MECH && pass == 0);
         fc.pad = 0;
-        if (fc.on) {
+        if (fc.on && MECH == 1 && pass <= 2) {
+          fc.on = eb > 0;  // a cut-off edge: one branch of Eq. (10) at all its nodes
+        } else if (fc.on && MECH == 1) {
+          // a breakpoint: the branch changes only at its own threshold near these nodes
+          const int64_t rel = c + (kr ? chi_break_fx(kb) : -chi_break_fx(kb)) - Xa;
+          fc.r3 = clamp_node16(clamp32((kr == (kb == 0)) ? cl_sh(rel, kFineShift) : fl_sh(rel, kFineShift)));
+        } else if (fc.on) {
           ChiThr ct;
           ct.init(c, Xa, kFineShift, R.cut_fx);
           fc.r3 = clamp_node16(ct.r3); fc.r150 = clamp_node16(ct.r150); fc.r300 = clamp_node16(ct.r300);
@@ -2625,8 +2638,22 @@ __global__ void __launch_bounds__(kFineThreads, 4)
         if (!(MECH && pass == 0)) {  // chi = 1 in the centre region
           // the chi factor by select (the groups of a step take different lines)
           const FineChi16 fc = sC[warp][li];
-          const ChiThr ct{fc.r3, fc.r150, fc.r300, fc.l3, fc.l150, fc.l300};
-          const float cv = ct.value_sel(j, fabsf((jf + fl.qf) + fl.phi) * ldexpf(1.0f, -kFineBits));
+          const float absd = fabsf((jf + fl.qf) + fl.phi) * ldexpf(1.0f, -kFineBits);
+          float cv;
+          if (MECH == 1 && pass <= 2) {  // an edge: its one branch
+            cv = eC * __expf(-er * absd);
+          } else if (MECH == 1) {  // a breakpoint: the branch from its threshold (in r3)
+            const int kthr = fc.r3;
+            const bool beyond = kr ? (kb == 0 ? j >= kthr : j > kthr) : (kb == 0 ? j <= kthr : j < kthr);
+            const int br = kb + (beyond ? 1 : 0);
+            const float C = br == 1 ? 1.084f : (br == 2 ? 0.208f : 0.025f);
+            const float r = br == 1 ? 0.027f : (br == 2 ? 0.016f : 0.009f);
+            const float e = C * __expf(-r * absd);
+            cv = br == 0 ? 1.0f : e;
+          } else {
+            const ChiThr ct{fc.r3, fc.r150, fc.r300, fc.l3, fc.l150, fc.l300};
+            cv = ct.value_sel(j, absd);
+          }
           v *= fc.on ? cv : 1.0f;
         }
         if (MARFA_DCHECK(jn >= 0 && jn < kWarpNodes, 202)) acc[jn] += inr ? v : 0.0f;
