@@ -2592,7 +2592,11 @@ __global__ void __launch_bounds__(kFineThreads, 4)
           if (ct.uniform(klo, khi) && ct.branch(klo) == 0) fc.on = 0;
         }
         sC[warp][lane] = fc;
-        if (voigt) {
+        if (voigt && MECH == 1) {
+          // by mechanism: a core (g* = 11, within R_w h_10 of the centre) lies in the near
+          // wing, an edge or a breakpoint in the far wing (the order of the job list only)
+          far = pass == 0 ? 0u : pm;
+        } else if (voigt) {
           // panels whose centre node lies in the far wing |z| >= 100: |j + q + phi| hs >= X
           // (the order of the job list only: approximate square root and division)
           const float X2 = fmaxf(1.0e4f - fl.y * fl.y, 1.0e-30f);
