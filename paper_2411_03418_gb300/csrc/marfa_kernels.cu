@@ -247,6 +247,7 @@ __device__ __forceinline__ int clamp32(int64_t v) {
 // chi-factor piece thresholds in node units relative to position X0, node spacing 2^sh.
 struct ChiThr {
   int r3, r150, r300, l3, l150, l300;
+  bool near = false;  // only r3 and l3 can be crossed (set by init)
   // cut: the request's cut-off. The nodes a line is evaluated at lie within its cut-off
   // (plus at most a four-step panel of grid 1); when that stays 8 cm^-1 short of the
   // 150 cm^-1 breakpoint, the two outer thresholds on each side are never crossed and
@@ -254,7 +255,8 @@ struct ChiThr {
   __device__ __forceinline__ void init(int64_t c, int64_t X0, int sh, int64_t cut) {
     r3 = clamp32(cl_sh(c + chi_break_fx(0) - X0, sh));
     l3 = clamp32(fl_sh(c - chi_break_fx(0) - X0, sh));
-    if (cut + (int64_t(8) << kFixBits) <= chi_break_fx(1)) {
+    near = cut + (int64_t(8) << kFixBits) <= chi_break_fx(1);
+    if (near) {
       r150 = r300 = 1 << 30;
       l150 = l300 = -(1 << 30);
       return;
@@ -265,12 +267,14 @@ struct ChiThr {
     l300 = clamp32(cl_sh(c - chi_break_fx(2) - X0, sh));
   }
   __device__ __forceinline__ int branch(int j) const {
+    if (near) return (j >= r3) + (j <= l3);
     return (j >= r3) + (j > r150) + (j > r300) + (j <= l3) + (j < l150) + (j < l300);
   }
   // The branch is the same at every node of [ja, jb] (it changes only at j = r3,
   // r150 + 1, r300 + 1, l3 + 1, l150, l300).
   __device__ __forceinline__ bool uniform(int ja, int jb) const {
     auto in = [&](int t) { return t > ja && t <= jb; };
+    if (near) return !(in(r3) || in(l3 + 1));
     return !(in(r3) || in(r150 + 1) || in(r300 + 1) || in(l3 + 1) || in(l150) || in(l300));
   }
   // Eq. (10): 1 below 3 cm^-1; 1.084 e^{-0.027|d|} on [3, 150]; 0.208 e^{-0.016|d|} on
