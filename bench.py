@@ -53,9 +53,9 @@ FLOPS_FAR, FLOPS_MID, FLOPS_NEAR, FLOPS_SMALL = 20.0, 70.0, 200.0, 90.0
 # profiles/traffic_dominant_kernels.md). Finest-grid variants: 1 flattened jobs, 2 the
 # same by mechanism, 3 by mechanism merged. They belong to the kernels as built when
 # captured; other workloads, windows and variants report null.
-TRAFFIC_BYTES = {("venus", "finest", 1): 653.5e6 + 621.9e6,
-                 ("venus", "finest", 2): 641.5e6 + 459.7e6,
-                 ("venus", "finest", 3): 643.5e6 + 465.4e6}
+TRAFFIC_BYTES = {("venus", "finest", 1): 653.5e6 + 620.3e6,
+                 ("venus", "finest", 2): 642.0e6 + 459.9e6,
+                 ("venus", "finest", 3): 642.9e6 + 465.0e6}
 N_SM = 152
 FP32_LANES = 128
 
