@@ -75,20 +75,42 @@ def start_clock_sampler(path):
             ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-             "--format=csv,noheader,nounits", "-lms", "200"], stdout=f, stderr=subprocess.DEVNULL), f
+             "--format=csv,noheader,nounits", "-lms", "50"], stdout=f, stderr=subprocess.DEVNULL), f
     except (OSError, FileNotFoundError):
         return None, None
 
 
-def read_clocks(path, dev_index):
+def sampler_lines(path, wait_s=0.0):
+    """Lines the clock sampler has written so far; with wait_s, first wait (at most that
+    long) until it has written one, so that the timed region starts with the sampler
+    running."""
+    t_end = time.perf_counter() + wait_s
+    while True:
+        try:
+            with open(path) as f:
+                n = sum(1 for _ in f)
+        except OSError:
+            n = 0
+        if n > 0 or time.perf_counter() >= t_end:
+            return n
+        time.sleep(0.01)
+
+
+def read_clocks(path, dev_index, skip=0):
+    """Median SM clock, max clock and throttle reasons of the sampler's rows for this
+    device, leaving out the first `skip` lines (written before the timed region) when
+    rows remain after them."""
     rows = []
     try:
-        for line in open(path):
+        for k, line in enumerate(open(path)):
             parts = [x.strip() for x in line.split(",")]
             if len(parts) >= 9 and parts[0] == str(dev_index):
-                rows.append(parts)
+                rows.append((k, parts))
     except OSError:
         return None
+    if any(k >= skip for k, _ in rows):
+        rows = [r for r in rows if r[0] >= skip]
+    rows = [r for _, r in rows]
     if not rows:
         return None
     sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
@@ -410,6 +432,7 @@ def main():
 
     clk_path = os.path.join(tempfile.gettempdir(), f"marfa_clocks_{os.getpid()}.csv")
     sampler, fh = start_clock_sampler(clk_path)
+    n_before = sampler_lines(clk_path, 5.0) if sampler else 0
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     torch.cuda.synchronize()
     for i in range(args.steps):
@@ -424,7 +447,7 @@ def main():
         sampler.terminate()
         sampler.wait()
         fh.close()
-    clocks = read_clocks(clk_path, torch.cuda.current_device()) if sampler else None
+    clocks = read_clocks(clk_path, torch.cuda.current_device(), n_before) if sampler else None
     t_total = max_over_ranks(float(sum(step_ms)) / 1e3, dist, dev)
     ms_per_step = t_total / args.steps * 1e3
     M.marfa_plan_destroy(plan)
