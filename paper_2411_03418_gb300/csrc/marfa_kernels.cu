@@ -248,10 +248,10 @@ __device__ __forceinline__ int clamp32(int64_t v) {
 struct ChiThr {
   int r3, r150, r300, l3, l150, l300;
   bool near = false;  // only r3 and l3 can be crossed (set by init)
-  // cut: the request's cut-off. The nodes a line is evaluated at lie within its cut-off
-  // (plus at most a four-step panel of grid 1); when that stays 8 cm^-1 short of the
-  // 150 cm^-1 breakpoint, the two outer thresholds on each side are never crossed and
-  // are set out of reach instead of computed.
+  // cut: the request's cut-off. The nodes a line contributes to lie within its cut-off
+  // (an owned panel lies wholly inside it); when the cut-off stays short of the 150 cm^-1
+  // breakpoint (by a margin of 8 cm^-1), the two outer thresholds on each side are never
+  // crossed and are set out of reach instead of computed.
   __device__ __forceinline__ void init(int64_t c, int64_t X0, int sh, int64_t cut) {
     r3 = clamp32(cl_sh(c + chi_break_fx(0) - X0, sh));
     l3 = clamp32(fl_sh(c - chi_break_fx(0) - X0, sh));
