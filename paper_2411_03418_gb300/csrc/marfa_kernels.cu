@@ -471,6 +471,28 @@ static void launch_surr(void (*k)(KA...), int n_items, int threads, cudaStream_t
 
 // ------------------------------------------------------------------ K1: level prep
 // The per-(level, line) data of line i at level lev.
+// rint(t 2^43) (round half to even) for a finite double t, from its bits: |t| 2^43 =
+// m 2^(e - 9) with m the 53-bit significand and e the unbiased exponent, so the product
+// is exact and only a right shift rounds. Equal to __double2ll_rn(t * 2^43) for every
+// finite t with |t| 2^43 < 2^62, without instructions of the FP64 pipe.
+__device__ __forceinline__ int64_t fix43_rint(double t) {
+  const uint64_t b = (uint64_t)__double_as_longlong(t);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex == 0) return 0;  // zero or subnormal: |t| 2^43 < 2^-979
+  const uint64_t m = (b & ((uint64_t(1) << 52) - 1)) | (uint64_t(1) << 52);
+  const int sh = ex - 1023 - 9;
+  uint64_t q = 0;
+  if (sh >= 0) {
+    q = m << sh;
+  } else if (sh >= -53) {
+    const int k = -sh;
+    q = m >> k;
+    const uint64_t r = m & ((uint64_t(1) << k) - 1), half = uint64_t(1) << (k - 1);
+    q += (r > half || (r == half && (q & 1))) ? 1 : 0;
+  }  // else |t| 2^43 < 1/2
+  return (b >> 63) ? -(int64_t)q : (int64_t)q;
+}
+
 __device__ __forceinline__ void level_prep_pair(const PrepArgs& a, int64_t i, int lev) {
   const LevelDev L = a.lev[lev];
   const int s = a.species[i];
@@ -480,9 +502,10 @@ __device__ __forceinline__ void level_prep_pair(const PrepArgs& a, int64_t i, in
               da = a.da[i];
   const int64_t o = (int64_t)lev * a.n + i;
 
-  // centre: rint((nu0 + delta p) 2^43), FP64, no contraction (identical on the host)
+  // centre: rint((nu0 + delta p) 2^43), FP64, no contraction (identical on the host);
+  // the scaling by 2^43 and the rounding to an integer from the bits of the sum
   const double nt = __dadd_rn(nu0, __dmul_rn((double)da, L.p));
-  a.c[o] = __double2ll_rn(__dmul_rn(nt, kFix));
+  a.c[o] = fix43_rint(nt);
 
   // widths and intensity in FP32 (Sec. 2.2)
   const float gL = exp2f(na * L.log2_ratio) * fmaf(ga, L.pf - LS.ps, gs * LS.ps);
